@@ -1,0 +1,352 @@
+"""Benchmark of the SPH hot path on GB300 (one JSON line on stdout).
+
+Workload: the Sedov-Taylor blast of the paper's test suite (Sec. 3.3) on a
+64^3 = 262,144-particle jittered periodic lattice, Wendland C2 with 64
+neighbours, alpha = 1, beta = 2, gamma = 5/3, starting at t = 0.  One step =
+sph_step: Morton sort + bounds tree, density/h Newton pass, force pass,
+kick-drift-kick with the Courant step (every row of the hot path), plus the
+conserved-totals reduction.
+
+  value       particle-steps/s with the state resident in HBM; each timed step
+              is bracketed by CUDA events on the launch stream, and a 256 MiB
+              buffer is written between steps so no step starts with a warm L2
+  e2e         the same metric through sph_step_host: pinned host arrays copied
+              to the device, stepped, and copied back inside the timed region
+  roofline    the dominant pair kernel against the FP32 pipe peak
+              (152 SMs x 128 lanes x 2 flop x 2.07 GHz), algorithmic flops only
+  cpu_baseline the FP64 oracle on a bounded sample of the same state
+
+--impl reference times the oracle (the deliberately slow FP64 brute force)
+on the same workload and metric.  Under torchrun every rank runs its own
+independent replica (weak scaling, no data exchange); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_GHZ = 2.070
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
+# algorithmic flops (FMA = 2) per unit, counted from the kernels' inner loops
+FLOPS_DENSITY_PAIR = 26      # one useful (r < h) pair evaluation of one Newton pass
+FLOPS_FORCE_PAIR = 56        # one unordered pair, pressure terms, both sides
+FLOPS_FORCE_AV = 25          # extra flops of a pair with active viscosity
+METRIC = "SPH particle-steps/s"
+UNIT = "particle-steps/s"
+
+
+def _workload(rank=0):
+    from paper_2511_11425_gb300 import inputs
+    return inputs.sedov(n=64, seed=2511 + rank)
+
+
+def _config(prob, extra=None):
+    c = {"workload": "sedov_taylor_64^3 (262,144 particles, periodic unit box, t from 0)",
+         "particles": prob.n, "kernel": "wendland_c2", "n_ngb": 64, "gamma": prob.gamma,
+         "alpha": prob.alpha, "beta": prob.beta,
+         "precision": "fp32 pair arithmetic on cell-relative offsets, fp64 positions and "
+                      "kick-drift-kick",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except (ValueError, IndexError):
+                continue
+            for k, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_for(kernel_file, kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = open(os.path.join(ROOT, "paper_2511_11425_gb300", "csrc", kernel_file), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha"):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(prob, target_s=15.0):
+    """The oracle as it stands on this host: density (Newton, brute force over
+    all N) + forces for a sample of sink particles; particle-steps/s."""
+    import oracle
+    from oracle import build as obuild
+    obuild.build()
+    p = oracle.Params(gamma=prob.gamma, alpha=prob.alpha, beta=prob.beta,
+                      box_lo=prob.box_lo, box_hi=prob.box_hi, periodic=prob.periodic)
+    rng = np.random.default_rng(0)
+
+    def run(S):
+        sinks = rng.choice(prob.n, size=S, replace=False)
+        t0 = time.perf_counter()
+        d = oracle.density_h(p, prob.pos, prob.m, prob.h0, sinks)
+        h = np.array(prob.h0, dtype=np.float64)
+        rho = np.ones(prob.n)
+        om = np.ones(prob.n)
+        h[sinks], rho[sinks], om[sinks] = d["h"], d["rho"], d["omega"]
+        oracle.forces(p, prob.pos, prob.vel, prob.m, h, rho, om, prob.u, sinks)
+        return time.perf_counter() - t0
+
+    t = run(64)
+    S = int(min(16384, max(64, 64 * target_s / max(t, 1e-3))))
+    t = run(S)
+    cores = int(oracle.lib().orc_num_threads())
+    return {"value": S / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d random sink particles of the t=0 state: Newton density (seeded from "
+                      "the lattice h) and forces, each brute force over all %d particles in "
+                      "FP64; %.1f s" % (S, prob.n, t)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    prob = _workload(0)
+    import oracle
+    from oracle import build as obuild
+    obuild.build()
+    p = oracle.Params(gamma=prob.gamma, alpha=prob.alpha, beta=prob.beta,
+                      box_lo=prob.box_lo, box_hi=prob.box_hi, periodic=prob.periodic)
+    rng = np.random.default_rng(1)
+    S = 512
+
+    def one_step():
+        sinks = rng.choice(prob.n, size=S, replace=False)
+        t0 = time.perf_counter()
+        d = oracle.density_h(p, prob.pos, prob.m, prob.h0, sinks)
+        h = np.array(prob.h0, dtype=np.float64)
+        h[sinks] = d["h"]
+        rho = np.ones(prob.n)
+        om = np.ones(prob.n)
+        rho[sinks], om[sinks] = d["rho"], d["omega"]
+        oracle.forces(p, prob.pos, prob.vel, prob.m, h, rho, om, prob.u, sinks)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one_step()
+    tot = sum(one_step() for _ in range(args.steps))
+    value = S * args.steps / tot
+    cores = int(oracle.lib().orc_num_threads())
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(prob, {"sample_per_step": S}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: %d random sinks of the t=0 state, density "
+                                       "Newton + forces, brute force over all particles" % S},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2511_11425_gb300 as sph
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    sph.lib()
+    prob = _workload(rank)
+    s = torch.cuda.current_stream(dev)
+    sim = sph.Simulation(prob, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def step():
+        dt = sph.sph_step(sim.ctx, sim.parts, 0.0, s)
+        sph.sph_reduce_conserved(sim.ctx, sim.parts, s)
+        return dt
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    st0 = sph.sph_get_stats(sim.ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kd = kf = 0.0
+    dpairs = fpairs = fav = 0
+    t_sim = 0.0
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(s)
+            t_sim += step()
+            ev[k][1].record(s)
+            st = sph.sph_get_stats(sim.ctx)
+            kd += st["ms_density_kernel"]
+            kf += st["ms_force_kernel"]
+            dpairs += st["density_pairs"]
+            fpairs += st["force_pairs"]
+            fav += st["force_av_pairs"]
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    st1 = sph.sph_get_stats(sim.ctx)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    tmax = ms
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    value = world * prob.n * args.steps / (tmax / 1000.0)
+    launches = int(st1["launches"] - st0["launches"])
+
+    # roofline of the dominant pair kernel
+    flop_d = FLOPS_DENSITY_PAIR * dpairs
+    flop_f = FLOPS_FORCE_PAIR * fpairs + FLOPS_FORCE_AV * fav
+    rd = {"kernel": "k_density", "bound": "alu", "achieved": flop_d / (kd * 1e-3) / 1e12,
+          "ms_per_launch": kd / args.steps}
+    rf = {"kernel": "k_forces", "bound": "alu", "achieved": flop_f / (kf * 1e-3) / 1e12,
+          "ms_per_launch": kf / args.steps}
+    dom, other = (rd, rf) if kd >= kf else (rf, rd)
+    dom_file = "sph_density.cu" if dom is rd else "sph_forces.cu"
+    roof = {"bound": "alu", "achieved": dom["achieved"], "peak": FP32_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": dom["achieved"] / FP32_PEAK_TFLOPS,
+            "traffic": _traffic_for(dom_file, dom["kernel"]), "kernel": dom["kernel"],
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+            "ms_per_launch": dom["ms_per_launch"]}
+    other_line = {**other, "frac": other["achieved"] / FP32_PEAK_TFLOPS}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        prob2 = _workload(rank)
+        host = sph.Particles.from_problem(prob2, "cpu", pin=True)
+        ctx2 = sph.sph_create(sph.Params.for_problem(prob2), prob2.n)
+        try:
+            for _ in range(min(args.warmup, 3)):
+                sph.sph_step_host(ctx2, host, 0.0, s)
+            tt = 0.0
+            hb = db = 0
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                _, hb, db = sph.sph_step_host(ctx2, host, 0.0, s)
+                tt += time.perf_counter() - t0
+        finally:
+            sph.sph_destroy(ctx2)
+        e2e = {"value": world * prob2.n * args.steps / tt, "unit": UNIT,
+               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+    if rank == 0:
+        secs = tmax / 1000.0
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": _config(prob, {"sim_time_covered": t_sim,
+                                         "parallelism": "replicas" if world > 1 else "single"}),
+                "pair_interactions_per_s": {
+                    "density": world * dpairs / secs, "force": world * fpairs / secs,
+                    "total": world * (dpairs + fpairs) / secs},
+                "roofline": roof, "roofline_other": other_line, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
+                "impl": "ours"}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+        try:
+            return run_ours(args, rank, world, local_rank)
+        finally:
+            dist.destroy_process_group()
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,255 @@
+/*
+ * sph.h -- C ABI of the GB300 SPH hot path (libsph).
+ *
+ * The library implements one global time step of the SPH method of
+ * Meier, Potter, Reinhardt & Stadel, "Smoothed Particle Hydrodynamics in
+ * pkdgrav3 for Shock Physics Simulations. I. Hydrodynamics" (arXiv:2511.11425),
+ * for ideal gases without gravity, on one GPU:
+ *
+ *   sph_build_cells       Morton sort + bucket bounds (Sec. 2.1 tree order,
+ *                         Sec. 2.3.2 cell bounds and box-of-balls bounds)
+ *   sph_density_h         rho_i = sum_j m_j W_ij(h_i) (Eq. Density_estimate) with
+ *                         h_i from Newton-Raphson on the constant kernel mass
+ *                         4/3 pi h_i^3 rho_i = N_ngb m_i, and the grad-h term
+ *                         Omega_i (Sec. 2.3.3)
+ *   sph_forces            predictor + ideal-gas EOS (Sec. 2.3.6 step 2,
+ *                         Sec. 2.3.1), momentum / PdV / Monaghan viscosity
+ *                         equations (Sec. 2.3.5, Eq. AV_heating) and the
+ *                         per-particle time-step criteria (Sec. 2.3.6,
+ *                         Eq. courant_condition)
+ *   sph_kdk_step          closing kick, global step choice, opening kick and
+ *                         drift (Sec. 2.3.6 steps 4-5, one global step size)
+ *   sph_reduce_conserved  mass, momentum, angular momentum, kinetic and
+ *                         internal energy totals
+ *
+ * Conventions shared by every call
+ *   - Pointers inside sph_particles are DEVICE pointers of the current CUDA
+ *     device, owned by the caller; each array has n elements (x, v, a are
+ *     arrays of three separate component arrays).  The library never frees
+ *     them.  sph_build_cells permutes every array of the struct in place
+ *     into Morton order; `id` travels with the particles so callers can map
+ *     back to their own order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is queued on it; every call returns after a
+ *     device-to-host read of the library's status word on that stream, so
+ *     a returned SPH_OK means the queued work has completed without a
+ *     detected error.
+ *   - The context owns all scratch memory (keys, buckets, tree, interaction
+ *     lists, staged particle records); it is sized by `capacity` at
+ *     sph_create and grown on demand only for interaction lists.
+ *   - Errors are status codes; nothing aborts, traps or throws across the
+ *     ABI.  sph_last_error returns a human-readable message for the last
+ *     non-OK status of a context.
+ *   - h is the kernel's support radius: W(r,h) = w(r/h)/h^3 vanishes for r >= h.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = 1,        /* invalid argument (NULL pointer, n > capacity, h >= L/2 ...) */
+    SPH_ERR_CUDA = 2,       /* a CUDA runtime call failed                                  */
+    SPH_ERR_CAPACITY = 3,   /* a fixed-size internal buffer would overflow                 */
+    SPH_ERR_NOCONV = 4,     /* Newton iteration on h did not converge within max_newton    */
+    SPH_ERR_NONFINITE = 5,  /* a NaN / Inf was produced or found in the inputs             */
+    SPH_ERR_TIMEOUT = 6,    /* a bounded device-side wait ran out                          */
+    SPH_ERR_STATE = 7       /* calls made out of order (e.g. forces before density)        */
+} sph_status;
+
+/* opaque context: scratch memory, bounds tree, integration state */
+typedef struct sph_ctx sph_ctx;
+
+/* smoothing kernels named in Sec. 2.3 (support radius h) */
+enum { SPH_KERNEL_WC2 = 0, SPH_KERNEL_WC4 = 1, SPH_KERNEL_WC6 = 2, SPH_KERNEL_M4 = 3 };
+/* internal-energy update: PdV equation (Sec. 2.3.5) or entropy-conserving
+ * rescale u <- u (rho/rho_old)^(gamma-1) plus viscous heating only */
+enum { SPH_ENERGY_PDV = 0, SPH_ENERGY_ISENTROPIC = 1 };
+
+typedef struct {
+    int32_t kernel;        /* SPH_KERNEL_*                                       */
+    int32_t energy_mode;   /* SPH_ENERGY_*                                       */
+    double  n_ngb;         /* target 4/3 pi h^3 rho / m (self included)          */
+    double  gamma;         /* ideal-gas adiabatic index                          */
+    double  alpha, beta;   /* Monaghan viscosity parameters                      */
+    double  eps_av;        /* epsilon of the mu_ij denominator                   */
+    double  eta_courant;   /* eta_C of Eq. courant_condition                     */
+    double  eta_acc;       /* eta_a of the acceleration criterion                */
+    double  box_lo[3];     /* domain; positions on periodic axes stay inside     */
+    double  box_hi[3];
+    int32_t periodic[3];   /* 1 = periodic axis (minimum image), 0 = open        */
+    int32_t max_newton;    /* Newton iteration cap per particle (<= 255)         */
+    double  h_rel_tol;     /* Newton stops when |dh|/h < h_rel_tol               */
+    double  list_margin;   /* density lists gather within h (1 + list_margin)    */
+} sph_params;
+
+typedef struct {
+    int64_t   n;           /* number of particles                                */
+    double   *x[3];        /* positions x_i (FP64)                               */
+    double   *v[3];        /* velocities v_{i-1/2} between steps (FP64)          */
+    double   *u;           /* specific internal energy u_{i-1/2} (FP64)          */
+    float    *m;           /* masses                                             */
+    float    *h;           /* smoothing length (support radius); input seed,     */
+                           /* output of sph_density_h                            */
+    float    *rho;         /* density (output of sph_density_h)                  */
+    float    *omega;       /* grad-h term Omega (output of sph_density_h)        */
+    float    *a[3];        /* acceleration a_i (output of sph_forces)            */
+    float    *dudt_h;      /* du/dt|H, PdV term (output of sph_forces)           */
+    float    *dudt_av;     /* du/dt|Pi, viscous heating (output of sph_forces)   */
+    float    *divv;        /* velocity divergence (output of sph_forces)         */
+    float    *dt_i;        /* per-particle time-step limit (output of sph_forces)*/
+    uint16_t *nngb;        /* neighbours j != i with r_ij < h_i (sph_density_h)  */
+    uint8_t  *iters;       /* Newton iterations taken (sph_density_h)            */
+    int64_t  *id;          /* caller's particle ids, permuted with the particles */
+} sph_particles;
+
+/* Host-side view of the same state for sph_step_host: HOST pointers, same
+ * layout and meaning as sph_particles. */
+typedef sph_particles sph_host_particles;
+
+typedef struct {
+    uint64_t density_pairs;      /* sum over Newton passes of sum_i n_i (last density call) */
+    uint64_t force_pairs;        /* unordered pairs with r < max(h_i,h_j) (last force call)  */
+    uint64_t density_candidates; /* candidate pair tests in the density pass                 */
+    uint64_t force_candidates;   /* candidate pair tests in the force pass                   */
+    int32_t  max_newton_iters;   /* largest Newton iteration count of the last density call  */
+    int32_t  relists;            /* buckets re-walked because h left the list margin         */
+    int64_t  list_entries_density; /* source buckets in the density lists                    */
+    int64_t  list_entries_force;   /* source buckets in the force lists                      */
+    double   dt_old;             /* step size of the last sph_kdk_step (0 before the first)  */
+    float    ms_build, ms_density, ms_forces, ms_kdk; /* last call durations (CUDA events)    */
+    float    ms_walk;            /* interaction-list walks of the last density + force calls */
+    float    ms_density_kernel;  /* Newton kernel alone, all passes of the last density call */
+    float    ms_force_kernel;    /* pair-force kernel alone, last force call                 */
+    int32_t  pad_;
+    uint64_t force_av_pairs;     /* pairs of the last force call with v_ij.r_ij < 0          */
+    uint64_t launches;           /* kernels launched by this context since sph_create        */
+} sph_stats;
+
+/*
+ * sph_create: allocate a context for up to `capacity` particles on the current
+ * CUDA device.  `params` is copied.  Fails with SPH_ERR_ARG for capacity < 0,
+ * an unknown kernel, gamma <= 1, n_ngb <= 0, an empty box or max_newton not in
+ * [1,255]; SPH_ERR_CUDA if device memory cannot be allocated.
+ * On success *out receives the context (caller destroys it with sph_destroy).
+ */
+sph_status sph_create(const sph_params *params, int64_t capacity, sph_ctx **out);
+
+/* sph_destroy: free the context and its device memory (NULL is ignored). */
+void sph_destroy(sph_ctx *ctx);
+
+/*
+ * sph_build_cells (Sec. 2.1: particles reordered so that cells are contiguous;
+ * Sec. 2.3.2: cell bound and box-of-balls bound per cell).  Computes 48-bit
+ * Morton keys of x, stably sorts them, permutes EVERY array of *p in place,
+ * splits the order into buckets of 32 consecutive particles and builds the
+ * bounds tree over the buckets from x and the current h.  Positions on
+ * periodic axes must lie in [box_lo, box_hi).  SPH_ERR_ARG if p->n > capacity
+ * or a required pointer is NULL; SPH_ERR_NONFINITE for non-finite x or h.
+ */
+sph_status sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream);
+
+/*
+ * sph_density_h (Sec. 2.3.3).  For every particle solves
+ * 4/3 pi h^3 rho(h) = N_ngb m by Newton-Raphson with a bisection safeguard,
+ * starting from h_seed (device array of n floats, Morton order) or, if
+ * h_seed is NULL, from p->h.  Writes p->h, p->rho, p->omega, p->nngb,
+ * p->iters.  In SPH_ENERGY_ISENTROPIC mode it also moves u along its adiabat
+ * to the new density, u <- u (rho/rho_old)^(gamma-1), using the rho left in
+ * p->rho by the previous call.  Then refreshes the box-of-balls bounds with
+ * the new h (Sec. 2.3.3, bounds updated after the density pass).
+ * Requires sph_build_cells since the last change of positions
+ * (SPH_ERR_STATE otherwise).  SPH_ERR_NOCONV if a particle needs more than
+ * max_newton iterations; SPH_ERR_ARG if a converged h reaches half a
+ * periodic box length.
+ */
+sph_status sph_density_h(sph_ctx *ctx, sph_particles *p, const float *h_seed, void *stream);
+
+/*
+ * sph_density_at: rho, Omega and the neighbour count at the GIVEN h (device
+ * array, Morton order), without iterating; optionally lists neighbour ids.
+ * When ids != NULL it must hold n*cap int64 and receives, for particle i, the
+ * `id` values of its neighbours j != i (r_ij < h_i) in slots [i*cap, i*cap+cap);
+ * count[i] (device uint32, may be NULL) receives the full count even when it
+ * exceeds cap.  Outputs rho, omega and nngb go to *p.  Test and diagnostic
+ * entry point for neighbour-set checks.
+ */
+sph_status sph_density_at(sph_ctx *ctx, sph_particles *p, const float *h, int64_t cap,
+                          uint32_t *count, int64_t *ids, void *stream);
+
+/*
+ * sph_forces (Sec. 2.3.5, 2.3.6).  Predicts v, u to the current time with the
+ * previous derivatives and half the previous step (step 2 of the substep),
+ * evaluates P = (gamma-1) rho u and c, then accumulates over every unordered
+ * pair with r_ij < max(h_i, h_j), each pair evaluated once with equal and
+ * opposite contributions: the pressure acceleration (gather + scatter
+ * terms), du/dt|H, the Monaghan viscosity (acceleration and heating, averaged
+ * kernel), div v, and the Courant limit.  Writes p->a, p->dudt_h,
+ * p->dudt_av, p->divv, p->dt_i (= min(eta_a sqrt(h/|a|), Courant limit)).
+ * Requires sph_density_h since sph_build_cells (SPH_ERR_STATE otherwise).
+ */
+sph_status sph_forces(sph_ctx *ctx, sph_particles *p, void *stream);
+
+/*
+ * sph_kdk_step (Sec. 2.3.6 steps 4-5 with one global step size).  Closing
+ * kick of v and u over half the previous step with a and du/dt from
+ * sph_forces; new step = dt_fixed if dt_fixed > 0, else min_i dt_i (device
+ * reduction); opening kick over half the new step; drift x over the new
+ * step; periodic wrap.  If dt_used != NULL the new step is written there
+ * (this needs no extra synchronisation: every call already waits for its
+ * status).  Positions change, so the next sph_density_h needs
+ * sph_build_cells first.
+ */
+sph_status sph_kdk_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_used,
+                        void *stream);
+
+/*
+ * sph_step: one whole step = sph_build_cells, sph_density_h (seeded with the
+ * current h), sph_forces, sph_kdk_step.  Same arguments and errors.
+ */
+sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_used,
+                    void *stream);
+
+/*
+ * sph_step_host: sph_step on HOST arrays.  Copies every array of *hp to
+ * device buffers owned by the context (allocated on first use for the
+ * context's capacity), runs sph_step there and copies every array back
+ * (in Morton order, like sph_step).  Host memory may be pageable or pinned;
+ * pinned memory copies faster.  Bytes moved per call are reported through
+ * h2d_bytes / d2h_bytes when non-NULL.
+ */
+sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, double *dt_used,
+                         int64_t *h2d_bytes, int64_t *d2h_bytes, void *stream);
+
+/*
+ * sph_reduce_conserved: out[0..8] = M, P_x, P_y, P_z, L_x, L_y, L_z, E_kin,
+ * E_int from m, x, v, u of *p, summed in FP64 in a fixed order (bit-identical
+ * from run to run).  out is a HOST array of 9 doubles.
+ */
+sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double out[9], void *stream);
+
+/* sph_set_dt_old: set the previous step size used by the predictor and the
+ * closing kick (0 restarts the integration as at t = 0). */
+sph_status sph_set_dt_old(sph_ctx *ctx, double dt_old);
+
+/* sph_get_stats: counters and timings of the last calls (host struct). */
+sph_status sph_get_stats(const sph_ctx *ctx, sph_stats *out);
+
+/* sph_last_error: message of the last non-OK status ("" if none); the
+ * string is owned by the context. */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* sph_version: library version string. */
+const char *sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

@@ -92,6 +92,8 @@ def lib():
         i32p = C.POINTER(C.c_int32)
         pp = C.POINTER(_Params)
         L.orc_kernel_eval.argtypes = [C.c_int, C.c_int64, dp, dp, dp]
+        L.orc_num_threads.argtypes = []
+        L.orc_num_threads.restype = C.c_int
         L.orc_density_h.argtypes = [pp, C.c_int64, dp, dp, C.c_int64, ip, dp,
                                     dp, dp, dp, ip, i32p]
         L.orc_density_h.restype = C.c_int64

@@ -25,6 +25,7 @@
  * loop over sink particles only, so every per-sink sum is in plain j order.
  */
 #include <math.h>
+#include <omp.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -109,6 +110,9 @@ static void separation(const orc_params *p, const double *xi, const double *xj, 
         }
     }
 }
+
+/* threads the parallel loops use */
+int orc_num_threads(void) { return omp_get_max_threads(); }
 
 void orc_kernel_eval(int kernel, int64_t n, const double *q, double *w, double *dw)
 {

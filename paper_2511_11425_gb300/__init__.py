@@ -1,1 +1,339 @@
-"""GB300-native SPH hot path (placeholder; the binding is added with the C-ABI)."""
+"""GB300-native SPH hot path: Python binding of libsph (include/sph.h).
+
+This module only marshals arguments: device arrays are torch tensors whose
+data pointers go into the C structs, streams are passed as raw handles.
+Every computation runs in the CUDA kernels of ``_libsph.so``.  There is no
+fallback: if the library is missing or cannot be loaded, every call raises.
+
+Functions carry the C names (``sph_create``, ``sph_build_cells``,
+``sph_density_h``, ``sph_density_at``, ``sph_forces``, ``sph_kdk_step``,
+``sph_step``, ``sph_step_host``, ``sph_reduce_conserved``, ``sph_set_dt_old``,
+``sph_get_stats``, ``sph_last_error``, ``sph_version``, ``sph_destroy``) and
+raise ``SphError`` on a non-OK status.  ``Params`` and ``Particles`` build the
+C structs; ``Simulation`` strings the calls together for one problem.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_libsph.so")
+
+STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_CAPACITY",
+          4: "SPH_ERR_NOCONV", 5: "SPH_ERR_NONFINITE", 6: "SPH_ERR_TIMEOUT", 7: "SPH_ERR_STATE"}
+KERNELS = {"wc2": 0, "wc4": 1, "wc6": 2, "m4": 3}
+ENERGY = {"pdv": 0, "isentropic": 1}
+EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph_density_at",
+           "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
+           "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version")
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class c_params(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("energy_mode", C.c_int32), ("n_ngb", C.c_double),
+                ("gamma", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+                ("eps_av", C.c_double), ("eta_courant", C.c_double), ("eta_acc", C.c_double),
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+                ("periodic", C.c_int32 * 3), ("max_newton", C.c_int32),
+                ("h_rel_tol", C.c_double), ("list_margin", C.c_double)]
+
+
+class c_particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p * 3), ("v", C.c_void_p * 3),
+                ("u", C.c_void_p), ("m", C.c_void_p), ("h", C.c_void_p), ("rho", C.c_void_p),
+                ("omega", C.c_void_p), ("a", C.c_void_p * 3), ("dudt_h", C.c_void_p),
+                ("dudt_av", C.c_void_p), ("divv", C.c_void_p), ("dt_i", C.c_void_p),
+                ("nngb", C.c_void_p), ("iters", C.c_void_p), ("id", C.c_void_p)]
+
+
+class c_stats(C.Structure):
+    _fields_ = [("density_pairs", C.c_uint64), ("force_pairs", C.c_uint64),
+                ("density_candidates", C.c_uint64), ("force_candidates", C.c_uint64),
+                ("max_newton_iters", C.c_int32), ("relists", C.c_int32),
+                ("list_entries_density", C.c_int64), ("list_entries_force", C.c_int64),
+                ("dt_old", C.c_double), ("ms_build", C.c_float), ("ms_density", C.c_float),
+                ("ms_forces", C.c_float), ("ms_kdk", C.c_float), ("ms_walk", C.c_float),
+                ("ms_density_kernel", C.c_float), ("ms_force_kernel", C.c_float),
+                ("pad_", C.c_int32), ("force_av_pairs", C.c_uint64), ("launches", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load _libsph.so (build it first with __graft_entry__.build() or build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsph is not built (%s missing); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+        L.sph_create.argtypes = [C.POINTER(c_params), i64, C.POINTER(vp)]
+        L.sph_destroy.argtypes = [vp]
+        L.sph_destroy.restype = None
+        pp = C.POINTER(c_particles)
+        L.sph_build_cells.argtypes = [vp, pp, vp]
+        L.sph_density_h.argtypes = [vp, pp, vp, vp]
+        L.sph_density_at.argtypes = [vp, pp, vp, i64, vp, vp, vp]
+        L.sph_forces.argtypes = [vp, pp, vp]
+        L.sph_kdk_step.argtypes = [vp, pp, dbl, C.POINTER(dbl), vp]
+        L.sph_step.argtypes = [vp, pp, dbl, C.POINTER(dbl), vp]
+        L.sph_step_host.argtypes = [vp, pp, dbl, C.POINTER(dbl), C.POINTER(i64),
+                                    C.POINTER(i64), vp]
+        L.sph_reduce_conserved.argtypes = [vp, pp, C.POINTER(dbl), vp]
+        L.sph_set_dt_old.argtypes = [vp, dbl]
+        L.sph_get_stats.argtypes = [vp, C.POINTER(c_stats)]
+        L.sph_last_error.argtypes = [vp]
+        L.sph_last_error.restype = C.c_char_p
+        L.sph_version.argtypes = []
+        L.sph_version.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("sph_destroy", "sph_last_error", "sph_version"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = lib().sph_last_error(ctx).decode() if ctx else ""
+        raise SphError(rc, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+@dataclasses.dataclass
+class Params:
+    """Python mirror of sph_params (defaults follow the paper's settings)."""
+    kernel: str = "wc2"
+    energy: str = "pdv"
+    n_ngb: float = 64.0
+    gamma: float = 5.0 / 3.0
+    alpha: float = 1.0
+    beta: float = 2.0
+    eps_av: float = 0.01
+    eta_courant: float = 0.15
+    eta_acc: float = 0.2
+    box_lo: tuple = (0.0, 0.0, 0.0)
+    box_hi: tuple = (1.0, 1.0, 1.0)
+    periodic: tuple = (1, 1, 1)
+    max_newton: int = 64
+    h_rel_tol: float = 1e-6
+    list_margin: float = 0.1
+
+    def c(self) -> c_params:
+        p = c_params()
+        p.kernel = KERNELS[self.kernel]
+        p.energy_mode = ENERGY[self.energy]
+        for f in ("n_ngb", "gamma", "alpha", "beta", "eps_av", "eta_courant", "eta_acc",
+                  "h_rel_tol", "list_margin"):
+            setattr(p, f, float(getattr(self, f)))
+        p.max_newton = int(self.max_newton)
+        for a in range(3):
+            p.box_lo[a] = float(self.box_lo[a])
+            p.box_hi[a] = float(self.box_hi[a])
+            p.periodic[a] = int(bool(self.periodic[a]))
+        return p
+
+    @classmethod
+    def for_problem(cls, prob, **kw):
+        d = dict(kernel=prob.kernel, n_ngb=prob.n_ngb, gamma=prob.gamma, alpha=prob.alpha,
+                 beta=prob.beta, box_lo=tuple(prob.box_lo), box_hi=tuple(prob.box_hi),
+                 periodic=tuple(prob.periodic))
+        d.update(kw)
+        return cls(**d)
+
+
+class Particles:
+    """SoA particle state as torch tensors on one device, plus the C struct."""
+
+    FIELDS64 = ("x0", "x1", "x2", "v0", "v1", "v2", "u")
+    FIELDS32 = ("m", "h", "rho", "omega", "a0", "a1", "a2", "dudt_h", "dudt_av", "divv", "dt_i")
+
+    def __init__(self, n, device="cuda", pin=False):
+        import torch
+        self.n = int(n)
+        self.device = torch.device(device)
+        kw = dict(device=self.device)
+        if pin and self.device.type == "cpu":
+            kw["pin_memory"] = True
+        self.t = {}
+        for f in self.FIELDS64:
+            self.t[f] = torch.zeros(self.n, dtype=torch.float64, **kw)
+        for f in self.FIELDS32:
+            self.t[f] = torch.zeros(self.n, dtype=torch.float32, **kw)
+        self.t["nngb"] = torch.zeros(self.n, dtype=torch.int16, **kw)
+        self.t["iters"] = torch.zeros(self.n, dtype=torch.uint8, **kw)
+        self.t["id"] = torch.arange(self.n, dtype=torch.int64, **kw)
+
+    @classmethod
+    def from_problem(cls, prob, device="cuda", pin=False):
+        import torch
+        p = cls(prob.n, device, pin)
+        for a in range(3):
+            p.t["x%d" % a].copy_(torch.from_numpy(prob.pos[:, a].copy()))
+            p.t["v%d" % a].copy_(torch.from_numpy(prob.vel[:, a].copy()))
+        p.t["u"].copy_(torch.from_numpy(prob.u.copy()))
+        p.t["m"].copy_(torch.from_numpy(prob.m.astype("float32")))
+        p.t["h"].copy_(torch.from_numpy(prob.h0.astype("float32")))
+        return p
+
+    def c(self) -> c_particles:
+        s = c_particles()
+        t = self.t
+        s.n = self.n
+        for a in range(3):
+            s.x[a] = t["x%d" % a].data_ptr()
+            s.v[a] = t["v%d" % a].data_ptr()
+            s.a[a] = t["a%d" % a].data_ptr()
+        for f in ("u", "m", "h", "rho", "omega", "dudt_h", "dudt_av", "divv", "dt_i", "nngb",
+                  "iters", "id"):
+            setattr(s, f, t[f].data_ptr())
+        return s
+
+    def pos(self):
+        import torch
+        return torch.stack([self.t["x0"], self.t["x1"], self.t["x2"]], 1)
+
+    def vel(self):
+        import torch
+        return torch.stack([self.t["v0"], self.t["v1"], self.t["v2"]], 1)
+
+    def acc(self):
+        import torch
+        return torch.stack([self.t["a0"], self.t["a1"], self.t["a2"]], 1)
+
+    def numpy(self):
+        """Host copy of every array, in the current (Morton) order."""
+        return {k: v.detach().cpu().numpy() for k, v in self.t.items()}
+
+
+# ---- C-ABI calls, same names -------------------------------------------------
+def sph_version() -> str:
+    return lib().sph_version().decode()
+
+
+def sph_create(params: Params, capacity: int):
+    ctx = C.c_void_p()
+    cp = params.c()
+    rc = lib().sph_create(C.byref(cp), int(capacity), C.byref(ctx))
+    _check(None, rc)
+    return ctx
+
+
+def sph_destroy(ctx):
+    lib().sph_destroy(ctx)
+
+
+def sph_build_cells(ctx, parts: Particles, stream=None):
+    s = parts.c()
+    _check(ctx, lib().sph_build_cells(ctx, C.byref(s), _stream(stream)))
+
+
+def sph_density_h(ctx, parts: Particles, h_seed=None, stream=None):
+    s = parts.c()
+    hs = None if h_seed is None else C.c_void_p(h_seed.data_ptr())
+    _check(ctx, lib().sph_density_h(ctx, C.byref(s), hs, _stream(stream)))
+
+
+def sph_density_at(ctx, parts: Particles, h, cap=0, count=None, ids=None, stream=None):
+    s = parts.c()
+    cnt = None if count is None else C.c_void_p(count.data_ptr())
+    idp = None if ids is None else C.c_void_p(ids.data_ptr())
+    _check(ctx, lib().sph_density_at(ctx, C.byref(s), C.c_void_p(h.data_ptr()), int(cap), cnt,
+                                     idp, _stream(stream)))
+
+
+def sph_forces(ctx, parts: Particles, stream=None):
+    s = parts.c()
+    _check(ctx, lib().sph_forces(ctx, C.byref(s), _stream(stream)))
+
+
+def sph_kdk_step(ctx, parts: Particles, dt_fixed=0.0, stream=None) -> float:
+    s = parts.c()
+    dt = C.c_double()
+    _check(ctx, lib().sph_kdk_step(ctx, C.byref(s), float(dt_fixed), C.byref(dt), _stream(stream)))
+    return dt.value
+
+
+def sph_step(ctx, parts: Particles, dt_fixed=0.0, stream=None) -> float:
+    s = parts.c()
+    dt = C.c_double()
+    _check(ctx, lib().sph_step(ctx, C.byref(s), float(dt_fixed), C.byref(dt), _stream(stream)))
+    return dt.value
+
+
+def sph_step_host(ctx, host_parts: Particles, dt_fixed=0.0, stream=None):
+    """One step on host (CPU tensor) arrays; returns (dt, h2d_bytes, d2h_bytes)."""
+    s = host_parts.c()
+    dt = C.c_double()
+    hb = C.c_int64()
+    db = C.c_int64()
+    _check(ctx, lib().sph_step_host(ctx, C.byref(s), float(dt_fixed), C.byref(dt), C.byref(hb),
+                                    C.byref(db), _stream(stream)))
+    return dt.value, hb.value, db.value
+
+
+def sph_reduce_conserved(ctx, parts: Particles, stream=None):
+    s = parts.c()
+    out = (C.c_double * 9)()
+    _check(ctx, lib().sph_reduce_conserved(ctx, C.byref(s), out, _stream(stream)))
+    return list(out)
+
+
+def sph_set_dt_old(ctx, dt_old: float):
+    _check(ctx, lib().sph_set_dt_old(ctx, float(dt_old)))
+
+
+def sph_get_stats(ctx) -> dict:
+    st = c_stats()
+    _check(ctx, lib().sph_get_stats(ctx, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in c_stats._fields_}
+
+
+def sph_last_error(ctx) -> str:
+    return lib().sph_last_error(ctx).decode()
+
+
+class Simulation:
+    """One problem on one GPU: owns the context and the particle tensors."""
+
+    def __init__(self, prob, params: Params | None = None, device="cuda", capacity=None):
+        self.params = params or Params.for_problem(prob)
+        self.parts = Particles.from_problem(prob, device)
+        self.ctx = sph_create(self.params, capacity or prob.n)
+        self.t = 0.0
+
+    def step(self, dt_fixed=0.0, stream=None) -> float:
+        dt = sph_step(self.ctx, self.parts, dt_fixed, stream)
+        self.t += dt
+        return dt
+
+    def stats(self):
+        return sph_get_stats(self.ctx)
+
+    def conserved(self, stream=None):
+        return sph_reduce_conserved(self.ctx, self.parts, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,616 @@
+// sph_build.cu -- sph_build_cells and the interaction-list walk.
+//
+// Sec. 2.1 keeps particles ordered so that every tree cell is a contiguous
+// range; Sec. 2.3.2 bounds every cell by the box of its particles (cell
+// bound) and the box of the particles' kernel balls (box-of-balls), merged
+// bottom-up, and finds interaction partners of a whole group at once by
+// overlap tests of those bounds.  Here the order is a 48-bit Morton order
+// (stable LSD radix sort), a bucket is 32 consecutive particles (one warp),
+// and the tree is an implicit complete binary tree over the buckets.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// bounding box of open axes (periodic axes use the box)
+// ---------------------------------------------------------------------------
+__global__ void k_bbox_partial(int n, const double *__restrict__ x, const double *__restrict__ y,
+                               const double *__restrict__ z, double *part)
+{
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], v[a]);
+            mx[a] = fmax(mx[a], v[a]);
+        }
+    }
+    __shared__ double smn[3][32], smx[3][32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double a0 = warp_min(mn[a]), a1 = warp_max(mx[a]);
+        if (lane == 0) { smn[a][w] = a0; smx[a][w] = a1; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double a0 = lane < nw ? smn[a][lane] : INFINITY;
+            double a1 = lane < nw ? smx[a][lane] : -INFINITY;
+            a0 = warp_min(a0);
+            a1 = warp_max(a1);
+            if (lane == 0) {
+                part[blockIdx.x * 6 + a] = a0;
+                part[blockIdx.x * 6 + 3 + a] = a1;
+            }
+        }
+    }
+}
+
+// morton_box = [lo0, lo1, lo2, scale0, scale1, scale2]: cell = (x - lo) * scale
+__global__ void k_bbox_final(KParams kp, int nparts, const double *part, double *morton_box,
+                             DevStatus *st)
+{
+    if (threadIdx.x != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        double lo, hi;
+        if (kp.periodic[a]) {
+            lo = kp.lo[a];
+            hi = kp.hi[a];
+        } else {
+            lo = INFINITY;
+            hi = -INFINITY;
+            for (int b = 0; b < nparts; ++b) {
+                lo = fmin(lo, part[b * 6 + a]);
+                hi = fmax(hi, part[b * 6 + 3 + a]);
+            }
+        }
+        if (!isfinite(lo) || !isfinite(hi)) {
+            raise_status(st, ST_NONFINITE, a);
+            lo = 0.0;
+            hi = 1.0;
+        }
+        double ext = (hi - lo) * (1.0 + 1e-9) + 1e-300;
+        morton_box[a] = lo;
+        morton_box[3 + a] = 65536.0 / ext;
+    }
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned int v)
+{
+    unsigned long long x = v & 0xffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+__global__ void k_morton(int n, const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, const double *__restrict__ mbox,
+                         unsigned long long *keys, unsigned int *vals)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v[3] = {x[i], y[i], z[i]};
+    unsigned int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double t = (v[a] - mbox[a]) * mbox[3 + a];
+        t = fmin(fmax(t, 0.0), 65535.0);
+        c[a] = (unsigned int)t;
+    }
+    keys[i] = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+    vals[i] = (unsigned int)i;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits, tiles of 4096 keys (256 threads x 16)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sort_hist(const unsigned long long *__restrict__ keys,
+                                                   int n, int shift, unsigned int *hist, int ntiles)
+{
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    for (int k = threadIdx.x; k < kSortTile; k += 256) {
+        int i = base + k;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of the digit-major histogram (256 x ntiles) in one block
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned int *hist, int total)
+{
+    __shared__ unsigned int part[1024];
+    int t = threadIdx.x;
+    int per = (total + 1023) / 1024;
+    int b0 = min(total, t * per), b1 = min(total, b0 + per);
+    unsigned int s = 0;
+    for (int k = b0; k < b1; ++k) s += hist[k];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned int v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned int run = part[t] - s;
+    for (int k = b0; k < b1; ++k) {
+        unsigned int c = hist[k];
+        hist[k] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(const unsigned long long *__restrict__ kin,
+                                                      const unsigned int *__restrict__ vin,
+                                                      unsigned long long *__restrict__ kout,
+                                                      unsigned int *__restrict__ vout, int n,
+                                                      int shift, const unsigned int *__restrict__ hist,
+                                                      int ntiles)
+{
+    __shared__ unsigned int wcnt[8][256];
+    __shared__ unsigned int toff[256];
+    int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int k = tid; k < 8 * 256; k += 256) (&wcnt[0][0])[k] = 0;
+    toff[tid] = hist[tid * ntiles + blockIdx.x];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long key[16];
+    unsigned int val[16], rnk[16];
+    int base = blockIdx.x * kSortTile + w * 512;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int i = base + r * 32 + lane;
+        bool ok = i < n;
+        key[r] = ok ? kin[i] : 0ull;
+        val[r] = ok ? vin[i] : 0u;
+        unsigned d = ok ? (unsigned)((key[r] >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(kFull, d);
+        unsigned before = 0;
+        if (ok) before = wcnt[w][d];
+        __syncwarp();
+        rnk[r] = before + __popc(peers & lt);
+        if (ok && lane == __ffs(peers) - 1) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        unsigned s = 0;
+        for (int k = 0; k < 8; ++k) {
+            unsigned c = wcnt[k][tid];
+            wcnt[k][tid] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        int i = base + r * 32 + lane;
+        if (i < n) {
+            unsigned d = (unsigned)((key[r] >> shift) & 255u);
+            unsigned pos = toff[d] + wcnt[w][d] + rnk[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// in-place permutation of the caller's arrays through a scratch buffer
+// ---------------------------------------------------------------------------
+template <class T, int NF>
+struct Fields {
+    T *f[NF];
+    int nf;
+};
+
+template <class T, int NF>
+__global__ void k_gather(const unsigned int *__restrict__ perm, int n, Fields<T, NF> fp,
+                         T *__restrict__ tmp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned j = perm[i];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (f < fp.nf) tmp[(size_t)f * n + i] = fp.f[f][j];
+}
+
+template <class T, int NF>
+__global__ void k_copyback(int n, Fields<T, NF> fp, const T *__restrict__ tmp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (f < fp.nf) fp.f[f][i] = tmp[(size_t)f * n + i];
+}
+
+template <class T, int NF>
+static void permute(const unsigned *perm, int n, Fields<T, NF> fp, void *tmp, cudaStream_t s)
+{
+    int nb = (n + 255) / 256;
+    k_gather<T, NF><<<nb, 256, 0, s>>>(perm, n, fp, (T *)tmp);
+    k_copyback<T, NF><<<nb, 256, 0, s>>>(n, fp, (const T *)tmp);
+}
+
+// ---------------------------------------------------------------------------
+// buckets: origin, relative positions, leaf bounds
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_node(float4 *node, int k, float3 bc, float3 br, float3 oc,
+                                           float3 orr, float hmax)
+{
+    node[4 * k + 0] = make_float4(bc.x, bc.y, bc.z, 0.f);
+    node[4 * k + 1] = make_float4(br.x, br.y, br.z, 0.f);
+    node[4 * k + 2] = make_float4(oc.x, oc.y, oc.z, 0.f);
+    node[4 * k + 3] = make_float4(orr.x, orr.y, orr.z, hmax);
+}
+
+// one warp per bucket.  With update_pos = 1 it also (re)computes the bucket
+// origin and the relative positions pm; with 0 it refreshes only the
+// box-of-balls from the current h (bounds update after the density pass).
+__global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__restrict__ x,
+                                                 const double *__restrict__ y,
+                                                 const double *__restrict__ z,
+                                                 const float *__restrict__ m,
+                                                 const float *__restrict__ h, double *origin,
+                                                 float4 *pm, float4 *node, int update_pos,
+                                                 DevStatus *st)
+{
+    int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (b >= kp.nb) return;
+    int i = b * kBucket + lane;
+    bool ok = i < kp.n;
+    double xu[3];
+    if (update_pos) {
+        double v[3] = {0, 0, 0};
+        if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double first = __shfl_sync(kFull, v[a], 0);
+            double d = v[a] - first;
+            if (kp.periodic[a]) d = wrapd(d, (double)(kp.hi[a] - kp.lo[a]));
+            xu[a] = first + d;  // unwrapped next to the bucket's first particle
+        }
+        double o[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double mn = warp_min(ok ? xu[a] : INFINITY);
+            o[a] = floor(mn / kp.q) * kp.q;
+            if (lane == 0) origin[a * kp.nb + b] = o[a];
+        }
+        if (ok) {
+            float4 r = make_float4((float)(xu[0] - o[0]), (float)(xu[1] - o[1]),
+                                   (float)(xu[2] - o[2]), m[i]);
+            if (!(isfinite(r.x) && isfinite(r.y) && isfinite(r.z))) raise_status(st, ST_NONFINITE, i);
+            pm[i] = r;
+        }
+    } else {
+        float4 r = ok ? pm[i] : make_float4(0, 0, 0, 0);
+        xu[0] = origin[b] + (double)r.x;
+        xu[1] = origin[kp.nb + b] + (double)r.y;
+        xu[2] = origin[2 * kp.nb + b] + (double)r.z;
+    }
+    float hi = ok ? h[i] : 0.f;
+    if (ok && !(hi > 0.f && isfinite(hi))) raise_status(st, ST_NONFINITE, i);
+    float bc[3], br[3], oc[3], orr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double mn = warp_min(ok ? xu[a] : INFINITY), mx = warp_max(ok ? xu[a] : -INFINITY);
+        double mnb = warp_min(ok ? xu[a] - (double)hi : INFINITY);
+        double mxb = warp_max(ok ? xu[a] + (double)hi : -INFINITY);
+        bc[a] = (float)(0.5 * (mn + mx));
+        br[a] = (float)(0.5 * (mx - mn)) + kp.eps_abs;
+        oc[a] = (float)(0.5 * (mnb + mxb));
+        orr[a] = (float)(0.5 * (mxb - mnb)) + kp.eps_abs;
+    }
+    float hmax = warp_max(hi);
+    if (lane == 0) {
+        int k = kp.P + b;
+        if (update_pos) {
+            store_node(node, k, make_float3(bc[0], bc[1], bc[2]), make_float3(br[0], br[1], br[2]),
+                       make_float3(oc[0], oc[1], oc[2]), make_float3(orr[0], orr[1], orr[2]), hmax);
+        } else {
+            node[4 * k + 2] = make_float4(oc[0], oc[1], oc[2], 0.f);
+            node[4 * k + 3] = make_float4(orr[0], orr[1], orr[2], hmax);
+        }
+    }
+}
+
+// union of two centre/half-width intervals; on periodic axes the second is
+// first moved to its image nearest the first; r < 0 marks an empty interval
+__device__ __forceinline__ void union1(float c1, float r1, float c2, float r2, bool per, float L,
+                                       float invL, float eps, float &c, float &r)
+{
+    if (r1 < 0.f) { c = c2; r = r2; return; }
+    if (r2 < 0.f) { c = c1; r = r1; return; }
+    if (per) c2 = c1 + wrapf(c2 - c1, L, invL);
+    float lo = fminf(c1 - r1, c2 - r2), hi = fmaxf(c1 + r1, c2 + r2);
+    c = 0.5f * (lo + hi);
+    r = 0.5f * (hi - lo) + eps;
+    if (per && r >= 0.5f * L) r = L;  // covers the whole periodic axis
+}
+
+// bottom-up merge of the bounds (Sec. 2.3.2): one thread per leaf climbs;
+// the second child to arrive at a parent computes it
+__global__ void k_tree_up(KParams kp, float4 *node, unsigned int *flag, int bob_only)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= kp.P) return;
+    int k = kp.P + b;
+    if (b >= kp.nb) {
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f), er = make_float4(-1.f, -1.f, -1.f, 0.f);
+        if (!bob_only) { node[4 * k] = e; node[4 * k + 1] = er; }
+        node[4 * k + 2] = e;
+        node[4 * k + 3] = er;
+    }
+    while (k > 1) {
+        __threadfence();
+        int parent = k >> 1;
+        if (atomicAdd(&flag[parent], 1u) == 0u) return;
+        __threadfence();
+        int l = 2 * parent, r = 2 * parent + 1;
+        float4 out[4];
+#pragma unroll
+        for (int s = bob_only ? 1 : 0; s < 2; ++s) {
+            float4 c1 = __ldcg(&node[4 * l + 2 * s]), r1 = __ldcg(&node[4 * l + 2 * s + 1]);
+            float4 c2 = __ldcg(&node[4 * r + 2 * s]), r2 = __ldcg(&node[4 * r + 2 * s + 1]);
+            float cc[3], rr[3];
+            float a1[3] = {c1.x, c1.y, c1.z}, b1[3] = {r1.x, r1.y, r1.z};
+            float a2[3] = {c2.x, c2.y, c2.z}, b2[3] = {r2.x, r2.y, r2.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                union1(a1[a], b1[a], a2[a], b2[a], kp.periodic[a], kp.L[a], kp.invL[a], kp.eps_abs,
+                       cc[a], rr[a]);
+            out[2 * s] = make_float4(cc[0], cc[1], cc[2], 0.f);
+            out[2 * s + 1] = make_float4(rr[0], rr[1], rr[2], fmaxf(r1.w, r2.w));
+        }
+        if (!bob_only) { __stcg(&node[4 * parent], out[0]); __stcg(&node[4 * parent + 1], out[1]); }
+        __stcg(&node[4 * parent + 2], out[2]);
+        __stcg(&node[4 * parent + 3], out[3]);
+        k = parent;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// interaction-list walk (Sec. 2.3.2): one warp per sink bucket, breadth-first
+// over the implicit tree, 32 node tests at a time.
+//   density: source cell bound overlaps the sink's box of balls of radius
+//            h_walk (1 + margin)                             (gather)
+//   force:   source cell bound overlaps the sink box-of-balls (gather) OR
+//            source box-of-balls overlaps the sink cell bound (scatter),
+//            restricted to source buckets >= sink (each pair once)
+// Each list entry carries the source bucket id and the f32 offset between
+// the bucket origins (nearest periodic image), exact since origins are
+// multiples of q.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool ovl(float ca, float ra, float cb, float rb, bool per, float L,
+                                    float invL)
+{
+    float d = ca - cb;
+    if (per) d = wrapf(d, L, invL);
+    return fabsf(d) <= ra + rb;
+}
+
+__global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4 *__restrict__ node,
+                                              const float4 *__restrict__ pm,
+                                              const double *__restrict__ origin,
+                                              const float *__restrict__ h_walk,
+                                              const unsigned *__restrict__ bucket_ids, int nbuckets,
+                                              unsigned *list_start, unsigned *list_cnt,
+                                              uint4 *list, long long list_cap, DevStatus *st)
+{
+    __shared__ unsigned buf[kWarpsPerBlock][2][kWalkCap];
+    int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int bi = blockIdx.x * kWarpsPerBlock + wib;
+    if (bi >= nbuckets) return;
+    int A = bucket_ids ? (int)bucket_ids[bi] : bi;
+
+    // sink bounds in absolute (unwrapped) f32 coordinates
+    float gc[3], gr[3], sc[3], sr[3];  // gather box, sink cell box
+    if (mode == WALK_DENSITY) {
+        int i = A * kBucket + lane;
+        bool ok = i < kp.n;
+        float4 r = ok ? pm[i] : make_float4(0, 0, 0, 0);
+        float R = ok ? h_walk[i] * (1.f + kp.margin) : 0.f;
+        float rp[3] = {r.x, r.y, r.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float lo = warp_min(ok ? rp[a] - R : INFINITY), hi = warp_max(ok ? rp[a] + R : -INFINITY);
+            double o = origin[a * kp.nb + A];
+            gc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
+            gr[a] = 0.5f * (hi - lo) + 2.f * kp.eps_abs;
+            sc[a] = gc[a];
+            sr[a] = -1.f;
+        }
+    } else {
+        int k = kp.P + A;
+        float4 b0 = node[4 * k], b1 = node[4 * k + 1], o0 = node[4 * k + 2], o1 = node[4 * k + 3];
+        gc[0] = o0.x; gc[1] = o0.y; gc[2] = o0.z;
+        gr[0] = o1.x; gr[1] = o1.y; gr[2] = o1.z;
+        sc[0] = b0.x; sc[1] = b0.y; sc[2] = b0.z;
+        sr[0] = b1.x; sr[1] = b1.y; sr[2] = b1.z;
+    }
+
+    unsigned *cur = buf[wib][0], *nxt = buf[wib][1];
+    int L0 = kp.logP < 5 ? kp.logP : 5;
+    int ncur = 1 << L0;
+    for (int k = lane; k < ncur; k += 32) cur[k] = (1u << L0) + k;
+    __syncwarp();
+    bool overflow = false;
+    for (int lvl = L0; lvl <= kp.logP; ++lvl) {
+        bool leaf = lvl == kp.logP;
+        int nnext = 0;
+        for (int base = 0; base < ncur; base += 32) {
+            int k = base + lane;
+            bool acc = false;
+            unsigned nd = 0;
+            if (k < ncur) {
+                nd = cur[k];
+                float4 b0 = node[4 * nd], b1 = node[4 * nd + 1];
+                if (b1.x >= 0.f) {  // non-empty
+                    bool g = ovl(gc[0], gr[0], b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                             ovl(gc[1], gr[1], b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                             ovl(gc[2], gr[2], b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                    if (mode == WALK_FORCE) {
+                        // only subtrees holding buckets >= A
+                        int shift = kp.logP - lvl;
+                        int last = (int)(((nd + 1u) << shift) - 1u) - kp.P;
+                        if (last < A) {
+                            g = false;
+                        } else if (!g) {
+                            float4 o0 = node[4 * nd + 2], o1 = node[4 * nd + 3];
+                            g = ovl(sc[0], sr[0], o0.x, o1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                                ovl(sc[1], sr[1], o0.y, o1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                                ovl(sc[2], sr[2], o0.z, o1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                        }
+                        if (leaf && (int)(nd - kp.P) < A) g = false;
+                    }
+                    acc = g;
+                }
+            }
+            unsigned bal = __ballot_sync(kFull, acc);
+            int per = leaf ? 1 : 2;
+            int pos = nnext + per * __popc(bal & ((1u << lane) - 1u));
+            int tot = nnext + per * __popc(bal);
+            if (tot > kWalkCap) {
+                overflow = true;
+            } else if (acc) {
+                if (leaf) {
+                    nxt[pos] = nd - (unsigned)kp.P;
+                } else {
+                    nxt[pos] = 2u * nd;
+                    nxt[pos + 1] = 2u * nd + 1u;
+                }
+            }
+            nnext = min(tot, kWalkCap);
+        }
+        __syncwarp();
+        unsigned *t = cur;
+        cur = nxt;
+        nxt = t;
+        ncur = nnext;
+        if (overflow) break;
+    }
+    if (overflow) {
+        if (lane == 0) raise_status(st, ST_CAPACITY, A);
+        ncur = 0;
+    }
+    // cur holds the accepted bucket ids; allocate and write them
+    unsigned start = 0;
+    if (lane == 0) start = atomicAdd(&st->list_need, (unsigned)ncur);
+    start = __shfl_sync(kFull, start, 0);
+    bool fits = (long long)start + ncur <= list_cap;
+    if (lane == 0) {
+        list_start[A] = start;
+        list_cnt[A] = fits ? (unsigned)ncur : 0u;
+    }
+    if (!fits) return;
+    double oA[3] = {origin[A], origin[kp.nb + A], origin[2 * kp.nb + A]};
+    for (int k = lane; k < ncur; k += 32) {
+        unsigned B = cur[k];
+        float d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double dd = origin[a * kp.nb + B] - oA[a];
+            if (kp.periodic[a]) dd = wrapd(dd, (double)(kp.hi[a] - kp.lo[a]));
+            d[a] = (float)dd;
+        }
+        list[start + k] = make_uint4(B, __float_as_uint(d[0]), __float_as_uint(d[1]),
+                                     __float_as_uint(d[2]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    const KParams &kp = c.kp;
+    int n = (int)p.n;
+    // bounding box for the Morton quantisation
+    int nbb = 152;
+    c.launches += 2 + 1 + 3 * kSortPasses + 2 * 4 + 2;
+    k_bbox_partial<<<nbb, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.bbox_part);
+    k_bbox_final<<<1, 32, 0, s>>>(kp, nbb, c.bbox_part, c.morton_box, c.st);
+    int g = (n + 255) / 256;
+    k_morton<<<g, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.morton_box, c.keys[0], c.vals[0]);
+    int ntiles = (n + kSortTile - 1) / kSortTile;
+    int cur = 0;
+    for (int pass = 0; pass < kSortPasses; ++pass) {
+        int shift = 8 * pass;
+        k_sort_hist<<<ntiles, 256, 0, s>>>(c.keys[cur], n, shift, c.hist, ntiles);
+        k_sort_scan<<<1, 1024, 0, s>>>(c.hist, 256 * ntiles);
+        k_sort_scatter<<<ntiles, 256, 0, s>>>(c.keys[cur], c.vals[cur], c.keys[cur ^ 1],
+                                              c.vals[cur ^ 1], n, shift, c.hist, ntiles);
+        cur ^= 1;
+    }
+    const unsigned *perm = c.vals[cur];
+    // permute every caller array (8-byte, 4-byte, 2-byte and 1-byte groups)
+    typedef unsigned long long u64;
+    Fields<u64, 8> f8{};
+    f8.f[0] = (u64 *)p.x[0]; f8.f[1] = (u64 *)p.x[1]; f8.f[2] = (u64 *)p.x[2];
+    f8.f[3] = (u64 *)p.v[0]; f8.f[4] = (u64 *)p.v[1]; f8.f[5] = (u64 *)p.v[2];
+    f8.f[6] = (u64 *)p.u; f8.f[7] = (u64 *)p.id;
+    f8.nf = 8;
+    permute(perm, n, f8, c.tmp, s);
+    Fields<float, 12> f4{};
+    f4.f[0] = p.m; f4.f[1] = p.h; f4.f[2] = p.rho; f4.f[3] = p.omega;
+    f4.f[4] = p.a[0]; f4.f[5] = p.a[1]; f4.f[6] = p.a[2];
+    f4.f[7] = p.dudt_h; f4.f[8] = p.dudt_av; f4.f[9] = p.divv; f4.f[10] = p.dt_i;
+    f4.nf = 11;
+    permute(perm, n, f4, c.tmp, s);
+    Fields<uint16_t, 1> f2{};
+    f2.f[0] = p.nngb;
+    f2.nf = 1;
+    permute(perm, n, f2, c.tmp, s);
+    Fields<uint8_t, 1> f1{};
+    f1.f[0] = p.iters;
+    f1.nf = 1;
+    permute(perm, n, f1, c.tmp, s);
+    // buckets and tree
+    int wb = (kp.nb * 32 + 127) / 128;
+    k_buckets<<<wb, 128, 0, s>>>(kp, p.x[0], p.x[1], p.x[2], p.m, p.h, c.origin, c.pm, c.node, 1,
+                                 c.st);
+    cudaMemsetAsync(c.node_flag, 0, sizeof(unsigned) * (size_t)kp.P, s);
+    k_tree_up<<<(kp.P + 255) / 256, 256, 0, s>>>(kp, c.node, c.node_flag, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    const KParams &kp = c.kp;
+    int wb = (kp.nb * 32 + 127) / 128;
+    c.launches += 2;
+    k_buckets<<<wb, 128, 0, s>>>(kp, p.x[0], p.x[1], p.x[2], p.m, p.h, c.origin, c.pm, c.node, 0,
+                                 c.st);
+    cudaMemsetAsync(c.node_flag, 0, sizeof(unsigned) * (size_t)kp.P, s);
+    k_tree_up<<<(kp.P + 255) / 256, 256, 0, s>>>(kp, c.node, c.node_flag, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned *bucket_ids,
+                        int nbuckets, const float *h_walk, cudaStream_t s)
+{
+    (void)p;
+    if (nbuckets <= 0) return cudaSuccess;
+    int g = (nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    c.launches += 1;
+    k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, mode, c.node, c.pm, c.origin, h_walk, bucket_ids,
+                                             nbuckets, c.list_start, c.list_cnt, (uint4 *)c.list,
+                                             (long long)c.list_cap, c.st);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,336 @@
+// sph_density.cu -- smoothing length and density (Sec. 2.3.3).
+//
+// rho_i = sum_j m_j W_ij(h_i) (Eq. Density_estimate), self included, and
+// h_i from Newton-Raphson on the constant kernel mass
+//     g(h) = 4/3 pi h^3 rho_i(h) / m_i - N_ngb = 4/3 pi sigma S_w / m_i - N_ngb,
+//     g'(h) = -4/3 pi sigma S_q / (m_i h),
+// with S_w = sum_j m_j w(q_j), S_q = sum_j m_j q_j w'(q_j), q_j = r_ij/h (the h^3
+// of W cancels against the h^3 of the kernel volume).  At the converged h
+//     rho = sigma S_w / h^3,    Omega = 1 + h/(3 rho) drho/dh = -S_q / (3 S_w).
+// The interaction list of each sink bucket was gathered once with radius
+// h_seed (1 + margin) (Sec. 2.3.3: the list is kept across iterations and
+// over-selects with a slightly larger kernel).  If a particle's h must grow
+// past that radius its bucket is queued for a new walk.
+//
+// GPU mapping: one warp per sink bucket (lane = sink particle).  For each
+// Newton pass the warp streams the list: every source bucket is loaded
+// coalesced (float4 relative position + mass), moved into the sink frame by
+// the exact origin offset, culled against the warp's box of balls and
+// compacted into a 128-entry shared-memory chunk.  Each lane then tests all
+// chunk entries against its own h (a 128-bit hit mask in registers) and
+// evaluates the kernel only on its hits, so the expensive arithmetic runs on
+// full warps.  Chunk partial sums are folded into Kahan-compensated totals.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+constexpr float kFourPiThird = 4.18879020478639098f;
+
+template <class K, bool WRAP, bool EMIT>
+__device__ __forceinline__ void density_chunk(const KParams &kp, const float4 *cand,
+                                              const int *candj, int c, float px, float py,
+                                              float pz, float h2, float ih, bool active,
+                                              Kahan &Sw, Kahan &Sq, int &cnt, int i, long long cap,
+                                              int &emitted, int64_t *ids_out,
+                                              const int64_t *__restrict__ id_in)
+{
+    unsigned long long m0 = 0ull, m1 = 0ull;
+    if (active) {
+        int c0 = c < 64 ? c : 64;
+        for (int k = 0; k < c0; ++k) {
+            float4 q = cand[k];
+            float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+            if (WRAP) {
+                if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+                if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+                if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+            }
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            m0 |= (unsigned long long)(r2 < h2) << k;
+        }
+        for (int k = 64; k < c; ++k) {
+            float4 q = cand[k];
+            float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+            if (WRAP) {
+                if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+                if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+                if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+            }
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            m1 |= (unsigned long long)(r2 < h2) << (k - 64);
+        }
+    }
+    float sw = 0.f, sq = 0.f;
+    int nh = 0;
+    while (m0 | m1) {
+        int k;
+        if (m0) {
+            k = __ffsll((long long)m0) - 1;
+            m0 &= m0 - 1ull;
+        } else {
+            k = 63 + __ffsll((long long)m1);
+            m1 &= m1 - 1ull;
+        }
+        float4 q = cand[k];
+        float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+        if (WRAP) {
+            if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+            if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+            if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+        }
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
+        float qq = r * ih;
+        float wv = K::w(qq), dq = K::dwq(qq);
+        sw = fmaf(q.w, wv, sw);
+        sq = fmaf(q.w * dq, qq * qq, sq);
+        ++nh;
+        if (EMIT) {
+            int j = candj[k];
+            if (j != i) {
+                if (emitted < cap) ids_out[(long long)i * cap + emitted] = id_in[j];
+                ++emitted;
+            }
+        }
+    }
+    Sw.add(sw);
+    Sq.add(sq);
+    cnt += nh;
+}
+
+template <class K, bool WRAP, bool EMIT>
+__device__ __forceinline__ void density_bucket(
+    const KParams &kp, int A, int lane, float4 *cand, int *candj, const float4 *__restrict__ pm,
+    const unsigned *__restrict__ list_start, const unsigned *__restrict__ list_cnt,
+    const uint4 *__restrict__ list, float *h_seed, float *h_out, float *rho_out, float *omega_out,
+    uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out,
+    int64_t *ids_out, const int64_t *__restrict__ id_in, unsigned *redo_out, DevStatus *st,
+    float4 me, bool valid, const float *cen)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    int i = A * kBucket + lane;
+    float h = valid ? h_seed[i] : 1.f;
+    const float R = h * (1.f + kp.margin);  // radius the list was gathered with
+    float lo = 0.f, hi = INFINITY;
+    bool done = !valid, relist = false, conv = false;
+    int iters = 0;
+    float out_h = h, out_rho = 0.f, out_om = 0.f;
+    int out_n = 0, emitted = 0;
+    unsigned long long pairs = 0, cands = 0;
+    const unsigned s0 = list_start[A], nl = list_cnt[A];
+    const float p[3] = {me.x, me.y, me.z};
+
+    for (int pass = 0; pass <= kp.max_newton; ++pass) {
+        if (__all_sync(kFull, done)) break;
+        const float h2 = h * h, ih = 1.f / h;
+        float bc[3], br[3];  // box of balls of the active lanes (centre, half width)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float bl = warp_min(done ? INFINITY : p[a] - h);
+            float bh = warp_max(done ? -INFINITY : p[a] + h);
+            bc[a] = 0.5f * (bl + bh);
+            br[a] = 0.5f * (bh - bl);
+        }
+        Kahan Sw, Sq;
+        int cnt = 0, c = 0;
+        for (unsigned e = 0; e < nl; ++e) {
+            uint4 L4 = list[s0 + e];
+            int j = (int)L4.x * kBucket + lane;
+            bool vj = j < kp.n;
+            float4 s = vj ? pm[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float sp[3] = {__uint_as_float(L4.y) + s.x, __uint_as_float(L4.z) + s.y,
+                           __uint_as_float(L4.w) + s.z};
+            bool in = vj;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float d = sp[a] - bc[a];
+                if (kp.periodic[a]) {
+                    sp[a] -= kp.L[a] * rintf((sp[a] - cen[a]) * kp.invL[a]);
+                    d = wrapf(d, kp.L[a], kp.invL[a]);
+                }
+                in = in && fabsf(d) <= br[a];
+            }
+            unsigned bal = __ballot_sync(kFull, in);
+            if (in) {
+                int pos = c + __popc(bal & lt);
+                cand[pos] = make_float4(sp[0], sp[1], sp[2], s.w);
+                if (EMIT) candj[pos] = j;
+            }
+            c += __popc(bal);
+            if (c > kChunk - 32) {
+                __syncwarp();
+                if (!done) cands += c;
+                density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, p[0], p[1], p[2], h2, ih, !done,
+                                             Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
+                __syncwarp();
+                c = 0;
+            }
+        }
+        if (c > 0) {
+            __syncwarp();
+            if (!done) cands += c;
+            density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, p[0], p[1], p[2], h2, ih, !done, Sw,
+                                         Sq, cnt, i, cap, emitted, ids_out, id_in);
+            __syncwarp();
+        }
+        if (!done) {
+            ++iters;
+            const float swv = Sw.s, sqv = Sq.s;
+            const int nn = cnt - 1;  // the particle itself is always in its own list
+            pairs += (unsigned long long)(nn > 0 ? nn : 0);
+            bool record = fixed_h != 0;
+            if (!record) {
+                float g = kFourPiThird * K::sigma * swv / me.w - kp.n_ngb;
+                float dg = -kFourPiThird * K::sigma * sqv / (me.w * h);
+                if (g < 0.f) lo = h; else hi = h;
+                float hn = dg > 0.f ? h - g / dg : NAN;
+                if (isfinite(hn) && fabsf(hn - h) < kp.h_rel_tol * h) {
+                    record = true;
+                } else {
+                    if (!(hn > lo && hn < hi)) hn = isfinite(hi) ? 0.5f * (lo + hi) : 2.f * h;
+                    if (hn > R) {
+                        if (h >= R) {  // g(R) < 0: the root lies beyond the list's coverage
+                            relist = true;
+                            done = true;
+                            out_h = hn;
+                        } else {
+                            hn = R;
+                        }
+                    }
+                    if (!done) {
+                        if (iters >= kp.max_newton) {
+                            done = true;
+                            raise_status(st, ST_NOCONV, i);
+                        } else {
+                            h = hn;
+                        }
+                    }
+                }
+            }
+            if (record) {
+                done = true;
+                conv = true;
+                out_h = h;
+                out_rho = K::sigma * swv * ih * ih * ih;
+                out_om = -sqv / (3.f * swv);
+                out_n = nn;
+                if (!(isfinite(out_rho) && isfinite(out_om) && out_rho > 0.f))
+                    raise_status(st, ST_NONFINITE, i);
+                if (h >= kp.hcap) raise_status(st, ST_ARG, i);
+            }
+        }
+    }
+    if (valid && !done) raise_status(st, ST_NOCONV, i);
+    bool any_relist = __any_sync(kFull, relist);
+    if (any_relist) {
+        if (valid) h_seed[i] = relist ? out_h : (conv ? out_h : h);
+        if (lane == 0) {
+            unsigned pos = atomicAdd(&st->redo_count, 1u);
+            redo_out[pos] = (unsigned)A;
+        }
+    } else if (valid && conv) {
+        h_out[i] = out_h;
+        rho_out[i] = out_rho;
+        omega_out[i] = out_om;
+        nngb_out[i] = (uint16_t)min(out_n, 65535);
+        iters_out[i] = (uint8_t)min(iters, 255);
+        if (EMIT && count_out) count_out[i] = (uint32_t)out_n;
+    }
+    unsigned long long wp = warp_sum(pairs), wc = warp_sum(cands);
+    int wi = (int)warp_max((float)iters);
+    if (lane == 0) {
+        atomicAdd(&st->density_pairs, wp);
+        atomicAdd(&st->density_cand, wc);
+        atomicMax(&st->max_iters, wi);
+    }
+}
+
+template <class K, bool EMIT>
+__global__ void __launch_bounds__(128) k_density(
+    KParams kp, const float4 *__restrict__ pm, const unsigned *__restrict__ list_start,
+    const unsigned *__restrict__ list_cnt, const uint4 *__restrict__ list,
+    const unsigned *__restrict__ bucket_ids, int nbuckets, float *h_seed, float *h_out,
+    float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
+    long long cap, uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
+    unsigned *redo_out, DevStatus *st)
+{
+    __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
+    __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi = blockIdx.x * kWarpsPerBlock + wib;
+    if (bi >= nbuckets) return;
+    const int A = bucket_ids ? (int)bucket_ids[bi] : bi;
+    const int i = A * kBucket + lane;
+    const bool valid = i < kp.n;
+    const float4 me = valid ? pm[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+    // sink centre (periodic images are chosen nearest to it) and whether
+    // pair separations need their own minimum-image wrap
+    float cen[3];
+    bool wrap = false;
+    {
+        const float R = valid ? h_seed[i] * (1.f + kp.margin) : 0.f;
+        const float Rm = warp_max(R);
+        const float p[3] = {me.x, me.y, me.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float mn = warp_min(valid ? p[a] : INFINITY), mx = warp_max(valid ? p[a] : -INFINITY);
+            cen[a] = 0.5f * (mn + mx);
+            if (kp.periodic[a] && 0.5f * (mx - mn) + Rm > 0.49f * kp.L[a]) wrap = true;
+        }
+    }
+    float4 *cand = cand_s[wib];
+    int *candj = EMIT ? candj_s[wib] : nullptr;
+    if (wrap)
+        density_bucket<K, true, EMIT>(kp, A, lane, cand, candj, pm, list_start, list_cnt, list,
+                                      h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
+                                      fixed_h, cap, count_out, ids_out, id_in, redo_out, st, me,
+                                      valid, cen);
+    else
+        density_bucket<K, false, EMIT>(kp, A, lane, cand, candj, pm, list_start, list_cnt, list,
+                                       h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
+                                       fixed_h, cap, count_out, ids_out, id_in, redo_out, st, me,
+                                       valid, cen);
+}
+
+__global__ void k_isentropic(int n, double g1, const float *__restrict__ rho,
+                             const float *__restrict__ rho_old, double *u)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float ro = rho_old[i];
+    if (ro > 0.f) u[i] *= pow((double)rho[i] / (double)ro, g1);
+}
+
+cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed,
+                           const unsigned *bucket_ids, int nbuckets, int fixed_h, int64_t cap,
+                           uint32_t *count, int64_t *ids, cudaStream_t s)
+{
+    if (nbuckets <= 0) return cudaSuccess;
+    int g = (nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    bool emit = ids != nullptr || count != nullptr;
+    unsigned *redo_out = c.redo + (bucket_ids == c.redo ? c.nb_cap : 0);
+    c.launches += 1;
+    SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
+        if (emit)
+            k_density<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
+                c.kp, c.pm, c.list_start, c.list_cnt, (const uint4 *)c.list, bucket_ids, nbuckets,
+                (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
+                count, ids, p.id, redo_out, c.st);
+        else
+            k_density<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
+                c.kp, c.pm, c.list_start, c.list_cnt, (const uint4 *)c.list, bucket_ids, nbuckets,
+                (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
+                count, ids, p.id, redo_out, c.st);
+    )
+    return cudaGetLastError();
+}
+
+cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    int n = (int)p.n;
+    c.launches += 1;
+    k_isentropic<<<(n + 255) / 256, 256, 0, s>>>(n, c.prm.gamma - 1.0, p.rho, c.rho_old, p.u);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

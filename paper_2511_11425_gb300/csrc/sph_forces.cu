@@ -1,0 +1,405 @@
+// sph_forces.cu -- time derivatives (Sec. 2.3.5) and time-step limits (Sec. 2.3.6).
+//
+// For every unordered pair (i, j) with r_ij < max(h_i, h_j), evaluated ONCE:
+//   F_i = dW_ij(h_i)/dr / r = sigma h_i^-5 (w'(q_i)/q_i)     (grad_i W_ij(h_i) = r_ij F_i)
+//   pressure:  a_i -= m_j (A_i F_i + A_j F_j) r_ij,  a_j += m_i (A_i F_i + A_j F_j) r_ij,
+//              A = P / (Omega rho^2)                               (momentum equation)
+//   S_i += m_j (v_ij.r_ij) F_i,  S_j += m_i (v_ij.r_ij) F_j          (S = sum m v_ij.grad W)
+//   viscosity, only for v_ij.r_ij < 0:
+//              mu = hbar (v_ij.r_ij)/(r^2 + eps hbar^2),
+//              Pi = (-alpha cbar mu + beta mu^2)/rhobar,  Fbar = (F_i + F_j)/2
+//              a_i -= m_j Pi Fbar r_ij,  a_j += m_i Pi Fbar r_ij
+//              du_i|Pi += m_j Pi (v_ij.r_ij) Fbar / 2,  du_j|Pi += m_i Pi (v_ij.r_ij) Fbar / 2
+//   Courant:   max_j |min(0, mu_ij)| for both particles
+// and afterwards (finalize)
+//   du/dt|H = A_i S_i (PdV equation),  div v = -S_i/(Omega_i rho_i),
+//   dt_i = min(eta_a sqrt(h_i/|a_i|), eta_C h_i / ((1+0.6 alpha) c_i + 0.6 beta max|mu|)).
+//
+// GPU mapping: one warp per sink bucket A, lane = sink particle.  The list
+// holds source buckets B >= A whose bounds pass the gather or scatter test
+// (Sec. 2.3.2); source particles are culled per particle, compacted into a
+// 128-entry shared-memory chunk, and each lane evaluates only its own hits
+// (128-bit mask).  Contributions to the sink stay in registers; the equal
+// and opposite contributions to the sources accumulate in shared memory per
+// chunk and are flushed with one vector reduction (red.global.add.v4.f32)
+// per touched source.  j > i is required inside bucket A, so every pair is
+// computed exactly once.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ---------------------------------------------------------------------------
+// predictor + EOS (Sec. 2.3.6 step 2, Sec. 2.3.1)
+// ---------------------------------------------------------------------------
+__global__ void k_predict(KParams kp, int n, const double *__restrict__ vx,
+                          const double *__restrict__ vy, const double *__restrict__ vz,
+                          const double *__restrict__ u, const float *__restrict__ ax,
+                          const float *__restrict__ ay, const float *__restrict__ az,
+                          const float *__restrict__ dudt_h, const float *__restrict__ dudt_av,
+                          const float *__restrict__ h, const float *__restrict__ rho,
+                          const float *__restrict__ omega, const float4 *__restrict__ pm,
+                          const double *__restrict__ dts, float4 *fpos, float4 *fvel, float4 *fth,
+                          float4 *acc, float2 *acc2, unsigned *dtmin, DevStatus *st)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *dtmin = 0x7f800000u;  // +inf
+    if (i >= n) return;
+    const double hdt = 0.5 * dts[0];
+    double v[3] = {vx[i], vy[i], vz[i]};
+    double uu = u[i];
+    if (hdt > 0.0) {
+        v[0] += hdt * (double)ax[i];
+        v[1] += hdt * (double)ay[i];
+        v[2] += hdt * (double)az[i];
+        double ud = (double)dudt_av[i];
+        if (kp.energy_mode == SPH_ENERGY_PDV) ud += (double)dudt_h[i];
+        uu += hdt * ud;
+    }
+    float r = rho[i], om = omega[i], hi = h[i];
+    float P = (kp.gamma - 1.f) * r * (float)uu;
+    float c = sqrtf(kp.gamma * P / r);
+    float A = P / (om * r * r);
+    if (!(isfinite(A) && isfinite(c) && uu >= 0.0)) raise_status(st, ST_NONFINITE, i);
+    float4 q = pm[i];
+    fpos[i] = make_float4(q.x, q.y, q.z, hi);
+    fvel[i] = make_float4((float)v[0], (float)v[1], (float)v[2], q.w);
+    fth[i] = make_float4(A, c, r, om);
+    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc2[i] = make_float2(0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// pair-symmetric force kernel
+// ---------------------------------------------------------------------------
+struct SinkState {
+    float px, py, pz, h, h2, ih, ih5;  // position, smoothing length, sigma h^-5
+    float vx, vy, vz, m;
+    float A, c, rho;
+    Kahan ax, ay, az, S;
+    float du, mumax;
+    int i;
+    unsigned long long pairs, av;
+};
+
+template <class K, bool WRAP>
+__device__ __forceinline__ void force_chunk(const KParams &kp, const float4 *cpos, const int *cidx,
+                                            float4 *fa, float2 *fb, int c, SinkState &s,
+                                            bool valid, int lane,
+                                            const float4 *__restrict__ fvel,
+                                            const float4 *__restrict__ fth, float4 *acc,
+                                            float2 *acc2)
+{
+    for (int k = lane; k < c; k += 32) {
+        fa[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        fb[k] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    unsigned long long m0 = 0ull, m1 = 0ull;
+    if (valid) {
+        for (int k = 0; k < c; ++k) {
+            float4 q = cpos[k];
+            float dx = s.px - q.x, dy = s.py - q.y, dz = s.pz - q.z;
+            if (WRAP) {
+                if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+                if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+                if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+            }
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool hit = r2 < fmaxf(s.h2, q.w * q.w) && cidx[k] > s.i;
+            if (k < 64) m0 |= (unsigned long long)hit << k;
+            else m1 |= (unsigned long long)hit << (k - 64);
+        }
+    }
+    float sax = 0.f, say = 0.f, saz = 0.f, sS = 0.f;
+    while (m0 | m1) {
+        int k;
+        if (m0) {
+            k = __ffsll((long long)m0) - 1;
+            m0 &= m0 - 1ull;
+        } else {
+            k = 63 + __ffsll((long long)m1);
+            m1 &= m1 - 1ull;
+        }
+        const float4 q = cpos[k];
+        const int j = cidx[k];
+        const float4 vj = __ldg(&fvel[j]);
+        const float4 tj = __ldg(&fth[j]);
+        float dx = s.px - q.x, dy = s.py - q.y, dz = s.pz - q.z;
+        if (WRAP) {
+            if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+            if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+            if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+        }
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
+        const float hj = q.w, ihj = 1.f / hj;
+        const float ihj2 = ihj * ihj;
+        const float qi = r * s.ih, qj = r * ihj;
+        const float Fi = qi < 1.f ? s.ih5 * K::dwq(qi) : 0.f;
+        const float Fj = qj < 1.f ? K::sigma * ihj2 * ihj2 * ihj * K::dwq(qj) : 0.f;
+        const float wx = s.vx - vj.x, wy = s.vy - vj.y, wz = s.vz - vj.z;
+        const float vr = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+        float coef = fmaf(s.A, Fi, tj.x * Fj);
+        float du = 0.f, mneg = 0.f;
+        if (vr < 0.f) {
+            const float hb = 0.5f * (s.h + hj), cb = 0.5f * (s.c + tj.y), rb = 0.5f * (s.rho + tj.z);
+            const float mu = hb * vr / fmaf(kp.eps_av * hb, hb, r2);
+            const float Pi = fmaf(-kp.alpha * cb, mu, kp.beta * mu * mu) / rb;
+            const float Fb = 0.5f * (Fi + Fj);
+            coef = fmaf(Pi, Fb, coef);
+            du = 0.5f * Pi * vr * Fb;
+            mneg = -mu;
+            ++s.av;
+        }
+        // sink side (registers)
+        const float cm = coef * vj.w;
+        sax = fmaf(-cm, dx, sax);
+        say = fmaf(-cm, dy, say);
+        saz = fmaf(-cm, dz, saz);
+        sS = fmaf(vj.w * vr, Fi, sS);
+        s.du = fmaf(vj.w, du, s.du);
+        s.mumax = fmaxf(s.mumax, mneg);
+        // source side (shared memory, equal and opposite)
+        const float cs = coef * s.m;
+        atomicAdd(&fa[k].x, cs * dx);
+        atomicAdd(&fa[k].y, cs * dy);
+        atomicAdd(&fa[k].z, cs * dz);
+        atomicAdd(&fa[k].w, s.m * vr * Fj);
+        if (vr < 0.f) {
+            atomicAdd(&fb[k].x, s.m * du);
+            atomicMax((int *)&fb[k].y, __float_as_int(mneg));
+        }
+        ++s.pairs;
+    }
+    s.ax.add(sax);
+    s.ay.add(say);
+    s.az.add(saz);
+    s.S.add(sS);
+    __syncwarp();
+    for (int k = lane; k < c; k += 32) {
+        float4 f = fa[k];
+        float2 g = fb[k];
+        int j = cidx[k];
+        if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) red_add_v4(&acc[j], f.x, f.y, f.z, f.w);
+        if (g.x != 0.f) red_add_f32(&acc2[j].x, g.x);
+        if (g.y > 0.f) atomicMax((int *)&acc2[j].y, __float_as_int(g.y));
+    }
+    __syncwarp();
+}
+
+template <class K, bool WRAP>
+__device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane, float4 *cpos,
+                                             int *cidx, float4 *fa, float2 *fb, SinkState &s,
+                                             bool valid, const float *cen, const float *sbl,
+                                             const float *sbh, const float *bxl,
+                                             const float *bxh,
+                                             const float4 *__restrict__ fpos,
+                                             const float4 *__restrict__ fvel,
+                                             const float4 *__restrict__ fth,
+                                             const unsigned *__restrict__ list_start,
+                                             const unsigned *__restrict__ list_cnt,
+                                             const uint4 *__restrict__ list, float4 *acc,
+                                             float2 *acc2, unsigned long long &cands)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned s0 = list_start[A], nl = list_cnt[A];
+    int c = 0;
+    for (unsigned e = 0; e < nl; ++e) {
+        uint4 L4 = list[s0 + e];
+        int j = (int)L4.x * kBucket + lane;
+        bool vj = j < kp.n;
+        float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float sp[3] = {__uint_as_float(L4.y) + q.x, __uint_as_float(L4.z) + q.y,
+                       __uint_as_float(L4.w) + q.z};
+        bool gather = true;
+        float dd = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // distances to the sink bounds on the circle of a periodic axis
+            float dg = sp[a] - 0.5f * (sbl[a] + sbh[a]);
+            float dc = sp[a] - cen[a];
+            if (kp.periodic[a]) {
+                sp[a] -= kp.L[a] * rintf(dc * kp.invL[a]);
+                dg = wrapf(dg, kp.L[a], kp.invL[a]);
+                dc = wrapf(dc, kp.L[a], kp.invL[a]);
+            }
+            gather = gather && fabsf(dg) <= 0.5f * (sbh[a] - sbl[a]);
+            float o = fmaxf(fabsf(dc) - 0.5f * (bxh[a] - bxl[a]), 0.f);
+            dd = fmaf(o, o, dd);
+        }
+        bool in = vj && (gather || dd < q.w * q.w);
+        unsigned bal = __ballot_sync(kFull, in);
+        if (in) {
+            int pos = c + __popc(bal & lt);
+            cpos[pos] = make_float4(sp[0], sp[1], sp[2], q.w);
+            cidx[pos] = j;
+        }
+        c += __popc(bal);
+        if (c > kChunk - 32) {
+            __syncwarp();
+            cands += c;
+            force_chunk<K, WRAP>(kp, cpos, cidx, fa, fb, c, s, valid, lane, fvel, fth, acc, acc2);
+            c = 0;
+        }
+    }
+    if (c > 0) {
+        __syncwarp();
+        cands += c;
+        force_chunk<K, WRAP>(kp, cpos, cidx, fa, fb, c, s, valid, lane, fvel, fth, acc, acc2);
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__restrict__ fpos,
+                                                const float4 *__restrict__ fvel,
+                                                const float4 *__restrict__ fth,
+                                                const unsigned *__restrict__ list_start,
+                                                const unsigned *__restrict__ list_cnt,
+                                                const uint4 *__restrict__ list,
+                                                const float4 *__restrict__ node, float4 *acc,
+                                                float2 *acc2, DevStatus *st)
+{
+    __shared__ float4 cpos_s[kWarpsPerBlock][kChunk];
+    __shared__ int cidx_s[kWarpsPerBlock][kChunk];
+    __shared__ float4 fa_s[kWarpsPerBlock][kChunk];
+    __shared__ float2 fb_s[kWarpsPerBlock][kChunk];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int A = blockIdx.x * kWarpsPerBlock + wib;
+    if (A >= kp.nb) return;
+    const int i = A * kBucket + lane;
+    const bool valid = i < kp.n;
+    SinkState s;
+    {
+        float4 q = valid ? fpos[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+        float4 v = valid ? fvel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 t = valid ? fth[i] : make_float4(0.f, 0.f, 1.f, 1.f);
+        s.px = q.x; s.py = q.y; s.pz = q.z; s.h = q.w;
+        s.h2 = q.w * q.w;
+        s.ih = 1.f / q.w;
+        float ih2 = s.ih * s.ih;
+        s.ih5 = K::sigma * ih2 * ih2 * s.ih;
+        s.vx = v.x; s.vy = v.y; s.vz = v.z; s.m = v.w;
+        s.A = t.x; s.c = t.y; s.rho = t.z;
+        s.du = 0.f;
+        s.mumax = 0.f;
+        s.i = valid ? i : 0x7fffffff;
+        s.pairs = 0;
+        s.av = 0;
+    }
+    // sink cell bound and box of balls in the sink frame; wrap decision
+    float cen[3], sbl[3], sbh[3], bxl[3], bxh[3];
+    bool wrap = false;
+    const float Hmax = node[4 * 1 + 3].w;  // largest h of all particles (root)
+    {
+        const float p[3] = {s.px, s.py, s.pz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bxl[a] = warp_min(valid ? p[a] : INFINITY);
+            bxh[a] = warp_max(valid ? p[a] : -INFINITY);
+            sbl[a] = warp_min(valid ? p[a] - s.h : INFINITY);
+            sbh[a] = warp_max(valid ? p[a] + s.h : -INFINITY);
+            cen[a] = 0.5f * (bxl[a] + bxh[a]);
+            if (kp.periodic[a] && 0.5f * (bxh[a] - bxl[a]) + Hmax > 0.49f * kp.L[a]) wrap = true;
+        }
+    }
+    unsigned long long cands = 0;
+    float4 *cpos = cpos_s[wib];
+    int *cidx = cidx_s[wib];
+    float4 *fa = fa_s[wib];
+    float2 *fb = fb_s[wib];
+    if (wrap)
+        force_bucket<K, true>(kp, A, lane, cpos, cidx, fa, fb, s, valid, cen, sbl, sbh, bxl, bxh,
+                              fpos, fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
+    else
+        force_bucket<K, false>(kp, A, lane, cpos, cidx, fa, fb, s, valid, cen, sbl, sbh, bxl, bxh,
+                               fpos, fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
+    if (valid) {
+        red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.S.s);
+        if (s.du != 0.f) red_add_f32(&acc2[i].x, s.du);
+        if (s.mumax > 0.f) atomicMax((int *)&acc2[i].y, __float_as_int(s.mumax));
+    }
+    unsigned long long wp = warp_sum(s.pairs), wav = warp_sum(s.av);
+    if (lane == 0) {
+        atomicAdd(&st->force_pairs, wp);
+        atomicAdd(&st->force_av_pairs, wav);
+        atomicAdd(&st->force_cand, cands * 32ull);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalize: PdV term, div v, time-step limits, global minimum
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(KParams kp, int n, const float4 *__restrict__ acc,
+                           const float2 *__restrict__ acc2, const float4 *__restrict__ fpos,
+                           const float4 *__restrict__ fth, float *ax, float *ay, float *az,
+                           float *dudt_h, float *dudt_av, float *divv, float *dt_i,
+                           unsigned *dtmin, DevStatus *st)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float dt = INFINITY;
+    if (i < n) {
+        float4 f = acc[i];
+        float2 g = acc2[i];
+        float4 t = fth[i];
+        float h = fpos[i].w;
+        ax[i] = f.x;
+        ay[i] = f.y;
+        az[i] = f.z;
+        dudt_h[i] = t.x * f.w;
+        dudt_av[i] = g.x;
+        divv[i] = -f.w / (t.w * t.z);
+        float amag = sqrtf(fmaf(f.x, f.x, fmaf(f.y, f.y, f.z * f.z)));
+        float dta = amag > 0.f ? kp.eta_acc * sqrtf(h / amag) : INFINITY;
+        float dtc = kp.eta_courant * h /
+                    fmaf(1.f + 0.6f * kp.alpha, t.y, 0.6f * kp.beta * g.y);
+        dt = fminf(dta, dtc);
+        dt_i[i] = dt;
+        if (!(isfinite(f.x) && isfinite(f.y) && isfinite(f.z) && isfinite(f.w) && isfinite(g.x)))
+            raise_status(st, ST_NONFINITE, i);
+    }
+    dt = warp_min(dt);
+    __shared__ float sm[8];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dt;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;
+        v = warp_min(v);
+        if (threadIdx.x == 0 && v < INFINITY) atomicMin(dtmin, __float_as_uint(v));
+    }
+}
+
+cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    int n = (int)p.n;
+    c.launches += 1;
+    k_predict<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, p.v[0], p.v[1], p.v[2], p.u, p.a[0], p.a[1],
+                                              p.a[2], p.dudt_h, p.dudt_av, p.h, p.rho, p.omega,
+                                              c.pm, c.dts, c.fpos, c.fvel, c.fth, c.acc, c.acc2,
+                                              c.dtmin, c.st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    (void)p;
+    int g = (c.kp.nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    c.launches += 1;
+    SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
+        k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.fpos, c.fvel, c.fth, c.list_start,
+                                                        c.list_cnt, (const uint4 *)c.list, c.node,
+                                                        c.acc, c.acc2, c.st);
+    )
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    int n = (int)p.n;
+    c.launches += 1;
+    k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.acc, c.acc2, c.fpos, c.fth, p.a[0],
+                                               p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, p.dt_i,
+                                               c.dtmin, c.st);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,129 @@
+// sph_integrate.cu -- kick-drift-kick with one global step (Sec. 2.3.6) and
+// the conserved totals.
+//
+//   closing kick   v_i = v_{i-1/2} + dt_old/2 a_i,      u_i likewise with du/dt
+//   step choice    dt_new = dt_fixed, or min_i dt_i (Sec. 2.3.6 criteria)
+//   opening kick   v_{i+1/2} = v_i + dt_new/2 a_i,     u likewise
+//   drift          x_{i+1} = x_i + dt_new v_{i+1/2}, wrapped into periodic boxes
+// du/dt is du/dt|H + du/dt|Pi (PdV form) or du/dt|Pi alone when u is moved
+// along its adiabat after the density pass (entropy-conserving form).
+// Everything here is FP64 per particle and memory-bound.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+__global__ void k_choose_dt(double *dts, const unsigned *dtmin, double dt_fixed, DevStatus *st)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dt = dt_fixed > 0.0 ? dt_fixed : (double)__uint_as_float(*dtmin);
+    if (!(dt > 0.0) || !isfinite(dt)) {
+        raise_status(st, ST_NONFINITE, -1);
+        dt = 0.0;
+    }
+    dts[1] = dt;
+}
+
+__global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double *vx, double *vy,
+                      double *vz, double *u, const float *__restrict__ ax,
+                      const float *__restrict__ ay, const float *__restrict__ az,
+                      const float *__restrict__ dudt_h, const float *__restrict__ dudt_av,
+                      const double *__restrict__ dts)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dt_old = dts[0], dt_new = dts[1];
+    const double kick = 0.5 * (dt_old + dt_new);
+    double ud = (double)dudt_av[i];
+    if (kp.energy_mode == SPH_ENERGY_PDV) ud += (double)dudt_h[i];
+    double v0 = vx[i] + kick * (double)ax[i];
+    double v1 = vy[i] + kick * (double)ay[i];
+    double v2 = vz[i] + kick * (double)az[i];
+    vx[i] = v0;
+    vy[i] = v1;
+    vz[i] = v2;
+    u[i] += kick * ud;
+    double p[3] = {x[i] + dt_new * v0, y[i] + dt_new * v1, z[i] + dt_new * v2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (kp.periodic[a]) {
+            double L = kp.hi[a] - kp.lo[a];
+            double t = p[a] - kp.lo[a];
+            t -= L * floor(t / L);
+            if (t >= L) t -= L;
+            p[a] = kp.lo[a] + t;
+        }
+    }
+    x[i] = p[0];
+    y[i] = p[1];
+    z[i] = p[2];
+}
+
+// conserved totals: fixed-order block tree reduction, then one block sums
+// the block partials in order (bit-identical from run to run)
+constexpr int kConsThreads = 256;
+
+__global__ void __launch_bounds__(kConsThreads) k_cons_partial(
+    int n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
+    const double *__restrict__ u, const float *__restrict__ m, double *part)
+{
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * kConsThreads + threadIdx.x; i < n; i += gridDim.x * kConsThreads) {
+        double mi = (double)m[i];
+        double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
+        acc[0] += mi;
+        acc[1] += mi * v[0];
+        acc[2] += mi * v[1];
+        acc[3] += mi * v[2];
+        acc[4] += mi * (p[1] * v[2] - p[2] * v[1]);
+        acc[5] += mi * (p[2] * v[0] - p[0] * v[2]);
+        acc[6] += mi * (p[0] * v[1] - p[1] * v[0]);
+        acc[7] += 0.5 * mi * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        acc[8] += mi * u[i];
+    }
+    __shared__ double sm[9][kConsThreads];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sm[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int o = kConsThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 9) part[blockIdx.x * 9 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_cons_final(int nparts, const double *part, double *out)
+{
+    if (threadIdx.x >= 9) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[b * 9 + threadIdx.x];
+    out[threadIdx.x] = s;
+}
+
+constexpr int kConsBlocks = 304;
+
+cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s)
+{
+    int n = (int)p.n;
+    c.launches += 2;
+    k_choose_dt<<<1, 32, 0, s>>>(c.dts, c.dtmin, dt_fixed, c.st);
+    k_kdk<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2],
+                                          p.u, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av, c.dts);
+    cudaMemcpyAsync(c.dts, c.dts + 1, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    int n = (int)p.n;
+    c.launches += 2;
+    k_cons_partial<<<kConsBlocks, kConsThreads, 0, s>>>(n, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1],
+                                                        p.v[2], p.u, p.m, c.cons_part);
+    k_cons_final<<<1, 32, 0, s>>>(kConsBlocks, c.cons_part, c.cons_out);
+    return cudaGetLastError();
+}
+
+}  // namespace sph
