@@ -70,6 +70,7 @@ int ilog2_ceil(int v)
 bool particles_ok(const sph_particles *p)
 {
     if (!p) return false;
+    if (p->n == 0) return true;  // empty arrays may be NULL
     const void *ptrs[] = {p->x[0], p->x[1], p->x[2], p->v[0], p->v[1], p->v[2], p->u, p->m,
                           p->h, p->rho, p->omega, p->a[0], p->a[1], p->a[2], p->dudt_h,
                           p->dudt_av, p->divv, p->dt_i, p->nngb, p->iters, p->id};
