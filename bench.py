@@ -79,7 +79,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -235,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     kd = kf = 0.0
-    dpairs = fpairs = fav = 0
+    dpairs = fpairs = fav = dcand = fcand = 0
     t_sim = 0.0
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
@@ -249,6 +249,8 @@ def run_ours(args, rank, world, local_rank):
             dpairs += st["density_pairs"]
             fpairs += st["force_pairs"]
             fav += st["force_av_pairs"]
+            dcand += st["density_candidates"]
+            fcand += st["force_candidates"]
         torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
@@ -314,6 +316,8 @@ def run_ours(args, rank, world, local_rank):
                 "pair_interactions_per_s": {
                     "density": world * dpairs / secs, "force": world * fpairs / secs,
                     "total": world * (dpairs + fpairs) / secs},
+                "candidates_per_useful_pair": {"density": dcand / max(dpairs, 1),
+                                               "force": fcand / max(fpairs, 1)},
                 "roofline": roof, "roofline_other": other_line, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
                 "impl": "ours"}

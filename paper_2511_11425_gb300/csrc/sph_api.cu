@@ -48,8 +48,8 @@ cudaError_t dalloc(T **p, size_t count)
 void free_ctx(Ctx &c)
 {
     void *ptrs[] = {c.st, c.dts, c.dtmin, c.morton_box, c.bbox_part, c.cons_part, c.cons_out,
-                    c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist, c.tmp, c.origin, c.node,
-                    c.node_flag, c.pm, c.fpos, c.fvel, c.fth, c.acc, c.acc2, c.rho_old, c.h_seed,
+                    c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist, c.digit_tot, c.tmp, c.origin,
+                    c.node, c.pm, c.fpos, c.fvel, c.fth, c.acc, c.acc2, c.rho_old, c.h_seed,
                     c.list_start, c.list_cnt, c.list, c.redo, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -189,6 +189,11 @@ extern "C" sph_status sph_create(const sph_params *prm, int64_t capacity, sph_ct
     k.margin = (float)prm->list_margin;
     k.hcap = (float)hcap;
     k.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
+    k.inv_q = 1.0 / k.q;
+    for (int a = 0; a < 3; ++a) {
+        k.Ld[a] = prm->box_hi[a] - prm->box_lo[a];
+        k.invLd[a] = 1.0 / k.Ld[a];
+    }
     k.eps_abs = (float)(4.0 * std::ldexp(1.0, -23) * fmax(maxext, maxabs));
 
     int64_t cap = capacity > 0 ? capacity : 1;
@@ -214,14 +219,14 @@ extern "C" sph_status sph_create(const sph_params *prm, int64_t capacity, sph_ct
     AL(c.vals[0], cap);
     AL(c.vals[1], cap);
     AL(c.hist, (size_t)256 * ntiles);
+    AL(c.digit_tot, 256);
     {
         char *t = nullptr;
-        AL(t, (size_t)64 * cap);
+        AL(t, (size_t)112 * cap);
         c.tmp = t;
     }
     AL(c.origin, (size_t)3 * c.nb_cap);
     AL(c.node, (size_t)8 * c.P_cap);
-    AL(c.node_flag, c.P_cap);
     AL(c.pm, cap);
     AL(c.fpos, cap);
     AL(c.fvel, cap);

@@ -57,7 +57,7 @@ __global__ void k_bbox_final(KParams kp, int nparts, const double *part, double 
     if (threadIdx.x != 0) return;
     for (int a = 0; a < 3; ++a) {
         double lo, hi;
-        if (kp.periodic[a]) {
+        if (kp.periodic[a] || nparts == 0) {
             lo = kp.lo[a];
             hi = kp.hi[a];
         } else {
@@ -75,106 +75,122 @@ __global__ void k_bbox_final(KParams kp, int nparts, const double *part, double 
         }
         double ext = (hi - lo) * (1.0 + 1e-9) + 1e-300;
         morton_box[a] = lo;
-        morton_box[3 + a] = 65536.0 / ext;
+        morton_box[3 + a] = (double)(1 << kMortonBits) / ext;
     }
 }
 
-__device__ __forceinline__ unsigned long long spread3(unsigned int v)
+// 10-bit coordinate -> every third bit of a 30-bit word
+__device__ __forceinline__ unsigned spread3(unsigned x)
 {
-    unsigned long long x = v & 0xffffu;
-    x = (x | (x << 32)) & 0x1f00000000ffffULL;
-    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
-    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
-    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
     return x;
 }
 
 __global__ void k_morton(int n, const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, const double *__restrict__ mbox,
-                         unsigned long long *keys, unsigned int *vals)
+                         unsigned *keys, unsigned int *vals)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v[3] = {x[i], y[i], z[i]};
-    unsigned int c[3];
+    unsigned c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double t = (v[a] - mbox[a]) * mbox[3 + a];
-        t = fmin(fmax(t, 0.0), 65535.0);
-        c[a] = (unsigned int)t;
+        t = fmin(fmax(t, 0.0), (double)((1 << kMortonBits) - 1));
+        c[a] = (unsigned)t;
     }
     keys[i] = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
-    vals[i] = (unsigned int)i;
+    vals[i] = (unsigned)i;
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, 8-bit digits, tiles of 4096 keys (256 threads x 16)
+// stable LSD radix sort of 30-bit keys, 8-bit digits, tiles of 2048 keys
+// (256 threads x 8).  Per pass: tile histograms, a per-digit scan over the
+// tiles (one block per digit), and a stable scatter whose ranks come from
+// warp-level match_any in key order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sort_hist(const unsigned long long *__restrict__ keys,
-                                                   int n, int shift, unsigned int *hist, int ntiles)
+__global__ void __launch_bounds__(256) k_sort_hist(const unsigned *__restrict__ keys, int n,
+                                                   int shift, unsigned *hist, int ntiles)
 {
-    __shared__ unsigned int h[256];
+    __shared__ unsigned h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     int base = blockIdx.x * kSortTile;
-    for (int k = threadIdx.x; k < kSortTile; k += 256) {
-        int i = base + k;
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        int i = base + k * 256 + threadIdx.x;
         if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of the digit-major histogram (256 x ntiles) in one block
-__global__ void __launch_bounds__(1024) k_sort_scan(unsigned int *hist, int total)
+// block d: exclusive scan of digit d's counts over the tiles; total -> tot[d]
+__global__ void __launch_bounds__(1024) k_sort_rowscan(unsigned *hist, int ntiles, unsigned *tot)
 {
-    __shared__ unsigned int part[1024];
+    __shared__ unsigned part[1024];
+    unsigned *row = hist + (size_t)blockIdx.x * ntiles;
     int t = threadIdx.x;
-    int per = (total + 1023) / 1024;
-    int b0 = min(total, t * per), b1 = min(total, b0 + per);
-    unsigned int s = 0;
-    for (int k = b0; k < b1; ++k) s += hist[k];
+    int per = (ntiles + 1023) / 1024;
+    int b0 = min(ntiles, t * per), b1 = min(ntiles, b0 + per);
+    unsigned s = 0;
+    for (int k = b0; k < b1; ++k) s += row[k];
     part[t] = s;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
-        unsigned int v = t >= o ? part[t - o] : 0u;
+        unsigned v = t >= o ? part[t - o] : 0u;
         __syncthreads();
         part[t] += v;
         __syncthreads();
     }
-    unsigned int run = part[t] - s;
+    unsigned run = part[t] - s;
     for (int k = b0; k < b1; ++k) {
-        unsigned int c = hist[k];
-        hist[k] = run;
+        unsigned c = row[k];
+        row[k] = run;
         run += c;
     }
+    if (t == 1023) tot[blockIdx.x] = part[1023];
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(const unsigned long long *__restrict__ kin,
-                                                      const unsigned int *__restrict__ vin,
-                                                      unsigned long long *__restrict__ kout,
-                                                      unsigned int *__restrict__ vout, int n,
-                                                      int shift, const unsigned int *__restrict__ hist,
-                                                      int ntiles)
+__global__ void __launch_bounds__(256) k_sort_scatter(const unsigned *__restrict__ kin,
+                                                      const unsigned *__restrict__ vin,
+                                                      unsigned *__restrict__ kout,
+                                                      unsigned *__restrict__ vout, int n,
+                                                      int shift, const unsigned *__restrict__ hist,
+                                                      const unsigned *__restrict__ tot, int ntiles)
 {
-    __shared__ unsigned int wcnt[8][256];
-    __shared__ unsigned int toff[256];
+    __shared__ unsigned wcnt[8][256];
+    __shared__ unsigned toff[256];
+    __shared__ unsigned base_s[256];
     int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int k = tid; k < 8 * 256; k += 256) (&wcnt[0][0])[k] = 0;
-    toff[tid] = hist[tid * ntiles + blockIdx.x];
+    base_s[tid] = tot[tid];
+    __syncthreads();
+    // exclusive prefix of the digit totals (Hillis-Steele in shared memory)
+    for (int o = 1; o < 256; o <<= 1) {
+        unsigned v = tid >= o ? base_s[tid - o] : 0u;
+        __syncthreads();
+        base_s[tid] += v;
+        __syncthreads();
+    }
+    toff[tid] = base_s[tid] - tot[tid] + hist[tid * ntiles + blockIdx.x];
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long key[16];
-    unsigned int val[16], rnk[16];
-    int base = blockIdx.x * kSortTile + w * 512;
+    unsigned key[kSortItems], val[kSortItems], rnk[kSortItems];
+    const int per_warp = 32 * kSortItems;
+    int base = blockIdx.x * kSortTile + w * per_warp;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < kSortItems; ++r) {
         int i = base + r * 32 + lane;
         bool ok = i < n;
-        key[r] = ok ? kin[i] : 0ull;
+        key[r] = ok ? kin[i] : 0u;
         val[r] = ok ? vin[i] : 0u;
-        unsigned d = ok ? (unsigned)((key[r] >> shift) & 255u) : 256u;
+        unsigned d = ok ? ((key[r] >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(kFull, d);
         unsigned before = 0;
         if (ok) before = wcnt[w][d];
@@ -194,10 +210,10 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const unsigned long long *
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < kSortItems; ++r) {
         int i = base + r * 32 + lane;
         if (i < n) {
-            unsigned d = (unsigned)((key[r] >> shift) & 255u);
+            unsigned d = (key[r] >> shift) & 255u;
             unsigned pos = toff[d] + wcnt[w][d] + rnk[r];
             kout[pos] = key[r];
             vout[pos] = val[r];
@@ -206,59 +222,55 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const unsigned long long *
 }
 
 // ---------------------------------------------------------------------------
-// in-place permutation of the caller's arrays through a scratch buffer
+// in-place permutation of every caller array through one scratch buffer
 // ---------------------------------------------------------------------------
-template <class T, int NF>
-struct Fields {
-    T *f[NF];
-    int nf;
+struct PermFields {
+    unsigned long long *f8[8];
+    float *f4[11];
+    uint16_t *f2;
+    uint8_t *f1;
 };
 
-template <class T, int NF>
-__global__ void k_gather(const unsigned int *__restrict__ perm, int n, Fields<T, NF> fp,
-                         T *__restrict__ tmp)
+__global__ void k_gather_all(const unsigned *__restrict__ perm, int n, PermFields pf, char *tmp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     unsigned j = perm[i];
+    unsigned long long *t8 = (unsigned long long *)tmp;
+    float *t4 = (float *)(t8 + (size_t)8 * n);
+    uint16_t *t2 = (uint16_t *)(t4 + (size_t)11 * n);
+    uint8_t *t1 = (uint8_t *)(t2 + n);
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-        if (f < fp.nf) tmp[(size_t)f * n + i] = fp.f[f][j];
+    for (int f = 0; f < 8; ++f) t8[(size_t)f * n + i] = pf.f8[f][j];
+#pragma unroll
+    for (int f = 0; f < 11; ++f) t4[(size_t)f * n + i] = pf.f4[f][j];
+    t2[i] = pf.f2[j];
+    t1[i] = pf.f1[j];
 }
 
-template <class T, int NF>
-__global__ void k_copyback(int n, Fields<T, NF> fp, const T *__restrict__ tmp)
+__global__ void k_copyback_all(int n, PermFields pf, const char *tmp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const unsigned long long *t8 = (const unsigned long long *)tmp;
+    const float *t4 = (const float *)(t8 + (size_t)8 * n);
+    const uint16_t *t2 = (const uint16_t *)(t4 + (size_t)11 * n);
+    const uint8_t *t1 = (const uint8_t *)(t2 + n);
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-        if (f < fp.nf) fp.f[f][i] = tmp[(size_t)f * n + i];
-}
-
-template <class T, int NF>
-static void permute(const unsigned *perm, int n, Fields<T, NF> fp, void *tmp, cudaStream_t s)
-{
-    int nb = (n + 255) / 256;
-    k_gather<T, NF><<<nb, 256, 0, s>>>(perm, n, fp, (T *)tmp);
-    k_copyback<T, NF><<<nb, 256, 0, s>>>(n, fp, (const T *)tmp);
+    for (int f = 0; f < 8; ++f) pf.f8[f][i] = t8[(size_t)f * n + i];
+#pragma unroll
+    for (int f = 0; f < 11; ++f) pf.f4[f][i] = t4[(size_t)f * n + i];
+    pf.f2[i] = t2[i];
+    pf.f1[i] = t1[i];
 }
 
 // ---------------------------------------------------------------------------
-// buckets: origin, relative positions, leaf bounds
+// buckets: origin, relative positions, leaf bounds.  One warp per bucket.
+// Offsets from the bucket's first particle are formed in FP64 (minimum image
+// on periodic axes) and every reduction runs in FP32 on those offsets.
+// With update_pos = 0 only the box-of-balls is refreshed from the current h
+// (bounds update after the density pass, Sec. 2.3.3).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_node(float4 *node, int k, float3 bc, float3 br, float3 oc,
-                                           float3 orr, float hmax)
-{
-    node[4 * k + 0] = make_float4(bc.x, bc.y, bc.z, 0.f);
-    node[4 * k + 1] = make_float4(br.x, br.y, br.z, 0.f);
-    node[4 * k + 2] = make_float4(oc.x, oc.y, oc.z, 0.f);
-    node[4 * k + 3] = make_float4(orr.x, orr.y, orr.z, hmax);
-}
-
-// one warp per bucket.  With update_pos = 1 it also (re)computes the bucket
-// origin and the relative positions pm; with 0 it refreshes only the
-// box-of-balls from the current h (bounds update after the density pass).
 __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__restrict__ x,
                                                  const double *__restrict__ y,
                                                  const double *__restrict__ z,
@@ -272,59 +284,57 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
     if (b >= kp.nb) return;
     int i = b * kBucket + lane;
     bool ok = i < kp.n;
-    double xu[3];
+    float rel[3];
+    double o[3];
     if (update_pos) {
-        double v[3] = {0, 0, 0};
+        double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double first = __shfl_sync(kFull, v[a], 0);
             double d = v[a] - first;
-            if (kp.periodic[a]) d = wrapd(d, (double)(kp.hi[a] - kp.lo[a]));
-            xu[a] = first + d;  // unwrapped next to the bucket's first particle
-        }
-        double o[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double mn = warp_min(ok ? xu[a] : INFINITY);
-            o[a] = floor(mn / kp.q) * kp.q;
+            if (kp.periodic[a]) d -= kp.Ld[a] * rint(d * kp.invLd[a]);
+            float mn = warp_min(ok ? (float)d : INFINITY);
+            o[a] = floor((first + (double)mn) * kp.inv_q) * kp.q;
+            rel[a] = (float)((first - o[a]) + d);
             if (lane == 0) origin[a * kp.nb + b] = o[a];
         }
         if (ok) {
-            float4 r = make_float4((float)(xu[0] - o[0]), (float)(xu[1] - o[1]),
-                                   (float)(xu[2] - o[2]), m[i]);
-            if (!(isfinite(r.x) && isfinite(r.y) && isfinite(r.z))) raise_status(st, ST_NONFINITE, i);
-            pm[i] = r;
+            if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
+                raise_status(st, ST_NONFINITE, i);
+            pm[i] = make_float4(rel[0], rel[1], rel[2], m[i]);
         }
     } else {
-        float4 r = ok ? pm[i] : make_float4(0, 0, 0, 0);
-        xu[0] = origin[b] + (double)r.x;
-        xu[1] = origin[kp.nb + b] + (double)r.y;
-        xu[2] = origin[2 * kp.nb + b] + (double)r.z;
+        float4 r = ok ? pm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        rel[0] = r.x; rel[1] = r.y; rel[2] = r.z;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o[a] = origin[a * kp.nb + b];
     }
     float hi = ok ? h[i] : 0.f;
     if (ok && !(hi > 0.f && isfinite(hi))) raise_status(st, ST_NONFINITE, i);
     float bc[3], br[3], oc[3], orr[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double mn = warp_min(ok ? xu[a] : INFINITY), mx = warp_max(ok ? xu[a] : -INFINITY);
-        double mnb = warp_min(ok ? xu[a] - (double)hi : INFINITY);
-        double mxb = warp_max(ok ? xu[a] + (double)hi : -INFINITY);
-        bc[a] = (float)(0.5 * (mn + mx));
-        br[a] = (float)(0.5 * (mx - mn)) + kp.eps_abs;
-        oc[a] = (float)(0.5 * (mnb + mxb));
-        orr[a] = (float)(0.5 * (mxb - mnb)) + kp.eps_abs;
+        float mn = warp_min(ok ? rel[a] : INFINITY), mx = warp_max(ok ? rel[a] : -INFINITY);
+        float mnb = warp_min(ok ? rel[a] - hi : INFINITY), mxb = warp_max(ok ? rel[a] + hi : -INFINITY);
+        // absolute centres (FP64 add of the origin, then one rounding) and
+        // half widths inflated by the rounding allowance
+        bc[a] = (float)(o[a] + 0.5 * ((double)mn + (double)mx));
+        br[a] = 0.5f * (mx - mn) + kp.eps_abs;
+        oc[a] = (float)(o[a] + 0.5 * ((double)mnb + (double)mxb));
+        orr[a] = 0.5f * (mxb - mnb) + kp.eps_abs;
     }
     float hmax = warp_max(hi);
     if (lane == 0) {
         int k = kp.P + b;
         if (update_pos) {
-            store_node(node, k, make_float3(bc[0], bc[1], bc[2]), make_float3(br[0], br[1], br[2]),
-                       make_float3(oc[0], oc[1], oc[2]), make_float3(orr[0], orr[1], orr[2]), hmax);
-        } else {
-            node[4 * k + 2] = make_float4(oc[0], oc[1], oc[2], 0.f);
-            node[4 * k + 3] = make_float4(orr[0], orr[1], orr[2], hmax);
+            // .w of the cell half widths: the bucket's largest full extent
+            float ext = 2.f * fmaxf(br[0], fmaxf(br[1], br[2]));
+            node[4 * k + 0] = make_float4(bc[0], bc[1], bc[2], 0.f);
+            node[4 * k + 1] = make_float4(br[0], br[1], br[2], ext);
         }
+        node[4 * k + 2] = make_float4(oc[0], oc[1], oc[2], 0.f);
+        node[4 * k + 3] = make_float4(orr[0], orr[1], orr[2], hmax);
     }
 }
 
@@ -342,44 +352,90 @@ __device__ __forceinline__ void union1(float c1, float r1, float c2, float r2, b
     if (per && r >= 0.5f * L) r = L;  // covers the whole periodic axis
 }
 
-// bottom-up merge of the bounds (Sec. 2.3.2): one thread per leaf climbs;
-// the second child to arrive at a parent computes it
-__global__ void k_tree_up(KParams kp, float4 *node, unsigned int *flag, int bob_only)
+__device__ __forceinline__ void union_pair(const KParams &kp, const float4 *a, const float4 *b,
+                                           float4 *out, int s)
 {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= kp.P) return;
-    int k = kp.P + b;
-    if (b >= kp.nb) {
-        float4 e = make_float4(0.f, 0.f, 0.f, 0.f), er = make_float4(-1.f, -1.f, -1.f, 0.f);
-        if (!bob_only) { node[4 * k] = e; node[4 * k + 1] = er; }
-        node[4 * k + 2] = e;
-        node[4 * k + 3] = er;
-    }
-    while (k > 1) {
-        __threadfence();
-        int parent = k >> 1;
-        if (atomicAdd(&flag[parent], 1u) == 0u) return;
-        __threadfence();
-        int l = 2 * parent, r = 2 * parent + 1;
-        float4 out[4];
+    float4 c1 = a[2 * s], r1 = a[2 * s + 1], c2 = b[2 * s], r2 = b[2 * s + 1];
+    float cc[3], rr[3];
+    float a1[3] = {c1.x, c1.y, c1.z}, b1[3] = {r1.x, r1.y, r1.z};
+    float a2[3] = {c2.x, c2.y, c2.z}, b2[3] = {r2.x, r2.y, r2.z};
 #pragma unroll
-        for (int s = bob_only ? 1 : 0; s < 2; ++s) {
-            float4 c1 = __ldcg(&node[4 * l + 2 * s]), r1 = __ldcg(&node[4 * l + 2 * s + 1]);
-            float4 c2 = __ldcg(&node[4 * r + 2 * s]), r2 = __ldcg(&node[4 * r + 2 * s + 1]);
-            float cc[3], rr[3];
-            float a1[3] = {c1.x, c1.y, c1.z}, b1[3] = {r1.x, r1.y, r1.z};
-            float a2[3] = {c2.x, c2.y, c2.z}, b2[3] = {r2.x, r2.y, r2.z};
+    for (int ax = 0; ax < 3; ++ax)
+        union1(a1[ax], b1[ax], a2[ax], b2[ax], kp.periodic[ax], kp.L[ax], kp.invL[ax], kp.eps_abs,
+               cc[ax], rr[ax]);
+    out[2 * s] = make_float4(cc[0], cc[1], cc[2], 0.f);
+    out[2 * s + 1] = make_float4(rr[0], rr[1], rr[2], fmaxf(r1.w, r2.w));
+}
+
+// Bottom-up merge of the bounds (Sec. 2.3.2), `levels` tree levels per
+// launch: block b loads 2^levels consecutive nodes of level `lvl` into shared
+// memory and reduces them to one node of level lvl - levels.  Leaves of
+// padding buckets (b >= nb) are written empty on the first launch.
+__global__ void __launch_bounds__(256) k_tree_levels(KParams kp, float4 *node, int lvl, int levels,
+                                                     int bob_only)
+{
+    __shared__ float4 sn[256][4];
+    const int width = 1 << levels;
+    const int t = threadIdx.x;
+    const unsigned first = (1u << lvl) + (unsigned)blockIdx.x * width;
+    if (t < width) {
+        unsigned k = first + t;
+        if (lvl == kp.logP && (int)(k - kp.P) >= kp.nb) {
+            float4 e = make_float4(0.f, 0.f, 0.f, 0.f), er = make_float4(-1.f, -1.f, -1.f, 0.f);
+            sn[t][0] = e; sn[t][1] = er; sn[t][2] = e; sn[t][3] = er;
+            if (!bob_only) { node[4 * k] = e; node[4 * k + 1] = er; }
+            node[4 * k + 2] = e;
+            node[4 * k + 3] = er;
+        } else {
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                union1(a1[a], b1[a], a2[a], b2[a], kp.periodic[a], kp.L[a], kp.invL[a], kp.eps_abs,
-                       cc[a], rr[a]);
-            out[2 * s] = make_float4(cc[0], cc[1], cc[2], 0.f);
-            out[2 * s + 1] = make_float4(rr[0], rr[1], rr[2], fmaxf(r1.w, r2.w));
+            for (int q = 0; q < 4; ++q) sn[t][q] = node[4 * k + q];
         }
-        if (!bob_only) { __stcg(&node[4 * parent], out[0]); __stcg(&node[4 * parent + 1], out[1]); }
-        __stcg(&node[4 * parent + 2], out[2]);
-        __stcg(&node[4 * parent + 3], out[3]);
-        k = parent;
+    }
+    __syncthreads();
+    for (int l = 0; l < levels; ++l) {
+        int cnt = width >> (l + 1);
+        float4 out[4];
+        if (t < cnt) {
+            out[0] = sn[2 * t][0];
+            out[1] = sn[2 * t][1];
+            if (!bob_only) union_pair(kp, sn[2 * t], sn[2 * t + 1], out, 0);
+            union_pair(kp, sn[2 * t], sn[2 * t + 1], out, 1);
+        }
+        __syncthreads();
+        if (t < cnt) {
+            unsigned k = ((first >> (l + 1)) + t);
+            if (!bob_only) {
+                sn[t][0] = out[0];
+                sn[t][1] = out[1];
+                node[4 * k] = out[0];
+                node[4 * k + 1] = out[1];
+            } else {
+                sn[t][0] = node[4 * k];
+                sn[t][1] = node[4 * k + 1];
+            }
+            sn[t][2] = out[2];
+            sn[t][3] = out[3];
+            node[4 * k + 2] = out[2];
+            node[4 * k + 3] = out[3];
+        }
+        __syncthreads();
+    }
+}
+
+static void tree_refit(Ctx &c, cudaStream_t s, int bob_only)
+{
+    const KParams &kp = c.kp;
+    int lvl = kp.logP;
+    if (lvl == 0) {
+        // single bucket: the leaf is the root
+        return;
+    }
+    while (lvl > 0) {
+        int levels = lvl < 8 ? lvl : 8;
+        int blocks = 1 << (lvl - levels);
+        k_tree_levels<<<blocks, 256, 0, s>>>(kp, c.node, lvl, levels, bob_only);
+        c.launches += 1;
+        lvl -= levels;
     }
 }
 
@@ -539,10 +595,12 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;
     int n = (int)p.n;
-    // bounding box for the Morton quantisation
-    int nbb = 152;
-    c.launches += 2 + 1 + 3 * kSortPasses + 2 * 4 + 2;
-    k_bbox_partial<<<nbb, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.bbox_part);
+    // bounding box for the Morton quantisation (only open axes need data)
+    int nbb = (kp.periodic[0] && kp.periodic[1] && kp.periodic[2]) ? 0 : 152;
+    if (nbb) {
+        k_bbox_partial<<<nbb, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.bbox_part);
+        c.launches += 1;
+    }
     k_bbox_final<<<1, 32, 0, s>>>(kp, nbb, c.bbox_part, c.morton_box, c.st);
     int g = (n + 255) / 256;
     k_morton<<<g, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.morton_box, c.keys[0], c.vals[0]);
@@ -551,40 +609,32 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     for (int pass = 0; pass < kSortPasses; ++pass) {
         int shift = 8 * pass;
         k_sort_hist<<<ntiles, 256, 0, s>>>(c.keys[cur], n, shift, c.hist, ntiles);
-        k_sort_scan<<<1, 1024, 0, s>>>(c.hist, 256 * ntiles);
+        k_sort_rowscan<<<256, 1024, 0, s>>>(c.hist, ntiles, c.digit_tot);
         k_sort_scatter<<<ntiles, 256, 0, s>>>(c.keys[cur], c.vals[cur], c.keys[cur ^ 1],
-                                              c.vals[cur ^ 1], n, shift, c.hist, ntiles);
+                                              c.vals[cur ^ 1], n, shift, c.hist, c.digit_tot,
+                                              ntiles);
         cur ^= 1;
     }
     const unsigned *perm = c.vals[cur];
-    // permute every caller array (8-byte, 4-byte, 2-byte and 1-byte groups)
+    // permute every caller array through the scratch buffer
     typedef unsigned long long u64;
-    Fields<u64, 8> f8{};
-    f8.f[0] = (u64 *)p.x[0]; f8.f[1] = (u64 *)p.x[1]; f8.f[2] = (u64 *)p.x[2];
-    f8.f[3] = (u64 *)p.v[0]; f8.f[4] = (u64 *)p.v[1]; f8.f[5] = (u64 *)p.v[2];
-    f8.f[6] = (u64 *)p.u; f8.f[7] = (u64 *)p.id;
-    f8.nf = 8;
-    permute(perm, n, f8, c.tmp, s);
-    Fields<float, 12> f4{};
-    f4.f[0] = p.m; f4.f[1] = p.h; f4.f[2] = p.rho; f4.f[3] = p.omega;
-    f4.f[4] = p.a[0]; f4.f[5] = p.a[1]; f4.f[6] = p.a[2];
-    f4.f[7] = p.dudt_h; f4.f[8] = p.dudt_av; f4.f[9] = p.divv; f4.f[10] = p.dt_i;
-    f4.nf = 11;
-    permute(perm, n, f4, c.tmp, s);
-    Fields<uint16_t, 1> f2{};
-    f2.f[0] = p.nngb;
-    f2.nf = 1;
-    permute(perm, n, f2, c.tmp, s);
-    Fields<uint8_t, 1> f1{};
-    f1.f[0] = p.iters;
-    f1.nf = 1;
-    permute(perm, n, f1, c.tmp, s);
+    PermFields pf;
+    pf.f8[0] = (u64 *)p.x[0]; pf.f8[1] = (u64 *)p.x[1]; pf.f8[2] = (u64 *)p.x[2];
+    pf.f8[3] = (u64 *)p.v[0]; pf.f8[4] = (u64 *)p.v[1]; pf.f8[5] = (u64 *)p.v[2];
+    pf.f8[6] = (u64 *)p.u; pf.f8[7] = (u64 *)p.id;
+    pf.f4[0] = p.m; pf.f4[1] = p.h; pf.f4[2] = p.rho; pf.f4[3] = p.omega;
+    pf.f4[4] = p.a[0]; pf.f4[5] = p.a[1]; pf.f4[6] = p.a[2];
+    pf.f4[7] = p.dudt_h; pf.f4[8] = p.dudt_av; pf.f4[9] = p.divv; pf.f4[10] = p.dt_i;
+    pf.f2 = p.nngb;
+    pf.f1 = p.iters;
+    k_gather_all<<<g, 256, 0, s>>>(perm, n, pf, (char *)c.tmp);
+    k_copyback_all<<<g, 256, 0, s>>>(n, pf, (const char *)c.tmp);
     // buckets and tree
     int wb = (kp.nb * 32 + 127) / 128;
     k_buckets<<<wb, 128, 0, s>>>(kp, p.x[0], p.x[1], p.x[2], p.m, p.h, c.origin, c.pm, c.node, 1,
                                  c.st);
-    cudaMemsetAsync(c.node_flag, 0, sizeof(unsigned) * (size_t)kp.P, s);
-    k_tree_up<<<(kp.P + 255) / 256, 256, 0, s>>>(kp, c.node, c.node_flag, 0);
+    c.launches += 2 + 3 * kSortPasses + 2 + 1;
+    tree_refit(c, s, 0);
     return cudaGetLastError();
 }
 
@@ -592,11 +642,10 @@ cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;
     int wb = (kp.nb * 32 + 127) / 128;
-    c.launches += 2;
+    c.launches += 1;
     k_buckets<<<wb, 128, 0, s>>>(kp, p.x[0], p.x[1], p.x[2], p.m, p.h, c.origin, c.pm, c.node, 0,
                                  c.st);
-    cudaMemsetAsync(c.node_flag, 0, sizeof(unsigned) * (size_t)kp.P, s);
-    k_tree_up<<<(kp.P + 255) / 256, 256, 0, s>>>(kp, c.node, c.node_flag, 1);
+    tree_refit(c, s, 1);
     return cudaGetLastError();
 }
 

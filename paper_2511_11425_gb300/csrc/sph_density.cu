@@ -26,62 +26,80 @@ namespace sph {
 
 constexpr float kFourPiThird = 4.18879020478639098f;
 
+template <bool WRAP>
+__device__ __forceinline__ float sep2(const KParams &kp, float px, float py, float pz, float4 q)
+{
+    float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    if (WRAP) {
+        if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+        if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+        if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+    }
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Hit masks of one lane against the staged chunk: bit k of word w is set when
+// candidate 32w + k lies inside radius^2.  The chunk is padded with NaN
+// positions to a multiple of 32, so the fully unrolled inner loop needs no
+// bounds checks and every bit is set with an immediate mask.
+template <bool WRAP>
+__device__ __forceinline__ void hit_masks(const KParams &kp, const float4 *cand, int nwords,
+                                          float px, float py, float pz, float h2, bool active,
+                                          unsigned long long &m0, unsigned long long &m1)
+{
+    unsigned w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+    if (active) {
+#pragma unroll 1
+        for (int ww = 0; ww < nwords; ++ww) {
+            unsigned mw = 0u;
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                float r2 = sep2<WRAP>(kp, px, py, pz, cand[32 * ww + b]);
+                mw |= r2 < h2 ? (1u << b) : 0u;
+            }
+            if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
+        }
+    }
+    m0 = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
+    m1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
+}
+
+__device__ __forceinline__ int next_hit(unsigned long long &m0, unsigned long long &m1)
+{
+    int k;
+    if (m0) {
+        k = __ffsll((long long)m0) - 1;
+        m0 &= m0 - 1ull;
+    } else {
+        k = 63 + __ffsll((long long)m1);
+        m1 &= m1 - 1ull;
+    }
+    return k;
+}
+
 template <class K, bool WRAP, bool EMIT>
-__device__ __forceinline__ void density_chunk(const KParams &kp, const float4 *cand,
-                                              const int *candj, int c, float px, float py,
-                                              float pz, float h2, float ih, bool active,
-                                              Kahan &Sw, Kahan &Sq, int &cnt, int i, long long cap,
+__device__ __forceinline__ void density_chunk(const KParams &kp, float4 *cand, const int *candj,
+                                              int c, int lane, float px, float py, float pz,
+                                              float h2, float ih, bool active, Kahan &Sw,
+                                              Kahan &Sq, int &cnt, int i, long long cap,
                                               int &emitted, int64_t *ids_out,
                                               const int64_t *__restrict__ id_in)
 {
-    unsigned long long m0 = 0ull, m1 = 0ull;
-    if (active) {
-        int c0 = c < 64 ? c : 64;
-        for (int k = 0; k < c0; ++k) {
-            float4 q = cand[k];
-            float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-            if (WRAP) {
-                if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-                if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-                if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
-            }
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            m0 |= (unsigned long long)(r2 < h2) << k;
-        }
-        for (int k = 64; k < c; ++k) {
-            float4 q = cand[k];
-            float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-            if (WRAP) {
-                if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-                if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-                if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
-            }
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            m1 |= (unsigned long long)(r2 < h2) << (k - 64);
-        }
-    }
+    const int nwords = (c + 31) >> 5;
+    for (int k = c + lane; k < 32 * nwords; k += 32)
+        cand[k] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+    __syncwarp();
+    unsigned long long m0, m1;
+    hit_masks<WRAP>(kp, cand, nwords, px, py, pz, h2, active, m0, m1);
     float sw = 0.f, sq = 0.f;
     int nh = 0;
     while (m0 | m1) {
-        int k;
-        if (m0) {
-            k = __ffsll((long long)m0) - 1;
-            m0 &= m0 - 1ull;
-        } else {
-            k = 63 + __ffsll((long long)m1);
-            m1 &= m1 - 1ull;
-        }
-        float4 q = cand[k];
-        float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-        if (WRAP) {
-            if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-            if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-            if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
-        }
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
-        float qq = r * ih;
-        float wv = K::w(qq), dq = K::dwq(qq);
+        const int k = next_hit(m0, m1);
+        const float4 q = cand[k];
+        const float r2 = sep2<WRAP>(kp, px, py, pz, q);
+        const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
+        const float qq = r * ih;
+        const float wv = K::w(qq), dq = K::dwq(qq);
         sw = fmaf(q.w, wv, sw);
         sq = fmaf(q.w * dq, qq * qq, sq);
         ++nh;
@@ -123,13 +141,22 @@ __device__ __forceinline__ void density_bucket(
     for (int pass = 0; pass <= kp.max_newton; ++pass) {
         if (__all_sync(kFull, done)) break;
         const float h2 = h * h, ih = 1.f / h;
-        float bc[3], br[3];  // box of balls of the active lanes (centre, half width)
+        // box of balls and ball of balls of the active lanes (Sec. 2.3.2: a
+        // source must overlap both shapes)
+        float bc[3], br[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float bl = warp_min(done ? INFINITY : p[a] - h);
             float bh = warp_max(done ? -INFINITY : p[a] + h);
             bc[a] = 0.5f * (bl + bh);
             br[a] = 0.5f * (bh - bl);
+        }
+        float bb2;
+        {
+            float dx = p[0] - bc[0], dy = p[1] - bc[1], dz = p[2] - bc[2];
+            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + h;
+            rr = warp_max(rr) * (1.f + 1e-6f) + kp.eps_abs;
+            bb2 = rr * rr;
         }
         Kahan Sw, Sq;
         int cnt = 0, c = 0;
@@ -141,15 +168,18 @@ __device__ __forceinline__ void density_bucket(
             float sp[3] = {__uint_as_float(L4.y) + s.x, __uint_as_float(L4.z) + s.y,
                            __uint_as_float(L4.w) + s.z};
             bool in = vj;
+            float dd2 = 0.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float d = sp[a] - bc[a];
-                if (kp.periodic[a]) {
+                if (WRAP && kp.periodic[a]) {
                     sp[a] -= kp.L[a] * rintf((sp[a] - cen[a]) * kp.invL[a]);
                     d = wrapf(d, kp.L[a], kp.invL[a]);
                 }
                 in = in && fabsf(d) <= br[a];
+                dd2 = fmaf(d, d, dd2);
             }
+            in = in && dd2 <= bb2;
             unsigned bal = __ballot_sync(kFull, in);
             if (in) {
                 int pos = c + __popc(bal & lt);
@@ -160,8 +190,8 @@ __device__ __forceinline__ void density_bucket(
             if (c > kChunk - 32) {
                 __syncwarp();
                 if (!done) cands += c;
-                density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, p[0], p[1], p[2], h2, ih, !done,
-                                             Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
+                density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
+                                             !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
                 __syncwarp();
                 c = 0;
             }
@@ -169,8 +199,8 @@ __device__ __forceinline__ void density_bucket(
         if (c > 0) {
             __syncwarp();
             if (!done) cands += c;
-            density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, p[0], p[1], p[2], h2, ih, !done, Sw,
-                                         Sq, cnt, i, cap, emitted, ids_out, id_in);
+            density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
+                                         !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
             __syncwarp();
         }
         if (!done) {
@@ -252,7 +282,7 @@ __global__ void __launch_bounds__(128) k_density(
     const unsigned *__restrict__ bucket_ids, int nbuckets, float *h_seed, float *h_out,
     float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
     long long cap, uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
-    unsigned *redo_out, DevStatus *st)
+    unsigned *redo_out, const float4 *__restrict__ node, DevStatus *st)
 {
     __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
@@ -269,13 +299,13 @@ __global__ void __launch_bounds__(128) k_density(
     bool wrap = false;
     {
         const float R = valid ? h_seed[i] * (1.f + kp.margin) : 0.f;
-        const float Rm = warp_max(R);
+        const float Rm = warp_max(R) + node[4 * 1 + 1].w;  // + largest bucket extent
         const float p[3] = {me.x, me.y, me.z};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float mn = warp_min(valid ? p[a] : INFINITY), mx = warp_max(valid ? p[a] : -INFINITY);
             cen[a] = 0.5f * (mn + mx);
-            if (kp.periodic[a] && 0.5f * (mx - mn) + Rm > 0.49f * kp.L[a]) wrap = true;
+            if (kp.periodic[a] && (mx - mn) + Rm > 0.49f * kp.L[a]) wrap = true;
         }
     }
     float4 *cand = cand_s[wib];
@@ -315,12 +345,12 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed,
             k_density<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
                 c.kp, c.pm, c.list_start, c.list_cnt, (const uint4 *)c.list, bucket_ids, nbuckets,
                 (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
-                count, ids, p.id, redo_out, c.st);
+                count, ids, p.id, redo_out, c.node, c.st);
         else
             k_density<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
                 c.kp, c.pm, c.list_start, c.list_cnt, (const uint4 *)c.list, bucket_ids, nbuckets,
                 (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
-                count, ids, p.id, redo_out, c.st);
+                count, ids, p.id, redo_out, c.node, c.st);
     )
     return cudaGetLastError();
 }

@@ -81,35 +81,65 @@ struct SinkState {
     unsigned long long pairs, av;
 };
 
-template <class K, bool WRAP>
-__device__ __forceinline__ void force_chunk(const KParams &kp, const float4 *cpos, const int *cidx,
-                                            float4 *fa, float2 *fb, int c, SinkState &s,
-                                            bool valid, int lane,
-                                            const float4 *__restrict__ fvel,
-                                            const float4 *__restrict__ fth, float4 *acc,
-                                            float2 *acc2)
+// per-warp shared-memory stage of one chunk of source candidates, plus the
+// equal-and-opposite sums they receive (structure of arrays: lanes that hit
+// different candidates touch different banks)
+struct ForceStage {
+    float4 pos[kChunk];  // position in the sink frame, h
+    float4 vel[kChunk];  // predicted velocity, m
+    float4 th[kChunk];   // A = P/(Omega rho^2), c, rho, -
+    int idx[kChunk];
+    float fx[kChunk], fy[kChunk], fz[kChunk], fS[kChunk], fdu[kChunk];
+    int fmu[kChunk];
+};
+
+template <bool WRAP>
+__device__ __forceinline__ void sep3(const KParams &kp, float px, float py, float pz, float4 q,
+                                     float &dx, float &dy, float &dz)
 {
+    dx = px - q.x;
+    dy = py - q.y;
+    dz = pz - q.z;
+    if (WRAP) {
+        if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
+        if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
+        if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+    }
+}
+
+template <class K, bool WRAP>
+__device__ __forceinline__ void force_chunk(const KParams &kp, ForceStage &S, int c, SinkState &s,
+                                            bool valid, int lane, float4 *acc, float2 *acc2)
+{
+    const int nwords = (c + 31) >> 5;
+    for (int k = c + lane; k < 32 * nwords; k += 32) {
+        S.pos[k] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        S.idx[k] = -1;
+    }
     for (int k = lane; k < c; k += 32) {
-        fa[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        fb[k] = make_float2(0.f, 0.f);
+        S.fx[k] = 0.f; S.fy[k] = 0.f; S.fz[k] = 0.f; S.fS[k] = 0.f; S.fdu[k] = 0.f; S.fmu[k] = 0;
     }
     __syncwarp();
-    unsigned long long m0 = 0ull, m1 = 0ull;
+    // hit masks: r < max(h_i, h_j) and j > i (each unordered pair once)
+    unsigned w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
     if (valid) {
-        for (int k = 0; k < c; ++k) {
-            float4 q = cpos[k];
-            float dx = s.px - q.x, dy = s.py - q.y, dz = s.pz - q.z;
-            if (WRAP) {
-                if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-                if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-                if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+#pragma unroll 1
+        for (int ww = 0; ww < nwords; ++ww) {
+            unsigned mw = 0u;
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                const float4 q = S.pos[32 * ww + b];
+                float dx, dy, dz;
+                sep3<WRAP>(kp, s.px, s.py, s.pz, q, dx, dy, dz);
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bool hit = r2 < fmaxf(s.h2, q.w * q.w) && S.idx[32 * ww + b] > s.i;
+                mw |= hit ? (1u << b) : 0u;
             }
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool hit = r2 < fmaxf(s.h2, q.w * q.w) && cidx[k] > s.i;
-            if (k < 64) m0 |= (unsigned long long)hit << k;
-            else m1 |= (unsigned long long)hit << (k - 64);
+            if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
         }
     }
+    unsigned long long m0 = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
+    unsigned long long m1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
     float sax = 0.f, say = 0.f, saz = 0.f, sS = 0.f;
     while (m0 | m1) {
         int k;
@@ -120,37 +150,29 @@ __device__ __forceinline__ void force_chunk(const KParams &kp, const float4 *cpo
             k = 63 + __ffsll((long long)m1);
             m1 &= m1 - 1ull;
         }
-        const float4 q = cpos[k];
-        const int j = cidx[k];
-        const float4 vj = __ldg(&fvel[j]);
-        const float4 tj = __ldg(&fth[j]);
-        float dx = s.px - q.x, dy = s.py - q.y, dz = s.pz - q.z;
-        if (WRAP) {
-            if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-            if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-            if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
-        }
+        const float4 q = S.pos[k];
+        const float4 vj = S.vel[k];
+        const float4 tj = S.th[k];
+        float dx, dy, dz;
+        sep3<WRAP>(kp, s.px, s.py, s.pz, q, dx, dy, dz);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
-        const float hj = q.w, ihj = 1.f / hj;
+        const float hj = q.w, ihj = __frcp_rn(hj);
         const float ihj2 = ihj * ihj;
         const float qi = r * s.ih, qj = r * ihj;
         const float Fi = qi < 1.f ? s.ih5 * K::dwq(qi) : 0.f;
         const float Fj = qj < 1.f ? K::sigma * ihj2 * ihj2 * ihj * K::dwq(qj) : 0.f;
         const float wx = s.vx - vj.x, wy = s.vy - vj.y, wz = s.vz - vj.z;
         const float vr = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
-        float coef = fmaf(s.A, Fi, tj.x * Fj);
-        float du = 0.f, mneg = 0.f;
-        if (vr < 0.f) {
-            const float hb = 0.5f * (s.h + hj), cb = 0.5f * (s.c + tj.y), rb = 0.5f * (s.rho + tj.z);
-            const float mu = hb * vr / fmaf(kp.eps_av * hb, hb, r2);
-            const float Pi = fmaf(-kp.alpha * cb, mu, kp.beta * mu * mu) / rb;
-            const float Fb = 0.5f * (Fi + Fj);
-            coef = fmaf(Pi, Fb, coef);
-            du = 0.5f * Pi * vr * Fb;
-            mneg = -mu;
-            ++s.av;
-        }
+        // viscosity, evaluated for every pair and switched by v_ij.r_ij < 0
+        const bool app = vr < 0.f;
+        const float hb = 0.5f * (s.h + hj), cb = 0.5f * (s.c + tj.y), rb = 0.5f * (s.rho + tj.z);
+        const float mu = __fdividef(hb * vr, fmaf(kp.eps_av * hb, hb, r2));
+        const float Pi = app ? __fdividef(fmaf(-kp.alpha * cb, mu, kp.beta * mu * mu), rb) : 0.f;
+        const float Fb = 0.5f * (Fi + Fj);
+        const float coef = fmaf(s.A, Fi, fmaf(tj.x, Fj, Pi * Fb));
+        const float du = 0.5f * Pi * vr * Fb;
+        const float mneg = app ? -mu : 0.f;
         // sink side (registers)
         const float cm = coef * vj.w;
         sax = fmaf(-cm, dx, sax);
@@ -161,13 +183,14 @@ __device__ __forceinline__ void force_chunk(const KParams &kp, const float4 *cpo
         s.mumax = fmaxf(s.mumax, mneg);
         // source side (shared memory, equal and opposite)
         const float cs = coef * s.m;
-        atomicAdd(&fa[k].x, cs * dx);
-        atomicAdd(&fa[k].y, cs * dy);
-        atomicAdd(&fa[k].z, cs * dz);
-        atomicAdd(&fa[k].w, s.m * vr * Fj);
-        if (vr < 0.f) {
-            atomicAdd(&fb[k].x, s.m * du);
-            atomicMax((int *)&fb[k].y, __float_as_int(mneg));
+        atomicAdd(&S.fx[k], cs * dx);
+        atomicAdd(&S.fy[k], cs * dy);
+        atomicAdd(&S.fz[k], cs * dz);
+        atomicAdd(&S.fS[k], s.m * vr * Fj);
+        if (app) {
+            atomicAdd(&S.fdu[k], s.m * du);
+            atomicMax(&S.fmu[k], __float_as_int(mneg));
+            ++s.av;
         }
         ++s.pairs;
     }
@@ -177,22 +200,24 @@ __device__ __forceinline__ void force_chunk(const KParams &kp, const float4 *cpo
     s.S.add(sS);
     __syncwarp();
     for (int k = lane; k < c; k += 32) {
-        float4 f = fa[k];
-        float2 g = fb[k];
-        int j = cidx[k];
-        if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) red_add_v4(&acc[j], f.x, f.y, f.z, f.w);
-        if (g.x != 0.f) red_add_f32(&acc2[j].x, g.x);
-        if (g.y > 0.f) atomicMax((int *)&acc2[j].y, __float_as_int(g.y));
+        const int j = S.idx[k];
+        const float fx = S.fx[k], fy = S.fy[k], fz = S.fz[k], fS = S.fS[k], fdu = S.fdu[k];
+        const int fmu = S.fmu[k];
+        if (fx != 0.f || fy != 0.f || fz != 0.f || fS != 0.f) red_add_v4(&acc[j], fx, fy, fz, fS);
+        if (fdu != 0.f) red_add_f32(&acc2[j].x, fdu);
+        if (fmu > 0) atomicMax((int *)&acc2[j].y, fmu);
     }
     __syncwarp();
 }
 
+struct SinkBounds {
+    float cen[3], gc[3], gr[3], bc[3], br[3];
+    float gR2;
+};
+
 template <class K, bool WRAP>
-__device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane, float4 *cpos,
-                                             int *cidx, float4 *fa, float2 *fb, SinkState &s,
-                                             bool valid, const float *cen, const float *sbl,
-                                             const float *sbh, const float *bxl,
-                                             const float *bxh,
+__device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane, ForceStage &S,
+                                             SinkState &s, bool valid, const SinkBounds sb,
                                              const float4 *__restrict__ fpos,
                                              const float4 *__restrict__ fvel,
                                              const float4 *__restrict__ fth,
@@ -205,47 +230,51 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
     const unsigned s0 = list_start[A], nl = list_cnt[A];
     int c = 0;
     for (unsigned e = 0; e < nl; ++e) {
-        uint4 L4 = list[s0 + e];
-        int j = (int)L4.x * kBucket + lane;
-        bool vj = j < kp.n;
-        float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint4 L4 = list[s0 + e];
+        const int j = (int)L4.x * kBucket + lane;
+        const bool vj = j < kp.n;
+        const float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         float sp[3] = {__uint_as_float(L4.y) + q.x, __uint_as_float(L4.z) + q.y,
                        __uint_as_float(L4.w) + q.z};
-        bool gather = true;
-        float dd = 0.f;
+        // gather: inside the sink's box of balls and ball of balls;
+        // scatter: the source's own ball reaches the sink cell bound
+        bool gbox = true;
+        float dg2 = 0.f, dd = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            // distances to the sink bounds on the circle of a periodic axis
-            float dg = sp[a] - 0.5f * (sbl[a] + sbh[a]);
-            float dc = sp[a] - cen[a];
-            if (kp.periodic[a]) {
-                sp[a] -= kp.L[a] * rintf(dc * kp.invL[a]);
+            float dg = sp[a] - sb.gc[a];
+            float dc = sp[a] - sb.bc[a];
+            if (WRAP && kp.periodic[a]) {
+                sp[a] -= kp.L[a] * rintf((sp[a] - sb.cen[a]) * kp.invL[a]);
                 dg = wrapf(dg, kp.L[a], kp.invL[a]);
                 dc = wrapf(dc, kp.L[a], kp.invL[a]);
             }
-            gather = gather && fabsf(dg) <= 0.5f * (sbh[a] - sbl[a]);
-            float o = fmaxf(fabsf(dc) - 0.5f * (bxh[a] - bxl[a]), 0.f);
+            gbox = gbox && fabsf(dg) <= sb.gr[a];
+            dg2 = fmaf(dg, dg, dg2);
+            float o = fmaxf(fabsf(dc) - sb.br[a], 0.f);
             dd = fmaf(o, o, dd);
         }
-        bool in = vj && (gather || dd < q.w * q.w);
-        unsigned bal = __ballot_sync(kFull, in);
+        const bool in = vj && ((gbox && dg2 <= sb.gR2) || dd < q.w * q.w);
+        const unsigned bal = __ballot_sync(kFull, in);
         if (in) {
-            int pos = c + __popc(bal & lt);
-            cpos[pos] = make_float4(sp[0], sp[1], sp[2], q.w);
-            cidx[pos] = j;
+            const int pos = c + __popc(bal & lt);
+            S.pos[pos] = make_float4(sp[0], sp[1], sp[2], q.w);
+            S.vel[pos] = fvel[j];
+            S.th[pos] = fth[j];
+            S.idx[pos] = j;
         }
         c += __popc(bal);
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
-            force_chunk<K, WRAP>(kp, cpos, cidx, fa, fb, c, s, valid, lane, fvel, fth, acc, acc2);
+            force_chunk<K, WRAP>(kp, S, c, s, valid, lane, acc, acc2);
             c = 0;
         }
     }
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP>(kp, cpos, cidx, fa, fb, c, s, valid, lane, fvel, fth, acc, acc2);
+        force_chunk<K, WRAP>(kp, S, c, s, valid, lane, acc, acc2);
     }
 }
 
@@ -259,10 +288,7 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
                                                 const float4 *__restrict__ node, float4 *acc,
                                                 float2 *acc2, DevStatus *st)
 {
-    __shared__ float4 cpos_s[kWarpsPerBlock][kChunk];
-    __shared__ int cidx_s[kWarpsPerBlock][kChunk];
-    __shared__ float4 fa_s[kWarpsPerBlock][kChunk];
-    __shared__ float2 fb_s[kWarpsPerBlock][kChunk];
+    __shared__ ForceStage stage[kWarpsPerBlock];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = blockIdx.x * kWarpsPerBlock + wib;
     if (A >= kp.nb) return;
@@ -286,33 +312,40 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
         s.pairs = 0;
         s.av = 0;
     }
-    // sink cell bound and box of balls in the sink frame; wrap decision
-    float cen[3], sbl[3], sbh[3], bxl[3], bxh[3];
+    // sink bounds in the sink frame: cell bound (bc, br), box of balls
+    // (gc, gr) and ball of balls (centre gc, radius^2 gR2); wrap decision
+    SinkBounds sb;
     bool wrap = false;
     const float Hmax = node[4 * 1 + 3].w;  // largest h of all particles (root)
+    const float Emax = node[4 * 1 + 1].w;  // largest bucket extent (root)
     {
         const float p[3] = {s.px, s.py, s.pz};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            bxl[a] = warp_min(valid ? p[a] : INFINITY);
-            bxh[a] = warp_max(valid ? p[a] : -INFINITY);
-            sbl[a] = warp_min(valid ? p[a] - s.h : INFINITY);
-            sbh[a] = warp_max(valid ? p[a] + s.h : -INFINITY);
-            cen[a] = 0.5f * (bxl[a] + bxh[a]);
-            if (kp.periodic[a] && 0.5f * (bxh[a] - bxl[a]) + Hmax > 0.49f * kp.L[a]) wrap = true;
+            float lo = warp_min(valid ? p[a] : INFINITY), hi = warp_max(valid ? p[a] : -INFINITY);
+            float glo = warp_min(valid ? p[a] - s.h : INFINITY);
+            float ghi = warp_max(valid ? p[a] + s.h : -INFINITY);
+            sb.bc[a] = 0.5f * (lo + hi);
+            sb.br[a] = 0.5f * (hi - lo);
+            sb.gc[a] = 0.5f * (glo + ghi);
+            sb.gr[a] = 0.5f * (ghi - glo);
+            sb.cen[a] = sb.bc[a];
+            if (kp.periodic[a] && (hi - lo) + Hmax + Emax > 0.49f * kp.L[a]) wrap = true;
         }
     }
+    {
+        float dx = s.px - sb.gc[0], dy = s.py - sb.gc[1], dz = s.pz - sb.gc[2];
+        float rr = valid ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + s.h : 0.f;
+        rr = warp_max(rr) * (1.f + 1e-6f) + kp.eps_abs;
+        sb.gR2 = rr * rr;
+    }
     unsigned long long cands = 0;
-    float4 *cpos = cpos_s[wib];
-    int *cidx = cidx_s[wib];
-    float4 *fa = fa_s[wib];
-    float2 *fb = fb_s[wib];
     if (wrap)
-        force_bucket<K, true>(kp, A, lane, cpos, cidx, fa, fb, s, valid, cen, sbl, sbh, bxl, bxh,
-                              fpos, fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
+        force_bucket<K, true>(kp, A, lane, stage[wib], s, valid, sb, fpos,
+                              fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
     else
-        force_bucket<K, false>(kp, A, lane, cpos, cidx, fa, fb, s, valid, cen, sbl, sbh, bxl, bxh,
-                               fpos, fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
+        force_bucket<K, false>(kp, A, lane, stage[wib], s, valid, sb, fpos,
+                               fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
     if (valid) {
         red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.S.s);
         if (s.du != 0.f) red_add_f32(&acc2[i].x, s.du);

@@ -46,10 +46,11 @@ __global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (kp.periodic[a]) {
-            double L = kp.hi[a] - kp.lo[a];
+            // a particle moves far less than a box length per step
             double t = p[a] - kp.lo[a];
-            t -= L * floor(t / L);
-            if (t >= L) t -= L;
+            if (t < 0.0 || t >= kp.Ld[a]) t -= kp.Ld[a] * floor(t * kp.invLd[a]);
+            if (t >= kp.Ld[a]) t -= kp.Ld[a];
+            if (t < 0.0) t = 0.0;
             p[a] = kp.lo[a] + t;
         }
     }
@@ -95,12 +96,16 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(
     if (threadIdx.x < 9) part[blockIdx.x * 9 + threadIdx.x] = sm[threadIdx.x][0];
 }
 
+// nine warps, one per total; each lane sums a fixed stride of the block
+// partials and the warp folds the lanes in a fixed butterfly order
 __global__ void k_cons_final(int nparts, const double *part, double *out)
 {
-    if (threadIdx.x >= 9) return;
+    int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (q >= 9) return;
     double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[b * 9 + threadIdx.x];
-    out[threadIdx.x] = s;
+    for (int b = lane; b < nparts; b += 32) s += part[b * 9 + q];
+    s = warp_sum(s);
+    if (lane == 0) out[q] = s;
 }
 
 constexpr int kConsBlocks = 304;
@@ -122,7 +127,7 @@ cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
     c.launches += 2;
     k_cons_partial<<<kConsBlocks, kConsThreads, 0, s>>>(n, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1],
                                                         p.v[2], p.u, p.m, c.cons_part);
-    k_cons_final<<<1, 32, 0, s>>>(kConsBlocks, c.cons_part, c.cons_out);
+    k_cons_final<<<1, 288, 0, s>>>(kConsBlocks, c.cons_part, c.cons_out);
     return cudaGetLastError();
 }
 

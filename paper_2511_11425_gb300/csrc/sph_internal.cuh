@@ -31,8 +31,10 @@ constexpr int kBucket = 32;       // particles per bucket = one warp
 constexpr int kChunk = 128;       // staged candidates processed per chunk
 constexpr int kWalkCap = 1024;    // frontier / list entries per sink bucket
 constexpr int kWarpsPerBlock = 4; // pair kernels and walks: 4 warps per block
-constexpr int kSortTile = 4096;   // keys per radix-sort tile (256 threads x 16)
-constexpr int kSortPasses = 6;    // 48-bit keys, 8-bit digits
+constexpr int kSortItems = 8;     // keys per thread in a radix-sort tile
+constexpr int kSortTile = 256 * kSortItems;  // keys per radix-sort tile
+constexpr int kMortonBits = 10;   // bits per axis of the Morton key (30-bit keys)
+constexpr int kSortPasses = 4;    // 8-bit digits cover the 30-bit keys
 constexpr unsigned kFull = 0xffffffffu;
 
 enum StatusCode : int {
@@ -66,7 +68,8 @@ struct KParams {
     float n_ngb, gamma, alpha, beta, eps_av, eta_courant, eta_acc, h_rel_tol, margin;
     float eps_abs;        // absolute inflation of f32 bounds (covers rounding)
     float hcap;           // h must stay below half the shortest periodic length
-    double q;             // origin quantum
+    double q, inv_q;      // origin quantum and its inverse (powers of two)
+    double Ld[3], invLd[3];  // periodic lengths in FP64
     double lo[3], hi[3];  // box
 };
 
@@ -91,18 +94,17 @@ struct Ctx {
     double *cons_out = nullptr;    // device 9 doubles
 
     // sort
-    unsigned long long *keys[2] = {nullptr, nullptr};
+    unsigned int *keys[2] = {nullptr, nullptr};
     unsigned int *vals[2] = {nullptr, nullptr};
     unsigned int *hist = nullptr;     // 256 x tiles
-    unsigned int *digit_tot = nullptr;  // per pass digit totals (skip detection)
-    void *tmp = nullptr;              // permutation scratch, 8 B x capacity x 7
+    unsigned int *digit_tot = nullptr;  // per-digit totals of the current sort pass
+    void *tmp = nullptr;              // permutation scratch, 112 B x capacity
     unsigned int *perm = nullptr;     // final permutation (sorted -> old index)
 
     // buckets / tree
     int nb_cap = 0, P_cap = 0;
     double *origin = nullptr;         // 3 x nb (SoA: ox, oy, oz)
     float4 *node = nullptr;           // 4 float4 per node: box_c, box_r, bob_c, bob_r
-    unsigned int *node_flag = nullptr;
 
     // particle records
     float4 *pm = nullptr;
