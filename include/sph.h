@@ -201,7 +201,10 @@ sph_status sph_forces(sph_ctx *ctx, sph_particles *p, void *stream);
  * kick of v and u over half the previous step with a and du/dt from
  * sph_forces; new step = dt_fixed if dt_fixed > 0, else min_i dt_i (device
  * reduction); opening kick over half the new step; drift x over the new
- * step; periodic wrap.  If dt_used != NULL the new step is written there
+ * step; periodic wrap.  The smoothing length is advanced with the drift,
+ * h <- h exp(dt div v / 3) (continuity equation, factor clamped to [1/2, 2]),
+ * so p->h holds the seed of the next density pass.  If dt_used != NULL the
+ * new step is written there
  * (this needs no extra synchronisation: every call already waits for its
  * status).  Positions change, so the next sph_density_h needs
  * sph_build_cells first.

@@ -50,7 +50,7 @@ void free_ctx(Ctx &c)
     void *ptrs[] = {c.st, c.dts, c.dtmin, c.morton_box, c.bbox_part, c.cons_part, c.cons_out,
                     c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist, c.digit_tot, c.tmp, c.origin,
                     c.node, c.pm, c.fpos, c.fvel, c.fth, c.acc, c.acc2, c.rho_old, c.h_seed,
-                    c.list_start, c.list_cnt, c.list, c.redo, c.mirror};
+                    c.list_start, c.list_cnt, c.list, c.redo, c.gflag, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.st_host) cudaFreeHost(c.st_host);
@@ -123,7 +123,7 @@ cudaError_t grow_list(Ctx &c, int64_t need)
     if (c.list) cudaFree(c.list);
     c.list = nullptr;
     c.list_cap = 0;
-    cudaError_t e = cudaMalloc((void **)&c.list, sizeof(uint4) * (size_t)cap);
+    cudaError_t e = cudaMalloc((void **)&c.list, sizeof(unsigned) * (size_t)cap);
     if (e == cudaSuccess) c.list_cap = cap;
     return e;
 }
@@ -135,6 +135,9 @@ void set_geometry(Ctx &c, int64_t n)
     k.nb = (int)((n + kBucket - 1) / kBucket);
     k.logP = ilog2_ceil(k.nb > 0 ? k.nb : 1);
     k.P = 1 << k.logP;
+    k.logG = k.logP < 3 ? k.logP : 3;  // groups of 8 buckets (256 particles)
+    k.G = 1 << k.logG;
+    k.ng = (k.nb + k.G - 1) / k.G;
 }
 
 }  // namespace
@@ -190,6 +193,7 @@ extern "C" sph_status sph_create(const sph_params *prm, int64_t capacity, sph_ct
     k.hcap = (float)hcap;
     k.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
     k.inv_q = 1.0 / k.q;
+    k.qf = (float)k.q;
     for (int a = 0; a < 3; ++a) {
         k.Ld[a] = prm->box_hi[a] - prm->box_lo[a];
         k.invLd[a] = 1.0 / k.Ld[a];
@@ -236,10 +240,11 @@ extern "C" sph_status sph_create(const sph_params *prm, int64_t capacity, sph_ct
     AL(c.rho_old, cap);
     AL(c.h_seed, cap);
     AL(c.list_start, c.nb_cap);
+    AL(c.gflag, c.nb_cap);
     AL(c.list_cnt, c.nb_cap);
     AL(c.redo, (size_t)2 * c.nb_cap);
 #undef AL
-    if (rc == SPH_OK && grow_list(c, (int64_t)c.nb_cap * 64) != cudaSuccess)
+    if (rc == SPH_OK && grow_list(c, (int64_t)c.nb_cap * 96) != cudaSuccess)
         rc = failf(c, SPH_ERR_CUDA, "cudaMalloc of the interaction lists failed");
     if (rc == SPH_OK && cudaMallocHost((void **)&c.st_host, sizeof(DevStatus)) != cudaSuccess)
         rc = SPH_ERR_CUDA;
@@ -305,8 +310,8 @@ sph_status density_passes(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     int maxit = 0, relists = 0;
     int64_t entries = 0;
     float ms_walk = 0.f, ms_kernel = 0.f;
-    const unsigned *ids = nullptr;
-    int nids = c.kp.nb;
+    const unsigned *ids = nullptr;  // group ids of a re-walk pass (NULL: all groups)
+    int nids = c.kp.ng;
     for (int round = 0; round < 12; ++round) {
         sph_status rc = SPH_OK;
         for (int attempt = 0; attempt < 3; ++attempt) {
@@ -412,8 +417,8 @@ extern "C" sph_status sph_density_at(sph_ctx *ctx, sph_particles *p, const float
     for (int attempt = 0; attempt < 3; ++attempt) {
         rc = begin(ctx, s);
         if (rc) return rc;
-        CK(launch_walk(c, *p, WALK_DENSITY, nullptr, c.kp.nb, c.h_seed, s));
-        CK(launch_density(c, *p, c.h_seed, nullptr, c.kp.nb, 1, cap, count, ids, s));
+        CK(launch_walk(c, *p, WALK_DENSITY, nullptr, c.kp.ng, c.h_seed, s));
+        CK(launch_density(c, *p, c.h_seed, nullptr, c.kp.ng, 1, cap, count, ids, s));
         rc = finish(ctx, s, nullptr);
         if ((int64_t)c.st_host->list_need <= c.list_cap) break;
         CK(grow_list(c, (int64_t)c.st_host->list_need));
@@ -441,7 +446,7 @@ extern "C" sph_status sph_forces(sph_ctx *ctx, sph_particles *p, void *stream)
         if (rc) return rc;
         CK(launch_predict(c, *p, s));
         CK(cudaEventRecord(c.kev[0], s));
-        CK(launch_walk(c, *p, WALK_FORCE, nullptr, c.kp.nb, nullptr, s));
+        CK(launch_walk(c, *p, WALK_FORCE, nullptr, c.kp.ng, nullptr, s));
         CK(cudaEventRecord(c.kev[1], s));
         CK(launch_forces(c, *p, s));
         CK(cudaEventRecord(c.kev[2], s));

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
                                                  const double *__restrict__ y,
                                                  const double *__restrict__ z,
                                                  const float *__restrict__ m,
-                                                 const float *__restrict__ h, double *origin,
+                                                 const float *__restrict__ h, int *origin,
                                                  float4 *pm, float4 *node, int update_pos,
                                                  DevStatus *st)
 {
@@ -295,9 +295,14 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
             double d = v[a] - first;
             if (kp.periodic[a]) d -= kp.Ld[a] * rint(d * kp.invLd[a]);
             float mn = warp_min(ok ? (float)d : INFINITY);
-            o[a] = floor((first + (double)mn) * kp.inv_q) * kp.q;
+            double kd = floor((first + (double)mn) * kp.inv_q);
+            if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
+                if (lane == 0) raise_status(st, ST_ARG, b);
+                kd = 0.0;
+            }
+            o[a] = kd * kp.q;
             rel[a] = (float)((first - o[a]) + d);
-            if (lane == 0) origin[a * kp.nb + b] = o[a];
+            if (lane == 0) origin[a * kp.nb + b] = (int)kd;
         }
         if (ok) {
             if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
         float4 r = ok ? pm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         rel[0] = r.x; rel[1] = r.y; rel[2] = r.z;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) o[a] = origin[a * kp.nb + b];
+        for (int a = 0; a < 3; ++a) o[a] = (double)origin[a * kp.nb + b] * kp.q;
     }
     float hi = ok ? h[i] : 0.f;
     if (ok && !(hi > 0.f && isfinite(hi))) raise_status(st, ST_NONFINITE, i);
@@ -440,58 +445,63 @@ static void tree_refit(Ctx &c, cudaStream_t s, int bob_only)
 }
 
 // ---------------------------------------------------------------------------
-// interaction-list walk (Sec. 2.3.2): one warp per sink bucket, breadth-first
-// over the implicit tree, 32 node tests at a time.
-//   density: source cell bound overlaps the sink's box of balls of radius
-//            h_walk (1 + margin)                             (gather)
-//   force:   source cell bound overlaps the sink box-of-balls (gather) OR
-//            source box-of-balls overlaps the sink cell bound (scatter),
-//            restricted to source buckets >= sink (each pair once)
-// Each list entry carries the source bucket id and the f32 offset between
-// the bucket origins (nearest periodic image), exact since origins are
-// multiples of q.
+// interaction-list walk (Sec. 2.3.2): one walk per GROUP of G = 8 consecutive
+// buckets (256 particles, the paper's GPU group size), breadth-first over the
+// implicit tree, 32 node tests per round.
+//   density: source cell bound overlaps the group's box of balls of radius
+//            h_walk (1 + margin)                              (gather)
+//   force:   source cell bound overlaps the group box-of-balls (gather) OR
+//            source box-of-balls overlaps the group cell bound (scatter),
+//            restricted to source buckets >= the group's first bucket
+// The list holds source bucket ids; each sink bucket of the group filters it
+// against its own bounds inside the pair kernels.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool ovl(float ca, float ra, float cb, float rb, bool per, float L,
-                                    float invL)
-{
-    float d = ca - cb;
-    if (per) d = wrapf(d, L, invL);
-    return fabsf(d) <= ra + rb;
-}
-
 __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4 *__restrict__ node,
                                               const float4 *__restrict__ pm,
-                                              const double *__restrict__ origin,
+                                              const int *__restrict__ origin,
                                               const float *__restrict__ h_walk,
-                                              const unsigned *__restrict__ bucket_ids, int nbuckets,
+                                              const unsigned *__restrict__ group_ids, int ngroups,
                                               unsigned *list_start, unsigned *list_cnt,
-                                              uint4 *list, long long list_cap, DevStatus *st)
+                                              unsigned *list, long long list_cap, DevStatus *st)
 {
     __shared__ unsigned buf[kWarpsPerBlock][2][kWalkCap];
     int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int bi = blockIdx.x * kWarpsPerBlock + wib;
-    if (bi >= nbuckets) return;
-    int A = bucket_ids ? (int)bucket_ids[bi] : bi;
+    int gi = blockIdx.x * kWarpsPerBlock + wib;
+    if (gi >= ngroups) return;
+    const int g = group_ids ? (int)group_ids[gi] : gi;
+    const int fb = g * kp.G;
 
-    // sink bounds in absolute (unwrapped) f32 coordinates
-    float gc[3], gr[3], sc[3], sr[3];  // gather box, sink cell box
+    // group bounds in absolute (unwrapped) f32 coordinates
+    float gc[3], gr[3], sc[3], sr[3];  // gather box, group cell box
     if (mode == WALK_DENSITY) {
-        int i = A * kBucket + lane;
-        bool ok = i < kp.n;
-        float4 r = ok ? pm[i] : make_float4(0, 0, 0, 0);
-        float R = ok ? h_walk[i] * (1.f + kp.margin) : 0.f;
-        float rp[3] = {r.x, r.y, r.z};
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int j = 0; j < kp.G; ++j) {
+            const int b = fb + j;
+            if (b >= kp.nb) break;
+            const float3 off = origin_offset(kp, origin, fb, b);
+            const int i = b * kBucket + lane;
+            if (i < kp.n) {
+                const float4 r = pm[i];
+                const float R = h_walk[i] * (1.f + kp.margin);
+                const float p[3] = {off.x + r.x, off.y + r.y, off.z + r.z};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = fminf(lo[a], p[a] - R);
+                    hi[a] = fmaxf(hi[a], p[a] + R);
+                }
+            }
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float lo = warp_min(ok ? rp[a] - R : INFINITY), hi = warp_max(ok ? rp[a] + R : -INFINITY);
-            double o = origin[a * kp.nb + A];
-            gc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
-            gr[a] = 0.5f * (hi - lo) + 2.f * kp.eps_abs;
+            float l = warp_min(lo[a]), h = warp_max(hi[a]);
+            double o = (double)origin[a * kp.nb + fb] * kp.q;
+            gc[a] = (float)(o + 0.5 * ((double)l + (double)h));
+            gr[a] = 0.5f * (h - l) + 2.f * kp.eps_abs;
             sc[a] = gc[a];
             sr[a] = -1.f;
         }
     } else {
-        int k = kp.P + A;
+        const int k = (kp.P >> kp.logG) + g;
         float4 b0 = node[4 * k], b1 = node[4 * k + 1], o0 = node[4 * k + 2], o1 = node[4 * k + 3];
         gc[0] = o0.x; gc[1] = o0.y; gc[2] = o0.z;
         gr[0] = o1.x; gr[1] = o1.y; gr[2] = o1.z;
@@ -516,24 +526,24 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
                 nd = cur[k];
                 float4 b0 = node[4 * nd], b1 = node[4 * nd + 1];
                 if (b1.x >= 0.f) {  // non-empty
-                    bool g = ovl(gc[0], gr[0], b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                             ovl(gc[1], gr[1], b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                             ovl(gc[2], gr[2], b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                    bool gth = ovl(gc[0], gr[0], b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                               ovl(gc[1], gr[1], b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                               ovl(gc[2], gr[2], b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
                     if (mode == WALK_FORCE) {
-                        // only subtrees holding buckets >= A
+                        // only subtrees holding buckets >= the group's first
                         int shift = kp.logP - lvl;
                         int last = (int)(((nd + 1u) << shift) - 1u) - kp.P;
-                        if (last < A) {
-                            g = false;
-                        } else if (!g) {
+                        if (last < fb) {
+                            gth = false;
+                        } else if (!gth) {
                             float4 o0 = node[4 * nd + 2], o1 = node[4 * nd + 3];
-                            g = ovl(sc[0], sr[0], o0.x, o1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                                ovl(sc[1], sr[1], o0.y, o1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                                ovl(sc[2], sr[2], o0.z, o1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                            gth = ovl(sc[0], sr[0], o0.x, o1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                                  ovl(sc[1], sr[1], o0.y, o1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                                  ovl(sc[2], sr[2], o0.z, o1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
                         }
-                        if (leaf && (int)(nd - kp.P) < A) g = false;
+                        if (leaf && (int)(nd - kp.P) < fb) gth = false;
                     }
-                    acc = g;
+                    acc = gth;
                 }
             }
             unsigned bal = __ballot_sync(kFull, acc);
@@ -560,7 +570,7 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
         if (overflow) break;
     }
     if (overflow) {
-        if (lane == 0) raise_status(st, ST_CAPACITY, A);
+        if (lane == 0) raise_status(st, ST_CAPACITY, g);
         ncur = 0;
     }
     // cur holds the accepted bucket ids; allocate and write them
@@ -569,23 +579,11 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
     start = __shfl_sync(kFull, start, 0);
     bool fits = (long long)start + ncur <= list_cap;
     if (lane == 0) {
-        list_start[A] = start;
-        list_cnt[A] = fits ? (unsigned)ncur : 0u;
+        list_start[g] = start;
+        list_cnt[g] = fits ? (unsigned)ncur : 0u;
     }
     if (!fits) return;
-    double oA[3] = {origin[A], origin[kp.nb + A], origin[2 * kp.nb + A]};
-    for (int k = lane; k < ncur; k += 32) {
-        unsigned B = cur[k];
-        float d[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double dd = origin[a * kp.nb + B] - oA[a];
-            if (kp.periodic[a]) dd = wrapd(dd, (double)(kp.hi[a] - kp.lo[a]));
-            d[a] = (float)dd;
-        }
-        list[start + k] = make_uint4(B, __float_as_uint(d[0]), __float_as_uint(d[1]),
-                                     __float_as_uint(d[2]));
-    }
+    for (int k = lane; k < ncur; k += 32) list[start + k] = cur[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -649,15 +647,15 @@ cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned *bucket_ids,
-                        int nbuckets, const float *h_walk, cudaStream_t s)
+cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned *group_ids,
+                        int ngroups, const float *h_walk, cudaStream_t s)
 {
     (void)p;
-    if (nbuckets <= 0) return cudaSuccess;
-    int g = (nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (ngroups <= 0) return cudaSuccess;
+    int g = (ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
     c.launches += 1;
-    k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, mode, c.node, c.pm, c.origin, h_walk, bucket_ids,
-                                             nbuckets, c.list_start, c.list_cnt, (uint4 *)c.list,
+    k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, mode, c.node, c.pm, c.origin, h_walk, group_ids,
+                                             ngroups, c.list_start, c.list_cnt, c.list,
                                              (long long)c.list_cap, c.st);
     return cudaGetLastError();
 }

@@ -120,10 +120,11 @@ template <class K, bool WRAP, bool EMIT>
 __device__ __forceinline__ void density_bucket(
     const KParams &kp, int A, int lane, float4 *cand, int *candj, const float4 *__restrict__ pm,
     const unsigned *__restrict__ list_start, const unsigned *__restrict__ list_cnt,
-    const uint4 *__restrict__ list, float *h_seed, float *h_out, float *rho_out, float *omega_out,
-    uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out,
-    int64_t *ids_out, const int64_t *__restrict__ id_in, unsigned *redo_out, DevStatus *st,
-    float4 me, bool valid, const float *cen)
+    const unsigned *__restrict__ list, const int *__restrict__ origin,
+    const float4 *__restrict__ node, float *h_seed, float *h_out, float *rho_out,
+    float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap,
+    uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in, unsigned *redo_out,
+    unsigned *gflag, DevStatus *st, float4 me, bool valid, const float *cen)
 {
     const unsigned lt = (1u << lane) - 1u;
     int i = A * kBucket + lane;
@@ -135,8 +136,37 @@ __device__ __forceinline__ void density_bucket(
     float out_h = h, out_rho = 0.f, out_om = 0.f;
     int out_n = 0, emitted = 0;
     unsigned long long pairs = 0, cands = 0;
-    const unsigned s0 = list_start[A], nl = list_cnt[A];
     const float p[3] = {me.x, me.y, me.z};
+    // Filter the group's list against this bucket's coverage box of balls
+    // (radius R): lane w keeps the acceptance bits of entries 32w .. 32w+31.
+    const int g = A >> kp.logG;
+    const unsigned s0 = list_start[g], nl = list_cnt[g];
+    unsigned myword = 0u;
+    {
+        float cc[3], cr[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float lo = warp_min(valid ? p[a] - R : INFINITY);
+            float hi = warp_max(valid ? p[a] + R : -INFINITY);
+            double o = (double)origin[a * kp.nb + A] * kp.q;
+            cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
+            cr[a] = 0.5f * (hi - lo) + 2.f * kp.eps_abs;
+        }
+        for (unsigned w = 0; 32 * w < nl; ++w) {
+            const unsigned e = 32 * w + lane;
+            bool acc = false;
+            if (e < nl) {
+                const unsigned k = (unsigned)kp.P + list[s0 + e];
+                const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
+                acc = ovl(cc[0], cr[0], b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                      ovl(cc[1], cr[1], b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                      ovl(cc[2], cr[2], b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+            }
+            const unsigned bal = __ballot_sync(kFull, acc);
+            if (lane == (int)w) myword = bal;
+        }
+    }
+    const unsigned nwords = (nl + 31) / 32;
 
     for (int pass = 0; pass <= kp.max_newton; ++pass) {
         if (__all_sync(kFull, done)) break;
@@ -160,13 +190,17 @@ __device__ __forceinline__ void density_bucket(
         }
         Kahan Sw, Sq;
         int cnt = 0, c = 0;
-        for (unsigned e = 0; e < nl; ++e) {
-            uint4 L4 = list[s0 + e];
-            int j = (int)L4.x * kBucket + lane;
+        for (unsigned w = 0; w < nwords; ++w) {
+          unsigned mw = __shfl_sync(kFull, myword, w);
+          while (mw) {
+            const unsigned e = 32 * w + __ffs(mw) - 1;
+            mw &= mw - 1u;
+            const int B = (int)list[s0 + e];
+            const float3 off = origin_offset(kp, origin, A, B);
+            int j = B * kBucket + lane;
             bool vj = j < kp.n;
             float4 s = vj ? pm[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float sp[3] = {__uint_as_float(L4.y) + s.x, __uint_as_float(L4.z) + s.y,
-                           __uint_as_float(L4.w) + s.z};
+            float sp[3] = {off.x + s.x, off.y + s.y, off.z + s.z};
             bool in = vj;
             float dd2 = 0.f;
 #pragma unroll
@@ -195,6 +229,7 @@ __device__ __forceinline__ void density_bucket(
                 __syncwarp();
                 c = 0;
             }
+          }
         }
         if (c > 0) {
             __syncwarp();
@@ -254,9 +289,9 @@ __device__ __forceinline__ void density_bucket(
     bool any_relist = __any_sync(kFull, relist);
     if (any_relist) {
         if (valid) h_seed[i] = relist ? out_h : (conv ? out_h : h);
-        if (lane == 0) {
+        if (lane == 0 && atomicOr(&gflag[g], 1u) == 0u) {
             unsigned pos = atomicAdd(&st->redo_count, 1u);
-            redo_out[pos] = (unsigned)A;
+            redo_out[pos] = (unsigned)g;
         }
     } else if (valid && conv) {
         h_out[i] = out_h;
@@ -278,18 +313,21 @@ __device__ __forceinline__ void density_bucket(
 template <class K, bool EMIT>
 __global__ void __launch_bounds__(128) k_density(
     KParams kp, const float4 *__restrict__ pm, const unsigned *__restrict__ list_start,
-    const unsigned *__restrict__ list_cnt, const uint4 *__restrict__ list,
-    const unsigned *__restrict__ bucket_ids, int nbuckets, float *h_seed, float *h_out,
-    float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
-    long long cap, uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
-    unsigned *redo_out, const float4 *__restrict__ node, DevStatus *st)
+    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list,
+    const int *__restrict__ origin, const unsigned *__restrict__ group_ids, int nbuckets,
+    float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
+    uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out, int64_t *ids_out,
+    const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *gflag,
+    const float4 *__restrict__ node, DevStatus *st)
 {
     __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * kWarpsPerBlock + wib;
     if (bi >= nbuckets) return;
-    const int A = bucket_ids ? (int)bucket_ids[bi] : bi;
+    // all buckets, or every bucket of the listed groups (re-walk passes)
+    const int A = group_ids ? (int)group_ids[bi >> kp.logG] * kp.G + (bi & (kp.G - 1)) : bi;
+    if (A >= kp.nb) return;
     const int i = A * kBucket + lane;
     const bool valid = i < kp.n;
     const float4 me = valid ? pm[i] : make_float4(0.f, 0.f, 0.f, 1.f);
@@ -312,13 +350,15 @@ __global__ void __launch_bounds__(128) k_density(
     int *candj = EMIT ? candj_s[wib] : nullptr;
     if (wrap)
         density_bucket<K, true, EMIT>(kp, A, lane, cand, candj, pm, list_start, list_cnt, list,
+                                      origin, node,
                                       h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
-                                      fixed_h, cap, count_out, ids_out, id_in, redo_out, st, me,
+                                      fixed_h, cap, count_out, ids_out, id_in, redo_out, gflag, st, me,
                                       valid, cen);
     else
         density_bucket<K, false, EMIT>(kp, A, lane, cand, candj, pm, list_start, list_cnt, list,
+                                      origin, node,
                                        h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
-                                       fixed_h, cap, count_out, ids_out, id_in, redo_out, st, me,
+                                       fixed_h, cap, count_out, ids_out, id_in, redo_out, gflag, st, me,
                                        valid, cen);
 }
 
@@ -332,25 +372,27 @@ __global__ void k_isentropic(int n, double g1, const float *__restrict__ rho,
 }
 
 cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed,
-                           const unsigned *bucket_ids, int nbuckets, int fixed_h, int64_t cap,
+                           const unsigned *group_ids, int ngroups, int fixed_h, int64_t cap,
                            uint32_t *count, int64_t *ids, cudaStream_t s)
 {
-    if (nbuckets <= 0) return cudaSuccess;
+    if (ngroups <= 0) return cudaSuccess;
+    int nbuckets = group_ids ? ngroups * c.kp.G : c.kp.nb;
     int g = (nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
     bool emit = ids != nullptr || count != nullptr;
-    unsigned *redo_out = c.redo + (bucket_ids == c.redo ? c.nb_cap : 0);
+    unsigned *redo_out = c.redo + (group_ids == c.redo ? c.nb_cap : 0);
+    cudaMemsetAsync(c.gflag, 0, sizeof(unsigned) * (size_t)c.kp.ng, s);
     c.launches += 1;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
         if (emit)
             k_density<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                c.kp, c.pm, c.list_start, c.list_cnt, (const uint4 *)c.list, bucket_ids, nbuckets,
+                c.kp, c.pm, c.list_start, c.list_cnt, c.list, c.origin, group_ids, nbuckets,
                 (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
-                count, ids, p.id, redo_out, c.node, c.st);
+                count, ids, p.id, redo_out, c.gflag, c.node, c.st);
         else
             k_density<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                c.kp, c.pm, c.list_start, c.list_cnt, (const uint4 *)c.list, bucket_ids, nbuckets,
+                c.kp, c.pm, c.list_start, c.list_cnt, c.list, c.origin, group_ids, nbuckets,
                 (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
-                count, ids, p.id, redo_out, c.node, c.st);
+                count, ids, p.id, redo_out, c.gflag, c.node, c.st);
     )
     return cudaGetLastError();
 }

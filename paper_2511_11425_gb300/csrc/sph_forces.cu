@@ -223,19 +223,59 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
                                              const float4 *__restrict__ fth,
                                              const unsigned *__restrict__ list_start,
                                              const unsigned *__restrict__ list_cnt,
-                                             const uint4 *__restrict__ list, float4 *acc,
+                                             const unsigned *__restrict__ list,
+                                             const int *__restrict__ origin,
+                                             const float4 *__restrict__ node, float4 *acc,
                                              float2 *acc2, unsigned long long &cands)
 {
     const unsigned lt = (1u << lane) - 1u;
-    const unsigned s0 = list_start[A], nl = list_cnt[A];
+    // Filter the group's list for this bucket (Sec. 2.3.2 tests with the
+    // bucket's own bounds): source bucket B >= A whose cell bound meets the
+    // sink box-of-balls (gather) or whose box-of-balls meets the sink cell
+    // bound (scatter).  Lane w keeps the bits of entries 32w .. 32w+31.
+    const int g = A >> kp.logG;
+    const unsigned s0 = list_start[g], nl = list_cnt[g];
+    unsigned myword = 0u;
+    {
+        const int ka = kp.P + A;
+        const float4 sb0 = node[4 * ka], sb1 = node[4 * ka + 1];
+        const float4 so0 = node[4 * ka + 2], so1 = node[4 * ka + 3];
+        for (unsigned w = 0; 32 * w < nl; ++w) {
+            const unsigned e = 32 * w + lane;
+            bool acc_ = false;
+            if (e < nl) {
+                const unsigned B = list[s0 + e];
+                const unsigned k = (unsigned)kp.P + B;
+                if ((int)B >= A) {
+                    const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
+                    acc_ = ovl(so0.x, so1.x, b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                           ovl(so0.y, so1.y, b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                           ovl(so0.z, so1.z, b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                    if (!acc_) {
+                        const float4 o0 = node[4 * k + 2], o1 = node[4 * k + 3];
+                        acc_ = ovl(sb0.x, sb1.x, o0.x, o1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
+                               ovl(sb0.y, sb1.y, o0.y, o1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
+                               ovl(sb0.z, sb1.z, o0.z, o1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                    }
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, acc_);
+            if (lane == (int)w) myword = bal;
+        }
+    }
+    const unsigned nwords = (nl + 31) / 32;
     int c = 0;
-    for (unsigned e = 0; e < nl; ++e) {
-        const uint4 L4 = list[s0 + e];
-        const int j = (int)L4.x * kBucket + lane;
+    for (unsigned w = 0; w < nwords; ++w) {
+      unsigned mw = __shfl_sync(kFull, myword, w);
+      while (mw) {
+        const unsigned e = 32 * w + __ffs(mw) - 1;
+        mw &= mw - 1u;
+        const int B = (int)list[s0 + e];
+        const float3 off = origin_offset(kp, origin, A, B);
+        const int j = B * kBucket + lane;
         const bool vj = j < kp.n;
         const float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float sp[3] = {__uint_as_float(L4.y) + q.x, __uint_as_float(L4.z) + q.y,
-                       __uint_as_float(L4.w) + q.z};
+        float sp[3] = {off.x + q.x, off.y + q.y, off.z + q.z};
         // gather: inside the sink's box of balls and ball of balls;
         // scatter: the source's own ball reaches the sink cell bound
         bool gbox = true;
@@ -270,6 +310,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
             force_chunk<K, WRAP>(kp, S, c, s, valid, lane, acc, acc2);
             c = 0;
         }
+      }
     }
     if (c > 0) {
         __syncwarp();
@@ -284,7 +325,8 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
                                                 const float4 *__restrict__ fth,
                                                 const unsigned *__restrict__ list_start,
                                                 const unsigned *__restrict__ list_cnt,
-                                                const uint4 *__restrict__ list,
+                                                const unsigned *__restrict__ list,
+                                                const int *__restrict__ origin,
                                                 const float4 *__restrict__ node, float4 *acc,
                                                 float2 *acc2, DevStatus *st)
 {
@@ -342,10 +384,12 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
     unsigned long long cands = 0;
     if (wrap)
         force_bucket<K, true>(kp, A, lane, stage[wib], s, valid, sb, fpos,
-                              fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
+                              fvel, fth, list_start, list_cnt, list, origin, node, acc, acc2,
+                              cands);
     else
         force_bucket<K, false>(kp, A, lane, stage[wib], s, valid, sb, fpos,
-                               fvel, fth, list_start, list_cnt, list, acc, acc2, cands);
+                               fvel, fth, list_start, list_cnt, list, origin, node, acc, acc2,
+                              cands);
     if (valid) {
         red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.S.s);
         if (s.du != 0.f) red_add_f32(&acc2[i].x, s.du);
@@ -419,7 +463,7 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
     c.launches += 1;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
         k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.fpos, c.fvel, c.fth, c.list_start,
-                                                        c.list_cnt, (const uint4 *)c.list, c.node,
+                                                        c.list_cnt, c.list, c.origin, c.node,
                                                         c.acc, c.acc2, c.st);
     )
     return cudaGetLastError();

@@ -23,11 +23,14 @@ __global__ void k_choose_dt(double *dts, const unsigned *dtmin, double dt_fixed,
     dts[1] = dt;
 }
 
+// The smoothing length is advanced with the drift as the seed of the next
+// density pass: the continuity equation gives rho(t + dt) ~ rho exp(-dt div v),
+// and h ~ rho^(-1/3), so h <- h exp(dt div v / 3) (factor clamped to [1/2, 2]).
 __global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double *vx, double *vy,
-                      double *vz, double *u, const float *__restrict__ ax,
+                      double *vz, double *u, float *h, const float *__restrict__ ax,
                       const float *__restrict__ ay, const float *__restrict__ az,
                       const float *__restrict__ dudt_h, const float *__restrict__ dudt_av,
-                      const double *__restrict__ dts)
+                      const float *__restrict__ divv, const double *__restrict__ dts)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -57,6 +60,8 @@ __global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double
     x[i] = p[0];
     y[i] = p[1];
     z[i] = p[2];
+    const float f = expf((float)dt_new * divv[i] * (1.f / 3.f));
+    h[i] *= fminf(fmaxf(f, 0.5f), 2.f);
 }
 
 // conserved totals: fixed-order block tree reduction, then one block sums
@@ -116,7 +121,8 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
     c.launches += 2;
     k_choose_dt<<<1, 32, 0, s>>>(c.dts, c.dtmin, dt_fixed, c.st);
     k_kdk<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2],
-                                          p.u, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av, c.dts);
+                                          p.u, p.h, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av,
+                                          p.divv, c.dts);
     cudaMemcpyAsync(c.dts, c.dts + 1, sizeof(double), cudaMemcpyDeviceToDevice, s);
     return cudaGetLastError();
 }

@@ -4,15 +4,18 @@
 // sph_build_cells):
 //   caller arrays   x,v (f64), u (f64), m,h,rho,omega,a,dudt,... (f32)
 //   pm[i]           float4 (x - o_b, y - o_b, z - o_b, m): position relative to
-//                   the FP64 origin o_b of the particle's bucket, plus mass
-//   buckets         32 consecutive particles; origin o_b (f64x3, a multiple of
-//                   the quantum q so differences of origins are exact in f32)
+//                   the origin o_b of the particle's bucket, plus mass
+//   buckets         32 consecutive particles; origin o_b = k_b q with integer
+//                   grid coordinates k_b (int32 x3) and the power-of-two quantum
+//                   q, so origin differences are exact in f32 and need no FP64
+//   groups          G = 8 consecutive buckets (256 particles) share one walk
 //   tree            implicit complete binary tree over the buckets padded to a
 //                   power of two P (root 1, leaf of bucket b = P + b); each node
 //                   stores its cell bound (AABB) and box-of-balls bound as
 //                   centre/half-width float4 pairs, Sec. 2.3.2
-//   lists           per sink bucket, the source buckets whose bounds overlap
-//                   (CSR: start/count per bucket into one u32 array)
+//   lists           per group, the source buckets whose bounds overlap the
+//                   group's bounds (CSR: start/count per group into one u32
+//                   array); each sink bucket filters them against its own bounds
 //   force records   fpos (rel xyz, h), fvel (v_pred xyz, m), fth (A, c, rho, -)
 //   accumulators    acc (a xyz, S = sum m_j v_ij.gradW_ij(h_i)), acc2 (du/dt|Pi,
 //                   max(-mu_ij) as float bits)
@@ -62,6 +65,7 @@ struct DevStatus {
 // parameters as the kernels see them (copied by value into every launch)
 struct KParams {
     int kernel, energy_mode, max_newton, nb, P, logP;
+    int G, logG, ng;      // buckets per group, log2, number of groups
     int periodic[3];
     int n;
     float L[3], invL[3], halfL[3];
@@ -69,6 +73,7 @@ struct KParams {
     float eps_abs;        // absolute inflation of f32 bounds (covers rounding)
     float hcap;           // h must stay below half the shortest periodic length
     double q, inv_q;      // origin quantum and its inverse (powers of two)
+    float qf;             // q in f32
     double Ld[3], invLd[3];  // periodic lengths in FP64
     double lo[3], hi[3];  // box
 };
@@ -103,7 +108,8 @@ struct Ctx {
 
     // buckets / tree
     int nb_cap = 0, P_cap = 0;
-    double *origin = nullptr;         // 3 x nb (SoA: ox, oy, oz)
+    int *origin = nullptr;            // 3 x nb grid coordinates (SoA: kx, ky, kz)
+    unsigned int *gflag = nullptr;    // per group: queued for a re-walk
     float4 *node = nullptr;           // 4 float4 per node: box_c, box_r, bob_c, bob_r
 
     // particle records
@@ -117,7 +123,7 @@ struct Ctx {
     // lists
     unsigned int *list_start = nullptr, *list_cnt = nullptr, *list = nullptr;
     int64_t list_cap = 0;
-    unsigned int *redo = nullptr;     // redo bucket ids
+    unsigned int *redo = nullptr;     // ids of groups queued for a re-walk (2 halves)
 
     // host-mode mirror buffers for sph_step_host
     void *mirror = nullptr;
@@ -189,6 +195,30 @@ __device__ __forceinline__ double warp_max(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
     return v;
+}
+
+// overlap of two centre/half-width intervals (on a circle for periodic axes)
+__device__ __forceinline__ bool ovl(float ca, float ra, float cb, float rb, bool per, float L,
+                                    float invL)
+{
+    float d = ca - cb;
+    if (per) d = wrapf(d, L, invL);
+    return fabsf(d) <= ra + rb;
+}
+
+// f32 offset o_B - o_A between two bucket origins (nearest periodic image):
+// integer grid difference times the power-of-two quantum, exact in f32
+__device__ __forceinline__ float3 origin_offset(const KParams &kp, const int *__restrict__ origin,
+                                                int A, int B)
+{
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float f = (float)(origin[a * kp.nb + B] - origin[a * kp.nb + A]) * kp.qf;
+        if (kp.periodic[a]) f -= kp.L[a] * rintf(f * kp.invL[a]);
+        d[a] = f;
+    }
+    return make_float3(d[0], d[1], d[2]);
 }
 
 // Kahan-compensated running sum (the density and force sums accumulate one
@@ -278,8 +308,8 @@ struct KM4 {
 // build (sph_build.cu)
 cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s);
-cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned int *bucket_ids,
-                        int nbuckets, const float *h_for_walk, cudaStream_t s);
+cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned int *group_ids,
+                        int ngroups, const float *h_for_walk, cudaStream_t s);
 // density (sph_density.cu)
 cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed,
                            const unsigned int *bucket_ids, int nbuckets, int fixed_h,
