@@ -237,6 +237,31 @@ sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, 
  */
 sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double out[9], void *stream);
 
+/*
+ * sph_reduce_conserved_noalloc: the totals of sph_reduce_conserved without a
+ * context and without allocating device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: applications whose pool allocator owns all device memory, hooks
+ * that run inside another library's time step (where an allocation would
+ * synchronise the device or fail under memory pressure), code that must keep
+ * the process's device footprint fixed.
+ *   p      device arrays x, v, u, m of p->n particles (other members ignored)
+ *   out    DEVICE array of 9 doubles owned by the caller; receives M, P_x,
+ *          P_y, P_z, L_x, L_y, L_z, E_kin, E_int (fixed summation order)
+ *   stream cudaStream_t as void*; the call only queues work and returns, so
+ *          synchronise the stream before reading out
+ * Partial sums live in a fixed file-scope device array of 576 KiB that every
+ * GPU loading the library keeps until exit; n is therefore limited to
+ * 8,388,608 particles and larger n returns SPH_ERR_CAPACITY without launching.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make it before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the GPU race and give wrong
+ * totals.  Errors: SPH_ERR_ARG (NULL pointer, n < 0), SPH_ERR_CUDA (launch or
+ * address lookup failed).  There is no context, so sph_last_error does not
+ * apply.
+ */
+sph_status sph_reduce_conserved_noalloc(const sph_particles *p, double *out, void *stream);
+
 /* sph_set_dt_old: set the previous step size used by the predictor and the
  * closing kick (0 restarts the integration as at t = 0). */
 sph_status sph_set_dt_old(sph_ctx *ctx, double dt_old);

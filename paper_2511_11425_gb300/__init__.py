@@ -27,7 +27,8 @@ KERNELS = {"wc2": 0, "wc4": 1, "wc6": 2, "m4": 3}
 ENERGY = {"pdv": 0, "isentropic": 1}
 EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph_density_at",
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
-           "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version")
+           "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
+           "sph_reduce_conserved_noalloc")
 
 
 class SphError(RuntimeError):
@@ -89,6 +90,7 @@ def lib():
         L.sph_step_host.argtypes = [vp, pp, dbl, C.POINTER(dbl), C.POINTER(i64),
                                     C.POINTER(i64), vp]
         L.sph_reduce_conserved.argtypes = [vp, pp, C.POINTER(dbl), vp]
+        L.sph_reduce_conserved_noalloc.argtypes = [pp, vp, vp]
         L.sph_set_dt_old.argtypes = [vp, dbl]
         L.sph_get_stats.argtypes = [vp, C.POINTER(c_stats)]
         L.sph_last_error.argtypes = [vp]
@@ -291,6 +293,15 @@ def sph_reduce_conserved(ctx, parts: Particles, stream=None):
     out = (C.c_double * 9)()
     _check(ctx, lib().sph_reduce_conserved(ctx, C.byref(s), out, _stream(stream)))
     return list(out)
+
+
+def sph_reduce_conserved_noalloc(parts: Particles, out, stream=None):
+    """Totals into `out` (a device tensor of 9 float64) without any allocation.
+
+    Only queues the work: synchronise the stream before reading `out`."""
+    s = parts.c()
+    _check(None, lib().sph_reduce_conserved_noalloc(C.byref(s), C.c_void_p(out.data_ptr()),
+                                                    _stream(stream)))
 
 
 def sph_set_dt_old(ctx, dt_old: float):
