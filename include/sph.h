@@ -141,6 +141,21 @@ typedef struct {
  */
 sph_status sph_create(const sph_params *params, int64_t capacity, sph_ctx **out);
 
+/*
+ * sph_batch_create: a context for `ninst` INDEPENDENT problems stepped
+ * together (the batched form): instance k owns particles
+ * [offsets[k], offsets[k+1]) of every array (offsets: host array of ninst+1,
+ * offsets[0] = 0), has its own box, periodicity, gamma, viscosity parameters
+ * and time step, and never interacts with another instance.  Every phase is
+ * one kernel launch over all instances.  params: host array of ninst structs;
+ * kernel, energy_mode, max_newton, h_rel_tol and list_margin must agree
+ * (SPH_ERR_ARG otherwise).  All calls below accept a batch context with
+ * p->n = offsets[ninst]; sph_kdk_step's dt_used reports instance 0 (all steps:
+ * sph_batch_get_dt), sph_reduce_conserved writes 9 totals per instance.
+ */
+sph_status sph_batch_create(const sph_params *params, int32_t ninst, const int64_t *offsets,
+                            sph_ctx **out);
+
 /* sph_destroy: free the context and its device memory (NULL is ignored). */
 void sph_destroy(sph_ctx *ctx);
 
@@ -231,11 +246,30 @@ sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, 
                          int64_t *h2d_bytes, int64_t *d2h_bytes, void *stream);
 
 /*
- * sph_reduce_conserved: out[0..8] = M, P_x, P_y, P_z, L_x, L_y, L_z, E_kin,
- * E_int from m, x, v, u of *p, summed in FP64 in a fixed order (bit-identical
- * from run to run).  out is a HOST array of 9 doubles.
+ * sph_reduce_conserved: out[9k .. 9k+8] = M, P_x, P_y, P_z, L_x, L_y, L_z,
+ * E_kin, E_int of instance k (one instance unless the context is a batch),
+ * from m, x, v, u of *p, summed in FP64 in a fixed order (bit-identical from
+ * run to run).  out is a HOST array of 9 doubles per instance.
  */
-sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double out[9], void *stream);
+sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double *out, void *stream);
+
+/*
+ * sph_graph_capture: record one whole sph_step (build, density with its
+ * re-walk rounds, forces, kick-drift-kick and the status read-back) on
+ * `stream` into a CUDA graph owned by the context, without running it.  The
+ * graph is bound to the arrays of *p and to dt_fixed; stream must not be the
+ * legacy default stream.  In SPH_ENERGY_ISENTROPIC mode capture after one
+ * plain sph_step, so the previous density exists.  A new capture replaces
+ * the old graph.
+ * sph_graph_launch: replay the captured step on `stream`, wait, and report
+ * the status like sph_step (dt_used: new step of instance 0, may be NULL).
+ */
+sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double dt_fixed, void *stream);
+sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stream);
+
+/* sph_batch_get_dt: the step size each instance used in the last
+ * kick-drift-kick (host array of one double per instance). */
+sph_status sph_batch_get_dt(const sph_ctx *ctx, double *out);
 
 /*
  * sph_reduce_conserved_noalloc: the totals of sph_reduce_conserved without a

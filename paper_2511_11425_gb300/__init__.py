@@ -28,7 +28,8 @@ ENERGY = {"pdv": 0, "isentropic": 1}
 EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph_density_at",
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
            "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
-           "sph_reduce_conserved_noalloc")
+           "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
+           "sph_graph_capture", "sph_graph_launch")
 
 
 class SphError(RuntimeError):
@@ -91,6 +92,11 @@ def lib():
                                     C.POINTER(i64), vp]
         L.sph_reduce_conserved.argtypes = [vp, pp, C.POINTER(dbl), vp]
         L.sph_reduce_conserved_noalloc.argtypes = [pp, vp, vp]
+        L.sph_batch_create.argtypes = [C.POINTER(c_params), C.c_int32, C.POINTER(i64),
+                                       C.POINTER(vp)]
+        L.sph_batch_get_dt.argtypes = [vp, C.POINTER(dbl)]
+        L.sph_graph_capture.argtypes = [vp, pp, dbl, vp]
+        L.sph_graph_launch.argtypes = [vp, C.POINTER(dbl), vp]
         L.sph_set_dt_old.argtypes = [vp, dbl]
         L.sph_get_stats.argtypes = [vp, C.POINTER(c_stats)]
         L.sph_last_error.argtypes = [vp]
@@ -235,6 +241,36 @@ def sph_create(params: Params, capacity: int):
     return ctx
 
 
+def sph_batch_create(params_list, offsets):
+    """Context for independent problems: params_list[k] governs particles
+    offsets[k]:offsets[k+1] of one concatenated Particles set."""
+    n = len(params_list)
+    cps = (c_params * n)(*[p.c() for p in params_list])
+    offs = (C.c_int64 * (n + 1))(*[int(o) for o in offsets])
+    ctx = C.c_void_p()
+    rc = lib().sph_batch_create(cps, n, offs, C.byref(ctx))
+    _check(None, rc)
+    ctx.ninst = n
+    return ctx
+
+
+def sph_batch_get_dt(ctx, ninst):
+    out = (C.c_double * ninst)()
+    _check(ctx, lib().sph_batch_get_dt(ctx, out))
+    return list(out)
+
+
+def sph_graph_capture(ctx, parts: Particles, dt_fixed=0.0, stream=None):
+    s = parts.c()
+    _check(ctx, lib().sph_graph_capture(ctx, C.byref(s), float(dt_fixed), _stream(stream)))
+
+
+def sph_graph_launch(ctx, stream=None) -> float:
+    dt = C.c_double()
+    _check(ctx, lib().sph_graph_launch(ctx, C.byref(dt), _stream(stream)))
+    return dt.value
+
+
 def sph_destroy(ctx):
     lib().sph_destroy(ctx)
 
@@ -288,9 +324,11 @@ def sph_step_host(ctx, host_parts: Particles, dt_fixed=0.0, stream=None):
     return dt.value, hb.value, db.value
 
 
-def sph_reduce_conserved(ctx, parts: Particles, stream=None):
+def sph_reduce_conserved(ctx, parts: Particles, stream=None, ninst=None):
+    """Totals [M, P, L, E_kin, E_int] (9 values; 9 per instance for a batch)."""
     s = parts.c()
-    out = (C.c_double * 9)()
+    k = ninst or getattr(ctx, "ninst", 1)
+    out = (C.c_double * (9 * k))()
     _check(ctx, lib().sph_reduce_conserved(ctx, C.byref(s), out, _stream(stream)))
     return list(out)
 

@@ -1,8 +1,12 @@
-// sph_api.cu -- the C ABI declared in include/sph.h: context management and
-// host orchestration of the kernels.  Every entry point queues its kernels on
-// the caller's stream, then reads the device status word back (one small
-// device-to-host copy + stream synchronisation) and turns it into a
-// sph_status.  No exception, abort or device trap crosses the ABI.
+// sph_api.cu -- the C ABI declared in include/sph.h: contexts, the layout of
+// instances, buckets, groups and trees, and host orchestration of the kernels.
+//
+// Every phase is queued on the caller's stream without host round trips; an
+// entry point ends with ONE device-to-host read of the status word and a
+// stream synchronisation, then turns the status into a sph_status.  The same
+// queue can be captured once into a CUDA graph and replayed.  No exception,
+// abort or device trap crosses the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -16,7 +20,6 @@ using namespace sph;
 
 struct sph_ctx {
     Ctx c;
-    double *hbuf = nullptr;  // pinned host scratch (dts, conserved totals)
 };
 
 namespace {
@@ -45,25 +48,10 @@ cudaError_t dalloc(T **p, size_t count)
     return cudaMalloc((void **)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
-void free_ctx(Ctx &c)
-{
-    void *ptrs[] = {c.st, c.dts, c.dtmin, c.morton_box, c.bbox_part, c.cons_part, c.cons_out,
-                    c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist, c.digit_tot, c.tmp, c.origin,
-                    c.node, c.pm, c.fpos, c.fvel, c.fth, c.acc, c.acc2, c.rho_old, c.h_seed,
-                    c.list_start, c.list_cnt, c.list, c.redo, c.gflag, c.mirror};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (c.st_host) cudaFreeHost(c.st_host);
-    if (c.ev0) cudaEventDestroy(c.ev0);
-    if (c.ev1) cudaEventDestroy(c.ev1);
-    for (cudaEvent_t e : c.kev)
-        if (e) cudaEventDestroy(e);
-}
-
-int ilog2_ceil(int v)
+int ilog2_ceil(int64_t v)
 {
     int l = 0;
-    while ((1 << l) < v) ++l;
+    while (((int64_t)1 << l) < v) ++l;
     return l;
 }
 
@@ -79,37 +67,283 @@ bool particles_ok(const sph_particles *p)
     return p->n >= 0;
 }
 
+bool params_ok(const sph_params *prm)
+{
+    if (!prm) return false;
+    if (prm->kernel < 0 || prm->kernel > 3 || !(prm->gamma > 1.0) || !(prm->n_ngb > 0.0) ||
+        prm->max_newton < 1 || prm->max_newton > 255 || !(prm->h_rel_tol > 0.0) ||
+        !(prm->list_margin >= 0.0) || !(prm->eta_courant > 0.0) || !(prm->eta_acc > 0.0) ||
+        !(prm->alpha >= 0.0) || !(prm->beta >= 0.0) || !(prm->eps_av > 0.0) ||
+        (prm->energy_mode != SPH_ENERGY_PDV && prm->energy_mode != SPH_ENERGY_ISENTROPIC))
+        return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(prm->box_hi[a] > prm->box_lo[a]) || !std::isfinite(prm->box_lo[a]) ||
+            !std::isfinite(prm->box_hi[a]))
+            return false;
+    return true;
+}
+
+// physical parameters of one instance (geometry fields are set by the layout)
+Inst inst_params(const sph_params &prm)
+{
+    Inst I;
+    std::memset(&I, 0, sizeof I);
+    double maxext = 0.0, maxabs = 0.0, hcap = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        const double L = prm.box_hi[a] - prm.box_lo[a];
+        I.periodic[a] = prm.periodic[a] ? 1 : 0;
+        I.L[a] = (float)L;
+        I.invL[a] = (float)(1.0 / L);
+        I.lo[a] = prm.box_lo[a];
+        I.hi[a] = prm.box_hi[a];
+        I.Ld[a] = L;
+        I.invLd[a] = 1.0 / L;
+        maxext = fmax(maxext, L);
+        maxabs = fmax(maxabs, fmax(fabs(prm.box_lo[a]), fabs(prm.box_hi[a])));
+        if (I.periodic[a]) hcap = fmin(hcap, 0.5 * L);
+    }
+    I.gamma = (float)prm.gamma;
+    I.alpha = (float)prm.alpha;
+    I.beta = (float)prm.beta;
+    I.eps_av = (float)prm.eps_av;
+    I.eta_courant = (float)prm.eta_courant;
+    I.eta_acc = (float)prm.eta_acc;
+    I.n_ngb = (float)prm.n_ngb;
+    I.hcap = (float)hcap;
+    I.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
+    I.inv_q = 1.0 / I.q;
+    I.qf = (float)I.q;
+    I.eps_abs = (float)(4.0 * std::ldexp(1.0, -23) * fmax(maxext, maxabs));
+    return I;
+}
+
+// sizes the layout of `counts` needs
+struct Sizes {
+    int64_t n = 0, nb = 0, ng = 0, nodes = 0, refit = 0, cons_blocks = 0;
+};
+
+Sizes layout_sizes(const std::vector<int64_t> &counts)
+{
+    Sizes z;
+    for (int64_t nk : counts) {
+        const int64_t nb = (nk + kBucket - 1) / kBucket;
+        const int logP = ilog2_ceil(std::max<int64_t>(nb, 1));
+        const int64_t P = (int64_t)1 << logP;
+        const int logG = std::min(logP, kGroupLog);
+        z.n += nk;
+        z.nb += nb;
+        z.ng += (nb + (1 << logG) - 1) >> logG;
+        z.nodes += 2 * P;
+        z.refit += P / 2 + 4;  // one block per 256 nodes of a band, plus the upper bands
+        z.cons_blocks = std::max<int64_t>(z.cons_blocks, (nk + kConsChunk - 1) / kConsChunk);
+    }
+    return z;
+}
+
+// allocate every buffer for the sizes `cap`
+sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
+{
+    const int64_t np = std::max<int64_t>(cap.n, 1);
+    const int64_t nb = std::max<int64_t>(cap.nb, 1), ng = std::max<int64_t>(cap.ng, 1);
+    const int64_t ntiles = (np + kSortTile - 1) / kSortTile;
+    sph_status rc = SPH_OK;
+#define AL(ptr, cnt)                                                                         \
+    do {                                                                                     \
+        if (rc == SPH_OK && dalloc(&(ptr), (size_t)(cnt)) != cudaSuccess) {                   \
+            rc = failf(c, SPH_ERR_CUDA, "cudaMalloc of %s failed", #ptr);                    \
+        }                                                                                    \
+    } while (0)
+    AL(c.st, 1);
+    AL(c.inst, ninst);
+    AL(c.dts, 2 * ninst);
+    AL(c.dtmin, ninst);
+    AL(c.morton_box, 6 * ninst);
+    AL(c.bbox_part, (size_t)6 * kBboxChunks * ninst);
+    AL(c.cons_part, (size_t)9 * std::max<int64_t>(cap.cons_blocks, 1) * ninst);
+    AL(c.cons_out, (size_t)9 * ninst);
+    AL(c.pinst, np);
+    AL(c.keys[0], np);
+    AL(c.keys[1], np);
+    AL(c.vals[0], np);
+    AL(c.vals[1], np);
+    AL(c.hist, (size_t)256 * ntiles);
+    AL(c.digit_tot, 256);
+    {
+        char *t = nullptr;
+        AL(t, (size_t)112 * np);
+        c.tmp = t;
+    }
+    AL(c.bstart, nb);
+    AL(c.binst, nb);
+    AL(c.origin, (size_t)3 * nb);
+    AL(c.gfirst, ng);
+    AL(c.gflag, ng);
+    AL(c.list_cnt, ng);
+    AL(c.list, (size_t)ng * kWalkCap);
+    AL(c.redo, (size_t)kRelistRounds * ng);
+    AL(c.node, (size_t)4 * std::max<int64_t>(cap.nodes, 2));
+    AL(c.refit, std::max<int64_t>(cap.refit, 1));
+    AL(c.pm, np);
+    AL(c.fpos, np);
+    AL(c.fvel, np);
+    AL(c.fth, np);
+    AL(c.acc, np);
+    AL(c.acc2, np);
+    AL(c.rho_old, np);
+    AL(c.h_seed, np);
+#undef AL
+    if (rc == SPH_OK && (cudaMallocHost((void **)&c.st_host, sizeof(DevStatus)) != cudaSuccess ||
+                         cudaMallocHost((void **)&c.dts_host, sizeof(double) * 2 * ninst) != cudaSuccess ||
+                         cudaMallocHost((void **)&c.cons_host, sizeof(double) * 9 * ninst) != cudaSuccess))
+        rc = failf(c, SPH_ERR_CUDA, "cudaMallocHost failed");
+    if (rc == SPH_OK) {
+        for (cudaEvent_t *e : {&c.ev0, &c.ev1, &c.kev[0], &c.kev[1], &c.kev[2], &c.kev[3],
+                               &c.kev[4], &c.kev[5]})
+            if (cudaEventCreate(e) != cudaSuccess) rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
+    }
+    if (rc == SPH_OK && cudaMemset(c.dts, 0, sizeof(double) * 2 * ninst) != cudaSuccess)
+        rc = SPH_ERR_CUDA;
+    if (rc == SPH_OK && c.st_host) std::memset(c.st_host, 0, sizeof(DevStatus));
+    if (rc == SPH_OK && c.dts_host) std::memset(c.dts_host, 0, sizeof(double) * 2 * ninst);
+    c.cons_blocks = (int)std::max<int64_t>(cap.cons_blocks, 1);
+    return rc;
+}
+
+void free_ctx(Ctx &c)
+{
+    if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    void *ptrs[] = {c.st, c.inst, c.dts, c.dtmin, c.morton_box, c.bbox_part, c.cons_part,
+                    c.cons_out, c.pinst, c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist,
+                    c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
+                    c.list_cnt, c.list, c.redo, c.node, c.refit, c.pm, c.fpos, c.fvel, c.fth,
+                    c.acc, c.acc2, c.rho_old, c.h_seed, c.mirror};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (void *p : {(void *)c.st_host, (void *)c.dts_host, (void *)c.cons_host})
+        if (p) cudaFreeHost(p);
+    for (cudaEvent_t e : {c.ev0, c.ev1, c.kev[0], c.kev[1], c.kev[2], c.kev[3], c.kev[4], c.kev[5]})
+        if (e) cudaEventDestroy(e);
+}
+
+// lay out instances of the given particle counts (offsets follow the order)
+// and upload the index maps; synchronous (only when the layout changes)
+sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
+{
+    const int ni = (int)counts.size();
+    std::vector<Inst> insts(ni);
+    std::vector<int> bstart, binst, gfirst;
+    std::vector<unsigned short> pinst;
+    std::vector<std::vector<RefitBlock>> bands;
+    int64_t off = 0, boff = 0, goff = 0, nbase = 0;
+    bool any_open = false;
+    for (int k = 0; k < ni; ++k) {
+        Inst I = inst_params(c.prm[k]);
+        const int64_t nk = counts[k];
+        I.off = (int)off;
+        I.n = (int)nk;
+        I.nb = (int)((nk + kBucket - 1) / kBucket);
+        I.boff = (int)boff;
+        I.logP = ilog2_ceil(std::max(I.nb, 1));
+        I.P = 1 << I.logP;
+        I.logG = std::min(I.logP, kGroupLog);
+        I.G = 1 << I.logG;
+        I.ng = (I.nb + I.G - 1) >> I.logG;
+        I.goff = (int)goff;
+        I.nbase = (int)nbase;
+        for (int a = 0; a < 3; ++a) any_open = any_open || !I.periodic[a];
+        for (int b = 0; b < I.nb; ++b) {
+            bstart.push_back(I.off + b * kBucket);
+            binst.push_back(k);
+        }
+        for (int g = 0; g < I.ng; ++g) gfirst.push_back(I.boff + (g << I.logG));
+        pinst.insert(pinst.end(), (size_t)nk, (unsigned short)k);
+        int lvl = I.logP, band = 0;
+        while (lvl > 0) {
+            const int levels = std::min(lvl, 8);
+            if ((int)bands.size() <= band) bands.emplace_back();
+            for (int blk = 0; blk < (1 << (lvl - levels)); ++blk)
+                bands[band].push_back(RefitBlock{k, lvl, levels, blk});
+            lvl -= levels;
+            ++band;
+        }
+        insts[k] = I;
+        off += nk;
+        boff += I.nb;
+        goff += I.ng;
+        nbase += 2 * (int64_t)I.P;
+    }
+    std::vector<RefitBlock> sched;
+    c.refit_band.clear();
+    for (auto &b : bands) {
+        c.refit_band.push_back((int)b.size());
+        sched.insert(sched.end(), b.begin(), b.end());
+    }
+    int nbits = 30;
+    while (((int64_t)1 << (nbits - 30)) < ni) ++nbits;
+    KParams &kp = c.kp;
+    kp.ninst = ni;
+    kp.n = (int)off;
+    kp.nb = (int)boff;
+    kp.ng = (int)goff;
+    kp.nnodes = (int)nbase;
+    kp.key_passes = (nbits + 7) / 8;
+    kp.any_open = any_open ? 1 : 0;
+    c.inst_host = insts;
+    int64_t cb = 1;
+    for (int64_t nk : counts) cb = std::max<int64_t>(cb, (nk + kConsChunk - 1) / kConsChunk);
+    c.cons_blocks = (int)cb;
+    CK(cudaMemcpy(c.inst, insts.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice));
+    if (!bstart.empty()) {
+        CK(cudaMemcpy(c.bstart, bstart.data(), sizeof(int) * bstart.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c.binst, binst.data(), sizeof(int) * binst.size(), cudaMemcpyHostToDevice));
+    }
+    if (!gfirst.empty())
+        CK(cudaMemcpy(c.gfirst, gfirst.data(), sizeof(int) * gfirst.size(), cudaMemcpyHostToDevice));
+    if (!pinst.empty())
+        CK(cudaMemcpy(c.pinst, pinst.data(), sizeof(unsigned short) * pinst.size(),
+                      cudaMemcpyHostToDevice));
+    if (!sched.empty())
+        CK(cudaMemcpy(c.refit, sched.data(), sizeof(RefitBlock) * sched.size(),
+                      cudaMemcpyHostToDevice));
+    c.n_built = off;
+    return SPH_OK;
+}
+
 sph_status begin(sph_ctx *ctx, cudaStream_t s)
 {
     Ctx &c = ctx->c;
     c.err.clear();
     CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
-    CK(cudaEventRecord(c.ev0, s));
     return SPH_OK;
 }
 
-// read the device status back; translate the first kernel error
-sph_status finish(sph_ctx *ctx, cudaStream_t s, float *ms)
+// queue the status read-back (also recorded into a captured graph)
+sph_status queue_status(Ctx &c, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c.dts_host, c.dts, sizeof(double) * 2 * c.kp.ninst, cudaMemcpyDeviceToHost, s));
+    return SPH_OK;
+}
+
+// wait for the queued work and translate the first kernel error
+sph_status settle(sph_ctx *ctx, cudaStream_t s)
 {
     Ctx &c = ctx->c;
-    CK(cudaGetLastError());
-    CK(cudaEventRecord(c.ev1, s));
-    CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->hbuf, c.dts, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (ms) cudaEventElapsedTime(ms, c.ev0, c.ev1);
+    CK(cudaGetLastError());
     const DevStatus &h = *c.st_host;
     switch (h.code) {
     case ST_OK: return SPH_OK;
     case ST_ARG:
-        return failf(c, SPH_ERR_ARG, "particle %d: smoothing length reached half a periodic box "
-                     "length (minimum image no longer unique)", h.detail);
+        return failf(c, SPH_ERR_ARG, "index %d: smoothing length reached half a periodic box "
+                     "length, or a bucket left the position grid", h.detail);
     case ST_CAPACITY:
-        return failf(c, SPH_ERR_CAPACITY, "bucket %d: more than %d bounds-tree nodes or source "
+        return failf(c, SPH_ERR_CAPACITY, "group %d: more than %d bounds-tree nodes or source "
                      "buckets overlap its bounds", h.detail, kWalkCap);
     case ST_NOCONV:
         return failf(c, SPH_ERR_NOCONV, "particle %d: Newton iteration on h did not converge in "
-                     "%d iterations", h.detail, c.prm.max_newton);
+                     "%d iterations or %d re-walks", h.detail, c.kp.max_newton, kRelistRounds);
     case ST_NONFINITE:
         return failf(c, SPH_ERR_NONFINITE, "non-finite value at index %d", h.detail);
     case ST_TIMEOUT: return failf(c, SPH_ERR_TIMEOUT, "device wait timed out (%d)", h.detail);
@@ -117,27 +351,126 @@ sph_status finish(sph_ctx *ctx, cudaStream_t s, float *ms)
     }
 }
 
-cudaError_t grow_list(Ctx &c, int64_t need)
+sph_status finish(sph_ctx *ctx, cudaStream_t s)
 {
-    int64_t cap = need + need / 2 + 1024;
-    if (c.list) cudaFree(c.list);
-    c.list = nullptr;
-    c.list_cap = 0;
-    cudaError_t e = cudaMalloc((void **)&c.list, sizeof(unsigned) * (size_t)cap);
-    if (e == cudaSuccess) c.list_cap = cap;
-    return e;
+    Ctx &c = ctx->c;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c.ev1, s));
+    sph_status rc = queue_status(c, s);
+    if (rc) return rc;
+    return settle(ctx, s);
 }
 
-void set_geometry(Ctx &c, int64_t n)
+float elapsed(cudaEvent_t a, cudaEvent_t b)
 {
-    KParams &k = c.kp;
-    k.n = (int)n;
-    k.nb = (int)((n + kBucket - 1) / kBucket);
-    k.logP = ilog2_ceil(k.nb > 0 ? k.nb : 1);
-    k.P = 1 << k.logP;
-    k.logG = k.logP < 3 ? k.logP : 3;  // groups of 8 buckets (256 particles)
-    k.G = 1 << k.logG;
-    k.ng = (k.nb + k.G - 1) / k.G;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 0.f;
+    return ms;
+}
+
+// make sure the layout matches p->n (single-problem contexts follow n)
+sph_status ensure_layout(Ctx &c, const sph_particles *p)
+{
+    if (!particles_ok(p)) return failf(c, SPH_ERR_ARG, "NULL particle array or n < 0");
+    if (p->n > c.capacity)
+        return failf(c, SPH_ERR_ARG, "n = %lld exceeds the capacity %lld", (long long)p->n,
+                     (long long)c.capacity);
+    if (c.prm.size() > 1) {
+        if (p->n != c.kp.n)
+            return failf(c, SPH_ERR_ARG, "a batch context needs exactly %d particles", c.kp.n);
+        return SPH_OK;
+    }
+    if (p->n != c.n_built || c.inst_host.empty()) return set_layout(c, {p->n});
+    return SPH_OK;
+}
+
+// ---- phases: queue only ------------------------------------------------------
+sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t s, bool timed)
+{
+    const size_t bytes = sizeof(float) * (size_t)p->n;
+    const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC && c.rho_valid;
+    if (isen) CK(cudaMemcpyAsync(c.rho_old, p->rho, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c.h_seed, h_seed ? h_seed : p->h, bytes, cudaMemcpyDeviceToDevice, s));
+    if (timed) CK(cudaEventRecord(c.kev[0], s));
+    CK(launch_walk(c, *p, WALK_DENSITY, -1, c.h_seed, s));
+    if (timed) CK(cudaEventRecord(c.kev[1], s));
+    CK(launch_density(c, *p, c.h_seed, -1, 0, 0, nullptr, nullptr, s));
+    if (timed) CK(cudaEventRecord(c.kev[2], s));
+    // groups whose h left the list coverage: re-walk and re-solve on the
+    // device (the launches exit at once when nothing is queued)
+    for (int r = 0; r < kRelistRounds; ++r) {
+        CK(launch_walk(c, *p, WALK_DENSITY, r, c.h_seed, s));
+        CK(launch_density(c, *p, c.h_seed, r, 0, 0, nullptr, nullptr, s));
+    }
+    if (isen) CK(launch_isentropic(c, *p, s));
+    CK(launch_bob_refit(c, *p, s));
+    return SPH_OK;
+}
+
+sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed)
+{
+    CK(launch_predict(c, *p, s));
+    if (timed) CK(cudaEventRecord(c.kev[3], s));
+    CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
+    if (timed) CK(cudaEventRecord(c.kev[4], s));
+    CK(launch_forces(c, *p, s));
+    if (timed) CK(cudaEventRecord(c.kev[5], s));
+    CK(launch_finalize(c, *p, s));
+    return SPH_OK;
+}
+
+void density_stats(Ctx &c)
+{
+    const DevStatus &h = *c.st_host;
+    c.stats.density_pairs = h.density_pairs;
+    c.stats.density_candidates = h.density_cand;
+    c.stats.max_newton_iters = h.max_iters;
+    c.stats.relists = (int)(h.redo_cnt[0] + h.redo_cnt[1] + h.redo_cnt[2]);
+}
+
+void force_stats(Ctx &c)
+{
+    const DevStatus &h = *c.st_host;
+    c.stats.force_pairs = h.force_pairs;
+    c.stats.force_candidates = h.force_cand;
+    c.stats.force_av_pairs = h.force_av_pairs;
+}
+
+sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_t> &counts,
+                      int64_t capacity, sph_ctx **out)
+{
+    for (int k = 0; k < ninst; ++k)
+        if (!params_ok(&prm[k])) return SPH_ERR_ARG;
+    for (int k = 1; k < ninst; ++k)
+        if (prm[k].kernel != prm[0].kernel || prm[k].energy_mode != prm[0].energy_mode ||
+            prm[k].max_newton != prm[0].max_newton || prm[k].h_rel_tol != prm[0].h_rel_tol ||
+            prm[k].list_margin != prm[0].list_margin)
+            return SPH_ERR_ARG;
+    sph_ctx *ctx = new (std::nothrow) sph_ctx;
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    c.prm.assign(prm, prm + ninst);
+    c.capacity = capacity;
+    c.dt_host.assign(ninst, 0.0);
+    cudaGetDevice(&c.device);
+    std::memset(&c.kp, 0, sizeof c.kp);
+    c.kp.kernel = prm[0].kernel;
+    c.kp.energy_mode = prm[0].energy_mode;
+    c.kp.max_newton = prm[0].max_newton;
+    c.kp.h_rel_tol = (float)prm[0].h_rel_tol;
+    c.kp.margin = (float)prm[0].list_margin;
+    c.kp.ninst = ninst;
+    const Sizes z = layout_sizes(counts);
+    sph_status rc = allocate(c, z, ninst);
+    if (rc == SPH_OK) rc = set_layout(c, counts);
+    if (rc == SPH_OK && cudaDeviceSynchronize() != cudaSuccess) rc = SPH_ERR_CUDA;
+    if (rc != SPH_OK) {
+        free_ctx(c);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return SPH_OK;
 }
 
 }  // namespace
@@ -147,125 +480,22 @@ extern "C" sph_status sph_create(const sph_params *prm, int64_t capacity, sph_ct
 {
     if (!prm || !out || capacity < 0 || capacity > (int64_t)0x7fffffff - 64) return SPH_ERR_ARG;
     *out = nullptr;
-    if (prm->kernel < 0 || prm->kernel > 3 || !(prm->gamma > 1.0) || !(prm->n_ngb > 0.0) ||
-        prm->max_newton < 1 || prm->max_newton > 255 || !(prm->h_rel_tol > 0.0) ||
-        !(prm->list_margin >= 0.0) || !(prm->eta_courant > 0.0) || !(prm->eta_acc > 0.0) ||
-        !(prm->alpha >= 0.0) || !(prm->beta >= 0.0) || !(prm->eps_av > 0.0) ||
-        (prm->energy_mode != SPH_ENERGY_PDV && prm->energy_mode != SPH_ENERGY_ISENTROPIC))
-        return SPH_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (!(prm->box_hi[a] > prm->box_lo[a]) || !std::isfinite(prm->box_lo[a]) ||
-            !std::isfinite(prm->box_hi[a]))
-            return SPH_ERR_ARG;
-    sph_ctx *ctx = new (std::nothrow) sph_ctx;
-    if (!ctx) return SPH_ERR_ARG;
-    Ctx &c = ctx->c;
-    c.prm = *prm;
-    c.capacity = capacity;
-    cudaGetDevice(&c.device);
-    KParams &k = c.kp;
-    std::memset(&k, 0, sizeof k);
-    k.kernel = prm->kernel;
-    k.energy_mode = prm->energy_mode;
-    k.max_newton = prm->max_newton;
-    double maxext = 0.0, maxabs = 0.0, hcap = INFINITY;
-    for (int a = 0; a < 3; ++a) {
-        double L = prm->box_hi[a] - prm->box_lo[a];
-        k.periodic[a] = prm->periodic[a] ? 1 : 0;
-        k.L[a] = (float)L;
-        k.invL[a] = (float)(1.0 / L);
-        k.halfL[a] = (float)(0.5 * L);
-        k.lo[a] = prm->box_lo[a];
-        k.hi[a] = prm->box_hi[a];
-        maxext = fmax(maxext, L);
-        maxabs = fmax(maxabs, fmax(fabs(prm->box_lo[a]), fabs(prm->box_hi[a])));
-        if (k.periodic[a]) hcap = fmin(hcap, 0.5 * L);
-    }
-    k.n_ngb = (float)prm->n_ngb;
-    k.gamma = (float)prm->gamma;
-    k.alpha = (float)prm->alpha;
-    k.beta = (float)prm->beta;
-    k.eps_av = (float)prm->eps_av;
-    k.eta_courant = (float)prm->eta_courant;
-    k.eta_acc = (float)prm->eta_acc;
-    k.h_rel_tol = (float)prm->h_rel_tol;
-    k.margin = (float)prm->list_margin;
-    k.hcap = (float)hcap;
-    k.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
-    k.inv_q = 1.0 / k.q;
-    k.qf = (float)k.q;
-    for (int a = 0; a < 3; ++a) {
-        k.Ld[a] = prm->box_hi[a] - prm->box_lo[a];
-        k.invLd[a] = 1.0 / k.Ld[a];
-    }
-    k.eps_abs = (float)(4.0 * std::ldexp(1.0, -23) * fmax(maxext, maxabs));
+    return create_ctx(prm, 1, {capacity}, capacity, out);
+}
 
-    int64_t cap = capacity > 0 ? capacity : 1;
-    c.nb_cap = (int)((cap + kBucket - 1) / kBucket);
-    c.P_cap = 1 << ilog2_ceil(c.nb_cap);
-    int ntiles = (int)((cap + kSortTile - 1) / kSortTile);
-    sph_status rc = SPH_OK;
-#define AL(ptr, cnt)                                                                         \
-    do {                                                                                     \
-        if (rc == SPH_OK && dalloc(&(ptr), (size_t)(cnt)) != cudaSuccess) {                   \
-            rc = failf(c, SPH_ERR_CUDA, "cudaMalloc of %s failed", #ptr);                    \
-        }                                                                                    \
-    } while (0)
-    AL(c.st, 1);
-    AL(c.dts, 2);
-    AL(c.dtmin, 1);
-    AL(c.morton_box, 6);
-    AL(c.bbox_part, 152 * 6);
-    AL(c.cons_part, 304 * 9);
-    AL(c.cons_out, 16);
-    AL(c.keys[0], cap);
-    AL(c.keys[1], cap);
-    AL(c.vals[0], cap);
-    AL(c.vals[1], cap);
-    AL(c.hist, (size_t)256 * ntiles);
-    AL(c.digit_tot, 256);
-    {
-        char *t = nullptr;
-        AL(t, (size_t)112 * cap);
-        c.tmp = t;
+extern "C" sph_status sph_batch_create(const sph_params *params, int32_t ninst,
+                                       const int64_t *offsets, sph_ctx **out)
+{
+    if (!params || !offsets || !out || ninst < 1 || ninst > 65535) return SPH_ERR_ARG;
+    *out = nullptr;
+    std::vector<int64_t> counts(ninst);
+    if (offsets[0] != 0) return SPH_ERR_ARG;
+    for (int k = 0; k < ninst; ++k) {
+        counts[k] = offsets[k + 1] - offsets[k];
+        if (counts[k] < 0) return SPH_ERR_ARG;
     }
-    AL(c.origin, (size_t)3 * c.nb_cap);
-    AL(c.node, (size_t)8 * c.P_cap);
-    AL(c.pm, cap);
-    AL(c.fpos, cap);
-    AL(c.fvel, cap);
-    AL(c.fth, cap);
-    AL(c.acc, cap);
-    AL(c.acc2, cap);
-    AL(c.rho_old, cap);
-    AL(c.h_seed, cap);
-    AL(c.list_start, c.nb_cap);
-    AL(c.gflag, c.nb_cap);
-    AL(c.list_cnt, c.nb_cap);
-    AL(c.redo, (size_t)2 * c.nb_cap);
-#undef AL
-    if (rc == SPH_OK && grow_list(c, (int64_t)c.nb_cap * 96) != cudaSuccess)
-        rc = failf(c, SPH_ERR_CUDA, "cudaMalloc of the interaction lists failed");
-    if (rc == SPH_OK && cudaMallocHost((void **)&c.st_host, sizeof(DevStatus)) != cudaSuccess)
-        rc = SPH_ERR_CUDA;
-    if (rc == SPH_OK && cudaMallocHost((void **)&ctx->hbuf, 32 * sizeof(double)) != cudaSuccess)
-        rc = SPH_ERR_CUDA;
-    if (rc == SPH_OK && (cudaEventCreate(&c.ev0) != cudaSuccess ||
-                         cudaEventCreate(&c.ev1) != cudaSuccess ||
-                         cudaEventCreate(&c.kev[0]) != cudaSuccess ||
-                         cudaEventCreate(&c.kev[1]) != cudaSuccess ||
-                         cudaEventCreate(&c.kev[2]) != cudaSuccess))
-        rc = SPH_ERR_CUDA;
-    if (rc == SPH_OK && cudaMemset(c.dts, 0, 2 * sizeof(double)) != cudaSuccess) rc = SPH_ERR_CUDA;
-    if (rc == SPH_OK && cudaDeviceSynchronize() != cudaSuccess) rc = SPH_ERR_CUDA;
-    if (rc != SPH_OK) {
-        free_ctx(c);
-        if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
-        delete ctx;
-        return rc;
-    }
-    *out = ctx;
-    return SPH_OK;
+    if (offsets[ninst] > (int64_t)0x7fffffff - 64) return SPH_ERR_ARG;
+    return create_ctx(params, ninst, counts, offsets[ninst], out);
 }
 
 extern "C" void sph_destroy(sph_ctx *ctx)
@@ -273,7 +503,6 @@ extern "C" void sph_destroy(sph_ctx *ctx)
     if (!ctx) return;
     cudaDeviceSynchronize();
     free_ctx(ctx->c);
-    if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
     delete ctx;
 }
 
@@ -281,83 +510,23 @@ extern "C" sph_status sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stre
 {
     if (!ctx) return SPH_ERR_ARG;
     Ctx &c = ctx->c;
-    if (!particles_ok(p) || p->n > c.capacity)
-        return failf(c, SPH_ERR_ARG, "sph_build_cells: NULL array or n = %lld > capacity %lld",
-                     p ? (long long)p->n : -1LL, (long long)c.capacity);
+    sph_status rc = ensure_layout(c, p);
+    if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     c.cells_valid = c.density_valid = c.forces_valid = false;
-    set_geometry(c, p->n);
-    c.n_built = p->n;
     if (p->n == 0) {
         c.cells_valid = true;
         return SPH_OK;
     }
-    sph_status rc = begin(ctx, s);
+    rc = begin(ctx, s);
     if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
     CK(launch_build(c, *p, s));
-    rc = finish(ctx, s, &c.stats.ms_build);
+    rc = finish(ctx, s);
+    c.stats.ms_build = elapsed(c.ev0, c.ev1);
     if (rc == SPH_OK) c.cells_valid = true;
     return rc;
 }
-
-namespace {
-
-// walk + Newton, re-walking buckets whose h left the list coverage
-sph_status density_passes(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
-{
-    Ctx &c = ctx->c;
-    unsigned long long dpairs = 0, dcand = 0;
-    int maxit = 0, relists = 0;
-    int64_t entries = 0;
-    float ms_walk = 0.f, ms_kernel = 0.f;
-    const unsigned *ids = nullptr;  // group ids of a re-walk pass (NULL: all groups)
-    int nids = c.kp.ng;
-    for (int round = 0; round < 12; ++round) {
-        sph_status rc = SPH_OK;
-        for (int attempt = 0; attempt < 3; ++attempt) {
-            rc = begin(ctx, s);
-            if (rc) return rc;
-            CK(cudaEventRecord(c.kev[0], s));
-            CK(launch_walk(c, *p, WALK_DENSITY, ids, nids, c.h_seed, s));
-            CK(cudaEventRecord(c.kev[1], s));
-            CK(launch_density(c, *p, c.h_seed, ids, nids, 0, 0, nullptr, nullptr, s));
-            CK(cudaEventRecord(c.kev[2], s));
-            rc = finish(ctx, s, nullptr);
-            float t01 = 0.f, t12 = 0.f;
-            cudaEventElapsedTime(&t01, c.kev[0], c.kev[1]);
-            cudaEventElapsedTime(&t12, c.kev[1], c.kev[2]);
-            ms_walk += t01;
-            ms_kernel += t12;
-            if ((int64_t)c.st_host->list_need <= c.list_cap) break;
-            CK(grow_list(c, (int64_t)c.st_host->list_need));
-            c.err.clear();
-        }
-        if (rc) return rc;
-        dpairs += c.st_host->density_pairs;
-        dcand += c.st_host->density_cand;
-        maxit = maxit > c.st_host->max_iters ? maxit : c.st_host->max_iters;
-        entries += c.st_host->list_need;
-        unsigned nredo = c.st_host->redo_count;
-        if (nredo == 0) {
-            c.stats.density_pairs = dpairs;
-            c.stats.density_candidates = dcand;
-            c.stats.max_newton_iters = maxit;
-            c.stats.relists = relists;
-            c.stats.list_entries_density = entries;
-            c.stats.ms_walk = ms_walk;
-            c.stats.ms_density_kernel = ms_kernel;
-            return SPH_OK;
-        }
-        relists += (int)nredo;
-        // redo ids were written into the half of c.redo not being read
-        ids = (ids == c.redo) ? c.redo + c.nb_cap : c.redo;
-        nids = (int)nredo;
-    }
-    return failf(c, SPH_ERR_NOCONV, "smoothing lengths kept leaving the interaction-list "
-                 "coverage after 12 re-walks");
-}
-
-}  // namespace
 
 extern "C" sph_status sph_density_h(sph_ctx *ctx, sph_particles *p, const float *h_seed, void *stream)
 {
@@ -371,28 +540,16 @@ extern "C" sph_status sph_density_h(sph_ctx *ctx, sph_particles *p, const float 
         return SPH_OK;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    size_t bytes = sizeof(float) * (size_t)p->n;
-    if (c.prm.energy_mode == SPH_ENERGY_ISENTROPIC && c.rho_valid)
-        CK(cudaMemcpyAsync(c.rho_old, p->rho, bytes, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(c.h_seed, h_seed ? h_seed : p->h, bytes, cudaMemcpyDeviceToDevice, s));
-    cudaEvent_t t0 = nullptr;
-    cudaEventCreate(&t0);
-    cudaEventRecord(t0, s);
-    sph_status rc = density_passes(ctx, p, s);
-    if (rc) {
-        cudaEventDestroy(t0);
-        return rc;
-    }
-    rc = begin(ctx, s);
-    if (rc) {
-        cudaEventDestroy(t0);
-        return rc;
-    }
-    if (c.prm.energy_mode == SPH_ENERGY_ISENTROPIC && c.rho_valid) CK(launch_isentropic(c, *p, s));
-    CK(launch_bob_refit(c, *p, s));
-    rc = finish(ctx, s, nullptr);
-    cudaEventElapsedTime(&c.stats.ms_density, t0, c.ev1);
-    cudaEventDestroy(t0);
+    sph_status rc = begin(ctx, s);
+    if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
+    rc = q_density(c, p, h_seed, s, true);
+    if (rc) return rc;
+    rc = finish(ctx, s);
+    c.stats.ms_density = elapsed(c.ev0, c.ev1);
+    c.stats.ms_walk = elapsed(c.kev[0], c.kev[1]);
+    c.stats.ms_density_kernel = elapsed(c.kev[1], c.kev[2]);
+    density_stats(c);
     if (rc == SPH_OK) {
         c.density_valid = true;
         c.rho_valid = true;
@@ -412,17 +569,13 @@ extern "C" sph_status sph_density_at(sph_ctx *ctx, sph_particles *p, const float
         return failf(c, SPH_ERR_STATE, "sph_density_at needs sph_build_cells on these particles first");
     if (p->n == 0) return SPH_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    sph_status rc = begin(ctx, s);
+    if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
     CK(cudaMemcpyAsync(c.h_seed, h, sizeof(float) * (size_t)p->n, cudaMemcpyDeviceToDevice, s));
-    sph_status rc = SPH_OK;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        rc = begin(ctx, s);
-        if (rc) return rc;
-        CK(launch_walk(c, *p, WALK_DENSITY, nullptr, c.kp.ng, c.h_seed, s));
-        CK(launch_density(c, *p, c.h_seed, nullptr, c.kp.ng, 1, cap, count, ids, s));
-        rc = finish(ctx, s, nullptr);
-        if ((int64_t)c.st_host->list_need <= c.list_cap) break;
-        CK(grow_list(c, (int64_t)c.st_host->list_need));
-    }
+    CK(launch_walk(c, *p, WALK_DENSITY, -1, c.h_seed, s));
+    CK(launch_density(c, *p, c.h_seed, -1, 1, cap, count, ids, s));
+    rc = finish(ctx, s);
     c.density_valid = false;
     c.forces_valid = false;
     return rc;
@@ -440,34 +593,17 @@ extern "C" sph_status sph_forces(sph_ctx *ctx, sph_particles *p, void *stream)
         return SPH_OK;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    sph_status rc = SPH_OK;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        rc = begin(ctx, s);
-        if (rc) return rc;
-        CK(launch_predict(c, *p, s));
-        CK(cudaEventRecord(c.kev[0], s));
-        CK(launch_walk(c, *p, WALK_FORCE, nullptr, c.kp.ng, nullptr, s));
-        CK(cudaEventRecord(c.kev[1], s));
-        CK(launch_forces(c, *p, s));
-        CK(cudaEventRecord(c.kev[2], s));
-        CK(launch_finalize(c, *p, s));
-        rc = finish(ctx, s, &c.stats.ms_forces);
-        if ((int64_t)c.st_host->list_need <= c.list_cap) break;
-        CK(grow_list(c, (int64_t)c.st_host->list_need));
-        c.err.clear();
-    }
-    if (rc == SPH_OK) {
-        c.forces_valid = true;
-        c.stats.force_pairs = c.st_host->force_pairs;
-        c.stats.force_candidates = c.st_host->force_cand;
-        c.stats.list_entries_force = c.st_host->list_need;
-        c.stats.force_av_pairs = c.st_host->force_av_pairs;
-        float t01 = 0.f, t12 = 0.f;
-        cudaEventElapsedTime(&t01, c.kev[0], c.kev[1]);
-        cudaEventElapsedTime(&t12, c.kev[1], c.kev[2]);
-        c.stats.ms_walk += t01;
-        c.stats.ms_force_kernel = t12;
-    }
+    sph_status rc = begin(ctx, s);
+    if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
+    rc = q_forces(c, p, s, true);
+    if (rc) return rc;
+    rc = finish(ctx, s);
+    c.stats.ms_forces = elapsed(c.ev0, c.ev1);
+    c.stats.ms_walk += elapsed(c.kev[3], c.kev[4]);
+    c.stats.ms_force_kernel = elapsed(c.kev[4], c.kev[5]);
+    force_stats(c);
+    if (rc == SPH_OK) c.forces_valid = true;
     return rc;
 }
 
@@ -488,26 +624,136 @@ extern "C" sph_status sph_kdk_step(sph_ctx *ctx, sph_particles *p, double dt_fix
     }
     sph_status rc = begin(ctx, s);
     if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
     CK(launch_kdk(c, *p, dt_fixed, s));
-    rc = finish(ctx, s, &c.stats.ms_kdk);
+    rc = finish(ctx, s);
+    c.stats.ms_kdk = elapsed(c.ev0, c.ev1);
     c.cells_valid = c.density_valid = c.forces_valid = false;
     if (rc == SPH_OK) {
-        c.stats.dt_old = ctx->hbuf[0];
-        if (dt_used) *dt_used = ctx->hbuf[0];
+        for (int k = 0; k < c.kp.ninst; ++k) c.dt_host[k] = c.dts_host[2 * k];
+        c.stats.dt_old = c.dt_host[0];
+        if (dt_used) *dt_used = c.dt_host[0];
     }
     return rc;
 }
 
+namespace {
+// the whole step queued without host round trips
+sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool timed)
+{
+    if (timed) CK(cudaEventRecord(c.ev0, s));
+    CK(launch_build(c, *p, s));
+    sph_status rc = q_density(c, p, nullptr, s, timed);
+    if (rc) return rc;
+    rc = q_forces(c, p, s, timed);
+    if (rc) return rc;
+    CK(launch_kdk(c, *p, dt_fixed, s));
+    return SPH_OK;
+}
+
+void step_done(Ctx &c, sph_status rc, bool timed)
+{
+    if (timed) {
+        c.stats.ms_build = elapsed(c.ev0, c.kev[0]);
+        c.stats.ms_walk = elapsed(c.kev[0], c.kev[1]) + elapsed(c.kev[3], c.kev[4]);
+        c.stats.ms_density_kernel = elapsed(c.kev[1], c.kev[2]);
+        c.stats.ms_force_kernel = elapsed(c.kev[4], c.kev[5]);
+        c.stats.ms_density = elapsed(c.kev[0], c.kev[3]);
+        c.stats.ms_forces = elapsed(c.kev[3], c.ev1);
+    }
+    density_stats(c);
+    force_stats(c);
+    c.cells_valid = c.density_valid = c.forces_valid = false;
+    if (rc == SPH_OK) {
+        c.rho_valid = true;
+        for (int k = 0; k < c.kp.ninst; ++k) c.dt_host[k] = c.dts_host[2 * k];
+        c.stats.dt_old = c.dt_host[0];
+    }
+}
+}  // namespace
+
 extern "C" sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_used,
                                void *stream)
 {
-    sph_status rc = sph_build_cells(ctx, p, stream);
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    sph_status rc = ensure_layout(c, p);
     if (rc) return rc;
-    rc = sph_density_h(ctx, p, nullptr, stream);
+    if (!(dt_fixed == dt_fixed) || std::isinf(dt_fixed))
+        return failf(c, SPH_ERR_ARG, "sph_step: dt_fixed must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->n == 0) {
+        if (dt_used) *dt_used = dt_fixed > 0 ? dt_fixed : 0.0;
+        return SPH_OK;
+    }
+    rc = begin(ctx, s);
     if (rc) return rc;
-    rc = sph_forces(ctx, p, stream);
+    rc = queue_step(c, p, dt_fixed, s, true);
     if (rc) return rc;
-    return sph_kdk_step(ctx, p, dt_fixed, dt_used, stream);
+    rc = finish(ctx, s);
+    step_done(c, rc, true);
+    if (rc == SPH_OK && dt_used) *dt_used = c.dt_host[0];
+    return rc;
+}
+
+extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double dt_fixed,
+                                        void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    sph_status rc = ensure_layout(c, p);
+    if (rc) return rc;
+    if (!stream) return failf(c, SPH_ERR_ARG, "sph_graph_capture needs a non-default stream");
+    if (p->n == 0) return failf(c, SPH_ERR_ARG, "sph_graph_capture needs particles");
+    if (!(dt_fixed == dt_fixed) || std::isinf(dt_fixed))
+        return failf(c, SPH_ERR_ARG, "sph_graph_capture: dt_fixed must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c.graph_exec = nullptr;
+    c.graph = nullptr;
+    const uint64_t l0 = c.launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    c.err.clear();
+    sph_status qrc = SPH_OK;
+    if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) qrc = SPH_ERR_CUDA;
+    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, false);
+    if (qrc == SPH_OK) qrc = queue_status(c, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    const uint64_t kernels = c.launches - l0;
+    c.launches = l0;
+    if (qrc != SPH_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return failf(c, SPH_ERR_CUDA, "stream capture of the step failed: %s",
+                     e != cudaSuccess ? cudaGetErrorString(e) : c.err.c_str());
+    }
+    c.graph = g;
+    CK(cudaGraphInstantiate(&c.graph_exec, g, 0));
+    c.graph_p = *p;
+    c.graph_dt = dt_fixed;
+    c.graph_kernels = kernels;
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!c.graph_exec) return failf(c, SPH_ERR_STATE, "no captured step: call sph_graph_capture");
+    cudaStream_t s = (cudaStream_t)stream;
+    c.err.clear();
+    CK(cudaEventRecord(c.ev0, s));
+    CK(cudaGraphLaunch(c.graph_exec, s));
+    CK(cudaEventRecord(c.ev1, s));
+    c.launches += c.graph_kernels;
+    sph_status rc = settle(ctx, s);
+    step_done(c, rc, false);
+    c.stats.ms_build = elapsed(c.ev0, c.ev1);  // the whole replay
+    c.stats.ms_density = c.stats.ms_forces = 0.f;
+    c.stats.ms_density_kernel = c.stats.ms_force_kernel = c.stats.ms_walk = 0.f;
+    if (rc == SPH_OK && dt_used) *dt_used = c.dt_host[0];
+    return rc;
 }
 
 namespace {
@@ -553,7 +799,7 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
     if (!particles_ok(hp) || hp->n > c.capacity)
         return failf(c, SPH_ERR_ARG, "sph_step_host: NULL array or n > capacity");
     cudaStream_t s = (cudaStream_t)stream;
-    size_t cap = (size_t)(c.capacity > 0 ? c.capacity : 1);
+    const size_t cap = (size_t)(c.capacity > 0 ? c.capacity : 1);
     if (!c.mirror) {
         size_t total = 0;
         for (const ArrDesc &d : kArrays) total += ((d.elem * cap + 255) / 256) * 256;
@@ -567,7 +813,7 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
     c.dmirror.n = hp->n;
     int64_t moved = 0;
     for (const ArrDesc &d : kArrays) {
-        size_t b = d.elem * (size_t)hp->n;
+        const size_t b = d.elem * (size_t)hp->n;
         CK(cudaMemcpyAsync(member(c.dmirror, d), member(*hp, d), b, cudaMemcpyHostToDevice, s));
         moved += (int64_t)b;
     }
@@ -575,7 +821,7 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
     sph_status rc = sph_step(ctx, &c.dmirror, dt_fixed, dt_used, stream);
     if (rc) return rc;
     for (const ArrDesc &d : kArrays) {
-        size_t b = d.elem * (size_t)hp->n;
+        const size_t b = d.elem * (size_t)hp->n;
         CK(cudaMemcpyAsync(member(*hp, d), member(c.dmirror, d), b, cudaMemcpyDeviceToHost, s));
     }
     if (d2h_bytes) *d2h_bytes = moved;
@@ -583,19 +829,23 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
     return SPH_OK;
 }
 
-extern "C" sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double out[9],
+extern "C" sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double *out,
                                            void *stream)
 {
     if (!ctx) return SPH_ERR_ARG;
     Ctx &c = ctx->c;
     if (!particles_ok(p) || !out) return failf(c, SPH_ERR_ARG, "sph_reduce_conserved: bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
-    sph_status rc = begin(ctx, s);
+    sph_status rc = ensure_layout(c, p);
     if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = begin(ctx, s);
+    if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
     CK(launch_conserved(c, *p, s));
-    CK(cudaMemcpyAsync(ctx->hbuf + 8, c.cons_out, 9 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    rc = finish(ctx, s, nullptr);
-    if (rc == SPH_OK) std::memcpy(out, ctx->hbuf + 8, 9 * sizeof(double));
+    CK(cudaMemcpyAsync(c.cons_host, c.cons_out, sizeof(double) * 9 * c.kp.ninst,
+                       cudaMemcpyDeviceToHost, s));
+    rc = finish(ctx, s);
+    if (rc == SPH_OK) std::memcpy(out, c.cons_host, sizeof(double) * 9 * c.kp.ninst);
     return rc;
 }
 
@@ -604,9 +854,17 @@ extern "C" sph_status sph_set_dt_old(sph_ctx *ctx, double dt_old)
     if (!ctx) return SPH_ERR_ARG;
     Ctx &c = ctx->c;
     if (!(dt_old >= 0.0) || std::isinf(dt_old)) return failf(c, SPH_ERR_ARG, "dt_old must be >= 0");
-    double v[2] = {dt_old, dt_old};
-    CK(cudaMemcpy(c.dts, v, sizeof v, cudaMemcpyHostToDevice));
+    std::vector<double> v(2 * (size_t)c.kp.ninst, dt_old);
+    CK(cudaMemcpy(c.dts, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+    for (double &d : c.dt_host) d = dt_old;
     c.stats.dt_old = dt_old;
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_batch_get_dt(const sph_ctx *ctx, double *out)
+{
+    if (!ctx || !out) return SPH_ERR_ARG;
+    std::memcpy(out, ctx->c.dt_host.data(), sizeof(double) * ctx->c.dt_host.size());
     return SPH_OK;
 }
 
@@ -623,4 +881,4 @@ extern "C" const char *sph_last_error(const sph_ctx *ctx)
     return ctx ? ctx->c.err.c_str() : "NULL context";
 }
 
-extern "C" const char *sph_version(void) { return "libsph 0.1 (sm_103a)"; }
+extern "C" const char *sph_version(void) { return "libsph 0.2 (sm_103a)"; }

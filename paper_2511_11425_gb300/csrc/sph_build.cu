@@ -4,21 +4,26 @@
 // range; Sec. 2.3.2 bounds every cell by the box of its particles (cell
 // bound) and the box of the particles' kernel balls (box-of-balls), merged
 // bottom-up, and finds interaction partners of a whole group at once by
-// overlap tests of those bounds.  Here the order is a 48-bit Morton order
-// (stable LSD radix sort), a bucket is 32 consecutive particles (one warp),
-// and the tree is an implicit complete binary tree over the buckets.
+// overlap tests of those bounds.  Here the order is a 30-bit Morton order per
+// instance (stable LSD radix sort of (instance, Morton) keys, so instances
+// keep their particle ranges), a bucket is up to 32 consecutive particles of
+// one instance (one warp), and each instance has an implicit complete binary
+// tree over its buckets.  Every phase is one launch over all instances.
 #include "sph_internal.cuh"
 
 namespace sph {
 
 // ---------------------------------------------------------------------------
-// bounding box of open axes (periodic axes use the box)
+// bounding boxes of open axes (periodic axes use the box); grid (chunks, ninst)
 // ---------------------------------------------------------------------------
-__global__ void k_bbox_partial(int n, const double *__restrict__ x, const double *__restrict__ y,
-                               const double *__restrict__ z, double *part)
+__global__ void k_bbox_partial(const Inst *__restrict__ insts, const double *__restrict__ x,
+                               const double *__restrict__ y, const double *__restrict__ z,
+                               double *part)
 {
+    const Inst &I = insts[blockIdx.y];
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = I.off + blockIdx.x * blockDim.x + threadIdx.x; i < I.off + I.n;
+         i += gridDim.x * blockDim.x) {
         double v[3] = {x[i], y[i], z[i]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -36,6 +41,7 @@ __global__ void k_bbox_partial(int n, const double *__restrict__ x, const double
     __syncthreads();
     if (threadIdx.x < 32) {
         int nw = blockDim.x >> 5;
+        double *out = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 6;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double a0 = lane < nw ? smn[a][lane] : INFINITY;
@@ -43,39 +49,41 @@ __global__ void k_bbox_partial(int n, const double *__restrict__ x, const double
             a0 = warp_min(a0);
             a1 = warp_max(a1);
             if (lane == 0) {
-                part[blockIdx.x * 6 + a] = a0;
-                part[blockIdx.x * 6 + 3 + a] = a1;
+                out[a] = a0;
+                out[3 + a] = a1;
             }
         }
     }
 }
 
-// morton_box = [lo0, lo1, lo2, scale0, scale1, scale2]: cell = (x - lo) * scale
-__global__ void k_bbox_final(KParams kp, int nparts, const double *part, double *morton_box,
-                             DevStatus *st)
+// morton_box per instance = [lo0, lo1, lo2, scale0, scale1, scale2]
+__global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const double *part,
+                             double *morton_box, DevStatus *st)
 {
-    if (threadIdx.x != 0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kp.ninst) return;
+    const Inst &I = insts[k];
     for (int a = 0; a < 3; ++a) {
         double lo, hi;
-        if (kp.periodic[a] || nparts == 0) {
-            lo = kp.lo[a];
-            hi = kp.hi[a];
+        if (I.periodic[a] || !kp.any_open || I.n == 0) {
+            lo = I.lo[a];
+            hi = I.hi[a];
         } else {
             lo = INFINITY;
             hi = -INFINITY;
-            for (int b = 0; b < nparts; ++b) {
-                lo = fmin(lo, part[b * 6 + a]);
-                hi = fmax(hi, part[b * 6 + 3 + a]);
+            for (int b = 0; b < kBboxChunks; ++b) {
+                lo = fmin(lo, part[((size_t)k * kBboxChunks + b) * 6 + a]);
+                hi = fmax(hi, part[((size_t)k * kBboxChunks + b) * 6 + 3 + a]);
             }
         }
         if (!isfinite(lo) || !isfinite(hi)) {
-            raise_status(st, ST_NONFINITE, a);
+            raise_status(st, ST_NONFINITE, k);
             lo = 0.0;
             hi = 1.0;
         }
         double ext = (hi - lo) * (1.0 + 1e-9) + 1e-300;
-        morton_box[a] = lo;
-        morton_box[3 + a] = (double)(1 << kMortonBits) / ext;
+        morton_box[k * 6 + a] = lo;
+        morton_box[k * 6 + 3 + a] = (double)(1 << kMortonBits) / ext;
     }
 }
 
@@ -90,32 +98,37 @@ __device__ __forceinline__ unsigned spread3(unsigned x)
     return x;
 }
 
-__global__ void k_morton(int n, const double *__restrict__ x, const double *__restrict__ y,
+// key = instance << 30 | Morton code in the instance's box
+__global__ void k_morton(int n, const unsigned short *__restrict__ pinst,
+                         const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, const double *__restrict__ mbox,
-                         unsigned *keys, unsigned int *vals)
+                         unsigned long long *keys, unsigned int *vals)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int k = pinst[i];
+    const double *mb = mbox + 6 * k;
     double v[3] = {x[i], y[i], z[i]};
     unsigned c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double t = (v[a] - mbox[a]) * mbox[3 + a];
+        double t = (v[a] - mb[a]) * mb[3 + a];
         t = fmin(fmax(t, 0.0), (double)((1 << kMortonBits) - 1));
         c[a] = (unsigned)t;
     }
-    keys[i] = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+    keys[i] = ((unsigned long long)k << 30) |
+              (unsigned long long)(spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
     vals[i] = (unsigned)i;
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort of 30-bit keys, 8-bit digits, tiles of 2048 keys
-// (256 threads x 8).  Per pass: tile histograms, a per-digit scan over the
-// tiles (one block per digit), and a stable scatter whose ranks come from
-// warp-level match_any in key order.
+// stable LSD radix sort of (instance, Morton) keys, 8-bit digits, tiles of
+// 2048 keys (256 threads x 8).  Per pass: tile histograms, a per-digit scan
+// over the tiles (one block per digit), and a stable scatter whose ranks
+// come from warp-level match_any in key order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sort_hist(const unsigned *__restrict__ keys, int n,
-                                                   int shift, unsigned *hist, int ntiles)
+__global__ void __launch_bounds__(256) k_sort_hist(const unsigned long long *__restrict__ keys,
+                                                   int n, int shift, unsigned *hist, int ntiles)
 {
     __shared__ unsigned h[256];
     h[threadIdx.x] = 0;
@@ -157,9 +170,9 @@ __global__ void __launch_bounds__(1024) k_sort_rowscan(unsigned *hist, int ntile
     if (t == 1023) tot[blockIdx.x] = part[1023];
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(const unsigned *__restrict__ kin,
+__global__ void __launch_bounds__(256) k_sort_scatter(const unsigned long long *__restrict__ kin,
                                                       const unsigned *__restrict__ vin,
-                                                      unsigned *__restrict__ kout,
+                                                      unsigned long long *__restrict__ kout,
                                                       unsigned *__restrict__ vout, int n,
                                                       int shift, const unsigned *__restrict__ hist,
                                                       const unsigned *__restrict__ tot, int ntiles)
@@ -181,16 +194,17 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const unsigned *__restrict
     toff[tid] = base_s[tid] - tot[tid] + hist[tid * ntiles + blockIdx.x];
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    unsigned key[kSortItems], val[kSortItems], rnk[kSortItems];
+    unsigned long long key[kSortItems];
+    unsigned val[kSortItems], rnk[kSortItems];
     const int per_warp = 32 * kSortItems;
     int base = blockIdx.x * kSortTile + w * per_warp;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         int i = base + r * 32 + lane;
         bool ok = i < n;
-        key[r] = ok ? kin[i] : 0u;
+        key[r] = ok ? kin[i] : 0ull;
         val[r] = ok ? vin[i] : 0u;
-        unsigned d = ok ? ((key[r] >> shift) & 255u) : 256u;
+        unsigned d = ok ? (unsigned)((key[r] >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(kFull, d);
         unsigned before = 0;
         if (ok) before = wcnt[w][d];
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const unsigned *__restrict
     for (int r = 0; r < kSortItems; ++r) {
         int i = base + r * 32 + lane;
         if (i < n) {
-            unsigned d = (key[r] >> shift) & 255u;
+            unsigned d = (unsigned)((key[r] >> shift) & 255u);
             unsigned pos = toff[d] + wcnt[w][d] + rnk[r];
             kout[pos] = key[r];
             vout[pos] = val[r];
@@ -271,7 +285,10 @@ __global__ void k_copyback_all(int n, PermFields pf, const char *tmp)
 // With update_pos = 0 only the box-of-balls is refreshed from the current h
 // (bounds update after the density pass, Sec. 2.3.3).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__restrict__ x,
+__global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restrict__ insts,
+                                                 const int *__restrict__ bstart,
+                                                 const int *__restrict__ binst,
+                                                 const double *__restrict__ x,
                                                  const double *__restrict__ y,
                                                  const double *__restrict__ z,
                                                  const float *__restrict__ m,
@@ -279,11 +296,13 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
                                                  float4 *pm, float4 *node, int update_pos,
                                                  DevStatus *st)
 {
-    int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (b >= kp.nb) return;
-    int i = b * kBucket + lane;
-    bool ok = i < kp.n;
+    const Inst &I = insts[binst[b]];
+    const int i0 = bstart[b];
+    const int i = i0 + lane;
+    const bool ok = lane < bucket_count(I, i0);
     float rel[3];
     double o[3];
     if (update_pos) {
@@ -293,14 +312,14 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
         for (int a = 0; a < 3; ++a) {
             double first = __shfl_sync(kFull, v[a], 0);
             double d = v[a] - first;
-            if (kp.periodic[a]) d -= kp.Ld[a] * rint(d * kp.invLd[a]);
+            if (I.periodic[a]) d -= I.Ld[a] * rint(d * I.invLd[a]);
             float mn = warp_min(ok ? (float)d : INFINITY);
-            double kd = floor((first + (double)mn) * kp.inv_q);
+            double kd = floor((first + (double)mn) * I.inv_q);
             if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
                 if (lane == 0) raise_status(st, ST_ARG, b);
                 kd = 0.0;
             }
-            o[a] = kd * kp.q;
+            o[a] = kd * I.q;
             rel[a] = (float)((first - o[a]) + d);
             if (lane == 0) origin[a * kp.nb + b] = (int)kd;
         }
@@ -313,9 +332,9 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
         float4 r = ok ? pm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         rel[0] = r.x; rel[1] = r.y; rel[2] = r.z;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) o[a] = (double)origin[a * kp.nb + b] * kp.q;
+        for (int a = 0; a < 3; ++a) o[a] = (double)origin[a * kp.nb + b] * I.q;
     }
-    float hi = ok ? h[i] : 0.f;
+    const float hi = ok ? h[i] : 0.f;
     if (ok && !(hi > 0.f && isfinite(hi))) raise_status(st, ST_NONFINITE, i);
     float bc[3], br[3], oc[3], orr[3];
 #pragma unroll
@@ -325,13 +344,13 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const double *__res
         // absolute centres (FP64 add of the origin, then one rounding) and
         // half widths inflated by the rounding allowance
         bc[a] = (float)(o[a] + 0.5 * ((double)mn + (double)mx));
-        br[a] = 0.5f * (mx - mn) + kp.eps_abs;
+        br[a] = 0.5f * (mx - mn) + I.eps_abs;
         oc[a] = (float)(o[a] + 0.5 * ((double)mnb + (double)mxb));
-        orr[a] = 0.5f * (mxb - mnb) + kp.eps_abs;
+        orr[a] = 0.5f * (mxb - mnb) + I.eps_abs;
     }
-    float hmax = warp_max(hi);
+    const float hmax = warp_max(hi);
     if (lane == 0) {
-        int k = kp.P + b;
+        const size_t k = (size_t)I.nbase + I.P + (b - I.boff);
         if (update_pos) {
             // .w of the cell half widths: the bucket's largest full extent
             float ext = 2.f * fmaxf(br[0], fmaxf(br[1], br[2]));
@@ -357,7 +376,7 @@ __device__ __forceinline__ void union1(float c1, float r1, float c2, float r2, b
     if (per && r >= 0.5f * L) r = L;  // covers the whole periodic axis
 }
 
-__device__ __forceinline__ void union_pair(const KParams &kp, const float4 *a, const float4 *b,
+__device__ __forceinline__ void union_pair(const Inst &I, const float4 *a, const float4 *b,
                                            float4 *out, int s)
 {
     float4 c1 = a[2 * s], r1 = a[2 * s + 1], c2 = b[2 * s], r2 = b[2 * s + 1];
@@ -366,62 +385,64 @@ __device__ __forceinline__ void union_pair(const KParams &kp, const float4 *a, c
     float a2[3] = {c2.x, c2.y, c2.z}, b2[3] = {r2.x, r2.y, r2.z};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
-        union1(a1[ax], b1[ax], a2[ax], b2[ax], kp.periodic[ax], kp.L[ax], kp.invL[ax], kp.eps_abs,
+        union1(a1[ax], b1[ax], a2[ax], b2[ax], I.periodic[ax], I.L[ax], I.invL[ax], I.eps_abs,
                cc[ax], rr[ax]);
     out[2 * s] = make_float4(cc[0], cc[1], cc[2], 0.f);
     out[2 * s + 1] = make_float4(rr[0], rr[1], rr[2], fmaxf(r1.w, r2.w));
 }
 
-// Bottom-up merge of the bounds (Sec. 2.3.2), `levels` tree levels per
-// launch: block b loads 2^levels consecutive nodes of level `lvl` into shared
-// memory and reduces them to one node of level lvl - levels.  Leaves of
-// padding buckets (b >= nb) are written empty on the first launch.
-__global__ void __launch_bounds__(256) k_tree_levels(KParams kp, float4 *node, int lvl, int levels,
-                                                     int bob_only)
+// Bottom-up merge of the bounds (Sec. 2.3.2).  Each block follows one entry
+// of the refit schedule: it loads 2^levels consecutive nodes of level `lvl`
+// of one instance's tree into shared memory and reduces them to one node of
+// level lvl - levels.  Leaves of padding buckets are written empty.
+__global__ void __launch_bounds__(256) k_tree_levels(const Inst *__restrict__ insts,
+                                                     const RefitBlock *__restrict__ sched,
+                                                     float4 *node, int bob_only)
 {
     __shared__ float4 sn[256][4];
-    const int width = 1 << levels;
+    const RefitBlock rb = sched[blockIdx.x];
+    const Inst &I = insts[rb.inst];
+    const int width = 1 << rb.levels;
     const int t = threadIdx.x;
-    const unsigned first = (1u << lvl) + (unsigned)blockIdx.x * width;
+    const unsigned first = (1u << rb.lvl) + (unsigned)rb.blk * width;
     if (t < width) {
-        unsigned k = first + t;
-        if (lvl == kp.logP && (int)(k - kp.P) >= kp.nb) {
+        const unsigned k = first + t;
+        float4 *nd = node + 4 * ((size_t)I.nbase + k);
+        if (rb.lvl == I.logP && (int)(k - I.P) >= I.nb) {
             float4 e = make_float4(0.f, 0.f, 0.f, 0.f), er = make_float4(-1.f, -1.f, -1.f, 0.f);
             sn[t][0] = e; sn[t][1] = er; sn[t][2] = e; sn[t][3] = er;
-            if (!bob_only) { node[4 * k] = e; node[4 * k + 1] = er; }
-            node[4 * k + 2] = e;
-            node[4 * k + 3] = er;
+            if (!bob_only) { nd[0] = e; nd[1] = er; }
+            nd[2] = e;
+            nd[3] = er;
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sn[t][q] = node[4 * k + q];
+            for (int q = 0; q < 4; ++q) sn[t][q] = nd[q];
         }
     }
     __syncthreads();
-    for (int l = 0; l < levels; ++l) {
-        int cnt = width >> (l + 1);
+    for (int l = 0; l < rb.levels; ++l) {
+        const int cnt = width >> (l + 1);
         float4 out[4];
         if (t < cnt) {
             out[0] = sn[2 * t][0];
             out[1] = sn[2 * t][1];
-            if (!bob_only) union_pair(kp, sn[2 * t], sn[2 * t + 1], out, 0);
-            union_pair(kp, sn[2 * t], sn[2 * t + 1], out, 1);
+            if (!bob_only) union_pair(I, sn[2 * t], sn[2 * t + 1], out, 0);
+            union_pair(I, sn[2 * t], sn[2 * t + 1], out, 1);
         }
         __syncthreads();
         if (t < cnt) {
-            unsigned k = ((first >> (l + 1)) + t);
+            const unsigned k = (first >> (l + 1)) + t;
+            float4 *nd = node + 4 * ((size_t)I.nbase + k);
             if (!bob_only) {
                 sn[t][0] = out[0];
                 sn[t][1] = out[1];
-                node[4 * k] = out[0];
-                node[4 * k + 1] = out[1];
-            } else {
-                sn[t][0] = node[4 * k];
-                sn[t][1] = node[4 * k + 1];
+                nd[0] = out[0];
+                nd[1] = out[1];
             }
             sn[t][2] = out[2];
             sn[t][3] = out[3];
-            node[4 * k + 2] = out[2];
-            node[4 * k + 3] = out[3];
+            nd[2] = out[2];
+            nd[3] = out[3];
         }
         __syncthreads();
     }
@@ -429,25 +450,20 @@ __global__ void __launch_bounds__(256) k_tree_levels(KParams kp, float4 *node, i
 
 static void tree_refit(Ctx &c, cudaStream_t s, int bob_only)
 {
-    const KParams &kp = c.kp;
-    int lvl = kp.logP;
-    if (lvl == 0) {
-        // single bucket: the leaf is the root
-        return;
-    }
-    while (lvl > 0) {
-        int levels = lvl < 8 ? lvl : 8;
-        int blocks = 1 << (lvl - levels);
-        k_tree_levels<<<blocks, 256, 0, s>>>(kp, c.node, lvl, levels, bob_only);
-        c.launches += 1;
-        lvl -= levels;
+    size_t off = 0;
+    for (int nblk : c.refit_band) {
+        if (nblk > 0) {
+            k_tree_levels<<<nblk, 256, 0, s>>>(c.inst, c.refit + off, c.node, bob_only);
+            c.launches += 1;
+        }
+        off += nblk;
     }
 }
 
 // ---------------------------------------------------------------------------
-// interaction-list walk (Sec. 2.3.2): one walk per GROUP of G = 8 consecutive
-// buckets (256 particles, the paper's GPU group size), breadth-first over the
-// implicit tree, 32 node tests per round.
+// interaction-list walk (Sec. 2.3.2): one walk per GROUP of up to 8
+// consecutive buckets (256 particles, the paper's GPU group size) of one
+// instance, breadth-first over that instance's tree, 32 node tests per round.
 //   density: source cell bound overlaps the group's box of balls of radius
 //            h_walk (1 + margin)                              (gather)
 //   force:   source cell bound overlaps the group box-of-balls (gather) OR
@@ -456,31 +472,38 @@ static void tree_refit(Ctx &c, cudaStream_t s, int bob_only)
 // The list holds source bucket ids; each sink bucket of the group filters it
 // against its own bounds inside the pair kernels.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4 *__restrict__ node,
+__global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict__ insts,
+                                              const int *__restrict__ gfirst,
+                                              const int *__restrict__ bstart,
+                                              const int *__restrict__ binst, int mode,
+                                              const float4 *__restrict__ node,
                                               const float4 *__restrict__ pm,
                                               const int *__restrict__ origin,
                                               const float *__restrict__ h_walk,
-                                              const unsigned *__restrict__ group_ids, int ngroups,
-                                              unsigned *list_start, unsigned *list_cnt,
-                                              unsigned *list, long long list_cap, DevStatus *st)
+                                              const unsigned *__restrict__ group_ids,
+                                              const unsigned *__restrict__ group_cnt,
+                                              unsigned *list, unsigned *list_cnt, DevStatus *st)
 {
     __shared__ unsigned buf[kWarpsPerBlock][2][kWalkCap];
-    int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int gi = blockIdx.x * kWarpsPerBlock + wib;
-    if (gi >= ngroups) return;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gi = blockIdx.x * kWarpsPerBlock + wib;
+    if (group_ids ? gi >= (int)*group_cnt : gi >= kp.ng) return;
     const int g = group_ids ? (int)group_ids[gi] : gi;
-    const int fb = g * kp.G;
+    const int fb = gfirst[g];
+    const Inst &I = insts[binst[fb]];
+    const int nbg = min(I.G, I.boff + I.nb - fb);
+    const int fl = fb - I.boff;  // local index of the group's first bucket
 
     // group bounds in absolute (unwrapped) f32 coordinates
     float gc[3], gr[3], sc[3], sr[3];  // gather box, group cell box
     if (mode == WALK_DENSITY) {
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int j = 0; j < kp.G; ++j) {
+        for (int j = 0; j < nbg; ++j) {
             const int b = fb + j;
-            if (b >= kp.nb) break;
-            const float3 off = origin_offset(kp, origin, fb, b);
-            const int i = b * kBucket + lane;
-            if (i < kp.n) {
+            const float3 off = origin_offset(I, kp.nb, origin, fb, b);
+            const int i0 = bstart[b];
+            if (lane < bucket_count(I, i0)) {
+                const int i = i0 + lane;
                 const float4 r = pm[i];
                 const float R = h_walk[i] * (1.f + kp.margin);
                 const float p[3] = {off.x + r.x, off.y + r.y, off.z + r.z};
@@ -494,14 +517,14 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float l = warp_min(lo[a]), h = warp_max(hi[a]);
-            double o = (double)origin[a * kp.nb + fb] * kp.q;
+            double o = (double)origin[a * kp.nb + fb] * I.q;
             gc[a] = (float)(o + 0.5 * ((double)l + (double)h));
-            gr[a] = 0.5f * (h - l) + 2.f * kp.eps_abs;
+            gr[a] = 0.5f * (h - l) + 2.f * I.eps_abs;
             sc[a] = gc[a];
             sr[a] = -1.f;
         }
     } else {
-        const int k = (kp.P >> kp.logG) + g;
+        const size_t k = (size_t)I.nbase + (I.P >> I.logG) + (fl >> I.logG);
         float4 b0 = node[4 * k], b1 = node[4 * k + 1], o0 = node[4 * k + 2], o1 = node[4 * k + 3];
         gc[0] = o0.x; gc[1] = o0.y; gc[2] = o0.z;
         gr[0] = o1.x; gr[1] = o1.y; gr[2] = o1.z;
@@ -509,52 +532,53 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
         sr[0] = b1.x; sr[1] = b1.y; sr[2] = b1.z;
     }
 
+    const float4 *tn = node + 4 * (size_t)I.nbase;  // this instance's tree
     unsigned *cur = buf[wib][0], *nxt = buf[wib][1];
-    int L0 = kp.logP < 5 ? kp.logP : 5;
+    const int L0 = I.logP < 5 ? I.logP : 5;
     int ncur = 1 << L0;
     for (int k = lane; k < ncur; k += 32) cur[k] = (1u << L0) + k;
     __syncwarp();
     bool overflow = false;
-    for (int lvl = L0; lvl <= kp.logP; ++lvl) {
-        bool leaf = lvl == kp.logP;
+    for (int lvl = L0; lvl <= I.logP; ++lvl) {
+        const bool leaf = lvl == I.logP;
         int nnext = 0;
         for (int base = 0; base < ncur; base += 32) {
-            int k = base + lane;
+            const int k = base + lane;
             bool acc = false;
             unsigned nd = 0;
             if (k < ncur) {
                 nd = cur[k];
-                float4 b0 = node[4 * nd], b1 = node[4 * nd + 1];
+                const float4 b0 = tn[4 * nd], b1 = tn[4 * nd + 1];
                 if (b1.x >= 0.f) {  // non-empty
-                    bool gth = ovl(gc[0], gr[0], b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                               ovl(gc[1], gr[1], b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                               ovl(gc[2], gr[2], b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                    bool gth = ovl(gc[0], gr[0], b0.x, b1.x, I.periodic[0], I.L[0], I.invL[0]) &&
+                               ovl(gc[1], gr[1], b0.y, b1.y, I.periodic[1], I.L[1], I.invL[1]) &&
+                               ovl(gc[2], gr[2], b0.z, b1.z, I.periodic[2], I.L[2], I.invL[2]);
                     if (mode == WALK_FORCE) {
                         // only subtrees holding buckets >= the group's first
-                        int shift = kp.logP - lvl;
-                        int last = (int)(((nd + 1u) << shift) - 1u) - kp.P;
-                        if (last < fb) {
+                        const int shift = I.logP - lvl;
+                        const int last = (int)(((nd + 1u) << shift) - 1u) - I.P;
+                        if (last < fl) {
                             gth = false;
                         } else if (!gth) {
-                            float4 o0 = node[4 * nd + 2], o1 = node[4 * nd + 3];
-                            gth = ovl(sc[0], sr[0], o0.x, o1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                                  ovl(sc[1], sr[1], o0.y, o1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                                  ovl(sc[2], sr[2], o0.z, o1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                            const float4 o0 = tn[4 * nd + 2], o1 = tn[4 * nd + 3];
+                            gth = ovl(sc[0], sr[0], o0.x, o1.x, I.periodic[0], I.L[0], I.invL[0]) &&
+                                  ovl(sc[1], sr[1], o0.y, o1.y, I.periodic[1], I.L[1], I.invL[1]) &&
+                                  ovl(sc[2], sr[2], o0.z, o1.z, I.periodic[2], I.L[2], I.invL[2]);
                         }
-                        if (leaf && (int)(nd - kp.P) < fb) gth = false;
+                        if (leaf && (int)(nd - I.P) < fl) gth = false;
                     }
                     acc = gth;
                 }
             }
-            unsigned bal = __ballot_sync(kFull, acc);
-            int per = leaf ? 1 : 2;
-            int pos = nnext + per * __popc(bal & ((1u << lane) - 1u));
-            int tot = nnext + per * __popc(bal);
+            const unsigned bal = __ballot_sync(kFull, acc);
+            const int per = leaf ? 1 : 2;
+            const int pos = nnext + per * __popc(bal & ((1u << lane) - 1u));
+            const int tot = nnext + per * __popc(bal);
             if (tot > kWalkCap) {
                 overflow = true;
             } else if (acc) {
                 if (leaf) {
-                    nxt[pos] = nd - (unsigned)kp.P;
+                    nxt[pos] = (unsigned)I.boff + (nd - (unsigned)I.P);  // global bucket id
                 } else {
                     nxt[pos] = 2u * nd;
                     nxt[pos + 1] = 2u * nd + 1u;
@@ -573,17 +597,9 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
         if (lane == 0) raise_status(st, ST_CAPACITY, g);
         ncur = 0;
     }
-    // cur holds the accepted bucket ids; allocate and write them
-    unsigned start = 0;
-    if (lane == 0) start = atomicAdd(&st->list_need, (unsigned)ncur);
-    start = __shfl_sync(kFull, start, 0);
-    bool fits = (long long)start + ncur <= list_cap;
-    if (lane == 0) {
-        list_start[g] = start;
-        list_cnt[g] = fits ? (unsigned)ncur : 0u;
-    }
-    if (!fits) return;
-    for (int k = lane; k < ncur; k += 32) list[start + k] = cur[k];
+    unsigned *out = list + (size_t)g * kWalkCap;
+    for (int k = lane; k < ncur; k += 32) out[k] = cur[k];
+    if (lane == 0) list_cnt[g] = (unsigned)ncur;
 }
 
 // ---------------------------------------------------------------------------
@@ -592,20 +608,22 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, int mode, const float4
 cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;
-    int n = (int)p.n;
-    // bounding box for the Morton quantisation (only open axes need data)
-    int nbb = (kp.periodic[0] && kp.periodic[1] && kp.periodic[2]) ? 0 : 152;
-    if (nbb) {
-        k_bbox_partial<<<nbb, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.bbox_part);
+    const int n = (int)p.n;
+    // bounding boxes for the Morton quantisation (only open axes need data)
+    if (kp.any_open) {
+        k_bbox_partial<<<dim3(kBboxChunks, kp.ninst), 256, 0, s>>>(c.inst, p.x[0], p.x[1], p.x[2],
+                                                                 c.bbox_part);
         c.launches += 1;
     }
-    k_bbox_final<<<1, 32, 0, s>>>(kp, nbb, c.bbox_part, c.morton_box, c.st);
-    int g = (n + 255) / 256;
-    k_morton<<<g, 256, 0, s>>>(n, p.x[0], p.x[1], p.x[2], c.morton_box, c.keys[0], c.vals[0]);
-    int ntiles = (n + kSortTile - 1) / kSortTile;
+    k_bbox_final<<<(kp.ninst + 127) / 128, 128, 0, s>>>(kp, c.inst, c.bbox_part, c.morton_box,
+                                                        c.st);
+    const int g = (n + 255) / 256;
+    k_morton<<<g, 256, 0, s>>>(n, c.pinst, p.x[0], p.x[1], p.x[2], c.morton_box, c.keys[0],
+                               c.vals[0]);
+    const int ntiles = (n + kSortTile - 1) / kSortTile;
     int cur = 0;
-    for (int pass = 0; pass < kSortPasses; ++pass) {
-        int shift = 8 * pass;
+    for (int pass = 0; pass < kp.key_passes; ++pass) {
+        const int shift = 8 * pass;
         k_sort_hist<<<ntiles, 256, 0, s>>>(c.keys[cur], n, shift, c.hist, ntiles);
         k_sort_rowscan<<<256, 1024, 0, s>>>(c.hist, ntiles, c.digit_tot);
         k_sort_scatter<<<ntiles, 256, 0, s>>>(c.keys[cur], c.vals[cur], c.keys[cur ^ 1],
@@ -627,11 +645,11 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     pf.f1 = p.iters;
     k_gather_all<<<g, 256, 0, s>>>(perm, n, pf, (char *)c.tmp);
     k_copyback_all<<<g, 256, 0, s>>>(n, pf, (const char *)c.tmp);
-    // buckets and tree
-    int wb = (kp.nb * 32 + 127) / 128;
-    k_buckets<<<wb, 128, 0, s>>>(kp, p.x[0], p.x[1], p.x[2], p.m, p.h, c.origin, c.pm, c.node, 1,
-                                 c.st);
-    c.launches += 2 + 3 * kSortPasses + 2 + 1;
+    // buckets and trees
+    const int wb = (kp.nb * 32 + 127) / 128;
+    k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
+                                 c.origin, c.pm, c.node, 1, c.st);
+    c.launches += 2 + 3 * kp.key_passes + 2 + 1;
     tree_refit(c, s, 0);
     return cudaGetLastError();
 }
@@ -639,24 +657,27 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
 cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;
-    int wb = (kp.nb * 32 + 127) / 128;
+    const int wb = (kp.nb * 32 + 127) / 128;
     c.launches += 1;
-    k_buckets<<<wb, 128, 0, s>>>(kp, p.x[0], p.x[1], p.x[2], p.m, p.h, c.origin, c.pm, c.node, 0,
-                                 c.st);
+    k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
+                                 c.origin, c.pm, c.node, 0, c.st);
     tree_refit(c, s, 1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned *group_ids,
-                        int ngroups, const float *h_walk, cudaStream_t s)
+cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, const float *h_walk,
+                        cudaStream_t s)
 {
     (void)p;
-    if (ngroups <= 0) return cudaSuccess;
-    int g = (ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const KParams &kp = c.kp;
+    if (kp.ng <= 0) return cudaSuccess;
+    const unsigned *ids = round < 0 ? nullptr : c.redo + (size_t)round * kp.ng;
+    const unsigned *cnt = round < 0 ? nullptr : &c.st->redo_cnt[round];
+    const int g = (kp.ng + kWarpsPerBlock - 1) / kWarpsPerBlock;
     c.launches += 1;
-    k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, mode, c.node, c.pm, c.origin, h_walk, group_ids,
-                                             ngroups, c.list_start, c.list_cnt, c.list,
-                                             (long long)c.list_cap, c.st);
+    k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(kp, c.inst, c.gfirst, c.bstart, c.binst, mode, c.node,
+                                             c.pm, c.origin, h_walk, ids, cnt, c.list, c.list_cnt,
+                                             c.st);
     return cudaGetLastError();
 }
 

@@ -27,13 +27,13 @@ namespace sph {
 constexpr float kFourPiThird = 4.18879020478639098f;
 
 template <bool WRAP>
-__device__ __forceinline__ float sep2(const KParams &kp, float px, float py, float pz, float4 q)
+__device__ __forceinline__ float sep2(const PBox &bx, float px, float py, float pz, float4 q)
 {
     float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
     if (WRAP) {
-        if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-        if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-        if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+        if (bx.per[0]) dx = wrapf(dx, bx.L[0], bx.invL[0]);
+        if (bx.per[1]) dy = wrapf(dy, bx.L[1], bx.invL[1]);
+        if (bx.per[2]) dz = wrapf(dz, bx.L[2], bx.invL[2]);
     }
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
@@ -43,7 +43,7 @@ __device__ __forceinline__ float sep2(const KParams &kp, float px, float py, flo
 // positions to a multiple of 32, so the fully unrolled inner loop needs no
 // bounds checks and every bit is set with an immediate mask.
 template <bool WRAP>
-__device__ __forceinline__ void hit_masks(const KParams &kp, const float4 *cand, int nwords,
+__device__ __forceinline__ void hit_masks(const PBox &bx, const float4 *cand, int nwords,
                                           float px, float py, float pz, float h2, bool active,
                                           unsigned long long &m0, unsigned long long &m1)
 {
@@ -54,7 +54,7 @@ __device__ __forceinline__ void hit_masks(const KParams &kp, const float4 *cand,
             unsigned mw = 0u;
 #pragma unroll
             for (int b = 0; b < 32; ++b) {
-                float r2 = sep2<WRAP>(kp, px, py, pz, cand[32 * ww + b]);
+                float r2 = sep2<WRAP>(bx, px, py, pz, cand[32 * ww + b]);
                 mw |= r2 < h2 ? (1u << b) : 0u;
             }
             if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
@@ -78,7 +78,7 @@ __device__ __forceinline__ int next_hit(unsigned long long &m0, unsigned long lo
 }
 
 template <class K, bool WRAP, bool EMIT>
-__device__ __forceinline__ void density_chunk(const KParams &kp, float4 *cand, const int *candj,
+__device__ __forceinline__ void density_chunk(const PBox &bx, float4 *cand, const int *candj,
                                               int c, int lane, float px, float py, float pz,
                                               float h2, float ih, bool active, Kahan &Sw,
                                               Kahan &Sq, int &cnt, int i, long long cap,
@@ -90,13 +90,13 @@ __device__ __forceinline__ void density_chunk(const KParams &kp, float4 *cand, c
         cand[k] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
     __syncwarp();
     unsigned long long m0, m1;
-    hit_masks<WRAP>(kp, cand, nwords, px, py, pz, h2, active, m0, m1);
+    hit_masks<WRAP>(bx, cand, nwords, px, py, pz, h2, active, m0, m1);
     float sw = 0.f, sq = 0.f;
     int nh = 0;
     while (m0 | m1) {
         const int k = next_hit(m0, m1);
         const float4 q = cand[k];
-        const float r2 = sep2<WRAP>(kp, px, py, pz, q);
+        const float r2 = sep2<WRAP>(bx, px, py, pz, q);
         const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
         const float qq = r * ih;
         const float wv = K::w(qq), dq = K::dwq(qq);
@@ -118,16 +118,18 @@ __device__ __forceinline__ void density_chunk(const KParams &kp, float4 *cand, c
 
 template <class K, bool WRAP, bool EMIT>
 __device__ __forceinline__ void density_bucket(
-    const KParams &kp, int A, int lane, float4 *cand, int *candj, const float4 *__restrict__ pm,
-    const unsigned *__restrict__ list_start, const unsigned *__restrict__ list_cnt,
-    const unsigned *__restrict__ list, const int *__restrict__ origin,
-    const float4 *__restrict__ node, float *h_seed, float *h_out, float *rho_out,
-    float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap,
-    uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in, unsigned *redo_out,
-    unsigned *gflag, DevStatus *st, float4 me, bool valid, const float *cen)
+    const KParams &kp, const Inst &I, const PBox &bx, int A, int i0, int lane, float4 *cand,
+    int *candj, const float4 *__restrict__ pm, const int *__restrict__ bstart,
+    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list,
+    const int *__restrict__ origin, const float4 *__restrict__ node, float *h_seed, float *h_out,
+    float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
+    long long cap, uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
+    unsigned *redo_out, unsigned *redo_cnt_out, unsigned *gflag, DevStatus *st, float4 me,
+    bool valid, const float *cen)
 {
     const unsigned lt = (1u << lane) - 1u;
-    int i = A * kBucket + lane;
+    const int i = i0 + lane;
+    const float n_ngb = I.n_ngb, eps_abs = I.eps_abs;
     float h = valid ? h_seed[i] : 1.f;
     const float R = h * (1.f + kp.margin);  // radius the list was gathered with
     float lo = 0.f, hi = INFINITY;
@@ -139,8 +141,8 @@ __device__ __forceinline__ void density_bucket(
     const float p[3] = {me.x, me.y, me.z};
     // Filter the group's list against this bucket's coverage box of balls
     // (radius R): lane w keeps the acceptance bits of entries 32w .. 32w+31.
-    const int g = A >> kp.logG;
-    const unsigned s0 = list_start[g], nl = list_cnt[g];
+    const int g = group_of(I, A);
+    const unsigned s0 = (unsigned)g * kWalkCap, nl = list_cnt[g];
     unsigned myword = 0u;
     {
         float cc[3], cr[3];
@@ -148,19 +150,19 @@ __device__ __forceinline__ void density_bucket(
         for (int a = 0; a < 3; ++a) {
             float lo = warp_min(valid ? p[a] - R : INFINITY);
             float hi = warp_max(valid ? p[a] + R : -INFINITY);
-            double o = (double)origin[a * kp.nb + A] * kp.q;
+            double o = (double)origin[a * kp.nb + A] * I.q;
             cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
-            cr[a] = 0.5f * (hi - lo) + 2.f * kp.eps_abs;
+            cr[a] = 0.5f * (hi - lo) + 2.f * eps_abs;
         }
         for (unsigned w = 0; 32 * w < nl; ++w) {
             const unsigned e = 32 * w + lane;
             bool acc = false;
             if (e < nl) {
-                const unsigned k = (unsigned)kp.P + list[s0 + e];
+                const size_t k = leaf_of(I, (int)list[s0 + e]);
                 const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
-                acc = ovl(cc[0], cr[0], b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                      ovl(cc[1], cr[1], b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                      ovl(cc[2], cr[2], b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                acc = ovl(cc[0], cr[0], b0.x, b1.x, bx.per[0], bx.L[0], bx.invL[0]) &&
+                      ovl(cc[1], cr[1], b0.y, b1.y, bx.per[1], bx.L[1], bx.invL[1]) &&
+                      ovl(cc[2], cr[2], b0.z, b1.z, bx.per[2], bx.L[2], bx.invL[2]);
             }
             const unsigned bal = __ballot_sync(kFull, acc);
             if (lane == (int)w) myword = bal;
@@ -185,7 +187,7 @@ __device__ __forceinline__ void density_bucket(
         {
             float dx = p[0] - bc[0], dy = p[1] - bc[1], dz = p[2] - bc[2];
             float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + h;
-            rr = warp_max(rr) * (1.f + 1e-6f) + kp.eps_abs;
+            rr = warp_max(rr) * (1.f + 1e-6f) + eps_abs;
             bb2 = rr * rr;
         }
         Kahan Sw, Sq;
@@ -196,9 +198,10 @@ __device__ __forceinline__ void density_bucket(
             const unsigned e = 32 * w + __ffs(mw) - 1;
             mw &= mw - 1u;
             const int B = (int)list[s0 + e];
-            const float3 off = origin_offset(kp, origin, A, B);
-            int j = B * kBucket + lane;
-            bool vj = j < kp.n;
+            const float3 off = origin_offset(I, kp.nb, origin, A, B);
+            const int j0 = bstart[B];
+            const int j = j0 + lane;
+            const bool vj = lane < bucket_count(I, j0);
             float4 s = vj ? pm[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             float sp[3] = {off.x + s.x, off.y + s.y, off.z + s.z};
             bool in = vj;
@@ -206,9 +209,9 @@ __device__ __forceinline__ void density_bucket(
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float d = sp[a] - bc[a];
-                if (WRAP && kp.periodic[a]) {
-                    sp[a] -= kp.L[a] * rintf((sp[a] - cen[a]) * kp.invL[a]);
-                    d = wrapf(d, kp.L[a], kp.invL[a]);
+                if (WRAP && bx.per[a]) {
+                    sp[a] -= bx.L[a] * rintf((sp[a] - cen[a]) * bx.invL[a]);
+                    d = wrapf(d, bx.L[a], bx.invL[a]);
                 }
                 in = in && fabsf(d) <= br[a];
                 dd2 = fmaf(d, d, dd2);
@@ -224,7 +227,7 @@ __device__ __forceinline__ void density_bucket(
             if (c > kChunk - 32) {
                 __syncwarp();
                 if (!done) cands += c;
-                density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
+                density_chunk<K, WRAP, EMIT>(bx, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
                                              !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
                 __syncwarp();
                 c = 0;
@@ -234,7 +237,7 @@ __device__ __forceinline__ void density_bucket(
         if (c > 0) {
             __syncwarp();
             if (!done) cands += c;
-            density_chunk<K, WRAP, EMIT>(kp, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
+            density_chunk<K, WRAP, EMIT>(bx, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
                                          !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
             __syncwarp();
         }
@@ -245,7 +248,7 @@ __device__ __forceinline__ void density_bucket(
             pairs += (unsigned long long)(nn > 0 ? nn : 0);
             bool record = fixed_h != 0;
             if (!record) {
-                float g = kFourPiThird * K::sigma * swv / me.w - kp.n_ngb;
+                float g = kFourPiThird * K::sigma * swv / me.w - n_ngb;
                 float dg = -kFourPiThird * K::sigma * sqv / (me.w * h);
                 if (g < 0.f) lo = h; else hi = h;
                 float hn = dg > 0.f ? h - g / dg : NAN;
@@ -281,7 +284,7 @@ __device__ __forceinline__ void density_bucket(
                 out_n = nn;
                 if (!(isfinite(out_rho) && isfinite(out_om) && out_rho > 0.f))
                     raise_status(st, ST_NONFINITE, i);
-                if (h >= kp.hcap) raise_status(st, ST_ARG, i);
+                if (h >= I.hcap) raise_status(st, ST_ARG, i);
             }
         }
     }
@@ -290,8 +293,12 @@ __device__ __forceinline__ void density_bucket(
     if (any_relist) {
         if (valid) h_seed[i] = relist ? out_h : (conv ? out_h : h);
         if (lane == 0 && atomicOr(&gflag[g], 1u) == 0u) {
-            unsigned pos = atomicAdd(&st->redo_count, 1u);
-            redo_out[pos] = (unsigned)g;
+            if (redo_out) {
+                unsigned pos = atomicAdd(redo_cnt_out, 1u);
+                redo_out[pos] = (unsigned)g;
+            } else {
+                raise_status(st, ST_NOCONV, i);  // no re-walk round left
+            }
         }
     } else if (valid && conv) {
         h_out[i] = out_h;
@@ -312,24 +319,40 @@ __device__ __forceinline__ void density_bucket(
 
 template <class K, bool EMIT>
 __global__ void __launch_bounds__(128) k_density(
-    KParams kp, const float4 *__restrict__ pm, const unsigned *__restrict__ list_start,
-    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list,
-    const int *__restrict__ origin, const unsigned *__restrict__ group_ids, int nbuckets,
+    KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
+    const int *__restrict__ bstart, const int *__restrict__ binst,
+    const int *__restrict__ gfirst, const unsigned *__restrict__ list_cnt,
+    const unsigned *__restrict__ list, const int *__restrict__ origin,
+    const unsigned *__restrict__ group_ids, const unsigned *__restrict__ group_cnt,
     float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
     uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out, int64_t *ids_out,
-    const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *gflag,
-    const float4 *__restrict__ node, DevStatus *st)
+    const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *redo_cnt_out,
+    unsigned *gflag, const float4 *__restrict__ node, DevStatus *st)
 {
     __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bi = blockIdx.x * kWarpsPerBlock + wib;
-    if (bi >= nbuckets) return;
-    // all buckets, or every bucket of the listed groups (re-walk passes)
-    const int A = group_ids ? (int)group_ids[bi >> kp.logG] * kp.G + (bi & (kp.G - 1)) : bi;
-    if (A >= kp.nb) return;
-    const int i = A * kBucket + lane;
-    const bool valid = i < kp.n;
+    // all buckets, or the buckets of the groups queued for this re-walk round
+    // (8 warp slots per queued group)
+    int A;
+    if (group_ids) {
+        const int gi = bi >> kGroupLog;
+        if (gi >= (int)*group_cnt) return;
+        const int fb = gfirst[group_ids[gi]];
+        const Inst &Ig = insts[binst[fb]];
+        const int j = bi & ((1 << kGroupLog) - 1);
+        if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) return;
+        A = fb + j;
+    } else {
+        if (bi >= kp.nb) return;
+        A = bi;
+    }
+    const Inst &I = insts[binst[A]];
+    const PBox bx = make_pbox(I);
+    const int i0 = bstart[A];
+    const int i = i0 + lane;
+    const bool valid = lane < bucket_count(I, i0);
     const float4 me = valid ? pm[i] : make_float4(0.f, 0.f, 0.f, 1.f);
     // sink centre (periodic images are chosen nearest to it) and whether
     // pair separations need their own minimum-image wrap
@@ -337,62 +360,70 @@ __global__ void __launch_bounds__(128) k_density(
     bool wrap = false;
     {
         const float R = valid ? h_seed[i] * (1.f + kp.margin) : 0.f;
-        const float Rm = warp_max(R) + node[4 * 1 + 1].w;  // + largest bucket extent
+        const float Rm = warp_max(R) + node[4 * ((size_t)I.nbase + 1) + 1].w;  // + largest bucket extent
         const float p[3] = {me.x, me.y, me.z};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float mn = warp_min(valid ? p[a] : INFINITY), mx = warp_max(valid ? p[a] : -INFINITY);
             cen[a] = 0.5f * (mn + mx);
-            if (kp.periodic[a] && (mx - mn) + Rm > 0.49f * kp.L[a]) wrap = true;
+            if (bx.per[a] && (mx - mn) + Rm > 0.49f * bx.L[a]) wrap = true;
         }
     }
     float4 *cand = cand_s[wib];
     int *candj = EMIT ? candj_s[wib] : nullptr;
     if (wrap)
-        density_bucket<K, true, EMIT>(kp, A, lane, cand, candj, pm, list_start, list_cnt, list,
-                                      origin, node,
-                                      h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
-                                      fixed_h, cap, count_out, ids_out, id_in, redo_out, gflag, st, me,
-                                      valid, cen);
+        density_bucket<K, true, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
+                                      list, origin, node, h_seed, h_out, rho_out, omega_out,
+                                      nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
+                                      redo_out, redo_cnt_out, gflag, st, me, valid, cen);
     else
-        density_bucket<K, false, EMIT>(kp, A, lane, cand, candj, pm, list_start, list_cnt, list,
-                                      origin, node,
-                                       h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
-                                       fixed_h, cap, count_out, ids_out, id_in, redo_out, gflag, st, me,
-                                       valid, cen);
+        density_bucket<K, false, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
+                                       list, origin, node, h_seed, h_out, rho_out, omega_out,
+                                       nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
+                                       redo_out, redo_cnt_out, gflag, st, me, valid, cen);
 }
 
-__global__ void k_isentropic(int n, double g1, const float *__restrict__ rho,
-                             const float *__restrict__ rho_old, double *u)
+__global__ void k_isentropic(int n, const Inst *__restrict__ insts,
+                             const unsigned short *__restrict__ pinst,
+                             const float *__restrict__ rho, const float *__restrict__ rho_old,
+                             double *u)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float ro = rho_old[i];
+    const double g1 = (double)insts[pinst[i]].gamma - 1.0;
     if (ro > 0.f) u[i] *= pow((double)rho[i] / (double)ro, g1);
 }
 
-cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed,
-                           const unsigned *group_ids, int ngroups, int fixed_h, int64_t cap,
-                           uint32_t *count, int64_t *ids, cudaStream_t s)
+cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, int round,
+                           int fixed_h, int64_t cap, uint32_t *count, int64_t *ids,
+                           cudaStream_t s)
 {
-    if (ngroups <= 0) return cudaSuccess;
-    int nbuckets = group_ids ? ngroups * c.kp.G : c.kp.nb;
-    int g = (nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    bool emit = ids != nullptr || count != nullptr;
-    unsigned *redo_out = c.redo + (group_ids == c.redo ? c.nb_cap : 0);
-    cudaMemsetAsync(c.gflag, 0, sizeof(unsigned) * (size_t)c.kp.ng, s);
+    const KParams &kp = c.kp;
+    if (kp.nb <= 0) return cudaSuccess;
+    // round < 0: every bucket, queueing re-walks for round 0; round r: the
+    // buckets of the groups queued for round r, queueing for round r + 1
+    const int slots = round < 0 ? kp.nb : kp.ng << kGroupLog;
+    const int g = (slots + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const bool emit = ids != nullptr || count != nullptr;
+    const unsigned *gids = round < 0 ? nullptr : c.redo + (size_t)round * kp.ng;
+    const unsigned *gcnt = round < 0 ? nullptr : &c.st->redo_cnt[round];
+    const int next = round + 1;
+    unsigned *redo_out = next < kRelistRounds ? c.redo + (size_t)next * kp.ng : nullptr;
+    unsigned *redo_cnt_out = next < kRelistRounds ? &c.st->redo_cnt[next] : nullptr;
+    cudaMemsetAsync(c.gflag, 0, sizeof(unsigned) * (size_t)kp.ng, s);
     c.launches += 1;
-    SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
+    SPH_KERNEL_DISPATCH(kp.kernel, KT,
         if (emit)
             k_density<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                c.kp, c.pm, c.list_start, c.list_cnt, c.list, c.origin, group_ids, nbuckets,
-                (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
-                count, ids, p.id, redo_out, c.gflag, c.node, c.st);
+                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list, c.origin, gids,
+                gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,
+                (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st);
         else
             k_density<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                c.kp, c.pm, c.list_start, c.list_cnt, c.list, c.origin, group_ids, nbuckets,
-                (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h, (long long)cap,
-                count, ids, p.id, redo_out, c.gflag, c.node, c.st);
+                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list, c.origin, gids,
+                gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,
+                (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st);
     )
     return cudaGetLastError();
 }
@@ -401,7 +432,7 @@ cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     int n = (int)p.n;
     c.launches += 1;
-    k_isentropic<<<(n + 255) / 256, 256, 0, s>>>(n, c.prm.gamma - 1.0, p.rho, c.rho_old, p.u);
+    k_isentropic<<<(n + 255) / 256, 256, 0, s>>>(n, c.inst, c.pinst, p.rho, c.rho_old, p.u);
     return cudaGetLastError();
 }
 

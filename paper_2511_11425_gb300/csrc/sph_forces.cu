@@ -32,7 +32,8 @@ namespace sph {
 // ---------------------------------------------------------------------------
 // predictor + EOS (Sec. 2.3.6 step 2, Sec. 2.3.1)
 // ---------------------------------------------------------------------------
-__global__ void k_predict(KParams kp, int n, const double *__restrict__ vx,
+__global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
+                          const unsigned short *__restrict__ pinst, const double *__restrict__ vx,
                           const double *__restrict__ vy, const double *__restrict__ vz,
                           const double *__restrict__ u, const float *__restrict__ ax,
                           const float *__restrict__ ay, const float *__restrict__ az,
@@ -43,9 +44,11 @@ __global__ void k_predict(KParams kp, int n, const double *__restrict__ vx,
                           float4 *acc, float2 *acc2, unsigned *dtmin, DevStatus *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) *dtmin = 0x7f800000u;  // +inf
+    if (i < kp.ninst) dtmin[i] = 0x7f800000u;  // +inf
     if (i >= n) return;
-    const double hdt = 0.5 * dts[0];
+    const int k = pinst[i];
+    const float gamma = insts[k].gamma;
+    const double hdt = 0.5 * dts[2 * k];
     double v[3] = {vx[i], vy[i], vz[i]};
     double uu = u[i];
     if (hdt > 0.0) {
@@ -57,8 +60,8 @@ __global__ void k_predict(KParams kp, int n, const double *__restrict__ vx,
         uu += hdt * ud;
     }
     float r = rho[i], om = omega[i], hi = h[i];
-    float P = (kp.gamma - 1.f) * r * (float)uu;
-    float c = sqrtf(kp.gamma * P / r);
+    float P = (gamma - 1.f) * r * (float)uu;
+    float c = sqrtf(gamma * P / r);
     float A = P / (om * r * r);
     if (!(isfinite(A) && isfinite(c) && uu >= 0.0)) raise_status(st, ST_NONFINITE, i);
     float4 q = pm[i];
@@ -91,22 +94,28 @@ struct ForceStage {
 };
 
 template <bool WRAP>
-__device__ __forceinline__ void sep3(const KParams &kp, float px, float py, float pz, float4 q,
+__device__ __forceinline__ void sep3(const PBox &bx, float px, float py, float pz, float4 q,
                                      float &dx, float &dy, float &dz)
 {
     dx = px - q.x;
     dy = py - q.y;
     dz = pz - q.z;
     if (WRAP) {
-        if (kp.periodic[0]) dx = wrapf(dx, kp.L[0], kp.invL[0]);
-        if (kp.periodic[1]) dy = wrapf(dy, kp.L[1], kp.invL[1]);
-        if (kp.periodic[2]) dz = wrapf(dz, kp.L[2], kp.invL[2]);
+        if (bx.per[0]) dx = wrapf(dx, bx.L[0], bx.invL[0]);
+        if (bx.per[1]) dy = wrapf(dy, bx.L[1], bx.invL[1]);
+        if (bx.per[2]) dz = wrapf(dz, bx.L[2], bx.invL[2]);
     }
 }
 
+// viscosity parameters of the sink's instance
+struct Visc {
+    float alpha, beta, eps_av;
+};
+
 template <class K, bool WRAP>
-__device__ __forceinline__ void force_chunk(const KParams &kp, ForceStage &S, int c, SinkState &s,
-                                            bool valid, int lane, float4 *acc, float2 *acc2)
+__device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, ForceStage &S, int c,
+                                            SinkState &s, bool valid, int lane, float4 *acc,
+                                            float2 *acc2)
 {
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32) {
@@ -124,7 +133,7 @@ __device__ __forceinline__ void force_chunk(const KParams &kp, ForceStage &S, in
             for (int b = 0; b < 32; ++b) {
                 const float4 q = S.pos[32 * ww + b];
                 float dx, dy, dz;
-                sep3<WRAP>(kp, s.px, s.py, s.pz, q, dx, dy, dz);
+                sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 bool hit = r2 < fmaxf(s.h2, q.w * q.w) && S.idx[32 * ww + b] > s.i;
                 mw |= hit ? (1u << b) : 0u;
@@ -148,7 +157,7 @@ __device__ __forceinline__ void force_chunk(const KParams &kp, ForceStage &S, in
         const float4 vj = S.vel[k];
         const float4 tj = S.th[k];
         float dx, dy, dz;
-        sep3<WRAP>(kp, s.px, s.py, s.pz, q, dx, dy, dz);
+        sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
         const float hj = q.w, ihj = __frcp_rn(hj);
@@ -161,8 +170,8 @@ __device__ __forceinline__ void force_chunk(const KParams &kp, ForceStage &S, in
         // viscosity, evaluated for every pair and switched by v_ij.r_ij < 0
         const bool app = vr < 0.f;
         const float hb = 0.5f * (s.h + hj), cb = 0.5f * (s.c + tj.y), rb = 0.5f * (s.rho + tj.z);
-        const float mu = __fdividef(hb * vr, fmaf(kp.eps_av * hb, hb, r2));
-        const float Pi = app ? __fdividef(fmaf(-kp.alpha * cb, mu, kp.beta * mu * mu), rb) : 0.f;
+        const float mu = __fdividef(hb * vr, fmaf(vp.eps_av * hb, hb, r2));
+        const float Pi = app ? __fdividef(fmaf(-vp.alpha * cb, mu, vp.beta * mu * mu), rb) : 0.f;
         const float Fb = 0.5f * (Fi + Fj);
         const float coef = fmaf(s.A, Fi, fmaf(tj.x, Fj, Pi * Fb));
         const float du = 0.5f * Pi * vr * Fb;
@@ -199,12 +208,13 @@ struct SinkBounds {
 };
 
 template <class K, bool WRAP>
-__device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane, ForceStage &S,
+__device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, const PBox &bx,
+                                             const Visc &vp, int A, int lane, ForceStage &S,
                                              SinkState &s, bool valid, const SinkBounds sb,
+                                             const int *__restrict__ bstart,
                                              const float4 *__restrict__ fpos,
                                              const float4 *__restrict__ fvel,
                                              const float4 *__restrict__ fth,
-                                             const unsigned *__restrict__ list_start,
                                              const unsigned *__restrict__ list_cnt,
                                              const unsigned *__restrict__ list,
                                              const int *__restrict__ origin,
@@ -216,11 +226,11 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
     // bucket's own bounds): source bucket B >= A whose cell bound meets the
     // sink box-of-balls (gather) or whose box-of-balls meets the sink cell
     // bound (scatter).  Lane w keeps the bits of entries 32w .. 32w+31.
-    const int g = A >> kp.logG;
-    const unsigned s0 = list_start[g], nl = list_cnt[g];
+    const int g = group_of(I, A);
+    const unsigned s0 = (unsigned)g * kWalkCap, nl = list_cnt[g];
     unsigned myword = 0u;
     {
-        const int ka = kp.P + A;
+        const size_t ka = leaf_of(I, A);
         const float4 sb0 = node[4 * ka], sb1 = node[4 * ka + 1];
         const float4 so0 = node[4 * ka + 2], so1 = node[4 * ka + 3];
         for (unsigned w = 0; 32 * w < nl; ++w) {
@@ -228,17 +238,17 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
             bool acc_ = false;
             if (e < nl) {
                 const unsigned B = list[s0 + e];
-                const unsigned k = (unsigned)kp.P + B;
+                const size_t k = leaf_of(I, (int)B);
                 if ((int)B >= A) {
                     const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
-                    acc_ = ovl(so0.x, so1.x, b0.x, b1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                           ovl(so0.y, so1.y, b0.y, b1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                           ovl(so0.z, so1.z, b0.z, b1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                    acc_ = ovl(so0.x, so1.x, b0.x, b1.x, bx.per[0], bx.L[0], bx.invL[0]) &&
+                           ovl(so0.y, so1.y, b0.y, b1.y, bx.per[1], bx.L[1], bx.invL[1]) &&
+                           ovl(so0.z, so1.z, b0.z, b1.z, bx.per[2], bx.L[2], bx.invL[2]);
                     if (!acc_) {
                         const float4 o0 = node[4 * k + 2], o1 = node[4 * k + 3];
-                        acc_ = ovl(sb0.x, sb1.x, o0.x, o1.x, kp.periodic[0], kp.L[0], kp.invL[0]) &&
-                               ovl(sb0.y, sb1.y, o0.y, o1.y, kp.periodic[1], kp.L[1], kp.invL[1]) &&
-                               ovl(sb0.z, sb1.z, o0.z, o1.z, kp.periodic[2], kp.L[2], kp.invL[2]);
+                        acc_ = ovl(sb0.x, sb1.x, o0.x, o1.x, bx.per[0], bx.L[0], bx.invL[0]) &&
+                               ovl(sb0.y, sb1.y, o0.y, o1.y, bx.per[1], bx.L[1], bx.invL[1]) &&
+                               ovl(sb0.z, sb1.z, o0.z, o1.z, bx.per[2], bx.L[2], bx.invL[2]);
                     }
                 }
             }
@@ -254,9 +264,10 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
         const unsigned e = 32 * w + __ffs(mw) - 1;
         mw &= mw - 1u;
         const int B = (int)list[s0 + e];
-        const float3 off = origin_offset(kp, origin, A, B);
-        const int j = B * kBucket + lane;
-        const bool vj = j < kp.n;
+        const float3 off = origin_offset(I, kp.nb, origin, A, B);
+        const int j0 = bstart[B];
+        const int j = j0 + lane;
+        const bool vj = lane < bucket_count(I, j0);
         const float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         float sp[3] = {off.x + q.x, off.y + q.y, off.z + q.z};
         // gather: inside the sink's box of balls and ball of balls;
@@ -267,10 +278,10 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
         for (int a = 0; a < 3; ++a) {
             float dg = sp[a] - sb.gc[a];
             float dc = sp[a] - sb.bc[a];
-            if (WRAP && kp.periodic[a]) {
-                sp[a] -= kp.L[a] * rintf((sp[a] - sb.cen[a]) * kp.invL[a]);
-                dg = wrapf(dg, kp.L[a], kp.invL[a]);
-                dc = wrapf(dc, kp.L[a], kp.invL[a]);
+            if (WRAP && bx.per[a]) {
+                sp[a] -= bx.L[a] * rintf((sp[a] - sb.cen[a]) * bx.invL[a]);
+                dg = wrapf(dg, bx.L[a], bx.invL[a]);
+                dc = wrapf(dc, bx.L[a], bx.invL[a]);
             }
             gbox = gbox && fabsf(dg) <= sb.gr[a];
             dg2 = fmaf(dg, dg, dg2);
@@ -290,7 +301,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
-            force_chunk<K, WRAP>(kp, S, c, s, valid, lane, acc, acc2);
+            force_chunk<K, WRAP>(bx, vp, S, c, s, valid, lane, acc, acc2);
             c = 0;
         }
       }
@@ -298,15 +309,17 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, int A, int lane,
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP>(kp, S, c, s, valid, lane, acc, acc2);
+        force_chunk<K, WRAP>(bx, vp, S, c, s, valid, lane, acc, acc2);
     }
 }
 
 template <class K>
-__global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__restrict__ fpos,
+__global__ void __launch_bounds__(128) k_forces(KParams kp, const Inst *__restrict__ insts,
+                                                const int *__restrict__ bstart,
+                                                const int *__restrict__ binst,
+                                                const float4 *__restrict__ fpos,
                                                 const float4 *__restrict__ fvel,
                                                 const float4 *__restrict__ fth,
-                                                const unsigned *__restrict__ list_start,
                                                 const unsigned *__restrict__ list_cnt,
                                                 const unsigned *__restrict__ list,
                                                 const int *__restrict__ origin,
@@ -317,8 +330,12 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = blockIdx.x * kWarpsPerBlock + wib;
     if (A >= kp.nb) return;
-    const int i = A * kBucket + lane;
-    const bool valid = i < kp.n;
+    const Inst &I = insts[binst[A]];
+    const PBox bx = make_pbox(I);
+    const Visc vp = {I.alpha, I.beta, I.eps_av};
+    const int i0 = bstart[A];
+    const int i = i0 + lane;
+    const bool valid = lane < bucket_count(I, i0);
     SinkState s;
     {
         float4 q = valid ? fpos[i] : make_float4(0.f, 0.f, 0.f, 1.f);
@@ -341,8 +358,9 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
     // (gc, gr) and ball of balls (centre gc, radius^2 gR2); wrap decision
     SinkBounds sb;
     bool wrap = false;
-    const float Hmax = node[4 * 1 + 3].w;  // largest h of all particles (root)
-    const float Emax = node[4 * 1 + 1].w;  // largest bucket extent (root)
+    const size_t root = (size_t)I.nbase + 1;
+    const float Hmax = node[4 * root + 3].w;  // largest h of the instance (root)
+    const float Emax = node[4 * root + 1].w;  // largest bucket extent (root)
     {
         const float p[3] = {s.px, s.py, s.pz};
 #pragma unroll
@@ -355,24 +373,24 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
             sb.gc[a] = 0.5f * (glo + ghi);
             sb.gr[a] = 0.5f * (ghi - glo);
             sb.cen[a] = sb.bc[a];
-            if (kp.periodic[a] && (hi - lo) + Hmax + Emax > 0.49f * kp.L[a]) wrap = true;
+            if (bx.per[a] && (hi - lo) + Hmax + Emax > 0.49f * bx.L[a]) wrap = true;
         }
     }
     {
         float dx = s.px - sb.gc[0], dy = s.py - sb.gc[1], dz = s.pz - sb.gc[2];
         float rr = valid ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + s.h : 0.f;
-        rr = warp_max(rr) * (1.f + 1e-6f) + kp.eps_abs;
+        rr = warp_max(rr) * (1.f + 1e-6f) + I.eps_abs;
         sb.gR2 = rr * rr;
     }
     unsigned long long cands = 0;
     if (wrap)
-        force_bucket<K, true>(kp, A, lane, stage[wib], s, valid, sb, fpos,
-                              fvel, fth, list_start, list_cnt, list, origin, node, acc, acc2,
-                              cands);
+        force_bucket<K, true>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+                              fpos, fvel, fth, list_cnt, list, origin, node, acc,
+                              acc2, cands);
     else
-        force_bucket<K, false>(kp, A, lane, stage[wib], s, valid, sb, fpos,
-                               fvel, fth, list_start, list_cnt, list, origin, node, acc, acc2,
-                              cands);
+        force_bucket<K, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+                              fpos, fvel, fth, list_cnt, list, origin, node, acc,
+                              acc2, cands);
     if (valid) {
         red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.S.s);
         if (s.du != 0.f) red_add_f32(&acc2[i].x, s.du);
@@ -389,42 +407,46 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const float4 *__rest
 // ---------------------------------------------------------------------------
 // finalize: PdV term, div v, time-step limits, global minimum
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(KParams kp, int n, const float4 *__restrict__ acc,
+__global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
+                           const unsigned short *__restrict__ pinst, const float4 *__restrict__ acc,
                            const float2 *__restrict__ acc2, const float4 *__restrict__ fpos,
                            const float4 *__restrict__ fth, float *ax, float *ay, float *az,
                            float *dudt_h, float *dudt_av, float *divv, float *dt_i,
                            unsigned *dtmin, DevStatus *st)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = INFINITY;
+    int k = -1;
     if (i < n) {
-        float4 f = acc[i];
-        float2 g = acc2[i];
-        float4 t = fth[i];
-        float h = fpos[i].w;
+        k = pinst[i];
+        const Inst &I = insts[k];
+        const float4 f = acc[i];
+        const float2 g = acc2[i];
+        const float4 t = fth[i];
+        const float h = fpos[i].w;
         ax[i] = f.x;
         ay[i] = f.y;
         az[i] = f.z;
         dudt_h[i] = t.x * f.w;
         dudt_av[i] = g.x;
         divv[i] = -f.w / (t.w * t.z);
-        float amag = sqrtf(fmaf(f.x, f.x, fmaf(f.y, f.y, f.z * f.z)));
-        float dta = amag > 0.f ? kp.eta_acc * sqrtf(h / amag) : INFINITY;
-        float dtc = kp.eta_courant * h /
-                    fmaf(1.f + 0.6f * kp.alpha, t.y, 0.6f * kp.beta * g.y);
+        const float amag = sqrtf(fmaf(f.x, f.x, fmaf(f.y, f.y, f.z * f.z)));
+        const float dta = amag > 0.f ? I.eta_acc * sqrtf(h / amag) : INFINITY;
+        const float dtc = I.eta_courant * h / fmaf(1.f + 0.6f * I.alpha, t.y, 0.6f * I.beta * g.y);
         dt = fminf(dta, dtc);
         dt_i[i] = dt;
         if (!(isfinite(f.x) && isfinite(f.y) && isfinite(f.z) && isfinite(f.w) && isfinite(g.x)))
             raise_status(st, ST_NONFINITE, i);
     }
-    dt = warp_min(dt);
-    __shared__ float sm[8];
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dt;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;
-        v = warp_min(v);
-        if (threadIdx.x == 0 && v < INFINITY) atomicMin(dtmin, __float_as_uint(v));
+    // minimum per instance: one atomic per warp when the warp lies in one
+    // instance (the usual case), else one per particle
+    const int k0 = __shfl_sync(kFull, k, 0);
+    if (__all_sync(kFull, k == k0 || k < 0)) {
+        dt = warp_min(dt);
+        if ((threadIdx.x & 31) == 0 && k0 >= 0 && dt < INFINITY)
+            atomicMin(&dtmin[k0], __float_as_uint(dt));
+    } else if (k >= 0 && dt < INFINITY) {
+        atomicMin(&dtmin[k], __float_as_uint(dt));
     }
 }
 
@@ -432,7 +454,8 @@ cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     int n = (int)p.n;
     c.launches += 1;
-    k_predict<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, p.v[0], p.v[1], p.v[2], p.u, p.a[0], p.a[1],
+    const int nt = n > c.kp.ninst ? n : c.kp.ninst;
+    k_predict<<<(nt + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.v[0], p.v[1], p.v[2], p.u, p.a[0], p.a[1],
                                               p.a[2], p.dudt_h, p.dudt_av, p.h, p.rho, p.omega,
                                               c.pm, c.dts, c.fpos, c.fvel, c.fth, c.acc, c.acc2,
                                               c.dtmin, c.st);
@@ -445,9 +468,9 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
     int g = (c.kp.nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
     c.launches += 1;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
-        k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.fpos, c.fvel, c.fth, c.list_start,
-                                                        c.list_cnt, c.list, c.origin, c.node,
-                                                        c.acc, c.acc2, c.st);
+        k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.inst, c.bstart, c.binst, c.fpos,
+                                                        c.fvel, c.fth, c.list_cnt, c.list,
+                                                        c.origin, c.node, c.acc, c.acc2, c.st);
     )
     return cudaGetLastError();
 }
@@ -456,7 +479,7 @@ cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     int n = (int)p.n;
     c.launches += 1;
-    k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.acc, c.acc2, c.fpos, c.fth, p.a[0],
+    k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, c.acc, c.acc2, c.fpos, c.fth, p.a[0],
                                                p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, p.dt_i,
                                                c.dtmin, c.st);
     return cudaGetLastError();

@@ -1,5 +1,5 @@
-// sph_integrate.cu -- kick-drift-kick with one global step (Sec. 2.3.6) and
-// the conserved totals.
+// sph_integrate.cu -- kick-drift-kick with one global step per instance
+// (Sec. 2.3.6) and the conserved totals.
 //
 //   closing kick   v_i = v_{i-1/2} + dt_old/2 a_i,      u_i likewise with du/dt
 //   step choice    dt_new = dt_fixed, or min_i dt_i (Sec. 2.3.6 criteria)
@@ -12,35 +12,48 @@
 
 namespace sph {
 
-__global__ void k_choose_dt(double *dts, const unsigned *dtmin, double dt_fixed, DevStatus *st)
+// one thread per instance: dts[2k] = dt_old, dts[2k+1] = dt_new
+__global__ void k_choose_dt(int ninst, double *dts, const unsigned *dtmin, double dt_fixed,
+                            DevStatus *st)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double dt = dt_fixed > 0.0 ? dt_fixed : (double)__uint_as_float(*dtmin);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ninst) return;
+    double dt = dt_fixed > 0.0 ? dt_fixed : (double)__uint_as_float(dtmin[k]);
     if (!(dt > 0.0) || !isfinite(dt)) {
-        raise_status(st, ST_NONFINITE, -1);
+        raise_status(st, ST_NONFINITE, -1 - k);
         dt = 0.0;
     }
-    dts[1] = dt;
+    dts[2 * k + 1] = dt;
+}
+
+__global__ void k_dt_shift(int ninst, double *dts)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ninst) dts[2 * k] = dts[2 * k + 1];
 }
 
 // The smoothing length is advanced with the drift as the seed of the next
 // density pass: the continuity equation gives rho(t + dt) ~ rho exp(-dt div v),
 // and h ~ rho^(-1/3), so h <- h exp(dt div v / 3) (factor clamped to [1/2, 2]).
-__global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double *vx, double *vy,
-                      double *vz, double *u, float *h, const float *__restrict__ ax,
-                      const float *__restrict__ ay, const float *__restrict__ az,
-                      const float *__restrict__ dudt_h, const float *__restrict__ dudt_av,
-                      const float *__restrict__ divv, const double *__restrict__ dts)
+__global__ void k_kdk(KParams kp, int n, const Inst *__restrict__ insts,
+                      const unsigned short *__restrict__ pinst, double *x, double *y, double *z,
+                      double *vx, double *vy, double *vz, double *u, float *h,
+                      const float *__restrict__ ax, const float *__restrict__ ay,
+                      const float *__restrict__ az, const float *__restrict__ dudt_h,
+                      const float *__restrict__ dudt_av, const float *__restrict__ divv,
+                      const double *__restrict__ dts)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double dt_old = dts[0], dt_new = dts[1];
+    const int k = pinst[i];
+    const Inst &I = insts[k];
+    const double dt_old = dts[2 * k], dt_new = dts[2 * k + 1];
     const double kick = 0.5 * (dt_old + dt_new);
     double ud = (double)dudt_av[i];
     if (kp.energy_mode == SPH_ENERGY_PDV) ud += (double)dudt_h[i];
-    double v0 = vx[i] + kick * (double)ax[i];
-    double v1 = vy[i] + kick * (double)ay[i];
-    double v2 = vz[i] + kick * (double)az[i];
+    const double v0 = vx[i] + kick * (double)ax[i];
+    const double v1 = vy[i] + kick * (double)ay[i];
+    const double v2 = vz[i] + kick * (double)az[i];
     vx[i] = v0;
     vy[i] = v1;
     vz[i] = v2;
@@ -48,13 +61,13 @@ __global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double
     double p[3] = {x[i] + dt_new * v0, y[i] + dt_new * v1, z[i] + dt_new * v2};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (kp.periodic[a]) {
+        if (I.periodic[a]) {
             // a particle moves far less than a box length per step
-            double t = p[a] - kp.lo[a];
-            if (t < 0.0 || t >= kp.Ld[a]) t -= kp.Ld[a] * floor(t * kp.invLd[a]);
-            if (t >= kp.Ld[a]) t -= kp.Ld[a];
+            double t = p[a] - I.lo[a];
+            if (t < 0.0 || t >= I.Ld[a]) t -= I.Ld[a] * floor(t * I.invLd[a]);
+            if (t >= I.Ld[a]) t -= I.Ld[a];
             if (t < 0.0) t = 0.0;
-            p[a] = kp.lo[a] + t;
+            p[a] = I.lo[a] + t;
         }
     }
     x[i] = p[0];
@@ -64,19 +77,23 @@ __global__ void k_kdk(KParams kp, int n, double *x, double *y, double *z, double
     h[i] *= fminf(fmaxf(f, 0.5f), 2.f);
 }
 
-// conserved totals: fixed-order block tree reduction, then one block sums
-// the block partials in order (bit-identical from run to run)
+// conserved totals per instance: grid (blocks, ninst); each block sums a
+// fixed slice of its instance in a fixed tree order, then one block per
+// instance folds the block partials in order (bit-identical from run to run)
 constexpr int kConsThreads = 256;
 
 __global__ void __launch_bounds__(kConsThreads) k_cons_partial(
-    int n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-    const double *__restrict__ vx, const double *__restrict__ vy, const double *__restrict__ vz,
-    const double *__restrict__ u, const float *__restrict__ m, double *part)
+    const Inst *__restrict__ insts, const double *__restrict__ x, const double *__restrict__ y,
+    const double *__restrict__ z, const double *__restrict__ vx, const double *__restrict__ vy,
+    const double *__restrict__ vz, const double *__restrict__ u, const float *__restrict__ m,
+    double *part)
 {
+    const Inst &I = insts[blockIdx.y];
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = blockIdx.x * kConsThreads + threadIdx.x; i < n; i += gridDim.x * kConsThreads) {
-        double mi = (double)m[i];
-        double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
+    const int b0 = I.off + blockIdx.x * kConsChunk, b1 = min(b0 + kConsChunk, I.off + I.n);
+    for (int i = b0 + threadIdx.x; i < b1; i += kConsThreads) {
+        const double mi = (double)m[i];
+        const double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
         acc[0] += mi;
         acc[1] += mi * v[0];
         acc[2] += mi * v[1];
@@ -98,42 +115,43 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(
         }
         __syncthreads();
     }
-    if (threadIdx.x < 9) part[blockIdx.x * 9 + threadIdx.x] = sm[threadIdx.x][0];
+    if (threadIdx.x < 9)
+        part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 9 + threadIdx.x] = sm[threadIdx.x][0];
 }
 
-// nine warps, one per total; each lane sums a fixed stride of the block
-// partials and the warp folds the lanes in a fixed butterfly order
-__global__ void k_cons_final(int nparts, const double *part, double *out)
+// nine warps per instance, one per total; each lane sums a fixed stride of
+// the block partials and the warp folds the lanes in a fixed butterfly order
+__global__ void k_cons_final(int nblocks, const double *part, double *out)
 {
-    int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= 9) return;
+    const double *pp = part + (size_t)blockIdx.x * nblocks * 9;
     double s = 0.0;
-    for (int b = lane; b < nparts; b += 32) s += part[b * 9 + q];
+    for (int b = lane; b < nblocks; b += 32) s += pp[b * 9 + q];
     s = warp_sum(s);
-    if (lane == 0) out[q] = s;
+    if (lane == 0) out[blockIdx.x * 9 + q] = s;
 }
-
-constexpr int kConsBlocks = 304;
 
 cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s)
 {
-    int n = (int)p.n;
-    c.launches += 2;
-    k_choose_dt<<<1, 32, 0, s>>>(c.dts, c.dtmin, dt_fixed, c.st);
-    k_kdk<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2],
-                                          p.u, p.h, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av,
-                                          p.divv, c.dts);
-    cudaMemcpyAsync(c.dts, c.dts + 1, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    const int n = (int)p.n;
+    const int ni = c.kp.ninst;
+    c.launches += 3;
+    k_choose_dt<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts, c.dtmin, dt_fixed, c.st);
+    k_kdk<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
+                                          p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
+                                          p.dudt_h, p.dudt_av, p.divv, c.dts);
+    k_dt_shift<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
-    int n = (int)p.n;
+    const int nb = c.cons_blocks > 0 ? c.cons_blocks : 1;
     c.launches += 2;
-    k_cons_partial<<<kConsBlocks, kConsThreads, 0, s>>>(n, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1],
-                                                        p.v[2], p.u, p.m, c.cons_part);
-    k_cons_final<<<1, 288, 0, s>>>(kConsBlocks, c.cons_part, c.cons_out);
+    k_cons_partial<<<dim3(nb, c.kp.ninst), kConsThreads, 0, s>>>(
+        c.inst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.m, c.cons_part);
+    k_cons_final<<<c.kp.ninst, 288, 0, s>>>(nb, c.cons_part, c.cons_out);
     return cudaGetLastError();
 }
 

@@ -1,22 +1,32 @@
 // sph_internal.cuh -- shared declarations of the libsph translation units.
 //
-// Data layout in device memory (structure of arrays, Morton order after
-// sph_build_cells):
+// A context holds one or more independent problems ("instances", each with
+// its own box, periodicity, gas and viscosity parameters and time step) that
+// are stepped together: every phase is ONE launch over all instances.  A
+// single problem is a batch of one.
+//
+// Data layout in device memory (structure of arrays, Morton order within each
+// instance after sph_build_cells; instances stay in their particle ranges):
 //   caller arrays   x,v (f64), u (f64), m,h,rho,omega,a,dudt,... (f32)
+//   pinst[i]        instance of particle i (u16)
 //   pm[i]           float4 (x - o_b, y - o_b, z - o_b, m): position relative to
 //                   the origin o_b of the particle's bucket, plus mass
-//   buckets         32 consecutive particles; origin o_b = k_b q with integer
-//                   grid coordinates k_b (int32 x3) and the power-of-two quantum
-//                   q, so origin differences are exact in f32 and need no FP64
-//   groups          G = 8 consecutive buckets (256 particles) share one walk
-//   tree            implicit complete binary tree over the buckets padded to a
-//                   power of two P (root 1, leaf of bucket b = P + b); each node
-//                   stores its cell bound (AABB) and box-of-balls bound as
-//                   centre/half-width float4 pairs, Sec. 2.3.2
-//   lists           per group, the source buckets whose bounds overlap the
-//                   group's bounds (CSR: start/count per group into one u32
-//                   array); each sink bucket filters them against its own bounds
-//   force records   fpos (rel xyz, h), fvel (v_pred xyz, m), fth (A, c, rho, -)
+//   buckets         up to 32 consecutive particles of one instance (one warp):
+//                   first particle bstart[b], instance binst[b], origin
+//                   o_b = k_b q with integer grid coordinates k_b (int32 x3) and
+//                   the instance's power-of-two quantum q, so origin
+//                   differences are exact in f32 and need no FP64
+//   tree            per instance an implicit complete binary tree over its
+//                   buckets padded to a power of two P (node nbase + k, root
+//                   k = 1, leaf of local bucket j = k P + j); each node stores
+//                   its cell bound (AABB) and box-of-balls bound as centre /
+//                   half-width float4 pairs (Sec. 2.3.2); .w of the cell half
+//                   widths = largest bucket extent below, .w of the
+//                   box-of-balls half widths = largest h below
+//   groups          G <= 8 consecutive buckets of one instance (<= 256
+//                   particles) share one tree walk: first bucket gfirst[g]
+//   lists           per group, kWalkCap slots of source bucket ids
+//   force records   fpos (rel xyz, h), fvel (v_pred xyz, m), fth (A, c, rho, Omega)
 //   accumulators    acc (a xyz, S = sum m_j v_ij.gradW_ij(h_i)), acc2 (du/dt|Pi,
 //                   max(-mu_ij) as float bits)
 #pragma once
@@ -25,6 +35,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sph.h"
 
@@ -32,12 +43,15 @@ namespace sph {
 
 constexpr int kBucket = 32;       // particles per bucket = one warp
 constexpr int kChunk = 128;       // staged candidates processed per chunk
-constexpr int kWalkCap = 1024;    // frontier / list entries per sink bucket
+constexpr int kWalkCap = 1024;    // frontier / list entries per group
+constexpr int kGroupLog = 3;      // groups of up to 8 buckets
 constexpr int kWarpsPerBlock = 4; // pair kernels and walks: 4 warps per block
 constexpr int kSortItems = 8;     // keys per thread in a radix-sort tile
 constexpr int kSortTile = 256 * kSortItems;  // keys per radix-sort tile
-constexpr int kMortonBits = 10;   // bits per axis of the Morton key (30-bit keys)
-constexpr int kSortPasses = 4;    // 8-bit digits cover the 30-bit keys
+constexpr int kMortonBits = 10;   // bits per axis of the Morton key (30 bits)
+constexpr int kRelistRounds = 3;  // re-walk rounds queued after the first density pass
+constexpr int kBboxChunks = 32;   // blocks per instance for open-axis bounding boxes
+constexpr int kConsChunk = 2048;  // particles per block of the conserved totals
 constexpr unsigned kFull = 0xffffffffu;
 
 enum StatusCode : int {
@@ -48,38 +62,53 @@ enum StatusCode : int {
 // device-resident status + counters, reset at the start of every API call
 struct DevStatus {
     int code;            // first error code raised by a kernel
-    int detail;          // what raised it (bucket or particle index, needed size ...)
+    int detail;          // what raised it (bucket or particle index, group ...)
     unsigned long long density_pairs;
     unsigned long long force_pairs;
     unsigned long long density_cand;
     unsigned long long force_cand;
     unsigned long long force_av_pairs;
     int max_iters;
-    unsigned int redo_count;   // buckets whose h left the list coverage
-    unsigned int list_used;    // entries allocated in the list buffer
-    unsigned int list_need;    // entries the walk wanted (>= list_used on overflow)
-    unsigned int dt_min_bits;  // min_i dt_i as float bits (positive floats order as ints)
+    unsigned int relists;                      // groups re-walked in total
+    unsigned int redo_cnt[kRelistRounds + 1];  // groups queued for round r
     unsigned int pad;
 };
 
-// parameters as the kernels see them (copied by value into every launch)
-struct KParams {
-    int kernel, energy_mode, max_newton, nb, P, logP;
-    int G, logG, ng;      // buckets per group, log2, number of groups
+// one independent problem (device array; every kernel reads its instance)
+struct Inst {
+    int off, n;          // particles [off, off + n)
+    int boff, nb;        // buckets [boff, boff + nb)
+    int goff, ng;        // groups [goff, goff + ng)
+    int nbase, P, logP;  // tree nodes nbase + [1, 2P)
+    int G, logG;         // buckets per group
     int periodic[3];
-    int n;
-    float L[3], invL[3], halfL[3];
-    float n_ngb, gamma, alpha, beta, eps_av, eta_courant, eta_acc, h_rel_tol, margin;
-    float eps_abs;        // absolute inflation of f32 bounds (covers rounding)
-    float hcap;           // h must stay below half the shortest periodic length
-    double q, inv_q;      // origin quantum and its inverse (powers of two)
-    float qf;             // q in f32
-    double Ld[3], invLd[3];  // periodic lengths in FP64
-    double lo[3], hi[3];  // box
+    float L[3], invL[3];
+    float gamma, alpha, beta, eps_av, eta_courant, eta_acc, n_ngb;
+    float eps_abs;       // absolute inflation of f32 bounds (covers rounding)
+    float hcap;          // h must stay below half the shortest periodic length
+    float qf;            // origin quantum in f32
+    double q, inv_q;     // origin quantum and its inverse (powers of two)
+    double lo[3], hi[3], Ld[3], invLd[3];
+};
+
+// batch-wide settings (copied by value into every launch)
+struct KParams {
+    int kernel, energy_mode, max_newton;
+    int ninst, n, nb, ng, nnodes;
+    int key_passes;      // 8-bit radix passes over (instance, Morton) keys
+    int any_open;        // some instance has an open axis
+    float h_rel_tol, margin;
+};
+
+// one block of the bottom-up tree refit: reduce `levels` levels of instance
+// `inst` starting at level `lvl`, block index `blk` within that level
+struct RefitBlock {
+    int inst, lvl, levels, blk;
 };
 
 struct Ctx {
-    sph_params prm;
+    std::vector<sph_params> prm;  // per instance
+    std::vector<Inst> inst_host;
     KParams kp;
     int64_t capacity = 0;
     int device = 0;
@@ -87,27 +116,37 @@ struct Ctx {
     sph_stats stats{};
     bool cells_valid = false, density_valid = false, forces_valid = false, rho_valid = false;
     int64_t n_built = 0;
+    std::vector<double> dt_host;  // per instance step of the last kick-drift-kick
+
+    // instances and their static index maps
+    Inst *inst = nullptr;          // device copy of inst_host
+    unsigned short *pinst = nullptr;
+    int *bstart = nullptr, *binst = nullptr;
+    int *gfirst = nullptr;
+    RefitBlock *refit = nullptr;   // refit schedule (all bands)
+    std::vector<int> refit_band;   // blocks per band (host)
 
     // status
     DevStatus *st = nullptr;       // device
     DevStatus *st_host = nullptr;  // pinned host mirror
-    double *dts = nullptr;         // device [dt_old, dt_new]
-    unsigned int *dtmin = nullptr; // device min_i dt_i as float bits
-    double *morton_box = nullptr;  // device [lo0,lo1,lo2, inv0,inv1,inv2]
-    double *bbox_part = nullptr;   // device partial min/max for open axes
-    double *cons_part = nullptr;   // device partial sums for sph_reduce_conserved
-    double *cons_out = nullptr;    // device 9 doubles
+    double *dts = nullptr;         // device per instance [dt_old, dt_new]
+    double *dts_host = nullptr;    // pinned mirror
+    unsigned int *dtmin = nullptr; // device per instance min_i dt_i as float bits
+    double *morton_box = nullptr;  // device per instance [lo0,lo1,lo2, scale0,scale1,scale2]
+    double *bbox_part = nullptr;   // device per instance partial min/max for open axes
+    double *cons_part = nullptr;   // device per (instance, block) partial sums
+    double *cons_out = nullptr;    // device 9 doubles per instance
+    double *cons_host = nullptr;   // pinned mirror
+    int cons_blocks = 0;           // largest number of blocks of one instance
 
     // sort
-    unsigned int *keys[2] = {nullptr, nullptr};
+    unsigned long long *keys[2] = {nullptr, nullptr};
     unsigned int *vals[2] = {nullptr, nullptr};
     unsigned int *hist = nullptr;     // 256 x tiles
     unsigned int *digit_tot = nullptr;  // per-digit totals of the current sort pass
     void *tmp = nullptr;              // permutation scratch, 112 B x capacity
-    unsigned int *perm = nullptr;     // final permutation (sorted -> old index)
 
     // buckets / tree
-    int nb_cap = 0, P_cap = 0;
     int *origin = nullptr;            // 3 x nb grid coordinates (SoA: kx, ky, kz)
     unsigned int *gflag = nullptr;    // per group: queued for a re-walk
     float4 *node = nullptr;           // 4 float4 per node: box_c, box_r, bob_c, bob_r
@@ -118,19 +157,25 @@ struct Ctx {
     float4 *acc = nullptr;
     float2 *acc2 = nullptr;
     float *rho_old = nullptr;
-    float *h_seed = nullptr;          // density seeds / redo seeds
+    float *h_seed = nullptr;          // density seeds / re-walk seeds
 
-    // lists
-    unsigned int *list_start = nullptr, *list_cnt = nullptr, *list = nullptr;
-    int64_t list_cap = 0;
-    unsigned int *redo = nullptr;     // ids of groups queued for a re-walk (2 halves)
+    // lists: kWalkCap slots per group
+    unsigned int *list = nullptr, *list_cnt = nullptr;
+    unsigned int *redo = nullptr;     // per round r: group ids queued (ng entries each)
 
     // host-mode mirror buffers for sph_step_host
     void *mirror = nullptr;
     sph_particles dmirror{};
 
+    // captured step
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    sph_particles graph_p{};
+    double graph_dt = 0.0;
+    uint64_t graph_kernels = 0;   // kernels in one replay
+
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};  // walk start / kernel start / kernel end
+    cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     uint64_t launches = 0;
 };
 
@@ -206,19 +251,56 @@ __device__ __forceinline__ bool ovl(float ca, float ra, float cb, float rb, bool
     return fabsf(d) <= ra + rb;
 }
 
-// f32 offset o_B - o_A between two bucket origins (nearest periodic image):
-// integer grid difference times the power-of-two quantum, exact in f32
-__device__ __forceinline__ float3 origin_offset(const KParams &kp, const int *__restrict__ origin,
-                                                int A, int B)
+// f32 offset o_B - o_A between two bucket origins of one instance (nearest
+// periodic image): integer grid difference times the power-of-two quantum,
+// exact in f32 whenever the periodic length is a multiple of q
+__device__ __forceinline__ float3 origin_offset(const Inst &I, int nb_total,
+                                                const int *__restrict__ origin, int A, int B)
 {
     float d[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float f = (float)(origin[a * kp.nb + B] - origin[a * kp.nb + A]) * kp.qf;
-        if (kp.periodic[a]) f -= kp.L[a] * rintf(f * kp.invL[a]);
+        float f = (float)(origin[a * nb_total + B] - origin[a * nb_total + A]) * I.qf;
+        if (I.periodic[a]) f -= I.L[a] * rintf(f * I.invL[a]);
         d[a] = f;
     }
     return make_float3(d[0], d[1], d[2]);
+}
+
+// periodic geometry of one instance, held in registers by the pair kernels
+struct PBox {
+    int per[3];
+    float L[3], invL[3];
+};
+__device__ __forceinline__ PBox make_pbox(const Inst &I)
+{
+    PBox b;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b.per[a] = I.periodic[a];
+        b.L[a] = I.L[a];
+        b.invL[a] = I.invL[a];
+    }
+    return b;
+}
+
+// bucket -> group (global index) of instance I
+__device__ __forceinline__ int group_of(const Inst &I, int b)
+{
+    return I.goff + ((b - I.boff) >> I.logG);
+}
+
+// leaf node (global index) of bucket b of instance I
+__device__ __forceinline__ size_t leaf_of(const Inst &I, int b)
+{
+    return (size_t)I.nbase + I.P + (b - I.boff);
+}
+
+// particles in bucket b (global index) of instance I
+__device__ __forceinline__ int bucket_count(const Inst &I, int bstart)
+{
+    int c = I.off + I.n - bstart;
+    return c < kBucket ? c : kBucket;
 }
 
 // Kahan-compensated running sum (the density and force sums accumulate one
@@ -303,17 +385,21 @@ struct KM4 {
     }
 
 // ---------------------------------------------------------------------------
-// host-side launchers (defined in the .cu files)
+// host-side launchers (defined in the .cu files); every one queues work on
+// stream s and counts its launches in c.launches
 // ---------------------------------------------------------------------------
+enum WalkMode { WALK_DENSITY = 0, WALK_FORCE = 1 };
 // build (sph_build.cu)
 cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s);
-cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, const unsigned int *group_ids,
-                        int ngroups, const float *h_for_walk, cudaStream_t s);
-// density (sph_density.cu)
-cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed,
-                           const unsigned int *bucket_ids, int nbuckets, int fixed_h,
-                           int64_t cap, uint32_t *count, int64_t *ids, cudaStream_t s);
+// group walk: all groups (round < 0) or the groups queued for re-walk round r
+cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, const float *h_walk,
+                        cudaStream_t s);
+// density (sph_density.cu): round < 0 = all buckets, else the buckets of the
+// groups queued for round r; fixed_h evaluates at the given h once
+cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, int round,
+                           int fixed_h, int64_t cap, uint32_t *count, int64_t *ids,
+                           cudaStream_t s);
 cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s);
 // forces (sph_forces.cu)
 cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s);
@@ -322,7 +408,5 @@ cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s);
 // integration (sph_integrate.cu)
 cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s);
 cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s);
-
-enum WalkMode { WALK_DENSITY = 0, WALK_FORCE = 1 };
 
 }  // namespace sph
