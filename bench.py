@@ -206,6 +206,96 @@ def run_reference(args, rank, world):
     return 0
 
 
+def forms_batch(dev, steps, warmup):
+    """The batched form against the plain form on the 256-instance workload.
+
+    plain          one context per problem, sph_step called for each in turn
+    batched        one batch context: one launch per phase over all instances
+    batched_graph  the batch step captured once as a CUDA graph and replayed
+    All three advance every instance by the same number of steps from the same
+    state; the per-instance step sizes they end with are compared (the batched
+    forms compute the same pairs as the plain one)."""
+    import torch
+    import paper_2511_11425_gb300 as sph
+    from paper_2511_11425_gb300 import inputs
+
+    probs = inputs.batch()
+    ntot = sum(q.n for q in probs)
+    s = torch.cuda.Stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(step, ctxs):
+        l0 = sum(sph.sph_get_stats(c)["launches"] for c in ctxs)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        dp = fp = 0
+        with torch.cuda.stream(s):
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(s)
+                step()
+                ev[k][1].record(s)
+                for c in ctxs:
+                    st = sph.sph_get_stats(c)
+                    dp += st["density_pairs"]
+                    fp += st["force_pairs"]
+            s.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        l1 = sum(sph.sph_get_stats(c)["launches"] for c in ctxs)
+        return {"value": ntot * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                "launches_per_step": (l1 - l0) / steps,
+                "pair_interactions_per_s": (dp + fp) / (ms * 1e-3)}
+
+    out = {"workload": "256 independent Sod (gamma 1.4) and Sedov (gamma 5/3) instances, "
+                       "particle counts log-uniform in [2k, 200k]",
+           "instances": len(probs), "particles": ntot, "steps": steps, "warmup": warmup}
+    sims = [sph.Simulation(q, device=dev) for q in probs]
+    last = [0.0] * len(sims)
+
+    def plain():
+        for k, sim in enumerate(sims):
+            last[k] = sph.sph_step(sim.ctx, sim.parts, 0.0, s)
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            plain()
+    out["plain"] = timed(plain, [sim.ctx for sim in sims])
+    dt_plain = np.array(last)
+    for sim in sims:
+        sim.close()
+    del sims
+    torch.cuda.empty_cache()
+
+    b = sph.BatchSimulation(probs, device=dev)
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            sph.sph_step(b.ctx, b.parts, 0.0, s)
+    out["batched"] = timed(lambda: sph.sph_step(b.ctx, b.parts, 0.0, s), [b.ctx])
+    dt_b = np.array(sph.sph_batch_get_dt(b.ctx, b.ninst))
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+
+    g = sph.BatchSimulation(probs, device=dev)
+    with torch.cuda.stream(s):
+        sph.sph_step(g.ctx, g.parts, 0.0, s)
+        g.capture(s)
+        for _ in range(warmup - 1):
+            sph.sph_graph_launch(g.ctx, s)
+    out["batched_graph"] = timed(lambda: sph.sph_graph_launch(g.ctx, s), [g.ctx])
+    dt_g = np.array(sph.sph_batch_get_dt(g.ctx, g.ninst))
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+
+    out["speedup_vs_plain"] = {
+        "batched": out["batched"]["value"] / out["plain"]["value"],
+        "batched_graph": out["batched_graph"]["value"] / out["plain"]["value"]}
+    out["max_rel_dt_diff_vs_plain"] = {
+        "batched": float(np.max(np.abs(dt_b - dt_plain) / dt_plain)),
+        "batched_graph": float(np.max(np.abs(dt_g - dt_plain) / dt_plain))}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2511_11425_gb300 as sph
@@ -302,6 +392,10 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * prob2.n * args.steps / tt, "unit": UNIT,
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
 
+    sim.close()
+    forms = None
+    if world == 1 and not args.no_forms:
+        forms = forms_batch(dev, max(2, min(args.steps, 5)), max(args.warmup, 3))
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)
@@ -320,9 +414,8 @@ def run_ours(args, rank, world, local_rank):
                                                "force": fcand / max(fpairs, 1)},
                 "roofline": roof, "roofline_other": other_line, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
-                "impl": "ours"}
+                "forms": forms, "impl": "ours"}
         print(json.dumps(line), flush=True)
-    sim.close()
     return 0
 
 
@@ -334,6 +427,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the plain / batched / graph comparison on 256 instances")
     args = ap.parse_args(argv)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -71,6 +71,10 @@ enum { SPH_KERNEL_WC2 = 0, SPH_KERNEL_WC4 = 1, SPH_KERNEL_WC6 = 2, SPH_KERNEL_M4
 /* internal-energy update: PdV equation (Sec. 2.3.5) or entropy-conserving
  * rescale u <- u (rho/rho_old)^(gamma-1) plus viscous heating only */
 enum { SPH_ENERGY_PDV = 0, SPH_ENERGY_ISENTROPIC = 1 };
+/* space-filling curve that orders the particles into buckets (Sec. 2.1 sorts
+ * along a curve so that cells are contiguous; both curves visit the octree
+ * cells depth first, the Hilbert curve without jumps between cells) */
+enum { SPH_CURVE_HILBERT = 0, SPH_CURVE_MORTON = 1 };
 
 typedef struct {
     int32_t kernel;        /* SPH_KERNEL_*                                       */
@@ -87,6 +91,8 @@ typedef struct {
     int32_t max_newton;    /* Newton iteration cap per particle (<= 255)         */
     double  h_rel_tol;     /* Newton stops when |dh|/h < h_rel_tol               */
     double  list_margin;   /* density lists gather within h (1 + list_margin)    */
+    int32_t curve;         /* particle order: SPH_CURVE_HILBERT or SPH_CURVE_MORTON */
+    int32_t group_log;     /* buckets per list walk = 2^group_log (1..3); 0 = 3  */
 } sph_params;
 
 typedef struct {

@@ -25,6 +25,7 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_CAPACITY
           4: "SPH_ERR_NOCONV", 5: "SPH_ERR_NONFINITE", 6: "SPH_ERR_TIMEOUT", 7: "SPH_ERR_STATE"}
 KERNELS = {"wc2": 0, "wc4": 1, "wc6": 2, "m4": 3}
 ENERGY = {"pdv": 0, "isentropic": 1}
+CURVES = {"hilbert": 0, "morton": 1}
 EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph_density_at",
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
            "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
@@ -44,7 +45,8 @@ class c_params(C.Structure):
                 ("eps_av", C.c_double), ("eta_courant", C.c_double), ("eta_acc", C.c_double),
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("periodic", C.c_int32 * 3), ("max_newton", C.c_int32),
-                ("h_rel_tol", C.c_double), ("list_margin", C.c_double)]
+                ("h_rel_tol", C.c_double), ("list_margin", C.c_double),
+                ("curve", C.c_int32), ("group_log", C.c_int32)]
 
 
 class c_particles(C.Structure):
@@ -140,6 +142,8 @@ class Params:
     max_newton: int = 64
     h_rel_tol: float = 1e-6
     list_margin: float = 0.1
+    curve: str = "hilbert"
+    group_log: int = 3
 
     def c(self) -> c_params:
         p = c_params()
@@ -149,6 +153,8 @@ class Params:
                   "h_rel_tol", "list_margin"):
             setattr(p, f, float(getattr(self, f)))
         p.max_newton = int(self.max_newton)
+        p.curve = CURVES[self.curve]
+        p.group_log = int(self.group_log)
         for a in range(3):
             p.box_lo[a] = float(self.box_lo[a])
             p.box_hi[a] = float(self.box_hi[a])
@@ -197,6 +203,25 @@ class Particles:
         p.t["m"].copy_(torch.from_numpy(prob.m.astype("float32")))
         p.t["h"].copy_(torch.from_numpy(prob.h0.astype("float32")))
         return p
+
+    @classmethod
+    def from_problems(cls, probs, device="cuda", pin=False):
+        """Concatenation of several problems (the layout of a batch context);
+        returns (particles, offsets) with offsets[k]:offsets[k+1] = problem k."""
+        import numpy as np
+        import torch
+        offs = np.cumsum([0] + [q.n for q in probs]).astype(np.int64)
+        p = cls(int(offs[-1]), device, pin)
+
+        def cat(get, dtype):
+            return torch.from_numpy(np.concatenate([get(q) for q in probs]).astype(dtype))
+        for a in range(3):
+            p.t["x%d" % a].copy_(cat(lambda q: q.pos[:, a], "float64"))
+            p.t["v%d" % a].copy_(cat(lambda q: q.vel[:, a], "float64"))
+        p.t["u"].copy_(cat(lambda q: q.u, "float64"))
+        p.t["m"].copy_(cat(lambda q: q.m, "float32"))
+        p.t["h"].copy_(cat(lambda q: q.h0, "float32"))
+        return p, offs
 
     def c(self) -> c_particles:
         s = c_particles()
@@ -386,3 +411,34 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class BatchSimulation(Simulation):
+    """Independent problems of uneven sizes stepped together: one launch per
+    phase over all of them, optionally replayed from a captured CUDA graph."""
+
+    def __init__(self, probs, params_list=None, device="cuda"):
+        self.params_list = params_list or [Params.for_problem(q) for q in probs]
+        self.parts, self.offsets = Particles.from_problems(probs, device)
+        self.ninst = len(probs)
+        self.ctx = sph_batch_create(self.params_list, self.offsets)
+        self.t = [0.0] * self.ninst
+        self.graph_stream = None
+
+    def step(self, dt_fixed=0.0, stream=None) -> list:
+        if self.graph_stream is not None:
+            sph_graph_launch(self.ctx, self.graph_stream)
+        else:
+            sph_step(self.ctx, self.parts, dt_fixed, stream)
+        dts = sph_batch_get_dt(self.ctx, self.ninst)
+        self.t = [t + d for t, d in zip(self.t, dts)]
+        return dts
+
+    def capture(self, stream, dt_fixed=0.0):
+        """Record one step as a CUDA graph on `stream` (not the default
+        stream); later step() calls replay it there."""
+        sph_graph_capture(self.ctx, self.parts, dt_fixed, stream)
+        self.graph_stream = stream
+
+    def conserved(self, stream=None):
+        return sph_reduce_conserved(self.ctx, self.parts, stream, self.ninst)

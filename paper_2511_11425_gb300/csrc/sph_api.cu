@@ -74,7 +74,9 @@ bool params_ok(const sph_params *prm)
         prm->max_newton < 1 || prm->max_newton > 255 || !(prm->h_rel_tol > 0.0) ||
         !(prm->list_margin >= 0.0) || !(prm->eta_courant > 0.0) || !(prm->eta_acc > 0.0) ||
         !(prm->alpha >= 0.0) || !(prm->beta >= 0.0) || !(prm->eps_av > 0.0) ||
-        (prm->energy_mode != SPH_ENERGY_PDV && prm->energy_mode != SPH_ENERGY_ISENTROPIC))
+        (prm->energy_mode != SPH_ENERGY_PDV && prm->energy_mode != SPH_ENERGY_ISENTROPIC) ||
+        (prm->curve != SPH_CURVE_HILBERT && prm->curve != SPH_CURVE_MORTON) ||
+        prm->group_log < 0 || prm->group_log > kGroupLog)
         return false;
     for (int a = 0; a < 3; ++a)
         if (!(prm->box_hi[a] > prm->box_lo[a]) || !std::isfinite(prm->box_lo[a]) ||
@@ -109,6 +111,7 @@ Inst inst_params(const sph_params &prm)
     I.eta_courant = (float)prm.eta_courant;
     I.eta_acc = (float)prm.eta_acc;
     I.n_ngb = (float)prm.n_ngb;
+    I.curve = prm.curve;
     I.hcap = (float)hcap;
     I.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
     I.inv_q = 1.0 / I.q;
@@ -122,14 +125,21 @@ struct Sizes {
     int64_t n = 0, nb = 0, ng = 0, nodes = 0, refit = 0, cons_blocks = 0;
 };
 
-Sizes layout_sizes(const std::vector<int64_t> &counts)
+// log2 of the buckets per walk group of an instance
+int group_log(const sph_params &prm, int logP)
+{
+    return std::min(logP, prm.group_log > 0 ? prm.group_log : kGroupLog);
+}
+
+Sizes layout_sizes(const std::vector<int64_t> &counts, const std::vector<sph_params> &prm)
 {
     Sizes z;
-    for (int64_t nk : counts) {
+    for (size_t k = 0; k < counts.size(); ++k) {
+        const int64_t nk = counts[k];
         const int64_t nb = (nk + kBucket - 1) / kBucket;
         const int logP = ilog2_ceil(std::max<int64_t>(nb, 1));
         const int64_t P = (int64_t)1 << logP;
-        const int logG = std::min(logP, kGroupLog);
+        const int logG = group_log(prm[k], logP);
         z.n += nk;
         z.nb += nb;
         z.ng += (nb + (1 << logG) - 1) >> logG;
@@ -157,7 +167,7 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.inst, ninst);
     AL(c.dts, 2 * ninst);
     AL(c.dtmin, ninst);
-    AL(c.morton_box, 6 * ninst);
+    AL(c.morton_box, kKeyBox * ninst);
     AL(c.bbox_part, (size_t)6 * kBboxChunks * ninst);
     AL(c.cons_part, (size_t)9 * std::max<int64_t>(cap.cons_blocks, 1) * ninst);
     AL(c.cons_out, (size_t)9 * ninst);
@@ -246,7 +256,7 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
         I.boff = (int)boff;
         I.logP = ilog2_ceil(std::max(I.nb, 1));
         I.P = 1 << I.logP;
-        I.logG = std::min(I.logP, kGroupLog);
+        I.logG = group_log(c.prm[k], I.logP);
         I.G = 1 << I.logG;
         I.ng = (I.nb + I.G - 1) >> I.logG;
         I.goff = (int)goff;
@@ -460,7 +470,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.kp.h_rel_tol = (float)prm[0].h_rel_tol;
     c.kp.margin = (float)prm[0].list_margin;
     c.kp.ninst = ninst;
-    const Sizes z = layout_sizes(counts);
+    const Sizes z = layout_sizes(counts, c.prm);
     sph_status rc = allocate(c, z, ninst);
     if (rc == SPH_OK) rc = set_layout(c, counts);
     if (rc == SPH_OK && cudaDeviceSynchronize() != cudaSuccess) rc = SPH_ERR_CUDA;

@@ -56,13 +56,19 @@ __global__ void k_bbox_partial(const Inst *__restrict__ insts, const double *__r
     }
 }
 
-// morton_box per instance = [lo0, lo1, lo2, scale0, scale1, scale2]
+// key box per instance = [lo0, lo1, lo2, 2^bin / S, cubes0, cubes1, cubes2, bin]
 __global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const double *part,
                              double *morton_box, DevStatus *st)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kp.ninst) return;
     const Inst &I = insts[k];
+    // The domain is cut into equal cubes of side S = its shortest extent
+    // (at least 1/1024 of the longest), visited in a snake order (every cube
+    // is a face neighbour of the one before); the curve orders the particles
+    // inside each cube on 2^bin cells per axis.  Key cells stay cubic however
+    // elongated the domain (a tube, a slab), so curve ranges stay compact.
+    double lo3[3], ext3[3], emin = INFINITY, emax = 0.0;
     for (int a = 0; a < 3; ++a) {
         double lo, hi;
         if (I.periodic[a] || !kp.any_open || I.n == 0) {
@@ -81,10 +87,28 @@ __global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const d
             lo = 0.0;
             hi = 1.0;
         }
-        double ext = (hi - lo) * (1.0 + 1e-9) + 1e-300;
-        morton_box[k * 6 + a] = lo;
-        morton_box[k * 6 + 3 + a] = (double)(1 << kMortonBits) / ext;
+        lo3[a] = lo;
+        ext3[a] = hi - lo;
+        emin = fmin(emin, hi - lo);
+        emax = fmax(emax, hi - lo);
     }
+    const double S = fmax(emin, emax / (double)(1 << kMortonBits)) * (1.0 + 1e-9) + 1e-300;
+    long long ncubes = 1;
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)fmin(fmax(ceil(ext3[a] / S), 1.0), (double)(1 << kMortonBits));
+        ncubes *= nc[a];
+    }
+    int bpre = 0;
+    while ((1ll << bpre) < ncubes) ++bpre;
+    const int bin = min(kMortonBits, (30 - bpre) / 3);
+    double *mb = morton_box + kKeyBox * k;
+    for (int a = 0; a < 3; ++a) {
+        mb[a] = lo3[a];
+        mb[4 + a] = (double)nc[a];
+    }
+    mb[3] = ldexp(1.0, bin) / S;
+    mb[7] = (double)bin;
 }
 
 // 10-bit coordinate -> every third bit of a 30-bit word
@@ -98,8 +122,43 @@ __device__ __forceinline__ unsigned spread3(unsigned x)
     return x;
 }
 
-// key = instance << 30 | Morton code in the instance's box
-__global__ void k_morton(int n, const unsigned short *__restrict__ pinst,
+// Hilbert index of a 10-bit cell (Skilling 2004, "Programming the Hilbert
+// curve"): the axes are turned into the transposed index by undoing, level
+// by level from the top, the reflections and axis exchanges of the curve,
+// then Gray-decoded; the transposed bits interleaved (axis 0 highest in each
+// triple) are the index.  Cells consecutive on the curve share a face.
+__device__ __forceinline__ unsigned hilbert3(unsigned c0, unsigned c1, unsigned c2, int bits)
+{
+    if (bits <= 0) return 0u;
+    unsigned X[3] = {c0, c1, c2};
+    for (unsigned Q = 1u << (bits - 1); Q > 1u; Q >>= 1) {
+        const unsigned P = Q - 1u;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (X[a] & Q) {
+                X[0] ^= P;  // reflect the low bits of axis 0
+            } else {        // exchange the low bits of axes 0 and a
+                const unsigned t = (X[0] ^ X[a]) & P;
+                X[0] ^= t;
+                X[a] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    unsigned t = 0;
+    for (unsigned Q = 1u << (bits - 1); Q > 1u; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1u;
+    X[0] ^= t;
+    X[1] ^= t;
+    X[2] ^= t;
+    return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
+}
+
+// key = instance << 30 | snake index of the cube << 3 bin | curve index in
+// the cube (at most 30 bits per instance)
+__global__ void k_morton(int n, const Inst *__restrict__ insts,
+                         const unsigned short *__restrict__ pinst,
                          const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, const double *__restrict__ mbox,
                          unsigned long long *keys, unsigned int *vals)
@@ -107,17 +166,27 @@ __global__ void k_morton(int n, const unsigned short *__restrict__ pinst,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = pinst[i];
-    const double *mb = mbox + 6 * k;
-    double v[3] = {x[i], y[i], z[i]};
-    unsigned c[3];
+    const double *mb = mbox + kKeyBox * k;
+    const int bin = (int)mb[7];
+    const double v[3] = {x[i], y[i], z[i]};
+    unsigned cube[3], w[3], nc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double t = (v[a] - mb[a]) * mb[3 + a];
-        t = fmin(fmax(t, 0.0), (double)((1 << kMortonBits) - 1));
-        c[a] = (unsigned)t;
+        nc[a] = (unsigned)mb[4 + a];
+        double t = (v[a] - mb[a]) * mb[3];
+        t = fmin(fmax(t, 0.0), ldexp((double)nc[a], bin) - 1.0);
+        const unsigned ti = (unsigned)t;
+        cube[a] = ti >> bin;
+        w[a] = ti & ((1u << bin) - 1u);
     }
-    keys[i] = ((unsigned long long)k << 30) |
-              (unsigned long long)(spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
+    // snake: layers along axis 2, rows along axis 1, reversed on odd layers
+    // and odd rows, so consecutive cubes share a face
+    const unsigned r = cube[2] * nc[1] + ((cube[2] & 1u) ? nc[1] - 1u - cube[1] : cube[1]);
+    const unsigned cidx = r * nc[0] + ((r & 1u) ? nc[0] - 1u - cube[0] : cube[0]);
+    const unsigned in = insts[k].curve == SPH_CURVE_HILBERT
+                            ? hilbert3(w[0], w[1], w[2], bin)
+                            : spread3(w[0]) | (spread3(w[1]) << 1) | (spread3(w[2]) << 2);
+    keys[i] = ((unsigned long long)k << 30) | ((unsigned long long)cidx << (3 * bin)) | in;
     vals[i] = (unsigned)i;
 }
 
@@ -618,8 +687,8 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     k_bbox_final<<<(kp.ninst + 127) / 128, 128, 0, s>>>(kp, c.inst, c.bbox_part, c.morton_box,
                                                         c.st);
     const int g = (n + 255) / 256;
-    k_morton<<<g, 256, 0, s>>>(n, c.pinst, p.x[0], p.x[1], p.x[2], c.morton_box, c.keys[0],
-                               c.vals[0]);
+    k_morton<<<g, 256, 0, s>>>(n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], c.morton_box,
+                               c.keys[0], c.vals[0]);
     const int ntiles = (n + kSortTile - 1) / kSortTile;
     int cur = 0;
     for (int pass = 0; pass < kp.key_passes; ++pass) {

@@ -48,6 +48,7 @@ constexpr int kGroupLog = 3;      // groups of up to 8 buckets
 constexpr int kWarpsPerBlock = 4; // pair kernels and walks: 4 warps per block
 constexpr int kSortItems = 8;     // keys per thread in a radix-sort tile
 constexpr int kSortTile = 256 * kSortItems;  // keys per radix-sort tile
+constexpr int kKeyBox = 8;  // doubles per instance of the key box
 constexpr int kMortonBits = 10;   // bits per axis of the Morton key (30 bits)
 constexpr int kRelistRounds = 3;  // re-walk rounds queued after the first density pass
 constexpr int kBboxChunks = 32;   // blocks per instance for open-axis bounding boxes
@@ -81,6 +82,7 @@ struct Inst {
     int goff, ng;        // groups [goff, goff + ng)
     int nbase, P, logP;  // tree nodes nbase + [1, 2P)
     int G, logG;         // buckets per group
+    int curve;           // SPH_CURVE_*
     int periodic[3];
     float L[3], invL[3];
     float gamma, alpha, beta, eps_av, eta_courant, eta_acc, n_ngb;

@@ -100,21 +100,24 @@ def _wrap(pos, lo, hi, periodic):
 
 
 def sod(seed: int = 2511, nl: int = 12, length_cells: int = 96, gamma: float = 1.4,
-        alpha: float = 1.5, beta: float = 3.0, jitter: float = 1e-3) -> Problem:
+        alpha: float = 1.5, beta: float = 3.0, jitter: float = 1e-3, dx: float = None) -> Problem:
     """Sod tube: left block length_cells x nl x nl at dx, right block at 2 dx.
 
-    Defaults give dx = 1/192, a 1/16 cross-section and N = 15,552.
+    Defaults give dx = 1/192 (each half 1/2 long), a 1/16 cross-section and
+    N = 15,552.  With dx given, each half is length_cells * dx long.
     """
     if nl % 2 or length_cells % 2:
         raise ValueError("nl and length_cells must be even")
-    dx = 0.5 / length_cells
+    if dx is None:
+        dx = 0.5 / length_cells
+    half = length_cells * dx
     L_yz = nl * dx
-    left = _lattice(length_cells, nl, nl, (-0.5, 0.0, 0.0), dx)
+    left = _lattice(length_cells, nl, nl, (-half, 0.0, 0.0), dx)
     right = _lattice(length_cells // 2, nl // 2, nl // 2, (0.0, 0.0, 0.0), 2 * dx)
     pos = np.concatenate([left, right])
     sp = np.concatenate([np.full(len(left), dx), np.full(len(right), 2 * dx)])
     pos = _jitter(pos, sp, seed, 0, jitter)
-    lo, hi, per = (-0.5, 0.0, 0.0), (0.5, L_yz, L_yz), (1, 1, 1)
+    lo, hi, per = (-half, 0.0, 0.0), (half, L_yz, L_yz), (1, 1, 1)
     pos = _wrap(pos, lo, hi, per)
     n = len(pos)
     m = np.full(n, dx ** 3)
@@ -224,16 +227,20 @@ def collision(n_total: int = 8_000_000, seed: int = 2511, gamma: float = 5.0 / 3
 
 
 def batch(n_inst: int = 256, lo_n: int = 2000, hi_n: int = 200000, seed: int = 2511):
-    """Independent sod / sedov instances with log-uniform particle counts."""
+    """Independent sod / sedov instances with log-uniform particle counts.
+
+    Even instances are Sod tubes with the 12/6 cross-section and dx = 1/192
+    whose length grows with the count (162 particles per left-lattice
+    column); odd instances are Sedov blasts on round(N^(1/3))^3 lattices."""
     idx = np.arange(n_inst, dtype=np.uint64)
     x = uniform01(seed, idx, 3)
     target = np.exp(math.log(lo_n) + x * (math.log(hi_n) - math.log(lo_n)))
     out = []
     for k in range(n_inst):
         if k % 2 == 0:
-            nx_r = max(2, int(round(target[k] / 324.0)))
-            out.append(sod(seed + k, nl=12, length_cells=2 * nx_r))
+            lc = max(2, 2 * int(round(target[k] / 324.0)))
+            out.append(sod(seed + k, nl=12, length_cells=lc, dx=1.0 / 192.0))
         else:
-            nn = max(8, int(round(target[k] ** (1.0 / 3.0))))
+            nn = max(13, int(round(target[k] ** (1.0 / 3.0))))
             out.append(sedov(n=nn, seed=seed + k))
     return out

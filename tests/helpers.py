@@ -85,3 +85,17 @@ def oracle_sampled(prob, p, sinks, hood_factor=2.2):
     assert float(np.max(h)) * 1.05 + float(np.max(h[sinks])) < R
     f = oracle.forces(p, prob.pos, prob.vel, prob.m, h, rho, om, prob.u, sinks)
     return {"h": h[sinks], "rho": rho[sinks], "omega": om[sinks], **f}
+
+
+def motion_err(xa, xb, prob):
+    """max |xa - xb| over the largest displacement of xb from the initial
+    positions of prob (minimum image on periodic axes).  Two GPU runs differ
+    by the reassociation of float atomics in the force sums, so their
+    positions agree relative to how far the particles moved, not absolutely."""
+    L = np.array(prob.box_hi) - np.array(prob.box_lo)
+    per = np.array(prob.periodic) > 0
+
+    def wrap(d):
+        return d - np.where(per, L * np.round(d / L), 0.0)
+    mv = np.max(np.abs(wrap(xb - prob.pos)))
+    return np.max(np.abs(wrap(xa - xb))) / max(mv, 1e-300)

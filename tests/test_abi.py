@@ -45,9 +45,45 @@ def test_struct_layouts_match_header(libpath):
     # sph_particles: n + 21 pointers; sph_params as laid out by a C compiler
     import paper_2511_11425_gb300 as sph
     assert ctypes.sizeof(sph.c_particles) == 8 + 21 * 8
-    assert ctypes.sizeof(sph.c_params) == 144
+    assert ctypes.sizeof(sph.c_params) == 152
     assert sph.c_params.h_rel_tol.offset == 128 and sph.c_params.list_margin.offset == 136
+    assert sph.c_params.curve.offset == 144 and sph.c_params.group_log.offset == 148
     assert ctypes.sizeof(sph.c_stats) == 112
+
+
+def test_struct_offsets_agree_with_the_c_compiler(tmp_path):
+    """Every member offset of the ctypes mirrors equals the one gcc gives the
+    header's structs (catches a member added to one side only)."""
+    import shutil
+    import subprocess
+    import paper_2511_11425_gb300 as sph
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    mirrors = {"sph_params": sph.c_params, "sph_particles": sph.c_particles,
+               "sph_stats": sph.c_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", "#include \"sph.h\"",
+             "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "off.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "off"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            c, f, v = line.split()
+            got[(c, f)] = int(v)
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
 
 
 def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
@@ -58,3 +94,5 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
         sph.sph_create(sph.Params(box_hi=(0.0, 1.0, 1.0)), 10)
     with pytest.raises(sph.SphError):
         sph.sph_create(sph.Params(max_newton=0), 10)
+    with pytest.raises(sph.SphError):
+        sph.sph_create(sph.Params(group_log=4), 10)

@@ -10,7 +10,7 @@
 import numpy as np
 import pytest
 
-from helpers import norm_err, to_input_order
+from helpers import motion_err, norm_err, to_input_order
 from paper_2511_11425_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -25,23 +25,6 @@ def sph():
     return m
 
 
-def _concat(sph, probs):
-    import torch
-    n = sum(p.n for p in probs)
-    parts = sph.Particles(n, "cuda:0")
-    off = 0
-    for p in probs:
-        sl = slice(off, off + p.n)
-        for a in range(3):
-            parts.t["x%d" % a][sl] = torch.from_numpy(p.pos[:, a].copy())
-            parts.t["v%d" % a][sl] = torch.from_numpy(p.vel[:, a].copy())
-        parts.t["u"][sl] = torch.from_numpy(p.u.copy())
-        parts.t["m"][sl] = torch.from_numpy(p.m.astype(np.float32))
-        parts.t["h"][sl] = torch.from_numpy(p.h0.astype(np.float32))
-        off += p.n
-    return parts
-
-
 def _problems():
     return [inputs.sod(length_cells=24, seed=1),
             inputs.sedov(n=14, seed=2),
@@ -52,8 +35,8 @@ def _problems():
 def test_batch_steps_like_separate_problems(sph):
     probs = _problems()
     params = [sph.Params.for_problem(p) for p in probs]
-    offs = np.cumsum([0] + [p.n for p in probs])
-    parts = _concat(sph, probs)
+    parts, offs = sph.Particles.from_problems(probs, "cuda:0")
+    assert list(offs) == list(np.cumsum([0] + [p.n for p in probs]))
     ctx = sph.sph_batch_create(params, offs)
     try:
         for _ in range(3):
@@ -78,9 +61,7 @@ def test_batch_steps_like_separate_problems(sph):
         sl = slice(offs[k], offs[k + 1])
         assert abs(dts[k] - dt) <= 1e-5 * dt, (k, dts[k], dt)
         L = np.array(p.box_hi) - np.array(p.box_lo)
-        dx = g["x"][sl] - one["x"]
-        dx -= np.where(np.array(p.periodic) > 0, L * np.round(dx / L), 0.0)
-        assert np.max(np.abs(dx)) < 1e-9 * np.max(L), k
+        assert motion_err(g["x"][sl], one["x"], p) < 1e-5, k
         assert norm_err(g["a"][sl], one["a"]) < 1e-5, k
         assert np.max(np.abs(g["h"][sl] - one["h"]) / one["h"]) < 1e-5, k
         # mass and energies agree closely; momentum and angular momentum are
@@ -113,7 +94,38 @@ def test_graph_replay_matches_plain_steps(sph):
         a.close()
         b.close()
     assert np.allclose(dta, dtb, rtol=1e-5)
-    assert np.max(np.abs(ga["x"] - gb["x"])) < 1e-9
+    assert motion_err(gb["x"], ga["x"], prob) < 1e-5
     assert norm_err(gb["v"], ga["v"]) < 1e-5
     assert norm_err(gb["a"], ga["a"]) < 1e-5
     assert launches > 0
+
+
+def test_batch_simulation_graph_matches_plain_batch(sph):
+    """BatchSimulation replaying a captured step advances every instance like
+    plain batch steps (same step sizes, same state)."""
+    import torch
+    probs = _problems()
+    stream = torch.cuda.Stream()
+    a = sph.BatchSimulation(probs)
+    b = sph.BatchSimulation(probs)
+    try:
+        with torch.cuda.stream(stream):
+            da = [a.step(0.0, stream) for _ in range(3)]
+            db = [b.step(0.0, stream)]
+            b.capture(stream)
+            db += [b.step() for _ in range(2)]
+        stream.synchronize()
+        ga = to_input_order(a.parts.numpy())
+        gb = to_input_order(b.parts.numpy())
+        ca = np.array(a.conserved()).reshape(len(probs), 9)
+        cb = np.array(b.conserved()).reshape(len(probs), 9)
+    finally:
+        a.close()
+        b.close()
+    assert np.allclose(np.array(da), np.array(db), rtol=1e-5)
+    assert np.allclose(a.t, b.t, rtol=1e-5)
+    for k, p in enumerate(probs):
+        sl = slice(a.offsets[k], a.offsets[k + 1])
+        assert motion_err(gb["x"][sl], ga["x"][sl], p) < 1e-5, k
+    assert norm_err(gb["a"], ga["a"]) < 1e-5
+    assert np.allclose(ca[:, [0, 7, 8]], cb[:, [0, 7, 8]], rtol=1e-6)
