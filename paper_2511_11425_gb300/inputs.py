@@ -244,3 +244,17 @@ def batch(n_inst: int = 256, lo_n: int = 2000, hi_n: int = 200000, seed: int = 2
             nn = max(13, int(round(target[k] ** (1.0 / 3.0))))
             out.append(sedov(n=nn, seed=seed + k))
     return out
+
+
+def mlp_init(seed: int = 2511, n_in: int = 4, n_hid: int = 32) -> np.ndarray:
+    """Initial parameters of the seed network as one flat float64 vector in
+    the order W1 (n_hid x n_in), b1, W2 (n_hid x n_hid), b2, W3 (n_hid), b3:
+    hidden weights uniform in +-sqrt(6 / fan_in) (He et al. 2015), biases and
+    the output layer zero, so the untrained network outputs exactly 0."""
+    def he(count, fan_in, stream):
+        u = uniform01(seed, np.arange(count, dtype=np.uint64), stream)
+        return (2.0 * u - 1.0) * math.sqrt(6.0 / fan_in)
+    W1 = he(n_hid * n_in, n_in, 0)
+    W2 = he(n_hid * n_hid, n_hid, 1)
+    return np.concatenate([W1, np.zeros(n_hid), W2, np.zeros(n_hid), np.zeros(n_hid),
+                           np.zeros(1)])
