@@ -296,6 +296,82 @@ def forms_batch(dev, steps, warmup):
     return out
 
 
+def forms_learned(dev, n_total=8_000_000, nrec=10, ncmp=20, tol=1e-5):
+    """The learned seed against the continuity seed on the colliding-spheres
+    workload: record `nrec` plain steps, train the network on the GPU, then
+    run the same `ncmp` steps from the same state both ways."""
+    import torch
+    import paper_2511_11425_gb300 as sph
+    from paper_2511_11425_gb300 import inputs
+
+    prob = inputs.collision(n_total=n_total)
+    params = sph.Params.for_problem(prob, h_rel_tol=tol)
+    s = torch.cuda.current_stream(dev)
+    sim = sph.Simulation(prob, params, device=dev)
+    ref = sph.Simulation(prob, params, device=dev)
+    out = {"workload": "two colliding 1/r gas spheres (radii 1 and 0.5, Mach 3, impact "
+                       "parameter 0.5), hydro only, open boundaries",
+           "particles": prob.n, "h_rel_tol": tol, "record_steps": nrec, "compare_steps": ncmp}
+    try:
+        sim.step(0.0, s)
+        sph.sph_mlp_record(sim.ctx, True, capacity=4 << 20,
+                           stride=max(1, prob.n * nrec // (4 << 20)))
+        for _ in range(nrec):
+            dt = sim.step(0.0, s)
+        sph.sph_mlp_record(sim.ctx, False)
+        out["samples"] = sph.sph_mlp_samples(sim.ctx)
+        sph.sph_mlp_set_weights(sim.ctx, inputs.mlp_init(3))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        l0, _ = sph.sph_mlp_train(sim.ctx, 2000, batch=8192, lr=2e-3, seed=1, stream=s)
+        _, l1 = sph.sph_mlp_train(sim.ctx, 2000, batch=8192, lr=5e-4, seed=2, stream=s)
+        out["train"] = {"adam_steps": 4000, "batch": 8192, "ms": 1e3 * (time.perf_counter() - t0),
+                        "loss_first": l0, "loss_last": l1}
+        for k, v in sim.parts.t.items():
+            ref.parts.t[k].copy_(v)
+        sph.sph_set_dt_old(ref.ctx, dt)
+        sph.sph_mlp_set_seed_mode(sim.ctx, "mlp")
+        for name, m in (("continuity_seed", ref), ("learned_seed", sim)):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(ncmp)]
+            it = kd = 0.0
+            pairs = 0
+            for k in range(ncmp):
+                ev[k][0].record(s)
+                sph.sph_step(m.ctx, m.parts, 0.0, s)
+                ev[k][1].record(s)
+                st = sph.sph_get_stats(m.ctx)
+                kd += st["ms_density_kernel"]
+                pairs += st["density_pairs"]
+                it += float(m.parts.t["iters"].float().mean())
+            torch.cuda.synchronize(dev)
+            ms = sum(a.elapsed_time(b) for a, b in ev)
+            out[name] = {"ms_per_step": ms / ncmp, "density_kernel_ms_per_step": kd / ncmp,
+                         "newton_passes_per_particle": it / ncmp,
+                         "density_pair_evaluations_per_step": pairs / ncmp}
+        a = ref.parts.numpy()
+        b = sim.parts.numpy()
+        oa = np.argsort(a["id"])
+        ob = np.argsort(b["id"])
+
+        def rel(f):
+            return float(np.max(np.abs(b[f][ob].astype(np.float64) /
+                                       a[f][oa].astype(np.float64) - 1.0)))
+        acc_a = np.stack([a["a%d" % i][oa] for i in range(3)], 1).astype(np.float64)
+        acc_b = np.stack([b["a%d" % i][ob] for i in range(3)], 1).astype(np.float64)
+        out["field_error_vs_continuity_seed"] = {
+            "h_max_rel": rel("h"), "rho_max_rel": rel("rho"), "u_max_rel": rel("u"),
+            "a_max_over_max_norm": float(np.max(np.abs(acc_b - acc_a)) / np.max(np.abs(acc_a)))}
+        out["passes_saved"] = 1.0 - (out["learned_seed"]["newton_passes_per_particle"] /
+                                     out["continuity_seed"]["newton_passes_per_particle"])
+        out["step_speedup"] = (out["continuity_seed"]["ms_per_step"] /
+                               out["learned_seed"]["ms_per_step"])
+    finally:
+        sim.close()
+        ref.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2511_11425_gb300 as sph
@@ -395,7 +471,10 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
     forms = None
     if world == 1 and not args.no_forms:
-        forms = forms_batch(dev, max(2, min(args.steps, 5)), max(args.warmup, 3))
+        forms = {"batch": forms_batch(dev, max(2, min(args.steps, 5)), max(args.warmup, 3))}
+        torch.cuda.empty_cache()
+        forms["learned"] = forms_learned(dev)
+        torch.cuda.empty_cache()
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)

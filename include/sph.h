@@ -302,6 +302,105 @@ sph_status sph_batch_get_dt(const sph_ctx *ctx, double *out);
  */
 sph_status sph_reduce_conserved_noalloc(const sph_particles *p, double *out, void *stream);
 
+/* ---- learned smoothing-length seed --------------------------------------
+ * The Newton iteration for h (Sec. 2.3.3) needs a starting value; the paper
+ * does not say where it starts.  By default sph_kdk_step leaves each
+ * particle's h at the continuity estimate h exp(dt divv / 3).  The paper has
+ * no counterpart for the alternative below: a 4-32-32-1 ReLU network, run
+ * on the tensor cores with bfloat16 weights and FP32 accumulation inside the
+ * kick-drift-kick, proposes a correction y, and
+ *     h_seed = h exp(phi0 + y / 100), factor clamped to [1/2, 2],
+ * except where |phi0| and |phi2| are both below h_rel_tol (the last seed was
+ * within the Newton tolerance and the continuity estimate moves h by less)
+ * or where |y| / 100 is below the root-mean-square residual of the last
+ * training call (the network's own fit error): there y is not applied.
+ * The iteration still runs to h_rel_tol from that seed, so the converged h
+ * does not depend on the network.
+ * Features of particle i at the end of a step (dt = new step, dt_old = last):
+ *     phi0 = dt divv_i / 3,  phi1 = nngb_i / n_ngb - 1,
+ *     phi2 = ln(h_i / seed_i) (seed_i = start of this step's iteration),
+ *     phi3 = ln(dt / dt_old) (0 on the first step);
+ * network inputs x = (100 phi0, 4 phi1, 100 phi2, 10 phi3).  Training
+ * samples (x, y*) pair the inputs with y* = 100 (ln(h_new / h) - phi0),
+ * h_new being what the next density pass converges to.
+ * Parameters: SPH_MLP_NPARAM floats in the order W1 (32 x 4, row-major by
+ * hidden unit), b1 (32), W2 (32 x 32), b2 (32), W3 (32), b3 (1); the master
+ * copy is FP32, the inference copy bfloat16 (round to nearest even).  One
+ * network per context (shared by the instances of a batch).
+ */
+#define SPH_MLP_NPARAM 1249
+enum { SPH_SEED_ANALYTIC = 0, SPH_SEED_MLP = 1 };
+
+/* sph_mlp_set_weights / sph_mlp_get_weights: copy the FP32 master
+ * parameters from / to a HOST array of count == SPH_MLP_NPARAM floats
+ * (SPH_ERR_ARG otherwise).  Setting resets the Adam moments and step count
+ * and refreshes the bfloat16 copy.  Both synchronise the device. */
+sph_status sph_mlp_set_weights(sph_ctx *ctx, const float *w, int64_t count);
+sph_status sph_mlp_get_weights(sph_ctx *ctx, float *w, int64_t count);
+
+/* sph_mlp_set_seed_mode: SPH_SEED_ANALYTIC (default) or SPH_SEED_MLP for
+ * the seeds written by later kick-drift-kick steps (a captured graph keeps
+ * the mode it was captured with). */
+sph_status sph_mlp_set_seed_mode(sph_ctx *ctx, int32_t mode);
+
+/* sph_mlp_record: on != 0 starts collecting training samples from the
+ * steps that follow: every kick-drift-kick stores the inputs x of its
+ * particles (they move with the particles), and the next density pass turns
+ * those particles whose hash of (index, step) is 0 modulo `stride` into
+ * samples.  Samples whose |ln(h_new / h)| exceeds ln 2 are skipped.  The
+ * device ring buffer holds `capacity` samples (the oldest are overwritten);
+ * it is allocated here (synchronous).  on == 0 stops recording and keeps the
+ * samples.  SPH_ERR_ARG for capacity < 1 or stride < 1 when on != 0. */
+sph_status sph_mlp_record(sph_ctx *ctx, int32_t on, int64_t capacity, int32_t stride);
+
+/* sph_mlp_samples: number of samples held (synchronises the device). */
+sph_status sph_mlp_samples(sph_ctx *ctx, int64_t *count);
+
+/* sph_mlp_get_samples: copy the first n samples held into HOST arrays x
+ * (n x 4 floats) and y (n floats); SPH_ERR_ARG if fewer are held.  The ring
+ * buffer keeps no order beyond the slots the recording passes wrote. */
+sph_status sph_mlp_get_samples(sph_ctx *ctx, float *x, float *y, int64_t n);
+
+/* sph_mlp_load_samples: replace the samples by n DEVICE pairs: x (n x 4
+ * floats, row-major), y (n floats).  The buffer grows to n if needed. */
+sph_status sph_mlp_load_samples(sph_ctx *ctx, const float *x, const float *y, int64_t n,
+                                void *stream);
+
+/* sph_mlp_train: `iters` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8,
+ * learning rate lr) on the mean squared error over minibatches of `batch`
+ * samples drawn uniformly with replacement from the samples held (counter-
+ * based SplitMix64 on seed); batch <= 0 or >= the number held takes every
+ * sample in order (full batch).  Gradients come from FP32 forward and
+ * backward kernels and are summed in a fixed order.  Refreshes the bfloat16
+ * copy at the end and synchronises; loss_first / loss_last (HOST, may be
+ * NULL) receive the minibatch loss of the first and the last step, and
+ * sqrt(last loss) / 100 becomes the dead zone of the correction
+ * (sph_mlp_set_weights resets it to 0).
+ * SPH_ERR_STATE when no samples are held. */
+sph_status sph_mlp_train(sph_ctx *ctx, int32_t iters, int32_t batch, double lr, uint64_t seed,
+                         double *loss_first, double *loss_last, void *stream);
+
+/* sph_mlp_grad: mean squared error of the FP32 master network over n DEVICE
+ * samples (x: n x 4 floats row-major, y: n floats) and its gradient, into
+ * HOST arrays grad (SPH_MLP_NPARAM floats) and loss (1 double); sums in a
+ * fixed order, synchronous.  Changes no state. */
+sph_status sph_mlp_grad(sph_ctx *ctx, const float *x, const float *y, int64_t n, float *grad,
+                        double *loss, void *stream);
+
+/* sph_mlp_infer: network outputs y (n DEVICE floats) for inputs x (n x 4
+ * DEVICE floats, row-major) through the bfloat16 tensor-core path the seed
+ * uses.  Asynchronous on stream. */
+sph_status sph_mlp_infer(sph_ctx *ctx, const float *x, int64_t n, float *y, void *stream);
+
+/* sph_bucket_layout: the bucket slots of the last sph_build_cells, for
+ * inspection.  Slot b holds particles [first[b], first[b + 1]) (in the order
+ * sph_build_cells left them; an empty range is a padding slot); slots of
+ * instance k are contiguous, groups are runs of 2^group_log slots.  first
+ * is a HOST array of cap entries; *nslots receives the number of slots
+ * (first needs nslots + 1 entries, SPH_ERR_ARG otherwise).  Synchronous.
+ * The paper has no counterpart (it is a view of the data layout). */
+sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t cap, int64_t *nslots);
+
 /* sph_set_dt_old: set the previous step size used by the predictor and the
  * closing kick (0 restarts the integration as at t = 0). */
 sph_status sph_set_dt_old(sph_ctx *ctx, double dt_old);

@@ -17,7 +17,10 @@ features of particle i at the end of step n (dt = new step, dt_old = last):
     phi3 = ln(dt / dt_old)            step-size change (0 on the first step)
 network input  x = (100 phi0, 4 phi1, 100 phi2, 10 phi3)
 network        y = W3 . relu(W2 relu(W1 x + b1) + b2) + b3     (4 -> 32 -> 32 -> 1)
-seed           h_seed = h_n * clamp(exp(phi0 + y / 100), 1/2, 2)
+seed           h_seed = h_n * clamp(exp(phi0 + y / 100), 1/2, 2), with y taken
+               as 0 where |phi0| and |phi2| are both below the Newton
+               tolerance (the estimate is already converged there) or where
+               |y| / 100 is below the dead zone sqrt(training loss) / 100
 training target y* = 100 (ln(h_{n+1} / h_n) - phi0), loss = mean (y - y*)^2,
 optimiser Adam (Kingma & Ba 2015) with bias correction.
 
@@ -134,10 +137,15 @@ def infer_bf16(w, X):
     return a2 @ bf16(W3) + b3
 
 
-def seed(h, X, y):
-    """h_seed from the previous h, the inputs X and the network output y."""
-    phi0 = np.asarray(X)[:, 0] / X_SCALE[0]
-    f = np.exp(phi0 + np.asarray(y) / Y_SCALE)
+def seed(h, X, y, tol=1e-6, dead=0.0):
+    """h_seed from the previous h, the inputs X and the network output y
+    (tol = the Newton tolerance on |dh|/h, dead = the dead zone in ln h)."""
+    X = np.asarray(X)
+    y = np.asarray(y, dtype=np.float64)
+    phi0 = X[:, 0] / X_SCALE[0]
+    rest = (np.abs(phi0) < tol) & (np.abs(X[:, 2] / X_SCALE[2]) < tol)
+    y = np.where(rest | (np.abs(y / Y_SCALE) < dead), 0.0, y)
+    f = np.exp(phi0 + y / Y_SCALE)
     return np.asarray(h) * np.clip(f, 0.5, 2.0)
 
 

@@ -30,7 +30,12 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
            "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
            "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
-           "sph_graph_capture", "sph_graph_launch")
+           "sph_graph_capture", "sph_graph_launch", "sph_mlp_set_weights", "sph_mlp_get_weights",
+           "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
+           "sph_mlp_load_samples", "sph_bucket_layout",
+           "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
+MLP_NPARAM = 1249
+SEED_MODES = {"analytic": 0, "mlp": 1}
 
 
 class SphError(RuntimeError):
@@ -100,6 +105,19 @@ def lib():
         L.sph_graph_capture.argtypes = [vp, pp, dbl, vp]
         L.sph_graph_launch.argtypes = [vp, C.POINTER(dbl), vp]
         L.sph_set_dt_old.argtypes = [vp, dbl]
+        fp = C.POINTER(C.c_float)
+        L.sph_mlp_set_weights.argtypes = [vp, fp, i64]
+        L.sph_mlp_get_weights.argtypes = [vp, fp, i64]
+        L.sph_mlp_set_seed_mode.argtypes = [vp, C.c_int32]
+        L.sph_mlp_record.argtypes = [vp, C.c_int32, i64, C.c_int32]
+        L.sph_mlp_samples.argtypes = [vp, C.POINTER(i64)]
+        L.sph_mlp_get_samples.argtypes = [vp, fp, fp, i64]
+        L.sph_mlp_load_samples.argtypes = [vp, vp, vp, i64, vp]
+        L.sph_mlp_train.argtypes = [vp, C.c_int32, C.c_int32, dbl, C.c_uint64, C.POINTER(dbl),
+                                    C.POINTER(dbl), vp]
+        L.sph_mlp_grad.argtypes = [vp, vp, vp, i64, fp, C.POINTER(dbl), vp]
+        L.sph_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
+        L.sph_bucket_layout.argtypes = [vp, C.POINTER(C.c_int32), i64, C.POINTER(i64)]
         L.sph_get_stats.argtypes = [vp, C.POINTER(c_stats)]
         L.sph_last_error.argtypes = [vp]
         L.sph_last_error.restype = C.c_char_p
@@ -365,6 +383,101 @@ def sph_reduce_conserved_noalloc(parts: Particles, out, stream=None):
     s = parts.c()
     _check(None, lib().sph_reduce_conserved_noalloc(C.byref(s), C.c_void_p(out.data_ptr()),
                                                     _stream(stream)))
+
+
+# ---- learned seed of the h iteration -----------------------------------------
+def sph_mlp_set_weights(ctx, w):
+    """Set the FP32 master parameters (MLP_NPARAM values); resets Adam."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.float32).ravel())
+    _check(ctx, lib().sph_mlp_set_weights(ctx, a.ctypes.data_as(C.POINTER(C.c_float)), a.size))
+
+
+def sph_mlp_get_weights(ctx):
+    import numpy as np
+    a = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check(ctx, lib().sph_mlp_get_weights(ctx, a.ctypes.data_as(C.POINTER(C.c_float)), a.size))
+    return a
+
+
+def sph_mlp_set_seed_mode(ctx, mode):
+    m = SEED_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(ctx, lib().sph_mlp_set_seed_mode(ctx, m))
+
+
+def sph_mlp_record(ctx, on=True, capacity=1 << 20, stride=1):
+    _check(ctx, lib().sph_mlp_record(ctx, 1 if on else 0, int(capacity), int(stride)))
+
+
+def sph_mlp_samples(ctx) -> int:
+    n = C.c_int64()
+    _check(ctx, lib().sph_mlp_samples(ctx, C.byref(n)))
+    return n.value
+
+
+def sph_mlp_get_samples(ctx, n=None):
+    """Host copies (x (n, 4), y (n,)) of the first n samples held (all by default)."""
+    import numpy as np
+    if n is None:
+        n = sph_mlp_samples(ctx)
+    x = np.zeros((n, 4), dtype=np.float32)
+    y = np.zeros(n, dtype=np.float32)
+    _check(ctx, lib().sph_mlp_get_samples(ctx, x.ctypes.data_as(C.POINTER(C.c_float)),
+                                          y.ctypes.data_as(C.POINTER(C.c_float)), int(n)))
+    return x, y
+
+
+def sph_mlp_load_samples(ctx, x, y, stream=None):
+    """x: (n, 4) float32 device tensor, y: (n,) float32 device tensor."""
+    x = x.contiguous()
+    y = y.contiguous()
+    _check(ctx, lib().sph_mlp_load_samples(ctx, C.c_void_p(x.data_ptr()),
+                                           C.c_void_p(y.data_ptr()), int(y.numel()),
+                                           _stream(stream)))
+
+
+def sph_mlp_train(ctx, iters, batch=0, lr=1e-3, seed=0, stream=None):
+    """Adam steps on the samples held; returns (first loss, last loss)."""
+    l0 = C.c_double()
+    l1 = C.c_double()
+    _check(ctx, lib().sph_mlp_train(ctx, int(iters), int(batch), float(lr), int(seed),
+                                    C.byref(l0), C.byref(l1), _stream(stream)))
+    return l0.value, l1.value
+
+
+def sph_mlp_grad(ctx, x, y, stream=None):
+    """(gradient as numpy float32, loss) of the master network on device samples."""
+    import numpy as np
+    x = x.contiguous()
+    y = y.contiguous()
+    g = np.zeros(MLP_NPARAM, dtype=np.float32)
+    loss = C.c_double()
+    _check(ctx, lib().sph_mlp_grad(ctx, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                   int(y.numel()), g.ctypes.data_as(C.POINTER(C.c_float)),
+                                   C.byref(loss), _stream(stream)))
+    return g, loss.value
+
+
+def sph_mlp_infer(ctx, x, out=None, stream=None):
+    """Network outputs for the (n, 4) float32 device tensor x (tensor-core path)."""
+    import torch
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(ctx, lib().sph_mlp_infer(ctx, C.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                    C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def sph_bucket_layout(ctx):
+    """First particle of every bucket slot (plus the end sentinel), numpy int32."""
+    import numpy as np
+    ns = C.c_int64()
+    lib().sph_bucket_layout(ctx, None, 0, C.byref(ns))
+    first = np.zeros(ns.value + 1, dtype=np.int32)
+    _check(ctx, lib().sph_bucket_layout(ctx, first.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        first.size, C.byref(ns)))
+    return first
 
 
 def sph_set_dt_old(ctx, dt_old: float):

@@ -136,7 +136,7 @@ Sizes layout_sizes(const std::vector<int64_t> &counts, const std::vector<sph_par
     Sizes z;
     for (size_t k = 0; k < counts.size(); ++k) {
         const int64_t nk = counts[k];
-        const int64_t nb = (nk + kBucket - 1) / kBucket;
+        const int64_t nb = bucket_slots(nk);
         const int logP = ilog2_ceil(std::max<int64_t>(nb, 1));
         const int64_t P = (int64_t)1 << logP;
         const int logG = group_log(prm[k], logP);
@@ -183,8 +183,10 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
         AL(t, (size_t)112 * np);
         c.tmp = t;
     }
-    AL(c.bstart, nb);
+    AL(c.bstart, nb + 1);
     AL(c.binst, nb);
+    AL(c.pad_agg, (np + kPadTile - 1) / kPadTile);
+    AL(c.pad_used, ninst);
     AL(c.origin, (size_t)3 * nb);
     AL(c.gfirst, ng);
     AL(c.gflag, ng);
@@ -224,11 +226,16 @@ void free_ctx(Ctx &c)
     if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
     if (c.graph) cudaGraphDestroy(c.graph);
     void *ptrs[] = {c.st, c.inst, c.dts, c.dtmin, c.morton_box, c.bbox_part, c.cons_part,
+                    c.pad_agg, c.pad_used,
                     c.cons_out, c.pinst, c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist,
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
                     c.list_cnt, c.list, c.redo, c.node, c.refit, c.pm, c.fpos, c.fvel, c.fth,
                     c.acc, c.acc2, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
+        if (p) cudaFree(p);
+    void *mptrs[] = {c.mlp.w, c.mlp.m, c.mlp.v, c.mlp.frag, c.mlp.gpart, c.mlp.loss,
+                     c.mlp.seed0, c.mlp.tfeat, c.mlp.th, c.mlp.sx, c.mlp.sy, c.mlp.scount};
+    for (void *p : mptrs)
         if (p) cudaFree(p);
     for (void *p : {(void *)c.st_host, (void *)c.dts_host, (void *)c.cons_host})
         if (p) cudaFreeHost(p);
@@ -252,7 +259,7 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
         const int64_t nk = counts[k];
         I.off = (int)off;
         I.n = (int)nk;
-        I.nb = (int)((nk + kBucket - 1) / kBucket);
+        I.nb = (int)bucket_slots(nk);
         I.boff = (int)boff;
         I.logP = ilog2_ceil(std::max(I.nb, 1));
         I.P = 1 << I.logP;
@@ -262,8 +269,8 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
         I.goff = (int)goff;
         I.nbase = (int)nbase;
         for (int a = 0; a < 3; ++a) any_open = any_open || !I.periodic[a];
-        for (int b = 0; b < I.nb; ++b) {
-            bstart.push_back(I.off + b * kBucket);
+        for (int b = 0; b < I.nb; ++b) {  // plain chunks until the first build
+            bstart.push_back((int)std::min<int64_t>(I.off + (int64_t)b * kBucket, I.off + nk));
             binst.push_back(k);
         }
         for (int g = 0; g < I.ng; ++g) gfirst.push_back(I.boff + (g << I.logG));
@@ -283,6 +290,7 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
         goff += I.ng;
         nbase += 2 * (int64_t)I.P;
     }
+    bstart.push_back((int)off);  // sentinel: one past the last slot
     std::vector<RefitBlock> sched;
     c.refit_band.clear();
     for (auto &b : bands) {
@@ -317,6 +325,8 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
         CK(cudaMemcpy(c.refit, sched.data(), sizeof(RefitBlock) * sched.size(),
                       cudaMemcpyHostToDevice));
     c.n_built = off;
+    // records of the last kick belong to the old layout
+    if (c.mlp.th) CK(cudaMemset(c.mlp.th, 0, sizeof(float) * (size_t)c.capacity));
     return SPH_OK;
 }
 
@@ -401,6 +411,10 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
     const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC && c.rho_valid;
     if (isen) CK(cudaMemcpyAsync(c.rho_old, p->rho, bytes, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c.h_seed, h_seed ? h_seed : p->h, bytes, cudaMemcpyDeviceToDevice, s));
+    // the learned seed's inputs compare h with the seed as given (re-walks
+    // overwrite c.h_seed)
+    if (c.mlp.seed0 && (c.mlp.record || c.mlp.seed_mode == SPH_SEED_MLP))
+        CK(cudaMemcpyAsync(c.mlp.seed0, c.h_seed, bytes, cudaMemcpyDeviceToDevice, s));
     if (timed) CK(cudaEventRecord(c.kev[0], s));
     CK(launch_walk(c, *p, WALK_DENSITY, -1, c.h_seed, s));
     if (timed) CK(cudaEventRecord(c.kev[1], s));
@@ -412,6 +426,7 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
         CK(launch_walk(c, *p, WALK_DENSITY, r, c.h_seed, s));
         CK(launch_density(c, *p, c.h_seed, r, 0, 0, nullptr, nullptr, s));
     }
+    if (c.mlp.record) CK(launch_mlp_harvest(c, *p, s));
     if (isen) CK(launch_isentropic(c, *p, s));
     CK(launch_bob_refit(c, *p, s));
     return SPH_OK;
@@ -857,6 +872,273 @@ extern "C" sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p,
     rc = finish(ctx, s);
     if (rc == SPH_OK) std::memcpy(out, c.cons_host, sizeof(double) * 9 * c.kp.ninst);
     return rc;
+}
+
+// ---- learned seed -------------------------------------------------------------
+namespace {
+// network buffers (zero weights = the continuity estimate) on first use
+sph_status ensure_mlp(Ctx &c)
+{
+    if (c.mlp.w) return SPH_OK;
+    CK(dalloc(&c.mlp.w, kMlpParams));
+    CK(dalloc(&c.mlp.m, kMlpParams));
+    CK(dalloc(&c.mlp.v, kMlpParams));
+    CK(dalloc(&c.mlp.frag, kMlpFragWords));
+    CK(dalloc(&c.mlp.scount, 1));
+    CK(dalloc(&c.mlp.seed0, (size_t)std::max<int64_t>(c.capacity, 1)));
+    CK(cudaMemset(c.mlp.seed0, 0, sizeof(float) * (size_t)std::max<int64_t>(c.capacity, 1)));
+    CK(cudaMemset(c.mlp.w, 0, sizeof(float) * kMlpParams));
+    CK(cudaMemset(c.mlp.m, 0, sizeof(float) * kMlpParams));
+    CK(cudaMemset(c.mlp.v, 0, sizeof(float) * kMlpParams));
+    CK(cudaMemset(c.mlp.scount, 0, sizeof(unsigned long long)));
+    CK(launch_mlp_pack(c, nullptr));
+    CK(cudaDeviceSynchronize());
+    return SPH_OK;
+}
+
+// sample buffer of at least `cap` samples (contents dropped when it grows)
+sph_status ensure_samples(Ctx &c, int64_t cap)
+{
+    if (c.mlp.sx && c.mlp.cap >= cap) return SPH_OK;
+    CK(cudaDeviceSynchronize());
+    if (c.mlp.sx) cudaFree(c.mlp.sx);
+    if (c.mlp.sy) cudaFree(c.mlp.sy);
+    c.mlp.sx = c.mlp.sy = nullptr;
+    c.mlp.cap = 0;
+    CK(dalloc(&c.mlp.sx, (size_t)cap * 4));
+    CK(dalloc(&c.mlp.sy, (size_t)cap));
+    CK(cudaMemset(c.mlp.scount, 0, sizeof(unsigned long long)));
+    c.mlp.cap = cap;
+    return SPH_OK;
+}
+
+sph_status ensure_grad_space(Ctx &c, long long batch, int iters)
+{
+    const int nb = mlp_grad_blocks(batch);
+    if (c.mlp.gpart_blocks < nb) {
+        if (c.mlp.gpart) cudaFree(c.mlp.gpart);
+        c.mlp.gpart = nullptr;
+        c.mlp.gpart_blocks = 0;
+        CK(dalloc(&c.mlp.gpart, (size_t)nb * (kMlpParams + 1)));
+        c.mlp.gpart_blocks = nb;
+    }
+    if (c.mlp.loss_cap < iters) {
+        if (c.mlp.loss) cudaFree(c.mlp.loss);
+        c.mlp.loss = nullptr;
+        c.mlp.loss_cap = 0;
+        CK(dalloc(&c.mlp.loss, (size_t)iters));
+        c.mlp.loss_cap = iters;
+    }
+    return SPH_OK;
+}
+
+int64_t samples_held(Ctx &c)
+{
+    unsigned long long cnt = 0;
+    if (cudaMemcpy(&cnt, c.mlp.scount, sizeof cnt, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    return (int64_t)(cnt < (unsigned long long)c.mlp.cap ? cnt : (unsigned long long)c.mlp.cap);
+}
+}  // namespace
+
+extern "C" sph_status sph_mlp_set_weights(sph_ctx *ctx, const float *w, int64_t count)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!w || count != kMlpParams)
+        return failf(c, SPH_ERR_ARG, "sph_mlp_set_weights needs %d floats", kMlpParams);
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(c.mlp.w, w, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
+    CK(cudaMemset(c.mlp.m, 0, sizeof(float) * kMlpParams));
+    CK(cudaMemset(c.mlp.v, 0, sizeof(float) * kMlpParams));
+    c.mlp.t = 0;
+    c.mlp.dead = 0.f;
+    CK(launch_mlp_pack(c, nullptr));
+    CK(cudaDeviceSynchronize());
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_get_weights(sph_ctx *ctx, float *w, int64_t count)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!w || count != kMlpParams)
+        return failf(c, SPH_ERR_ARG, "sph_mlp_get_weights needs %d floats", kMlpParams);
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(w, c.mlp.w, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_set_seed_mode(sph_ctx *ctx, int32_t mode)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (mode != SPH_SEED_ANALYTIC && mode != SPH_SEED_MLP)
+        return failf(c, SPH_ERR_ARG, "unknown seed mode %d", mode);
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    c.mlp.seed_mode = mode;
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_record(sph_ctx *ctx, int32_t on, int64_t capacity, int32_t stride)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!on) {
+        c.mlp.record = false;
+        return SPH_OK;
+    }
+    if (capacity < 1 || stride < 1)
+        return failf(c, SPH_ERR_ARG, "sph_mlp_record: capacity and stride must be >= 1");
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    if (!c.mlp.th) {
+        CK(dalloc(&c.mlp.tfeat, (size_t)c.capacity * 4));
+        CK(dalloc(&c.mlp.th, (size_t)c.capacity));
+    }
+    rc = ensure_samples(c, capacity);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(c.mlp.th, 0, sizeof(float) * (size_t)std::max<int64_t>(c.capacity, 1)));
+    c.mlp.stride = stride;
+    c.mlp.record = true;
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_samples(sph_ctx *ctx, int64_t *count)
+{
+    if (!ctx || !count) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    *count = 0;
+    if (!c.mlp.sx) return SPH_OK;
+    CK(cudaDeviceSynchronize());
+    const int64_t k = samples_held(c);
+    if (k < 0) return failf(c, SPH_ERR_CUDA, "sph_mlp_samples: read-back failed");
+    *count = k;
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_get_samples(sph_ctx *ctx, float *x, float *y, int64_t n)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (n < 0 || (n > 0 && (!x || !y))) return failf(c, SPH_ERR_ARG, "sph_mlp_get_samples");
+    if (n == 0) return SPH_OK;
+    if (!c.mlp.sx) return failf(c, SPH_ERR_ARG, "sph_mlp_get_samples: no samples");
+    CK(cudaDeviceSynchronize());
+    if (n > samples_held(c))
+        return failf(c, SPH_ERR_ARG, "sph_mlp_get_samples: fewer than %lld samples", (long long)n);
+    CK(cudaMemcpy(x, c.mlp.sx, sizeof(float) * 4 * (size_t)n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(y, c.mlp.sy, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost));
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_load_samples(sph_ctx *ctx, const float *x, const float *y,
+                                           int64_t n, void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (n < 1 || !x || !y) return failf(c, SPH_ERR_ARG, "sph_mlp_load_samples: need n >= 1");
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    rc = ensure_samples(c, n);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned long long cnt = (unsigned long long)n;
+    CK(cudaMemcpyAsync(c.mlp.sx, x, sizeof(float) * 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c.mlp.sy, y, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c.mlp.scount, &cnt, sizeof cnt, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_train(sph_ctx *ctx, int32_t iters, int32_t batch, double lr,
+                                    uint64_t seed, double *loss_first, double *loss_last,
+                                    void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (iters < 1 || !(lr > 0.0)) return failf(c, SPH_ERR_ARG, "sph_mlp_train: iters, lr");
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    if (!c.mlp.sx) return failf(c, SPH_ERR_STATE, "sph_mlp_train: no samples");
+    CK(cudaDeviceSynchronize());
+    const int64_t count = samples_held(c);
+    if (count <= 0) return failf(c, SPH_ERR_STATE, "sph_mlp_train: no samples");
+    const bool random = batch > 0 && batch < count;
+    const long long B = random ? batch : count;
+    rc = ensure_grad_space(c, B, iters);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int it = 0; it < iters; ++it) {
+        CK(launch_mlp_grad(c, c.mlp.sx, c.mlp.sy, count, B, random ? 1 : 0, seed, it, s));
+        CK(launch_mlp_update(c, B, 1, lr, nullptr, c.mlp.loss + it, s));
+    }
+    CK(launch_mlp_pack(c, s));
+    CK(cudaStreamSynchronize(s));
+    double l0 = 0.0, l1 = 0.0;
+    CK(cudaMemcpy(&l0, c.mlp.loss, sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&l1, c.mlp.loss + iters - 1, sizeof(double), cudaMemcpyDeviceToHost));
+    if (loss_first) *loss_first = l0;
+    if (loss_last) *loss_last = l1;
+    if (!std::isfinite(l1)) return failf(c, SPH_ERR_NONFINITE, "sph_mlp_train: loss is not finite");
+    // the network's own fit error, in ln h: smaller corrections are noise
+    c.mlp.dead = (float)(std::sqrt(l1) / kMlpYScale);
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_grad(sph_ctx *ctx, const float *x, const float *y, int64_t n,
+                                   float *grad, double *loss, void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (n < 1 || !x || !y || !grad) return failf(c, SPH_ERR_ARG, "sph_mlp_grad: arguments");
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    rc = ensure_grad_space(c, n, 1);
+    if (rc) return rc;
+    float *gdev = nullptr;
+    CK(dalloc(&gdev, kMlpParams));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_mlp_grad(c, x, y, n, n, 0, 0ull, 0, s);
+    if (e == cudaSuccess) e = launch_mlp_update(c, n, 0, 0.0, gdev, c.mlp.loss, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(grad, gdev, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && loss) e = cudaMemcpy(loss, c.mlp.loss, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(gdev);
+    if (e != cudaSuccess) return failf(c, SPH_ERR_CUDA, "sph_mlp_grad: %s", cudaGetErrorString(e));
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_mlp_infer(sph_ctx *ctx, const float *x, int64_t n, float *y,
+                                    void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (n < 0 || (n > 0 && (!x || !y))) return failf(c, SPH_ERR_ARG, "sph_mlp_infer: arguments");
+    sph_status rc = ensure_mlp(c);
+    if (rc) return rc;
+    CK(launch_mlp_infer(c, x, n, y, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t cap,
+                                        int64_t *nslots)
+{
+    if (!ctx || !nslots) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    *nslots = c.kp.nb;
+    if (!first || cap < (int64_t)c.kp.nb + 1)
+        return failf(c, SPH_ERR_ARG, "sph_bucket_layout needs %d entries", c.kp.nb + 1);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(first, c.bstart, sizeof(int) * ((size_t)c.kp.nb + 1), cudaMemcpyDeviceToHost));
+    return SPH_OK;
 }
 
 extern "C" sph_status sph_set_dt_old(sph_ctx *ctx, double dt_old)

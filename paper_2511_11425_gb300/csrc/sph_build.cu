@@ -56,18 +56,20 @@ __global__ void k_bbox_partial(const Inst *__restrict__ insts, const double *__r
     }
 }
 
-// key box per instance = [lo0, lo1, lo2, 2^bin / S, cubes0, cubes1, cubes2, bin]
+// key box per instance = [lo0..2, cells per unit length 0..2, cubes0..2, bin]
 __global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const double *part,
                              double *morton_box, DevStatus *st)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kp.ninst) return;
     const Inst &I = insts[k];
-    // The domain is cut into equal cubes of side S = its shortest extent
-    // (at least 1/1024 of the longest), visited in a snake order (every cube
-    // is a face neighbour of the one before); the curve orders the particles
-    // inside each cube on 2^bin cells per axis.  Key cells stay cubic however
-    // elongated the domain (a tube, a slab), so curve ranges stay compact.
+    // The domain is cut into near-cubes: round(extent / S) per axis, S = the
+    // shortest extent (at least 1/1024 of the longest), visited in a snake
+    // order (every cube is a face neighbour of the one before); the curve
+    // orders the particles inside each cube on 2^bin cells per axis.  Key
+    // cells stay near-cubic (aspect below 3/2) however elongated the domain
+    // (a tube, a slab), so curve ranges stay compact, and no thin sliver
+    // cube is left at the far faces.
     double lo3[3], ext3[3], emin = INFINITY, emax = 0.0;
     for (int a = 0; a < 3; ++a) {
         double lo, hi;
@@ -92,11 +94,11 @@ __global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const d
         emin = fmin(emin, hi - lo);
         emax = fmax(emax, hi - lo);
     }
-    const double S = fmax(emin, emax / (double)(1 << kMortonBits)) * (1.0 + 1e-9) + 1e-300;
+    const double S = fmax(emin, emax / (double)(1 << kMortonBits)) + 1e-300;
     long long ncubes = 1;
     int nc[3];
     for (int a = 0; a < 3; ++a) {
-        nc[a] = (int)fmin(fmax(ceil(ext3[a] / S), 1.0), (double)(1 << kMortonBits));
+        nc[a] = (int)fmin(fmax(rint(ext3[a] / S), 1.0), (double)(1 << kMortonBits));
         ncubes *= nc[a];
     }
     int bpre = 0;
@@ -105,10 +107,10 @@ __global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const d
     double *mb = morton_box + kKeyBox * k;
     for (int a = 0; a < 3; ++a) {
         mb[a] = lo3[a];
-        mb[4 + a] = (double)nc[a];
+        mb[3 + a] = ldexp((double)nc[a], bin) / (ext3[a] * (1.0 + 1e-9) + 1e-300);
+        mb[6 + a] = (double)nc[a];
     }
-    mb[3] = ldexp(1.0, bin) / S;
-    mb[7] = (double)bin;
+    mb[9] = (double)bin;
 }
 
 // 10-bit coordinate -> every third bit of a 30-bit word
@@ -167,13 +169,13 @@ __global__ void k_morton(int n, const Inst *__restrict__ insts,
     if (i >= n) return;
     const int k = pinst[i];
     const double *mb = mbox + kKeyBox * k;
-    const int bin = (int)mb[7];
+    const int bin = (int)mb[9];
     const double v[3] = {x[i], y[i], z[i]};
     unsigned cube[3], w[3], nc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        nc[a] = (unsigned)mb[4 + a];
-        double t = (v[a] - mb[a]) * mb[3];
+        nc[a] = (unsigned)mb[6 + a];
+        double t = (v[a] - mb[a]) * mb[3 + a];
         t = fmin(fmax(t, 0.0), ldexp((double)nc[a], bin) - 1.0);
         const unsigned ti = (unsigned)t;
         cube[a] = ti >> bin;
@@ -348,6 +350,196 @@ __global__ void k_copyback_all(int n, PermFields pf, const char *tmp)
 }
 
 // ---------------------------------------------------------------------------
+// bucket layout.  The paper splits cells until a leaf holds few particles
+// (Sec. 2.3.2); here the curve-ordered particles are cut into warps that do
+// not straddle large octree cells.  Particle i gets a position P(i) in a
+// padded index space of its instance (bucket slot = P / 32, group = slot /
+// G): P = 0 at the instance's first particle and P(i) = align(P(i-1) + 1,
+// a_i), where a_i = 32 G when the smallest key cell holding particles i-1 and
+// i is wider than kKappaGroup h (a new group starts), 32 when it is wider than
+// kKappaBucket h (a new bucket starts), else 1.  The maps
+// x -> align(x + c, a) + d with power-of-two a are closed under composition,
+// so P is one parallel scan (tile reduce, scan of the tile totals, apply).
+// An instance whose layout needs more slots than it has keeps plain
+// 32-particle chunks.
+// ---------------------------------------------------------------------------
+struct PadF {
+    int reset, c, a, d;  // x -> align((reset ? -1 : x) + c, a) + d
+};
+
+__device__ __forceinline__ int align_up(int v, int a) { return ((v + a - 1) / a) * a; }
+
+// f first, then g
+__device__ __forceinline__ PadF pad_then(PadF f, PadF g)
+{
+    if (g.reset) return g;
+    const int e = f.d + g.c;
+    if (g.a <= f.a) return PadF{f.reset, f.c, f.a, align_up(e, g.a) + g.d};
+    return PadF{f.reset, f.c + f.a * ((e + f.a - 1) / f.a), g.a, g.d};
+}
+
+__device__ __forceinline__ int pad_apply(PadF f) { return align_up(f.c - 1, f.a) + f.d; }
+
+__device__ __forceinline__ PadF pad_shfl_up(PadF f, int o)
+{
+    return PadF{__shfl_up_sync(kFull, f.reset, o), __shfl_up_sync(kFull, f.c, o),
+                __shfl_up_sync(kFull, f.a, o), __shfl_up_sync(kFull, f.d, o)};
+}
+
+__device__ __forceinline__ PadF pad_elem(int i, const Inst *__restrict__ insts,
+                                         const unsigned short *__restrict__ pinst,
+                                         const unsigned long long *__restrict__ keys,
+                                         const float *__restrict__ h,
+                                         const double *__restrict__ mbox)
+{
+    const int k = pinst[i];
+    const Inst &I = insts[k];
+    if (i == I.off) return PadF{1, 1, 1, 0};
+    const double *mb = mbox + kKeyBox * k;
+    const int bin = (int)mb[9];
+    const unsigned long long x = keys[i - 1] ^ keys[i];
+    const int d = x ? 63 - __clzll((long long)x) : -1;
+    const int ga = kBucket * I.G;
+    if (d >= 3 * bin) return PadF{0, 1, ga, 0};  // another cube of the snake
+    // the smallest common cell has 2^(d/3 + 1) key cells per side
+    const float cell = 1.f / fminf(fminf((float)mb[3], (float)mb[4]), (float)mb[5]);
+    const float side = ldexpf(cell, d < 0 ? 0 : d / 3 + 1);
+    const float hh = fmaxf(h[i - 1], h[i]);
+    const int a = side > kKappaGroup * hh ? ga : (side > kKappaBucket * hh ? kBucket : 1);
+    return PadF{0, 1, a, 0};
+}
+
+// composition of the 8 consecutive items of each thread, then of the block
+__global__ void __launch_bounds__(256) k_pad_reduce(int n, const Inst *__restrict__ insts,
+                                                    const unsigned short *__restrict__ pinst,
+                                                    const unsigned long long *__restrict__ keys,
+                                                    const float *__restrict__ h,
+                                                    const double *__restrict__ mbox, int4 *agg)
+{
+    __shared__ PadF wtot[8];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int base = blockIdx.x * kPadTile + t * 8;
+    PadF f = {0, 0, 1, 0};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (base + q < n) f = pad_then(f, pad_elem(base + q, insts, pinst, keys, h, mbox));
+    // inclusive scan over the warp (its last lane holds the warp total)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const PadF u = pad_shfl_up(f, o);
+        if (lane >= o) f = pad_then(u, f);
+    }
+    if (lane == 31) wtot[w] = f;
+    __syncthreads();
+    if (t == 0) {
+        PadF tot = wtot[0];
+        for (int k = 1; k < 8; ++k) tot = pad_then(tot, wtot[k]);
+        agg[blockIdx.x] = make_int4(tot.reset, tot.c, tot.a, tot.d);
+    }
+}
+
+// exclusive scan of the tile totals, in place (one block)
+__global__ void __launch_bounds__(1024) k_pad_scan(int ntiles, int4 *agg)
+{
+    __shared__ PadF part[1024];
+    const int t = threadIdx.x;
+    const int per = (ntiles + 1023) / 1024;
+    const int b0 = min(ntiles, t * per), b1 = min(ntiles, b0 + per);
+    PadF f = {0, 0, 1, 0};
+    for (int k = b0; k < b1; ++k) {
+        const int4 v = agg[k];
+        f = pad_then(f, PadF{v.x, v.y, v.z, v.w});
+    }
+    part[t] = f;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const PadF u = t >= o ? part[t - o] : PadF{0, 0, 1, 0};
+        __syncthreads();
+        if (t >= o) part[t] = pad_then(u, part[t]);
+        __syncthreads();
+    }
+    PadF run = t > 0 ? part[t - 1] : PadF{0, 0, 1, 0};
+    for (int k = b0; k < b1; ++k) {
+        const int4 v = agg[k];
+        agg[k] = make_int4(run.reset, run.c, run.a, run.d);
+        run = pad_then(run, PadF{v.x, v.y, v.z, v.w});
+    }
+}
+
+// every slot starts out empty at its instance's end
+__global__ void k_pad_init(int nb, const Inst *__restrict__ insts, const int *__restrict__ binst,
+                           int *bstart)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const Inst &I = insts[binst[b]];
+    bstart[b] = I.off + I.n;
+}
+
+// positions P(i); a particle that starts a bucket writes its slot and the
+// padding slots before it; the last particle of an instance reports the
+// slots used
+__global__ void __launch_bounds__(256) k_pad_apply(int n, const Inst *__restrict__ insts,
+                                                   const unsigned short *__restrict__ pinst,
+                                                   const unsigned long long *__restrict__ keys,
+                                                   const float *__restrict__ h,
+                                                   const double *__restrict__ mbox,
+                                                   const int4 *__restrict__ excl, int *bstart,
+                                                   int *used)
+{
+    __shared__ PadF wtot[8];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int base = blockIdx.x * kPadTile + t * 8;
+    PadF f = {0, 0, 1, 0};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (base + q < n) f = pad_then(f, pad_elem(base + q, insts, pinst, keys, h, mbox));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const PadF u = pad_shfl_up(f, o);
+        if (lane >= o) f = pad_then(u, f);
+    }
+    if (lane == 31) wtot[w] = f;
+    PadF lane_ex = pad_shfl_up(f, 1);
+    if (lane == 0) lane_ex = PadF{0, 0, 1, 0};
+    __syncthreads();
+    const int4 ev = excl[blockIdx.x];
+    PadF run = PadF{ev.x, ev.y, ev.z, ev.w};
+    for (int k = 0; k < w; ++k) run = pad_then(run, wtot[k]);
+    run = pad_then(run, lane_ex);
+    int prev = pad_apply(run);  // P of the item before this thread's first
+    for (int q = 0; q < 8; ++q) {
+        const int i = base + q;
+        if (i >= n) break;
+        const PadF e = pad_elem(i, insts, pinst, keys, h, mbox);
+        run = pad_then(run, e);
+        const int P = pad_apply(run);
+        const int k = pinst[i];
+        const Inst &I = insts[k];
+        const int slot = P >> 5;
+        if ((P & 31) == 0) {
+            const int s0 = e.reset ? slot : (prev >> 5) + 1;
+            for (int sl = s0; sl <= slot && sl < I.nb; ++sl) bstart[I.boff + sl] = i;
+        }
+        if (i == I.off + I.n - 1) used[k] = slot + 1;
+        prev = P;
+    }
+}
+
+// instances whose layout did not fit keep plain 32-particle chunks
+__global__ void k_pad_fallback(int nb, const Inst *__restrict__ insts,
+                               const int *__restrict__ binst, const int *__restrict__ used,
+                               int *bstart)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int k = binst[b];
+    const Inst &I = insts[k];
+    if (used[k] <= I.nb) return;
+    bstart[b] = min(I.off + kBucket * (b - I.boff), I.off + I.n);
+}
+
+// ---------------------------------------------------------------------------
 // buckets: origin, relative positions, leaf bounds.  One warp per bucket.
 // Offsets from the bucket's first particle are formed in FP64 (minimum image
 // on periodic axes) and every reduction runs in FP32 on those offsets.
@@ -371,7 +563,22 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
     const Inst &I = insts[binst[b]];
     const int i0 = bstart[b];
     const int i = i0 + lane;
-    const bool ok = lane < bucket_count(I, i0);
+    const int cnt = bucket_len(bstart, b);
+    if (cnt == 0) {  // padding slot: an empty leaf
+        if (lane == 0) {
+            const size_t k = (size_t)I.nbase + I.P + (b - I.boff);
+            const float4 e = make_float4(0.f, 0.f, 0.f, 0.f), er = make_float4(-1.f, -1.f, -1.f, 0.f);
+            if (update_pos) {
+                for (int a = 0; a < 3; ++a) origin[a * kp.nb + b] = 0;
+                node[4 * k + 0] = e;
+                node[4 * k + 1] = er;
+            }
+            node[4 * k + 2] = e;
+            node[4 * k + 3] = er;
+        }
+        return;
+    }
+    const bool ok = lane < cnt;
     float rel[3];
     double o[3];
     if (update_pos) {
@@ -562,6 +769,10 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
     const Inst &I = insts[binst[fb]];
     const int nbg = min(I.G, I.boff + I.nb - fb);
     const int fl = fb - I.boff;  // local index of the group's first bucket
+    if (bstart[fb + nbg] == bstart[fb]) {  // only padding slots
+        if (lane == 0) list_cnt[g] = 0u;
+        return;
+    }
 
     // group bounds in absolute (unwrapped) f32 coordinates
     float gc[3], gr[3], sc[3], sr[3];  // gather box, group cell box
@@ -571,7 +782,7 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
             const int b = fb + j;
             const float3 off = origin_offset(I, kp.nb, origin, fb, b);
             const int i0 = bstart[b];
-            if (lane < bucket_count(I, i0)) {
+            if (lane < bucket_len(bstart, b)) {
                 const int i = i0 + lane;
                 const float4 r = pm[i];
                 const float R = h_walk[i] * (1.f + kp.margin);
@@ -602,65 +813,69 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
     }
 
     const float4 *tn = node + 4 * (size_t)I.nbase;  // this instance's tree
+    // does node nd (at level lvl) hold sources of this group?
+    auto accept = [&](unsigned nd, int lvl) -> bool {
+        const float4 b0 = tn[4 * nd], b1 = tn[4 * nd + 1];
+        if (!(b1.x >= 0.f)) return false;  // empty
+        bool gth = ovl(gc[0], gr[0], b0.x, b1.x, I.periodic[0], I.L[0], I.invL[0]) &&
+                   ovl(gc[1], gr[1], b0.y, b1.y, I.periodic[1], I.L[1], I.invL[1]) &&
+                   ovl(gc[2], gr[2], b0.z, b1.z, I.periodic[2], I.L[2], I.invL[2]);
+        if (mode == WALK_FORCE) {
+            // only subtrees holding buckets >= the group's first
+            const int shift = I.logP - lvl;
+            const int last = (int)(((nd + 1u) << shift) - 1u) - I.P;
+            if (last < fl) return false;
+            if (!gth) {
+                const float4 o0 = tn[4 * nd + 2], o1 = tn[4 * nd + 3];
+                gth = ovl(sc[0], sr[0], o0.x, o1.x, I.periodic[0], I.L[0], I.invL[0]) &&
+                      ovl(sc[1], sr[1], o0.y, o1.y, I.periodic[1], I.L[1], I.invL[1]) &&
+                      ovl(sc[2], sr[2], o0.z, o1.z, I.periodic[2], I.L[2], I.invL[2]);
+            }
+            if (lvl == I.logP && (int)(nd - I.P) < fl) gth = false;
+        }
+        return gth;
+    };
+    // the frontier holds ACCEPTED nodes only: each round tests both children
+    // of every accepted node and keeps the accepted ones (leaves become the
+    // list as global bucket ids)
     unsigned *cur = buf[wib][0], *nxt = buf[wib][1];
     const int L0 = I.logP < 5 ? I.logP : 5;
-    int ncur = 1 << L0;
-    for (int k = lane; k < ncur; k += 32) cur[k] = (1u << L0) + k;
-    __syncwarp();
     bool overflow = false;
-    for (int lvl = L0; lvl <= I.logP; ++lvl) {
+    int ncur = 0;
+    auto push = [&](bool acc, unsigned v, unsigned *dst, int &cnt) {
+        const unsigned bal = __ballot_sync(kFull, acc);
+        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        const int tot = cnt + __popc(bal);
+        if (tot > kWalkCap) overflow = true;
+        else if (acc) dst[pos] = v;
+        cnt = min(tot, kWalkCap);
+    };
+    const bool top_leaf = L0 == I.logP;
+    for (int base = 0; base < (1 << L0); base += 32) {
+        const int k = base + lane;
+        const unsigned nd = (1u << L0) + (unsigned)k;
+        const bool acc = k < (1 << L0) && accept(nd, L0);
+        push(acc, top_leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, cur, ncur);
+    }
+    __syncwarp();
+    for (int lvl = L0 + 1; lvl <= I.logP && !overflow; ++lvl) {
         const bool leaf = lvl == I.logP;
         int nnext = 0;
         for (int base = 0; base < ncur; base += 32) {
             const int k = base + lane;
-            bool acc = false;
-            unsigned nd = 0;
-            if (k < ncur) {
-                nd = cur[k];
-                const float4 b0 = tn[4 * nd], b1 = tn[4 * nd + 1];
-                if (b1.x >= 0.f) {  // non-empty
-                    bool gth = ovl(gc[0], gr[0], b0.x, b1.x, I.periodic[0], I.L[0], I.invL[0]) &&
-                               ovl(gc[1], gr[1], b0.y, b1.y, I.periodic[1], I.L[1], I.invL[1]) &&
-                               ovl(gc[2], gr[2], b0.z, b1.z, I.periodic[2], I.L[2], I.invL[2]);
-                    if (mode == WALK_FORCE) {
-                        // only subtrees holding buckets >= the group's first
-                        const int shift = I.logP - lvl;
-                        const int last = (int)(((nd + 1u) << shift) - 1u) - I.P;
-                        if (last < fl) {
-                            gth = false;
-                        } else if (!gth) {
-                            const float4 o0 = tn[4 * nd + 2], o1 = tn[4 * nd + 3];
-                            gth = ovl(sc[0], sr[0], o0.x, o1.x, I.periodic[0], I.L[0], I.invL[0]) &&
-                                  ovl(sc[1], sr[1], o0.y, o1.y, I.periodic[1], I.L[1], I.invL[1]) &&
-                                  ovl(sc[2], sr[2], o0.z, o1.z, I.periodic[2], I.L[2], I.invL[2]);
-                        }
-                        if (leaf && (int)(nd - I.P) < fl) gth = false;
-                    }
-                    acc = gth;
-                }
+            const unsigned parent = k < ncur ? cur[k] : 0u;
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                const unsigned nd = 2u * parent + (unsigned)ch;
+                const bool acc = k < ncur && accept(nd, lvl);
+                push(acc, leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, nxt, nnext);
             }
-            const unsigned bal = __ballot_sync(kFull, acc);
-            const int per = leaf ? 1 : 2;
-            const int pos = nnext + per * __popc(bal & ((1u << lane) - 1u));
-            const int tot = nnext + per * __popc(bal);
-            if (tot > kWalkCap) {
-                overflow = true;
-            } else if (acc) {
-                if (leaf) {
-                    nxt[pos] = (unsigned)I.boff + (nd - (unsigned)I.P);  // global bucket id
-                } else {
-                    nxt[pos] = 2u * nd;
-                    nxt[pos + 1] = 2u * nd + 1u;
-                }
-            }
-            nnext = min(tot, kWalkCap);
         }
         __syncwarp();
         unsigned *t = cur;
         cur = nxt;
         nxt = t;
         ncur = nnext;
-        if (overflow) break;
     }
     if (overflow) {
         if (lane == 0) raise_status(st, ST_CAPACITY, g);
@@ -714,6 +929,23 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     pf.f1 = p.iters;
     k_gather_all<<<g, 256, 0, s>>>(perm, n, pf, (char *)c.tmp);
     k_copyback_all<<<g, 256, 0, s>>>(n, pf, (const char *)c.tmp);
+    if (c.mlp.record) {
+        cudaError_t e = launch_mlp_permute(c, perm, n, s);
+        if (e != cudaSuccess) return e;
+    }
+    // bucket layout on the sorted keys
+    {
+        const int tiles = (n + kPadTile - 1) / kPadTile;
+        const unsigned long long *sk = c.keys[cur];
+        const int gb = (kp.nb + 255) / 256;
+        k_pad_reduce<<<tiles, 256, 0, s>>>(n, c.inst, c.pinst, sk, p.h, c.morton_box, c.pad_agg);
+        k_pad_scan<<<1, 1024, 0, s>>>(tiles, c.pad_agg);
+        k_pad_init<<<gb, 256, 0, s>>>(kp.nb, c.inst, c.binst, c.bstart);
+        k_pad_apply<<<tiles, 256, 0, s>>>(n, c.inst, c.pinst, sk, p.h, c.morton_box, c.pad_agg,
+                                          c.bstart, c.pad_used);
+        k_pad_fallback<<<gb, 256, 0, s>>>(kp.nb, c.inst, c.binst, c.pad_used, c.bstart);
+        c.launches += 5;
+    }
     // buckets and trees
     const int wb = (kp.nb * 32 + 127) / 128;
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,

@@ -201,7 +201,7 @@ __device__ __forceinline__ void density_bucket(
             const float3 off = origin_offset(I, kp.nb, origin, A, B);
             const int j0 = bstart[B];
             const int j = j0 + lane;
-            const bool vj = lane < bucket_count(I, j0);
+            const bool vj = lane < bucket_len(bstart, B);
             float4 s = vj ? pm[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             float sp[3] = {off.x + s.x, off.y + s.y, off.z + s.z};
             bool in = vj;
@@ -352,7 +352,9 @@ __global__ void __launch_bounds__(128) k_density(
     const PBox bx = make_pbox(I);
     const int i0 = bstart[A];
     const int i = i0 + lane;
-    const bool valid = lane < bucket_count(I, i0);
+    const int cnt = bucket_len(bstart, A);
+    if (cnt == 0) return;  // padding slot
+    const bool valid = lane < cnt;
     const float4 me = valid ? pm[i] : make_float4(0.f, 0.f, 0.f, 1.f);
     // sink centre (periodic images are chosen nearest to it) and whether
     // pair separations need their own minimum-image wrap
@@ -386,10 +388,10 @@ __global__ void __launch_bounds__(128) k_density(
 __global__ void k_isentropic(int n, const Inst *__restrict__ insts,
                              const unsigned short *__restrict__ pinst,
                              const float *__restrict__ rho, const float *__restrict__ rho_old,
-                             double *u)
+                             double *u, const DevStatus *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || st->code != 0) return;  // no state change after an error
     float ro = rho_old[i];
     const double g1 = (double)insts[pinst[i]].gamma - 1.0;
     if (ro > 0.f) u[i] *= pow((double)rho[i] / (double)ro, g1);
@@ -432,7 +434,8 @@ cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     int n = (int)p.n;
     c.launches += 1;
-    k_isentropic<<<(n + 255) / 256, 256, 0, s>>>(n, c.inst, c.pinst, p.rho, c.rho_old, p.u);
+    k_isentropic<<<(n + 255) / 256, 256, 0, s>>>(n, c.inst, c.pinst, p.rho, c.rho_old, p.u,
+                                                 c.st);
     return cudaGetLastError();
 }
 

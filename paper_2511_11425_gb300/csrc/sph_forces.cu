@@ -267,7 +267,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         const float3 off = origin_offset(I, kp.nb, origin, A, B);
         const int j0 = bstart[B];
         const int j = j0 + lane;
-        const bool vj = lane < bucket_count(I, j0);
+        const bool vj = lane < bucket_len(bstart, B);
         const float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         float sp[3] = {off.x + q.x, off.y + q.y, off.z + q.z};
         // gather: inside the sink's box of balls and ball of balls;
@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const Inst *__restri
     const Visc vp = {I.alpha, I.beta, I.eps_av};
     const int i0 = bstart[A];
     const int i = i0 + lane;
-    const bool valid = lane < bucket_count(I, i0);
+    const int cnt = bucket_len(bstart, A);
+    if (cnt == 0) return;  // padding slot
+    const bool valid = lane < cnt;
     SinkState s;
     {
         float4 q = valid ? fpos[i] : make_float4(0.f, 0.f, 0.f, 1.f);

@@ -5,14 +5,15 @@
 // are stepped together: every phase is ONE launch over all instances.  A
 // single problem is a batch of one.
 //
-// Data layout in device memory (structure of arrays, Morton order within each
+// Data layout in device memory (structure of arrays, curve order within each
 // instance after sph_build_cells; instances stay in their particle ranges):
 //   caller arrays   x,v (f64), u (f64), m,h,rho,omega,a,dudt,... (f32)
 //   pinst[i]        instance of particle i (u16)
 //   pm[i]           float4 (x - o_b, y - o_b, z - o_b, m): position relative to
 //                   the origin o_b of the particle's bucket, plus mass
-//   buckets         up to 32 consecutive particles of one instance (one warp):
-//                   first particle bstart[b], instance binst[b], origin
+//   buckets         up to 32 consecutive particles of one instance (one warp)
+//                   inside one octree cell of side <= 3 h (slots of an instance
+//                   may be empty): first particle bstart[b], instance binst[b], origin
 //                   o_b = k_b q with integer grid coordinates k_b (int32 x3) and
 //                   the instance's power-of-two quantum q, so origin
 //                   differences are exact in f32 and need no FP64
@@ -23,14 +24,16 @@
 //                   half-width float4 pairs (Sec. 2.3.2); .w of the cell half
 //                   widths = largest bucket extent below, .w of the
 //                   box-of-balls half widths = largest h below
-//   groups          G <= 8 consecutive buckets of one instance (<= 256
-//                   particles) share one tree walk: first bucket gfirst[g]
+//   groups          G <= 8 consecutive bucket slots of one instance (<= 256
+//                   particles, inside one cell of side <= 6 h) share one tree
+//                   walk: first bucket gfirst[g]
 //   lists           per group, kWalkCap slots of source bucket ids
 //   force records   fpos (rel xyz, h), fvel (v_pred xyz, m), fth (A, c, rho, Omega)
 //   accumulators    acc (a xyz, S = sum m_j v_ij.gradW_ij(h_i)), acc2 (du/dt|Pi,
 //                   max(-mu_ij) as float bits)
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,12 +51,33 @@ constexpr int kGroupLog = 3;      // groups of up to 8 buckets
 constexpr int kWarpsPerBlock = 4; // pair kernels and walks: 4 warps per block
 constexpr int kSortItems = 8;     // keys per thread in a radix-sort tile
 constexpr int kSortTile = 256 * kSortItems;  // keys per radix-sort tile
-constexpr int kKeyBox = 8;  // doubles per instance of the key box
+constexpr int kKeyBox = 10;       // doubles per instance of the key box
+// Buckets and groups do not straddle large octree cells: consecutive
+// particles start a new bucket when their smallest common key cell is wider
+// than kKappaBucket h, a new group when it is wider than kKappaGroup h.
+constexpr float kKappaBucket = 3.f, kKappaGroup = 6.f;
+constexpr int kPadTile = 2048;    // particles per block of the bucket-layout scan
+
+// bucket slots reserved per instance: the plain 32-particle chunks plus half
+// as many again for buckets cut short at cell boundaries and group padding
+__host__ __device__ inline int64_t bucket_slots(int64_t n)
+{
+    return n > 0 ? (n + kBucket - 1) / kBucket + (n + 2 * kBucket - 1) / (2 * kBucket) + 8 : 0;
+}
 constexpr int kMortonBits = 10;   // bits per axis of the Morton key (30 bits)
 constexpr int kRelistRounds = 3;  // re-walk rounds queued after the first density pass
 constexpr int kBboxChunks = 32;   // blocks per instance for open-axis bounding boxes
 constexpr int kConsChunk = 2048;  // particles per block of the conserved totals
 constexpr unsigned kFull = 0xffffffffu;
+
+// learned seed network 4 -> 32 -> 32 -> 1 (parameter offsets in the flat vector)
+constexpr int kMlpIn = 4, kMlpHid = 32;
+constexpr int kMlpW1 = 0, kMlpB1 = 128, kMlpW2 = 160, kMlpB2 = 1184, kMlpW3 = 1216,
+              kMlpB3 = 1248, kMlpParams = 1249;
+constexpr int kMlpFragWords = 14 * 32 * 2;  // bf16x2 B fragments of all mma tiles
+constexpr float kMlpXScale0 = 100.f, kMlpXScale1 = 4.f, kMlpXScale2 = 100.f,
+                kMlpXScale3 = 10.f, kMlpYScale = 100.f;
+static_assert(kMlpParams == SPH_MLP_NPARAM, "network size");
 
 enum StatusCode : int {
     ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_CAPACITY = 3, ST_NOCONV = 4, ST_NONFINITE = 5,
@@ -125,6 +149,8 @@ struct Ctx {
     unsigned short *pinst = nullptr;
     int *bstart = nullptr, *binst = nullptr;
     int *gfirst = nullptr;
+    int4 *pad_agg = nullptr;       // bucket-layout scan: per tile aggregate / prefix
+    int *pad_used = nullptr;       // per instance: bucket slots the layout needs
     RefitBlock *refit = nullptr;   // refit schedule (all bands)
     std::vector<int> refit_band;   // blocks per band (host)
 
@@ -134,7 +160,7 @@ struct Ctx {
     double *dts = nullptr;         // device per instance [dt_old, dt_new]
     double *dts_host = nullptr;    // pinned mirror
     unsigned int *dtmin = nullptr; // device per instance min_i dt_i as float bits
-    double *morton_box = nullptr;  // device per instance [lo0,lo1,lo2, scale0,scale1,scale2]
+    double *morton_box = nullptr;  // device per instance key box (kKeyBox doubles)
     double *bbox_part = nullptr;   // device per instance partial min/max for open axes
     double *cons_part = nullptr;   // device per (instance, block) partial sums
     double *cons_out = nullptr;    // device 9 doubles per instance
@@ -168,6 +194,29 @@ struct Ctx {
     // host-mode mirror buffers for sph_step_host
     void *mirror = nullptr;
     sph_particles dmirror{};
+
+    // learned seed network
+    struct Mlp {
+        float *w = nullptr;          // FP32 master parameters
+        float *m = nullptr, *v = nullptr;  // Adam moments
+        uint32_t *frag = nullptr;    // bfloat16 copy as mma B fragments
+        float *gpart = nullptr;      // per-block gradient partials (+ loss)
+        int64_t gpart_blocks = 0;
+        double *loss = nullptr;      // per-step losses of the last training call
+        int loss_cap = 0;
+        int t = 0;                   // Adam steps taken
+        int seed_mode = SPH_SEED_ANALYTIC;
+        float dead = 0.f;            // corrections below this (in ln h) are dropped
+        bool record = false;
+        int stride = 1;
+        unsigned step = 0;           // harvest counter (sample selection)
+        float *seed0 = nullptr;      // capacity: seeds of the last density pass as given
+        float *tfeat = nullptr;      // 4 x capacity inputs of the last kick (SoA)
+        float *th = nullptr;         // capacity: h at the last kick (0 = none)
+        float *sx = nullptr, *sy = nullptr;  // samples: cap x 4, cap
+        unsigned long long *scount = nullptr;  // samples written (device)
+        int64_t cap = 0;
+    } mlp;
 
     // captured step
     cudaGraph_t graph = nullptr;
@@ -298,10 +347,12 @@ __device__ __forceinline__ size_t leaf_of(const Inst &I, int b)
     return (size_t)I.nbase + I.P + (b - I.boff);
 }
 
-// particles in bucket b (global index) of instance I
-__device__ __forceinline__ int bucket_count(const Inst &I, int bstart)
+// particles in bucket slot b: slots hold consecutive particle ranges, so the
+// count is the distance to the next slot's first particle (0 for a padding
+// slot; bstart has one sentinel entry past the last slot)
+__device__ __forceinline__ int bucket_len(const int *__restrict__ bstart, int b)
 {
-    int c = I.off + I.n - bstart;
+    const int c = bstart[b + 1] - bstart[b];
     return c < kBucket ? c : kBucket;
 }
 
@@ -410,5 +461,120 @@ cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s);
 // integration (sph_integrate.cu)
 cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s);
 cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s);
+// learned seed (sph_mlp.cu)
+cudaError_t launch_mlp_permute(Ctx &c, const unsigned *perm, int n, cudaStream_t s);
+cudaError_t launch_mlp_harvest(Ctx &c, const sph_particles &p, cudaStream_t s);
+cudaError_t launch_mlp_pack(Ctx &c, cudaStream_t s);
+int mlp_grad_blocks(long long batch);
+cudaError_t launch_mlp_grad(Ctx &c, const float *sx, const float *sy, long long count,
+                            long long batch, int random, unsigned long long seed, int iter,
+                            cudaStream_t s);
+cudaError_t launch_mlp_update(Ctx &c, long long batch, int adam, double lr, float *grad_out,
+                              double *loss, cudaStream_t s);
+cudaError_t launch_mlp_infer(Ctx &c, const float *x, long long n, float *y, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// warp-level inference of the seed network on the tensor cores: lane p of
+// the warp supplies the 4 inputs of its particle (zeros when it has none)
+// and receives the network output.  The 32 particles form two 16-row tiles;
+// each layer is a chain of mma.m16n8k16 (bfloat16 operands, FP32
+// accumulation) whose accumulator fragments are, after bias and ReLU,
+// exactly the A fragments of the next layer, so activations never leave
+// the registers.  frag holds the weights as B fragments: tile t, lane l,
+// word r at frag[(t * 32 + l) * 2 + r]; tiles 0-3 = layer 1 (n-tile j),
+// 4-11 = layer 2 (n-tile j, k-tile kk at 4 + 2 j + kk), 12-13 = layer 3.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&b);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1,
+                                               uint32_t a2, uint32_t a3, uint32_t b0,
+                                               uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float mlp_warp_infer(const uint32_t *__restrict__ frag,
+                                                const float *__restrict__ w, float x0, float x1,
+                                                float x2, float x3, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    const uint32_t p01 = pack_bf16x2(x0, x1), p23 = pack_bf16x2(x2, x3);
+    float out[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        // layer 1: A = inputs (k = 0..3, zero beyond), one k-tile
+        const uint32_t lo01 = __shfl_sync(kFull, p01, 16 * mt + g);
+        const uint32_t lo23 = __shfl_sync(kFull, p23, 16 * mt + g);
+        const uint32_t hi01 = __shfl_sync(kFull, p01, 16 * mt + g + 8);
+        const uint32_t hi23 = __shfl_sync(kFull, p23, 16 * mt + g + 8);
+        const uint32_t a0 = t == 0 ? lo01 : (t == 1 ? lo23 : 0u);
+        const uint32_t a1 = t == 0 ? hi01 : (t == 1 ? hi23 : 0u);
+        uint32_t A[2][4];  // A fragments of the next layer, per k-tile
+        {
+            float d[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint2 b = *reinterpret_cast<const uint2 *>(frag + (j * 32 + lane) * 2);
+                const float bb0 = w[kMlpB1 + 8 * j + 2 * t], bb1 = w[kMlpB1 + 8 * j + 2 * t + 1];
+                d[j][0] = bb0; d[j][1] = bb1; d[j][2] = bb0; d[j][3] = bb1;
+                mma_bf16_16816(d[j], a0, a1, 0u, 0u, b.x, b.y);
+            }
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                A[kk][0] = pack_bf16x2(fmaxf(d[2 * kk][0], 0.f), fmaxf(d[2 * kk][1], 0.f));
+                A[kk][1] = pack_bf16x2(fmaxf(d[2 * kk][2], 0.f), fmaxf(d[2 * kk][3], 0.f));
+                A[kk][2] = pack_bf16x2(fmaxf(d[2 * kk + 1][0], 0.f), fmaxf(d[2 * kk + 1][1], 0.f));
+                A[kk][3] = pack_bf16x2(fmaxf(d[2 * kk + 1][2], 0.f), fmaxf(d[2 * kk + 1][3], 0.f));
+            }
+        }
+        // layer 2: 4 n-tiles x 2 k-tiles
+        {
+            float d[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float bb0 = w[kMlpB2 + 8 * j + 2 * t], bb1 = w[kMlpB2 + 8 * j + 2 * t + 1];
+                d[j][0] = bb0; d[j][1] = bb1; d[j][2] = bb0; d[j][3] = bb1;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint2 b =
+                        *reinterpret_cast<const uint2 *>(frag + ((4 + 2 * j + kk) * 32 + lane) * 2);
+                    mma_bf16_16816(d[j], A[kk][0], A[kk][1], A[kk][2], A[kk][3], b.x, b.y);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                A[kk][0] = pack_bf16x2(fmaxf(d[2 * kk][0], 0.f), fmaxf(d[2 * kk][1], 0.f));
+                A[kk][1] = pack_bf16x2(fmaxf(d[2 * kk][2], 0.f), fmaxf(d[2 * kk][3], 0.f));
+                A[kk][2] = pack_bf16x2(fmaxf(d[2 * kk + 1][0], 0.f), fmaxf(d[2 * kk + 1][1], 0.f));
+                A[kk][3] = pack_bf16x2(fmaxf(d[2 * kk + 1][2], 0.f), fmaxf(d[2 * kk + 1][3], 0.f));
+            }
+        }
+        // layer 3: one n-tile whose column 0 is the output
+        {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint2 b = *reinterpret_cast<const uint2 *>(frag + ((12 + kk) * 32 + lane) * 2);
+                mma_bf16_16816(d, A[kk][0], A[kk][1], A[kk][2], A[kk][3], b.x, b.y);
+            }
+            out[mt][0] = d[0];  // row g, column 2t (column 0 on lanes with t == 0)
+            out[mt][1] = d[2];  // row g + 8
+        }
+    }
+    // row r of tile mt sits on lane 4 (r mod 8), register (r >= 8)
+    const int mt = lane >> 4, r = lane & 15, src = 4 * (r & 7);
+    const float v00 = __shfl_sync(kFull, out[0][0], src), v01 = __shfl_sync(kFull, out[0][1], src);
+    const float v10 = __shfl_sync(kFull, out[1][0], src), v11 = __shfl_sync(kFull, out[1][1], src);
+    const float y = mt == 0 ? (r < 8 ? v00 : v01) : (r < 8 ? v10 : v11);
+    return y + w[kMlpB3];
+}
 
 }  // namespace sph

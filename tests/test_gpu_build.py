@@ -89,3 +89,45 @@ def test_tube_is_cut_into_cubes_visited_in_order(sph):
     same = cube[1:] == cube[:-1]
     assert np.all(step[same] == 1)
     assert np.all(step[~same] <= 4)
+
+
+def _layout_checks(sph, prob, kappa_b=3.0, kappa_g=6.0, G=8):
+    ctx = sph.sph_create(sph.Params.for_problem(prob), prob.n)
+    parts = sph.Particles.from_problem(prob)
+    try:
+        sph.sph_build_cells(ctx, parts)
+        first = sph.sph_bucket_layout(ctx)
+        x = parts.pos().cpu().numpy()
+        h = parts.t["h"].cpu().numpy()
+    finally:
+        sph.sph_destroy(ctx)
+    cnt = np.diff(first)
+    # slots cover every particle once, in order, at most 32 per bucket
+    assert first[0] == 0 and first[-1] == prob.n
+    assert np.all(cnt >= 0) and np.all(cnt <= 32)
+    assert cnt.sum() == prob.n
+    ext, gext = [], []
+    for b in np.nonzero(cnt)[0]:
+        xb = x[first[b]:first[b + 1]]
+        ext.append(np.max(xb.max(0) - xb.min(0)) / h[first[b]:first[b + 1]].max())
+    for g in range(0, len(cnt), G):
+        lo, hi = first[g], first[min(g + G, len(cnt))]
+        if hi > lo:
+            xg = x[lo:hi]
+            gext.append(np.max(xg.max(0) - xg.min(0)) / h[lo:hi].max())
+    return cnt, np.array(ext), np.array(gext)
+
+
+def test_bucket_layout_keeps_buckets_inside_small_cells(sph):
+    """Free-surface sphere (random 1/r profile, open box): every bucket lies
+    inside one cell of side <= 3 h and every group inside one of side
+    <= 6 h (a box of that side fits within the cell); on an aligned periodic
+    lattice the layout is the plain 32-particle chunking."""
+    prob = inputs.collision(n_total=60000)
+    cnt, ext, gext = _layout_checks(sph, prob)
+    assert ext.max() <= 3.0 * 1.0001
+    assert gext.max() <= 6.0 * 1.0001
+    assert (cnt > 0).sum() <= 1.5 * prob.n / 32
+    lat = inputs.sedov(n=32)
+    cnt, ext, _ = _layout_checks(sph, lat)
+    assert np.all(cnt[:lat.n // 32] == 32) and np.all(cnt[lat.n // 32:] == 0)

@@ -117,6 +117,15 @@ def test_untrained_network_outputs_zero_and_seed_target_round_trip():
     X = mlp.features(0.01, divv, np.full(50, 64), 64.0, h, h, 0.0)
     assert np.all(X[:, 1:] == 0.0)
     assert np.allclose(mlp.seed(h, X, np.zeros(50)), h * np.exp(0.01 * divv / 3), rtol=1e-12)
+    # a particle at rest (both estimates below the tolerance) ignores the network
+    Xr = np.array([[1e-5, 0.3, -2e-5, 0.1], [1e-3, 0.3, 0.0, 0.1]])
+    assert np.allclose(mlp.seed(np.ones(2), Xr, np.array([5.0, 5.0]), tol=1e-6),
+                       [np.exp(1e-7), np.exp(1e-5 + 0.05)], rtol=1e-14)
+    # corrections inside the dead zone are dropped, larger ones kept whole
+    assert np.allclose(mlp.seed(np.ones(2), Xr, np.array([5.0, 5.0]), dead=0.06),
+                       [np.exp(1e-7), np.exp(1e-5)], rtol=1e-14)
+    assert np.allclose(mlp.seed(np.ones(2), Xr, np.array([5.0, 5.0]), dead=0.04),
+                       [np.exp(1e-7), np.exp(1e-5 + 0.05)], rtol=1e-14)
 
 
 def test_training_fits_a_smooth_target():
