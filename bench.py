@@ -28,6 +28,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -287,12 +288,35 @@ def forms_batch(dev, steps, warmup):
     del g
     torch.cuda.empty_cache()
 
+    # the same with the layout knobs picked by the autotuner
+    from paper_2511_11425_gb300 import autotune
+    plist = [sph.Params.for_problem(q) for q in probs]
+    parts, offs = sph.Particles.from_problems(probs, dev)
+    tuner = autotune.Autotuner(os.path.join(tempfile.gettempdir(), "sph_autotune.json"), steps=2)
+    plist = tuner.tune(parts, plist, offs, force=True)
+    del parts
+    g = sph.BatchSimulation(probs, plist, device=dev)
+    with torch.cuda.stream(s):
+        sph.sph_step(g.ctx, g.parts, 0.0, s)
+        g.capture(s)
+        for _ in range(warmup - 1):
+            sph.sph_graph_launch(g.ctx, s)
+    out["batched_graph_tuned"] = timed(lambda: sph.sph_graph_launch(g.ctx, s), [g.ctx])
+    out["batched_graph_tuned"]["knobs"] = tuner.report["knobs"]
+    out["batched_graph_tuned"]["tuning_trials"] = len(tuner.report["tried"])
+    dt_t = np.array(sph.sph_batch_get_dt(g.ctx, g.ninst))
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+
     out["speedup_vs_plain"] = {
         "batched": out["batched"]["value"] / out["plain"]["value"],
-        "batched_graph": out["batched_graph"]["value"] / out["plain"]["value"]}
+        "batched_graph": out["batched_graph"]["value"] / out["plain"]["value"],
+        "batched_graph_tuned": out["batched_graph_tuned"]["value"] / out["plain"]["value"]}
     out["max_rel_dt_diff_vs_plain"] = {
         "batched": float(np.max(np.abs(dt_b - dt_plain) / dt_plain)),
-        "batched_graph": float(np.max(np.abs(dt_g - dt_plain) / dt_plain))}
+        "batched_graph": float(np.max(np.abs(dt_g - dt_plain) / dt_plain)),
+        "batched_graph_tuned": float(np.max(np.abs(dt_t - dt_plain) / dt_plain))}
     return out
 
 
@@ -381,7 +405,15 @@ def run_ours(args, rank, world, local_rank):
     sph.lib()
     prob = _workload(rank)
     s = torch.cuda.current_stream(dev)
-    sim = sph.Simulation(prob, device=dev)
+    params = sph.Params.for_problem(prob)
+    layout = {"autotuned": False}
+    if not args.no_tune:
+        from paper_2511_11425_gb300 import autotune
+        tuner = autotune.Autotuner(os.path.join(tempfile.gettempdir(), "sph_autotune.json"), steps=3)
+        params = tuner.tune(sph.Particles.from_problem(prob, dev), params, force=True)
+        layout = {"autotuned": True, "knobs": tuner.report["knobs"],
+                  "trials": len(tuner.report["tried"])}
+    sim = sph.Simulation(prob, params, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     dist = None
     if world > 1:
@@ -451,7 +483,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         prob2 = _workload(rank)
         host = sph.Particles.from_problem(prob2, "cpu", pin=True)
-        ctx2 = sph.sph_create(sph.Params.for_problem(prob2), prob2.n)
+        ctx2 = sph.sph_create(params, prob2.n)
         try:
             for _ in range(min(args.warmup, 3)):
                 sph.sph_step_host(ctx2, host, 0.0, s)
@@ -484,7 +516,7 @@ def run_ours(args, rank, world, local_rank):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": _config(prob, {"sim_time_covered": t_sim,
+                "config": _config(prob, {"sim_time_covered": t_sim, "layout": layout,
                                          "parallelism": "replicas" if world > 1 else "single"}),
                 "pair_interactions_per_s": {
                     "density": world * dpairs / secs, "force": world * fpairs / secs,
@@ -506,6 +538,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="run the default layout knobs instead of autotuning them first")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the plain / batched / graph comparison on 256 instances")
     args = ap.parse_args(argv)

@@ -93,6 +93,10 @@ typedef struct {
     double  list_margin;   /* density lists gather within h (1 + list_margin)    */
     int32_t curve;         /* particle order: SPH_CURVE_HILBERT or SPH_CURVE_MORTON */
     int32_t group_log;     /* buckets per list walk = 2^group_log (1..3); 0 = 3  */
+    double  bucket_cell;   /* a bucket stays inside one key cell of side <=
+                              bucket_cell h (>= 1; 0 = 3)                        */
+    double  group_cell;    /* a walk group stays inside one key cell of side <=
+                              group_cell h (>= bucket_cell; 0 = 6)               */
 } sph_params;
 
 typedef struct {

@@ -51,7 +51,8 @@ class c_params(C.Structure):
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("periodic", C.c_int32 * 3), ("max_newton", C.c_int32),
                 ("h_rel_tol", C.c_double), ("list_margin", C.c_double),
-                ("curve", C.c_int32), ("group_log", C.c_int32)]
+                ("curve", C.c_int32), ("group_log", C.c_int32),
+                ("bucket_cell", C.c_double), ("group_cell", C.c_double)]
 
 
 class c_particles(C.Structure):
@@ -162,13 +163,15 @@ class Params:
     list_margin: float = 0.1
     curve: str = "hilbert"
     group_log: int = 3
+    bucket_cell: float = 3.0
+    group_cell: float = 6.0
 
     def c(self) -> c_params:
         p = c_params()
         p.kernel = KERNELS[self.kernel]
         p.energy_mode = ENERGY[self.energy]
         for f in ("n_ngb", "gamma", "alpha", "beta", "eps_av", "eta_courant", "eta_acc",
-                  "h_rel_tol", "list_margin"):
+                  "h_rel_tol", "list_margin", "bucket_cell", "group_cell"):
             setattr(p, f, float(getattr(self, f)))
         p.max_newton = int(self.max_newton)
         p.curve = CURVES[self.curve]

@@ -76,8 +76,13 @@ bool params_ok(const sph_params *prm)
         !(prm->alpha >= 0.0) || !(prm->beta >= 0.0) || !(prm->eps_av > 0.0) ||
         (prm->energy_mode != SPH_ENERGY_PDV && prm->energy_mode != SPH_ENERGY_ISENTROPIC) ||
         (prm->curve != SPH_CURVE_HILBERT && prm->curve != SPH_CURVE_MORTON) ||
-        prm->group_log < 0 || prm->group_log > kGroupLog)
+        prm->group_log < 0 || prm->group_log > kGroupLog ||
+        !(prm->bucket_cell == 0.0 || prm->bucket_cell >= 1.0) ||
+        !(prm->group_cell == 0.0 || prm->group_cell >= 1.0))
         return false;
+    const double kb = prm->bucket_cell > 0.0 ? prm->bucket_cell : kKappaBucket;
+    const double kg = prm->group_cell > 0.0 ? prm->group_cell : kKappaGroup;
+    if (!(kg >= kb) || !std::isfinite(kg)) return false;
     for (int a = 0; a < 3; ++a)
         if (!(prm->box_hi[a] > prm->box_lo[a]) || !std::isfinite(prm->box_lo[a]) ||
             !std::isfinite(prm->box_hi[a]))
@@ -112,6 +117,8 @@ Inst inst_params(const sph_params &prm)
     I.eta_acc = (float)prm.eta_acc;
     I.n_ngb = (float)prm.n_ngb;
     I.curve = prm.curve;
+    I.kb = (float)(prm.bucket_cell > 0.0 ? prm.bucket_cell : kKappaBucket);
+    I.kg = (float)(prm.group_cell > 0.0 ? prm.group_cell : kKappaGroup);
     I.hcap = (float)hcap;
     I.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
     I.inv_q = 1.0 / I.q;

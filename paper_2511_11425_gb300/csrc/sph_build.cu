@@ -356,8 +356,8 @@ __global__ void k_copyback_all(int n, PermFields pf, const char *tmp)
 // padded index space of its instance (bucket slot = P / 32, group = slot /
 // G): P = 0 at the instance's first particle and P(i) = align(P(i-1) + 1,
 // a_i), where a_i = 32 G when the smallest key cell holding particles i-1 and
-// i is wider than kKappaGroup h (a new group starts), 32 when it is wider than
-// kKappaBucket h (a new bucket starts), else 1.  The maps
+// i is wider than group_cell h (a new group starts), 32 when it is wider than
+// bucket_cell h (a new bucket starts), else 1.  The maps
 // x -> align(x + c, a) + d with power-of-two a are closed under composition,
 // so P is one parallel scan (tile reduce, scan of the tile totals, apply).
 // An instance whose layout needs more slots than it has keeps plain
@@ -405,7 +405,7 @@ __device__ __forceinline__ PadF pad_elem(int i, const Inst *__restrict__ insts,
     const float cell = 1.f / fminf(fminf((float)mb[3], (float)mb[4]), (float)mb[5]);
     const float side = ldexpf(cell, d < 0 ? 0 : d / 3 + 1);
     const float hh = fmaxf(h[i - 1], h[i]);
-    const int a = side > kKappaGroup * hh ? ga : (side > kKappaBucket * hh ? kBucket : 1);
+    const int a = side > I.kg * hh ? ga : (side > I.kb * hh ? kBucket : 1);
     return PadF{0, 1, a, 0};
 }
 

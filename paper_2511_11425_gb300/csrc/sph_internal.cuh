@@ -54,7 +54,8 @@ constexpr int kSortTile = 256 * kSortItems;  // keys per radix-sort tile
 constexpr int kKeyBox = 10;       // doubles per instance of the key box
 // Buckets and groups do not straddle large octree cells: consecutive
 // particles start a new bucket when their smallest common key cell is wider
-// than kKappaBucket h, a new group when it is wider than kKappaGroup h.
+// than bucket_cell h, a new group when it is wider than group_cell h
+// (defaults below; both are per instance parameters).
 constexpr float kKappaBucket = 3.f, kKappaGroup = 6.f;
 constexpr int kPadTile = 2048;    // particles per block of the bucket-layout scan
 
@@ -107,6 +108,7 @@ struct Inst {
     int nbase, P, logP;  // tree nodes nbase + [1, 2P)
     int G, logG;         // buckets per group
     int curve;           // SPH_CURVE_*
+    float kb, kg;        // bucket / group cell bounds in units of h
     int periodic[3];
     float L[3], invL[3];
     float gamma, alpha, beta, eps_av, eta_courant, eta_acc, n_ngb;
