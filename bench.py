@@ -407,7 +407,15 @@ def run_ours(args, rank, world, local_rank):
     s = torch.cuda.current_stream(dev)
     params = sph.Params.for_problem(prob)
     layout = {"autotuned": False}
-    if not args.no_tune:
+    if args.layout:
+        from paper_2511_11425_gb300 import autotune
+        knobs = {}
+        for item in args.layout.split(","):
+            k, v = item.split("=")
+            knobs[k] = v if k == "curve" else (int(v) if k == "group_log" else float(v))
+        params = autotune.with_knobs(params, knobs)
+        layout = {"autotuned": False, "knobs": knobs}
+    elif not args.no_tune:
         from paper_2511_11425_gb300 import autotune
         tuner = autotune.Autotuner(os.path.join(tempfile.gettempdir(), "sph_autotune.json"), steps=3)
         params = tuner.tune(sph.Particles.from_problem(prob, dev), params, force=True)
@@ -471,10 +479,15 @@ def run_ours(args, rank, world, local_rank):
           "ms_per_launch": kf / args.steps}
     dom, other = (rd, rf) if kd >= kf else (rf, rd)
     dom_file = "sph_density.cu" if dom is rd else "sph_forces.cu"
+    try:
+        fma_measured = sph.sph_probe_fp32_peak(s)
+    except sph.SphError:
+        fma_measured = None
     roof = {"bound": "alu", "achieved": dom["achieved"], "peak": FP32_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": dom["achieved"] / FP32_PEAK_TFLOPS,
             "traffic": _traffic_for(dom_file, dom["kernel"]), "kernel": dom["kernel"],
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+            "fp32_fma_measured_tflops": fma_measured,
             "ms_per_launch": dom["ms_per_launch"]}
     other_line = {**other, "frac": other["achieved"] / FP32_PEAK_TFLOPS}
 
@@ -538,6 +551,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--layout", default="",
+                    help="fixed layout knobs instead of tuning, e.g. curve=morton,bucket_cell=3")
     ap.add_argument("--no-tune", action="store_true",
                     help="run the default layout knobs instead of autotuning them first")
     ap.add_argument("--no-forms", action="store_true",

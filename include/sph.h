@@ -6,7 +6,7 @@
  * pkdgrav3 for Shock Physics Simulations. I. Hydrodynamics" (arXiv:2511.11425),
  * for ideal gases without gravity, on one GPU:
  *
- *   sph_build_cells       Morton sort + bucket bounds (Sec. 2.1 tree order,
+ *   sph_build_cells       curve sort + bucket bounds (Sec. 2.1 tree order,
  *                         Sec. 2.3.2 cell bounds and box-of-balls bounds)
  *   sph_density_h         rho_i = sum_j m_j W_ij(h_i) (Eq. Density_estimate) with
  *                         h_i from Newton-Raphson on the constant kernel mass
@@ -27,7 +27,7 @@
  *     device, owned by the caller; each array has n elements (x, v, a are
  *     arrays of three separate component arrays).  The library never frees
  *     them.  sph_build_cells permutes every array of the struct in place
- *     into Morton order; `id` travels with the particles so callers can map
+ *     into curve order; `id` travels with the particles so callers can map
  *     back to their own order.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is queued on it; every call returns after a
@@ -171,10 +171,13 @@ void sph_destroy(sph_ctx *ctx);
 
 /*
  * sph_build_cells (Sec. 2.1: particles reordered so that cells are contiguous;
- * Sec. 2.3.2: cell bound and box-of-balls bound per cell).  Computes 48-bit
- * Morton keys of x, stably sorts them, permutes EVERY array of *p in place,
- * splits the order into buckets of 32 consecutive particles and builds the
- * bounds tree over the buckets from x and the current h.  Positions on
+ * Sec. 2.3.2: cell bound and box-of-balls bound per cell).  Computes
+ * space-filling-curve keys of x (per instance: the box cut into near-cubes
+ * in snake order, params.curve inside each cube, 30 bits), stably sorts
+ * them, permutes EVERY array of *p in place, cuts the order into buckets of
+ * at most 32 consecutive particles that stay inside one key cell of side
+ * <= bucket_cell h (walk groups inside one of side <= group_cell h) and
+ * builds the bounds tree over the buckets from x and the current h.  Positions on
  * periodic axes must lie in [box_lo, box_hi).  SPH_ERR_ARG if p->n > capacity
  * or a required pointer is NULL; SPH_ERR_NONFINITE for non-finite x or h.
  */
@@ -183,7 +186,7 @@ sph_status sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream);
 /*
  * sph_density_h (Sec. 2.3.3).  For every particle solves
  * 4/3 pi h^3 rho(h) = N_ngb m by Newton-Raphson with a bisection safeguard,
- * starting from h_seed (device array of n floats, Morton order) or, if
+ * starting from h_seed (device array of n floats, curve order) or, if
  * h_seed is NULL, from p->h.  Writes p->h, p->rho, p->omega, p->nngb,
  * p->iters.  In SPH_ENERGY_ISENTROPIC mode it also moves u along its adiabat
  * to the new density, u <- u (rho/rho_old)^(gamma-1), using the rho left in
@@ -198,7 +201,7 @@ sph_status sph_density_h(sph_ctx *ctx, sph_particles *p, const float *h_seed, vo
 
 /*
  * sph_density_at: rho, Omega and the neighbour count at the GIVEN h (device
- * array, Morton order), without iterating; optionally lists neighbour ids.
+ * array, curve order), without iterating; optionally lists neighbour ids.
  * When ids != NULL it must hold n*cap int64 and receives, for particle i, the
  * `id` values of its neighbours j != i (r_ij < h_i) in slots [i*cap, i*cap+cap);
  * count[i] (device uint32, may be NULL) receives the full count even when it
@@ -248,7 +251,7 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * sph_step_host: sph_step on HOST arrays.  Copies every array of *hp to
  * device buffers owned by the context (allocated on first use for the
  * context's capacity), runs sph_step there and copies every array back
- * (in Morton order, like sph_step).  Host memory may be pageable or pinned;
+ * (in curve order, like sph_step).  Host memory may be pageable or pinned;
  * pinned memory copies faster.  Bytes moved per call are reported through
  * h2d_bytes / d2h_bytes when non-NULL.
  */
@@ -404,6 +407,13 @@ sph_status sph_mlp_infer(sph_ctx *ctx, const float *x, int64_t n, float *y, void
  * (first needs nslots + 1 entries, SPH_ERR_ARG otherwise).  Synchronous.
  * The paper has no counterpart (it is a view of the data layout). */
 sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t cap, int64_t *nslots);
+
+/* sph_probe_fp32_peak: measured FP32 FMA throughput of the current device
+ * in TFLOP/s (8 independent fmaf chains per thread on every SM, best of 3
+ * timed launches; allocates and frees a small device buffer, synchronous).
+ * A measuring stick for the pair kernels' roofline; the paper has no
+ * counterpart. */
+sph_status sph_probe_fp32_peak(double *tflops, void *stream);
 
 /* sph_set_dt_old: set the previous step size used by the predictor and the
  * closing kick (0 restarts the integration as at t = 0). */

@@ -32,7 +32,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
            "sph_graph_capture", "sph_graph_launch", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
-           "sph_mlp_load_samples", "sph_bucket_layout",
+           "sph_mlp_load_samples", "sph_bucket_layout", "sph_probe_fp32_peak",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
 MLP_NPARAM = 1249
 SEED_MODES = {"analytic": 0, "mlp": 1}
@@ -119,6 +119,7 @@ def lib():
         L.sph_mlp_grad.argtypes = [vp, vp, vp, i64, fp, C.POINTER(dbl), vp]
         L.sph_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
         L.sph_bucket_layout.argtypes = [vp, C.POINTER(C.c_int32), i64, C.POINTER(i64)]
+        L.sph_probe_fp32_peak.argtypes = [C.POINTER(dbl), vp]
         L.sph_get_stats.argtypes = [vp, C.POINTER(c_stats)]
         L.sph_last_error.argtypes = [vp]
         L.sph_last_error.restype = C.c_char_p
@@ -270,7 +271,7 @@ class Particles:
         return torch.stack([self.t["a0"], self.t["a1"], self.t["a2"]], 1)
 
     def numpy(self):
-        """Host copy of every array, in the current (Morton) order."""
+        """Host copy of every array, in the current (curve) order."""
         return {k: v.detach().cpu().numpy() for k, v in self.t.items()}
 
 
@@ -481,6 +482,13 @@ def sph_bucket_layout(ctx):
     _check(ctx, lib().sph_bucket_layout(ctx, first.ctypes.data_as(C.POINTER(C.c_int32)),
                                         first.size, C.byref(ns)))
     return first
+
+
+def sph_probe_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(None, lib().sph_probe_fp32_peak(C.byref(t), _stream(stream)))
+    return t.value
 
 
 def sph_set_dt_old(ctx, dt_old: float):

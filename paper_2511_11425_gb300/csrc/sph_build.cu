@@ -4,11 +4,12 @@
 // range; Sec. 2.3.2 bounds every cell by the box of its particles (cell
 // bound) and the box of the particles' kernel balls (box-of-balls), merged
 // bottom-up, and finds interaction partners of a whole group at once by
-// overlap tests of those bounds.  Here the order is a 30-bit Morton order per
-// instance (stable LSD radix sort of (instance, Morton) keys, so instances
-// keep their particle ranges), a bucket is up to 32 consecutive particles of
-// one instance (one warp), and each instance has an implicit complete binary
-// tree over its buckets.  Every phase is one launch over all instances.
+// overlap tests of those bounds.  Here the order is a 30-bit curve order per
+// instance (stable LSD radix sort of (instance, curve index) keys, so
+// instances keep their particle ranges), a bucket is up to 32 consecutive
+// particles of one instance inside one small key cell (one warp), and each
+// instance has an implicit complete binary tree over its bucket slots.  Every
+// phase is one launch over all instances.
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -193,7 +194,7 @@ __global__ void k_morton(int n, const Inst *__restrict__ insts,
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort of (instance, Morton) keys, 8-bit digits, tiles of
+// stable LSD radix sort of (instance, curve index) keys, 8-bit digits, tiles of
 // 2048 keys (256 threads x 8).  Per pass: tile histograms, a per-digit scan
 // over the tiles (one block per digit), and a stable scatter whose ranks
 // come from warp-level match_any in key order.
@@ -893,7 +894,7 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;
     const int n = (int)p.n;
-    // bounding boxes for the Morton quantisation (only open axes need data)
+    // bounding boxes for the key quantisation (only open axes need data)
     if (kp.any_open) {
         k_bbox_partial<<<dim3(kBboxChunks, kp.ninst), 256, 0, s>>>(c.inst, p.x[0], p.x[1], p.x[2],
                                                                  c.bbox_part);

@@ -65,7 +65,7 @@ __host__ __device__ inline int64_t bucket_slots(int64_t n)
 {
     return n > 0 ? (n + kBucket - 1) / kBucket + (n + 2 * kBucket - 1) / (2 * kBucket) + 8 : 0;
 }
-constexpr int kMortonBits = 10;   // bits per axis of the Morton key (30 bits)
+constexpr int kMortonBits = 10;   // bits per axis of a curve key (30 bits per instance)
 constexpr int kRelistRounds = 3;  // re-walk rounds queued after the first density pass
 constexpr int kBboxChunks = 32;   // blocks per instance for open-axis bounding boxes
 constexpr int kConsChunk = 2048;  // particles per block of the conserved totals
@@ -123,7 +123,7 @@ struct Inst {
 struct KParams {
     int kernel, energy_mode, max_newton;
     int ninst, n, nb, ng, nnodes;
-    int key_passes;      // 8-bit radix passes over (instance, Morton) keys
+    int key_passes;      // 8-bit radix passes over (instance, curve index) keys
     int any_open;        // some instance has an open axis
     float h_rel_tol, margin;
 };
