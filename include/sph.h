@@ -274,11 +274,16 @@ sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double *ou
  * legacy default stream.  In SPH_ENERGY_ISENTROPIC mode capture after one
  * plain sph_step, so the previous density exists.  A new capture replaces
  * the old graph.
+ * The graph also reduces the conserved totals of the stepped state (as
+ * sph_reduce_conserved).
  * sph_graph_launch: replay the captured step on `stream`, wait, and report
  * the status like sph_step (dt_used: new step of instance 0, may be NULL).
+ * sph_graph_totals: the totals of the last successful replay (HOST array of 9
+ * doubles per instance); SPH_ERR_STATE before the first replay.
  */
 sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double dt_fixed, void *stream);
 sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stream);
+sph_status sph_graph_totals(const sph_ctx *ctx, double *out);
 
 /* sph_batch_get_dt: the step size each instance used in the last
  * kick-drift-kick (host array of one double per instance). */

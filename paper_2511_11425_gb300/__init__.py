@@ -30,7 +30,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
            "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
            "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
-           "sph_graph_capture", "sph_graph_launch", "sph_mlp_set_weights", "sph_mlp_get_weights",
+           "sph_graph_capture", "sph_graph_launch", "sph_graph_totals", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
            "sph_mlp_load_samples", "sph_bucket_layout", "sph_probe_fp32_peak",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
@@ -105,6 +105,7 @@ def lib():
         L.sph_batch_get_dt.argtypes = [vp, C.POINTER(dbl)]
         L.sph_graph_capture.argtypes = [vp, pp, dbl, vp]
         L.sph_graph_launch.argtypes = [vp, C.POINTER(dbl), vp]
+        L.sph_graph_totals.argtypes = [vp, C.POINTER(dbl)]
         L.sph_set_dt_old.argtypes = [vp, dbl]
         fp = C.POINTER(C.c_float)
         L.sph_mlp_set_weights.argtypes = [vp, fp, i64]
@@ -316,6 +317,14 @@ def sph_graph_launch(ctx, stream=None) -> float:
     dt = C.c_double()
     _check(ctx, lib().sph_graph_launch(ctx, C.byref(dt), _stream(stream)))
     return dt.value
+
+
+def sph_graph_totals(ctx, ninst=None):
+    """Conserved totals after the last graph replay (9 per instance)."""
+    k = ninst or getattr(ctx, "ninst", 1)
+    out = (C.c_double * (9 * k))()
+    _check(ctx, lib().sph_graph_totals(ctx, out))
+    return list(out)
 
 
 def sph_destroy(ctx):

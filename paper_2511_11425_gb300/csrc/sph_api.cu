@@ -391,8 +391,19 @@ sph_status finish(sph_ctx *ctx, cudaStream_t s)
 float elapsed(cudaEvent_t a, cudaEvent_t b)
 {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        ms = 0.f;
+        (void)cudaGetLastError();  // a missing record is not a failure of the step
+    }
     return ms;
+}
+
+// phase event; under stream capture it must become a record node of the
+// graph (a plain record only orders the captured work)
+cudaError_t record(const Ctx &c, cudaEvent_t e, cudaStream_t s)
+{
+    return c.capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                       : cudaEventRecord(e, s);
 }
 
 // make sure the layout matches p->n (single-problem contexts follow n)
@@ -422,11 +433,11 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
     // overwrite c.h_seed)
     if (c.mlp.seed0 && (c.mlp.record || c.mlp.seed_mode == SPH_SEED_MLP))
         CK(cudaMemcpyAsync(c.mlp.seed0, c.h_seed, bytes, cudaMemcpyDeviceToDevice, s));
-    if (timed) CK(cudaEventRecord(c.kev[0], s));
+    if (timed) CK(record(c, c.kev[0], s));
     CK(launch_walk(c, *p, WALK_DENSITY, -1, c.h_seed, s));
-    if (timed) CK(cudaEventRecord(c.kev[1], s));
+    if (timed) CK(record(c, c.kev[1], s));
     CK(launch_density(c, *p, c.h_seed, -1, 0, 0, nullptr, nullptr, s));
-    if (timed) CK(cudaEventRecord(c.kev[2], s));
+    if (timed) CK(record(c, c.kev[2], s));
     // groups whose h left the list coverage: re-walk and re-solve on the
     // device (the launches exit at once when nothing is queued)
     for (int r = 0; r < kRelistRounds; ++r) {
@@ -442,11 +453,11 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
 sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed)
 {
     CK(launch_predict(c, *p, s));
-    if (timed) CK(cudaEventRecord(c.kev[3], s));
+    if (timed) CK(record(c, c.kev[3], s));
     CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
-    if (timed) CK(cudaEventRecord(c.kev[4], s));
+    if (timed) CK(record(c, c.kev[4], s));
     CK(launch_forces(c, *p, s));
-    if (timed) CK(cudaEventRecord(c.kev[5], s));
+    if (timed) CK(record(c, c.kev[5], s));
     CK(launch_finalize(c, *p, s));
     return SPH_OK;
 }
@@ -673,7 +684,7 @@ namespace {
 // the whole step queued without host round trips
 sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool timed)
 {
-    if (timed) CK(cudaEventRecord(c.ev0, s));
+    if (timed) CK(record(c, c.ev0, s));
     CK(launch_build(c, *p, s));
     sph_status rc = q_density(c, p, nullptr, s, timed);
     if (rc) return rc;
@@ -744,15 +755,25 @@ extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double d
     if (c.graph) cudaGraphDestroy(c.graph);
     c.graph_exec = nullptr;
     c.graph = nullptr;
+    c.graph_replayed = false;
     const uint64_t l0 = c.launches;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     c.err.clear();
+    c.capturing = true;
     sph_status qrc = SPH_OK;
     if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) qrc = SPH_ERR_CUDA;
-    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, false);
+    // phase events are captured too (event record nodes), so a replay reports
+    // the same per-phase times as sph_step
+    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true);
+    // the totals of the stepped state ride along (read with sph_graph_totals)
+    if (qrc == SPH_OK && launch_conserved(c, *p, s) != cudaSuccess) qrc = SPH_ERR_CUDA;
+    if (qrc == SPH_OK && cudaMemcpyAsync(c.cons_host, c.cons_out, sizeof(double) * 9 * c.kp.ninst,
+                                         cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        qrc = SPH_ERR_CUDA;
     if (qrc == SPH_OK) qrc = queue_status(c, s);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
+    c.capturing = false;
     const uint64_t kernels = c.launches - l0;
     c.launches = l0;
     if (qrc != SPH_OK || e != cudaSuccess || !g) {
@@ -768,6 +789,15 @@ extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double d
     return SPH_OK;
 }
 
+extern "C" sph_status sph_graph_totals(const sph_ctx *ctx, double *out)
+{
+    if (!ctx || !out) return SPH_ERR_ARG;
+    const Ctx &c = ctx->c;
+    if (!c.graph_exec || !c.graph_replayed) return SPH_ERR_STATE;
+    std::memcpy(out, c.graph_totals.data(), sizeof(double) * c.graph_totals.size());
+    return SPH_OK;
+}
+
 extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stream)
 {
     if (!ctx) return SPH_ERR_ARG;
@@ -775,15 +805,15 @@ extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stre
     if (!c.graph_exec) return failf(c, SPH_ERR_STATE, "no captured step: call sph_graph_capture");
     cudaStream_t s = (cudaStream_t)stream;
     c.err.clear();
-    CK(cudaEventRecord(c.ev0, s));
     CK(cudaGraphLaunch(c.graph_exec, s));
     CK(cudaEventRecord(c.ev1, s));
     c.launches += c.graph_kernels;
     sph_status rc = settle(ctx, s);
-    step_done(c, rc, false);
-    c.stats.ms_build = elapsed(c.ev0, c.ev1);  // the whole replay
-    c.stats.ms_density = c.stats.ms_forces = 0.f;
-    c.stats.ms_density_kernel = c.stats.ms_force_kernel = c.stats.ms_walk = 0.f;
+    step_done(c, rc, true);
+    if (rc == SPH_OK) {
+        c.graph_totals.assign(c.cons_host, c.cons_host + 9 * c.kp.ninst);
+        c.graph_replayed = true;
+    }
     if (rc == SPH_OK && dt_used) *dt_used = c.dt_host[0];
     return rc;
 }

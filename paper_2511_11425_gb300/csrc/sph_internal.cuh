@@ -226,6 +226,9 @@ struct Ctx {
     sph_particles graph_p{};
     double graph_dt = 0.0;
     uint64_t graph_kernels = 0;   // kernels in one replay
+    bool graph_replayed = false;
+    bool capturing = false;       // queueing into a stream capture
+    std::vector<double> graph_totals;  // conserved totals after the last replay
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -89,7 +89,11 @@ def test_graph_replay_matches_plain_steps(sph):
         stream.synchronize()
         ga = to_input_order(a.parts.numpy())
         gb = to_input_order(b.parts.numpy())
-        launches = sph.sph_get_stats(b.ctx)["launches"]
+        st = sph.sph_get_stats(b.ctx)
+        launches = st["launches"]
+        # the replay carries the totals of the stepped state and phase times
+        assert sph.sph_graph_totals(b.ctx) == sph.sph_reduce_conserved(b.ctx, b.parts)
+        assert st["ms_density_kernel"] > 0 and st["ms_force_kernel"] > 0
     finally:
         a.close()
         b.close()
