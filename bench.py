@@ -155,8 +155,10 @@ def cpu_baseline(prob, target_s=15.0):
         oracle.forces(p, prob.pos, prob.vel, prob.m, h, rho, om, prob.u, sinks)
         return time.perf_counter() - t0
 
-    t = run(64)
-    S = int(min(16384, max(64, 64 * target_s / max(t, 1e-3))))
+    # calibrate on two sizes, then one run of about target_s seconds
+    run(64)
+    t = run(1024)
+    S = int(min(prob.n, max(1024, 1024 * target_s / max(t, 1e-3))))
     t = run(S)
     cores = int(oracle.lib().orc_num_threads())
     return {"value": S / t, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -448,6 +450,8 @@ def run_ours(args, rank, world, local_rank):
           for _ in range(args.steps)]
     kd = kf = 0.0
     dpairs = fpairs = fav = dcand = fcand = 0
+    phase = {k: 0.0 for k in ("ms_build", "ms_walk", "ms_density_kernel", "ms_density",
+                              "ms_force_kernel", "ms_forces")}
     t_sim = 0.0
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
@@ -459,6 +463,8 @@ def run_ours(args, rank, world, local_rank):
             st = sph.sph_get_stats(sim.ctx)
             kd += st["ms_density_kernel"]
             kf += st["ms_force_kernel"]
+            for key in phase:
+                phase[key] += st[key] / args.steps
             dpairs += st["density_pairs"]
             fpairs += st["force_pairs"]
             fav += st["force_av_pairs"]
@@ -548,6 +554,13 @@ def run_ours(args, rank, world, local_rank):
                     "total": world * (dpairs + fpairs) / secs},
                 "candidates_per_useful_pair": {"density": dcand / max(dpairs, 1),
                                                "force": fcand / max(fpairs, 1)},
+                "phase_ms_per_step": {
+                    "build": phase["ms_build"],
+                    "density_walk_newton_refit": phase["ms_density"],
+                    "of_which_density_kernel": phase["ms_density_kernel"],
+                    "forces_predict_walk_pairs_finalize_kdk_totals": phase["ms_forces"],
+                    "of_which_force_kernel": phase["ms_force_kernel"],
+                    "walks": phase["ms_walk"]},
                 "roofline": roof, "roofline_other": other_line, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
                 "forms": forms, "impl": "ours"}

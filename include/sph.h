@@ -188,7 +188,8 @@ sph_status sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream);
  * 4/3 pi h^3 rho(h) = N_ngb m by Newton-Raphson with a bisection safeguard,
  * starting from h_seed (device array of n floats, curve order) or, if
  * h_seed is NULL, from p->h.  Writes p->h, p->rho, p->omega, p->nngb,
- * p->iters.  In SPH_ENERGY_ISENTROPIC mode it also moves u along its adiabat
+ * p->iters; h is the Newton update of the last evaluation (whose step was
+ * below h_rel_tol), rho, Omega and nngb are those of the evaluated h.  In SPH_ENERGY_ISENTROPIC mode it also moves u along its adiabat
  * to the new density, u <- u (rho/rho_old)^(gamma-1), using the rho left in
  * p->rho by the previous call.  Then refreshes the box-of-balls bounds with
  * the new h (Sec. 2.3.3, bounds updated after the density pass).

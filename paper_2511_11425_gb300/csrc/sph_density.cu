@@ -247,13 +247,18 @@ __device__ __forceinline__ void density_bucket(
             const int nn = cnt - 1;  // the particle itself is always in its own list
             pairs += (unsigned long long)(nn > 0 ? nn : 0);
             bool record = fixed_h != 0;
+            float h_final = h;
             if (!record) {
                 float g = kFourPiThird * K::sigma * swv / me.w - n_ngb;
                 float dg = -kFourPiThird * K::sigma * sqv / (me.w * h);
                 if (g < 0.f) lo = h; else hi = h;
                 float hn = dg > 0.f ? h - g / dg : NAN;
                 if (isfinite(hn) && fabsf(hn - h) < kp.h_rel_tol * h) {
+                    // converged: report the Newton update of the last
+                    // evaluation (quadratically closer to the root; rho,
+                    // Omega and n_i stay those of the evaluated h)
                     record = true;
+                    h_final = hn;
                 } else {
                     if (!(hn > lo && hn < hi)) hn = isfinite(hi) ? 0.5f * (lo + hi) : 2.f * h;
                     if (hn > R) {
@@ -278,7 +283,7 @@ __device__ __forceinline__ void density_bucket(
             if (record) {
                 done = true;
                 conv = true;
-                out_h = h;
+                out_h = h_final;
                 out_rho = K::sigma * swv * ih * ih * ih;
                 out_om = -sqv / (3.f * swv);
                 out_n = nn;

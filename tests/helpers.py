@@ -61,7 +61,7 @@ def oracle_neighbourhood(prob, sinks, radius):
     return np.nonzero(keep)[0]
 
 
-def oracle_sampled(prob, p, sinks, hood_factor=2.2):
+def oracle_sampled(prob, p, sinks, hood_factor=2.2, radius=None):
     """Oracle density + forces for the sinks only, exact for them.
 
     Density (h, rho, Omega) is solved by brute force over all N for every
@@ -71,7 +71,7 @@ def oracle_sampled(prob, p, sinks, hood_factor=2.2):
     so they cannot enter a sink's sums).
     """
     sinks = np.asarray(sinks)
-    R = hood_factor * float(np.max(prob.h0))
+    R = radius if radius is not None else hood_factor * float(np.max(prob.h0))
     hood = oracle_neighbourhood(prob, sinks, R)
     d = oracle.density_h(p, prob.pos, prob.m, prob.h0, hood)
     assert d["failed"] == 0

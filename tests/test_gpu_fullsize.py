@@ -1,0 +1,126 @@
+"""Parity at the full sizes of the paper-shaped workloads, on sampled sinks.
+
+Every particle is evaluated on the GPU (build, density/h, forces) exactly as
+the benchmark runs it; the FP64 oracle solves h by brute force over all N
+for the neighbourhoods of clusters of sink particles and evaluates the
+forces of those sinks (tests/helpers.oracle_sampled).  Tolerances: h, rho,
+Omega to 1e-5 relative; accelerations, du/dt and div v to 2e-4 of the
+field's max norm over the sinks.
+
+  Kelvin-Helmholtz shear layer, 128^3 = 2,097,152 particles, sinks at both
+  shear interfaces and at random points;
+  colliding spheres, 8,000,000 particles (open box, random 1/r profiles),
+  sinks in the large sphere's dense core, at its free surface and at the
+  small sphere's surface facing it;
+  the batch of 256 Sod / Sedov instances (10,785,863 particles) in one
+  batch context, sinks in the smallest and largest Sod and Sedov instances
+  (each checked against the oracle on its own instance)."""
+import numpy as np
+import pytest
+
+from helpers import norm_err, oracle_params, oracle_sampled, rel_max, to_input_order
+from paper_2511_11425_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_H = 1e-5
+TOL_F = 2e-4
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2511_11425_gb300 as m
+    m.lib()
+    return m
+
+
+def _evaluate(sph, parts, ctx):
+    sph.sph_build_cells(ctx, parts)
+    sph.sph_density_h(ctx, parts)
+    sph.sph_forces(ctx, parts)
+    return to_input_order(parts.numpy())
+
+
+def _clusters(prob, centres, per):
+    L = np.array(prob.box_hi) - np.array(prob.box_lo)
+    per_ax = np.array(prob.periodic, dtype=bool)
+    sinks = []
+    for c in centres:
+        d = prob.pos - np.asarray(c)
+        d[:, per_ax] -= L[per_ax] * np.round(d[:, per_ax] / L[per_ax])
+        sinks.extend(np.argsort((d * d).sum(1))[:per])
+    return np.unique(np.array(sinks))
+
+
+def _check(g, o, sinks, off=0):
+    idx = sinks + off
+    assert rel_max(g["h"][idx], o["h"]) < TOL_H
+    assert rel_max(g["rho"][idx], o["rho"]) < TOL_H
+    assert rel_max(g["omega"][idx], o["omega"]) < TOL_H
+    for k in ("a", "dudt_h", "dudt_av", "divv"):
+        assert norm_err(g[k][idx], o[k]) < TOL_F, k
+
+
+def test_kelvin_helmholtz_128_cubed(sph):
+    prob = inputs.kh(n=128)
+    parts = sph.Particles.from_problem(prob)
+    ctx = sph.sph_create(sph.Params.for_problem(prob), prob.n)
+    try:
+        g = _evaluate(sph, parts, ctx)
+    finally:
+        sph.sph_destroy(ctx)
+    rng = np.random.default_rng(11)
+    centres = [[0.3, 0.25, 0.6], [0.7, 0.75, 0.2], [0.05, 0.2501, 0.95]] + list(rng.random((2, 3)))
+    sinks = _clusters(prob, centres, 16)
+    o = oracle_sampled(prob, oracle_params(prob), sinks)
+    assert np.any(o["dudt_av"] != 0.0)          # viscosity is active at the shear
+    _check(g, o, sinks)
+
+
+def test_colliding_spheres_8m(sph):
+    prob = inputs.collision(n_total=8_000_000)
+    parts = sph.Particles.from_problem(prob)
+    ctx = sph.sph_create(sph.Params.for_problem(prob), prob.n)
+    try:
+        g = _evaluate(sph, parts, ctx)
+    finally:
+        sph.sph_destroy(ctx)
+    # the dense core of the large sphere, its free surface, and the small
+    # sphere's surface facing the large one; the oracle's neighbourhood
+    # radius follows the local smoothing length of each cluster
+    p = oracle_params(prob)
+    for c in ([0.0, 0.0, 0.0], [0.0, 0.0, 0.999], [1.1, 0.5, 0.0]):
+        sinks = _clusters(prob, [c], 8)
+        o = oracle_sampled(prob, p, sinks, radius=3.4 * float(np.max(prob.h0[sinks])))
+        _check(g, o, sinks)
+
+
+def test_batch_of_256_instances(sph):
+    probs = inputs.batch()
+    params = [sph.Params.for_problem(p) for p in probs]
+    parts, offs = sph.Particles.from_problems(probs, "cuda:0")
+    ctx = sph.sph_batch_create(params, offs)
+    try:
+        g = _evaluate(sph, parts, ctx)
+    finally:
+        sph.sph_destroy(ctx)
+    sizes = np.array([p.n for p in probs])
+    picks = set()
+    for name in ("sod", "sedov"):
+        ks = [k for k, p in enumerate(probs) if p.name == name]
+        picks.add(min(ks, key=lambda k: sizes[k]))
+        picks.add(max(ks, key=lambda k: sizes[k]))
+    rng = np.random.default_rng(3)
+    for k in sorted(picks):
+        prob = probs[k]
+        lo, hi = np.array(prob.box_lo), np.array(prob.box_hi)
+        centres = [lo + rng.random(3) * (hi - lo) for _ in range(2)]
+        if prob.name == "sod":
+            centres.append([0.0, 0.5 * hi[1], 0.5 * hi[2]])   # the contact
+        else:
+            centres.append([0.5, 0.5, 0.5])                    # the blast
+        sinks = _clusters(prob, centres, 12)
+        o = oracle_sampled(prob, oracle_params(prob), sinks)
+        _check(g, o, sinks, off=int(offs[k]))
