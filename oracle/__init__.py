@@ -102,7 +102,7 @@ def lib():
                                      ip, dp]
         L.orc_neighbours.restype = C.c_int64
         L.orc_forces.argtypes = [pp, C.c_int64, dp, dp, dp, dp, dp, dp, dp, C.c_int64, ip,
-                                 dp, dp, dp, dp, dp]
+                                 dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -205,14 +205,20 @@ def forces(params: Params, pos, vel, m, h, rho, omega, u, sinks=None):
     n = len(m)
     s, ns = _sinks(n, sinks)
     acc = np.empty((ns, 3))
-    out = {k: np.empty(ns) for k in ("dudt_h", "dudt_av", "divv", "dt")}
+    out = {k: np.empty(ns) for k in ("dudt_h", "dudt_av", "divv", "dt", "vdw_abs")}
     cp = params.c()
     lib().orc_forces(C.byref(cp), n, _ptr(pos), _ptr(vel), _ptr(m), _ptr(h), _ptr(rho),
                      _ptr(omega), _ptr(u), ns,
                      _ptr(s, C.c_int64) if s is not None else None,
                      _ptr(acc), _ptr(out["dudt_h"]), _ptr(out["dudt_av"]),
-                     _ptr(out["divv"]), _ptr(out["dt"]))
+                     _ptr(out["divv"]), _ptr(out["dt"]), _ptr(out["vdw_abs"]))
     out["a"] = acc
+    # conditioning of the PdV / div v sums (sum of the terms' magnitudes),
+    # in the units of dudt_h and divv
+    si = s if s is not None else np.arange(n)
+    P = (params.gamma - 1.0) * rho[si] * u[si]
+    out["dudt_h_scale"] = np.abs(P / (omega[si] * rho[si] ** 2)) * out["vdw_abs"]
+    out["divv_scale"] = out["vdw_abs"] / np.abs(omega[si] * rho[si])
     return out
 
 

@@ -262,7 +262,7 @@ void orc_forces(const orc_params *p, int64_t n, const double *pos, const double 
                 const double *m, const double *h, const double *rho, const double *omega,
                 const double *u, int64_t ns, const int64_t *sinks,
                 double *acc_out, double *dudt_h_out, double *dudt_av_out, double *divv_out,
-                double *dt_out)
+                double *dt_out, double *vdw_abs_out)
 {
     const double g = p->gamma;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -273,6 +273,7 @@ void orc_forces(const orc_params *p, int64_t n, const double *pos, const double 
         double Ai = Pi_ / (omega[i] * rho[i] * rho[i]);
         double a[3] = {0.0, 0.0, 0.0};
         double sum_vdw = 0.0, du_av = 0.0;
+        double abs_vdw = 0.0;  /* sum of |terms| of sum_vdw: its conditioning */
         double cfl = h[i] / ((1.0 + 0.6 * p->alpha) * ci);
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
@@ -293,6 +294,7 @@ void orc_forces(const orc_params *p, int64_t n, const double *pos, const double 
             /* hydro (pressure) part */
             for (int a_ = 0; a_ < 3; ++a_) a[a_] -= m[j] * (Ai * gi[a_] + Aj * gj[a_]);
             sum_vdw += m[j] * (vij[0] * gi[0] + vij[1] * gi[1] + vij[2] * gi[2]);
+            abs_vdw += fabs(m[j] * (vij[0] * gi[0] + vij[1] * gi[1] + vij[2] * gi[2]));
             /* artificial viscosity */
             double vr = vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2];
             double hb = 0.5 * (h[i] + h[j]);
@@ -316,6 +318,7 @@ void orc_forces(const orc_params *p, int64_t n, const double *pos, const double 
         dudt_h_out[s] = Ai * sum_vdw;
         dudt_av_out[s] = du_av;
         divv_out[s] = -sum_vdw / (omega[i] * rho[i]);
+        if (vdw_abs_out) vdw_abs_out[s] = abs_vdw;
         double amag = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
         double dta = amag > 0.0 ? p->eta_acc * sqrt(h[i] / amag) : INFINITY;
         double dtc = p->eta_courant * cfl;

@@ -82,14 +82,15 @@ struct SinkState {
     Kahan ax, ay, az, S;
     float du, mumax;
     int i;
-    unsigned long long pairs, av;
+    unsigned pairs, av;
 };
 
 // per-warp shared-memory stage of one chunk of source candidates
 struct ForceStage {
-    float4 pos[kChunk];  // position in the sink frame, h
+    float4 pos[kChunk];  // position in the sink frame, h^2
     float4 vel[kChunk];  // predicted velocity, m
-    float4 th[kChunk];   // A = P/(Omega rho^2), c, rho, -
+    float4 th[kChunk];   // A = P/(Omega rho^2), c, rho, h
+    float ih[kChunk];    // 1/h, correctly rounded (once per staged source)
     int idx[kChunk];
 };
 
@@ -112,7 +113,10 @@ struct Visc {
     float alpha, beta, eps_av;
 };
 
-template <class K, bool WRAP>
+// SELF: the chunk holds the sink bucket's own particles, where only j > i
+// counts (every other source bucket lies after the sink bucket, so all its
+// particles do)
+template <class K, bool WRAP, bool SELF>
 __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, ForceStage &S, int c,
                                             SinkState &s, bool valid, int lane, float4 *acc,
                                             float2 *acc2)
@@ -123,7 +127,8 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         S.idx[k] = -1;
     }
     __syncwarp();
-    // hit masks: r < max(h_i, h_j) and j > i (each unordered pair once)
+    // hit masks: r < max(h_i, h_j) (and j > i in the own bucket): each
+    // unordered pair once
     unsigned w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
     if (valid) {
 #pragma unroll 1
@@ -135,7 +140,8 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
                 float dx, dy, dz;
                 sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bool hit = r2 < fmaxf(s.h2, q.w * q.w) && S.idx[32 * ww + b] > s.i;
+                bool hit = r2 < fmaxf(s.h2, q.w);
+                if (SELF) hit = hit && S.idx[32 * ww + b] > s.i;
                 mw |= hit ? (1u << b) : 0u;
             }
             if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
@@ -160,7 +166,7 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
-        const float hj = q.w, ihj = __frcp_rn(hj);
+        const float hj = tj.w, ihj = S.ih[k];
         const float ihj2 = ihj * ihj;
         const float qi = r * s.ih, qj = r * ihj;
         const float Fi = qi < 1.f ? s.ih5 * K::dwq(qi) : 0.f;
@@ -256,14 +262,8 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
             if (lane == (int)w) myword = bal;
         }
     }
-    const unsigned nwords = (nl + 31) / 32;
-    int c = 0;
-    for (unsigned w = 0; w < nwords; ++w) {
-      unsigned mw = __shfl_sync(kFull, myword, w);
-      while (mw) {
-        const unsigned e = 32 * w + __ffs(mw) - 1;
-        mw &= mw - 1u;
-        const int B = (int)list[s0 + e];
+    // stage the culled particles of source bucket B after the c staged ones
+    auto stage = [&](int B, int c) -> int {
         const float3 off = origin_offset(I, kp.nb, origin, A, B);
         const int j0 = bstart[B];
         const int j = j0 + lane;
@@ -292,16 +292,37 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         const unsigned bal = __ballot_sync(kFull, in);
         if (in) {
             const int pos = c + __popc(bal & lt);
-            S.pos[pos] = make_float4(sp[0], sp[1], sp[2], q.w);
+            const float4 t = fth[j];
+            S.pos[pos] = make_float4(sp[0], sp[1], sp[2], q.w * q.w);
             S.vel[pos] = fvel[j];
-            S.th[pos] = fth[j];
+            S.th[pos] = make_float4(t.x, t.y, t.z, q.w);
+            S.ih[pos] = __frcp_rn(q.w);
             S.idx[pos] = j;
         }
         c += __popc(bal);
+        return c;
+    };
+    // the sink bucket itself (the only source bucket needing j > i)
+    int c = stage(A, 0);
+    if (c > 0) {
+        __syncwarp();
+        cands += c;
+        force_chunk<K, WRAP, true>(bx, vp, S, c, s, valid, lane, acc, acc2);
+        c = 0;
+    }
+    const unsigned nwords = (nl + 31) / 32;
+    for (unsigned w = 0; w < nwords; ++w) {
+      unsigned mw = __shfl_sync(kFull, myword, w);
+      while (mw) {
+        const unsigned e = 32 * w + __ffs(mw) - 1;
+        mw &= mw - 1u;
+        const int B = (int)list[s0 + e];
+        if (B == A) continue;
+        c = stage(B, c);
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
-            force_chunk<K, WRAP>(bx, vp, S, c, s, valid, lane, acc, acc2);
+            force_chunk<K, WRAP, false>(bx, vp, S, c, s, valid, lane, acc, acc2);
             c = 0;
         }
       }
@@ -309,7 +330,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP>(bx, vp, S, c, s, valid, lane, acc, acc2);
+        force_chunk<K, WRAP, false>(bx, vp, S, c, s, valid, lane, acc, acc2);
     }
 }
 
@@ -398,7 +419,8 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const Inst *__restri
         if (s.du != 0.f) red_add_f32(&acc2[i].x, s.du);
         if (s.mumax > 0.f) atomicMax((int *)&acc2[i].y, __float_as_int(s.mumax));
     }
-    unsigned long long wp = warp_sum(s.pairs), wav = warp_sum(s.av);
+    unsigned long long wp = warp_sum((unsigned long long)s.pairs);
+    unsigned long long wav = warp_sum((unsigned long long)s.av);
     if (lane == 0) {
         atomicAdd(&st->force_pairs, wp);
         atomicAdd(&st->force_av_pairs, wav);

@@ -218,3 +218,26 @@ def test_courant_limit_scales_with_approach_speed():
         vel = np.array([[vx, 0.0, 0.0], [-vx, 0.0, 0.0]])
         dts.append(oracle.forces(p, pos, vel, *args)["dt"])
     assert np.allclose(dts[1] / dts[0], 0.5, rtol=1e-5)
+
+
+def test_pdv_sum_conditioning_output():
+    """vdw_abs (the sum of the magnitudes of the PdV terms, used to bound
+    FP32 cancellation) equals |sum| when every term has one sign (a uniform
+    expansion v = x: v_ij . r_ij > 0 and dW/dr <= 0) and bounds it in a
+    random flow; a uniform translation has no terms at all."""
+    prob = inputs.uniform(n=6, seed=35, jitter=0.3, vamp=0.0, periodic=(0, 0, 0))
+    p = _params(prob)
+    d = oracle.density_h(p, prob.pos, prob.m, prob.h0)
+    hubble = prob.pos - 0.5
+    f = oracle.forces(p, prob.pos, hubble, prob.m, d["h"], d["rho"], d["omega"], prob.u)
+    S = -f["divv"] * d["omega"] * d["rho"]
+    assert np.allclose(f["vdw_abs"], np.abs(S), rtol=1e-12)
+    assert np.allclose(f["divv_scale"], np.abs(f["divv"]), rtol=1e-12)
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=prob.pos.shape)
+    f = oracle.forces(p, prob.pos, v, prob.m, d["h"], d["rho"], d["omega"], prob.u)
+    S = -f["divv"] * d["omega"] * d["rho"]
+    assert np.all(f["vdw_abs"] >= np.abs(S) * (1 - 1e-12))
+    assert np.all(f["dudt_h_scale"] >= np.abs(f["dudt_h"]) * (1 - 1e-12))
+    f = oracle.forces(p, prob.pos, np.ones_like(v), prob.m, d["h"], d["rho"], d["omega"], prob.u)
+    assert np.all(f["vdw_abs"] == 0.0)
