@@ -41,10 +41,19 @@ SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_GHZ = 2.070
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
-# algorithmic flops (FMA = 2) per unit, counted from the kernels' inner loops
+# Algorithmic flops per unit (FMA = 2; add, mul, divide, rsqrt = 1; compares,
+# selects and min/max not counted), tallied from the pair loops:
+#  density pair (Wendland C2): separation 3, r^2 5, r 2, q 1, w(q) 6,
+#    w'(q)/q 3, S_w 2, S_q 4                                          = 26
+#  force pair without viscosity: separation 3, r^2 5, r 2, 1/h_j^2 1,
+#    q_i q_j 2, F_i 5, F_j 8, v_ij 3, v_ij.r_ij 5, coefficient 5,
+#    sink a 1+6, sink S 3, source a+S 9 (incl. the four adds)          = 61 (incl. 1/h_j
+#    staged once per source, counted per pair as the method needs it)
+#  viscosity on top: h, c, rho averages 6, mu 5, Pi 6, du/dt|Pi 3,
+#    sink du 2, source du 2                                            = 24
 FLOPS_DENSITY_PAIR = 26      # one useful (r < h) pair evaluation of one Newton pass
-FLOPS_FORCE_PAIR = 56        # one unordered pair, pressure terms, both sides
-FLOPS_FORCE_AV = 25          # extra flops of a pair with active viscosity
+FLOPS_FORCE_PAIR = 61        # one unordered pair, pressure and PdV terms, both sides
+FLOPS_FORCE_AV = 24          # extra flops of a pair with active viscosity
 METRIC = "SPH particle-steps/s"
 UNIT = "particle-steps/s"
 

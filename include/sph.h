@@ -97,6 +97,11 @@ typedef struct {
                               bucket_cell h (>= 1; 0 = 3)                        */
     double  group_cell;    /* a walk group stays inside one key cell of side <=
                               group_cell h (>= bucket_cell; 0 = 6)               */
+    int32_t resort_period; /* sph_step / graph replays re-sort the particles every
+                              resort_period steps and only refit the buckets'
+                              bounds to the moved particles in between (1..64;
+                              0 = 1); taken from the first instance of a batch  */
+    int32_t reserved_;     /* must be 0                                          */
 } sph_params;
 
 typedef struct {
@@ -243,7 +248,10 @@ sph_status sph_kdk_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double 
 
 /*
  * sph_step: one whole step = sph_build_cells, sph_density_h (seeded with the
- * current h), sph_forces, sph_kdk_step.  Same arguments and errors.
+ * current h), sph_forces, sph_kdk_step.  Same arguments and errors.  With
+ * params.resort_period = k > 1 only every k-th step re-sorts; the steps in
+ * between keep the buckets and refit their bounds to the moved particles
+ * (the results are the same up to summation order).
  */
 sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_used,
                     void *stream);
@@ -276,7 +284,8 @@ sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double *ou
  * plain sph_step, so the previous density exists.  A new capture replaces
  * the old graph.
  * The graph also reduces the conserved totals of the stepped state (as
- * sph_reduce_conserved).
+ * sph_reduce_conserved).  With resort_period > 1 a second graph (refit
+ * instead of re-sort) is captured and replays follow sph_step's schedule.
  * sph_graph_launch: replay the captured step on `stream`, wait, and report
  * the status like sph_step (dt_used: new step of instance 0, may be NULL).
  * sph_graph_totals: the totals of the last successful replay (HOST array of 9

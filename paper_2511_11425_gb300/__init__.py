@@ -52,7 +52,8 @@ class c_params(C.Structure):
                 ("periodic", C.c_int32 * 3), ("max_newton", C.c_int32),
                 ("h_rel_tol", C.c_double), ("list_margin", C.c_double),
                 ("curve", C.c_int32), ("group_log", C.c_int32),
-                ("bucket_cell", C.c_double), ("group_cell", C.c_double)]
+                ("bucket_cell", C.c_double), ("group_cell", C.c_double),
+                ("resort_period", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class c_particles(C.Structure):
@@ -167,6 +168,7 @@ class Params:
     group_log: int = 3
     bucket_cell: float = 3.0
     group_cell: float = 6.0
+    resort_period: int = 1
 
     def c(self) -> c_params:
         p = c_params()
@@ -178,6 +180,7 @@ class Params:
         p.max_newton = int(self.max_newton)
         p.curve = CURVES[self.curve]
         p.group_log = int(self.group_log)
+        p.resort_period = int(self.resort_period)
         for a in range(3):
             p.box_lo[a] = float(self.box_lo[a])
             p.box_hi[a] = float(self.box_hi[a])

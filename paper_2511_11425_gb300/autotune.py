@@ -3,10 +3,11 @@
 The step's cost depends on how particles are cut into warps and walks, not
 only on the hardware: the space-filling curve, the buckets per walk group
 (the paper's group size of Sec. 2.3.2), the largest key cell a bucket may
-span (in units of h) and the margin of the density lists (Sec. 2.3.3: lists
-are built for a slightly larger kernel).  None of them changes the result
-beyond rounding; each changes the candidates per useful pair, the walk work
-and the warp fill.  The tuner times whole steps of the caller's own state
+span (in units of h), the margin of the density lists (Sec. 2.3.3: lists
+are built for a slightly larger kernel) and how often the particles are
+re-sorted (between re-sorts the buckets' bounds are refitted).  None of
+them changes the result beyond rounding; each changes the candidates per
+useful pair, the walk work, the warp fill or the build work.  The tuner times whole steps of the caller's own state
 (on a copy) for candidate settings, one knob at a time (coordinate
 descent from the defaults), keeps the fastest, and caches the choice per
 GPU and configuration class (size, instance count, boundaries, kernel,
@@ -28,8 +29,9 @@ SPACE = {
     "group_log": [3, 2],
     "bucket_cell": [3.0, 2.0, 4.0],
     "list_margin": [0.1, 0.05, 0.2],
+    "resort_period": [1, 4],
 }
-ORDER = ("curve", "bucket_cell", "group_log", "list_margin")
+ORDER = ("resort_period", "curve", "bucket_cell", "group_log", "list_margin")
 
 
 def default_cache_path() -> str:
@@ -116,17 +118,20 @@ class Autotuner:
         else:
             ctx = sph_batch_create(params_list, offsets)
         s = torch.cuda.current_stream(dev)
+        # whole re-sort periods, so every setting is timed on its own mix
+        period = max(p.resort_period for p in params_list)
+        steps = period * max(1, -(-self.steps // period))
         try:
             for _ in range(self.warmup):
                 sph_step(ctx, work, 0.0, s)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(s)
-            for _ in range(self.steps):
+            for _ in range(steps):
                 sph_step(ctx, work, 0.0, s)
             b.record(s)
             b.synchronize()
-            return a.elapsed_time(b) / self.steps
+            return a.elapsed_time(b) / steps
         finally:
             sph_destroy(ctx)
 

@@ -80,6 +80,7 @@ bool params_ok(const sph_params *prm)
         !(prm->bucket_cell == 0.0 || prm->bucket_cell >= 1.0) ||
         !(prm->group_cell == 0.0 || prm->group_cell >= 1.0))
         return false;
+    if (prm->resort_period < 0 || prm->resort_period > 64 || prm->reserved_ != 0) return false;
     const double kb = prm->bucket_cell > 0.0 ? prm->bucket_cell : kKappaBucket;
     const double kg = prm->group_cell > 0.0 ? prm->group_cell : kKappaGroup;
     if (!(kg >= kb) || !std::isfinite(kg)) return false;
@@ -232,6 +233,8 @@ void free_ctx(Ctx &c)
 {
     if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
     if (c.graph) cudaGraphDestroy(c.graph);
+    if (c.graph_exec_r) cudaGraphExecDestroy(c.graph_exec_r);
+    if (c.graph_r) cudaGraphDestroy(c.graph_r);
     void *ptrs[] = {c.st, c.inst, c.dts, c.dtmin, c.morton_box, c.bbox_part, c.cons_part,
                     c.pad_agg, c.pad_used,
                     c.cons_out, c.pinst, c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist,
@@ -332,6 +335,7 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
         CK(cudaMemcpy(c.refit, sched.data(), sizeof(RefitBlock) * sched.size(),
                       cudaMemcpyHostToDevice));
     c.n_built = off;
+    c.order_fresh = false;
     // records of the last kick belong to the old layout
     if (c.mlp.th) CK(cudaMemset(c.mlp.th, 0, sizeof(float) * (size_t)c.capacity));
     return SPH_OK;
@@ -502,6 +506,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.kp.max_newton = prm[0].max_newton;
     c.kp.h_rel_tol = (float)prm[0].h_rel_tol;
     c.kp.margin = (float)prm[0].list_margin;
+    c.resort_period = prm[0].resort_period > 0 ? prm[0].resort_period : 1;
     c.kp.ninst = ninst;
     const Sizes z = layout_sizes(counts, c.prm);
     sph_status rc = allocate(c, z, ninst);
@@ -568,6 +573,8 @@ extern "C" sph_status sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stre
     rc = finish(ctx, s);
     c.stats.ms_build = elapsed(c.ev0, c.ev1);
     if (rc == SPH_OK) c.cells_valid = true;
+    c.order_fresh = rc == SPH_OK;
+    c.since_sort = 0;
     return rc;
 }
 
@@ -681,11 +688,33 @@ extern "C" sph_status sph_kdk_step(sph_ctx *ctx, sph_particles *p, double dt_fix
 }
 
 namespace {
+// does the next sph_step / replay re-sort (else it refits the buckets)?
+bool need_full_build(const Ctx &c)
+{
+    return !c.order_fresh || c.since_sort + 1 >= c.resort_period;
+}
+
+void count_build(Ctx &c, bool full, sph_status rc)
+{
+    if (rc != SPH_OK) {
+        c.order_fresh = false;
+    } else if (full) {
+        c.order_fresh = true;
+        c.since_sort = 0;
+    } else {
+        ++c.since_sort;
+    }
+}
+
 // the whole step queued without host round trips
-sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool timed)
+sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool timed,
+                      bool full_build)
 {
     if (timed) CK(record(c, c.ev0, s));
-    CK(launch_build(c, *p, s));
+    if (full_build)
+        CK(launch_build(c, *p, s));
+    else
+        CK(launch_refit(c, *p, s));
     sph_status rc = q_density(c, p, nullptr, s, timed);
     if (rc) return rc;
     rc = q_forces(c, p, s, timed);
@@ -731,12 +760,18 @@ extern "C" sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, 
     }
     rc = begin(ctx, s);
     if (rc) return rc;
-    rc = queue_step(c, p, dt_fixed, s, true);
+    const bool full = need_full_build(c);
+    rc = queue_step(c, p, dt_fixed, s, true, full);
     if (rc) return rc;
     rc = finish(ctx, s);
     step_done(c, rc, true);
+    count_build(c, full, rc);
     if (rc == SPH_OK && dt_used) *dt_used = c.dt_host[0];
     return rc;
+}
+
+namespace {
+sph_status capture_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool full);
 }
 
 extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double dt_fixed,
@@ -751,11 +786,26 @@ extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double d
     if (!(dt_fixed == dt_fixed) || std::isinf(dt_fixed))
         return failf(c, SPH_ERR_ARG, "sph_graph_capture: dt_fixed must be finite");
     cudaStream_t s = (cudaStream_t)stream;
-    if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
-    if (c.graph) cudaGraphDestroy(c.graph);
-    c.graph_exec = nullptr;
-    c.graph = nullptr;
+    for (cudaGraphExec_t *ge : {&c.graph_exec, &c.graph_exec_r})
+        if (*ge) cudaGraphExecDestroy(*ge);
+    for (cudaGraph_t *gr : {&c.graph, &c.graph_r})
+        if (*gr) cudaGraphDestroy(*gr);
+    c.graph_exec = c.graph_exec_r = nullptr;
+    c.graph = c.graph_r = nullptr;
     c.graph_replayed = false;
+    // one graph that re-sorts, and with a re-sort period one that refits
+    for (int mode = 0; mode < (c.resort_period > 1 ? 2 : 1); ++mode) {
+        const sph_status r = capture_step(c, p, dt_fixed, s, mode == 0);
+        if (r) return r;
+    }
+    c.graph_p = *p;
+    c.graph_dt = dt_fixed;
+    return SPH_OK;
+}
+
+namespace {
+sph_status capture_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool full)
+{
     const uint64_t l0 = c.launches;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     c.err.clear();
@@ -764,7 +814,7 @@ extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double d
     if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) qrc = SPH_ERR_CUDA;
     // phase events are captured too (event record nodes), so a replay reports
     // the same per-phase times as sph_step
-    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true);
+    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true, full);
     // the totals of the stepped state ride along (read with sph_graph_totals)
     if (qrc == SPH_OK && launch_conserved(c, *p, s) != cudaSuccess) qrc = SPH_ERR_CUDA;
     if (qrc == SPH_OK && cudaMemcpyAsync(c.cons_host, c.cons_out, sizeof(double) * 9 * c.kp.ninst,
@@ -781,13 +831,18 @@ extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double d
         return failf(c, SPH_ERR_CUDA, "stream capture of the step failed: %s",
                      e != cudaSuccess ? cudaGetErrorString(e) : c.err.c_str());
     }
-    c.graph = g;
-    CK(cudaGraphInstantiate(&c.graph_exec, g, 0));
-    c.graph_p = *p;
-    c.graph_dt = dt_fixed;
-    c.graph_kernels = kernels;
+    if (full) {
+        c.graph = g;
+        CK(cudaGraphInstantiate(&c.graph_exec, g, 0));
+        c.graph_kernels = kernels;
+    } else {
+        c.graph_r = g;
+        CK(cudaGraphInstantiate(&c.graph_exec_r, g, 0));
+        c.graph_kernels_r = kernels;
+    }
     return SPH_OK;
 }
+}  // namespace
 
 extern "C" sph_status sph_graph_totals(const sph_ctx *ctx, double *out)
 {
@@ -805,11 +860,13 @@ extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stre
     if (!c.graph_exec) return failf(c, SPH_ERR_STATE, "no captured step: call sph_graph_capture");
     cudaStream_t s = (cudaStream_t)stream;
     c.err.clear();
-    CK(cudaGraphLaunch(c.graph_exec, s));
+    const bool full = need_full_build(c) || !c.graph_exec_r;
+    CK(cudaGraphLaunch(full ? c.graph_exec : c.graph_exec_r, s));
     CK(cudaEventRecord(c.ev1, s));
-    c.launches += c.graph_kernels;
+    c.launches += full ? c.graph_kernels : c.graph_kernels_r;
     sph_status rc = settle(ctx, s);
     step_done(c, rc, true);
+    count_build(c, full, rc);
     if (rc == SPH_OK) {
         c.graph_totals.assign(c.cons_host, c.cons_host + 9 * c.kp.ninst);
         c.graph_replayed = true;

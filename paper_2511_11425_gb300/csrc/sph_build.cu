@@ -956,6 +956,17 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    const KParams &kp = c.kp;
+    const int wb = (kp.nb * 32 + 127) / 128;
+    c.launches += 1;
+    k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
+                                 c.origin, c.pm, c.node, 1, c.st);
+    tree_refit(c, s, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;

@@ -228,6 +228,14 @@ struct Ctx {
     uint64_t graph_kernels = 0;   // kernels in one replay
     bool graph_replayed = false;
     bool capturing = false;       // queueing into a stream capture
+    cudaGraph_t graph_r = nullptr;          // captured step that only refits
+    cudaGraphExec_t graph_exec_r = nullptr;
+    uint64_t graph_kernels_r = 0;
+
+    // re-sorting schedule of sph_step and graph replays
+    int resort_period = 1;
+    int since_sort = 0;           // refit-only steps since the last full build
+    bool order_fresh = false;     // a full build ran on this layout
     std::vector<double> graph_totals;  // conserved totals after the last replay
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -449,6 +457,8 @@ struct KM4 {
 enum WalkMode { WALK_DENSITY = 0, WALK_FORCE = 1 };
 // build (sph_build.cu)
 cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s);
+// bounds of the existing buckets refitted to moved particles (no re-sort)
+cudaError_t launch_refit(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s);
 // group walk: all groups (round < 0) or the groups queued for re-walk round r
 cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, const float *h_walk,

@@ -45,7 +45,7 @@ def test_struct_layouts_match_header(libpath):
     # sph_particles: n + 21 pointers; sph_params as laid out by a C compiler
     import paper_2511_11425_gb300 as sph
     assert ctypes.sizeof(sph.c_particles) == 8 + 21 * 8
-    assert ctypes.sizeof(sph.c_params) == 168
+    assert ctypes.sizeof(sph.c_params) == 176
     assert sph.c_params.h_rel_tol.offset == 128 and sph.c_params.list_margin.offset == 136
     assert sph.c_params.curve.offset == 144 and sph.c_params.group_log.offset == 148
     assert ctypes.sizeof(sph.c_stats) == 112
@@ -100,3 +100,5 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
         sph.sph_create(sph.Params(bucket_cell=0.5), 10)
     with pytest.raises(sph.SphError):
         sph.sph_create(sph.Params(bucket_cell=4.0, group_cell=3.0), 10)
+    with pytest.raises(sph.SphError):
+        sph.sph_create(sph.Params(resort_period=65), 10)

@@ -19,16 +19,20 @@ def test_coordinate_descent_finds_the_separable_optimum():
     def measure(k):
         calls.append(dict(k))
         return 10.0 + sum(cost[n][k[n]] for n in cost)
-    start = {"curve": "hilbert", "bucket_cell": 3.0, "group_log": 3, "list_margin": 0.1}
+    start = {"curve": "hilbert", "bucket_cell": 3.0, "group_log": 3, "list_margin": 0.1,
+             "resort_period": 1}
+    cost["resort_period"] = {1: 1.0, 4: 0.0}
+    best["resort_period"] = 4
     knobs, t, tried = autotune.coordinate_descent(measure, start)
     assert knobs == best and t == 10.0
-    assert len(tried) == len(calls) == 1 + 1 + 2 + 1 + 2
+    assert len(tried) == len(calls) == 1 + 1 + 1 + 2 + 1 + 2
 
 
 def test_small_gains_are_not_taken():
     def measure(k):
         return 100.0 - (1.0 if k["curve"] == "morton" else 0.0)   # 1 % faster only
-    start = {"curve": "hilbert", "bucket_cell": 3.0, "group_log": 3, "list_margin": 0.1}
+    start = {"curve": "hilbert", "bucket_cell": 3.0, "group_log": 3, "list_margin": 0.1,
+             "resort_period": 1}
     knobs, _, _ = autotune.coordinate_descent(measure, start)
     assert knobs["curve"] == "hilbert"
 
@@ -66,8 +70,8 @@ def test_cache_is_keyed_by_gpu_and_configuration(tmp_path):
 def test_tuned_params_change_only_layout_knobs():
     p = Params.for_problem(inputs.sod())
     q = autotune.with_knobs(p, {"curve": "morton", "bucket_cell": 4.0, "group_log": 2,
-                                "list_margin": 0.2})
-    assert q.group_cell == 8.0 and q.curve == "morton"
+                                "list_margin": 0.2, "resort_period": 4})
+    assert q.group_cell == 8.0 and q.curve == "morton" and q.resort_period == 4
     for f in ("gamma", "alpha", "beta", "n_ngb", "kernel", "box_lo", "box_hi", "periodic",
               "eta_courant", "h_rel_tol"):
         assert getattr(q, f) == getattr(p, f)
@@ -84,7 +88,7 @@ def test_tuned_step_matches_default_step(tmp_path):
     parts = sph.Particles.from_problem(prob)
     tuner = autotune.Autotuner(str(tmp_path / "t.json"), steps=1, warmup=1)
     tuned = tuner.tune(parts, base, force=True)
-    assert len(tuner.report["tried"]) >= 7
+    assert len(tuner.report["tried"]) >= 8
     assert all(r["ms_per_step"] > 0 for r in tuner.report["tried"])
     out = {}
     for name, prm in (("default", base), ("tuned", tuned)):

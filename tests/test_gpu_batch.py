@@ -133,3 +133,40 @@ def test_batch_simulation_graph_matches_plain_batch(sph):
         assert motion_err(gb["x"][sl], ga["x"][sl], p) < 1e-5, k
     assert norm_err(gb["a"], ga["a"]) < 1e-5
     assert np.allclose(ca[:, [0, 7, 8]], cb[:, [0, 7, 8]], rtol=1e-6)
+
+
+def test_resort_period_refits_between_sorts(sph):
+    """With resort_period 4, three of every four steps keep the bucket layout
+    and only refit its bounds: fewer kernels per step, the same motion (up to
+    summation order), in plain steps and in graph replays."""
+    import torch
+    prob = inputs.uniform(n=16, seed=13, vamp=0.4, jitter=0.3)
+    stream = torch.cuda.Stream()
+    runs = {}
+    for name, period, graph in (("sorted", 1, False), ("refit", 4, False),
+                                ("refit_graph", 4, True)):
+        s = sph.Simulation(prob, sph.Params.for_problem(prob, resort_period=period))
+        try:
+            with torch.cuda.stream(stream):
+                launches = []
+                if graph:
+                    sph.sph_step(s.ctx, s.parts, 0.0, stream)
+                    sph.sph_graph_capture(s.ctx, s.parts, 0.0, stream)
+                for k in range(8 if not graph else 7):
+                    l0 = sph.sph_get_stats(s.ctx)["launches"]
+                    if graph:
+                        sph.sph_graph_launch(s.ctx, stream)
+                    else:
+                        sph.sph_step(s.ctx, s.parts, 0.0, stream)
+                    launches.append(sph.sph_get_stats(s.ctx)["launches"] - l0)
+            stream.synchronize()
+            runs[name] = (to_input_order(s.parts.numpy()), launches)
+        finally:
+            s.close()
+    ref, lref = runs["sorted"]
+    for name in ("refit", "refit_graph"):
+        g, ln = runs[name]
+        assert motion_err(g["x"], ref["x"], prob) < 1e-5, name
+        assert norm_err(g["a"], ref["a"]) < 1e-5, name
+        assert min(ln) < min(lref), name      # refit steps launch fewer kernels
+    assert runs["refit"][1][0] == lref[0]     # the first step re-sorts
