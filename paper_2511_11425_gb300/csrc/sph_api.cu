@@ -244,7 +244,8 @@ void free_ctx(Ctx &c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mptrs[] = {c.mlp.w, c.mlp.m, c.mlp.v, c.mlp.frag, c.mlp.gpart, c.mlp.loss,
-                     c.mlp.seed0, c.mlp.tfeat, c.mlp.th, c.mlp.sx, c.mlp.sy, c.mlp.scount};
+                     c.mlp.seed0, c.mlp.corr, c.mlp.tfeat, c.mlp.th, c.mlp.sx, c.mlp.sy,
+                     c.mlp.scount};
     for (void *p : mptrs)
         if (p) cudaFree(p);
     for (void *p : {(void *)c.st_host, (void *)c.dts_host, (void *)c.cons_host})
@@ -980,6 +981,7 @@ sph_status ensure_mlp(Ctx &c)
     CK(dalloc(&c.mlp.frag, kMlpFragWords));
     CK(dalloc(&c.mlp.scount, 1));
     CK(dalloc(&c.mlp.seed0, (size_t)std::max<int64_t>(c.capacity, 1)));
+    CK(dalloc(&c.mlp.corr, (size_t)std::max<int64_t>(c.capacity, 1)));
     CK(cudaMemset(c.mlp.seed0, 0, sizeof(float) * (size_t)std::max<int64_t>(c.capacity, 1)));
     CK(cudaMemset(c.mlp.w, 0, sizeof(float) * kMlpParams));
     CK(cudaMemset(c.mlp.m, 0, sizeof(float) * kMlpParams));

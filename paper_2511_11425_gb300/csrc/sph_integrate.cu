@@ -74,71 +74,25 @@ __device__ __forceinline__ void kdk_particle(
 // The smoothing length is advanced with the drift as the seed of the next
 // density pass: the continuity equation gives rho(t + dt) ~ rho exp(-dt div v),
 // and h ~ rho^(-1/3), so h <- h exp(dt div v / 3) (factor clamped to [1/2, 2]).
-// MODE bit 0: the learned network adds its correction to that exponent;
-// MODE bit 1: the network inputs and h are stored for training samples.
-struct KdkMlp {
-    const uint32_t *frag;
-    const float *w;
-    const float *seed;           // seeds of this step's density pass
-    const unsigned short *nngb;
-    float *tfeat, *th;           // records (SoA x 4, h)
-    int cap;                     // record stride of tfeat
-    float dead;                  // corrections below this are not applied
-};
-
-template <int MODE>
+// CORR: the learned form adds the correction corr[i] (k_mlp_seed) to that
+// exponent.
+template <bool CORR>
 __global__ void k_kdk(KParams kp, int n, const Inst *__restrict__ insts,
                       const unsigned short *__restrict__ pinst, double *x, double *y, double *z,
                       double *vx, double *vy, double *vz, double *u, float *h,
                       const float *__restrict__ ax, const float *__restrict__ ay,
                       const float *__restrict__ az, const float *__restrict__ dudt_h,
                       const float *__restrict__ dudt_av, const float *__restrict__ divv,
-                      const double *__restrict__ dts, KdkMlp ml, const DevStatus *st)
+                      const double *__restrict__ dts, const float *__restrict__ corr,
+                      const DevStatus *st)
 {
     // an error raised earlier in the step leaves the state as it was
     if (st->code != 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (MODE != 0) {
-        // the network runs warp-wide: lanes past the end take part with zeros
-        const int lane = threadIdx.x & 31;
-        const bool valid = i < n;
-        float xin[4] = {0.f, 0.f, 0.f, 0.f};
-        float hi = 0.f, phi0 = 0.f;
-        if (valid) {
-            const int k = pinst[i];
-            const double dt_old = dts[2 * k], dt_new = dts[2 * k + 1];
-            hi = h[i];
-            phi0 = (float)dt_new * divv[i] * (1.f / 3.f);
-            xin[0] = kMlpXScale0 * phi0;
-            xin[1] = kMlpXScale1 * ((float)ml.nngb[i] / insts[k].n_ngb - 1.f);
-            const float sd = ml.seed[i];
-            xin[2] = sd > 0.f ? kMlpXScale2 * logf(hi / sd) : 0.f;
-            xin[3] = dt_old > 0.0 ? kMlpXScale3 * (float)log(dt_new / dt_old) : 0.f;
-            if (MODE & 2) {
-#pragma unroll
-                for (int a = 0; a < 4; ++a) ml.tfeat[(size_t)a * ml.cap + i] = xin[a];
-                ml.th[i] = hi;
-            }
-        }
-        float corr = 0.f;
-        // a particle whose last seed was within the Newton tolerance and whose
-        // continuity estimate moves h by less than it keeps that estimate:
-        // its h is already converged there, and a correction could only cost
-        // a Newton step (the whole warp still runs the network)
-        const float rest = kMlpXScale0 * kp.h_rel_tol;
-        const bool at_rest = fabsf(xin[0]) < rest && fabsf(xin[2]) < rest;
-        if (MODE & 1) {
-            corr = mlp_warp_infer(ml.frag, ml.w, xin[0], xin[1], xin[2], xin[3], lane) *
-                   (1.f / kMlpYScale);
-            if (!isfinite(corr) || at_rest || fabsf(corr) < ml.dead) corr = 0.f;
-        }
-        if (!valid) return;
-        kdk_particle(i, insts, pinst, x, y, z, vx, vy, vz, u, h, ax, ay, az, dudt_h, dudt_av,
-                     kp.energy_mode, dts, hi * fminf(fmaxf(expf(phi0 + corr), 0.5f), 2.f));
-        return;
-    }
     if (i >= n) return;
-    const float f = expf((float)dts[2 * pinst[i] + 1] * divv[i] * (1.f / 3.f));
+    float e = (float)dts[2 * pinst[i] + 1] * divv[i] * (1.f / 3.f);
+    if (CORR) e += corr[i];
+    const float f = expf(e);
     kdk_particle(i, insts, pinst, x, y, z, vx, vy, vz, u, h, ax, ay, az, dudt_h, dudt_av,
                  kp.energy_mode, dts, h[i] * fminf(fmaxf(f, 0.5f), 2.f));
 }
@@ -205,21 +159,20 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
     const int ni = c.kp.ninst;
     c.launches += 3;
     k_choose_dt<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts, c.dtmin, dt_fixed, c.st);
-    KdkMlp ml = {c.mlp.frag, c.mlp.w, c.mlp.seed0, p.nngb, c.mlp.tfeat, c.mlp.th,
-                 (int)c.capacity, c.mlp.dead};
-    const int mode = (c.mlp.seed_mode == SPH_SEED_MLP ? 1 : 0) | (c.mlp.record ? 2 : 0);
-    const int g = (n + 255) / 256;
-#define SPH_KDK(M)                                                                             \
-    k_kdk<M><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], \
-                               p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av,  \
-                               p.divv, c.dts, ml, c.st)
-    switch (mode) {
-    case 0: SPH_KDK(0); break;
-    case 1: SPH_KDK(1); break;
-    case 2: SPH_KDK(2); break;
-    default: SPH_KDK(3); break;
+    const bool corr = c.mlp.seed_mode == SPH_SEED_MLP;
+    if (corr || c.mlp.record) {  // network inputs, records, corrections
+        const cudaError_t e = launch_mlp_seed(c, p, s);
+        if (e != cudaSuccess) return e;
     }
-#undef SPH_KDK
+    const int g = (n + 255) / 256;
+    if (corr)
+        k_kdk<true><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
+                                      p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
+                                      p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr, c.st);
+    else
+        k_kdk<false><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
+                                       p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
+                                       p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr, c.st);
     k_dt_shift<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts);
     return cudaGetLastError();
 }

@@ -213,6 +213,7 @@ struct Ctx {
         int stride = 1;
         unsigned step = 0;           // harvest counter (sample selection)
         float *seed0 = nullptr;      // capacity: seeds of the last density pass as given
+        float *corr = nullptr;       // capacity: correction of the seed exponent
         float *tfeat = nullptr;      // 4 x capacity inputs of the last kick (SoA)
         float *th = nullptr;         // capacity: h at the last kick (0 = none)
         float *sx = nullptr, *sy = nullptr;  // samples: cap x 4, cap
@@ -479,6 +480,7 @@ cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s);
 // learned seed (sph_mlp.cu)
 cudaError_t launch_mlp_permute(Ctx &c, const unsigned *perm, int n, cudaStream_t s);
 cudaError_t launch_mlp_harvest(Ctx &c, const sph_particles &p, cudaStream_t s);
+cudaError_t launch_mlp_seed(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_mlp_pack(Ctx &c, cudaStream_t s);
 int mlp_grad_blocks(long long batch);
 cudaError_t launch_mlp_grad(Ctx &c, const float *sx, const float *sy, long long count,

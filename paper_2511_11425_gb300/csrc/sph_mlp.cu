@@ -279,7 +279,73 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const uint32_t *__restrict__ 
     if (valid) y[i] = out;
 }
 
+// Network inputs of every particle at the end of a step (after the step size
+// is chosen, before the kick moves h): MODE bit 1 records them with h for the
+// next harvest, bit 0 runs the network and leaves the correction of the
+// continuity exponent in corr[i] (0 where it is not applied: a particle at
+// rest within the Newton tolerance, a correction inside the dead zone, a
+// non-finite output).  Warps whose particles are all at rest skip the
+// network.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_mlp_seed(
+    KParams kp, int n, const Inst *__restrict__ insts, const unsigned short *__restrict__ pinst,
+    const float *__restrict__ h, const float *__restrict__ divv,
+    const unsigned short *__restrict__ nngb, const float *__restrict__ seed0,
+    const double *__restrict__ dts, const uint32_t *__restrict__ frag,
+    const float *__restrict__ w, float dead, int cap, float *tfeat, float *th, float *corr,
+    const DevStatus *st)
+{
+    if (st->code != 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    float xin[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const int k = pinst[i];
+        const double dt_old = dts[2 * k], dt_new = dts[2 * k + 1];
+        const float hi = h[i];
+        xin[0] = kMlpXScale0 * ((float)dt_new * divv[i] * (1.f / 3.f));
+        xin[1] = kMlpXScale1 * ((float)nngb[i] / insts[k].n_ngb - 1.f);
+        const float sd = seed0[i];
+        xin[2] = sd > 0.f ? kMlpXScale2 * logf(hi / sd) : 0.f;
+        // FP32 on purpose: a per-particle FP64 log costs more than the network
+        xin[3] = dt_old > 0.0 ? kMlpXScale3 * logf((float)dt_new / (float)dt_old) : 0.f;
+        if (MODE & 2) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) tfeat[(size_t)a * cap + i] = xin[a];
+            th[i] = hi;
+        }
+    }
+    if (!(MODE & 1)) return;
+    const float rest = kMlpXScale0 * kp.h_rel_tol;
+    const bool at_rest = !valid || (fabsf(xin[0]) < rest && fabsf(xin[2]) < rest);
+    float y = 0.f;
+    if (!__all_sync(kFull, at_rest)) {  // warp-uniform
+        y = mlp_warp_infer(frag, w, xin[0], xin[1], xin[2], xin[3], lane) * (1.f / kMlpYScale);
+        if (!isfinite(y) || at_rest || fabsf(y) < dead) y = 0.f;
+    }
+    if (valid) corr[i] = y;
+}
+
 // ---- launchers ---------------------------------------------------------------
+cudaError_t launch_mlp_seed(Ctx &c, const sph_particles &p, cudaStream_t s)
+{
+    const int n = (int)p.n;
+    const int mode = (c.mlp.seed_mode == SPH_SEED_MLP ? 1 : 0) | (c.mlp.record ? 2 : 0);
+    if (mode == 0 || n == 0) return cudaSuccess;
+    const int g = (n + 127) / 128;
+    c.launches += 1;
+#define SPH_SEED(M)                                                                           \
+    k_mlp_seed<M><<<g, 128, 0, s>>>(c.kp, n, c.inst, c.pinst, p.h, p.divv, p.nngb, c.mlp.seed0, \
+                                    c.dts, c.mlp.frag, c.mlp.w, c.mlp.dead, (int)c.capacity, \
+                                    c.mlp.tfeat, c.mlp.th, c.mlp.corr, c.st)
+    if (mode == 1) SPH_SEED(1);
+    else if (mode == 2) SPH_SEED(2);
+    else SPH_SEED(3);
+#undef SPH_SEED
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_pack(Ctx &c, cudaStream_t s)
 {
     c.launches += 1;
