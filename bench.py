@@ -176,6 +176,22 @@ def cpu_baseline(prob, target_s=15.0):
                       "FP64; %.1f s" % (S, prob.n, t)}
 
 
+def combine_ranks(ms, n_local, steps, world):
+    """Whole-job timing of independent replicas: the slowest rank's timed
+    milliseconds (every rank passed a barrier before its timed region) and
+    the particle-steps of all ranks per second of that time."""
+    tmax = float(ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = (torch.device("cuda", torch.cuda.current_device())
+               if dist.get_backend() == "nccl" else torch.device("cpu"))
+        t = torch.tensor([tmax], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    return tmax, world * n_local * steps / (tmax / 1000.0)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -484,12 +500,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     st1 = sph.sph_get_stats(sim.ctx)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    tmax = ms
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-    value = world * prob.n * args.steps / (tmax / 1000.0)
+    tmax, value = combine_ranks(ms, prob.n, args.steps, world)
     launches = int(st1["launches"] - st0["launches"])
 
     # roofline of the dominant pair kernel
