@@ -39,9 +39,10 @@ __device__ __forceinline__ float sep2(const PBox &bx, float px, float py, float 
 }
 
 // Hit masks of one lane against the staged chunk: bit k of word w is set when
-// candidate 32w + k lies inside radius^2.  The chunk is padded with NaN
-// positions to a multiple of 32, so the fully unrolled inner loop needs no
-// bounds checks and every bit is set with an immediate mask.
+// candidate 32w + k lies inside radius^2 (the sign bit of r^2 - h^2, shifted
+// in from the top candidate down).  The chunk is padded with NaN positions
+// (positive quiet NaN: never a hit) to a multiple of 32, so the fully
+// unrolled inner loop needs no bounds checks.
 template <bool WRAP>
 __device__ __forceinline__ void hit_masks(const PBox &bx, const float4 *cand, int nwords,
                                           float px, float py, float pz, float h2, bool active,
@@ -53,9 +54,9 @@ __device__ __forceinline__ void hit_masks(const PBox &bx, const float4 *cand, in
         for (int ww = 0; ww < nwords; ++ww) {
             unsigned mw = 0u;
 #pragma unroll
-            for (int b = 0; b < 32; ++b) {
+            for (int b = 31; b >= 0; --b) {  // bit b <- sign of r^2 - h^2
                 float r2 = sep2<WRAP>(bx, px, py, pz, cand[32 * ww + b]);
-                mw |= r2 < h2 ? (1u << b) : 0u;
+                mw = mw * 2u + (__float_as_uint(r2 - h2) >> 31);
             }
             if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
         }

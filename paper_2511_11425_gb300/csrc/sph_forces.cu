@@ -135,14 +135,14 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         for (int ww = 0; ww < nwords; ++ww) {
             unsigned mw = 0u;
 #pragma unroll
-            for (int b = 0; b < 32; ++b) {
+            for (int b = 31; b >= 0; --b) {  // bit b <- hit of candidate 32 ww + b
                 const float4 q = S.pos[32 * ww + b];
                 float dx, dy, dz;
                 sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bool hit = r2 < fmaxf(s.h2, q.w);
-                if (SELF) hit = hit && S.idx[32 * ww + b] > s.i;
-                mw |= hit ? (1u << b) : 0u;
+                unsigned hit = __float_as_uint(r2 - fmaxf(s.h2, q.w)) >> 31;
+                if (SELF) hit &= S.idx[32 * ww + b] > s.i ? 1u : 0u;
+                mw = mw * 2u + hit;
             }
             if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
         }
