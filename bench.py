@@ -348,10 +348,11 @@ def forms_batch(dev, steps, warmup):
     return out
 
 
-def forms_learned(dev, n_total=8_000_000, nrec=10, ncmp=20, tol=1e-5):
+def forms_learned(dev, n_total=8_000_000, nrec=50, ncmp=200, tol=1e-5):
     """The learned seed against the continuity seed on the colliding-spheres
     workload: record `nrec` plain steps, train the network on the GPU, then
-    run the same `ncmp` steps from the same state both ways."""
+    run the same `ncmp` steps from the same state both ways (the first 50
+    plain steps train, the next 200 are seeded)."""
     import torch
     import paper_2511_11425_gb300 as sph
     from paper_2511_11425_gb300 import inputs

@@ -749,23 +749,17 @@ static void tree_refit(Ctx &c, cudaStream_t s, int bob_only)
 // The list holds source bucket ids; each sink bucket of the group filters it
 // against its own bounds inside the pair kernels.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict__ insts,
-                                              const int *__restrict__ gfirst,
-                                              const int *__restrict__ bstart,
-                                              const int *__restrict__ binst, int mode,
-                                              const float4 *__restrict__ node,
-                                              const float4 *__restrict__ pm,
-                                              const int *__restrict__ origin,
-                                              const float *__restrict__ h_walk,
-                                              const unsigned *__restrict__ group_ids,
-                                              const unsigned *__restrict__ group_cnt,
-                                              unsigned *list, unsigned *list_cnt, DevStatus *st)
+__device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__restrict__ insts,
+                                           const int *__restrict__ gfirst,
+                                           const int *__restrict__ bstart,
+                                           const int *__restrict__ binst, int mode,
+                                           const float4 *__restrict__ node,
+                                           const float4 *__restrict__ pm,
+                                           const int *__restrict__ origin,
+                                           const float *__restrict__ h_walk, unsigned *list,
+                                           unsigned *list_cnt, DevStatus *st,
+                                           unsigned (*buf)[kWalkCap], int g, int lane, int wib)
 {
-    __shared__ unsigned buf[kWarpsPerBlock][2][kWalkCap];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gi = blockIdx.x * kWarpsPerBlock + wib;
-    if (group_ids ? gi >= (int)*group_cnt : gi >= kp.ng) return;
-    const int g = group_ids ? (int)group_ids[gi] : gi;
     const int fb = gfirst[g];
     const Inst &I = insts[binst[fb]];
     const int nbg = min(I.G, I.boff + I.nb - fb);
@@ -839,7 +833,7 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
     // the frontier holds ACCEPTED nodes only: each round tests both children
     // of every accepted node and keeps the accepted ones (leaves become the
     // list as global bucket ids)
-    unsigned *cur = buf[wib][0], *nxt = buf[wib][1];
+    unsigned *cur = buf[0], *nxt = buf[1];
     const int L0 = I.logP < 5 ? I.logP : 5;
     bool overflow = false;
     int ncur = 0;
@@ -885,6 +879,34 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
     unsigned *out = list + (size_t)g * kWalkCap;
     for (int k = lane; k < ncur; k += 32) out[k] = cur[k];
     if (lane == 0) list_cnt[g] = (unsigned)ncur;
+}
+
+__global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict__ insts,
+                                              const int *__restrict__ gfirst,
+                                              const int *__restrict__ bstart,
+                                              const int *__restrict__ binst, int mode,
+                                              const float4 *__restrict__ node,
+                                              const float4 *__restrict__ pm,
+                                              const int *__restrict__ origin,
+                                              const float *__restrict__ h_walk,
+                                              const unsigned *__restrict__ group_ids,
+                                              const unsigned *__restrict__ group_cnt,
+                                              unsigned *list, unsigned *list_cnt, DevStatus *st)
+{
+    __shared__ unsigned buf[kWarpsPerBlock][2][kWalkCap];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gi0 = blockIdx.x * kWarpsPerBlock + wib;
+    if (!group_ids) {  // every group, one warp each
+        if (gi0 < kp.ng)
+            walk_group(kp, insts, gfirst, bstart, binst, mode, node, pm, origin, h_walk, list,
+                       list_cnt, st, buf[wib], gi0, lane, wib);
+        return;
+    }
+    // the groups queued for a re-walk round, grid-stride over a small grid
+    const int nq = (int)*group_cnt;
+    for (int gi = gi0; gi < nq; gi += gridDim.x * kWarpsPerBlock)
+        walk_group(kp, insts, gfirst, bstart, binst, mode, node, pm, origin, h_walk, list,
+                   list_cnt, st, buf[wib], (int)group_ids[gi], lane, wib);
 }
 
 // ---------------------------------------------------------------------------
@@ -986,7 +1008,8 @@ cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, con
     if (kp.ng <= 0) return cudaSuccess;
     const unsigned *ids = round < 0 ? nullptr : c.redo + (size_t)round * kp.ng;
     const unsigned *cnt = round < 0 ? nullptr : &c.st->redo_cnt[round];
-    const int g = (kp.ng + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    int g = (kp.ng + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (round >= 0 && g > kRoundBlocks) g = kRoundBlocks;
     c.launches += 1;
     k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(kp, c.inst, c.gfirst, c.bstart, c.binst, mode, c.node,
                                              c.pm, c.origin, h_walk, ids, cnt, c.list, c.list_cnt,

@@ -323,37 +323,18 @@ __device__ __forceinline__ void density_bucket(
     }
 }
 
+// one sink bucket A (one warp)
 template <class K, bool EMIT>
-__global__ void __launch_bounds__(128) k_density(
-    KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
+__device__ __forceinline__ void density_slot(
+    const KParams &kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const int *__restrict__ bstart, const int *__restrict__ binst,
-    const int *__restrict__ gfirst, const unsigned *__restrict__ list_cnt,
-    const unsigned *__restrict__ list, const int *__restrict__ origin,
-    const unsigned *__restrict__ group_ids, const unsigned *__restrict__ group_cnt,
-    float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
-    uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out, int64_t *ids_out,
-    const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *redo_cnt_out,
-    unsigned *gflag, const float4 *__restrict__ node, DevStatus *st)
+    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list,
+    const int *__restrict__ origin, float *h_seed, float *h_out, float *rho_out,
+    float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap,
+    uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
+    unsigned *redo_out, unsigned *redo_cnt_out, unsigned *gflag,
+    const float4 *__restrict__ node, DevStatus *st, float4 *cand, int *candj, int A, int lane)
 {
-    __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
-    __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bi = blockIdx.x * kWarpsPerBlock + wib;
-    // all buckets, or the buckets of the groups queued for this re-walk round
-    // (8 warp slots per queued group)
-    int A;
-    if (group_ids) {
-        const int gi = bi >> kGroupLog;
-        if (gi >= (int)*group_cnt) return;
-        const int fb = gfirst[group_ids[gi]];
-        const Inst &Ig = insts[binst[fb]];
-        const int j = bi & ((1 << kGroupLog) - 1);
-        if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) return;
-        A = fb + j;
-    } else {
-        if (bi >= kp.nb) return;
-        A = bi;
-    }
     const Inst &I = insts[binst[A]];
     const PBox bx = make_pbox(I);
     const int i0 = bstart[A];
@@ -377,8 +358,6 @@ __global__ void __launch_bounds__(128) k_density(
             if (bx.per[a] && (mx - mn) + Rm > 0.49f * bx.L[a]) wrap = true;
         }
     }
-    float4 *cand = cand_s[wib];
-    int *candj = EMIT ? candj_s[wib] : nullptr;
     if (wrap)
         density_bucket<K, true, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
                                       list, origin, node, h_seed, h_out, rho_out, omega_out,
@@ -390,6 +369,47 @@ __global__ void __launch_bounds__(128) k_density(
                                        nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
                                        redo_out, redo_cnt_out, gflag, st, me, valid, cen);
 }
+
+template <class K, bool EMIT>
+__global__ void __launch_bounds__(128) k_density(
+    KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
+    const int *__restrict__ bstart, const int *__restrict__ binst,
+    const int *__restrict__ gfirst, const unsigned *__restrict__ list_cnt,
+    const unsigned *__restrict__ list, const int *__restrict__ origin,
+    const unsigned *__restrict__ group_ids, const unsigned *__restrict__ group_cnt,
+    float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
+    uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out, int64_t *ids_out,
+    const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *redo_cnt_out,
+    unsigned *gflag, const float4 *__restrict__ node, DevStatus *st)
+{
+    __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
+    __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (!group_ids) {  // every bucket, one warp each
+        const int A = blockIdx.x * kWarpsPerBlock + wib;
+        if (A < kp.nb)
+            density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list, origin, h_seed,
+                                  h_out, rho_out, omega_out, nngb_out, iters_out, fixed_h, cap,
+                                  count_out, ids_out, id_in, redo_out, redo_cnt_out, gflag, node,
+                                  st, cand_s[wib], EMIT ? candj_s[wib] : nullptr, A, lane);
+        return;
+    }
+    // the buckets of the groups queued for this re-walk round (8 warp slots
+    // per queued group), grid-stride: the grid is small and mostly idle
+    const int nslots = (int)*group_cnt << kGroupLog;
+    for (int bi = blockIdx.x * kWarpsPerBlock + wib; bi < nslots;
+         bi += gridDim.x * kWarpsPerBlock) {
+        const int fb = gfirst[group_ids[bi >> kGroupLog]];
+        const Inst &Ig = insts[binst[fb]];
+        const int j = bi & ((1 << kGroupLog) - 1);
+        if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) continue;
+        density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list, origin, h_seed, h_out,
+                              rho_out, omega_out, nngb_out, iters_out, fixed_h, cap, count_out,
+                              ids_out, id_in, redo_out, redo_cnt_out, gflag, node, st,
+                              cand_s[wib], EMIT ? candj_s[wib] : nullptr, fb + j, lane);
+    }
+}
+
 
 __global__ void k_isentropic(int n, const Inst *__restrict__ insts,
                              const unsigned short *__restrict__ pinst,
@@ -411,8 +431,10 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     if (kp.nb <= 0) return cudaSuccess;
     // round < 0: every bucket, queueing re-walks for round 0; round r: the
     // buckets of the groups queued for round r, queueing for round r + 1
+    // a re-walk round covers the queued groups with a small grid-stride grid
     const int slots = round < 0 ? kp.nb : kp.ng << kGroupLog;
-    const int g = (slots + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    int g = (slots + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (round >= 0 && g > kRoundBlocks) g = kRoundBlocks;
     const bool emit = ids != nullptr || count != nullptr;
     const unsigned *gids = round < 0 ? nullptr : c.redo + (size_t)round * kp.ng;
     const unsigned *gcnt = round < 0 ? nullptr : &c.st->redo_cnt[round];

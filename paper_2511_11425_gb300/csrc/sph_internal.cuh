@@ -67,6 +67,7 @@ __host__ __device__ inline int64_t bucket_slots(int64_t n)
 }
 constexpr int kMortonBits = 10;   // bits per axis of a curve key (30 bits per instance)
 constexpr int kRelistRounds = 3;  // re-walk rounds queued after the first density pass
+constexpr int kRoundBlocks = 304; // blocks of a re-walk round's grid-stride launches
 constexpr int kBboxChunks = 32;   // blocks per instance for open-axis bounding boxes
 constexpr int kConsChunk = 2048;  // particles per block of the conserved totals
 constexpr unsigned kFull = 0xffffffffu;
