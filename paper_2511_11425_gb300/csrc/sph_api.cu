@@ -199,7 +199,13 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.gfirst, ng);
     AL(c.gflag, ng);
     AL(c.list_cnt, ng);
-    AL(c.list, (size_t)ng * kWalkCap);
+    AL(c.list_off, ng);
+    AL(c.arena_used, 1);
+    c.arena_cap = std::max<int64_t>((int64_t)1 << 23, 16 * ng);
+    if (rc == SPH_OK && ng * kWalkCap + c.arena_cap > (int64_t)0xffffffffLL)
+        rc = failf(c, SPH_ERR_CAPACITY, "too many walk groups (%lld) for 32-bit list offsets",
+                   (long long)ng);
+    AL(c.list, (size_t)ng * kWalkCap + (size_t)c.arena_cap);
     AL(c.redo, (size_t)kRelistRounds * ng);
     AL(c.node, (size_t)4 * std::max<int64_t>(cap.nodes, 2));
     AL(c.refit, std::max<int64_t>(cap.refit, 1));
@@ -239,7 +245,8 @@ void free_ctx(Ctx &c)
                     c.pad_agg, c.pad_used,
                     c.cons_out, c.pinst, c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist,
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
-                    c.list_cnt, c.list, c.redo, c.node, c.refit, c.pm, c.fpos, c.fvel, c.fth,
+                    c.list_cnt, c.list_off, c.arena_used, c.list, c.redo, c.node, c.refit,
+                    c.pm, c.fpos, c.fvel, c.fth,
                     c.acc, c.acc2, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -371,8 +378,8 @@ sph_status settle(sph_ctx *ctx, cudaStream_t s)
         return failf(c, SPH_ERR_ARG, "index %d: smoothing length reached half a periodic box "
                      "length, or a bucket left the position grid", h.detail);
     case ST_CAPACITY:
-        return failf(c, SPH_ERR_CAPACITY, "group %d: more than %d bounds-tree nodes or source "
-                     "buckets overlap its bounds", h.detail, kWalkCap);
+        return failf(c, SPH_ERR_CAPACITY, "group %d: the interaction-list overflow arena "
+                     "(%lld entries) is full", h.detail, (long long)c.arena_cap);
     case ST_NOCONV:
         return failf(c, SPH_ERR_NOCONV, "particle %d: Newton iteration on h did not converge in "
                      "%d iterations or %d re-walks", h.detail, c.kp.max_newton, kRelistRounds);

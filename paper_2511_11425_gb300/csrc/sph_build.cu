@@ -757,15 +757,20 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
                                            const float4 *__restrict__ pm,
                                            const int *__restrict__ origin,
                                            const float *__restrict__ h_walk, unsigned *list,
-                                           unsigned *list_cnt, DevStatus *st,
-                                           unsigned (*buf)[kWalkCap], int g, int lane, int wib)
+                                           unsigned *list_cnt, unsigned *list_off,
+                                           unsigned *arena_used, unsigned arena_cap,
+                                           DevStatus *st, unsigned (*buf)[kWalkCap], int g,
+                                           int lane)
 {
     const int fb = gfirst[g];
     const Inst &I = insts[binst[fb]];
     const int nbg = min(I.G, I.boff + I.nb - fb);
     const int fl = fb - I.boff;  // local index of the group's first bucket
     if (bstart[fb + nbg] == bstart[fb]) {  // only padding slots
-        if (lane == 0) list_cnt[g] = 0u;
+        if (lane == 0) {
+            list_cnt[g] = 0u;
+            list_off[g] = (unsigned)g * kWalkCap;
+        }
         return;
     }
 
@@ -830,6 +835,43 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
         }
         return gth;
     };
+    // a group whose frontier or list outgrows kWalkCap (a particle with a
+    // huge h, e.g. one leaving a free surface): the same warp tests every
+    // leaf of the instance and writes the list to the shared overflow arena
+    // behind the fixed per-group slots (two sweeps: count, write)
+    auto exhaustive = [&]() {
+        const unsigned lt = (1u << lane) - 1u;
+        unsigned total = 0u;
+        for (int base = 0; base < I.nb; base += 32) {
+            const int k = base + lane;
+            const bool acc = k < I.nb && accept((unsigned)(I.P + k), I.logP);
+            total += __popc(__ballot_sync(kFull, acc));
+        }
+        unsigned off = 0u;
+        if (lane == 0) off = atomicAdd(arena_used, total);
+        off = __shfl_sync(kFull, off, 0);
+        if ((unsigned long long)off + total > arena_cap) {
+            if (lane == 0) {
+                raise_status(st, ST_CAPACITY, g);
+                list_cnt[g] = 0u;
+                list_off[g] = (unsigned)g * kWalkCap;
+            }
+            return;
+        }
+        unsigned *out = list + (size_t)kp.ng * kWalkCap + off;
+        unsigned pos = 0u;
+        for (int base = 0; base < I.nb; base += 32) {
+            const int k = base + lane;
+            const bool acc = k < I.nb && accept((unsigned)(I.P + k), I.logP);
+            const unsigned bal = __ballot_sync(kFull, acc);
+            if (acc) out[pos + __popc(bal & lt)] = (unsigned)(I.boff + k);
+            pos += __popc(bal);
+        }
+        if (lane == 0) {
+            list_cnt[g] = total;
+            list_off[g] = (unsigned)kp.ng * kWalkCap + off;
+        }
+    };
     // the frontier holds ACCEPTED nodes only: each round tests both children
     // of every accepted node and keeps the accepted ones (leaves become the
     // list as global bucket ids)
@@ -873,12 +915,15 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
         ncur = nnext;
     }
     if (overflow) {
-        if (lane == 0) raise_status(st, ST_CAPACITY, g);
-        ncur = 0;
+        exhaustive();
+        return;
     }
     unsigned *out = list + (size_t)g * kWalkCap;
     for (int k = lane; k < ncur; k += 32) out[k] = cur[k];
-    if (lane == 0) list_cnt[g] = (unsigned)ncur;
+    if (lane == 0) {
+        list_cnt[g] = (unsigned)ncur;
+        list_off[g] = (unsigned)g * kWalkCap;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict__ insts,
@@ -891,7 +936,9 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
                                               const float *__restrict__ h_walk,
                                               const unsigned *__restrict__ group_ids,
                                               const unsigned *__restrict__ group_cnt,
-                                              unsigned *list, unsigned *list_cnt, DevStatus *st)
+                                              unsigned *list, unsigned *list_cnt,
+                                              unsigned *list_off, unsigned *arena_used,
+                                              unsigned arena_cap, DevStatus *st)
 {
     __shared__ unsigned buf[kWarpsPerBlock][2][kWalkCap];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -899,14 +946,15 @@ __global__ void __launch_bounds__(128) k_walk(KParams kp, const Inst *__restrict
     if (!group_ids) {  // every group, one warp each
         if (gi0 < kp.ng)
             walk_group(kp, insts, gfirst, bstart, binst, mode, node, pm, origin, h_walk, list,
-                       list_cnt, st, buf[wib], gi0, lane, wib);
+                       list_cnt, list_off, arena_used, arena_cap, st, buf[wib], gi0, lane);
         return;
     }
     // the groups queued for a re-walk round, grid-stride over a small grid
     const int nq = (int)*group_cnt;
     for (int gi = gi0; gi < nq; gi += gridDim.x * kWarpsPerBlock)
         walk_group(kp, insts, gfirst, bstart, binst, mode, node, pm, origin, h_walk, list,
-                   list_cnt, st, buf[wib], (int)group_ids[gi], lane, wib);
+                   list_cnt, list_off, arena_used, arena_cap, st, buf[wib], (int)group_ids[gi],
+                   lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1010,9 +1058,12 @@ cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, con
     const unsigned *cnt = round < 0 ? nullptr : &c.st->redo_cnt[round];
     int g = (kp.ng + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (round >= 0 && g > kRoundBlocks) g = kRoundBlocks;
+    // the overflow arena is emptied when every list is rebuilt
+    if (round < 0) cudaMemsetAsync(c.arena_used, 0, sizeof(unsigned), s);
     c.launches += 1;
     k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(kp, c.inst, c.gfirst, c.bstart, c.binst, mode, c.node,
                                              c.pm, c.origin, h_walk, ids, cnt, c.list, c.list_cnt,
+                                             c.list_off, c.arena_used, (unsigned)c.arena_cap,
                                              c.st);
     return cudaGetLastError();
 }

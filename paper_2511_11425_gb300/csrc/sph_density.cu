@@ -121,7 +121,8 @@ template <class K, bool WRAP, bool EMIT>
 __device__ __forceinline__ void density_bucket(
     const KParams &kp, const Inst &I, const PBox &bx, int A, int i0, int lane, float4 *cand,
     int *candj, const float4 *__restrict__ pm, const int *__restrict__ bstart,
-    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list,
+    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list_off,
+    const unsigned *__restrict__ list,
     const int *__restrict__ origin, const float4 *__restrict__ node, float *h_seed, float *h_out,
     float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
     long long cap, uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
@@ -141,35 +142,40 @@ __device__ __forceinline__ void density_bucket(
     unsigned long long pairs = 0, cands = 0;
     const float p[3] = {me.x, me.y, me.z};
     // Filter the group's list against this bucket's coverage box of balls
-    // (radius R): lane w keeps the acceptance bits of entries 32w .. 32w+31.
+    // (radius R), 1024 entries (one segment) at a time: lane w keeps the
+    // acceptance bits of entries 32w .. 32w+31 of the segment.  Lists longer
+    // than a segment (overflow arena) are re-filtered per segment and pass.
     const int g = group_of(I, A);
-    const unsigned s0 = (unsigned)g * kWalkCap, nl = list_cnt[g];
-    unsigned myword = 0u;
-    {
-        float cc[3], cr[3];
+    const unsigned nl = list_cnt[g];
+    const unsigned *__restrict__ gl = list + list_off[g];
+    float cc[3], cr[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float lo = warp_min(valid ? p[a] - R : INFINITY);
-            float hi = warp_max(valid ? p[a] + R : -INFINITY);
-            double o = (double)origin[a * kp.nb + A] * I.q;
-            cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
-            cr[a] = 0.5f * (hi - lo) + 2.f * eps_abs;
-        }
-        for (unsigned w = 0; 32 * w < nl; ++w) {
+    for (int a = 0; a < 3; ++a) {
+        float lo = warp_min(valid ? p[a] - R : INFINITY);
+        float hi = warp_max(valid ? p[a] + R : -INFINITY);
+        double o = (double)origin[a * kp.nb + A] * I.q;
+        cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
+        cr[a] = 0.5f * (hi - lo) + 2.f * eps_abs;
+    }
+    auto filter = [&](unsigned seg) -> unsigned {
+        unsigned word = 0u;
+        const unsigned ns = min(nl - seg, (unsigned)kWalkCap);
+        for (unsigned w = 0; 32 * w < ns; ++w) {
             const unsigned e = 32 * w + lane;
             bool acc = false;
-            if (e < nl) {
-                const size_t k = leaf_of(I, (int)list[s0 + e]);
+            if (e < ns) {
+                const size_t k = leaf_of(I, (int)gl[seg + e]);
                 const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
                 acc = ovl(cc[0], cr[0], b0.x, b1.x, bx.per[0], bx.L[0], bx.invL[0]) &&
                       ovl(cc[1], cr[1], b0.y, b1.y, bx.per[1], bx.L[1], bx.invL[1]) &&
                       ovl(cc[2], cr[2], b0.z, b1.z, bx.per[2], bx.L[2], bx.invL[2]);
             }
             const unsigned bal = __ballot_sync(kFull, acc);
-            if (lane == (int)w) myword = bal;
+            if (lane == (int)w) word = bal;
         }
-    }
-    const unsigned nwords = (nl + 31) / 32;
+        return word;
+    };
+    const unsigned word0 = filter(0u);
 
     for (int pass = 0; pass <= kp.max_newton; ++pass) {
         if (__all_sync(kFull, done)) break;
@@ -193,12 +199,15 @@ __device__ __forceinline__ void density_bucket(
         }
         Kahan Sw, Sq;
         int cnt = 0, c = 0;
-        for (unsigned w = 0; w < nwords; ++w) {
+        for (unsigned seg = 0; seg < nl; seg += kWalkCap) {
+         const unsigned myword = seg == 0 ? word0 : filter(seg);
+         const unsigned nwords = (min(nl - seg, (unsigned)kWalkCap) + 31) / 32;
+         for (unsigned w = 0; w < nwords; ++w) {
           unsigned mw = __shfl_sync(kFull, myword, w);
           while (mw) {
-            const unsigned e = 32 * w + __ffs(mw) - 1;
+            const unsigned e = seg + 32 * w + __ffs(mw) - 1;
             mw &= mw - 1u;
-            const int B = (int)list[s0 + e];
+            const int B = (int)gl[e];
             const float3 off = origin_offset(I, kp.nb, origin, A, B);
             const int j0 = bstart[B];
             const int j = j0 + lane;
@@ -234,6 +243,7 @@ __device__ __forceinline__ void density_bucket(
                 c = 0;
             }
           }
+         }
         }
         if (c > 0) {
             __syncwarp();
@@ -328,7 +338,8 @@ template <class K, bool EMIT>
 __device__ __forceinline__ void density_slot(
     const KParams &kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const int *__restrict__ bstart, const int *__restrict__ binst,
-    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list,
+    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list_off,
+    const unsigned *__restrict__ list,
     const int *__restrict__ origin, float *h_seed, float *h_out, float *rho_out,
     float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap,
     uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
@@ -360,12 +371,12 @@ __device__ __forceinline__ void density_slot(
     }
     if (wrap)
         density_bucket<K, true, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
-                                      list, origin, node, h_seed, h_out, rho_out, omega_out,
+                                      list_off, list, origin, node, h_seed, h_out, rho_out, omega_out,
                                       nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
                                       redo_out, redo_cnt_out, gflag, st, me, valid, cen);
     else
         density_bucket<K, false, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
-                                       list, origin, node, h_seed, h_out, rho_out, omega_out,
+                                       list_off, list, origin, node, h_seed, h_out, rho_out, omega_out,
                                        nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
                                        redo_out, redo_cnt_out, gflag, st, me, valid, cen);
 }
@@ -375,6 +386,7 @@ __global__ void __launch_bounds__(128) k_density(
     KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const int *__restrict__ bstart, const int *__restrict__ binst,
     const int *__restrict__ gfirst, const unsigned *__restrict__ list_cnt,
+    const unsigned *__restrict__ list_off,
     const unsigned *__restrict__ list, const int *__restrict__ origin,
     const unsigned *__restrict__ group_ids, const unsigned *__restrict__ group_cnt,
     float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(128) k_density(
     if (!group_ids) {  // every bucket, one warp each
         const int A = blockIdx.x * kWarpsPerBlock + wib;
         if (A < kp.nb)
-            density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list, origin, h_seed,
+            density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list_off, list, origin, h_seed,
                                   h_out, rho_out, omega_out, nngb_out, iters_out, fixed_h, cap,
                                   count_out, ids_out, id_in, redo_out, redo_cnt_out, gflag, node,
                                   st, cand_s[wib], EMIT ? candj_s[wib] : nullptr, A, lane);
@@ -403,7 +415,7 @@ __global__ void __launch_bounds__(128) k_density(
         const Inst &Ig = insts[binst[fb]];
         const int j = bi & ((1 << kGroupLog) - 1);
         if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) continue;
-        density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list, origin, h_seed, h_out,
+        density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list_off, list, origin, h_seed, h_out,
                               rho_out, omega_out, nngb_out, iters_out, fixed_h, cap, count_out,
                               ids_out, id_in, redo_out, redo_cnt_out, gflag, node, st,
                               cand_s[wib], EMIT ? candj_s[wib] : nullptr, fb + j, lane);
@@ -446,12 +458,12 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     SPH_KERNEL_DISPATCH(kp.kernel, KT,
         if (emit)
             k_density<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list, c.origin, gids,
+                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list, c.origin, gids,
                 gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,
                 (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st);
         else
             k_density<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list, c.origin, gids,
+                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list, c.origin, gids,
                 gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,
                 (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st);
     )

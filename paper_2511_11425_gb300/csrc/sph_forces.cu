@@ -222,6 +222,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
                                              const float4 *__restrict__ fvel,
                                              const float4 *__restrict__ fth,
                                              const unsigned *__restrict__ list_cnt,
+                                             const unsigned *__restrict__ list_off,
                                              const unsigned *__restrict__ list,
                                              const int *__restrict__ origin,
                                              const float4 *__restrict__ node, float4 *acc,
@@ -232,18 +233,22 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     // bucket's own bounds): source bucket B >= A whose cell bound meets the
     // sink box-of-balls (gather) or whose box-of-balls meets the sink cell
     // bound (scatter).  Lane w keeps the bits of entries 32w .. 32w+31.
+    // Lists longer than one 1024-entry segment (overflow arena) are filtered
+    // and processed segment by segment.
     const int g = group_of(I, A);
-    const unsigned s0 = (unsigned)g * kWalkCap, nl = list_cnt[g];
-    unsigned myword = 0u;
-    {
-        const size_t ka = leaf_of(I, A);
-        const float4 sb0 = node[4 * ka], sb1 = node[4 * ka + 1];
-        const float4 so0 = node[4 * ka + 2], so1 = node[4 * ka + 3];
-        for (unsigned w = 0; 32 * w < nl; ++w) {
+    const unsigned nl = list_cnt[g];
+    const unsigned *__restrict__ gl = list + list_off[g];
+    const size_t ka = leaf_of(I, A);
+    const float4 sb0 = node[4 * ka], sb1 = node[4 * ka + 1];
+    const float4 so0 = node[4 * ka + 2], so1 = node[4 * ka + 3];
+    auto filter = [&](unsigned seg) -> unsigned {
+        unsigned myword = 0u;
+        const unsigned ns = min(nl - seg, (unsigned)kWalkCap);
+        for (unsigned w = 0; 32 * w < ns; ++w) {
             const unsigned e = 32 * w + lane;
             bool acc_ = false;
-            if (e < nl) {
-                const unsigned B = list[s0 + e];
+            if (e < ns) {
+                const unsigned B = gl[seg + e];
                 const size_t k = leaf_of(I, (int)B);
                 if ((int)B >= A) {
                     const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
@@ -261,7 +266,8 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
             const unsigned bal = __ballot_sync(kFull, acc_);
             if (lane == (int)w) myword = bal;
         }
-    }
+        return myword;
+    };
     // stage the culled particles of source bucket B after the c staged ones
     auto stage = [&](int B, int c) -> int {
         const float3 off = origin_offset(I, kp.nb, origin, A, B);
@@ -310,13 +316,15 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         force_chunk<K, WRAP, true>(bx, vp, S, c, s, valid, lane, acc, acc2);
         c = 0;
     }
-    const unsigned nwords = (nl + 31) / 32;
-    for (unsigned w = 0; w < nwords; ++w) {
+    for (unsigned seg = 0; seg < nl; seg += kWalkCap) {
+     const unsigned myword = filter(seg);
+     const unsigned nwords = (min(nl - seg, (unsigned)kWalkCap) + 31) / 32;
+     for (unsigned w = 0; w < nwords; ++w) {
       unsigned mw = __shfl_sync(kFull, myword, w);
       while (mw) {
-        const unsigned e = 32 * w + __ffs(mw) - 1;
+        const unsigned e = seg + 32 * w + __ffs(mw) - 1;
         mw &= mw - 1u;
-        const int B = (int)list[s0 + e];
+        const int B = (int)gl[e];
         if (B == A) continue;
         c = stage(B, c);
         if (c > kChunk - 32) {
@@ -326,6 +334,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
             c = 0;
         }
       }
+     }
     }
     if (c > 0) {
         __syncwarp();
@@ -342,6 +351,7 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const Inst *__restri
                                                 const float4 *__restrict__ fvel,
                                                 const float4 *__restrict__ fth,
                                                 const unsigned *__restrict__ list_cnt,
+                                                const unsigned *__restrict__ list_off,
                                                 const unsigned *__restrict__ list,
                                                 const int *__restrict__ origin,
                                                 const float4 *__restrict__ node, float4 *acc,
@@ -408,11 +418,11 @@ __global__ void __launch_bounds__(128) k_forces(KParams kp, const Inst *__restri
     unsigned long long cands = 0;
     if (wrap)
         force_bucket<K, true>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
-                              fpos, fvel, fth, list_cnt, list, origin, node, acc,
+                              fpos, fvel, fth, list_cnt, list_off, list, origin, node, acc,
                               acc2, cands);
     else
         force_bucket<K, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
-                              fpos, fvel, fth, list_cnt, list, origin, node, acc,
+                              fpos, fvel, fth, list_cnt, list_off, list, origin, node, acc,
                               acc2, cands);
     if (valid) {
         red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.S.s);
@@ -493,7 +503,7 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
     c.launches += 1;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
         k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.inst, c.bstart, c.binst, c.fpos,
-                                                        c.fvel, c.fth, c.list_cnt, c.list,
+                                                        c.fvel, c.fth, c.list_cnt, c.list_off, c.list,
                                                         c.origin, c.node, c.acc, c.acc2, c.st);
     )
     return cudaGetLastError();

@@ -190,8 +190,12 @@ struct Ctx {
     float *rho_old = nullptr;
     float *h_seed = nullptr;          // density seeds / re-walk seeds
 
-    // lists: kWalkCap slots per group
-    unsigned int *list = nullptr, *list_cnt = nullptr;
+    // lists: kWalkCap slots per group, then an overflow arena of arena_cap
+    // entries for groups whose lists outgrow them; list_off[g] = where g's
+    // list starts
+    unsigned int *list = nullptr, *list_cnt = nullptr, *list_off = nullptr;
+    unsigned int *arena_used = nullptr;  // overflow arena entries handed out
+    int64_t arena_cap = 0;
     unsigned int *redo = nullptr;     // per round r: group ids queued (ng entries each)
 
     // host-mode mirror buffers for sph_step_host
