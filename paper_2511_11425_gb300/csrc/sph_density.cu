@@ -142,40 +142,44 @@ __device__ __forceinline__ void density_bucket(
     unsigned long long pairs = 0, cands = 0;
     const float p[3] = {me.x, me.y, me.z};
     // Filter the group's list against this bucket's coverage box of balls
-    // (radius R), 1024 entries (one segment) at a time: lane w keeps the
-    // acceptance bits of entries 32w .. 32w+31 of the segment.  Lists longer
-    // than a segment (overflow arena) are re-filtered per segment and pass.
+    // (radius R): lane w keeps the acceptance bits of entries 32w .. 32w+31
+    // of the first 1024.  Longer lists (overflow arena) get the bits of each
+    // later word by a ballot when the pass reaches it.
     const int g = group_of(I, A);
     const unsigned nl = list_cnt[g];
     const unsigned *__restrict__ gl = list + list_off[g];
-    float cc[3], cr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float lo = warp_min(valid ? p[a] - R : INFINITY);
-        float hi = warp_max(valid ? p[a] + R : -INFINITY);
-        double o = (double)origin[a * kp.nb + A] * I.q;
-        cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
-        cr[a] = 0.5f * (hi - lo) + 2.f * eps_abs;
-    }
-    auto filter = [&](unsigned seg) -> unsigned {
-        unsigned word = 0u;
-        const unsigned ns = min(nl - seg, (unsigned)kWalkCap);
-        for (unsigned w = 0; 32 * w < ns; ++w) {
-            const unsigned e = 32 * w + lane;
-            bool acc = false;
-            if (e < ns) {
-                const size_t k = leaf_of(I, (int)gl[seg + e]);
-                const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
-                acc = ovl(cc[0], cr[0], b0.x, b1.x, bx.per[0], bx.L[0], bx.invL[0]) &&
-                      ovl(cc[1], cr[1], b0.y, b1.y, bx.per[1], bx.L[1], bx.invL[1]) &&
-                      ovl(cc[2], cr[2], b0.z, b1.z, bx.per[2], bx.L[2], bx.invL[2]);
-            }
-            const unsigned bal = __ballot_sync(kFull, acc);
-            if (lane == (int)w) word = bal;
+    auto filter_word = [&](unsigned w, const float *cc, const float *cr) -> unsigned {
+        const unsigned e = 32 * w + lane;
+        bool acc = false;
+        if (e < nl) {
+            const size_t k = leaf_of(I, (int)gl[e]);
+            const float4 b0 = node[4 * k], b1 = node[4 * k + 1];
+            acc = ovl(cc[0], cr[0], b0.x, b1.x, bx.per[0], bx.L[0], bx.invL[0]) &&
+                  ovl(cc[1], cr[1], b0.y, b1.y, bx.per[1], bx.L[1], bx.invL[1]) &&
+                  ovl(cc[2], cr[2], b0.z, b1.z, bx.per[2], bx.L[2], bx.invL[2]);
         }
-        return word;
+        return __ballot_sync(kFull, acc);
     };
-    const unsigned word0 = filter(0u);
+    auto coverage = [&](float *cc, float *cr) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float lo = warp_min(valid ? p[a] - R : INFINITY);
+            float hi = warp_max(valid ? p[a] + R : -INFINITY);
+            double o = (double)origin[a * kp.nb + A] * I.q;
+            cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
+            cr[a] = 0.5f * (hi - lo) + 2.f * eps_abs;
+        }
+    };
+    unsigned myword = 0u;
+    {
+        float cc[3], cr[3];
+        coverage(cc, cr);
+        for (unsigned w = 0; 32 * w < nl && w < 32; ++w) {
+            const unsigned bal = filter_word(w, cc, cr);
+            if (lane == (int)w) myword = bal;
+        }
+    }
+    const unsigned nwords = (nl + 31) / 32;
 
     for (int pass = 0; pass <= kp.max_newton; ++pass) {
         if (__all_sync(kFull, done)) break;
@@ -199,13 +203,17 @@ __device__ __forceinline__ void density_bucket(
         }
         Kahan Sw, Sq;
         int cnt = 0, c = 0;
-        for (unsigned seg = 0; seg < nl; seg += kWalkCap) {
-         const unsigned myword = seg == 0 ? word0 : filter(seg);
-         const unsigned nwords = (min(nl - seg, (unsigned)kWalkCap) + 31) / 32;
-         for (unsigned w = 0; w < nwords; ++w) {
-          unsigned mw = __shfl_sync(kFull, myword, w);
+        for (unsigned w = 0; w < nwords; ++w) {
+          unsigned mw;
+          if (w < 32) {
+            mw = __shfl_sync(kFull, myword, w);
+          } else {  // long list: this word's bits now (the box is recomputed)
+            float cc[3], cr[3];
+            coverage(cc, cr);
+            mw = filter_word(w, cc, cr);
+          }
           while (mw) {
-            const unsigned e = seg + 32 * w + __ffs(mw) - 1;
+            const unsigned e = 32 * w + __ffs(mw) - 1;
             mw &= mw - 1u;
             const int B = (int)gl[e];
             const float3 off = origin_offset(I, kp.nb, origin, A, B);
@@ -243,7 +251,6 @@ __device__ __forceinline__ void density_bucket(
                 c = 0;
             }
           }
-         }
         }
         if (c > 0) {
             __syncwarp();
@@ -382,7 +389,9 @@ __device__ __forceinline__ void density_slot(
 }
 
 template <class K, bool EMIT>
-__global__ void __launch_bounds__(128) k_density(
+// 5 blocks of 4 warps per SM: the register cap (96) measured faster than
+// the compiler's own choice (about 128 registers, 4 blocks)
+__global__ void __launch_bounds__(128, 5) k_density(
     KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const int *__restrict__ bstart, const int *__restrict__ binst,
     const int *__restrict__ gfirst, const unsigned *__restrict__ list_cnt,
