@@ -106,12 +106,16 @@ __global__ void k_bbox_final(KParams kp, const Inst *__restrict__ insts, const d
     while ((1ll << bpre) < ncubes) ++bpre;
     const int bin = min(kMortonBits, (30 - bpre) / 3);
     double *mb = morton_box + kKeyBox * k;
+    // integers are stored as their bit patterns (readers decode them
+    // without FP64 conversions); slot 10 holds the FP32 side of one key cell
     for (int a = 0; a < 3; ++a) {
         mb[a] = lo3[a];
         mb[3 + a] = ldexp((double)nc[a], bin) / (ext3[a] * (1.0 + 1e-9) + 1e-300);
-        mb[6 + a] = (double)nc[a];
+        mb[6 + a] = __longlong_as_double((long long)nc[a]);
     }
-    mb[9] = (double)bin;
+    mb[9] = __longlong_as_double((long long)bin);
+    const float cell = 1.f / fminf(fminf((float)mb[3], (float)mb[4]), (float)mb[5]);
+    mb[10] = __longlong_as_double((long long)__float_as_uint(cell));
 }
 
 // 10-bit coordinate -> every third bit of a 30-bit word
@@ -170,15 +174,17 @@ __global__ void k_morton(int n, const Inst *__restrict__ insts,
     if (i >= n) return;
     const int k = pinst[i];
     const double *mb = mbox + kKeyBox * k;
-    const int bin = (int)mb[9];
+    const int bin = (int)__double_as_longlong(mb[9]);
     const double v[3] = {x[i], y[i], z[i]};
     unsigned cube[3], w[3], nc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        nc[a] = (unsigned)mb[6 + a];
-        double t = (v[a] - mb[a]) * mb[3 + a];
-        t = fmin(fmax(t, 0.0), ldexp((double)nc[a], bin) - 1.0);
-        const unsigned ti = (unsigned)t;
+        nc[a] = (unsigned)__double_as_longlong(mb[6 + a]);
+        // cell index: truncation toward zero, then clamped to the key box
+        // in integers (a NaN converts to 0)
+        const long long tl = __double2ll_rz((v[a] - mb[a]) * mb[3 + a]);
+        const long long top = ((long long)nc[a] << bin) - 1;
+        const unsigned ti = (unsigned)(tl < 0 ? 0 : (tl > top ? top : tl));
         cube[a] = ti >> bin;
         w[a] = ti & ((1u << bin) - 1u);
     }
@@ -397,13 +403,13 @@ __device__ __forceinline__ PadF pad_elem(int i, const Inst *__restrict__ insts,
     const Inst &I = insts[k];
     if (i == I.off) return PadF{1, 1, 1, 0};
     const double *mb = mbox + kKeyBox * k;
-    const int bin = (int)mb[9];
+    const int bin = (int)__double_as_longlong(mb[9]);
     const unsigned long long x = keys[i - 1] ^ keys[i];
     const int d = x ? 63 - __clzll((long long)x) : -1;
     const int ga = kBucket * I.G;
     if (d >= 3 * bin) return PadF{0, 1, ga, 0};  // another cube of the snake
     // the smallest common cell has 2^(d/3 + 1) key cells per side
-    const float cell = 1.f / fminf(fminf((float)mb[3], (float)mb[4]), (float)mb[5]);
+    const float cell = __uint_as_float((unsigned)__double_as_longlong(mb[10]));
     const float side = ldexpf(cell, d < 0 ? 0 : d / 3 + 1);
     const float hh = fmaxf(h[i - 1], h[i]);
     const int a = side > I.kg * hh ? ga : (side > I.kb * hh ? kBucket : 1);
@@ -579,26 +585,35 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         }
         return;
     }
+    // FP64 runs at a small fraction of the FP32 rate on this part: each lane
+    // does only its own offset in FP64 (one subtract, one add, one rounding
+    // per axis; the minimum-image wrap only when the offset could exceed half
+    // a period), and the warp-uniform origin and bounds arithmetic runs in
+    // lane 0 alone.
     const bool ok = lane < cnt;
     float rel[3];
-    double o[3];
     if (update_pos) {
         double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double first = __shfl_sync(kFull, v[a], 0);
+            const double first = __shfl_sync(kFull, v[a], 0);
             double d = v[a] - first;
-            if (I.periodic[a]) d -= I.Ld[a] * rint(d * I.invLd[a]);
-            float mn = warp_min(ok ? (float)d : INFINITY);
-            double kd = floor((first + (double)mn) * I.inv_q);
-            if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
-                if (lane == 0) raise_status(st, ST_ARG, b);
-                kd = 0.0;
+            if (I.periodic[a] && fabsf((float)d) > 0.49f * (float)I.Ld[a])
+                d -= I.Ld[a] * rint(d * I.invLd[a]);
+            const float mn = warp_min(ok ? (float)d : INFINITY);
+            double fo = 0.0;  // first - origin (lane 0)
+            if (lane == 0) {
+                double kd = floor((first + (double)mn) * I.inv_q);
+                if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
+                    raise_status(st, ST_ARG, b);
+                    kd = 0.0;
+                }
+                origin[a * kp.nb + b] = (int)kd;
+                fo = first - kd * I.q;
             }
-            o[a] = kd * I.q;
-            rel[a] = (float)((first - o[a]) + d);
-            if (lane == 0) origin[a * kp.nb + b] = (int)kd;
+            fo = __shfl_sync(kFull, fo, 0);
+            rel[a] = (float)(fo + d);
         }
         if (ok) {
             if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
@@ -608,25 +623,30 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
     } else {
         float4 r = ok ? pm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         rel[0] = r.x; rel[1] = r.y; rel[2] = r.z;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) o[a] = (double)origin[a * kp.nb + b] * I.q;
     }
     const float hi = ok ? h[i] : 0.f;
     if (ok && !(hi > 0.f && isfinite(hi))) raise_status(st, ST_NONFINITE, i);
-    float bc[3], br[3], oc[3], orr[3];
+    float mn[3], mx[3], mnb[3], mxb[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float mn = warp_min(ok ? rel[a] : INFINITY), mx = warp_max(ok ? rel[a] : -INFINITY);
-        float mnb = warp_min(ok ? rel[a] - hi : INFINITY), mxb = warp_max(ok ? rel[a] + hi : -INFINITY);
-        // absolute centres (FP64 add of the origin, then one rounding) and
-        // half widths inflated by the rounding allowance
-        bc[a] = (float)(o[a] + 0.5 * ((double)mn + (double)mx));
-        br[a] = 0.5f * (mx - mn) + I.eps_abs;
-        oc[a] = (float)(o[a] + 0.5 * ((double)mnb + (double)mxb));
-        orr[a] = 0.5f * (mxb - mnb) + I.eps_abs;
+        mn[a] = warp_min(ok ? rel[a] : INFINITY);
+        mx[a] = warp_max(ok ? rel[a] : -INFINITY);
+        mnb[a] = warp_min(ok ? rel[a] - hi : INFINITY);
+        mxb[a] = warp_max(ok ? rel[a] + hi : -INFINITY);
     }
     const float hmax = warp_max(hi);
     if (lane == 0) {
+        float bc[3], br[3], oc[3], orr[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // absolute centres (FP64 add of the origin, then one rounding) and
+            // half widths inflated by the rounding allowance
+            const double o = (double)origin[a * kp.nb + b] * I.q;
+            bc[a] = (float)(o + 0.5 * ((double)mn[a] + (double)mx[a]));
+            br[a] = 0.5f * (mx[a] - mn[a]) + I.eps_abs;
+            oc[a] = (float)(o + 0.5 * ((double)mnb[a] + (double)mxb[a]));
+            orr[a] = 0.5f * (mxb[a] - mnb[a]) + I.eps_abs;
+        }
         const size_t k = (size_t)I.nbase + I.P + (b - I.boff);
         if (update_pos) {
             // .w of the cell half widths: the bucket's largest full extent

@@ -51,7 +51,7 @@ constexpr int kGroupLog = 3;      // groups of up to 8 buckets
 constexpr int kWarpsPerBlock = 4; // pair kernels and walks: 4 warps per block
 constexpr int kSortItems = 8;     // keys per thread in a radix-sort tile
 constexpr int kSortTile = 256 * kSortItems;  // keys per radix-sort tile
-constexpr int kKeyBox = 10;       // doubles per instance of the key box
+constexpr int kKeyBox = 11;       // doubles per instance of the key box
 // Buckets and groups do not straddle large octree cells: consecutive
 // particles start a new bucket when their smallest common key cell is wider
 // than bucket_cell h, a new group when it is wider than group_cell h
