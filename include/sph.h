@@ -257,15 +257,29 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
                     void *stream);
 
 /*
- * sph_step_host: sph_step on HOST arrays.  Copies every array of *hp to
- * device buffers owned by the context (allocated on first use for the
- * context's capacity), runs sph_step there and copies every array back
- * (in curve order, like sph_step).  Host memory may be pageable or pinned;
- * pinned memory copies faster.  Bytes moved per call are reported through
- * h2d_bytes / d2h_bytes when non-NULL.
+ * sph_step_host: sph_step on HOST arrays.  Copies the arrays a step reads
+ * (x, v, u, m, h, a, dudt_h, dudt_av, id, and rho in SPH_ENERGY_ISENTROPIC
+ * mode) to device buffers owned by the context (allocated on first use for
+ * the context's capacity), runs the step there and copies every array back
+ * (in curve order, like sph_step).  If sph_step_host_capture recorded a step
+ * for this context with the same dt_fixed and n, the step is that graph's
+ * replay (as sph_graph_launch), else sph_step.  Host memory may be pageable
+ * or pinned; pinned memory copies faster.  Bytes moved per call are reported
+ * through h2d_bytes / d2h_bytes when non-NULL.
  */
 sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, double *dt_used,
                          int64_t *h2d_bytes, int64_t *d2h_bytes, void *stream);
+
+/*
+ * sph_step_host_capture (no counterpart in the paper, like sph_step_host):
+ * copy the step inputs of *hp into the context's
+ * device buffers and record one step on them as sph_graph_capture does
+ * (same rules: non-default stream, finite dt_fixed, isentropic mode after
+ * one plain step); later sph_step_host calls with this dt_fixed and n
+ * replay it.  *hp is not modified.  Replaces any graph the context held.
+ */
+sph_status sph_step_host_capture(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed,
+                                 void *stream);
 
 /*
  * sph_reduce_conserved: out[9k .. 9k+8] = M, P_x, P_y, P_z, L_x, L_y, L_z,

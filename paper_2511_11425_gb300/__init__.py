@@ -105,6 +105,7 @@ def lib():
                                        C.POINTER(vp)]
         L.sph_batch_get_dt.argtypes = [vp, C.POINTER(dbl)]
         L.sph_graph_capture.argtypes = [vp, pp, dbl, vp]
+        L.sph_step_host_capture.argtypes = [vp, pp, dbl, vp]
         L.sph_graph_launch.argtypes = [vp, C.POINTER(dbl), vp]
         L.sph_graph_totals.argtypes = [vp, C.POINTER(dbl)]
         L.sph_set_dt_old.argtypes = [vp, dbl]
@@ -381,6 +382,13 @@ def sph_step_host(ctx, host_parts: Particles, dt_fixed=0.0, stream=None):
     _check(ctx, lib().sph_step_host(ctx, C.byref(s), float(dt_fixed), C.byref(dt), C.byref(hb),
                                     C.byref(db), _stream(stream)))
     return dt.value, hb.value, db.value
+
+
+def sph_step_host_capture(ctx, host_parts: Particles, dt_fixed=0.0, stream=None):
+    """Record one step on the context's device copy of host arrays; later
+    sph_step_host calls with this dt_fixed replay it."""
+    s = host_parts.c()
+    _check(ctx, lib().sph_step_host_capture(ctx, C.byref(s), float(dt_fixed), _stream(stream)))
 
 
 def sph_reduce_conserved(ctx, parts: Particles, stream=None, ninst=None):

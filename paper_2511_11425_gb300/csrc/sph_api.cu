@@ -887,29 +887,30 @@ namespace {
 struct ArrDesc {
     size_t off;   // offset of the pointer member in sph_particles
     size_t elem;  // element size
+    int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode, 0 never
 };
 const ArrDesc kArrays[] = {
-    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8},
-    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8},
-    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8},
-    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8},
-    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8},
-    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8},
-    {offsetof(sph_particles, u), 8},
-    {offsetof(sph_particles, m), 4},
-    {offsetof(sph_particles, h), 4},
-    {offsetof(sph_particles, rho), 4},
-    {offsetof(sph_particles, omega), 4},
-    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4},
-    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4},
-    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4},
-    {offsetof(sph_particles, dudt_h), 4},
-    {offsetof(sph_particles, dudt_av), 4},
-    {offsetof(sph_particles, divv), 4},
-    {offsetof(sph_particles, dt_i), 4},
-    {offsetof(sph_particles, nngb), 2},
-    {offsetof(sph_particles, iters), 1},
-    {offsetof(sph_particles, id), 8},
+    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1},
+    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1},
+    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1},
+    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1},
+    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1},
+    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1},
+    {offsetof(sph_particles, u), 8, 1},
+    {offsetof(sph_particles, m), 4, 1},
+    {offsetof(sph_particles, h), 4, 1},
+    {offsetof(sph_particles, rho), 4, 2},
+    {offsetof(sph_particles, omega), 4, 0},
+    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1},
+    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1},
+    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1},
+    {offsetof(sph_particles, dudt_h), 4, 1},
+    {offsetof(sph_particles, dudt_av), 4, 1},
+    {offsetof(sph_particles, divv), 4, 0},
+    {offsetof(sph_particles, dt_i), 4, 0},
+    {offsetof(sph_particles, nngb), 2, 0},
+    {offsetof(sph_particles, iters), 1, 0},
+    {offsetof(sph_particles, id), 8, 1},
 };
 void *&member(sph_particles &p, const ArrDesc &d)
 {
@@ -917,15 +918,11 @@ void *&member(sph_particles &p, const ArrDesc &d)
 }
 }  // namespace
 
-extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed,
-                                    double *dt_used, int64_t *h2d_bytes, int64_t *d2h_bytes,
-                                    void *stream)
+namespace {
+// device mirror of the host arrays (allocated once for the capacity) and the
+// host-to-device copy of the arrays a step reads
+sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t *moved)
 {
-    if (!ctx) return SPH_ERR_ARG;
-    Ctx &c = ctx->c;
-    if (!particles_ok(hp) || hp->n > c.capacity)
-        return failf(c, SPH_ERR_ARG, "sph_step_host: NULL array or n > capacity");
-    cudaStream_t s = (cudaStream_t)stream;
     const size_t cap = (size_t)(c.capacity > 0 ? c.capacity : 1);
     if (!c.mirror) {
         size_t total = 0;
@@ -938,22 +935,72 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
         }
     }
     c.dmirror.n = hp->n;
-    int64_t moved = 0;
+    const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC;
+    int64_t b_in = 0;
     for (const ArrDesc &d : kArrays) {
+        if (d.in == 0 || (d.in == 2 && !isen)) continue;
         const size_t b = d.elem * (size_t)hp->n;
-        CK(cudaMemcpyAsync(member(c.dmirror, d), member(*hp, d), b, cudaMemcpyHostToDevice, s));
-        moved += (int64_t)b;
+        CK(cudaMemcpyAsync(member(c.dmirror, d), member(*const_cast<sph_host_particles *>(hp), d),
+                           b, cudaMemcpyHostToDevice, s));
+        b_in += (int64_t)b;
     }
-    if (h2d_bytes) *h2d_bytes = moved;
-    sph_status rc = sph_step(ctx, &c.dmirror, dt_fixed, dt_used, stream);
+    if (moved) *moved = b_in;
+    return SPH_OK;
+}
+
+bool graph_on_mirror(const Ctx &c, double dt_fixed)
+{
+    if (!c.graph_exec || !c.mirror || c.graph_dt != dt_fixed) return false;
+    if (c.graph_p.n != c.dmirror.n) return false;
+    for (const ArrDesc &d : kArrays)
+        if (member(const_cast<sph_particles &>(c.graph_p), d) !=
+            member(const_cast<sph_particles &>(c.dmirror), d))
+            return false;
+    return true;
+}
+}  // namespace
+
+extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed,
+                                    double *dt_used, int64_t *h2d_bytes, int64_t *d2h_bytes,
+                                    void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!particles_ok(hp) || hp->n > c.capacity)
+        return failf(c, SPH_ERR_ARG, "sph_step_host: NULL array or n > capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t moved = 0;
+    sph_status rc = host_in(c, hp, s, &moved);
     if (rc) return rc;
+    if (h2d_bytes) *h2d_bytes = moved;
+    // the captured step when sph_step_host_capture recorded one for these
+    // buffers and this dt_fixed, else the plain step
+    rc = graph_on_mirror(c, dt_fixed) ? sph_graph_launch(ctx, dt_used, stream)
+                                      : sph_step(ctx, &c.dmirror, dt_fixed, dt_used, stream);
+    if (rc) return rc;
+    int64_t out = 0;
     for (const ArrDesc &d : kArrays) {
         const size_t b = d.elem * (size_t)hp->n;
         CK(cudaMemcpyAsync(member(*hp, d), member(c.dmirror, d), b, cudaMemcpyDeviceToHost, s));
+        out += (int64_t)b;
     }
-    if (d2h_bytes) *d2h_bytes = moved;
+    if (d2h_bytes) *d2h_bytes = out;
     CK(cudaStreamSynchronize(s));
     return SPH_OK;
+}
+
+extern "C" sph_status sph_step_host_capture(sph_ctx *ctx, sph_host_particles *hp,
+                                            double dt_fixed, void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!particles_ok(hp) || hp->n > c.capacity)
+        return failf(c, SPH_ERR_ARG, "sph_step_host_capture: NULL array or n > capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    sph_status rc = host_in(c, hp, s, nullptr);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    return sph_graph_capture(ctx, &c.dmirror, dt_fixed, stream);
 }
 
 extern "C" sph_status sph_reduce_conserved(sph_ctx *ctx, const sph_particles *p, double *out,

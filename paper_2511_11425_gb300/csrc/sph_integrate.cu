@@ -56,10 +56,11 @@ __device__ __forceinline__ void kdk_particle(
     double p[3] = {x[i] + dt_new * v0, y[i] + dt_new * v1, z[i] + dt_new * v2};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (I.periodic[a]) {
-            // a particle moves far less than a box length per step
+        // a particle moves far less than a box length per step: only one
+        // that left [lo, hi) is wrapped (two FP64 compares otherwise)
+        if (I.periodic[a] && !(p[a] >= I.lo[a] && p[a] < I.hi[a])) {
             double t = p[a] - I.lo[a];
-            if (t < 0.0 || t >= I.Ld[a]) t -= I.Ld[a] * floor(t * I.invLd[a]);
+            t -= I.Ld[a] * floor(t * I.invLd[a]);
             if (t >= I.Ld[a]) t -= I.Ld[a];
             if (t < 0.0) t = 0.0;
             p[a] = I.lo[a] + t;

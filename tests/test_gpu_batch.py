@@ -104,6 +104,43 @@ def test_graph_replay_matches_plain_steps(sph):
     assert launches > 0
 
 
+def test_step_host_replays_captured_step(sph):
+    """sph_step_host after sph_step_host_capture replays the recorded step on
+    the context's device buffers: same states as plain device steps, only the
+    step's inputs copied in, every array copied out."""
+    import torch
+    prob = inputs.uniform(n=14, seed=12, vamp=0.3, jitter=0.3)
+    stream = torch.cuda.Stream()
+    a = sph.Simulation(prob)
+    host = sph.Particles.from_problem(prob, "cpu", pin=True)
+    ctx = sph.sph_create(sph.Params.for_problem(prob), prob.n)
+    try:
+        with torch.cuda.stream(stream):
+            dta = [sph.sph_step(a.ctx, a.parts, 0.0, stream) for _ in range(4)]
+        stream.synchronize()
+        ga = to_input_order(a.parts.numpy())
+        dtb = [sph.sph_step_host(ctx, host, 0.0, stream)[0]]
+        with pytest.raises(sph.SphError):
+            sph.sph_graph_totals(ctx)                     # nothing replayed yet
+        sph.sph_step_host_capture(ctx, host, 0.0, stream)
+        for _ in range(3):
+            dt, hb, db = sph.sph_step_host(ctx, host, 0.0, stream)
+            dtb.append(dt)
+        totals = sph.sph_graph_totals(ctx)                # set by a replay
+    finally:
+        a.close()
+        sph.sph_destroy(ctx)
+    gb = to_input_order(host.numpy())
+    assert len(totals) == 9
+    assert np.allclose(dta, dtb, rtol=1e-5)
+    assert motion_err(gb["x"], ga["x"], prob) < 1e-5
+    assert norm_err(gb["v"], ga["v"]) < 1e-5
+    assert norm_err(gb["a"], ga["a"]) < 1e-5
+    # inputs only in (x, v, u: 7 x 8 B; m, h, a, du/dt: 7 x 4 B; id 8 B),
+    # everything out (111 B per particle)
+    assert hb == 92 * prob.n and db == 111 * prob.n
+
+
 def test_batch_simulation_graph_matches_plain_batch(sph):
     """BatchSimulation replaying a captured step advances every instance like
     plain batch steps (same step sizes, same state)."""

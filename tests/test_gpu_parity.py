@@ -195,7 +195,7 @@ def test_step_host_matches_device_step(sph):
         sph.sph_destroy(ctx)
     gh = to_input_order(host.numpy())
     assert abs(dt_h - dt_dev) < 1e-6 * dt_dev
-    assert hb == db and hb > prob.n * 100
+    assert hb == 92 * prob.n and db == 111 * prob.n   # step inputs in, every array out
     assert norm_err(gh["a"], gd["a"]) < 1e-5
     assert np.max(np.abs(gh["x"] - gd["x"])) < 1e-9
 
