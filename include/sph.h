@@ -264,8 +264,11 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * (in curve order, like sph_step).  If sph_step_host_capture recorded a step
  * for this context with the same dt_fixed and n, the step is that graph's
  * replay (as sph_graph_launch), else sph_step.  Host memory may be pageable
- * or pinned; pinned memory copies faster.  Bytes moved per call are reported
- * through h2d_bytes / d2h_bytes when non-NULL.
+ * or pinned.  Arrays in pinned memory that the GPU can address are read and
+ * written by one copy kernel per direction (all such arrays in one launch),
+ * the others by cudaMemcpyAsync; either way every host array must hold n
+ * elements.  Bytes moved per call are reported through h2d_bytes /
+ * d2h_bytes when non-NULL.
  */
 sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, double *dt_used,
                          int64_t *h2d_bytes, int64_t *d2h_bytes, void *stream);

@@ -919,6 +919,104 @@ void *&member(sph_particles &p, const ArrDesc &d)
 }  // namespace
 
 namespace {
+// Host <-> device copies of sph_step_host.  Host arrays the GPU can address
+// (pinned memory, mapped into the device's address space) are moved by ONE
+// kernel per direction that reads or writes them over the CPU-GPU link,
+// every array in the same launch: per-array copy-engine transfers cost a few
+// microseconds each, which for the 14 input and 25 output arrays of a step
+// is more than the data time.  Other host memory (pageable) goes through
+// cudaMemcpyAsync.
+constexpr int kMaxCopy = sizeof(kArrays) / sizeof(kArrays[0]);
+struct CopyJob {
+    const char *src[kMaxCopy];
+    char *dst[kMaxCopy];
+    unsigned long long bytes[kMaxCopy];
+};
+
+// blockIdx.y = array; 16-byte words where both ends are 16-byte aligned, the
+// ragged tail (or a misaligned array) byte by byte
+__global__ void __launch_bounds__(256) k_copy_arrays(CopyJob job)
+{
+    const int a = blockIdx.y;
+    const char *__restrict__ src = job.src[a];
+    char *__restrict__ dst = job.dst[a];
+    const unsigned long long nb = job.bytes[a];
+    const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long done = 0;
+    if ((((uintptr_t)src | (uintptr_t)dst) & 15u) == 0) {
+        const unsigned long long n16 = nb / 16;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (unsigned long long i = t; i < n16; i += stride) d4[i] = s4[i];
+        done = n16 * 16;
+    }
+    for (unsigned long long i = done + t; i < nb; i += stride) dst[i] = src[i];
+}
+
+// device address of each host array (NULL where the GPU cannot address it),
+// looked up on every call: an address the caller freed and reused for
+// pageable memory must not keep an old mapping
+void map_host(Ctx &c, const sph_host_particles *hp)
+{
+    c.hkey = *hp;
+    for (const ArrDesc &d : kArrays) {
+        void *h = member(c.hkey, d);
+        void *dev = nullptr;
+        cudaPointerAttributes at;
+        if (h && cudaPointerGetAttributes(&at, h) == cudaSuccess && at.type == cudaMemoryTypeHost)
+            dev = at.devicePointer;
+        cudaGetLastError();  // a failed lookup only means "not mapped"
+        member(c.hdev, d) = dev;
+    }
+}
+
+// copy n elements of every selected array, host -> mirror (in) or mirror ->
+// host (!in); returns the bytes moved
+cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStream_t s,
+                        int64_t *moved)
+{
+    const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC;
+    CopyJob job;
+    int na = 0;
+    unsigned long long most = 0;
+    int64_t b_all = 0;
+    for (const ArrDesc &d : kArrays) {
+        if (in && (d.in == 0 || (d.in == 2 && !isen))) continue;
+        const size_t b = d.elem * (size_t)hp->n;
+        if (b == 0) continue;
+        b_all += (int64_t)b;
+        char *host = (char *)member(*const_cast<sph_host_particles *>(hp), d);
+        char *mapped = (char *)member(c.hdev, d);
+        char *dev = (char *)member(c.dmirror, d);
+        if (mapped) {
+            job.src[na] = in ? mapped : dev;
+            job.dst[na] = in ? dev : mapped;
+            job.bytes[na] = b;
+            most = std::max<unsigned long long>(most, b);
+            ++na;
+        } else {
+            cudaError_t e = cudaMemcpyAsync(in ? dev : host, in ? host : dev, b,
+                                            in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                                            s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (na > 0) {
+        // about four blocks per SM over all arrays, at most one 16-byte word
+        // per thread of the largest array
+        const unsigned long long words = (most + 15) / 16;
+        unsigned gx = (unsigned)std::min<unsigned long long>(
+            (words + 255) / 256, (unsigned long long)std::max(1, 608 / na));
+        c.launches += 1;
+        k_copy_arrays<<<dim3(std::max(gx, 1u), (unsigned)na), 256, 0, s>>>(job);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (moved) *moved = b_all;
+    return cudaSuccess;
+}
+
 // device mirror of the host arrays (allocated once for the capacity) and the
 // host-to-device copy of the arrays a step reads
 sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t *moved)
@@ -935,16 +1033,8 @@ sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t
         }
     }
     c.dmirror.n = hp->n;
-    const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC;
-    int64_t b_in = 0;
-    for (const ArrDesc &d : kArrays) {
-        if (d.in == 0 || (d.in == 2 && !isen)) continue;
-        const size_t b = d.elem * (size_t)hp->n;
-        CK(cudaMemcpyAsync(member(c.dmirror, d), member(*const_cast<sph_host_particles *>(hp), d),
-                           b, cudaMemcpyHostToDevice, s));
-        b_in += (int64_t)b;
-    }
-    if (moved) *moved = b_in;
+    map_host(c, hp);
+    CK(copy_arrays(c, hp, true, s, moved));
     return SPH_OK;
 }
 
@@ -979,11 +1069,7 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
                                       : sph_step(ctx, &c.dmirror, dt_fixed, dt_used, stream);
     if (rc) return rc;
     int64_t out = 0;
-    for (const ArrDesc &d : kArrays) {
-        const size_t b = d.elem * (size_t)hp->n;
-        CK(cudaMemcpyAsync(member(*hp, d), member(c.dmirror, d), b, cudaMemcpyDeviceToHost, s));
-        out += (int64_t)b;
-    }
+    CK(copy_arrays(c, hp, false, s, &out));
     if (d2h_bytes) *d2h_bytes = out;
     CK(cudaStreamSynchronize(s));
     return SPH_OK;

@@ -201,6 +201,11 @@ struct Ctx {
     // host-mode mirror buffers for sph_step_host
     void *mirror = nullptr;
     sph_particles dmirror{};
+    // host arrays of the current sph_step_host call and, per array, the
+    // address the GPU reaches it at (mapped pinned memory) or NULL (copied by
+    // the copy engines instead)
+    sph_particles hkey{};
+    sph_particles hdev{};
 
     // learned seed network
     struct Mlp {

@@ -179,7 +179,12 @@ def test_sod_twenty_steps_track_oracle(sph):
     assert abs(Eg) < 1e-3
 
 
-def test_step_host_matches_device_step(sph):
+@pytest.mark.parametrize("memory", ["pinned", "pageable", "mixed"])
+def test_step_host_matches_device_step(sph, memory):
+    """sph_step_host moves pinned arrays with its copy kernel and the others
+    with copy-engine transfers; 'mixed' has pageable arrays and a pinned array
+    whose start is not 16-byte aligned (byte-wise copy) beside pinned ones."""
+    import torch
     prob = inputs.uniform(n=10, seed=8, jitter=0.3, vamp=0.2)
     dev = sph.Simulation(prob)
     try:
@@ -187,7 +192,14 @@ def test_step_host_matches_device_step(sph):
         gd = to_input_order(dev.parts.numpy())
     finally:
         dev.close()
-    host = sph.Particles.from_problem(prob, "cpu", pin=True)
+    host = sph.Particles.from_problem(prob, "cpu", pin=memory != "pageable")
+    if memory == "mixed":
+        for f in ("u", "v1", "rho", "iters"):
+            host.t[f] = host.t[f].clone()      # pageable copies
+        shifted = torch.zeros(prob.n + 1, dtype=torch.float32, pin_memory=True)[1:]
+        shifted.copy_(host.t["h"])
+        host.t["h"] = shifted                  # pinned, 4 bytes past a 16-byte boundary
+        assert host.t["h"].data_ptr() % 16 == 4 and host.t["h"].is_pinned()
     ctx = sph.sph_create(sph.Params.for_problem(prob), prob.n)
     try:
         dt_h, hb, db = sph.sph_step_host(ctx, host)
