@@ -585,36 +585,42 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         }
         return;
     }
-    // FP64 runs at a small fraction of the FP32 rate on this part: each lane
-    // does only its own offset in FP64 (one subtract, one add, one rounding
-    // per axis; the minimum-image wrap only when the offset could exceed half
-    // a period), and the warp-uniform origin and bounds arithmetic runs in
-    // lane 0 alone.
+    // FP64 runs at a small fraction of the FP32 rate on this part, and an
+    // FP64 instruction costs the pipe about as much for one active lane as
+    // for 32: each lane does only its own offset in FP64 (one subtract, one
+    // add, one rounding per axis; the minimum-image wrap only when the offset
+    // could exceed half a period), and the warp-uniform origin and bounds
+    // arithmetic of axis a runs in lane a, all three axes in one instruction.
     const bool ok = lane < cnt;
+    const int ax = lane < 3 ? lane : 0;  // the axis of lanes 0, 1, 2
+    auto sel = [&](const auto *v3) { return ax == 0 ? v3[0] : (ax == 1 ? v3[1] : v3[2]); };
     float rel[3];
     if (update_pos) {
         double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
+        double first[3], d[3];
+        float mnd[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double first = __shfl_sync(kFull, v[a], 0);
-            double d = v[a] - first;
-            if (I.periodic[a] && fabsf((float)d) > 0.49f * (float)I.Ld[a])
-                d -= I.Ld[a] * rint(d * I.invLd[a]);
-            const float mn = warp_min(ok ? (float)d : INFINITY);
-            double fo = 0.0;  // first - origin (lane 0)
-            if (lane == 0) {
-                double kd = floor((first + (double)mn) * I.inv_q);
-                if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
-                    raise_status(st, ST_ARG, b);
-                    kd = 0.0;
-                }
-                origin[a * kp.nb + b] = (int)kd;
-                fo = first - kd * I.q;
-            }
-            fo = __shfl_sync(kFull, fo, 0);
-            rel[a] = (float)(fo + d);
+            first[a] = __shfl_sync(kFull, v[a], 0);
+            d[a] = v[a] - first[a];
+            if (I.periodic[a] && fabsf((float)d[a]) > 0.49f * (float)I.Ld[a])
+                d[a] -= I.Ld[a] * rint(d[a] * I.invLd[a]);
+            mnd[a] = warp_min(ok ? (float)d[a] : INFINITY);
         }
+        double fo = 0.0;  // first - origin of axis `ax` (lanes 0, 1, 2)
+        if (lane < 3) {
+            const double fa = sel(first);
+            double kd = floor((fa + (double)sel(mnd)) * I.inv_q);
+            if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
+                raise_status(st, ST_ARG, b);
+                kd = 0.0;
+            }
+            origin[ax * kp.nb + b] = (int)kd;
+            fo = fa - kd * I.q;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rel[a] = (float)(__shfl_sync(kFull, fo, a) + d[a]);
         if (ok) {
             if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
                 raise_status(st, ST_NONFINITE, i);
@@ -635,18 +641,26 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         mxb[a] = warp_max(ok ? rel[a] + hi : -INFINITY);
     }
     const float hmax = warp_max(hi);
-    if (lane == 0) {
-        float bc[3], br[3], oc[3], orr[3];
+    // absolute centres (FP64 add of the origin, then one rounding) and half
+    // widths inflated by the rounding allowance, axis `ax` in lane ax
+    float bca = 0.f, bra = 0.f, oca = 0.f, ora = 0.f;
+    if (lane < 3) {
+        const double o = (double)origin[ax * kp.nb + b] * I.q;
+        const float mna = sel(mn), mxa = sel(mx), mnba = sel(mnb), mxba = sel(mxb);
+        bca = (float)(o + 0.5 * ((double)mna + (double)mxa));
+        bra = 0.5f * (mxa - mna) + I.eps_abs;
+        oca = (float)(o + 0.5 * ((double)mnba + (double)mxba));
+        ora = 0.5f * (mxba - mnba) + I.eps_abs;
+    }
+    float bc[3], br[3], oc[3], orr[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // absolute centres (FP64 add of the origin, then one rounding) and
-            // half widths inflated by the rounding allowance
-            const double o = (double)origin[a * kp.nb + b] * I.q;
-            bc[a] = (float)(o + 0.5 * ((double)mn[a] + (double)mx[a]));
-            br[a] = 0.5f * (mx[a] - mn[a]) + I.eps_abs;
-            oc[a] = (float)(o + 0.5 * ((double)mnb[a] + (double)mxb[a]));
-            orr[a] = 0.5f * (mxb[a] - mnb[a]) + I.eps_abs;
-        }
+    for (int a = 0; a < 3; ++a) {
+        bc[a] = __shfl_sync(kFull, bca, a);
+        br[a] = __shfl_sync(kFull, bra, a);
+        oc[a] = __shfl_sync(kFull, oca, a);
+        orr[a] = __shfl_sync(kFull, ora, a);
+    }
+    if (lane == 0) {
         const size_t k = (size_t)I.nbase + I.P + (b - I.boff);
         if (update_pos) {
             // .w of the cell half widths: the bucket's largest full extent
@@ -816,12 +830,25 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float l = warp_min(lo[a]), h = warp_max(hi[a]);
-            double o = (double)origin[a * kp.nb + fb] * I.q;
-            gc[a] = (float)(o + 0.5 * ((double)l + (double)h));
-            gr[a] = 0.5f * (h - l) + 2.f * I.eps_abs;
-            sc[a] = gc[a];
+            lo[a] = warp_min(lo[a]);
+            hi[a] = warp_max(hi[a]);
+            gr[a] = 0.5f * (hi[a] - lo[a]) + 2.f * I.eps_abs;
             sr[a] = -1.f;
+        }
+        // absolute centre in FP64 (origin + offset, one rounding), axis a in
+        // lane a: one FP64 instruction sequence for the three axes
+        float gca = 0.f;
+        if (lane < 3) {
+            const int ax = lane;
+            const float la = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
+            const float ha = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
+            const double o = (double)origin[ax * kp.nb + fb] * I.q;
+            gca = (float)(o + 0.5 * ((double)la + (double)ha));
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gc[a] = __shfl_sync(kFull, gca, a);
+            sc[a] = gc[a];
         }
     } else {
         const size_t k = (size_t)I.nbase + (I.P >> I.logG) + (fl >> I.logG);

@@ -161,14 +161,25 @@ __device__ __forceinline__ void density_bucket(
         return __ballot_sync(kFull, acc);
     };
     auto coverage = [&](float *cc, float *cr) {
+        float lo[3], hi[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float lo = warp_min(valid ? p[a] - R : INFINITY);
-            float hi = warp_max(valid ? p[a] + R : -INFINITY);
-            double o = (double)origin[a * kp.nb + A] * I.q;
-            cc[a] = (float)(o + 0.5 * ((double)lo + (double)hi));
-            cr[a] = 0.5f * (hi - lo) + 2.f * eps_abs;
+            lo[a] = warp_min(valid ? p[a] - R : INFINITY);
+            hi[a] = warp_max(valid ? p[a] + R : -INFINITY);
+            cr[a] = 0.5f * (hi[a] - lo[a]) + 2.f * eps_abs;
         }
+        // absolute centre in FP64 (origin + offset, one rounding): axis a in
+        // lane a, so the three axes cost one FP64 instruction sequence
+        float cca = 0.f;
+        if (lane < 3) {
+            const int ax = lane;
+            const float la = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
+            const float ha = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
+            const double o = (double)origin[ax * kp.nb + A] * I.q;
+            cca = (float)(o + 0.5 * ((double)la + (double)ha));
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cc[a] = __shfl_sync(kFull, cca, a);
     };
     unsigned myword = 0u;
     {
