@@ -29,7 +29,7 @@ SPACE = {
     "group_log": [3, 2],
     "bucket_cell": [3.0, 2.0, 4.0],
     "list_margin": [0.1, 0.05, 0.2],
-    "resort_period": [1, 4],
+    "resort_period": [1, 4, 8, 16],
 }
 ORDER = ("resort_period", "curve", "bucket_cell", "group_log", "list_margin")
 

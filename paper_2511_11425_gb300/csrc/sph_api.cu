@@ -226,6 +226,11 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
         for (cudaEvent_t *e : {&c.ev0, &c.ev1, &c.kev[0], &c.kev[1], &c.kev[2], &c.kev[3],
                                &c.kev[4], &c.kev[5]})
             if (cudaEventCreate(e) != cudaSuccess) rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
+        for (cudaEvent_t *e : {&c.fork, &c.join})
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+                rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
+        if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess)
+            rc = failf(c, SPH_ERR_CUDA, "cudaStreamCreate failed");
     }
     if (rc == SPH_OK && cudaMemset(c.dts, 0, sizeof(double) * 2 * ninst) != cudaSuccess)
         rc = SPH_ERR_CUDA;
@@ -257,8 +262,10 @@ void free_ctx(Ctx &c)
         if (p) cudaFree(p);
     for (void *p : {(void *)c.st_host, (void *)c.dts_host, (void *)c.cons_host})
         if (p) cudaFreeHost(p);
-    for (cudaEvent_t e : {c.ev0, c.ev1, c.kev[0], c.kev[1], c.kev[2], c.kev[3], c.kev[4], c.kev[5]})
+    for (cudaEvent_t e : {c.ev0, c.ev1, c.kev[0], c.kev[1], c.kev[2], c.kev[3], c.kev[4], c.kev[5],
+                          c.fork, c.join})
         if (e) cudaEventDestroy(e);
+    if (c.side) cudaStreamDestroy(c.side);
 }
 
 // lay out instances of the given particle counts (offsets follow the order)
@@ -464,9 +471,14 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
 
 sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed)
 {
-    CK(launch_predict(c, *p, s));
+    // predictor + EOS on the side stream while the force walk runs here
     if (timed) CK(record(c, c.kev[3], s));
+    CK(cudaEventRecord(c.fork, s));
+    CK(cudaStreamWaitEvent(c.side, c.fork, 0));
+    CK(launch_predict(c, *p, c.side));
+    CK(cudaEventRecord(c.join, c.side));
     CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
+    CK(cudaStreamWaitEvent(s, c.join, 0));
     if (timed) CK(record(c, c.kev[4], s));
     CK(launch_forces(c, *p, s));
     if (timed) CK(record(c, c.kev[5], s));

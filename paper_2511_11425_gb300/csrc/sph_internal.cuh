@@ -251,6 +251,10 @@ struct Ctx {
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // side stream of the force phase: the predictor runs there beside the
+    // force walk (fork and join events; graph edges when captured)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     uint64_t launches = 0;
 };
 

@@ -21,11 +21,11 @@ def test_coordinate_descent_finds_the_separable_optimum():
         return 10.0 + sum(cost[n][k[n]] for n in cost)
     start = {"curve": "hilbert", "bucket_cell": 3.0, "group_log": 3, "list_margin": 0.1,
              "resort_period": 1}
-    cost["resort_period"] = {1: 1.0, 4: 0.0}
+    cost["resort_period"] = {1: 1.0, 4: 0.0, 8: 0.5, 16: 0.7}
     best["resort_period"] = 4
     knobs, t, tried = autotune.coordinate_descent(measure, start)
     assert knobs == best and t == 10.0
-    assert len(tried) == len(calls) == 1 + 1 + 1 + 2 + 1 + 2
+    assert len(tried) == len(calls) == 1 + 3 + 1 + 2 + 1 + 2
 
 
 def test_small_gains_are_not_taken():
