@@ -860,9 +860,10 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
     }
 
     const float4 *tn = node + 4 * (size_t)I.nbase;  // this instance's tree
-    // does node nd (at level lvl) hold sources of this group?
-    auto accept = [&](unsigned nd, int lvl) -> bool {
-        const float4 b0 = tn[4 * nd], b1 = tn[4 * nd + 1];
+    // does node nd (at level lvl), with cell bound (b0, b1) and box of balls
+    // (o0, o1; force walks only), hold sources of this group?
+    auto accept_b = [&](unsigned nd, int lvl, float4 b0, float4 b1, float4 o0,
+                        float4 o1) -> bool {
         if (!(b1.x >= 0.f)) return false;  // empty
         bool gth = ovl(gc[0], gr[0], b0.x, b1.x, I.periodic[0], I.L[0], I.invL[0]) &&
                    ovl(gc[1], gr[1], b0.y, b1.y, I.periodic[1], I.L[1], I.invL[1]) &&
@@ -873,7 +874,6 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
             const int last = (int)(((nd + 1u) << shift) - 1u) - I.P;
             if (last < fl) return false;
             if (!gth) {
-                const float4 o0 = tn[4 * nd + 2], o1 = tn[4 * nd + 3];
                 gth = ovl(sc[0], sr[0], o0.x, o1.x, I.periodic[0], I.L[0], I.invL[0]) &&
                       ovl(sc[1], sr[1], o0.y, o1.y, I.periodic[1], I.L[1], I.invL[1]) &&
                       ovl(sc[2], sr[2], o0.z, o1.z, I.periodic[2], I.L[2], I.invL[2]);
@@ -881,6 +881,15 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
             if (lvl == I.logP && (int)(nd - I.P) < fl) gth = false;
         }
         return gth;
+    };
+    auto accept = [&](unsigned nd, int lvl) -> bool {
+        const float4 b0 = tn[4 * nd], b1 = tn[4 * nd + 1];
+        float4 o0 = b0, o1 = b1;
+        if (mode == WALK_FORCE) {
+            o0 = tn[4 * nd + 2];
+            o1 = tn[4 * nd + 3];
+        }
+        return accept_b(nd, lvl, b0, b1, o0, o1);
     };
     // a group whose frontier or list outgrows kWalkCap (a particle with a
     // huge h, e.g. one leaving a free surface): the same warp tests every
@@ -947,11 +956,29 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
         int nnext = 0;
         for (int base = 0; base < ncur; base += 32) {
             const int k = base + lane;
-            const unsigned parent = k < ncur ? cur[k] : 0u;
+            const bool have = k < ncur;
+            const unsigned parent = have ? cur[k] : 1u;
+            // both children's bounds in one round of loads (the two nodes
+            // are adjacent), then the tests
+            const float4 *cn = tn + 8 * (size_t)parent;
+            float4 nb[2][4];
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                nb[ch][0] = cn[4 * ch];
+                nb[ch][1] = cn[4 * ch + 1];
+                if (mode == WALK_FORCE) {
+                    nb[ch][2] = cn[4 * ch + 2];
+                    nb[ch][3] = cn[4 * ch + 3];
+                } else {
+                    nb[ch][2] = nb[ch][0];
+                    nb[ch][3] = nb[ch][1];
+                }
+            }
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
                 const unsigned nd = 2u * parent + (unsigned)ch;
-                const bool acc = k < ncur && accept(nd, lvl);
+                const bool acc = have && accept_b(nd, lvl, nb[ch][0], nb[ch][1], nb[ch][2],
+                                                  nb[ch][3]);
                 push(acc, leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, nxt, nnext);
             }
         }

@@ -33,6 +33,15 @@ __global__ void k_dt_shift(int ninst, double *dts)
 }
 
 // one particle's kicks and drift; h_next is the seed of the next density pass
+// order-preserving integer key of a double: for non-NaN a, b,
+// a < b  <=>  dkey(a) < dkey(b), except that -0 sorts just below +0 (IEEE 754
+// binary64: sign-magnitude, so negative patterns are reflected)
+__device__ __forceinline__ long long dkey(double d)
+{
+    const long long b = __double_as_longlong(d);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
 __device__ __forceinline__ void kdk_particle(
     int i, const Inst *__restrict__ insts, const unsigned short *__restrict__ pinst, double *x,
     double *y, double *z, double *vx, double *vy, double *vz, double *u, float *h,
@@ -57,8 +66,13 @@ __device__ __forceinline__ void kdk_particle(
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         // a particle moves far less than a box length per step: only one
-        // that left [lo, hi) is wrapped (two FP64 compares otherwise)
-        if (I.periodic[a] && !(p[a] >= I.lo[a] && p[a] < I.hi[a])) {
+        // that left [lo, hi) is wrapped.  The test compares order-preserving
+        // integer keys of the IEEE 754 bit patterns (integer pipes; FP64
+        // compares issue at the FP64 rate); a NaN lands in the wrap branch,
+        // as with the FP64 compare, and -0 counts as below +0 (the wrap
+        // then returns +0, the same value)
+        const long long kp_ = dkey(p[a]);
+        if (I.periodic[a] && !(kp_ >= dkey(I.lo[a]) && kp_ < dkey(I.hi[a]))) {
             double t = p[a] - I.lo[a];
             t -= I.Ld[a] * floor(t * I.invLd[a]);
             if (t >= I.Ld[a]) t -= I.Ld[a];
@@ -113,18 +127,22 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(
     const Inst &I = insts[blockIdx.y];
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int b0 = I.off + blockIdx.x * kConsChunk, b1 = min(b0 + kConsChunk, I.off + I.n);
+    // per particle: momentum q = m v, then L += x × q, 2 E_kin += q·v and
+    // E_int += m u as fused multiply-adds into the running sums (the factor
+    // 1/2 of E_kin is applied once, to the total)
     for (int i = b0 + threadIdx.x; i < b1; i += kConsThreads) {
         const double mi = (double)m[i];
         const double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
+        const double q[3] = {mi * v[0], mi * v[1], mi * v[2]};
         acc[0] += mi;
-        acc[1] += mi * v[0];
-        acc[2] += mi * v[1];
-        acc[3] += mi * v[2];
-        acc[4] += mi * (p[1] * v[2] - p[2] * v[1]);
-        acc[5] += mi * (p[2] * v[0] - p[0] * v[2]);
-        acc[6] += mi * (p[0] * v[1] - p[1] * v[0]);
-        acc[7] += 0.5 * mi * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        acc[8] += mi * u[i];
+        acc[1] += q[0];
+        acc[2] += q[1];
+        acc[3] += q[2];
+        acc[4] = fma(p[1], q[2], fma(-p[2], q[1], acc[4]));
+        acc[5] = fma(p[2], q[0], fma(-p[0], q[2], acc[5]));
+        acc[6] = fma(p[0], q[1], fma(-p[1], q[0], acc[6]));
+        acc[7] = fma(q[0], v[0], fma(q[1], v[1], fma(q[2], v[2], acc[7])));
+        acc[8] = fma(mi, u[i], acc[8]);
     }
     __shared__ double sm[9][kConsThreads];
 #pragma unroll
@@ -151,7 +169,7 @@ __global__ void k_cons_final(int nblocks, const double *part, double *out)
     double s = 0.0;
     for (int b = lane; b < nblocks; b += 32) s += pp[b * 9 + q];
     s = warp_sum(s);
-    if (lane == 0) out[blockIdx.x * 9 + q] = s;
+    if (lane == 0) out[blockIdx.x * 9 + q] = q == 7 ? 0.5 * s : s;  // E_kin = (sum m v^2) / 2
 }
 
 cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s)
