@@ -267,7 +267,10 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * or pinned.  Arrays in pinned memory that the GPU can address are read and
  * written by one copy kernel per direction (all such arrays in one launch),
  * the others by cudaMemcpyAsync; either way every host array must hold n
- * elements.  Bytes moved per call are reported through h2d_bytes /
+ * elements.  The inputs that no kernel reads before the end of the density
+ * phase (v, u, a, dudt_h, dudt_av) are copied by the copy engines on a
+ * stream of the context while the step's first phases run (in a step that
+ * re-sorts, before it: the re-sort permutes every array).  Bytes moved per call are reported through h2d_bytes /
  * d2h_bytes when non-NULL.
  */
 sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, double *dt_used,

@@ -226,11 +226,12 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
         for (cudaEvent_t *e : {&c.ev0, &c.ev1, &c.kev[0], &c.kev[1], &c.kev[2], &c.kev[3],
                                &c.kev[4], &c.kev[5]})
             if (cudaEventCreate(e) != cudaSuccess) rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
-        for (cudaEvent_t *e : {&c.fork, &c.join})
+        for (cudaEvent_t *e : {&c.fork, &c.join, &c.call0, &c.late_in})
             if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
                 rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
-        if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess)
-            rc = failf(c, SPH_ERR_CUDA, "cudaStreamCreate failed");
+        for (cudaStream_t *st : {&c.side, &c.copy})
+            if (cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess)
+                rc = failf(c, SPH_ERR_CUDA, "cudaStreamCreate failed");
     }
     if (rc == SPH_OK && cudaMemset(c.dts, 0, sizeof(double) * 2 * ninst) != cudaSuccess)
         rc = SPH_ERR_CUDA;
@@ -263,9 +264,10 @@ void free_ctx(Ctx &c)
     for (void *p : {(void *)c.st_host, (void *)c.dts_host, (void *)c.cons_host})
         if (p) cudaFreeHost(p);
     for (cudaEvent_t e : {c.ev0, c.ev1, c.kev[0], c.kev[1], c.kev[2], c.kev[3], c.kev[4], c.kev[5],
-                          c.fork, c.join})
+                          c.fork, c.join, c.call0, c.late_in})
         if (e) cudaEventDestroy(e);
-    if (c.side) cudaStreamDestroy(c.side);
+    for (cudaStream_t st : {c.side, c.copy})
+        if (st) cudaStreamDestroy(st);
 }
 
 // lay out instances of the given particle counts (offsets follow the order)
@@ -425,6 +427,15 @@ cudaError_t record(const Ctx &c, cudaEvent_t e, cudaStream_t s)
                        : cudaEventRecord(e, s);
 }
 
+// the step inputs sph_step_host copies in beside the step (v, u, a, du/dt):
+// every kernel that reads them comes after this wait.  The event's last
+// record is resolved when the wait (or the graph holding it) is launched;
+// with no sph_step_host call in flight it has completed and costs nothing.
+cudaError_t wait_late_inputs(const Ctx &c, cudaStream_t s)
+{
+    return cudaStreamWaitEvent(s, c.late_in, c.capturing ? cudaEventWaitExternal : 0);
+}
+
 // make sure the layout matches p->n (single-problem contexts follow n)
 sph_status ensure_layout(Ctx &c, const sph_particles *p)
 {
@@ -463,6 +474,7 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
         CK(launch_walk(c, *p, WALK_DENSITY, r, c.h_seed, s));
         CK(launch_density(c, *p, c.h_seed, r, 0, 0, nullptr, nullptr, s));
     }
+    CK(wait_late_inputs(c, s));  // everything before read x, m, h (and rho, id) only
     if (c.mlp.record) CK(launch_mlp_harvest(c, *p, s));
     if (isen) CK(launch_isentropic(c, *p, s));
     CK(launch_bob_refit(c, *p, s));
@@ -731,10 +743,12 @@ sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s,
                       bool full_build)
 {
     if (timed) CK(record(c, c.ev0, s));
-    if (full_build)
+    if (full_build) {
+        CK(wait_late_inputs(c, s));  // the re-sort permutes every array
         CK(launch_build(c, *p, s));
-    else
+    } else {
         CK(launch_refit(c, *p, s));
+    }
     sph_status rc = q_density(c, p, nullptr, s, timed);
     if (rc) return rc;
     rc = q_forces(c, p, s, timed);
@@ -900,29 +914,30 @@ struct ArrDesc {
     size_t off;   // offset of the pointer member in sph_particles
     size_t elem;  // element size
     int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode, 0 never
+    int late;     // first read after the density phase (1): copied in beside the step
 };
 const ArrDesc kArrays[] = {
-    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1},
-    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1},
-    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1},
-    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1},
-    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1},
-    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1},
-    {offsetof(sph_particles, u), 8, 1},
-    {offsetof(sph_particles, m), 4, 1},
-    {offsetof(sph_particles, h), 4, 1},
-    {offsetof(sph_particles, rho), 4, 2},
-    {offsetof(sph_particles, omega), 4, 0},
-    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1},
-    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1},
-    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1},
-    {offsetof(sph_particles, dudt_h), 4, 1},
-    {offsetof(sph_particles, dudt_av), 4, 1},
-    {offsetof(sph_particles, divv), 4, 0},
-    {offsetof(sph_particles, dt_i), 4, 0},
-    {offsetof(sph_particles, nngb), 2, 0},
-    {offsetof(sph_particles, iters), 1, 0},
-    {offsetof(sph_particles, id), 8, 1},
+    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0},
+    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0},
+    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0},
+    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1},
+    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1},
+    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1},
+    {offsetof(sph_particles, u), 8, 1, 1},
+    {offsetof(sph_particles, m), 4, 1, 0},
+    {offsetof(sph_particles, h), 4, 1, 0},
+    {offsetof(sph_particles, rho), 4, 2, 0},
+    {offsetof(sph_particles, omega), 4, 0, 0},
+    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1},
+    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1},
+    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1},
+    {offsetof(sph_particles, dudt_h), 4, 1, 1},
+    {offsetof(sph_particles, dudt_av), 4, 1, 1},
+    {offsetof(sph_particles, divv), 4, 0, 0},
+    {offsetof(sph_particles, dt_i), 4, 0, 0},
+    {offsetof(sph_particles, nngb), 2, 0, 0},
+    {offsetof(sph_particles, iters), 1, 0, 0},
+    {offsetof(sph_particles, id), 8, 1, 0},
 };
 void *&member(sph_particles &p, const ArrDesc &d)
 {
@@ -984,9 +999,11 @@ void map_host(Ctx &c, const sph_host_particles *hp)
 }
 
 // copy n elements of every selected array, host -> mirror (in) or mirror ->
-// host (!in); returns the bytes moved
+// host (!in); part 1: the arrays read early in a step, 2: the late ones
+// (ArrDesc::late), 0: all; engines: copy-engine transfers only (no SMs
+// taken from kernels running beside them); returns the bytes moved
 cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStream_t s,
-                        int64_t *moved)
+                        int64_t *moved, int part = 0, bool engines = false)
 {
     const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC;
     CopyJob job;
@@ -995,11 +1012,12 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
     int64_t b_all = 0;
     for (const ArrDesc &d : kArrays) {
         if (in && (d.in == 0 || (d.in == 2 && !isen))) continue;
+        if ((part == 1 && d.late) || (part == 2 && !d.late)) continue;
         const size_t b = d.elem * (size_t)hp->n;
         if (b == 0) continue;
         b_all += (int64_t)b;
         char *host = (char *)member(*const_cast<sph_host_particles *>(hp), d);
-        char *mapped = (char *)member(c.hdev, d);
+        char *mapped = engines ? nullptr : (char *)member(c.hdev, d);
         char *dev = (char *)member(c.dmirror, d);
         if (mapped) {
             job.src[na] = in ? mapped : dev;
@@ -1046,7 +1064,16 @@ sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t
     }
     c.dmirror.n = hp->n;
     map_host(c, hp);
-    CK(copy_arrays(c, hp, true, s, moved));
+    // the early inputs first, with the whole link; then the late ones on
+    // the copy stream by the copy engines, beside the first phases of the
+    // step (refit, walk, density), which wait for them only at their end
+    int64_t b1 = 0, b2 = 0;
+    CK(copy_arrays(c, hp, true, s, &b1, 1));
+    CK(cudaEventRecord(c.call0, s));
+    CK(cudaStreamWaitEvent(c.copy, c.call0, 0));
+    CK(copy_arrays(c, hp, true, c.copy, &b2, 2, true));
+    CK(cudaEventRecord(c.late_in, c.copy));
+    if (moved) *moved = b1 + b2;
     return SPH_OK;
 }
 
@@ -1098,6 +1125,7 @@ extern "C" sph_status sph_step_host_capture(sph_ctx *ctx, sph_host_particles *hp
     sph_status rc = host_in(c, hp, s, nullptr);
     if (rc) return rc;
     CK(cudaStreamSynchronize(s));
+    CK(cudaStreamSynchronize(c.copy));
     return sph_graph_capture(ctx, &c.dmirror, dt_fixed, stream);
 }
 

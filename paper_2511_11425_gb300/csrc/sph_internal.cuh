@@ -255,6 +255,11 @@ struct Ctx {
     // force walk (fork and join events; graph edges when captured)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // sph_step_host: the step inputs no kernel reads before the end of the
+    // density phase are copied in on `copy` while the step starts; the step
+    // waits for `late_in` there (an external event-wait node when captured)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t call0 = nullptr, late_in = nullptr;
     uint64_t launches = 0;
 };
 
