@@ -226,7 +226,8 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
         for (cudaEvent_t *e : {&c.ev0, &c.ev1, &c.kev[0], &c.kev[1], &c.kev[2], &c.kev[3],
                                &c.kev[4], &c.kev[5]})
             if (cudaEventCreate(e) != cudaSuccess) rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
-        for (cudaEvent_t *e : {&c.fork, &c.join, &c.call0, &c.late_in})
+        for (cudaEvent_t *e : {&c.fork, &c.join, &c.call0, &c.late_in, &c.out_dens, &c.out_force,
+                               &c.out_done})
             if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
                 rc = failf(c, SPH_ERR_CUDA, "cudaEventCreate failed");
         for (cudaStream_t *st : {&c.side, &c.copy})
@@ -264,7 +265,8 @@ void free_ctx(Ctx &c)
     for (void *p : {(void *)c.st_host, (void *)c.dts_host, (void *)c.cons_host})
         if (p) cudaFreeHost(p);
     for (cudaEvent_t e : {c.ev0, c.ev1, c.kev[0], c.kev[1], c.kev[2], c.kev[3], c.kev[4], c.kev[5],
-                          c.fork, c.join, c.call0, c.late_in})
+                          c.fork, c.join, c.call0, c.late_in, c.out_dens, c.out_force,
+                          c.out_done})
         if (e) cudaEventDestroy(e);
     for (cudaStream_t st : {c.side, c.copy})
         if (st) cudaStreamDestroy(st);
@@ -474,6 +476,7 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
         CK(launch_walk(c, *p, WALK_DENSITY, r, c.h_seed, s));
         CK(launch_density(c, *p, c.h_seed, r, 0, 0, nullptr, nullptr, s));
     }
+    CK(record(c, c.out_dens, s));  // rho, Omega, n_i, iterations are final
     CK(wait_late_inputs(c, s));  // everything before read x, m, h (and rho, id) only
     if (c.mlp.record) CK(launch_mlp_harvest(c, *p, s));
     if (isen) CK(launch_isentropic(c, *p, s));
@@ -495,6 +498,7 @@ sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed)
     CK(launch_forces(c, *p, s));
     if (timed) CK(record(c, c.kev[5], s));
     CK(launch_finalize(c, *p, s));
+    CK(record(c, c.out_force, s));  // a, du/dt, div v, dt_i are final
     return SPH_OK;
 }
 
@@ -887,17 +891,23 @@ extern "C" sph_status sph_graph_totals(const sph_ctx *ctx, double *out)
     return SPH_OK;
 }
 
-extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stream)
+namespace {
+// replay of the captured step, queued only (the re-sorting graph when a
+// re-sort is due)
+sph_status graph_enqueue(Ctx &c, cudaStream_t s, bool *full)
 {
-    if (!ctx) return SPH_ERR_ARG;
-    Ctx &c = ctx->c;
-    if (!c.graph_exec) return failf(c, SPH_ERR_STATE, "no captured step: call sph_graph_capture");
-    cudaStream_t s = (cudaStream_t)stream;
     c.err.clear();
-    const bool full = need_full_build(c) || !c.graph_exec_r;
-    CK(cudaGraphLaunch(full ? c.graph_exec : c.graph_exec_r, s));
+    *full = need_full_build(c) || !c.graph_exec_r;
+    CK(cudaGraphLaunch(*full ? c.graph_exec : c.graph_exec_r, s));
     CK(cudaEventRecord(c.ev1, s));
-    c.launches += full ? c.graph_kernels : c.graph_kernels_r;
+    c.launches += *full ? c.graph_kernels : c.graph_kernels_r;
+    return SPH_OK;
+}
+
+// wait for a queued replay and take its status, step size and totals
+sph_status graph_settle(sph_ctx *ctx, cudaStream_t s, bool full, double *dt_used)
+{
+    Ctx &c = ctx->c;
     sph_status rc = settle(ctx, s);
     step_done(c, rc, true);
     count_build(c, full, rc);
@@ -908,6 +918,19 @@ extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stre
     if (rc == SPH_OK && dt_used) *dt_used = c.dt_host[0];
     return rc;
 }
+}  // namespace
+
+extern "C" sph_status sph_graph_launch(sph_ctx *ctx, double *dt_used, void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (!c.graph_exec) return failf(c, SPH_ERR_STATE, "no captured step: call sph_graph_capture");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool full = false;
+    sph_status rc = graph_enqueue(c, s, &full);
+    if (rc) return rc;
+    return graph_settle(ctx, s, full, dt_used);
+}
 
 namespace {
 struct ArrDesc {
@@ -915,29 +938,30 @@ struct ArrDesc {
     size_t elem;  // element size
     int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode, 0 never
     int late;     // first read after the density phase (1): copied in beside the step
+    int out;      // final after the density phase (1), after the forces (2), at the end (0)
 };
 const ArrDesc kArrays[] = {
-    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0},
-    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0},
-    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0},
-    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1},
-    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1},
-    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1},
-    {offsetof(sph_particles, u), 8, 1, 1},
-    {offsetof(sph_particles, m), 4, 1, 0},
-    {offsetof(sph_particles, h), 4, 1, 0},
-    {offsetof(sph_particles, rho), 4, 2, 0},
-    {offsetof(sph_particles, omega), 4, 0, 0},
-    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1},
-    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1},
-    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1},
-    {offsetof(sph_particles, dudt_h), 4, 1, 1},
-    {offsetof(sph_particles, dudt_av), 4, 1, 1},
-    {offsetof(sph_particles, divv), 4, 0, 0},
-    {offsetof(sph_particles, dt_i), 4, 0, 0},
-    {offsetof(sph_particles, nngb), 2, 0, 0},
-    {offsetof(sph_particles, iters), 1, 0, 0},
-    {offsetof(sph_particles, id), 8, 1, 0},
+    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0, 0},
+    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0, 0},
+    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0, 0},
+    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1, 0},
+    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1, 0},
+    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1, 0},
+    {offsetof(sph_particles, u), 8, 1, 1, 0},
+    {offsetof(sph_particles, m), 4, 1, 0, 0},
+    {offsetof(sph_particles, h), 4, 1, 0, 0},
+    {offsetof(sph_particles, rho), 4, 2, 0, 1},
+    {offsetof(sph_particles, omega), 4, 0, 0, 1},
+    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1, 2},
+    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1, 2},
+    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1, 2},
+    {offsetof(sph_particles, dudt_h), 4, 1, 1, 2},
+    {offsetof(sph_particles, dudt_av), 4, 1, 1, 2},
+    {offsetof(sph_particles, divv), 4, 0, 0, 2},
+    {offsetof(sph_particles, dt_i), 4, 0, 0, 2},
+    {offsetof(sph_particles, nngb), 2, 0, 0, 1},
+    {offsetof(sph_particles, iters), 1, 0, 0, 1},
+    {offsetof(sph_particles, id), 8, 1, 0, 0},
 };
 void *&member(sph_particles &p, const ArrDesc &d)
 {
@@ -999,9 +1023,10 @@ void map_host(Ctx &c, const sph_host_particles *hp)
 }
 
 // copy n elements of every selected array, host -> mirror (in) or mirror ->
-// host (!in); part 1: the arrays read early in a step, 2: the late ones
-// (ArrDesc::late), 0: all; engines: copy-engine transfers only (no SMs
-// taken from kernels running beside them); returns the bytes moved
+// host (!in).  part 0: all; in: 1 the arrays read early in a step, 2 the late
+// ones (ArrDesc::late); out: 1 the density outputs, 2 the force outputs, 3
+// the rest (ArrDesc::out).  engines: copy-engine transfers only (no SMs
+// taken from kernels running beside them).  Returns the bytes moved.
 cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStream_t s,
                         int64_t *moved, int part = 0, bool engines = false)
 {
@@ -1012,7 +1037,8 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
     int64_t b_all = 0;
     for (const ArrDesc &d : kArrays) {
         if (in && (d.in == 0 || (d.in == 2 && !isen))) continue;
-        if ((part == 1 && d.late) || (part == 2 && !d.late)) continue;
+        if (in && ((part == 1 && d.late) || (part == 2 && !d.late))) continue;
+        if (!in && part > 0 && d.out != part % 3) continue;
         const size_t b = d.elem * (size_t)hp->n;
         if (b == 0) continue;
         b_all += (int64_t)b;
@@ -1102,15 +1128,36 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
     sph_status rc = host_in(c, hp, s, &moved);
     if (rc) return rc;
     if (h2d_bytes) *h2d_bytes = moved;
-    // the captured step when sph_step_host_capture recorded one for these
-    // buffers and this dt_fixed, else the plain step
-    rc = graph_on_mirror(c, dt_fixed) ? sph_graph_launch(ctx, dt_used, stream)
-                                      : sph_step(ctx, &c.dmirror, dt_fixed, dt_used, stream);
-    if (rc) return rc;
     int64_t out = 0;
-    CK(copy_arrays(c, hp, false, s, &out));
+    if (graph_on_mirror(c, dt_fixed)) {
+        // the step sph_step_host_capture recorded for these buffers and this
+        // dt_fixed.  Outputs that are final before the step ends are copied
+        // back by the copy engines while it finishes (the replay records
+        // the events out_dens and out_force at those points), the rest by
+        // the copy kernel after it; one wait for all.  On an error status
+        // the host arrays hold what the failed step left in the device
+        // buffers (x, v, u as they were).
+        bool full = false;
+        rc = graph_enqueue(c, s, &full);
+        if (rc) return rc;
+        int64_t o1 = 0, o2 = 0, o3 = 0;
+        CK(cudaStreamWaitEvent(c.copy, c.out_dens, 0));
+        CK(copy_arrays(c, hp, false, c.copy, &o1, 1, true));
+        CK(cudaStreamWaitEvent(c.copy, c.out_force, 0));
+        CK(copy_arrays(c, hp, false, c.copy, &o2, 2, true));
+        CK(cudaEventRecord(c.out_done, c.copy));
+        CK(copy_arrays(c, hp, false, s, &o3, 3));
+        CK(cudaStreamWaitEvent(s, c.out_done, 0));
+        out = o1 + o2 + o3;
+        rc = graph_settle(ctx, s, full, dt_used);
+        if (rc) return rc;
+    } else {
+        rc = sph_step(ctx, &c.dmirror, dt_fixed, dt_used, stream);
+        if (rc) return rc;
+        CK(copy_arrays(c, hp, false, s, &out));
+        CK(cudaStreamSynchronize(s));
+    }
     if (d2h_bytes) *d2h_bytes = out;
-    CK(cudaStreamSynchronize(s));
     return SPH_OK;
 }
 

@@ -260,6 +260,10 @@ struct Ctx {
     // waits for `late_in` there (an external event-wait node when captured)
     cudaStream_t copy = nullptr;
     cudaEvent_t call0 = nullptr, late_in = nullptr;
+    // ... and the outputs final before the step ends are copied back on
+    // `copy` once these are reached: density outputs, force outputs; then
+    // out_done joins the copy stream back
+    cudaEvent_t out_dens = nullptr, out_force = nullptr, out_done = nullptr;
     uint64_t launches = 0;
 };
 

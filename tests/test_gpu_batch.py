@@ -136,6 +136,12 @@ def test_step_host_replays_captured_step(sph):
     assert motion_err(gb["x"], ga["x"], prob) < 1e-5
     assert norm_err(gb["v"], ga["v"]) < 1e-5
     assert norm_err(gb["a"], ga["a"]) < 1e-5
+    # outputs copied back while the replay finishes (density and force
+    # outputs) arrive complete, like the ones copied after it
+    for f in ("rho", "omega", "h", "u", "dt_i"):
+        assert norm_err(gb[f], ga[f]) < 1e-5, f
+    assert norm_err(gb["divv"], ga["divv"]) < 1e-3
+    assert np.mean(gb["nngb"] != ga["nngb"]) < 1e-2 and np.all(gb["iters"] >= 1)
     # inputs only in (x, v, u: 7 x 8 B; m, h, a, du/dt: 7 x 4 B; id 8 B),
     # everything out (111 B per particle)
     assert hb == 92 * prob.n and db == 111 * prob.n
