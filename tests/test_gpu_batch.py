@@ -147,6 +147,36 @@ def test_step_host_replays_captured_step(sph):
     assert hb == 92 * prob.n and db == 111 * prob.n
 
 
+def test_step_host_isentropic_replay_matches_device_steps(sph):
+    """In the entropy-conserving mode rho is a step input (read before the
+    density pass) and u is first read after it (copied in beside the step):
+    host-buffer steps, plain and replayed, follow plain device steps."""
+    import torch
+    prob = inputs.uniform(n=12, seed=21, vamp=0.3, jitter=0.3)
+    prm = sph.Params.for_problem(prob, energy="isentropic", resort_period=2)
+    stream = torch.cuda.Stream()
+    a = sph.Simulation(prob, prm)
+    host = sph.Particles.from_problem(prob, "cpu", pin=True)
+    ctx = sph.sph_create(prm, prob.n)
+    try:
+        with torch.cuda.stream(stream):
+            dta = [sph.sph_step(a.ctx, a.parts, 0.0, stream) for _ in range(5)]
+        stream.synchronize()
+        ga = to_input_order(a.parts.numpy())
+        dtb = [sph.sph_step_host(ctx, host, 0.0, stream)[0]]
+        sph.sph_step_host_capture(ctx, host, 0.0, stream)
+        for _ in range(4):                                # re-sorting and refitting replays
+            dtb.append(sph.sph_step_host(ctx, host, 0.0, stream)[0])
+    finally:
+        a.close()
+        sph.sph_destroy(ctx)
+    gb = to_input_order(host.numpy())
+    assert np.allclose(dta, dtb, rtol=1e-5)
+    assert motion_err(gb["x"], ga["x"], prob) < 1e-5
+    for f in ("v", "a", "u", "rho", "h"):
+        assert norm_err(gb[f], ga[f]) < 1e-5, f
+
+
 def test_batch_simulation_graph_matches_plain_batch(sph):
     """BatchSimulation replaying a captured step advances every instance like
     plain batch steps (same step sizes, same state)."""
