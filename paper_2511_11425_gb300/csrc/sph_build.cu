@@ -812,7 +812,11 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
     float gc[3], gr[3], sc[3], sr[3];  // gather box, group cell box
     if (mode == WALK_DENSITY) {
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int j = 0; j < nbg; ++j) {
+        // unrolled over the group's (at most 8) buckets so that their loads
+        // are issued together
+#pragma unroll
+        for (int j = 0; j < (1 << kGroupLog); ++j) {
+            if (j >= nbg) break;
             const int b = fb + j;
             const float3 off = origin_offset(I, kp.nb, origin, fb, b);
             const int i0 = bstart[b];
@@ -954,32 +958,49 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
     for (int lvl = L0 + 1; lvl <= I.logP && !overflow; ++lvl) {
         const bool leaf = lvl == I.logP;
         int nnext = 0;
-        for (int base = 0; base < ncur; base += 32) {
-            const int k = base + lane;
-            const bool have = k < ncur;
-            const unsigned parent = have ? cur[k] : 1u;
-            // both children's bounds in one round of loads (the two nodes
-            // are adjacent), then the tests
-            const float4 *cn = tn + 8 * (size_t)parent;
-            float4 nb[2][4];
+        // two chunks of 32 parents per round: the bounds of all their
+        // children (adjacent node pairs) in one round of loads, then the
+        // tests and pushes in frontier order
+        for (int base = 0; base < ncur; base += 64) {
+            unsigned parent[2];
+            bool have[2];
+            float4 nb[2][2][4];
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
-                nb[ch][0] = cn[4 * ch];
-                nb[ch][1] = cn[4 * ch + 1];
-                if (mode == WALK_FORCE) {
-                    nb[ch][2] = cn[4 * ch + 2];
-                    nb[ch][3] = cn[4 * ch + 3];
-                } else {
-                    nb[ch][2] = nb[ch][0];
-                    nb[ch][3] = nb[ch][1];
+            for (int q = 0; q < 2; ++q) {
+                const int k = base + 32 * q + lane;
+                have[q] = k < ncur;
+                parent[q] = have[q] ? cur[k] : 1u;
+                const float4 *cn = tn + 8 * (size_t)parent[q];
+#pragma unroll
+                for (int ch = 0; ch < 2; ++ch) {
+                    nb[q][ch][0] = cn[4 * ch];
+                    nb[q][ch][1] = cn[4 * ch + 1];
+                    if (mode == WALK_FORCE) {
+                        nb[q][ch][2] = cn[4 * ch + 2];
+                        nb[q][ch][3] = cn[4 * ch + 3];
+                    } else {
+                        nb[q][ch][2] = nb[q][ch][0];
+                        nb[q][ch][3] = nb[q][ch][1];
+                    }
                 }
             }
+            bool acc[2][2];
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
-                const unsigned nd = 2u * parent + (unsigned)ch;
-                const bool acc = have && accept_b(nd, lvl, nb[ch][0], nb[ch][1], nb[ch][2],
-                                                  nb[ch][3]);
-                push(acc, leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, nxt, nnext);
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int ch = 0; ch < 2; ++ch)
+                    acc[q][ch] = have[q] && accept_b(2u * parent[q] + (unsigned)ch, lvl,
+                                                     nb[q][ch][0], nb[q][ch][1], nb[q][ch][2],
+                                                     nb[q][ch][3]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (base + 32 * q >= ncur) break;  // (warp-uniform)
+#pragma unroll
+                for (int ch = 0; ch < 2; ++ch) {
+                    const unsigned nd = 2u * parent[q] + (unsigned)ch;
+                    push(acc[q][ch], leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, nxt,
+                         nnext);
+                }
             }
         }
         __syncwarp();
