@@ -129,9 +129,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_for(kernel_file, kernel_name):
-    """DRAM bytes per launch from the committed ncu summary, if it still
-    describes the current source of that kernel."""
+def _ncu_record(kernel_file, kernel_name):
+    """The committed ncu summary of a kernel (profiles/traffic.json), if it
+    still describes the current source of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel_name)
@@ -141,6 +141,15 @@ def _traffic_for(kernel_file, kernel_name):
         return None
     src = open(os.path.join(ROOT, "paper_2511_11425_gb300", "csrc", kernel_file), "rb").read()
     if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha"):
+        return None
+    return rec
+
+
+def _traffic_for(kernel_file, kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current source of that kernel."""
+    rec = _ncu_record(kernel_file, kernel_name)
+    if rec is None:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -525,6 +534,12 @@ def run_ours(args, rank, world, local_rank):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
             "fp32_fma_measured_tflops": fma_measured,
             "ms_per_launch": dom["ms_per_launch"]}
+    # the hardware view of the same kernel (ncu, committed summary): pipe
+    # utilisation counts every issued instruction, rejected candidates included
+    rec = _ncu_record(dom_file, dom["kernel"])
+    if rec and "fma_pipe_active_pct" in rec:
+        roof["ncu_pipes_active_pct"] = {"fma": rec["fma_pipe_active_pct"],
+                                        "alu": rec["alu_pipe_active_pct"]}
     other_line = {**other, "frac": other["achieved"] / FP32_PEAK_TFLOPS}
 
     # end to end through the host-buffer entry point
