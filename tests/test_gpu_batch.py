@@ -177,6 +177,45 @@ def test_step_host_isentropic_replay_matches_device_steps(sph):
         assert norm_err(gb[f], ga[f]) < 1e-5, f
 
 
+def test_replayed_rewalk_rounds_match_plain_steps(sph):
+    """Seeding every density pass 20 % below the converged h (the seed is
+    the h array the step starts from) puts the root beyond the lists'
+    10 % coverage, so the re-walk rounds do work, in plain steps and inside
+    replayed graphs alike.  Replays give the plain steps' states and report
+    their re-walks."""
+    import torch
+    prob = inputs.uniform(n=12, seed=33, vamp=0.3, jitter=0.3)
+    prm = sph.Params.for_problem(prob)
+    stream = torch.cuda.Stream()
+    a = sph.Simulation(prob, prm)
+    b = sph.Simulation(prob, prm)
+    try:
+        with torch.cuda.stream(stream):
+            dta, dtb, relists_a, relists_b = [], [], [], []
+            for k in range(4):
+                a.parts.t["h"].mul_(0.8)
+                dta.append(sph.sph_step(a.ctx, a.parts, 0.0, stream))
+                relists_a.append(sph.sph_get_stats(a.ctx)["relists"])
+            b.parts.t["h"].mul_(0.8)
+            dtb.append(sph.sph_step(b.ctx, b.parts, 0.0, stream))
+            sph.sph_graph_capture(b.ctx, b.parts, 0.0, stream)
+            for _ in range(3):
+                b.parts.t["h"].mul_(0.8)
+                dtb.append(sph.sph_graph_launch(b.ctx, stream))
+                relists_b.append(sph.sph_get_stats(b.ctx)["relists"])
+        stream.synchronize()
+        ga = to_input_order(a.parts.numpy())
+        gb = to_input_order(b.parts.numpy())
+    finally:
+        a.close()
+        b.close()
+    assert min(relists_a) > 0 and min(relists_b) > 0   # the rounds ran inside the replays
+    assert np.allclose(dta, dtb, rtol=1e-5)
+    assert motion_err(gb["x"], ga["x"], prob) < 1e-5
+    for f in ("h", "rho", "omega", "v", "a"):
+        assert norm_err(gb[f], ga[f]) < 1e-5, f
+
+
 def test_batch_simulation_graph_matches_plain_batch(sph):
     """BatchSimulation replaying a captured step advances every instance like
     plain batch steps (same step sizes, same state)."""
