@@ -774,7 +774,7 @@ static void tree_refit(Ctx &c, cudaStream_t s, int bob_only)
 // ---------------------------------------------------------------------------
 // interaction-list walk (Sec. 2.3.2): one walk per GROUP of up to 8
 // consecutive buckets (256 particles, the paper's GPU group size) of one
-// instance, breadth-first over that instance's tree, 32 node tests per round.
+// instance, breadth-first over that instance's tree, one round of node loads per level.
 //   density: source cell bound overlaps the group's box of balls of radius
 //            h_walk (1 + margin)                              (gather)
 //   force:   source cell bound overlaps the group box-of-balls (gather) OR
