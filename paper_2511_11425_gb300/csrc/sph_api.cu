@@ -974,8 +974,8 @@ namespace {
 // (pinned memory, mapped into the device's address space) are moved by ONE
 // kernel per direction that reads or writes them over the CPU-GPU link,
 // every array in the same launch: per-array copy-engine transfers cost a few
-// microseconds each, which for the 14 input and 25 output arrays of a step
-// is more than the data time.  Other host memory (pageable) goes through
+// microseconds each, which for the 15 input (16 in the entropy-conserving
+// mode) and 21 output arrays of a step is more than the data time.  Other host memory (pageable) goes through
 // cudaMemcpyAsync.
 constexpr int kMaxCopy = sizeof(kArrays) / sizeof(kArrays[0]);
 struct CopyJob {
