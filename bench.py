@@ -561,8 +561,14 @@ def run_ours(args, rank, world, local_rank):
                 flush.zero_()
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
-                _, hb, db = sph.sph_step_host(ctx2, host, 0.0, s)
+                _, hbi, dbi = sph.sph_step_host(ctx2, host, 0.0, s)
                 tt += time.perf_counter() - t0
+                hb += hbi
+                db += dbi
+            # bytes per step, averaged: a refitting step copies m and id back
+            # only when a re-sort changed them
+            hb = hb // args.steps
+            db = db // args.steps
         finally:
             sph.sph_destroy(ctx2)
         e2e = {"value": world * prob2.n * args.steps / tt, "unit": UNIT,

@@ -939,29 +939,30 @@ struct ArrDesc {
     int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode, 0 never
     int late;     // first read after the density phase (1): copied in beside the step
     int out;      // final after the density phase (1), after the forces (2), at the end (0)
+    int sorted;   // changed only by a re-sort (1: m, id), so unchanged by a refitting step
 };
 const ArrDesc kArrays[] = {
-    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0, 0},
-    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0, 0},
-    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0, 0},
-    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1, 0},
-    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1, 0},
-    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1, 0},
-    {offsetof(sph_particles, u), 8, 1, 1, 0},
-    {offsetof(sph_particles, m), 4, 1, 0, 0},
-    {offsetof(sph_particles, h), 4, 1, 0, 0},
-    {offsetof(sph_particles, rho), 4, 2, 0, 1},
-    {offsetof(sph_particles, omega), 4, 0, 0, 1},
-    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1, 2},
-    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1, 2},
-    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1, 2},
-    {offsetof(sph_particles, dudt_h), 4, 1, 1, 2},
-    {offsetof(sph_particles, dudt_av), 4, 1, 1, 2},
-    {offsetof(sph_particles, divv), 4, 0, 0, 2},
-    {offsetof(sph_particles, dt_i), 4, 0, 0, 2},
-    {offsetof(sph_particles, nngb), 2, 0, 0, 1},
-    {offsetof(sph_particles, iters), 1, 0, 0, 1},
-    {offsetof(sph_particles, id), 8, 1, 0, 0},
+    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0, 0, 0},
+    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0, 0, 0},
+    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0, 0, 0},
+    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1, 0, 0},
+    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1, 0, 0},
+    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1, 0, 0},
+    {offsetof(sph_particles, u), 8, 1, 1, 0, 0},
+    {offsetof(sph_particles, m), 4, 1, 0, 0, 1},
+    {offsetof(sph_particles, h), 4, 1, 0, 0, 0},
+    {offsetof(sph_particles, rho), 4, 2, 0, 1, 0},
+    {offsetof(sph_particles, omega), 4, 0, 0, 1, 0},
+    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1, 2, 0},
+    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1, 2, 0},
+    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1, 2, 0},
+    {offsetof(sph_particles, dudt_h), 4, 1, 1, 2, 0},
+    {offsetof(sph_particles, dudt_av), 4, 1, 1, 2, 0},
+    {offsetof(sph_particles, divv), 4, 0, 0, 2, 0},
+    {offsetof(sph_particles, dt_i), 4, 0, 0, 2, 0},
+    {offsetof(sph_particles, nngb), 2, 0, 0, 1, 0},
+    {offsetof(sph_particles, iters), 1, 0, 0, 1, 0},
+    {offsetof(sph_particles, id), 8, 1, 0, 0, 1},
 };
 void *&member(sph_particles &p, const ArrDesc &d)
 {
@@ -1026,9 +1027,11 @@ void map_host(Ctx &c, const sph_host_particles *hp)
 // host (!in).  part 0: all; in: 1 the arrays read early in a step, 2 the late
 // ones (ArrDesc::late); out: 1 the density outputs, 2 the force outputs, 3
 // the rest (ArrDesc::out).  engines: copy-engine transfers only (no SMs
-// taken from kernels running beside them).  Returns the bytes moved.
+// taken from kernels running beside them).  skip_sorted: leave out the
+// arrays only a re-sort changes.  Returns the bytes moved.
 cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStream_t s,
-                        int64_t *moved, int part = 0, bool engines = false)
+                        int64_t *moved, int part = 0, bool engines = false,
+                        bool skip_sorted = false)
 {
     const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC;
     CopyJob job;
@@ -1039,6 +1042,7 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
         if (in && (d.in == 0 || (d.in == 2 && !isen))) continue;
         if (in && ((part == 1 && d.late) || (part == 2 && !d.late))) continue;
         if (!in && part > 0 && d.out != part % 3) continue;
+        if (skip_sorted && d.sorted) continue;
         const size_t b = d.elem * (size_t)hp->n;
         if (b == 0) continue;
         b_all += (int64_t)b;
@@ -1146,7 +1150,9 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
         CK(cudaStreamWaitEvent(c.copy, c.out_force, 0));
         CK(copy_arrays(c, hp, false, c.copy, &o2, 2, true));
         CK(cudaEventRecord(c.out_done, c.copy));
-        CK(copy_arrays(c, hp, false, s, &o3, 3));
+        // a refitting replay leaves m and id as they were copied in: the
+        // host arrays already hold them
+        CK(copy_arrays(c, hp, false, s, &o3, 3, false, !full));
         CK(cudaStreamWaitEvent(s, c.out_done, 0));
         out = o1 + o2 + o3;
         rc = graph_settle(ctx, s, full, dt_used);
