@@ -271,8 +271,9 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * phase (v, u, a, dudt_h, dudt_av) are copied by the copy engines on a
  * stream of the context while the step's first phases run (in a step that
  * re-sorts, before it: the re-sort permutes every array).  A replay that only
- * refits leaves m and id, which only a re-sort changes, as they are on the
- * host and does not copy them back (d2h_bytes counts what was copied).  Bytes moved per call are reported through h2d_bytes /
+ * refits reads no id and leaves m and id, which only a re-sort changes, as
+ * they are on the host: id is not copied in, m and id are not copied back
+ * (h2d_bytes and d2h_bytes count what was copied).  Bytes moved per call are reported through h2d_bytes /
  * d2h_bytes when non-NULL.
  */
 sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, double *dt_used,

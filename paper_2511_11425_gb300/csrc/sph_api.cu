@@ -940,29 +940,30 @@ struct ArrDesc {
     int late;     // first read after the density phase (1): copied in beside the step
     int out;      // final after the density phase (1), after the forces (2), at the end (0)
     int sorted;   // changed only by a re-sort (1: m, id), so unchanged by a refitting step
+    int sort_in;  // read only by a re-sort (1: id)
 };
 const ArrDesc kArrays[] = {
-    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0, 0, 0},
-    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0, 0, 0},
-    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0, 0, 0},
-    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1, 0, 0},
-    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1, 0, 0},
-    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1, 0, 0},
-    {offsetof(sph_particles, u), 8, 1, 1, 0, 0},
-    {offsetof(sph_particles, m), 4, 1, 0, 0, 1},
-    {offsetof(sph_particles, h), 4, 1, 0, 0, 0},
-    {offsetof(sph_particles, rho), 4, 2, 0, 1, 0},
-    {offsetof(sph_particles, omega), 4, 0, 0, 1, 0},
-    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1, 2, 0},
-    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1, 2, 0},
-    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1, 2, 0},
-    {offsetof(sph_particles, dudt_h), 4, 1, 1, 2, 0},
-    {offsetof(sph_particles, dudt_av), 4, 1, 1, 2, 0},
-    {offsetof(sph_particles, divv), 4, 0, 0, 2, 0},
-    {offsetof(sph_particles, dt_i), 4, 0, 0, 2, 0},
-    {offsetof(sph_particles, nngb), 2, 0, 0, 1, 0},
-    {offsetof(sph_particles, iters), 1, 0, 0, 1, 0},
-    {offsetof(sph_particles, id), 8, 1, 0, 0, 1},
+    {offsetof(sph_particles, x) + 0 * sizeof(double *), 8, 1, 0, 0, 0, 0},
+    {offsetof(sph_particles, x) + 1 * sizeof(double *), 8, 1, 0, 0, 0, 0},
+    {offsetof(sph_particles, x) + 2 * sizeof(double *), 8, 1, 0, 0, 0, 0},
+    {offsetof(sph_particles, v) + 0 * sizeof(double *), 8, 1, 1, 0, 0, 0},
+    {offsetof(sph_particles, v) + 1 * sizeof(double *), 8, 1, 1, 0, 0, 0},
+    {offsetof(sph_particles, v) + 2 * sizeof(double *), 8, 1, 1, 0, 0, 0},
+    {offsetof(sph_particles, u), 8, 1, 1, 0, 0, 0},
+    {offsetof(sph_particles, m), 4, 1, 0, 0, 1, 0},
+    {offsetof(sph_particles, h), 4, 1, 0, 0, 0, 0},
+    {offsetof(sph_particles, rho), 4, 2, 0, 1, 0, 0},
+    {offsetof(sph_particles, omega), 4, 0, 0, 1, 0, 0},
+    {offsetof(sph_particles, a) + 0 * sizeof(float *), 4, 1, 1, 2, 0, 0},
+    {offsetof(sph_particles, a) + 1 * sizeof(float *), 4, 1, 1, 2, 0, 0},
+    {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1, 2, 0, 0},
+    {offsetof(sph_particles, dudt_h), 4, 1, 1, 2, 0, 0},
+    {offsetof(sph_particles, dudt_av), 4, 1, 1, 2, 0, 0},
+    {offsetof(sph_particles, divv), 4, 0, 0, 2, 0, 0},
+    {offsetof(sph_particles, dt_i), 4, 0, 0, 2, 0, 0},
+    {offsetof(sph_particles, nngb), 2, 0, 0, 1, 0, 0},
+    {offsetof(sph_particles, iters), 1, 0, 0, 1, 0, 0},
+    {offsetof(sph_particles, id), 8, 1, 0, 0, 1, 1},
 };
 void *&member(sph_particles &p, const ArrDesc &d)
 {
@@ -1028,7 +1029,8 @@ void map_host(Ctx &c, const sph_host_particles *hp)
 // ones (ArrDesc::late); out: 1 the density outputs, 2 the force outputs, 3
 // the rest (ArrDesc::out).  engines: copy-engine transfers only (no SMs
 // taken from kernels running beside them).  skip_sorted: leave out the
-// arrays only a re-sort changes.  Returns the bytes moved.
+// arrays only a re-sort reads (in) or changes (out).  Returns the bytes
+// moved.
 cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStream_t s,
                         int64_t *moved, int part = 0, bool engines = false,
                         bool skip_sorted = false)
@@ -1042,7 +1044,7 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
         if (in && (d.in == 0 || (d.in == 2 && !isen))) continue;
         if (in && ((part == 1 && d.late) || (part == 2 && !d.late))) continue;
         if (!in && part > 0 && d.out != part % 3) continue;
-        if (skip_sorted && d.sorted) continue;
+        if (skip_sorted && (in ? d.sort_in : d.sorted)) continue;
         const size_t b = d.elem * (size_t)hp->n;
         if (b == 0) continue;
         b_all += (int64_t)b;
@@ -1079,7 +1081,8 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
 
 // device mirror of the host arrays (allocated once for the capacity) and the
 // host-to-device copy of the arrays a step reads
-sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t *moved)
+sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t *moved,
+                   bool refit_replay = false)
 {
     const size_t cap = (size_t)(c.capacity > 0 ? c.capacity : 1);
     if (!c.mirror) {
@@ -1098,7 +1101,7 @@ sph_status host_in(Ctx &c, const sph_host_particles *hp, cudaStream_t s, int64_t
     // the copy stream by the copy engines, beside the first phases of the
     // step (refit, walk, density), which wait for them only at their end
     int64_t b1 = 0, b2 = 0;
-    CK(copy_arrays(c, hp, true, s, &b1, 1));
+    CK(copy_arrays(c, hp, true, s, &b1, 1, false, refit_replay));
     CK(cudaEventRecord(c.call0, s));
     CK(cudaStreamWaitEvent(c.copy, c.call0, 0));
     CK(copy_arrays(c, hp, true, c.copy, &b2, 2, true));
@@ -1129,7 +1132,12 @@ extern "C" sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double
         return failf(c, SPH_ERR_ARG, "sph_step_host: NULL array or n > capacity");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t moved = 0;
-    sph_status rc = host_in(c, hp, s, &moved);
+    // a replay of the recorded step that only refits reads no id (only a
+    // re-sort permutes it): the mirror's copy is refreshed by the next
+    // re-sorting step's input copy, and the host's stays as it is
+    const bool replay = c.mirror && hp->n == c.dmirror.n && graph_on_mirror(c, dt_fixed);
+    const bool refit_replay = replay && !(need_full_build(c) || !c.graph_exec_r);
+    sph_status rc = host_in(c, hp, s, &moved, refit_replay);
     if (rc) return rc;
     if (h2d_bytes) *h2d_bytes = moved;
     int64_t out = 0;

@@ -165,10 +165,11 @@ def test_step_host_isentropic_replay_matches_device_steps(sph):
         ga = to_input_order(a.parts.numpy())
         dtb = [sph.sph_step_host(ctx, host, 0.0, stream)[0]]
         sph.sph_step_host_capture(ctx, host, 0.0, stream)
-        out_bytes = []
+        in_bytes, out_bytes = [], []
         for _ in range(4):                                # re-sorting and refitting replays
             dt, hb, db = sph.sph_step_host(ctx, host, 0.0, stream)
             dtb.append(dt)
+            in_bytes.append(hb)
             out_bytes.append(db)
     finally:
         a.close()
@@ -178,8 +179,10 @@ def test_step_host_isentropic_replay_matches_device_steps(sph):
     assert motion_err(gb["x"], ga["x"], prob) < 1e-5
     for f in ("v", "a", "u", "rho", "h"):
         assert norm_err(gb[f], ga[f]) < 1e-5, f
-    # a refitting replay leaves m and id on the host as they were (12 B per
-    # particle not copied back); the ids still order the particles above
+    # a refitting replay reads no id (8 B per particle not copied in; rho
+    # is an input in this mode) and leaves m and id on the host as they were
+    # (12 B per particle not copied back); the ids still order the particles
+    assert sorted(set(in_bytes)) == [88 * prob.n, 96 * prob.n]
     assert sorted(set(out_bytes)) == [99 * prob.n, 111 * prob.n]
     assert np.array_equal(gb["m"], ga["m"]) and np.array_equal(np.sort(gb["id"]), np.arange(prob.n))
 
