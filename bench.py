@@ -18,6 +18,9 @@ conserved-totals reduction.
   roofline    the dominant pair kernel against the FP32 pipe peak
               (152 SMs x 128 lanes x 2 flop x 2.07 GHz), algorithmic flops only
   cpu_baseline the FP64 oracle on a bounded sample of the same state
+  error_vs_oracle  per-field error of the GPU path against the oracle on
+              sampled sinks of the stepped state (the 'stated error' of the
+              metric), computed in the oracle's leg
 
 --impl reference times the oracle (the deliberately slow FP64 brute force)
 on the same workload and metric.  Under torchrun every rank runs its own
@@ -154,9 +157,11 @@ def _traffic_for(kernel_file, kernel_name):
     return rec.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(prob, target_s=15.0):
+def cpu_baseline(prob, target_s=15.0, gpu=None, err_prob=None):
     """The oracle as it stands on this host: density (Newton, brute force over
-    all N) + forces for a sample of sink particles; particle-steps/s."""
+    all N) + forces for a sample of sink particles; particle-steps/s.  With
+    the GPU's t = 0 fields given, also the per-field error of the GPU path
+    against the oracle (error_vs_oracle)."""
     import oracle
     from oracle import build as obuild
     obuild.build()
@@ -181,10 +186,86 @@ def cpu_baseline(prob, target_s=15.0):
     S = int(min(prob.n, max(1024, 1024 * target_s / max(t, 1e-3))))
     t = run(S)
     cores = int(oracle.lib().orc_num_threads())
-    return {"value": S / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d random sink particles of the t=0 state: Newton density (seeded from "
-                      "the lattice h) and forces, each brute force over all %d particles in "
-                      "FP64; %.1f s" % (S, prob.n, t)}
+    out = {"value": S / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d random sink particles of the t=0 state: Newton density (seeded from "
+                     "the lattice h) and forces, each brute force over all %d particles in "
+                     "FP64; %.1f s" % (S, prob.n, t)}
+    err = error_vs_oracle(err_prob or prob, gpu, p) if gpu is not None else None
+    return out, err
+
+
+def gpu_fields(prob, params, dev):
+    """One evaluation of a state on the GPU through the C ABI (build_cells,
+    density_h seeded from prob.h0, forces) with the timed layout knobs;
+    fields in input order."""
+    import paper_2511_11425_gb300 as sph
+    parts = sph.Particles.from_problem(prob, dev)
+    ctx = sph.sph_create(params, prob.n)
+    try:
+        sph.sph_build_cells(ctx, parts)
+        sph.sph_density_h(ctx, parts)
+        sph.sph_forces(ctx, parts)
+        g = parts.numpy()
+    finally:
+        sph.sph_destroy(ctx)
+    order = np.argsort(g["id"], kind="stable")
+    out = {k: v[order] for k, v in g.items()}
+    out["a"] = np.stack([out["a0"], out["a1"], out["a2"]], 1)
+    return out
+
+
+def error_vs_oracle(prob, gpu, p):
+    """Per-field error of the GPU's fields of a state against the FP64 oracle on
+    sampled sinks (compact clusters round seeded centres and the blast
+    centre).  The oracle solves h, rho and Omega by brute force over all N for
+    every particle within 2.2 h_max of a sink, so the sinks' force sums see
+    exact neighbour values.  h, rho, Omega: max relative error; a, du/dt and
+    div v: max error over the field's max norm (the parity tolerances are
+    1e-5 and 2e-4)."""
+    import oracle
+    rng = np.random.default_rng(5)
+    centres = np.concatenate([rng.random((5, 3)), [[0.5, 0.5, 0.5]]])
+    lo, hi = np.array(prob.box_lo), np.array(prob.box_hi)
+    L = hi - lo
+    per = np.array(prob.periodic, dtype=bool)
+
+    def wrap(d):
+        d = d.copy()
+        d[:, per] -= L[per] * np.round(d[:, per] / L[per])
+        return d
+    sinks = []
+    for c in centres:
+        d = wrap(prob.pos - (lo + c * L))
+        sinks.extend(np.argsort((d * d).sum(1))[:24])
+    sinks = np.unique(np.array(sinks))
+    R = 2.2 * float(np.max(prob.h0))
+    keep = np.zeros(prob.n, dtype=bool)
+    for s_ in sinks:
+        d = wrap(prob.pos - prob.pos[s_])
+        keep |= (d * d).sum(1) < R * R
+    hood = np.nonzero(keep)[0]
+    t0 = time.perf_counter()
+    d = oracle.density_h(p, prob.pos, prob.m, prob.h0, hood)
+    h = np.zeros(prob.n)
+    rho = np.ones(prob.n)
+    om = np.ones(prob.n)
+    h[hood], rho[hood], om[hood] = d["h"], d["rho"], d["omega"]
+    f = oracle.forces(p, prob.pos, prob.vel, prob.m, h, rho, om, prob.u, sinks)
+    secs = time.perf_counter() - t0
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+
+    def norm(a, b):
+        return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+    return {"h": rel(gpu["h"][sinks], h[sinks]), "rho": rel(gpu["rho"][sinks], rho[sinks]),
+            "omega": rel(gpu["omega"][sinks], om[sinks]), "a": norm(gpu["a"][sinks], f["a"]),
+            "dudt_h": norm(gpu["dudt_h"][sinks], f["dudt_h"]),
+            "dudt_av": norm(gpu["dudt_av"][sinks], f["dudt_av"]),
+            "divv": norm(gpu["divv"][sinks], f["divv"]),
+            "tolerance": {"h_rho_omega_rel": 1e-5, "a_dudt_divv_max_norm": 2e-4},
+            "sinks": int(len(sinks)), "neighbourhood": int(len(hood)),
+            "oracle_s": round(secs, 1)}
 
 
 def combine_ranks(ms, n_local, steps, world):
@@ -575,6 +656,16 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
 
     totals = sph.sph_graph_totals(sim.ctx)
+    stepped = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the stepped state (in motion round the blast) for the error report
+        import dataclasses
+        g = sim.parts.numpy()
+        o = np.argsort(g["id"], kind="stable")
+        stepped = dataclasses.replace(
+            prob, pos=np.stack([g["x0"], g["x1"], g["x2"]], 1)[o],
+            vel=np.stack([g["v0"], g["v1"], g["v2"]], 1)[o], u=g["u"][o],
+            h0=g["h"][o].astype(np.float64))
     sim.close()
     forms = None
     if world == 1 and not args.no_forms:
@@ -582,9 +673,11 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         forms["learned"] = forms_learned(dev)
         torch.cuda.empty_cache()
-    cpu = None
+    cpu = err = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(prob)
+        cpu, err = cpu_baseline(prob, gpu=gpu_fields(stepped, params, dev), err_prob=stepped)
+        err["state"] = ("the state after the %d warm-up and %d timed steps, evaluated with "
+                        "the timed layout knobs" % (args.warmup, args.steps))
     if rank == 0:
         secs = tmax / 1000.0
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -611,6 +704,7 @@ def run_ours(args, rank, world, local_rank):
                     "walks": phase["ms_walk"]},
                 "roofline": roof, "roofline_other": other_line, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
+                "error_vs_oracle": err,
                 "forms": forms, "impl": "ours"}
         print(json.dumps(line), flush=True)
     return 0
