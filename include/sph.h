@@ -260,21 +260,24 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * sph_step_host: sph_step on HOST arrays.  Copies the arrays a step reads
  * (x, v, u, m, h, a, dudt_h, dudt_av, id, and rho in SPH_ENERGY_ISENTROPIC
  * mode) to device buffers owned by the context (allocated on first use for
- * the context's capacity), runs the step there and copies every array back
- * (in curve order, like sph_step).  If sph_step_host_capture recorded a step
- * for this context with the same dt_fixed and n, the step is that graph's
- * replay (as sph_graph_launch), else sph_step.  Host memory may be pageable
- * or pinned.  Arrays in pinned memory that the GPU can address are read and
- * written by one copy kernel per direction (all such arrays in one launch),
- * the others by cudaMemcpyAsync; either way every host array must hold n
- * elements.  The inputs that no kernel reads before the end of the density
- * phase (v, u, a, dudt_h, dudt_av) are copied by the copy engines on a
- * stream of the context while the step's first phases run (in a step that
- * re-sorts, before it: the re-sort permutes every array).  A replay that only
- * refits reads no id and leaves m and id, which only a re-sort changes, as
- * they are on the host: id is not copied in, m and id are not copied back
- * (h2d_bytes and d2h_bytes count what was copied).  Bytes moved per call are reported through h2d_bytes /
- * d2h_bytes when non-NULL.
+ * the context's capacity), runs the step there and copies every array it
+ * changes back (in curve order, like sph_step).  If sph_step_host_capture
+ * recorded a step for this context with the same dt_fixed and n, the step is
+ * that graph's replay (as sph_graph_launch), else sph_step.
+ * Memory: host arrays may be pageable or pinned and must hold n elements.
+ * Pinned arrays that the GPU can address are read and written by one copy
+ * kernel per direction (all such arrays in one launch), the others by
+ * cudaMemcpyAsync.
+ * Overlap: the inputs no kernel reads before the end of the density phase
+ * (v, u, a, dudt_h, dudt_av) are copied by the copy engines on a stream of
+ * the context while the step's first phases run (in a step that re-sorts,
+ * before it: the re-sort permutes every array).  In a replay, the density
+ * and force outputs are copied back while the rest of the step runs; a
+ * replay that only refits neither reads id nor changes m and id, so id is
+ * not copied in and m and id are not copied back.  On an error status of a
+ * replay the host arrays hold what the failed step left (x, v, u as they
+ * were).
+ * h2d_bytes / d2h_bytes (when non-NULL) receive the bytes copied in and out.
  */
 sph_status sph_step_host(sph_ctx *ctx, sph_host_particles *hp, double dt_fixed, double *dt_used,
                          int64_t *h2d_bytes, int64_t *d2h_bytes, void *stream);
