@@ -5,7 +5,8 @@ Workload: the Sedov-Taylor blast of the paper's test suite (Sec. 3.3) on a
 neighbours, alpha = 1, beta = 2, gamma = 5/3, starting at t = 0.  One step =
 sph_step: Morton sort + bounds tree, density/h Newton pass, force pass,
 kick-drift-kick with the Courant step (every row of the hot path), plus the
-conserved-totals reduction.
+conserved-totals reduction.  --workload kh128 times the Kelvin-Helmholtz
+shear layer (Sec. 3.8 setting) on 128^3 = 2,097,152 particles instead.
 
   value       particle-steps/s with the state resident in HBM; each timed step
               is one replay of the captured step (CUDA graph, conserved totals
@@ -63,13 +64,22 @@ METRIC = "SPH particle-steps/s"
 UNIT = "particle-steps/s"
 
 
+WORKLOADS = {
+    "sedov64": "sedov_taylor_64^3 (262,144 particles, periodic unit box, t from 0)",
+    "kh128": "kelvin_helmholtz_128^3 (2,097,152 particles, periodic unit box, t from 0)",
+}
+_WORKLOAD = ["sedov64"]  # set from --workload
+
+
 def _workload(rank=0):
     from paper_2511_11425_gb300 import inputs
+    if _WORKLOAD[0] == "kh128":
+        return inputs.kh(n=128, seed=2511 + rank)
     return inputs.sedov(n=64, seed=2511 + rank)
 
 
 def _config(prob, extra=None):
-    c = {"workload": "sedov_taylor_64^3 (262,144 particles, periodic unit box, t from 0)",
+    c = {"workload": WORKLOADS[_WORKLOAD[0]],
          "particles": prob.n, "kernel": "wendland_c2", "n_ngb": 64, "gamma": prob.gamma,
          "alpha": prob.alpha, "beta": prob.beta,
          "precision": "fp32 pair arithmetic on cell-relative offsets, fp64 positions and "
@@ -134,13 +144,14 @@ class ClockSampler:
 
 def _ncu_record(kernel_file, kernel_name):
     """The committed ncu summary of a kernel (profiles/traffic.json), if it
-    still describes the current source of that kernel."""
+    still describes the current source of that kernel and was taken on the
+    workload being timed."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel_name)
     except (OSError, ValueError):
         return None
-    if not rec:
+    if not rec or rec.get("bench_workload") != _WORKLOAD[0]:
         return None
     src = open(os.path.join(ROOT, "paper_2511_11425_gb300", "csrc", kernel_file), "rb").read()
     if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha"):
@@ -722,9 +733,13 @@ def main(argv=None):
                     help="fixed layout knobs instead of tuning, e.g. curve=morton,bucket_cell=3")
     ap.add_argument("--no-tune", action="store_true",
                     help="run the default layout knobs instead of autotuning them first")
+    ap.add_argument("--workload", default="sedov64", choices=sorted(WORKLOADS),
+                    help="the timed problem: the Sedov-Taylor blast on 64^3 particles "
+                         "(default) or the Kelvin-Helmholtz shear layer on 128^3")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the plain / batched / graph comparison on 256 instances")
     args = ap.parse_args(argv)
+    _WORKLOAD[0] = args.workload
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
