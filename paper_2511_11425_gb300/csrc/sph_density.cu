@@ -191,54 +191,29 @@ __device__ __forceinline__ void density_bucket(
         }
     }
     const unsigned nwords = (nl + 31) / 32;
-    constexpr bool CACHE = !EMIT;
-    int cached = -1;    // candidates kept in shared memory from an earlier pass (-1: none)
-    float hcull = 0.f;  // the lane's cull radius when they were staged
 
     for (int pass = 0; pass <= kp.max_newton; ++pass) {
         if (__all_sync(kFull, done)) break;
         const float h2 = h * h, ih = 1.f / h;
-        Kahan Sw, Sq;
-        int cnt = 0;
-        // candidates staged by an earlier pass of this warp stay in shared
-        // memory (non-emitting passes): reused while every active lane's h
-        // lies inside the radius its ball was culled with
-        const bool reuse = CACHE && cached >= 0 && __all_sync(kFull, done || h <= hcull);
-        if (reuse) {
-            for (int k0 = 0; k0 < cached; k0 += kChunk) {
-                const int cc = min(kChunk, cached - k0);
-                if (!done) cands += cc;
-                density_chunk<K, WRAP, EMIT>(bx, cand + k0, candj, cc, lane, p[0], p[1], p[2], h2,
-                                             ih, !done, Sw, Sq, cnt, i, cap, emitted, ids_out,
-                                             id_in);
-                __syncwarp();
-            }
-        } else {
-        // cull radius: h, slightly inflated when the staged set is kept for
-        // later passes (the hit test itself uses h)
-        const float hs = CACHE ? h * (1.f + kCacheSlack) : h;
         // box of balls and ball of balls of the active lanes (Sec. 2.3.2: a
         // source must overlap both shapes)
         float bc[3], br[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float bl = warp_min(done ? INFINITY : p[a] - hs);
-            float bh = warp_max(done ? -INFINITY : p[a] + hs);
+            float bl = warp_min(done ? INFINITY : p[a] - h);
+            float bh = warp_max(done ? -INFINITY : p[a] + h);
             bc[a] = 0.5f * (bl + bh);
             br[a] = 0.5f * (bh - bl);
         }
         float bb2;
         {
             float dx = p[0] - bc[0], dy = p[1] - bc[1], dz = p[2] - bc[2];
-            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + hs;
+            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + h;
             rr = warp_max(rr) * (1.f + 1e-6f) + eps_abs;
             bb2 = rr * rr;
         }
-        // c: candidates staged, c0: start of the chunk not yet evaluated.  With
-        // the cache the chunks follow one another in shared memory; without
-        // it (or once the cache would overflow) the buffer restarts at 0
-        int c = 0, c0 = 0;
-        bool spill = false;
+        Kahan Sw, Sq;
+        int cnt = 0, c = 0;
         for (unsigned w = 0; w < nwords; ++w) {
           unsigned mw;
           if (w < 32) {
@@ -278,32 +253,22 @@ __device__ __forceinline__ void density_bucket(
                 if (EMIT) candj[pos] = j;
             }
             c += __popc(bal);
-            if (c - c0 > kChunk - 32) {
+            if (c > kChunk - 32) {
                 __syncwarp();
-                if (!done) cands += c - c0;
-                density_chunk<K, WRAP, EMIT>(bx, cand + c0, candj, c - c0, lane, p[0], p[1], p[2],
-                                             h2, ih, !done, Sw, Sq, cnt, i, cap, emitted, ids_out,
-                                             id_in);
+                if (!done) cands += c;
+                density_chunk<K, WRAP, EMIT>(bx, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
+                                             !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
                 __syncwarp();
-                c0 = c;
-                if (!CACHE || c > kCacheCap - kChunk) {
-                    c = c0 = 0;
-                    spill = true;
-                }
+                c = 0;
             }
           }
         }
-        if (c > c0) {
+        if (c > 0) {
             __syncwarp();
-            if (!done) cands += c - c0;
-            density_chunk<K, WRAP, EMIT>(bx, cand + c0, candj, c - c0, lane, p[0], p[1], p[2], h2,
-                                         ih, !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
+            if (!done) cands += c;
+            density_chunk<K, WRAP, EMIT>(bx, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
+                                         !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
             __syncwarp();
-        }
-        if (CACHE) {
-            cached = spill ? -1 : c;
-            hcull = hs;
-        }
         }
         if (!done) {
             ++iters;
@@ -449,7 +414,7 @@ __global__ void __launch_bounds__(128, 5) k_density(
     const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *redo_cnt_out,
     unsigned *gflag, const float4 *__restrict__ node, DevStatus *st)
 {
-    __shared__ float4 cand_s[kWarpsPerBlock][EMIT ? kChunk : kCacheCap + 32];
+    __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!group_ids) {  // every bucket, one warp each

@@ -46,10 +46,6 @@ namespace sph {
 
 constexpr int kBucket = 32;       // particles per bucket = one warp
 constexpr int kChunk = 128;       // staged candidates processed per chunk
-// density passes keep up to kCacheCap staged candidates per warp for the
-// next pass, culled with h (1 + kCacheSlack)
-constexpr int kCacheCap = 512;
-constexpr float kCacheSlack = 4e-3f;
 constexpr int kWalkCap = 1024;    // frontier / list entries per group
 constexpr int kGroupLog = 3;      // groups of up to 8 buckets
 constexpr int kWarpsPerBlock = 4; // pair kernels and walks: 4 warps per block
