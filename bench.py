@@ -43,10 +43,33 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SM_COUNT = 152
-FP32_LANES = 128
-SM_MAX_GHZ = 2.070
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
+FP32_LANES = 128      # FP32 lanes per SM (4 sub-partitions x 32)
+SM_MAX_GHZ = 2.070    # maximum SM clock of the GB300 (nvidia-smi clocks.max.sm)
+
+
+def fp32_peak_tflops(sms):
+    """Derived FP32 peak: SMs x 128 lanes x 2 flop (FMA) x maximum SM clock."""
+    return sms * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
+
+
+def fma_probe(stream):
+    """Measured FP32 FMA throughput (TFLOP/s) and SM count of the current
+    device, from the benchmark's own probe library (_fma_probe.so, built
+    beside libsph but not part of it); (None, None) if it cannot run."""
+    import ctypes as C
+    import paper_2511_11425_gb300 as sph
+    path = os.path.join(os.path.dirname(sph.LIB_PATH), "_fma_probe.so")
+    try:
+        L = C.CDLL(path)
+    except OSError:
+        return None, None
+    L.fma_probe_tflops.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]
+    L.fma_probe_tflops.restype = C.c_int
+    t, n = C.c_double(), C.c_int()
+    handle = stream.cuda_stream if stream is not None else None
+    if L.fma_probe_tflops(C.byref(t), C.byref(n), C.c_void_p(handle)) != 0:
+        return None, None
+    return t.value, n.value
 # Algorithmic flops per unit (FMA = 2; add, mul, divide, rsqrt = 1; compares,
 # selects and min/max not counted), tallied from the pair loops:
 #  density pair (Wendland C2): separation 3, r^2 5, r 2, q 1, w(q) 6,
@@ -616,14 +639,14 @@ def run_ours(args, rank, world, local_rank):
           "ms_per_launch": kf / args.steps}
     dom, other = (rd, rf) if kd >= kf else (rf, rd)
     dom_file = "sph_density.cu" if dom is rd else "sph_forces.cu"
-    try:
-        fma_measured = sph.sph_probe_fp32_peak(s)
-    except sph.SphError:
-        fma_measured = None
-    roof = {"bound": "alu", "achieved": dom["achieved"], "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": dom["achieved"] / FP32_PEAK_TFLOPS,
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sms)
+    fma_measured, _ = fma_probe(s)
+    roof = {"bound": "alu", "achieved": dom["achieved"], "peak": peak,
+            "unit": "TFLOP/s", "frac": dom["achieved"] / peak,
             "traffic": _traffic_for(dom_file, dom["kernel"]), "kernel": dom["kernel"],
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+            "peak_source": "derived: %d SMs (device properties) x 128 FP32 lanes x 2 flop x "
+                           "2.07 GHz" % sms,
             "fp32_fma_measured_tflops": fma_measured,
             "ms_per_launch": dom["ms_per_launch"]}
     # the hardware view of the same kernel (ncu, committed summary): pipe
@@ -632,7 +655,7 @@ def run_ours(args, rank, world, local_rank):
     if rec and "fma_pipe_active_pct" in rec:
         roof["ncu_pipes_active_pct"] = {"fma": rec["fma_pipe_active_pct"],
                                         "alu": rec["alu_pipe_active_pct"]}
-    other_line = {**other, "frac": other["achieved"] / FP32_PEAK_TFLOPS}
+    other_line = {**other, "frac": other["achieved"] / peak}
 
     # end to end through the host-buffer entry point
     e2e = None

@@ -59,7 +59,7 @@ typedef enum {
     SPH_ERR_CAPACITY = 3,   /* a fixed-size internal buffer would overflow                 */
     SPH_ERR_NOCONV = 4,     /* Newton iteration on h did not converge within max_newton    */
     SPH_ERR_NONFINITE = 5,  /* a NaN / Inf was produced or found in the inputs             */
-    SPH_ERR_TIMEOUT = 6,    /* a bounded device-side wait ran out                          */
+                            /* 6 is unused: no kernel of the library waits on another   */
     SPH_ERR_STATE = 7       /* calls made out of order (e.g. forces before density)        */
 } sph_status;
 
@@ -341,12 +341,18 @@ sph_status sph_batch_get_dt(const sph_ctx *ctx, double *out);
  * Partial sums live in a fixed file-scope device array of 576 KiB that every
  * GPU loading the library keeps until exit; n is therefore limited to
  * 8,388,608 particles and larger n returns SPH_ERR_CAPACITY without launching.
- * The first call on each device looks up the array's device address (with
- * that device current); make it before any stream capture.  All calls on a
- * device share the array: calls that overlap on the GPU race and give wrong
- * totals.  Errors: SPH_ERR_ARG (NULL pointer, n < 0), SPH_ERR_CUDA (launch or
- * address lookup failed).  There is no context, so sph_last_error does not
- * apply.
+ * The array's device address is looked up in the CUDA context current at
+ * the call (afresh on every call whose stream is not being captured, and
+ * cached per context for calls made during a stream capture): make the first
+ * call in each context before any stream capture.  All calls on a device
+ * share the array: calls that overlap on the GPU race and give wrong totals.
+ * n = 0 writes nine zeros to out.
+ * Errors: SPH_ERR_ARG (NULL pointer, n < 0); SPH_ERR_CAPACITY (n > 8,388,608,
+ * nothing launched); SPH_ERR_CUDA (a CUDA error was already pending from the
+ * caller's earlier work: it is left pending and nothing is launched; or the
+ * address lookup or a launch of this call failed; or the first call in a
+ * context was made during a stream capture).  There is no context, so
+ * sph_last_error does not apply.
  */
 sph_status sph_reduce_conserved_noalloc(const sph_particles *p, double *out, void *stream);
 
@@ -448,13 +454,6 @@ sph_status sph_mlp_infer(sph_ctx *ctx, const float *x, int64_t n, float *y, void
  * (first needs nslots + 1 entries, SPH_ERR_ARG otherwise).  Synchronous.
  * The paper has no counterpart (it is a view of the data layout). */
 sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t cap, int64_t *nslots);
-
-/* sph_probe_fp32_peak: measured FP32 FMA throughput of the current device
- * in TFLOP/s (8 independent fmaf chains per thread on every SM, best of 3
- * timed launches; allocates and frees a small device buffer, synchronous).
- * A measuring stick for the pair kernels' roofline; the paper has no
- * counterpart. */
-sph_status sph_probe_fp32_peak(double *tflops, void *stream);
 
 /* sph_set_dt_old: set the previous step size used by the predictor and the
  * closing kick (0 restarts the integration as at t = 0). */

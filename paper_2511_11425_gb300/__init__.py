@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_libsph.so")
 
 STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_CAPACITY",
-          4: "SPH_ERR_NOCONV", 5: "SPH_ERR_NONFINITE", 6: "SPH_ERR_TIMEOUT", 7: "SPH_ERR_STATE"}
+          4: "SPH_ERR_NOCONV", 5: "SPH_ERR_NONFINITE", 7: "SPH_ERR_STATE"}
 KERNELS = {"wc2": 0, "wc4": 1, "wc6": 2, "m4": 3}
 ENERGY = {"pdv": 0, "isentropic": 1}
 CURVES = {"hilbert": 0, "morton": 1}
@@ -32,7 +32,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
            "sph_graph_capture", "sph_graph_launch", "sph_graph_totals", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
-           "sph_mlp_load_samples", "sph_bucket_layout", "sph_probe_fp32_peak",
+           "sph_mlp_load_samples", "sph_bucket_layout",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
 MLP_NPARAM = 1249
 SEED_MODES = {"analytic": 0, "mlp": 1}
@@ -122,7 +122,6 @@ def lib():
         L.sph_mlp_grad.argtypes = [vp, vp, vp, i64, fp, C.POINTER(dbl), vp]
         L.sph_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
         L.sph_bucket_layout.argtypes = [vp, C.POINTER(C.c_int32), i64, C.POINTER(i64)]
-        L.sph_probe_fp32_peak.argtypes = [C.POINTER(dbl), vp]
         L.sph_get_stats.argtypes = [vp, C.POINTER(c_stats)]
         L.sph_last_error.argtypes = [vp]
         L.sph_last_error.restype = C.c_char_p
@@ -403,10 +402,29 @@ def sph_reduce_conserved(ctx, parts: Particles, stream=None, ninst=None):
 def sph_reduce_conserved_noalloc(parts: Particles, out, stream=None):
     """Totals into `out` (a device tensor of 9 float64) without any allocation.
 
-    Only queues the work: synchronise the stream before reading `out`."""
+    Only queues the work: synchronise the stream before reading `out`.
+    Raises ValueError unless `out` is a contiguous float64 CUDA tensor of at
+    least 9 elements on the current device (the kernel writes 9 doubles)."""
+    _check_totals_out(out)
     s = parts.c()
     _check(None, lib().sph_reduce_conserved_noalloc(C.byref(s), C.c_void_p(out.data_ptr()),
                                                     _stream(stream)))
+
+
+def _check_totals_out(out):
+    import torch
+    if not isinstance(out, torch.Tensor):
+        raise ValueError("out must be a torch tensor")
+    if not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor")
+    if out.dtype != torch.float64:
+        raise ValueError("out must be float64")
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    if out.numel() < 9:
+        raise ValueError("out needs at least 9 elements")
+    if out.device.index != torch.cuda.current_device():
+        raise ValueError("out must be on the current CUDA device")
 
 
 # ---- learned seed of the h iteration -----------------------------------------
@@ -502,13 +520,6 @@ def sph_bucket_layout(ctx):
     _check(ctx, lib().sph_bucket_layout(ctx, first.ctypes.data_as(C.POINTER(C.c_int32)),
                                         first.size, C.byref(ns)))
     return first
-
-
-def sph_probe_fp32_peak(stream=None) -> float:
-    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
-    t = C.c_double()
-    _check(None, lib().sph_probe_fp32_peak(C.byref(t), _stream(stream)))
-    return t.value
 
 
 def sph_set_dt_old(ctx, dt_old: float):

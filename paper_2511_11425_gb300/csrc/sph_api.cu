@@ -396,7 +396,6 @@ sph_status settle(sph_ctx *ctx, cudaStream_t s)
                      "%d iterations or %d re-walks", h.detail, c.kp.max_newton, kRelistRounds);
     case ST_NONFINITE:
         return failf(c, SPH_ERR_NONFINITE, "non-finite value at index %d", h.detail);
-    case ST_TIMEOUT: return failf(c, SPH_ERR_TIMEOUT, "device wait timed out (%d)", h.detail);
     default: return failf(c, SPH_ERR_CUDA, "unknown device status %d", h.code);
     }
 }

@@ -83,7 +83,7 @@ static_assert(kMlpParams == SPH_MLP_NPARAM, "network size");
 
 enum StatusCode : int {
     ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_CAPACITY = 3, ST_NOCONV = 4, ST_NONFINITE = 5,
-    ST_TIMEOUT = 6, ST_STATE = 7
+    ST_STATE = 7
 };
 
 // device-resident status + counters, reset at the start of every API call
