@@ -102,3 +102,18 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(libpath):
         sph.sph_create(sph.Params(bucket_cell=4.0, group_cell=3.0), 10)
     with pytest.raises(sph.SphError):
         sph.sph_create(sph.Params(resort_period=65), 10)
+
+
+def test_noalloc_binding_refuses_unusable_out_buffers():
+    """The allocation-free totals write 9 doubles through a raw device
+    pointer: the binding refuses anything else before calling the library."""
+    import numpy as np
+    import torch
+
+    import paper_2511_11425_gb300 as sph
+    from paper_2511_11425_gb300 import inputs
+    prob = inputs.uniform(n=4, seed=1)
+    parts = sph.Particles.from_problem(prob, "cpu")
+    for bad in (np.zeros(9), torch.zeros(9, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            sph.sph_reduce_conserved_noalloc(parts, bad)

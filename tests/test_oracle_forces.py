@@ -241,3 +241,44 @@ def test_pdv_sum_conditioning_output():
     assert np.all(f["dudt_h_scale"] >= np.abs(f["dudt_h"]) * (1 - 1e-12))
     f = oracle.forces(p, prob.pos, np.ones_like(v), prob.m, d["h"], d["rho"], d["omega"], prob.u)
     assert np.all(f["vdw_abs"] == 0.0)
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    vals = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_two_particle_forces_match_hand_values():
+    """Absolute size of every force term, including the viscosity's mu_ij
+    (h-bar factor, eps h-bar^2 in the denominator), Pi_ij, its acceleration
+    and heating, and the Courant limit (tests/golden/two_particle_forces.txt)."""
+    g = _golden("two_particle_forces.txt")
+    p = oracle.Params(kernel="wc2", gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps_av=0.01,
+                      eta_courant=0.15, eta_acc=0.2, box_lo=(-1.0, -1.0, -1.0),
+                      box_hi=(1.0, 1.0, 1.0), periodic=(0, 0, 0))
+    pos = np.array([[0.0, 0.0, 0.0], [0.3, 0.0, 0.0]])
+    vel = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+    f = oracle.forces(p, pos, vel, np.array([0.01, 0.02]), np.array([1.0, 0.5]),
+                      np.array([1.2, 0.8]), np.array([1.0, 1.0]), np.array([0.9, 0.9]))
+    tol = 1e-12
+    assert f["a"][0, 0] == pytest.approx(g["a1x"], rel=tol)
+    assert f["a"][1, 0] == pytest.approx(g["a2x"], rel=tol)
+    assert np.all(f["a"][:, 1:] == 0.0)
+    for k, idx in (("dudt_h", 0), ("dudt_av", 0), ("divv", 0), ("dt", 0)):
+        for i in (0, 1):
+            assert f[k][i] == pytest.approx(g["%s%d" % (k, i + 1)], rel=tol), (k, i)
+
+
+def test_three_particle_totals_match_hand_values():
+    g = _golden("three_particle_totals.txt")
+    x = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]])
+    v = np.array([[0, 2.0, 0], [0, 0, 3.0], [4.0, 0, 0]])
+    t = oracle.conserved(x, v, np.array([1.0, 2.0, 0.5]), np.array([1.0, 2.0, 3.0]))
+    want = [g[k] for k in ("M", "Px", "Py", "Pz", "Lx", "Ly", "Lz", "Ekin", "Eint")]
+    assert np.allclose(t, want, rtol=0, atol=1e-14), (t, want)

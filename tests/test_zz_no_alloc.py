@@ -25,6 +25,7 @@ def _reference(sph, prob, parts):
 def test_noalloc_totals_match_context_totals_twice():
     import torch
 
+    import oracle
     import paper_2511_11425_gb300 as sph
     from paper_2511_11425_gb300 import inputs
 
@@ -44,6 +45,15 @@ def test_noalloc_totals_match_context_totals_twice():
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), (got, ref)
+        # and against the FP64 oracle's totals of the same state (masses as
+        # the device holds them, in float32)
+        g = parts.numpy()
+        x = np.stack([g["x0"], g["x1"], g["x2"]], 1)
+        v = np.stack([g["v0"], g["v1"], g["v2"]], 1)
+        o = oracle.conserved(x, v, g["m"].astype(np.float64), g["u"])
+        scale = np.array([o[0]] + [np.max(np.abs(o[1:4])) + 1e-300] * 3 +
+                         [np.max(np.abs(o[4:7])) + 1e-300] * 3 + [o[7], o[8]])
+        assert np.all(np.abs(got - o) <= 1e-12 * np.maximum(scale, np.abs(o))), (got, o)
 
 
 def test_noalloc_rejects_too_many_particles():
