@@ -75,6 +75,11 @@ enum { SPH_ENERGY_PDV = 0, SPH_ENERGY_ISENTROPIC = 1 };
  * along a curve so that cells are contiguous; both curves visit the octree
  * cells depth first, the Hilbert curve without jumps between cells) */
 enum { SPH_CURVE_HILBERT = 0, SPH_CURVE_MORTON = 1 };
+/* arithmetic of the pair sums: the mixed-precision form (FP32 pairs on
+ * positions relative to their bucket, FP64 positions and integration) or
+ * FP64 throughout the pair sums (the per-particle arrays of sph_particles
+ * keep their types in both) */
+enum { SPH_PRECISION_MIXED = 0, SPH_PRECISION_FP64 = 1 };
 
 typedef struct {
     int32_t kernel;        /* SPH_KERNEL_*                                       */
@@ -101,7 +106,11 @@ typedef struct {
                               resort_period steps and only refit the buckets'
                               bounds to the moved particles in between (1..64;
                               0 = 1); taken from the first instance of a batch  */
-    int32_t reserved_;     /* must be 0                                          */
+    int32_t precision;     /* SPH_PRECISION_MIXED (0, default): FP32 pair
+                              arithmetic on cell-relative offsets with compensated
+                              sums; SPH_PRECISION_FP64: every pair sum, the h
+                              iteration and the force accumulators in FP64 (the
+                              plain form); must agree across a batch            */
 } sph_params;
 
 typedef struct {
@@ -454,6 +463,20 @@ sph_status sph_mlp_infer(sph_ctx *ctx, const float *x, int64_t n, float *y, void
  * (first needs nslots + 1 entries, SPH_ERR_ARG otherwise).  Synchronous.
  * The paper has no counterpart (it is a view of the data layout). */
 sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t cap, int64_t *nslots);
+
+/* sph_set_list_arena: size of the shared overflow arena that holds the
+ * interaction lists of walk groups whose lists outgrow their 1024 fixed slots
+ * (a group whose h spans most of its problem: a very heavy particle, one
+ * leaving a free surface).  The default is max(2^23, 16 x groups) entries of
+ * 4 bytes.  A walk that finds the arena full fails the call with
+ * SPH_ERR_CAPACITY (a failed step leaves x, v, u as they were); a larger arena
+ * lets such problems run, a smaller one caps the memory.  Shrinking only
+ * lowers the limit; growing past the allocated size reallocates the list
+ * buffer (synchronous) and drops a step recorded by sph_graph_capture or
+ * sph_step_host_capture (record it again).  SPH_ERR_ARG for entries < 0,
+ * SPH_ERR_CAPACITY if the lists would pass 2^32 entries.  The paper has no
+ * counterpart (it is a memory-budget setting of this library). */
+sph_status sph_set_list_arena(sph_ctx *ctx, int64_t entries);
 
 /* sph_set_dt_old: set the previous step size used by the predictor and the
  * closing kick (0 restarts the integration as at t = 0). */

@@ -26,13 +26,14 @@ STATUS = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_CAPACITY
 KERNELS = {"wc2": 0, "wc4": 1, "wc6": 2, "m4": 3}
 ENERGY = {"pdv": 0, "isentropic": 1}
 CURVES = {"hilbert": 0, "morton": 1}
+PRECISIONS = {"mixed": 0, "fp64": 1}
 EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph_density_at",
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
            "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
            "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
            "sph_graph_capture", "sph_graph_launch", "sph_graph_totals", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
-           "sph_mlp_load_samples", "sph_bucket_layout",
+           "sph_mlp_load_samples", "sph_bucket_layout", "sph_set_list_arena",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
 MLP_NPARAM = 1249
 SEED_MODES = {"analytic": 0, "mlp": 1}
@@ -53,7 +54,7 @@ class c_params(C.Structure):
                 ("h_rel_tol", C.c_double), ("list_margin", C.c_double),
                 ("curve", C.c_int32), ("group_log", C.c_int32),
                 ("bucket_cell", C.c_double), ("group_cell", C.c_double),
-                ("resort_period", C.c_int32), ("reserved_", C.c_int32)]
+                ("resort_period", C.c_int32), ("precision", C.c_int32)]
 
 
 class c_particles(C.Structure):
@@ -109,6 +110,7 @@ def lib():
         L.sph_graph_launch.argtypes = [vp, C.POINTER(dbl), vp]
         L.sph_graph_totals.argtypes = [vp, C.POINTER(dbl)]
         L.sph_set_dt_old.argtypes = [vp, dbl]
+        L.sph_set_list_arena.argtypes = [vp, i64]
         fp = C.POINTER(C.c_float)
         L.sph_mlp_set_weights.argtypes = [vp, fp, i64]
         L.sph_mlp_get_weights.argtypes = [vp, fp, i64]
@@ -169,6 +171,7 @@ class Params:
     bucket_cell: float = 3.0
     group_cell: float = 6.0
     resort_period: int = 1
+    precision: str = "mixed"
 
     def c(self) -> c_params:
         p = c_params()
@@ -181,6 +184,7 @@ class Params:
         p.curve = CURVES[self.curve]
         p.group_log = int(self.group_log)
         p.resort_period = int(self.resort_period)
+        p.precision = PRECISIONS[self.precision]
         for a in range(3):
             p.box_lo[a] = float(self.box_lo[a])
             p.box_hi[a] = float(self.box_hi[a])
@@ -520,6 +524,11 @@ def sph_bucket_layout(ctx):
     _check(ctx, lib().sph_bucket_layout(ctx, first.ctypes.data_as(C.POINTER(C.c_int32)),
                                         first.size, C.byref(ns)))
     return first
+
+
+def sph_set_list_arena(ctx, entries: int):
+    """Capacity of the interaction-list overflow arena (entries of 4 bytes)."""
+    _check(ctx, lib().sph_set_list_arena(ctx, int(entries)))
 
 
 def sph_set_dt_old(ctx, dt_old: float):

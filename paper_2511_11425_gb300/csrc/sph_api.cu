@@ -80,7 +80,8 @@ bool params_ok(const sph_params *prm)
         !(prm->bucket_cell == 0.0 || prm->bucket_cell >= 1.0) ||
         !(prm->group_cell == 0.0 || prm->group_cell >= 1.0))
         return false;
-    if (prm->resort_period < 0 || prm->resort_period > 64 || prm->reserved_ != 0) return false;
+    if (prm->resort_period < 0 || prm->resort_period > 64) return false;
+    if (prm->precision != SPH_PRECISION_MIXED && prm->precision != SPH_PRECISION_FP64) return false;
     const double kb = prm->bucket_cell > 0.0 ? prm->bucket_cell : kKappaBucket;
     const double kg = prm->group_cell > 0.0 ? prm->group_cell : kKappaGroup;
     if (!(kg >= kb) || !std::isfinite(kg)) return false;
@@ -124,6 +125,16 @@ Inst inst_params(const sph_params &prm)
     I.q = std::ldexp(1.0, (int)std::floor(std::log2(maxext)) - 20);
     I.inv_q = 1.0 / I.q;
     I.qf = (float)I.q;
+    // fixed-point positions of the force pairs (units qx = q 2^-kFixShift):
+    // bucket-relative coordinates and pair separations stay below 2^31 qx
+    // while bucket extents and h stay below fix_lim (checked per launch)
+    const double qx = std::ldexp(I.q, -kFixShift);
+    I.qx = (float)qx;
+    I.inv_qx = (float)(1.0 / qx);
+    I.qx2 = (float)(qx * qx);
+    I.fix_lim = (float)(0.99 * std::ldexp(qx, 31));
+    for (int a = 0; a < 3; ++a)
+        I.LQ[a] = I.periodic[a] ? (unsigned)std::llrint((prm.box_hi[a] - prm.box_lo[a]) / qx) : 0u;
     I.eps_abs = (float)(4.0 * std::ldexp(1.0, -23) * fmax(maxext, maxabs));
     return I;
 }
@@ -202,6 +213,8 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.list_off, ng);
     AL(c.arena_used, 1);
     c.arena_cap = std::max<int64_t>((int64_t)1 << 23, 16 * ng);
+    c.arena_alloc = c.arena_cap;
+    c.list_slots = ng * kWalkCap;
     if (rc == SPH_OK && ng * kWalkCap + c.arena_cap > (int64_t)0xffffffffLL)
         rc = failf(c, SPH_ERR_CAPACITY, "too many walk groups (%lld) for 32-bit list offsets",
                    (long long)ng);
@@ -213,8 +226,11 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.fpos, np);
     AL(c.fvel, np);
     AL(c.fth, np);
+    AL(c.ipos, np);
+    if (c.kp.fp64) AL(c.pmd, np);
     AL(c.acc, np);
-    AL(c.acc2, np);
+    AL(c.accS, np);
+    AL(c.mumax, np);
     AL(c.rho_old, np);
     AL(c.h_seed, np);
 #undef AL
@@ -253,8 +269,8 @@ void free_ctx(Ctx &c)
                     c.cons_out, c.pinst, c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist,
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
                     c.list_cnt, c.list_off, c.arena_used, c.list, c.redo, c.node, c.refit,
-                    c.pm, c.fpos, c.fvel, c.fth,
-                    c.acc, c.acc2, c.rho_old, c.h_seed, c.mirror};
+                    c.pm, c.pmd, c.ipos, c.fpos, c.fvel, c.fth,
+                    c.acc, c.accS, c.mumax, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mptrs[] = {c.mlp.w, c.mlp.m, c.mlp.v, c.mlp.frag, c.mlp.gpart, c.mlp.loss,
@@ -526,7 +542,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     for (int k = 1; k < ninst; ++k)
         if (prm[k].kernel != prm[0].kernel || prm[k].energy_mode != prm[0].energy_mode ||
             prm[k].max_newton != prm[0].max_newton || prm[k].h_rel_tol != prm[0].h_rel_tol ||
-            prm[k].list_margin != prm[0].list_margin)
+            prm[k].list_margin != prm[0].list_margin || prm[k].precision != prm[0].precision)
             return SPH_ERR_ARG;
     sph_ctx *ctx = new (std::nothrow) sph_ctx;
     if (!ctx) return SPH_ERR_ARG;
@@ -541,6 +557,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.kp.max_newton = prm[0].max_newton;
     c.kp.h_rel_tol = (float)prm[0].h_rel_tol;
     c.kp.margin = (float)prm[0].list_margin;
+    c.kp.fp64 = prm[0].precision == SPH_PRECISION_FP64 ? 1 : 0;
     c.resort_period = prm[0].resort_period > 0 ? prm[0].resort_period : 1;
     c.kp.ninst = ninst;
     const Sizes z = layout_sizes(counts, c.prm);
@@ -1474,6 +1491,37 @@ extern "C" sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t ca
         return failf(c, SPH_ERR_ARG, "sph_bucket_layout needs %d entries", c.kp.nb + 1);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(first, c.bstart, sizeof(int) * ((size_t)c.kp.nb + 1), cudaMemcpyDeviceToHost));
+    return SPH_OK;
+}
+
+extern "C" sph_status sph_set_list_arena(sph_ctx *ctx, int64_t entries)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (entries < 0) return failf(c, SPH_ERR_ARG, "arena entries must be >= 0");
+    if (c.list_slots + entries > (int64_t)0xffffffffLL)
+        return failf(c, SPH_ERR_CAPACITY, "arena of %lld entries exceeds 32-bit list offsets",
+                     (long long)entries);
+    if (entries > c.arena_alloc) {
+        // a larger buffer: lists are rebuilt by every walk, so nothing is
+        // copied, but recorded steps point at the old buffer and are dropped
+        CK(cudaDeviceSynchronize());
+        unsigned *nl = nullptr;
+        if (dalloc(&nl, (size_t)(c.list_slots + entries)) != cudaSuccess)
+            return failf(c, SPH_ERR_CUDA, "cudaMalloc of the interaction-list arena failed");
+        cudaFree(c.list);
+        c.list = nl;
+        c.arena_alloc = entries;
+        for (cudaGraphExec_t *ge : {&c.graph_exec, &c.graph_exec_r})
+            if (*ge) cudaGraphExecDestroy(*ge);
+        for (cudaGraph_t *gr : {&c.graph, &c.graph_r})
+            if (*gr) cudaGraphDestroy(*gr);
+        c.graph_exec = c.graph_exec_r = nullptr;
+        c.graph = c.graph_r = nullptr;
+        c.graph_replayed = false;
+        c.density_valid = c.forces_valid = false;
+    }
+    c.arena_cap = entries;
     return SPH_OK;
 }
 

@@ -561,8 +561,8 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
                                                  const double *__restrict__ z,
                                                  const float *__restrict__ m,
                                                  const float *__restrict__ h, int *origin,
-                                                 float4 *pm, float4 *node, int update_pos,
-                                                 DevStatus *st)
+                                                 float4 *pm, int4 *ipos, double4_16a *pmd,
+                                                 float4 *node, int update_pos, DevStatus *st)
 {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -619,12 +619,23 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
             origin[ax * kp.nb + b] = (int)kd;
             fo = fa - kd * I.q;
         }
+        int fix[3];
+        double rdd[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) rel[a] = (float)(__shfl_sync(kFull, fo, a) + d[a]);
+        for (int a = 0; a < 3; ++a) {
+            const double rd = __shfl_sync(kFull, fo, a) + d[a];
+            rdd[a] = rd;
+            rel[a] = (float)rd;
+            // fixed point in units of qx (saturates if the bucket is wider
+            // than the fixed-point range; the force kernel then does not use it)
+            fix[a] = __double2int_rn(rd * (double)I.inv_qx);
+        }
         if (ok) {
             if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
                 raise_status(st, ST_NONFINITE, i);
             pm[i] = make_float4(rel[0], rel[1], rel[2], m[i]);
+            ipos[i] = make_int4(fix[0], fix[1], fix[2], 0);
+            if (pmd) pmd[i] = make_double4_16a(rdd[0], rdd[1], rdd[2], (double)m[i]);
         }
     } else {
         float4 r = ok ? pm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1115,7 +1126,7 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     // buckets and trees
     const int wb = (kp.nb * 32 + 127) / 128;
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
-                                 c.origin, c.pm, c.node, 1, c.st);
+                                 c.origin, c.pm, c.ipos, c.pmd, c.node, 1, c.st);
     c.launches += 2 + 3 * kp.key_passes + 2 + 1;
     tree_refit(c, s, 0);
     return cudaGetLastError();
@@ -1127,7 +1138,7 @@ cudaError_t launch_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     const int wb = (kp.nb * 32 + 127) / 128;
     c.launches += 1;
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
-                                 c.origin, c.pm, c.node, 1, c.st);
+                                 c.origin, c.pm, c.ipos, c.pmd, c.node, 1, c.st);
     tree_refit(c, s, 0);
     return cudaGetLastError();
 }
@@ -1138,7 +1149,7 @@ cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     const int wb = (kp.nb * 32 + 127) / 128;
     c.launches += 1;
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
-                                 c.origin, c.pm, c.node, 0, c.st);
+                                 c.origin, c.pm, c.ipos, c.pmd, c.node, 0, c.st);
     tree_refit(c, s, 1);
     return cudaGetLastError();
 }

@@ -20,11 +20,12 @@
 // chunk entries against its own h (a 128-bit hit mask in registers) and
 // evaluates the kernel only on its hits, so the expensive arithmetic runs on
 // full warps.  Chunk partial sums are folded into Kahan-compensated totals.
+#include <type_traits>
+
 #include "sph_internal.cuh"
 
 namespace sph {
 
-constexpr float kFourPiThird = 4.18879020478639098f;
 
 template <bool WRAP>
 __device__ __forceinline__ float sep2(const PBox &bx, float px, float py, float pz, float4 q)
@@ -78,69 +79,119 @@ __device__ __forceinline__ int next_hit(unsigned long long &m0, unsigned long lo
     return k;
 }
 
-template <class K, bool WRAP, bool EMIT>
-__device__ __forceinline__ void density_chunk(const PBox &bx, float4 *cand, const int *candj,
-                                              int c, int lane, float px, float py, float pz,
-                                              float h2, float ih, bool active, Kahan &Sw,
-                                              Kahan &Sq, int &cnt, int i, long long cap,
-                                              int &emitted, int64_t *ids_out,
-                                              const int64_t *__restrict__ id_in)
+// the FP64 form's per-lane density sums of one pass
+struct DSums {
+    double w = 0.0, q = 0.0;
+};
+
+template <class K, bool WRAP, bool EMIT, bool D64>
+__device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, float4 *cand,
+                                              const double4_16a *candd, const int *candj, int c,
+                                              int lane, float px, float py, float pz, float h2,
+                                              float ih, const double *pd, double hd, double ihd,
+                                              bool active, Kahan &Sw, Kahan &Sq, DSums &D,
+                                              int &cnt, int i, long long cap, int &emitted,
+                                              int64_t *ids_out, const int64_t *__restrict__ id_in)
 {
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32)
         cand[k] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
     __syncwarp();
+    // FP64 form: h2 is the culling radius (inflated over the FP32 rounding
+    // of the staged positions); the support test on each hit is exact
     unsigned long long m0, m1;
     hit_masks<WRAP>(bx, cand, nwords, px, py, pz, h2, active, m0, m1);
-    float sw = 0.f, sq = 0.f;
     int nh = 0;
-    while (m0 | m1) {
-        const int k = next_hit(m0, m1);
-        const float4 q = cand[k];
-        const float r2 = sep2<WRAP>(bx, px, py, pz, q);
-        const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
-        const float qq = r * ih;
-        const float wv = K::w(qq), dq = K::dwq(qq);
-        sw = fmaf(q.w, wv, sw);
-        sq = fmaf(q.w * dq, qq * qq, sq);
-        ++nh;
-        if (EMIT) {
-            int j = candj[k];
-            if (j != i) {
-                if (emitted < cap) ids_out[(long long)i * cap + emitted] = id_in[j];
-                ++emitted;
+    if (!D64) {
+        float sw = 0.f, sq = 0.f;
+        while (m0 | m1) {
+            const int k = next_hit(m0, m1);
+            const float4 q = cand[k];
+            const float r2 = sep2<WRAP>(bx, px, py, pz, q);
+            const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
+            const float qq = r * ih;
+            const float wv = K::w(qq), dq = K::dwq(qq);
+            sw = fmaf(q.w, wv, sw);
+            sq = fmaf(q.w * dq, qq * qq, sq);
+            ++nh;
+            if (EMIT) {
+                int j = candj[k];
+                if (j != i) {
+                    if (emitted < cap) ids_out[(long long)i * cap + emitted] = id_in[j];
+                    ++emitted;
+                }
             }
         }
+        Sw.add(sw);
+        Sq.add(sq);
+    } else {
+        const double h2d = hd * hd;
+        double sw = 0.0, sq = 0.0;
+        while (m0 | m1) {
+            const int k = next_hit(m0, m1);
+            const double4_16a q = candd[k];
+            double d[3] = {pd[0] - q.x, pd[1] - q.y, pd[2] - q.z};
+            if (WRAP) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (bx.per[a]) d[a] -= I.Ld[a] * rint(d[a] * I.invLd[a]);
+            }
+            const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+            if (!(r2 < h2d)) continue;
+            const double qq = sqrt(r2) * ihd;
+            sw = fma(q.w, K::wd(qq), sw);
+            sq = fma(q.w * K::dwqd(qq), qq * qq, sq);
+            ++nh;
+            if (EMIT) {
+                int j = candj[k];
+                if (j != i) {
+                    if (emitted < cap) ids_out[(long long)i * cap + emitted] = id_in[j];
+                    ++emitted;
+                }
+            }
+        }
+        D.w += sw;
+        D.q += sq;
     }
-    Sw.add(sw);
-    Sq.add(sq);
     cnt += nh;
 }
 
-template <class K, bool WRAP, bool EMIT>
+// D64: the FP64 form (positions from pmd, sums, Newton iteration and the
+// outputs' arithmetic in FP64); otherwise FP32 pairs on cell-relative offsets
+template <class K, bool WRAP, bool EMIT, bool D64>
 __device__ __forceinline__ void density_bucket(
     const KParams &kp, const Inst &I, const PBox &bx, int A, int i0, int lane, float4 *cand,
-    int *candj, const float4 *__restrict__ pm, const int *__restrict__ bstart,
-    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list_off,
-    const unsigned *__restrict__ list,
+    double4_16a *candd, int *candj, const float4 *__restrict__ pm, const double4_16a *__restrict__ pmd,
+    const int *__restrict__ bstart, const unsigned *__restrict__ list_cnt,
+    const unsigned *__restrict__ list_off, const unsigned *__restrict__ list,
     const int *__restrict__ origin, const float4 *__restrict__ node, float *h_seed, float *h_out,
     float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
     long long cap, uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
     unsigned *redo_out, unsigned *redo_cnt_out, unsigned *gflag, DevStatus *st, float4 me,
     bool valid, const float *cen)
 {
+    using Real = typename std::conditional<D64, double, float>::type;
     const unsigned lt = (1u << lane) - 1u;
     const int i = i0 + lane;
-    const float n_ngb = I.n_ngb, eps_abs = I.eps_abs;
-    float h = valid ? h_seed[i] : 1.f;
-    const float R = h * (1.f + kp.margin);  // radius the list was gathered with
-    float lo = 0.f, hi = INFINITY;
+    const Real n_ngb = (Real)I.n_ngb;
+    const float eps_abs = I.eps_abs;
+    Real h = valid ? (Real)h_seed[i] : (Real)1;
+    const float R = (float)h * (1.f + kp.margin);  // radius the list was gathered with
+    Real lo = 0, hi = (Real)INFINITY;
     bool done = !valid, relist = false, conv = false;
     int iters = 0;
-    float out_h = h, out_rho = 0.f, out_om = 0.f;
+    Real out_h = h, out_rho = 0, out_om = 0;
     int out_n = 0, emitted = 0;
     unsigned long long pairs = 0, cands = 0;
     const float p[3] = {me.x, me.y, me.z};
+    double pd[3] = {0.0, 0.0, 0.0};
+    if (D64 && valid) {
+        const double4_16a q = pmd[i];
+        pd[0] = q.x;
+        pd[1] = q.y;
+        pd[2] = q.z;
+    }
+    const Real mi = D64 && valid ? (Real)pmd[i].w : (Real)me.w;
     // Filter the group's list against this bucket's coverage box of balls
     // (radius R): lane w keeps the acceptance bits of entries 32w .. 32w+31
     // of the first 1024.  Longer lists (overflow arena) get the bits of each
@@ -194,25 +245,30 @@ __device__ __forceinline__ void density_bucket(
 
     for (int pass = 0; pass <= kp.max_newton; ++pass) {
         if (__all_sync(kFull, done)) break;
-        const float h2 = h * h, ih = 1.f / h;
+        // culling radius: h itself, or in the FP64 form h inflated over the
+        // FP32 rounding of the staged positions (the support test is exact)
+        const float hf = D64 ? (float)h * (1.f + 1e-5f) + eps_abs : (float)h;
+        const float h2 = hf * hf, ih = 1.f / hf;
+        const double ihd = D64 ? 1.0 / (double)h : 0.0;
         // box of balls and ball of balls of the active lanes (Sec. 2.3.2: a
         // source must overlap both shapes)
         float bc[3], br[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float bl = warp_min(done ? INFINITY : p[a] - h);
-            float bh = warp_max(done ? -INFINITY : p[a] + h);
+            float bl = warp_min(done ? INFINITY : p[a] - hf);
+            float bh = warp_max(done ? -INFINITY : p[a] + hf);
             bc[a] = 0.5f * (bl + bh);
             br[a] = 0.5f * (bh - bl);
         }
         float bb2;
         {
             float dx = p[0] - bc[0], dy = p[1] - bc[1], dz = p[2] - bc[2];
-            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + h;
+            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + hf;
             rr = warp_max(rr) * (1.f + 1e-6f) + eps_abs;
             bb2 = rr * rr;
         }
         Kahan Sw, Sq;
+        DSums D;
         int cnt = 0, c = 0;
         for (unsigned w = 0; w < nwords; ++w) {
           unsigned mw;
@@ -233,13 +289,15 @@ __device__ __forceinline__ void density_bucket(
             const bool vj = lane < bucket_len(bstart, B);
             float4 s = vj ? pm[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             float sp[3] = {off.x + s.x, off.y + s.y, off.z + s.z};
+            float nw[3] = {0.f, 0.f, 0.f};  // periodic images moved by the wrap below
             bool in = vj;
             float dd2 = 0.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float d = sp[a] - bc[a];
                 if (WRAP && bx.per[a]) {
-                    sp[a] -= bx.L[a] * rintf((sp[a] - cen[a]) * bx.invL[a]);
+                    nw[a] = rintf((sp[a] - cen[a]) * bx.invL[a]);
+                    sp[a] -= bx.L[a] * nw[a];
                     d = wrapf(d, bx.L[a], bx.invL[a]);
                 }
                 in = in && fabsf(d) <= br[a];
@@ -251,13 +309,32 @@ __device__ __forceinline__ void density_bucket(
                 int pos = c + __popc(bal & lt);
                 cand[pos] = make_float4(sp[0], sp[1], sp[2], s.w);
                 if (EMIT) candj[pos] = j;
+                if (D64) {
+                    // the same source in FP64: its offset from its own bucket
+                    // origin plus the exact origin offset (the image the FP32
+                    // offset chose, then the wrap above)
+                    const double4_16a sd = pmd[j];
+                    double o[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int dk = origin[a * kp.nb + B] - origin[a * kp.nb + A];
+                        double f = (double)dk * I.q;
+                        if (bx.per[a]) {
+                            const float fi = (float)dk * I.qf;
+                            f -= I.Ld[a] * (double)rintf(fi * I.invL[a]);
+                        }
+                        o[a] = f - I.Ld[a] * (double)nw[a];
+                    }
+                    candd[pos] = make_double4_16a(o[0] + sd.x, o[1] + sd.y, o[2] + sd.z, sd.w);
+                }
             }
             c += __popc(bal);
             if (c > kChunk - 32) {
                 __syncwarp();
                 if (!done) cands += c;
-                density_chunk<K, WRAP, EMIT>(bx, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
-                                             !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
+                density_chunk<K, WRAP, EMIT, D64>(bx, I, cand, candd, candj, c, lane, p[0], p[1],
+                                                  p[2], h2, ih, pd, (double)h, ihd, !done, Sw, Sq,
+                                                  D, cnt, i, cap, emitted, ids_out, id_in);
                 __syncwarp();
                 c = 0;
             }
@@ -266,37 +343,40 @@ __device__ __forceinline__ void density_bucket(
         if (c > 0) {
             __syncwarp();
             if (!done) cands += c;
-            density_chunk<K, WRAP, EMIT>(bx, cand, candj, c, lane, p[0], p[1], p[2], h2, ih,
-                                         !done, Sw, Sq, cnt, i, cap, emitted, ids_out, id_in);
+            density_chunk<K, WRAP, EMIT, D64>(bx, I, cand, candd, candj, c, lane, p[0], p[1], p[2],
+                                              h2, ih, pd, (double)h, ihd, !done, Sw, Sq, D, cnt,
+                                              i, cap, emitted, ids_out, id_in);
             __syncwarp();
         }
         if (!done) {
             ++iters;
-            const float swv = Sw.s, sqv = Sq.s;
+            const Real swv = D64 ? (Real)D.w : (Real)Sw.s, sqv = D64 ? (Real)D.q : (Real)Sq.s;
+            const Real sigma = D64 ? (Real)K::sigmad : (Real)K::sigma;
+            const Real fpt = (Real)4.18879020478639098;  // 4 pi / 3
             const int nn = cnt - 1;  // the particle itself is always in its own list
             pairs += (unsigned long long)(nn > 0 ? nn : 0);
             bool record = fixed_h != 0;
-            float h_final = h;
+            Real h_final = h;
             if (!record) {
-                float g = kFourPiThird * K::sigma * swv / me.w - n_ngb;
-                float dg = -kFourPiThird * K::sigma * sqv / (me.w * h);
-                if (g < 0.f) lo = h; else hi = h;
-                float hn = dg > 0.f ? h - g / dg : NAN;
-                if (isfinite(hn) && fabsf(hn - h) < kp.h_rel_tol * h) {
+                Real g = fpt * sigma * swv / mi - n_ngb;
+                Real dg = -fpt * sigma * sqv / (mi * h);
+                if (g < 0) lo = h; else hi = h;
+                Real hn = dg > 0 ? h - g / dg : (Real)NAN;
+                if (isfinite(hn) && fabs(hn - h) < (Real)kp.h_rel_tol * h) {
                     // converged: report the Newton update of the last
                     // evaluation (quadratically closer to the root; rho,
                     // Omega and n_i stay those of the evaluated h)
                     record = true;
                     h_final = hn;
                 } else {
-                    if (!(hn > lo && hn < hi)) hn = isfinite(hi) ? 0.5f * (lo + hi) : 2.f * h;
-                    if (hn > R) {
-                        if (h >= R) {  // g(R) < 0: the root lies beyond the list's coverage
+                    if (!(hn > lo && hn < hi)) hn = isfinite(hi) ? (Real)0.5 * (lo + hi) : 2 * h;
+                    if (hn > (Real)R) {
+                        if (h >= (Real)R) {  // g(R) < 0: the root lies beyond the list's coverage
                             relist = true;
                             done = true;
                             out_h = hn;
                         } else {
-                            hn = R;
+                            hn = (Real)R;
                         }
                     }
                     if (!done) {
@@ -313,19 +393,23 @@ __device__ __forceinline__ void density_bucket(
                 done = true;
                 conv = true;
                 out_h = h_final;
-                out_rho = K::sigma * swv * ih * ih * ih;
-                out_om = -sqv / (3.f * swv);
+                const Real ihr = (Real)1 / h;
+                out_rho = sigma * swv * ihr * ihr * ihr;
+                out_om = -sqv / (3 * swv);
+                if (!D64) {  // the FP32 form keeps its arithmetic as FP32 ops
+                    out_rho = (Real)(K::sigma * (float)swv * ih * ih * ih);
+                }
                 out_n = nn;
-                if (!(isfinite(out_rho) && isfinite(out_om) && out_rho > 0.f))
+                if (!(isfinite(out_rho) && isfinite(out_om) && out_rho > 0))
                     raise_status(st, ST_NONFINITE, i);
-                if (h >= I.hcap) raise_status(st, ST_ARG, i);
+                if ((float)h >= I.hcap) raise_status(st, ST_ARG, i);
             }
         }
     }
     if (valid && !done) raise_status(st, ST_NOCONV, i);
     bool any_relist = __any_sync(kFull, relist);
     if (any_relist) {
-        if (valid) h_seed[i] = relist ? out_h : (conv ? out_h : h);
+        if (valid) h_seed[i] = (float)(relist ? out_h : (conv ? out_h : h));
         if (lane == 0 && atomicOr(&gflag[g], 1u) == 0u) {
             if (redo_out) {
                 unsigned pos = atomicAdd(redo_cnt_out, 1u);
@@ -335,9 +419,9 @@ __device__ __forceinline__ void density_bucket(
             }
         }
     } else if (valid && conv) {
-        h_out[i] = out_h;
-        rho_out[i] = out_rho;
-        omega_out[i] = out_om;
+        h_out[i] = (float)out_h;
+        rho_out[i] = (float)out_rho;
+        omega_out[i] = (float)out_om;
         nngb_out[i] = (uint16_t)min(out_n, 65535);
         iters_out[i] = (uint8_t)min(iters, 255);
         if (EMIT && count_out) count_out[i] = (uint32_t)out_n;
@@ -352,17 +436,18 @@ __device__ __forceinline__ void density_bucket(
 }
 
 // one sink bucket A (one warp)
-template <class K, bool EMIT>
+template <class K, bool EMIT, bool D64>
 __device__ __forceinline__ void density_slot(
     const KParams &kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
-    const int *__restrict__ bstart, const int *__restrict__ binst,
-    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list_off,
-    const unsigned *__restrict__ list,
+    const double4_16a *__restrict__ pmd, const int *__restrict__ bstart,
+    const int *__restrict__ binst, const unsigned *__restrict__ list_cnt,
+    const unsigned *__restrict__ list_off, const unsigned *__restrict__ list,
     const int *__restrict__ origin, float *h_seed, float *h_out, float *rho_out,
     float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap,
     uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
     unsigned *redo_out, unsigned *redo_cnt_out, unsigned *gflag,
-    const float4 *__restrict__ node, DevStatus *st, float4 *cand, int *candj, int A, int lane)
+    const float4 *__restrict__ node, DevStatus *st, float4 *cand, double4_16a *candd, int *candj,
+    int A, int lane)
 {
     const Inst &I = insts[binst[A]];
     const PBox bx = make_pbox(I);
@@ -388,25 +473,27 @@ __device__ __forceinline__ void density_slot(
         }
     }
     if (wrap)
-        density_bucket<K, true, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
-                                      list_off, list, origin, node, h_seed, h_out, rho_out, omega_out,
-                                      nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
-                                      redo_out, redo_cnt_out, gflag, st, me, valid, cen);
+        density_bucket<K, true, EMIT, D64>(kp, I, bx, A, i0, lane, cand, candd, candj, pm, pmd,
+                                           bstart, list_cnt, list_off, list, origin, node, h_seed,
+                                           h_out, rho_out, omega_out, nngb_out, iters_out, fixed_h,
+                                           cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
+                                           gflag, st, me, valid, cen);
     else
-        density_bucket<K, false, EMIT>(kp, I, bx, A, i0, lane, cand, candj, pm, bstart, list_cnt,
-                                       list_off, list, origin, node, h_seed, h_out, rho_out, omega_out,
-                                       nngb_out, iters_out, fixed_h, cap, count_out, ids_out, id_in,
-                                       redo_out, redo_cnt_out, gflag, st, me, valid, cen);
+        density_bucket<K, false, EMIT, D64>(kp, I, bx, A, i0, lane, cand, candd, candj, pm, pmd,
+                                            bstart, list_cnt, list_off, list, origin, node, h_seed,
+                                            h_out, rho_out, omega_out, nngb_out, iters_out,
+                                            fixed_h, cap, count_out, ids_out, id_in, redo_out,
+                                            redo_cnt_out, gflag, st, me, valid, cen);
 }
 
-template <class K, bool EMIT>
+template <class K, bool EMIT, bool D64>
 // 5 blocks of 4 warps per SM: the register cap (96) measured faster than
 // the compiler's own choice (about 128 registers, 4 blocks)
 __global__ void __launch_bounds__(128, 5) k_density(
     KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
-    const int *__restrict__ bstart, const int *__restrict__ binst,
-    const int *__restrict__ gfirst, const unsigned *__restrict__ list_cnt,
-    const unsigned *__restrict__ list_off,
+    const double4_16a *__restrict__ pmd, const int *__restrict__ bstart,
+    const int *__restrict__ binst, const int *__restrict__ gfirst,
+    const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list_off,
     const unsigned *__restrict__ list, const int *__restrict__ origin,
     const unsigned *__restrict__ group_ids, const unsigned *__restrict__ group_cnt,
     float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
@@ -415,15 +502,18 @@ __global__ void __launch_bounds__(128, 5) k_density(
     unsigned *gflag, const float4 *__restrict__ node, DevStatus *st)
 {
     __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
+    __shared__ double4_16a candd_s[D64 ? kWarpsPerBlock : 1][D64 ? kChunk : 1];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double4_16a *candd = D64 ? candd_s[wib] : nullptr;
     if (!group_ids) {  // every bucket, one warp each
         const int A = blockIdx.x * kWarpsPerBlock + wib;
         if (A < kp.nb)
-            density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list_off, list, origin, h_seed,
-                                  h_out, rho_out, omega_out, nngb_out, iters_out, fixed_h, cap,
-                                  count_out, ids_out, id_in, redo_out, redo_cnt_out, gflag, node,
-                                  st, cand_s[wib], EMIT ? candj_s[wib] : nullptr, A, lane);
+            density_slot<K, EMIT, D64>(kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
+                                       origin, h_seed, h_out, rho_out, omega_out, nngb_out,
+                                       iters_out, fixed_h, cap, count_out, ids_out, id_in,
+                                       redo_out, redo_cnt_out, gflag, node, st, cand_s[wib],
+                                       candd, EMIT ? candj_s[wib] : nullptr, A, lane);
         return;
     }
     // the buckets of the groups queued for this re-walk round (8 warp slots
@@ -435,10 +525,11 @@ __global__ void __launch_bounds__(128, 5) k_density(
         const Inst &Ig = insts[binst[fb]];
         const int j = bi & ((1 << kGroupLog) - 1);
         if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) continue;
-        density_slot<K, EMIT>(kp, insts, pm, bstart, binst, list_cnt, list_off, list, origin, h_seed, h_out,
-                              rho_out, omega_out, nngb_out, iters_out, fixed_h, cap, count_out,
-                              ids_out, id_in, redo_out, redo_cnt_out, gflag, node, st,
-                              cand_s[wib], EMIT ? candj_s[wib] : nullptr, fb + j, lane);
+        density_slot<K, EMIT, D64>(kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
+                                   origin, h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
+                                   fixed_h, cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
+                                   gflag, node, st, cand_s[wib], candd,
+                                   EMIT ? candj_s[wib] : nullptr, fb + j, lane);
     }
 }
 
@@ -475,18 +566,21 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     unsigned *redo_cnt_out = next < kRelistRounds ? &c.st->redo_cnt[next] : nullptr;
     cudaMemsetAsync(c.gflag, 0, sizeof(unsigned) * (size_t)kp.ng, s);
     c.launches += 1;
+#define SPH_DENSITY_LAUNCH(EMIT_, D64_)                                                      \
+    k_density<KT, EMIT_, D64_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                                 \
+        kp, c.inst, c.pm, c.pmd, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list,     \
+        c.origin, gids, gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,     \
+        (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st)
     SPH_KERNEL_DISPATCH(kp.kernel, KT,
-        if (emit)
-            k_density<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list, c.origin, gids,
-                gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,
-                (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st);
-        else
-            k_density<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                kp, c.inst, c.pm, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list, c.origin, gids,
-                gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,
-                (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st);
+        if (kp.fp64) {
+            if (emit) SPH_DENSITY_LAUNCH(true, true);
+            else SPH_DENSITY_LAUNCH(false, true);
+        } else {
+            if (emit) SPH_DENSITY_LAUNCH(true, false);
+            else SPH_DENSITY_LAUNCH(false, false);
+        }
     )
+#undef SPH_DENSITY_LAUNCH
     return cudaGetLastError();
 }
 

@@ -20,11 +20,25 @@
 // (Sec. 2.3.2); source particles are culled per particle, compacted into a
 // 128-entry shared-memory chunk, and each lane evaluates only its own hits
 // (128-bit mask).  Contributions to the sink stay in registers; the equal
-// and opposite contribution to the source goes straight to L2 as one vector
-// reduction (red.global.add.v4.f32, fire-and-forget: the SM does not wait),
-// which measured 37 % faster than accumulating in shared memory with float
-// atomics and flushing per chunk.  j > i is required inside bucket A, so every
-// pair is computed exactly once.
+// and opposite contribution to the source goes straight to L2 as
+// fire-and-forget reductions (the SM does not wait): a xyz and du/dt|Pi as one
+// red.global.add.v4.f32, S as one red.global.add.f64 (which measured as fast
+// as keeping S in the FP32 vector: the reductions are not the bottleneck).
+// j > i is required inside bucket A, so every pair is computed exactly once.
+//
+// Precision.  Pair arithmetic is FP32 on positions relative to the sink
+// bucket's origin.  S_i is a sum whose terms cancel (across a shear layer
+// v_ij.r_ij changes sign with the geometry and the sum is a small fraction of
+// the terms' magnitudes), so its terms are computed without the two roundings
+// that dominate there: the separations are exact integer differences of
+// fixed-point positions (units qx = q 2^-11 relative to the bucket origins),
+// converted to FP32 once, and the kernel factor 1 - q comes from the exact
+// integer N = h^2 - r^2 as (N qx^2 / h^2) / (1 + q) instead of from a rounded
+// q = r/h.  S is accumulated with a Kahan sum per term on the sink side and
+// in FP64 on the source side (the accelerations per 128-candidate chunk,
+// chunks Kahan-summed).  Instances whose buckets or h outgrow the
+// fixed-point range (tiny open boxes), and sink buckets whose pairs need a
+// periodic wrap of their own, use FP32 separations and q throughout.
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -41,13 +55,15 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
                           const float *__restrict__ h, const float *__restrict__ rho,
                           const float *__restrict__ omega, const float4 *__restrict__ pm,
                           const double *__restrict__ dts, float4 *fpos, float4 *fvel, float4 *fth,
-                          float4 *acc, float2 *acc2, unsigned *dtmin, DevStatus *st)
+                          int4 *ipos, float4 *acc, double *accS, unsigned *mumax, unsigned *dtmin,
+                          DevStatus *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kp.ninst) dtmin[i] = 0x7f800000u;  // +inf
     if (i >= n) return;
     const int k = pinst[i];
-    const float gamma = insts[k].gamma;
+    const Inst &I = insts[k];
+    const float gamma = I.gamma;
     const double hdt = 0.5 * dts[2 * k];
     double v[3] = {vx[i], vy[i], vz[i]};
     double uu = u[i];
@@ -68,17 +84,26 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
     fpos[i] = make_float4(q.x, q.y, q.z, hi);
     fvel[i] = make_float4((float)v[0], (float)v[1], (float)v[2], q.w);
     fth[i] = make_float4(A, c, r, om);
+    // h in fixed-point units (h < fix_lim whenever the force kernel uses it)
+    reinterpret_cast<int *>(ipos + i)[3] = __float2int_rn(fminf(hi, I.fix_lim) * I.inv_qx);
     acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    acc2[i] = make_float2(0.f, 0.f);
+    accS[i] = 0.0;
+    mumax[i] = 0u;
 }
 
 // ---------------------------------------------------------------------------
 // pair-symmetric force kernel
 // ---------------------------------------------------------------------------
+#ifndef SPH_FORCE_BLOCKS_PER_SM
+#define SPH_FORCE_BLOCKS_PER_SM 5
+#endif
+constexpr int kForceBlocksPerSM = SPH_FORCE_BLOCKS_PER_SM;
+
 struct SinkState {
     float px, py, pz, h, h2, ih, ih5;  // position, smoothing length, sigma h^-5
     float vx, vy, vz, m;
     float A, c, rho;
+    int ix, iy, iz, hq;                // fixed-point position and h (units qx)
     Kahan ax, ay, az, S;
     float du, mumax;
     int i;
@@ -90,6 +115,7 @@ struct ForceStage {
     float4 pos[kChunk];  // position in the sink frame, h^2
     float4 vel[kChunk];  // predicted velocity, m
     float4 th[kChunk];   // A = P/(Omega rho^2), c, rho, h
+    int4 ipos[kChunk];   // fixed-point position in the sink frame, h (units qx)
     float ih[kChunk];    // 1/h, correctly rounded (once per staged source)
     int idx[kChunk];
 };
@@ -108,18 +134,18 @@ __device__ __forceinline__ void sep3(const PBox &bx, float px, float py, float p
     }
 }
 
-// viscosity parameters of the sink's instance
+// viscosity parameters and fixed-point quantum of the sink's instance
 struct Visc {
-    float alpha, beta, eps_av;
+    float alpha, beta, eps_av, qx, qx2;
 };
 
 // SELF: the chunk holds the sink bucket's own particles, where only j > i
 // counts (every other source bucket lies after the sink bucket, so all its
-// particles do)
-template <class K, bool WRAP, bool SELF>
+// particles do).  FIX: separations and 1 - q from the fixed-point positions.
+template <class K, bool WRAP, bool SELF, bool FIX>
 __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, ForceStage &S, int c,
                                             SinkState &s, bool valid, int lane, float4 *acc,
-                                            float2 *acc2)
+                                            double *accS, unsigned *mumax)
 {
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32) {
@@ -149,27 +175,50 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
     }
     unsigned long long m0 = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
     unsigned long long m1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
-    float sax = 0.f, say = 0.f, saz = 0.f, sS = 0.f;
+    float sax = 0.f, say = 0.f, saz = 0.f;
     // one pair (i, candidate k): every term, no side effects
     struct PairTerms {
-        float dx, dy, dz, cm, mvr, Fi, mj, du, mneg, cs, Sj, du_j;
+        float dx, dy, dz, cm, Si, mj, du, mneg, cs, Sj, du_j;
         int jj;
         bool app;
     };
     auto pair_terms = [&](int k) -> PairTerms {
         PairTerms o;
-        const float4 q = S.pos[k];
         const float4 vj = S.vel[k];
         const float4 tj = S.th[k];
-        float dx, dy, dz;
-        sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
         const float hj = tj.w, ihj = S.ih[k];
         const float ihj2 = ihj * ihj;
-        const float qi = r * s.ih, qj = r * ihj;
-        const float Fi = qi < 1.f ? s.ih5 * K::dwq(qi) : 0.f;
-        const float Fj = qj < 1.f ? K::sigma * ihj2 * ihj2 * ihj * K::dwq(qj) : 0.f;
+        float dx, dy, dz, Fi, Fj, r2;
+        if (FIX) {
+            // exact integer separation and N = h^2 - r^2 (units qx), each
+            // converted to FP32 with one rounding
+            const int4 p = S.ipos[k];
+            const int ex = (int)((unsigned)s.ix - (unsigned)p.x);
+            const int ey = (int)((unsigned)s.iy - (unsigned)p.y);
+            const int ez = (int)((unsigned)s.iz - (unsigned)p.z);
+            const long long r2q = (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
+            const long long ni = (long long)s.hq * s.hq - r2q;
+            const long long nj = (long long)p.w * p.w - r2q;
+            dx = (float)ex * vp.qx;
+            dy = (float)ey * vp.qx;
+            dz = (float)ez * vp.qx;
+            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
+            const float qi = r * s.ih, qj = r * ihj;
+            // 1 - q = (1 - q^2) / (1 + q) with 1 - q^2 = N qx^2 / h^2
+            const float ti = __fdividef((float)ni * (vp.qx2 * s.ih * s.ih), 1.f + qi);
+            const float tj_ = __fdividef((float)nj * (vp.qx2 * ihj2), 1.f + qj);
+            Fi = ni > 0 ? s.ih5 * K::dwqt(qi, ti) : 0.f;
+            Fj = nj > 0 ? K::sigma * ihj2 * ihj2 * ihj * K::dwqt(qj, tj_) : 0.f;
+        } else {
+            const float4 q = S.pos[k];
+            sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
+            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
+            const float qi = r * s.ih, qj = r * ihj;
+            Fi = qi < 1.f ? s.ih5 * K::dwq(qi) : 0.f;
+            Fj = qj < 1.f ? K::sigma * ihj2 * ihj2 * ihj * K::dwq(qj) : 0.f;
+        }
         const float wx = s.vx - vj.x, wy = s.vy - vj.y, wz = s.vz - vj.z;
         const float vr = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
         // viscosity, evaluated for every pair and switched by v_ij.r_ij < 0
@@ -185,8 +234,7 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         o.dy = dy;
         o.dz = dz;
         o.cm = coef * vj.w;
-        o.mvr = vj.w * vr;
-        o.Fi = Fi;
+        o.Si = vj.w * vr * Fi;
         o.mj = vj.w;
         o.du = du;
         o.cs = coef * s.m;
@@ -196,18 +244,18 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         return o;
     };
     // sink side in registers; source side straight into global memory
-    // (L2 vector reductions)
+    // (L2 reductions)
     auto apply = [&](const PairTerms &o) {
         sax = fmaf(-o.cm, o.dx, sax);
         say = fmaf(-o.cm, o.dy, say);
         saz = fmaf(-o.cm, o.dz, saz);
-        sS = fmaf(o.mvr, o.Fi, sS);
+        s.S.add(o.Si);
         s.du = fmaf(o.mj, o.du, s.du);
         s.mumax = fmaxf(s.mumax, o.mneg);
-        red_add_v4(&acc[o.jj], o.cs * o.dx, o.cs * o.dy, o.cs * o.dz, o.Sj);
+        red_add_v4(&acc[o.jj], o.cs * o.dx, o.cs * o.dy, o.cs * o.dz, o.du_j);
+        red_add_f64(&accS[o.jj], (double)o.Sj);
         if (o.app) {
-            red_add_f32(&acc2[o.jj].x, o.du_j);
-            atomicMax((int *)&acc2[o.jj].y, __float_as_int(o.mneg));
+            atomicMax(&mumax[o.jj], __float_as_uint(o.mneg));
             ++s.av;
         }
         ++s.pairs;
@@ -227,7 +275,6 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
     s.ax.add(sax);
     s.ay.add(say);
     s.az.add(saz);
-    s.S.add(sS);
     __syncwarp();
 }
 
@@ -236,7 +283,7 @@ struct SinkBounds {
     float gR2;
 };
 
-template <class K, bool WRAP>
+template <class K, bool WRAP, bool FIX>
 __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, const PBox &bx,
                                              const Visc &vp, int A, int lane, ForceStage &S,
                                              SinkState &s, bool valid, const SinkBounds sb,
@@ -244,12 +291,14 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
                                              const float4 *__restrict__ fpos,
                                              const float4 *__restrict__ fvel,
                                              const float4 *__restrict__ fth,
+                                             const int4 *__restrict__ ipos,
                                              const unsigned *__restrict__ list_cnt,
                                              const unsigned *__restrict__ list_off,
                                              const unsigned *__restrict__ list,
                                              const int *__restrict__ origin,
                                              const float4 *__restrict__ node, float4 *acc,
-                                             float2 *acc2, unsigned long long &cands)
+                                             double *accS, unsigned *mumax,
+                                             unsigned long long &cands)
 {
     const unsigned lt = (1u << lane) - 1u;
     // Filter the group's list for this bucket (Sec. 2.3.2 tests with the
@@ -294,7 +343,26 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     }
     // stage the culled particles of source bucket B after the c staged ones
     auto stage = [&](int B, int c) -> int {
-        const float3 off = origin_offset(I, kp.nb, origin, A, B);
+        // origin offset o_B - o_A in the sink frame (nearest periodic image),
+        // as FP32 and, for the fixed-point path, in units of qx modulo 2^32
+        float3 off;
+        unsigned o3[3];
+        {
+            float d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int dk = origin[a * kp.nb + B] - origin[a * kp.nb + A];
+                float f = (float)dk * I.qf;
+                int nimg = 0;
+                if (bx.per[a]) {
+                    nimg = (int)rintf(f * bx.invL[a]);
+                    f -= bx.L[a] * (float)nimg;
+                }
+                d[a] = f;
+                o3[a] = ((unsigned)dk << kFixShift) - (unsigned)nimg * I.LQ[a];
+            }
+            off = make_float3(d[0], d[1], d[2]);
+        }
         const int j0 = bstart[B];
         const int j = j0 + lane;
         const bool vj = lane < bucket_len(bstart, B);
@@ -328,6 +396,13 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
             S.th[pos] = make_float4(t.x, t.y, t.z, q.w);
             S.ih[pos] = __frcp_rn(q.w);
             S.idx[pos] = j;
+            if (FIX) {
+                // the source in the sink frame: its fixed-point position plus
+                // the origin offset, modulo 2^32
+                const int4 p = ipos[j];
+                S.ipos[pos] = make_int4((int)((unsigned)p.x + o3[0]), (int)((unsigned)p.y + o3[1]),
+                                        (int)((unsigned)p.z + o3[2]), p.w);
+            }
         }
         c += __popc(bal);
         return c;
@@ -337,7 +412,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP, true>(bx, vp, S, c, s, valid, lane, acc, acc2);
+        force_chunk<K, WRAP, true, FIX>(bx, vp, S, c, s, valid, lane, acc, accS, mumax);
         c = 0;
     }
     const unsigned nwords = (nl + 31) / 32;
@@ -354,7 +429,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
-            force_chunk<K, WRAP, false>(bx, vp, S, c, s, valid, lane, acc, acc2);
+            force_chunk<K, WRAP, false, FIX>(bx, vp, S, c, s, valid, lane, acc, accS, mumax);
             c = 0;
         }
       }
@@ -362,25 +437,27 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP, false>(bx, vp, S, c, s, valid, lane, acc, acc2);
+        force_chunk<K, WRAP, false, FIX>(bx, vp, S, c, s, valid, lane, acc, accS, mumax);
     }
 }
 
-// 5 blocks of 4 warps per SM (96 registers, no spills): measured faster than
-// the compiler's own choice (about 124 registers, 4 blocks)
+// 5 blocks of 4 warps per SM (96 registers; the fixed-point pair path spills
+// a few values): measured faster than 4 blocks with the 124 registers the
+// compiler picks without the cap
 template <class K>
-__global__ void __launch_bounds__(128, 5) k_forces(KParams kp, const Inst *__restrict__ insts,
+__global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, const Inst *__restrict__ insts,
                                                 const int *__restrict__ bstart,
                                                 const int *__restrict__ binst,
                                                 const float4 *__restrict__ fpos,
                                                 const float4 *__restrict__ fvel,
                                                 const float4 *__restrict__ fth,
+                                                const int4 *__restrict__ ipos,
                                                 const unsigned *__restrict__ list_cnt,
                                                 const unsigned *__restrict__ list_off,
                                                 const unsigned *__restrict__ list,
                                                 const int *__restrict__ origin,
                                                 const float4 *__restrict__ node, float4 *acc,
-                                                float2 *acc2, DevStatus *st)
+                                                double *accS, unsigned *mumax, DevStatus *st)
 {
     __shared__ ForceStage stage[kWarpsPerBlock];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -388,7 +465,7 @@ __global__ void __launch_bounds__(128, 5) k_forces(KParams kp, const Inst *__res
     if (A >= kp.nb) return;
     const Inst &I = insts[binst[A]];
     const PBox bx = make_pbox(I);
-    const Visc vp = {I.alpha, I.beta, I.eps_av};
+    const Visc vp = {I.alpha, I.beta, I.eps_av, I.qx, I.qx2};
     const int i0 = bstart[A];
     const int i = i0 + lane;
     const int cnt = bucket_len(bstart, A);
@@ -399,6 +476,7 @@ __global__ void __launch_bounds__(128, 5) k_forces(KParams kp, const Inst *__res
         float4 q = valid ? fpos[i] : make_float4(0.f, 0.f, 0.f, 1.f);
         float4 v = valid ? fvel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 t = valid ? fth[i] : make_float4(0.f, 0.f, 1.f, 1.f);
+        int4 p = valid ? ipos[i] : make_int4(0, 0, 0, 0);
         s.px = q.x; s.py = q.y; s.pz = q.z; s.h = q.w;
         s.h2 = q.w * q.w;
         s.ih = 1.f / q.w;
@@ -406,6 +484,8 @@ __global__ void __launch_bounds__(128, 5) k_forces(KParams kp, const Inst *__res
         s.ih5 = K::sigma * ih2 * ih2 * s.ih;
         s.vx = v.x; s.vy = v.y; s.vz = v.z; s.m = v.w;
         s.A = t.x; s.c = t.y; s.rho = t.z;
+        s.ix = p.x; s.iy = p.y; s.iz = p.z;
+        s.hq = p.w;
         s.du = 0.f;
         s.mumax = 0.f;
         s.i = valid ? i : 0x7fffffff;
@@ -440,19 +520,27 @@ __global__ void __launch_bounds__(128, 5) k_forces(KParams kp, const Inst *__res
         rr = warp_max(rr) * (1.f + 1e-6f) + I.eps_abs;
         sb.gR2 = rr * rr;
     }
+    // fixed point while every bucket-relative coordinate and every pair
+    // separation fits 2^31 qx (largest bucket extent and largest h below the
+    // limit) and no pair needs its own periodic wrap
+    const bool fix = !wrap && Emax < I.fix_lim && Hmax < I.fix_lim;
     unsigned long long cands = 0;
-    if (wrap)
-        force_bucket<K, true>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
-                              fpos, fvel, fth, list_cnt, list_off, list, origin, node, acc,
-                              acc2, cands);
+    if (fix)
+        force_bucket<K, false, true>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+                                     fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
+                                     node, acc, accS, mumax, cands);
+    else if (wrap)
+        force_bucket<K, true, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+                                     fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
+                                     node, acc, accS, mumax, cands);
     else
-        force_bucket<K, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
-                              fpos, fvel, fth, list_cnt, list_off, list, origin, node, acc,
-                              acc2, cands);
+        force_bucket<K, false, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+                                      fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
+                                      node, acc, accS, mumax, cands);
     if (valid) {
-        red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.S.s);
-        if (s.du != 0.f) red_add_f32(&acc2[i].x, s.du);
-        if (s.mumax > 0.f) atomicMax((int *)&acc2[i].y, __float_as_int(s.mumax));
+        red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.du);
+        red_add_f64(&accS[i], (double)s.S.s - (double)s.S.c);
+        if (s.mumax > 0.f) atomicMax(&mumax[i], __float_as_uint(s.mumax));
     }
     unsigned long long wp = warp_sum((unsigned long long)s.pairs);
     unsigned long long wav = warp_sum((unsigned long long)s.av);
@@ -468,10 +556,10 @@ __global__ void __launch_bounds__(128, 5) k_forces(KParams kp, const Inst *__res
 // ---------------------------------------------------------------------------
 __global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
                            const unsigned short *__restrict__ pinst, const float4 *__restrict__ acc,
-                           const float2 *__restrict__ acc2, const float4 *__restrict__ fpos,
-                           const float4 *__restrict__ fth, float *ax, float *ay, float *az,
-                           float *dudt_h, float *dudt_av, float *divv, float *dt_i,
-                           unsigned *dtmin, DevStatus *st)
+                           const double *__restrict__ accS, const unsigned *__restrict__ mumax,
+                           const float4 *__restrict__ fpos, const float4 *__restrict__ fth,
+                           float *ax, float *ay, float *az, float *dudt_h, float *dudt_av,
+                           float *divv, float *dt_i, unsigned *dtmin, DevStatus *st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = INFINITY;
@@ -480,21 +568,22 @@ __global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
         k = pinst[i];
         const Inst &I = insts[k];
         const float4 f = acc[i];
-        const float2 g = acc2[i];
+        const float S = (float)accS[i];
+        const float mu = __uint_as_float(mumax[i]);
         const float4 t = fth[i];
         const float h = fpos[i].w;
         ax[i] = f.x;
         ay[i] = f.y;
         az[i] = f.z;
-        dudt_h[i] = t.x * f.w;
-        dudt_av[i] = g.x;
-        divv[i] = -f.w / (t.w * t.z);
+        dudt_h[i] = t.x * S;
+        dudt_av[i] = f.w;
+        divv[i] = -S / (t.w * t.z);
         const float amag = sqrtf(fmaf(f.x, f.x, fmaf(f.y, f.y, f.z * f.z)));
         const float dta = amag > 0.f ? I.eta_acc * sqrtf(h / amag) : INFINITY;
-        const float dtc = I.eta_courant * h / fmaf(1.f + 0.6f * I.alpha, t.y, 0.6f * I.beta * g.y);
+        const float dtc = I.eta_courant * h / fmaf(1.f + 0.6f * I.alpha, t.y, 0.6f * I.beta * mu);
         dt = fminf(dta, dtc);
         dt_i[i] = dt;
-        if (!(isfinite(f.x) && isfinite(f.y) && isfinite(f.z) && isfinite(f.w) && isfinite(g.x)))
+        if (!(isfinite(f.x) && isfinite(f.y) && isfinite(f.z) && isfinite(f.w) && isfinite(S)))
             raise_status(st, ST_NONFINITE, i);
     }
     // minimum per instance: one atomic per warp when the warp lies in one
@@ -514,10 +603,11 @@ cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
     int n = (int)p.n;
     c.launches += 1;
     const int nt = n > c.kp.ninst ? n : c.kp.ninst;
-    k_predict<<<(nt + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.v[0], p.v[1], p.v[2], p.u, p.a[0], p.a[1],
-                                              p.a[2], p.dudt_h, p.dudt_av, p.h, p.rho, p.omega,
-                                              c.pm, c.dts, c.fpos, c.fvel, c.fth, c.acc, c.acc2,
-                                              c.dtmin, c.st);
+    k_predict<<<(nt + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.v[0], p.v[1], p.v[2],
+                                              p.u, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av,
+                                              p.h, p.rho, p.omega, c.pm, c.dts, c.fpos, c.fvel,
+                                              c.fth, c.ipos, c.acc, c.accS, c.mumax, c.dtmin,
+                                              c.st);
     return cudaGetLastError();
 }
 
@@ -528,8 +618,9 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
     c.launches += 1;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
         k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.inst, c.bstart, c.binst, c.fpos,
-                                                        c.fvel, c.fth, c.list_cnt, c.list_off, c.list,
-                                                        c.origin, c.node, c.acc, c.acc2, c.st);
+                                                        c.fvel, c.fth, c.ipos, c.list_cnt,
+                                                        c.list_off, c.list, c.origin, c.node,
+                                                        c.acc, c.accS, c.mumax, c.st);
     )
     return cudaGetLastError();
 }
@@ -538,9 +629,9 @@ cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     int n = (int)p.n;
     c.launches += 1;
-    k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, c.acc, c.acc2, c.fpos, c.fth, p.a[0],
-                                               p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, p.dt_i,
-                                               c.dtmin, c.st);
+    k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, c.acc, c.accS, c.mumax,
+                                               c.fpos, c.fth, p.a[0], p.a[1], p.a[2], p.dudt_h,
+                                               p.dudt_av, p.divv, p.dt_i, c.dtmin, c.st);
     return cudaGetLastError();
 }
 

@@ -26,10 +26,12 @@ __global__ void k_choose_dt(int ninst, double *dts, const unsigned *dtmin, doubl
     dts[2 * k + 1] = dt;
 }
 
-__global__ void k_dt_shift(int ninst, double *dts)
+// the new step becomes the old one, unless the step failed: then neither
+// the state nor the step clock moves
+__global__ void k_dt_shift(int ninst, double *dts, const DevStatus *st)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < ninst) dts[2 * k] = dts[2 * k + 1];
+    if (k < ninst && st->code == 0) dts[2 * k] = dts[2 * k + 1];
 }
 
 // one particle's kicks and drift; h_next is the seed of the next density pass
@@ -192,7 +194,7 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
         k_kdk<false><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
                                        p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
                                        p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr, c.st);
-    k_dt_shift<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts);
+    k_dt_shift<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts, c.st);
     return cudaGetLastError();
 }
 

@@ -28,9 +28,13 @@
 //                   particles, inside one cell of side <= 6 h) share one tree
 //                   walk: first bucket gfirst[g]
 //   lists           per group, kWalkCap slots of source bucket ids
+//   pmd[i]          double4_16a, FP64 form only: the same in FP64 (pair sums in FP64)
+//   ipos[i]         int4: the same position relative to o_b in fixed point,
+//                   units of qx = q 2^-kFixShift (exact integer differences for
+//                   the force pairs), .w = h in units of qx (set by the predictor)
 //   force records   fpos (rel xyz, h), fvel (v_pred xyz, m), fth (A, c, rho, Omega)
-//   accumulators    acc (a xyz, S = sum m_j v_ij.gradW_ij(h_i)), acc2 (du/dt|Pi,
-//                   max(-mu_ij) as float bits)
+//   accumulators    acc (a xyz, du/dt|Pi), accS (S = sum m_j v_ij.gradW_ij(h_i),
+//                   FP64), mumax (max(-mu_ij) as float bits)
 #pragma once
 
 #include <cuda_bf16.h>
@@ -70,6 +74,9 @@ constexpr int kRelistRounds = 3;  // re-walk rounds queued after the first densi
 constexpr int kRoundBlocks = 304; // blocks of a re-walk round's grid-stride launches
 constexpr int kBboxChunks = 32;   // blocks per instance for open-axis bounding boxes
 constexpr int kConsChunk = 2048;  // particles per block of the conserved totals
+// fixed-point positions of the force pairs: qx = q 2^-11, so 2^31 qx = 2^20 q
+// is at least half the longest box side (q = 2^(floor(log2 maxext) - 20))
+constexpr int kFixShift = 11;
 constexpr unsigned kFull = 0xffffffffu;
 
 // learned seed network 4 -> 32 -> 32 -> 1 (parameter offsets in the flat vector)
@@ -116,6 +123,10 @@ struct Inst {
     float eps_abs;       // absolute inflation of f32 bounds (covers rounding)
     float hcap;          // h must stay below half the shortest periodic length
     float qf;            // origin quantum in f32
+    float qx, inv_qx;    // fixed-point quantum q 2^-kFixShift and its inverse
+    float qx2;           // qx^2
+    float fix_lim;       // fixed point usable while bucket extents and h stay below
+    unsigned LQ[3];      // periodic length in units of qx (rounded; < 2^32)
     double q, inv_q;     // origin quantum and its inverse (powers of two)
     double lo[3], hi[3], Ld[3], invLd[3];
 };
@@ -126,6 +137,7 @@ struct KParams {
     int ninst, n, nb, ng, nnodes;
     int key_passes;      // 8-bit radix passes over (instance, curve index) keys
     int any_open;        // some instance has an open axis
+    int fp64;            // SPH_PRECISION_FP64: pair sums and h iteration in FP64
     float h_rel_tol, margin;
 };
 
@@ -184,9 +196,12 @@ struct Ctx {
 
     // particle records
     float4 *pm = nullptr;
+    double4_16a *pmd = nullptr;           // FP64 form: position relative to the bucket origin, m
     float4 *fpos = nullptr, *fvel = nullptr, *fth = nullptr;
+    int4 *ipos = nullptr;
     float4 *acc = nullptr;
-    float2 *acc2 = nullptr;
+    double *accS = nullptr;
+    unsigned *mumax = nullptr;
     float *rho_old = nullptr;
     float *h_seed = nullptr;          // density seeds / re-walk seeds
 
@@ -195,7 +210,9 @@ struct Ctx {
     // list starts
     unsigned int *list = nullptr, *list_cnt = nullptr, *list_off = nullptr;
     unsigned int *arena_used = nullptr;  // overflow arena entries handed out
-    int64_t arena_cap = 0;
+    int64_t arena_cap = 0;            // arena entries in use (<= arena_alloc)
+    int64_t arena_alloc = 0;          // arena entries allocated behind the slots
+    int64_t list_slots = 0;           // fixed list slots (groups x kWalkCap)
     unsigned int *redo = nullptr;     // per round r: group ids queued (ng entries each)
 
     // host-mode mirror buffers for sph_step_host
@@ -283,6 +300,11 @@ __device__ __forceinline__ float wrapf(float d, float L, float invL)
 __device__ __forceinline__ double wrapd(double d, double L)
 {
     return d - L * rint(d / L);
+}
+
+__device__ __forceinline__ void red_add_f64(double *addr, double a)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(a) : "memory");
 }
 
 // vector reduction into global memory (sm_90+): one L2 atomic per 16 bytes
@@ -414,6 +436,17 @@ struct Kahan {
 // ---------------------------------------------------------------------------
 struct KWC2 {
     static constexpr float sigma = 3.3422538049298023f;  // 21 / (2 pi)
+    static constexpr double sigmad = 3.3422538049298023;
+    __device__ __forceinline__ static double wd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t;
+        return t2 * t2 * fma(4.0, q, 1.0);
+    }
+    __device__ __forceinline__ static double dwqd(double q)
+    {
+        const double t = 1.0 - q;
+        return -20.0 * t * t * t;
+    }
     __device__ __forceinline__ static float w(float q)
     {
         float t = 1.f - q, t2 = t * t;
@@ -424,43 +457,84 @@ struct KWC2 {
         float t = 1.f - q;
         return -20.f * t * t * t;
     }
+    // the same with 1 - q supplied (t, computed without cancellation)
+    __device__ __forceinline__ static float dwqt(float q, float t)
+    {
+        (void)q;
+        return -20.f * t * t * t;
+    }
 };
 struct KWC4 {
     static constexpr float sigma = 4.923856051905513f;  // 495 / (32 pi)
+    static constexpr double sigmad = 4.923856051905513;
+    __device__ __forceinline__ static double wd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t, t6 = t2 * t2 * t2;
+        return t6 * fma(q, fma(35.0 / 3.0, q, 6.0), 1.0);
+    }
+    __device__ __forceinline__ static double dwqd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t, t5 = t2 * t2 * t;
+        return (-56.0 / 3.0) * t5 * fma(5.0, q, 1.0);
+    }
     __device__ __forceinline__ static float w(float q)
     {
         float t = 1.f - q, t2 = t * t, t6 = t2 * t2 * t2;
         return t6 * fmaf(q, fmaf(35.f / 3.f, q, 6.f), 1.f);
     }
-    __device__ __forceinline__ static float dwq(float q)
+    __device__ __forceinline__ static float dwq(float q) { return dwqt(q, 1.f - q); }
+    __device__ __forceinline__ static float dwqt(float q, float t)
     {
-        float t = 1.f - q, t2 = t * t, t5 = t2 * t2 * t;
+        float t2 = t * t, t5 = t2 * t2 * t;
         return (-56.f / 3.f) * t5 * fmaf(5.f, q, 1.f);
     }
 };
 struct KWC6 {
     static constexpr float sigma = 6.788953041263660f;  // 1365 / (64 pi)
+    static constexpr double sigmad = 6.788953041263660;
+    __device__ __forceinline__ static double wd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t, t4 = t2 * t2, t8 = t4 * t4;
+        return t8 * fma(q, fma(q, fma(32.0, q, 25.0), 8.0), 1.0);
+    }
+    __device__ __forceinline__ static double dwqd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
+        return -22.0 * t7 * fma(q, fma(16.0, q, 7.0), 1.0);
+    }
     __device__ __forceinline__ static float w(float q)
     {
         float t = 1.f - q, t2 = t * t, t4 = t2 * t2, t8 = t4 * t4;
         return t8 * fmaf(q, fmaf(q, fmaf(32.f, q, 25.f), 8.f), 1.f);
     }
-    __device__ __forceinline__ static float dwq(float q)
+    __device__ __forceinline__ static float dwq(float q) { return dwqt(q, 1.f - q); }
+    __device__ __forceinline__ static float dwqt(float q, float t)
     {
-        float t = 1.f - q, t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
+        float t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
         return -22.f * t7 * fmaf(q, fmaf(16.f, q, 7.f), 1.f);
     }
 };
 struct KM4 {
     static constexpr float sigma = 2.5464790894703255f;  // 8 / pi
+    static constexpr double sigmad = 2.5464790894703255;
+    __device__ __forceinline__ static double wd(double q)
+    {
+        const double t = 1.0 - q;
+        return q < 0.5 ? fma(6.0 * q * q, q - 1.0, 1.0) : 2.0 * t * t * t;
+    }
+    __device__ __forceinline__ static double dwqd(double q)
+    {
+        const double t = 1.0 - q;
+        return q < 0.5 ? fma(18.0, q, -12.0) : -6.0 * t * t / q;
+    }
     __device__ __forceinline__ static float w(float q)
     {
         float t = 1.f - q;
         return q < 0.5f ? fmaf(6.f * q * q, q - 1.f, 1.f) : 2.f * t * t * t;
     }
-    __device__ __forceinline__ static float dwq(float q)
+    __device__ __forceinline__ static float dwq(float q) { return dwqt(q, 1.f - q); }
+    __device__ __forceinline__ static float dwqt(float q, float t)
     {
-        float t = 1.f - q;
         return q < 0.5f ? fmaf(18.f, q, -12.f) : -6.f * t * t / q;
     }
 };

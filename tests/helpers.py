@@ -99,20 +99,3 @@ def motion_err(xa, xb, prob):
         return d - np.where(per, L * np.round(d / L), 0.0)
     mv = np.max(np.abs(wrap(xb - prob.pos)))
     return np.max(np.abs(wrap(xa - xb))) / max(mv, 1e-300)
-
-
-# FP32 evaluation of a sum of terms that cancel: each term carries ~16
-# roundings of relative size 2^-23 (FP32 positions relative to the bucket
-# origin, the kernel gradient's rsqrt and polynomial, the velocity
-# difference, the dot product, the accumulation), so the sum can be off by
-# that much of the sum of the terms' magnitudes, whatever its own size
-FP32_SUM_BOUND = 16 * 2.0 ** -23
-
-
-def norm_err_cond(gpu, ref, scale):
-    """norm_err after allowing each entry the FP32 bound of its sum
-    (scale = sum of the magnitudes of the terms of that entry)."""
-    gpu = np.asarray(gpu, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
-    excess = np.maximum(np.abs(gpu - ref) - FP32_SUM_BOUND * np.asarray(scale), 0.0)
-    return float(np.max(excess) / max(np.max(np.abs(ref)), 1e-300))

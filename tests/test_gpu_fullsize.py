@@ -5,8 +5,10 @@ the benchmark runs it; the FP64 oracle solves h by brute force over all N
 for the neighbourhoods of clusters of sink particles and evaluates the
 forces of those sinks (tests/helpers.oracle_sampled).  Tolerances: h, rho,
 Omega to 1e-5 relative; accelerations, du/dt and div v to 2e-4 of the
-field's max norm over the sinks, du/dt|H and div v after the FP32 bound of
-their near-cancelling sums.
+field's max norm over the sinks.  du/dt|H and div v are sums whose terms
+cancel across the KH shear (the printed condition number is the sum of the
+terms' magnitudes over the largest |sum|); they are held to the same plain
+max-norm tolerance.
 
   Kelvin-Helmholtz shear layer, 128^3 = 2,097,152 particles, sinks at both
   shear interfaces and at random points;
@@ -19,8 +21,7 @@ their near-cancelling sums.
 import numpy as np
 import pytest
 
-from helpers import (norm_err, norm_err_cond, oracle_params, oracle_sampled, rel_max,
-                     to_input_order)
+from helpers import norm_err, oracle_params, oracle_sampled, rel_max, to_input_order
 from paper_2511_11425_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -61,14 +62,11 @@ def _check(g, o, sinks, off=0):
     assert rel_max(g["h"][idx], o["h"]) < TOL_H
     assert rel_max(g["rho"][idx], o["rho"]) < TOL_H
     assert rel_max(g["omega"][idx], o["omega"]) < TOL_H
-    for k in ("a", "dudt_av"):
-        assert norm_err(g[k][idx], o[k]) < TOL_F, k
-    # du/dt|H and div v are sums whose terms can cancel (|v_ij| = 1 across
-    # the shear of the KH layer): each entry also gets the FP32 bound of its
-    # own sum (helpers.FP32_SUM_BOUND times the sum of the terms' magnitudes)
-    for k in ("dudt_h", "divv"):
-        err = norm_err_cond(g[k][idx], o[k], o[k + "_scale"])
-        print("%s norm error %.3g (plain %.3g)" % (k, err, norm_err(g[k][idx], o[k])))
+    for k in ("a", "dudt_av", "dudt_h", "divv"):
+        err = norm_err(g[k][idx], o[k])
+        cond = (float(np.max(o[k + "_scale"])) / max(float(np.max(np.abs(o[k]))), 1e-300)
+                if k + "_scale" in o else 1.0)
+        print("%s max-norm error %.3g (condition %.3g)" % (k, err, cond))
         assert err < TOL_F, k
 
 
