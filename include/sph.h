@@ -137,6 +137,26 @@ typedef struct {
  * layout and meaning as sph_particles. */
 typedef sph_particles sph_host_particles;
 
+/* phases timed per launch group while sph_set_profiling is on (index into
+ * sph_stats.phase_ms / phase_launches) */
+enum {
+    SPH_PHASE_KEYS = 0,      /* bounding boxes + curve keys                       */
+    SPH_PHASE_SORT = 1,      /* radix-sort passes                                 */
+    SPH_PHASE_PERMUTE = 2,   /* gather + copy-back of every particle array        */
+    SPH_PHASE_LAYOUT = 3,    /* bucket layout scan                                */
+    SPH_PHASE_BUCKETS = 4,   /* bucket origins, relative positions, leaf bounds   */
+    SPH_PHASE_TREE = 5,      /* bottom-up bounds refit                            */
+    SPH_PHASE_BOB_REFIT = 6, /* box-of-balls refresh after the density pass       */
+    SPH_PHASE_WALK = 7,      /* interaction-list walks                            */
+    SPH_PHASE_DENSITY = 8,   /* Newton kernel (all passes, re-walk rounds)        */
+    SPH_PHASE_PREDICT = 9,   /* predictor + EOS                                   */
+    SPH_PHASE_FORCES = 10,   /* pair-force kernel                                 */
+    SPH_PHASE_FINALIZE = 11, /* finalize sums, time-step limits                   */
+    SPH_PHASE_KDK = 12,      /* step choice, kicks and drift                      */
+    SPH_PHASE_CONSERVED = 13,/* conserved totals                                  */
+    SPH_PHASE_COUNT = 14
+};
+
 typedef struct {
     uint64_t density_pairs;      /* sum over Newton passes of sum_i n_i (last density call) */
     uint64_t force_pairs;        /* unordered pairs with r < max(h_i,h_j) (last force call)  */
@@ -154,6 +174,8 @@ typedef struct {
     int32_t  pad_;
     uint64_t force_av_pairs;     /* pairs of the last force call with v_ij.r_ij < 0          */
     uint64_t launches;           /* kernels launched by this context since sph_create        */
+    double   phase_ms[16];       /* per SPH_PHASE_*: device time accumulated while profiling */
+    uint64_t phase_launches[16]; /* per SPH_PHASE_*: timed launch groups                     */
 } sph_stats;
 
 /*
@@ -477,6 +499,14 @@ sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t cap, int64_t 
  * SPH_ERR_CAPACITY if the lists would pass 2^32 entries.  The paper has no
  * counterpart (it is a memory-budget setting of this library). */
 sph_status sph_set_list_arena(sph_ctx *ctx, int64_t entries);
+
+/* sph_set_profiling: on != 0 starts timing every phase of the calls that
+ * follow (CUDA events around each launch group of a plain call; steps
+ * replayed from a captured graph and calls made during a capture are not
+ * timed) and clears the accumulated times in sph_stats.phase_ms; on == 0
+ * stops.  Costs two event records per launch group.  The paper has no
+ * counterpart (instrumentation of this library). */
+sph_status sph_set_profiling(sph_ctx *ctx, int32_t on);
 
 /* sph_set_dt_old: set the previous step size used by the predictor and the
  * closing kick (0 restarts the integration as at t = 0). */

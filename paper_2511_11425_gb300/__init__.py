@@ -33,7 +33,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_reduce_conserved_noalloc", "sph_batch_create", "sph_batch_get_dt",
            "sph_graph_capture", "sph_graph_launch", "sph_graph_totals", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
-           "sph_mlp_load_samples", "sph_bucket_layout", "sph_set_list_arena",
+           "sph_mlp_load_samples", "sph_bucket_layout", "sph_set_list_arena", "sph_set_profiling",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
 MLP_NPARAM = 1249
 SEED_MODES = {"analytic": 0, "mlp": 1}
@@ -73,7 +73,8 @@ class c_stats(C.Structure):
                 ("dt_old", C.c_double), ("ms_build", C.c_float), ("ms_density", C.c_float),
                 ("ms_forces", C.c_float), ("ms_kdk", C.c_float), ("ms_walk", C.c_float),
                 ("ms_density_kernel", C.c_float), ("ms_force_kernel", C.c_float),
-                ("pad_", C.c_int32), ("force_av_pairs", C.c_uint64), ("launches", C.c_uint64)]
+                ("pad_", C.c_int32), ("force_av_pairs", C.c_uint64), ("launches", C.c_uint64),
+                ("phase_ms", C.c_double * 16), ("phase_launches", C.c_uint64 * 16)]
 
 
 _lib = None
@@ -111,6 +112,7 @@ def lib():
         L.sph_graph_totals.argtypes = [vp, C.POINTER(dbl)]
         L.sph_set_dt_old.argtypes = [vp, dbl]
         L.sph_set_list_arena.argtypes = [vp, i64]
+        L.sph_set_profiling.argtypes = [vp, C.c_int32]
         fp = C.POINTER(C.c_float)
         L.sph_mlp_set_weights.argtypes = [vp, fp, i64]
         L.sph_mlp_get_weights.argtypes = [vp, fp, i64]
@@ -524,6 +526,22 @@ def sph_bucket_layout(ctx):
     _check(ctx, lib().sph_bucket_layout(ctx, first.ctypes.data_as(C.POINTER(C.c_int32)),
                                         first.size, C.byref(ns)))
     return first
+
+
+PHASES = ("keys", "sort", "permute", "layout", "buckets", "tree", "bob_refit", "walk",
+          "density", "predict", "forces", "finalize", "kdk", "conserved")
+
+
+def sph_set_profiling(ctx, on: bool):
+    """Start (and clear) or stop per-phase device timing of plain calls."""
+    _check(ctx, lib().sph_set_profiling(ctx, 1 if on else 0))
+
+
+def sph_phase_times(ctx):
+    """{phase: (total ms, launch groups)} accumulated while profiling."""
+    st = c_stats()
+    _check(ctx, lib().sph_get_stats(ctx, C.byref(st)))
+    return {name: (st.phase_ms[k], int(st.phase_launches[k])) for k, name in enumerate(PHASES)}
 
 
 def sph_set_list_arena(ctx, entries: int):

@@ -227,7 +227,12 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.fvel, np);
     AL(c.fth, np);
     AL(c.ipos, np);
-    if (c.kp.fp64) AL(c.pmd, np);
+    if (c.kp.fp64) {
+        AL(c.pmd, np);
+        AL(c.fveld, np);
+        AL(c.fthd, np);
+        AL(c.acc64, np);
+    }
     AL(c.acc, np);
     AL(c.accS, np);
     AL(c.mumax, np);
@@ -269,7 +274,7 @@ void free_ctx(Ctx &c)
                     c.cons_out, c.pinst, c.keys[0], c.keys[1], c.vals[0], c.vals[1], c.hist,
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
                     c.list_cnt, c.list_off, c.arena_used, c.list, c.redo, c.node, c.refit,
-                    c.pm, c.pmd, c.ipos, c.fpos, c.fvel, c.fth,
+                    c.pm, c.pmd, c.fveld, c.fthd, c.acc64, c.ipos, c.fpos, c.fvel, c.fth,
                     c.acc, c.accS, c.mumax, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -286,6 +291,9 @@ void free_ctx(Ctx &c)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t st : {c.side, c.copy})
         if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : c.prof.ev)
+        if (e) cudaEventDestroy(e);
+    c.prof.ev.clear();
 }
 
 // lay out instances of the given particle counts (offsets follow the order)
@@ -376,10 +384,27 @@ sph_status set_layout(Ctx &c, const std::vector<int64_t> &counts)
     return SPH_OK;
 }
 
+// add the timed launch groups of the call that just completed to the
+// per-phase totals (groups whose events did not complete are dropped)
+void prof_collect(Ctx &c)
+{
+    for (size_t k = 0; k < c.prof.phase.size(); ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c.prof.ev[2 * k], c.prof.ev[2 * k + 1]) == cudaSuccess) {
+            c.prof.ms[c.prof.phase[k]] += ms;
+            c.prof.launches[c.prof.phase[k]] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    c.prof.phase.clear();
+}
+
 sph_status begin(sph_ctx *ctx, cudaStream_t s)
 {
     Ctx &c = ctx->c;
     c.err.clear();
+    c.prof.phase.clear();
     CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
     return SPH_OK;
 }
@@ -398,6 +423,7 @@ sph_status settle(sph_ctx *ctx, cudaStream_t s)
     Ctx &c = ctx->c;
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
+    if (!c.prof.phase.empty()) prof_collect(c);
     const DevStatus &h = *c.st_host;
     switch (h.code) {
     case ST_OK: return SPH_OK;
@@ -1494,6 +1520,19 @@ extern "C" sph_status sph_bucket_layout(sph_ctx *ctx, int32_t *first, int64_t ca
     return SPH_OK;
 }
 
+extern "C" sph_status sph_set_profiling(sph_ctx *ctx, int32_t on)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    c.prof.on = on != 0;
+    c.prof.phase.clear();
+    for (int k = 0; k < SPH_PHASE_COUNT; ++k) {
+        c.prof.ms[k] = 0.0;
+        c.prof.launches[k] = 0;
+    }
+    return SPH_OK;
+}
+
 extern "C" sph_status sph_set_list_arena(sph_ctx *ctx, int64_t entries)
 {
     if (!ctx) return SPH_ERR_ARG;
@@ -1549,6 +1588,10 @@ extern "C" sph_status sph_get_stats(const sph_ctx *ctx, sph_stats *out)
     if (!ctx || !out) return SPH_ERR_ARG;
     *out = ctx->c.stats;
     out->launches = ctx->c.launches;
+    for (int k = 0; k < 16; ++k) {
+        out->phase_ms[k] = k < SPH_PHASE_COUNT ? ctx->c.prof.ms[k] : 0.0;
+        out->phase_launches[k] = k < SPH_PHASE_COUNT ? ctx->c.prof.launches[k] : 0;
+    }
     return SPH_OK;
 }
 

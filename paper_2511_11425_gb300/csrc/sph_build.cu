@@ -1070,6 +1070,7 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const KParams &kp = c.kp;
     const int n = (int)p.n;
+    int pr = prof_begin(c, s, SPH_PHASE_KEYS);
     // bounding boxes for the key quantisation (only open axes need data)
     if (kp.any_open) {
         k_bbox_partial<<<dim3(kBboxChunks, kp.ninst), 256, 0, s>>>(c.inst, p.x[0], p.x[1], p.x[2],
@@ -1081,8 +1082,10 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     const int g = (n + 255) / 256;
     k_morton<<<g, 256, 0, s>>>(n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], c.morton_box,
                                c.keys[0], c.vals[0]);
+    prof_end(c, s, pr);
     const int ntiles = (n + kSortTile - 1) / kSortTile;
     int cur = 0;
+    pr = prof_begin(c, s, SPH_PHASE_SORT);
     for (int pass = 0; pass < kp.key_passes; ++pass) {
         const int shift = 8 * pass;
         k_sort_hist<<<ntiles, 256, 0, s>>>(c.keys[cur], n, shift, c.hist, ntiles);
@@ -1092,6 +1095,7 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
                                               ntiles);
         cur ^= 1;
     }
+    prof_end(c, s, pr);
     const unsigned *perm = c.vals[cur];
     // permute every caller array through the scratch buffer
     typedef unsigned long long u64;
@@ -1104,8 +1108,10 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     pf.f4[7] = p.dudt_h; pf.f4[8] = p.dudt_av; pf.f4[9] = p.divv; pf.f4[10] = p.dt_i;
     pf.f2 = p.nngb;
     pf.f1 = p.iters;
+    pr = prof_begin(c, s, SPH_PHASE_PERMUTE);
     k_gather_all<<<g, 256, 0, s>>>(perm, n, pf, (char *)c.tmp);
     k_copyback_all<<<g, 256, 0, s>>>(n, pf, (const char *)c.tmp);
+    prof_end(c, s, pr);
     if (c.mlp.record) {
         cudaError_t e = launch_mlp_permute(c, perm, n, s);
         if (e != cudaSuccess) return e;
@@ -1115,20 +1121,26 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
         const int tiles = (n + kPadTile - 1) / kPadTile;
         const unsigned long long *sk = c.keys[cur];
         const int gb = (kp.nb + 255) / 256;
+        pr = prof_begin(c, s, SPH_PHASE_LAYOUT);
         k_pad_reduce<<<tiles, 256, 0, s>>>(n, c.inst, c.pinst, sk, p.h, c.morton_box, c.pad_agg);
         k_pad_scan<<<1, 1024, 0, s>>>(tiles, c.pad_agg);
         k_pad_init<<<gb, 256, 0, s>>>(kp.nb, c.inst, c.binst, c.bstart);
         k_pad_apply<<<tiles, 256, 0, s>>>(n, c.inst, c.pinst, sk, p.h, c.morton_box, c.pad_agg,
                                           c.bstart, c.pad_used);
         k_pad_fallback<<<gb, 256, 0, s>>>(kp.nb, c.inst, c.binst, c.pad_used, c.bstart);
+        prof_end(c, s, pr);
         c.launches += 5;
     }
     // buckets and trees
     const int wb = (kp.nb * 32 + 127) / 128;
+    pr = prof_begin(c, s, SPH_PHASE_BUCKETS);
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
                                  c.origin, c.pm, c.ipos, c.pmd, c.node, 1, c.st);
+    prof_end(c, s, pr);
     c.launches += 2 + 3 * kp.key_passes + 2 + 1;
+    pr = prof_begin(c, s, SPH_PHASE_TREE);
     tree_refit(c, s, 0);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
@@ -1137,9 +1149,13 @@ cudaError_t launch_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     const KParams &kp = c.kp;
     const int wb = (kp.nb * 32 + 127) / 128;
     c.launches += 1;
+    int pr = prof_begin(c, s, SPH_PHASE_BUCKETS);
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
                                  c.origin, c.pm, c.ipos, c.pmd, c.node, 1, c.st);
+    prof_end(c, s, pr);
+    pr = prof_begin(c, s, SPH_PHASE_TREE);
     tree_refit(c, s, 0);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
@@ -1148,9 +1164,11 @@ cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     const KParams &kp = c.kp;
     const int wb = (kp.nb * 32 + 127) / 128;
     c.launches += 1;
+    const int pr = prof_begin(c, s, SPH_PHASE_BOB_REFIT);
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
                                  c.origin, c.pm, c.ipos, c.pmd, c.node, 0, c.st);
     tree_refit(c, s, 1);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
@@ -1167,10 +1185,12 @@ cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, con
     // the overflow arena is emptied when every list is rebuilt
     if (round < 0) cudaMemsetAsync(c.arena_used, 0, sizeof(unsigned), s);
     c.launches += 1;
+    const int pr = prof_begin(c, s, SPH_PHASE_WALK);
     k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(kp, c.inst, c.gfirst, c.bstart, c.binst, mode, c.node,
                                              c.pm, c.origin, h_walk, ids, cnt, c.list, c.list_cnt,
                                              c.list_off, c.arena_used, (unsigned)c.arena_cap,
                                              c.st);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 

@@ -566,6 +566,7 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     unsigned *redo_cnt_out = next < kRelistRounds ? &c.st->redo_cnt[next] : nullptr;
     cudaMemsetAsync(c.gflag, 0, sizeof(unsigned) * (size_t)kp.ng, s);
     c.launches += 1;
+    const int pr = prof_begin(c, s, SPH_PHASE_DENSITY);
 #define SPH_DENSITY_LAUNCH(EMIT_, D64_)                                                      \
     k_density<KT, EMIT_, D64_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                                 \
         kp, c.inst, c.pm, c.pmd, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list,     \
@@ -581,6 +582,7 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
         }
     )
 #undef SPH_DENSITY_LAUNCH
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 

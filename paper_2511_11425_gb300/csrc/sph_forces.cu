@@ -56,6 +56,7 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
                           const float *__restrict__ omega, const float4 *__restrict__ pm,
                           const double *__restrict__ dts, float4 *fpos, float4 *fvel, float4 *fth,
                           int4 *ipos, float4 *acc, double *accS, unsigned *mumax, unsigned *dtmin,
+                          double4_16a *fveld, double4_16a *fthd, double4_16a *acc64,
                           DevStatus *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -80,6 +81,13 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
     float c = sqrtf(gamma * P / r);
     float A = P / (om * r * r);
     if (!(isfinite(A) && isfinite(c) && uu >= 0.0)) raise_status(st, ST_NONFINITE, i);
+    if (fveld) {  // FP64 form: the same records in FP64
+        const double rd = (double)r, od = (double)om, gd = (double)gamma;
+        const double Pd = (gd - 1.0) * rd * uu;
+        fveld[i] = make_double4_16a(v[0], v[1], v[2], (double)pm[i].w);
+        fthd[i] = make_double4_16a(Pd / (od * rd * rd), sqrt(gd * Pd / rd), rd, od);
+        acc64[i] = make_double4_16a(0.0, 0.0, 0.0, 0.0);
+    }
     float4 q = pm[i];
     fpos[i] = make_float4(q.x, q.y, q.z, hi);
     fvel[i] = make_float4((float)v[0], (float)v[1], (float)v[2], q.w);
@@ -559,7 +567,8 @@ __global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
                            const double *__restrict__ accS, const unsigned *__restrict__ mumax,
                            const float4 *__restrict__ fpos, const float4 *__restrict__ fth,
                            float *ax, float *ay, float *az, float *dudt_h, float *dudt_av,
-                           float *divv, float *dt_i, unsigned *dtmin, DevStatus *st)
+                           float *divv, float *dt_i, unsigned *dtmin,
+                           const double4_16a *__restrict__ acc64, DevStatus *st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = INFINITY;
@@ -567,7 +576,13 @@ __global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
     if (i < n) {
         k = pinst[i];
         const Inst &I = insts[k];
-        const float4 f = acc[i];
+        float4 f;
+        if (acc64) {  // FP64 form
+            const double4_16a d = acc64[i];
+            f = make_float4((float)d.x, (float)d.y, (float)d.z, (float)d.w);
+        } else {
+            f = acc[i];
+        }
         const float S = (float)accS[i];
         const float mu = __uint_as_float(mumax[i]);
         const float4 t = fth[i];
@@ -603,17 +618,26 @@ cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
     int n = (int)p.n;
     c.launches += 1;
     const int nt = n > c.kp.ninst ? n : c.kp.ninst;
+    const int pr = prof_begin(c, s, SPH_PHASE_PREDICT);
     k_predict<<<(nt + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.v[0], p.v[1], p.v[2],
                                               p.u, p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av,
                                               p.h, p.rho, p.omega, c.pm, c.dts, c.fpos, c.fvel,
                                               c.fth, c.ipos, c.acc, c.accS, c.mumax, c.dtmin,
+                                              c.kp.fp64 ? c.fveld : nullptr, c.fthd, c.acc64,
                                               c.st);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     (void)p;
+    const int pr = prof_begin(c, s, SPH_PHASE_FORCES);
+    if (c.kp.fp64) {
+        const cudaError_t e = launch_forces64(c, s);
+        prof_end(c, s, pr);
+        return e;
+    }
     int g = (c.kp.nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
     c.launches += 1;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
@@ -622,6 +646,7 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
                                                         c.list_off, c.list, c.origin, c.node,
                                                         c.acc, c.accS, c.mumax, c.st);
     )
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
@@ -629,9 +654,12 @@ cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     int n = (int)p.n;
     c.launches += 1;
+    const int pr = prof_begin(c, s, SPH_PHASE_FINALIZE);
     k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, c.acc, c.accS, c.mumax,
                                                c.fpos, c.fth, p.a[0], p.a[1], p.a[2], p.dudt_h,
-                                               p.dudt_av, p.divv, p.dt_i, c.dtmin, c.st);
+                                               p.dudt_av, p.divv, p.dt_i, c.dtmin,
+                                               c.kp.fp64 ? c.acc64 : nullptr, c.st);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 

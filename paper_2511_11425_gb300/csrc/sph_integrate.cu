@@ -179,6 +179,7 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
     const int n = (int)p.n;
     const int ni = c.kp.ninst;
     c.launches += 3;
+    const int pr = prof_begin(c, s, SPH_PHASE_KDK);
     k_choose_dt<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts, c.dtmin, dt_fixed, c.st);
     const bool corr = c.mlp.seed_mode == SPH_SEED_MLP;
     if (corr || c.mlp.record) {  // network inputs, records, corrections
@@ -195,6 +196,7 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
                                        p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
                                        p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr, c.st);
     k_dt_shift<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts, c.st);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
@@ -202,9 +204,11 @@ cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const int nb = c.cons_blocks > 0 ? c.cons_blocks : 1;
     c.launches += 2;
+    const int pr = prof_begin(c, s, SPH_PHASE_CONSERVED);
     k_cons_partial<<<dim3(nb, c.kp.ninst), kConsThreads, 0, s>>>(
         c.inst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.m, c.cons_part);
     k_cons_final<<<c.kp.ninst, 288, 0, s>>>(nb, c.cons_part, c.cons_out);
+    prof_end(c, s, pr);
     return cudaGetLastError();
 }
 

@@ -147,6 +147,16 @@ struct RefitBlock {
     int inst, lvl, levels, blk;
 };
 
+// per-phase device timing of plain calls (sph_set_profiling): an event pair
+// around each launch group, read back when the call settles
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // pool: pair k = events 2k, 2k + 1
+    std::vector<int> phase;       // phase of each pair recorded in this call
+    double ms[SPH_PHASE_COUNT] = {};
+    unsigned long long launches[SPH_PHASE_COUNT] = {};
+};
+
 struct Ctx {
     std::vector<sph_params> prm;  // per instance
     std::vector<Inst> inst_host;
@@ -196,7 +206,10 @@ struct Ctx {
 
     // particle records
     float4 *pm = nullptr;
-    double4_16a *pmd = nullptr;           // FP64 form: position relative to the bucket origin, m
+    double4_16a *pmd = nullptr;   // FP64 form: position relative to the bucket origin, m
+    double4_16a *fveld = nullptr; // FP64 form: v_pred xyz, m
+    double4_16a *fthd = nullptr;  // FP64 form: A, c, rho, Omega
+    double4_16a *acc64 = nullptr; // FP64 form: a xyz, du/dt|Pi
     float4 *fpos = nullptr, *fvel = nullptr, *fth = nullptr;
     int4 *ipos = nullptr;
     float4 *acc = nullptr;
@@ -282,7 +295,28 @@ struct Ctx {
     // out_done joins the copy stream back
     cudaEvent_t out_dens = nullptr, out_force = nullptr, out_done = nullptr;
     uint64_t launches = 0;
+    Prof prof;
 };
+
+// open a timed launch group of `phase` on stream s (returns its pair index,
+// or -1 when not profiling or capturing); close it with prof_end
+inline int prof_begin(Ctx &c, cudaStream_t s, int phase)
+{
+    if (!c.prof.on || c.capturing) return -1;
+    const size_t k = c.prof.phase.size();
+    while (c.prof.ev.size() < 2 * (k + 1)) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c.prof.ev.push_back(e);
+    }
+    if (cudaEventRecord(c.prof.ev[2 * k], s) != cudaSuccess) return -1;
+    c.prof.phase.push_back(phase);
+    return (int)k;
+}
+inline void prof_end(Ctx &c, cudaStream_t s, int k)
+{
+    if (k >= 0) cudaEventRecord(c.prof.ev[2 * k + 1], s);
+}
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -570,6 +604,7 @@ cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s);
 // forces (sph_forces.cu)
 cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s);
+cudaError_t launch_forces64(Ctx &c, cudaStream_t s);  // FP64 form (sph_forces64.cu)
 cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s);
 // integration (sph_integrate.cu)
 cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s);
