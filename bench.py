@@ -1,12 +1,12 @@
 """Benchmark of the SPH hot path on GB300 (one JSON line on stdout).
 
-Workload: the Sedov-Taylor blast of the paper's test suite (Sec. 3.3) on a
-64^3 = 262,144-particle jittered periodic lattice, Wendland C2 with 64
-neighbours, alpha = 1, beta = 2, gamma = 5/3, starting at t = 0.  One step =
-sph_step: Morton sort + bounds tree, density/h Newton pass, force pass,
-kick-drift-kick with the Courant step (every row of the hot path), plus the
-conserved-totals reduction.  --workload kh128 times the Kelvin-Helmholtz
-shear layer (Sec. 3.8 setting) on 128^3 = 2,097,152 particles instead.
+Workload (default): the Kelvin-Helmholtz shear layer (Sec. 3.8 setting) on
+a 128^3 = 2,097,152-particle jittered periodic lattice, Wendland C2 with 64
+neighbours, alpha = 1, beta = 2, gamma = 5/3, mixed precision, autotuned
+layout, starting at t = 0.  One step = sph_step: curve sort + bounds tree,
+density/h Newton pass, force pass, kick-drift-kick with the Courant step
+(every row of the hot path), plus the conserved-totals reduction.
+--workload sedov64 times the Sedov-Taylor blast (Sec. 3.3) on 64^3 instead.
 
   value       particle-steps/s with the state resident in HBM; each timed step
               is one replay of the captured step (CUDA graph, conserved totals
@@ -17,11 +17,18 @@ shear layer (Sec. 3.8 setting) on 128^3 = 2,097,152 particles instead.
               from pinned host memory, stepped, and every array copied back,
               all inside the timed region
   roofline    the dominant pair kernel against the FP32 pipe peak
-              (152 SMs x 128 lanes x 2 flop x 2.07 GHz), algorithmic flops only
+              (SMs x 128 lanes x 2 flop x 2.07 GHz), algorithmic flops only
+  roofline_hbm the memory-bound phases (sort, permute, buckets, predictor,
+              finalize, kick-drift-kick, totals): algorithmic bytes per launch
+              over the CUDA-event time per launch of a profiled pass, against
+              the measured HBM copy bandwidth
   cpu_baseline the FP64 oracle on a bounded sample of the same state
   error_vs_oracle  per-field error of the GPU path against the oracle on
               sampled sinks of the stepped state (the 'stated error' of the
               metric), computed in the oracle's leg
+  forms       the mixed-precision form against the plain FP64 form (Sedov
+              64^3 to t = 0.05, KH 128^3), the batched form, the learned seed,
+              and learned + mixed + batched against the plain form
 
 --impl reference times the oracle (the deliberately slow FP64 brute force)
 on the same workload and metric.  Under torchrun every rank runs its own
@@ -83,6 +90,10 @@ def fma_probe(stream):
 FLOPS_DENSITY_PAIR = 26      # one useful (r < h) pair evaluation of one Newton pass
 FLOPS_FORCE_PAIR = 61        # one unordered pair, pressure and PdV terms, both sides
 FLOPS_FORCE_AV = 24          # extra flops of a pair with active viscosity
+# the planning estimate of the same work (about 30 flops per density pair per
+# pass, about 100 per unique force pair), reported beside the tally
+FLOPS_DENSITY_PAIR_EST = 30
+FLOPS_FORCE_PAIR_EST = 100
 METRIC = "SPH particle-steps/s"
 UNIT = "particle-steps/s"
 
@@ -91,7 +102,39 @@ WORKLOADS = {
     "sedov64": "sedov_taylor_64^3 (262,144 particles, periodic unit box, t from 0)",
     "kh128": "kelvin_helmholtz_128^3 (2,097,152 particles, periodic unit box, t from 0)",
 }
-_WORKLOAD = ["sedov64"]  # set from --workload
+_WORKLOAD = ["kh128"]  # set from --workload
+HBM_PEAK_GBS_FALLBACK = 6800.0
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json,
+    driver-written), else the recipe's fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), \
+            "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_PEAK_GBS_FALLBACK, "fallback"
+
+
+# Algorithmic bytes per particle of the memory-bound phases (each array read
+# or written once; FP64 x, v, u = 56 B, FP32 per-particle fields 4 B each):
+#  keys      x (24) + instance (2) read, key (8) + index (4) written       = 38
+#  sort      per 8-bit pass: keys read by the histogram (8), keys and
+#            indices read and written by the scatter (24)                 = 32 x passes
+#  permute   gather: index (4) + 111 B of particle arrays read, 111 written
+#            to scratch; copy-back: 111 read, 111 written                 = 448
+#  layout    keys, h, instance read twice (scan and apply)                = 28
+#  buckets   x, m, h read (32), FP32 relative position + m (16) and
+#            fixed-point position (16) written                            = 64
+#  predict   v, u, a, du/dt, h, rho, Omega, relative position, instance
+#            read (82), force records, accumulators written (80)          = 162
+#  finalize  accumulators, records read (50), a, du/dt, div v, dt_i (28)  = 78
+#  kdk       x, v, u, a, du/dt, div v, h, instance read (86); x, v, u, h
+#            written (60)                                                 = 146
+#  conserved x, v, u, m read                                              = 60
+HBM_BYTES_PER_PARTICLE = {"keys": 38, "permute": 448, "layout": 28, "buckets": 64,
+                          "predict": 162, "finalize": 78, "kdk": 146, "conserved": 60}
+SORT_BYTES_PER_PASS = 32
 
 
 def _workload(rank=0):
@@ -300,6 +343,282 @@ def error_vs_oracle(prob, gpu, p):
             "tolerance": {"h_rho_omega_rel": 1e-5, "a_dudt_divv_max_norm": 2e-4},
             "sinks": int(len(sinks)), "neighbourhood": int(len(hood)),
             "oracle_s": round(secs, 1)}
+
+
+def phase_profile(prob, params, dev, steps=5, sort_passes=4):
+    """Per-phase device time of plain steps (sph_set_profiling: CUDA events
+    around each launch group) on a fresh copy of the workload, and the HBM
+    roofline of the memory-bound phases: algorithmic bytes per launch (bytes
+    per particle above x particles) over the measured time per launch."""
+    import torch
+    import paper_2511_11425_gb300 as sph
+    import dataclasses
+    peak, src = hbm_peak_gbs()
+    # every profiled step re-sorts (so the key, sort, permute and layout
+    # phases are timed) and is followed by the conserved totals
+    sim = sph.Simulation(prob, dataclasses.replace(params, resort_period=1), device=dev)
+    try:
+        for _ in range(3):
+            sim.step()
+        sph.sph_set_profiling(sim.ctx, True)
+        for _ in range(steps):
+            sim.step()
+            sim.conserved()
+        torch.cuda.synchronize(dev)
+        times = sph.sph_phase_times(sim.ctx)
+    finally:
+        sim.close()
+    per = {k: {"ms_per_launch": ms / n, "launches_per_step": n / steps}
+           for k, (ms, n) in times.items() if n > 0}
+    bpp = dict(HBM_BYTES_PER_PARTICLE, sort=SORT_BYTES_PER_PASS * sort_passes)
+    hbm = {}
+    for k, b in bpp.items():
+        if k not in per:
+            continue
+        nbytes = b * prob.n
+        ms = per[k]["ms_per_launch"]
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        hbm[k] = {"bound": "hbm", "bytes_per_particle": b, "bytes_per_launch": nbytes,
+                  "ms_per_launch": ms, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                  "frac": gbs / peak}
+    per_step = {k: ms / steps for k, (ms, n) in times.items() if n > 0}
+    return {"phase_ms_per_launch": per, "phase_ms_per_step": per_step, "hbm": hbm,
+            "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % src
+            if src == "measured" else "profiling recipe fallback 6.8 TB/s"}
+
+
+def _sampled_clusters(prob, centres, per):
+    lo, hi = np.array(prob.box_lo), np.array(prob.box_hi)
+    L = hi - lo
+    perd = np.array(prob.periodic, dtype=bool)
+    sinks = []
+    for c in centres:
+        d = prob.pos - np.asarray(c)
+        d[:, perd] -= L[perd] * np.round(d[:, perd] / L[perd])
+        sinks.extend(np.argsort((d * d).sum(1))[:per])
+    return np.unique(np.array(sinks))
+
+
+def _oracle_on(prob, sinks):
+    """FP64 oracle density + forces of `sinks`, exact for them (every particle
+    within 2.2 h_max of a sink solved by brute force over all N)."""
+    import oracle
+    p = oracle.Params(gamma=prob.gamma, alpha=prob.alpha, beta=prob.beta,
+                      box_lo=prob.box_lo, box_hi=prob.box_hi, periodic=prob.periodic)
+    lo, hi = np.array(prob.box_lo), np.array(prob.box_hi)
+    L = hi - lo
+    perd = np.array(prob.periodic, dtype=bool)
+    R = 2.2 * float(np.max(prob.h0))
+    keep = np.zeros(prob.n, dtype=bool)
+    for s_ in sinks:
+        d = prob.pos - prob.pos[s_]
+        d[:, perd] -= L[perd] * np.round(d[:, perd] / L[perd])
+        keep |= (d * d).sum(1) < R * R
+    hood = np.nonzero(keep)[0]
+    d = oracle.density_h(p, prob.pos, prob.m, prob.h0, hood)
+    h = np.zeros(prob.n)
+    rho = np.ones(prob.n)
+    om = np.ones(prob.n)
+    h[hood], rho[hood], om[hood] = d["h"], d["rho"], d["omega"]
+    f = oracle.forces(p, prob.pos, prob.vel, prob.m, h, rho, om, prob.u, sinks)
+    return {"h": h[sinks], "rho": rho[sinks], "omega": om[sinks], **f}
+
+
+def _field_errors(g, o, sinks):
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+
+    def norm(a, b):
+        return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+    return {"h": rel(g["h"][sinks], o["h"]), "rho": rel(g["rho"][sinks], o["rho"]),
+            "omega": rel(g["omega"][sinks], o["omega"]), "a": norm(g["a"][sinks], o["a"]),
+            "dudt_h": norm(g["dudt_h"][sinks], o["dudt_h"]),
+            "dudt_av": norm(g["dudt_av"][sinks], o["dudt_av"]),
+            "divv": norm(g["divv"][sinks], o["divv"])}
+
+
+def forms_precision(dev, kh_steps=5):
+    """The mixed-precision form against the plain FP64 form.
+
+    Sedov-Taylor 64^3 from t = 0 to t = 0.05 under the method's own global
+    step, both forms timed step by step (plain sph_step); at the end the
+    shock radius and energy error of each against the similarity solution.
+    Kelvin-Helmholtz 128^3: kh_steps timed steps of each form.  Accuracy:
+    both forms evaluated on the t = 0 state of each problem against the FP64
+    oracle on sampled sinks (at the shear interfaces and round the blast)."""
+    import torch
+    import paper_2511_11425_gb300 as sph
+    from paper_2511_11425_gb300 import inputs
+    from oracle.sedov import SedovSolution
+    out = {}
+    s = torch.cuda.current_stream(dev)
+
+    def run(prob, mode, t_end=None, nsteps=None):
+        params = sph.Params.for_problem(prob, precision=mode)
+        sim = sph.Simulation(prob, params, device=dev)
+        m64 = prob.m.astype(np.float32).astype(np.float64)
+        E0 = float((m64 * (prob.u + 0.5 * (prob.vel ** 2).sum(1))).sum())
+        ms, steps, dt = 0.0, 0, 0.0
+        try:
+            sim.step()  # first step (t = 0 evaluation) untimed
+            steps += 1
+            while (t_end is not None and sim.t < t_end) or (nsteps is not None and
+                                                             steps < nsteps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                dt = sim.step(0.0, s)
+                e1.record(s)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                steps += 1
+            g = sim.parts.numpy()
+        finally:
+            sim.close()
+        o = np.argsort(g["id"], kind="stable")
+        v = np.stack([g["v%d" % k][o] for k in range(3)], 1)
+        a = np.stack([g["a%d" % k][o] for k in range(3)], 1)
+        vs = v - 0.5 * dt * a
+        us = g["u"][o] - 0.5 * dt * (g["dudt_h"][o].astype(np.float64) + g["dudt_av"][o])
+        E1 = float((m64 * (us + 0.5 * (vs ** 2).sum(1))).sum())
+        x = np.stack([g["x%d" % k][o] for k in range(3)], 1)
+        timed = steps - 1
+        return {"particle_steps_per_s": prob.n * timed / (ms * 1e-3), "ms_per_step": ms / timed,
+                "timed_steps": timed, "t_end": sim.t, "energy_rel_error": abs(E1 - E0) / E0,
+                "x": x, "rho": g["rho"][o]}
+
+    sed = inputs.sedov(n=64)
+    sol = SedovSolution(sed.gamma)
+    res = {}
+    for mode in ("mixed", "fp64"):
+        r = run(sed, mode, t_end=0.05)
+        rr = np.linalg.norm(r.pop("x") - 0.5, axis=1)
+        rho = r.pop("rho")
+        edges = np.linspace(0.0, 0.5, 51)
+        idx = np.digitize(rr, edges) - 1
+        prof = np.array([rho[idx == k].mean() if np.any(idx == k) else 0.0 for k in range(50)])
+        r["shock_radius_peak"] = float(0.5 * (edges[np.argmax(prof)] + edges[np.argmax(prof) + 1]))
+        r["shock_radius_analytic"] = float(sol.shock_radius(r["t_end"]))
+        res[mode] = r
+        torch.cuda.empty_cache()
+    res["speedup_mixed_over_fp64"] = (res["mixed"]["particle_steps_per_s"] /
+                                      res["fp64"]["particle_steps_per_s"])
+    out["sedov64_to_t0.05"] = res
+    kh = inputs.kh(n=128)
+    res = {}
+    for mode in ("mixed", "fp64"):
+        r = run(kh, mode, nsteps=kh_steps)
+        r.pop("x")
+        r.pop("rho")
+        res[mode] = r
+        torch.cuda.empty_cache()
+    res["speedup_mixed_over_fp64"] = (res["mixed"]["particle_steps_per_s"] /
+                                      res["fp64"]["particle_steps_per_s"])
+    out["kh128"] = res
+    # accuracy of both forms on the t = 0 states
+    acc = {}
+    for name, prob, centres in (
+            ("sedov64", sed, [[0.5, 0.5, 0.5], [0.2, 0.7, 0.4]]),
+            ("kh128", kh, [[0.3, 0.25, 0.6], [0.7, 0.75, 0.2], [0.5, 0.5, 0.5]])):
+        sinks = _sampled_clusters(prob, centres, 16)
+        t0 = time.perf_counter()
+        o = _oracle_on(prob, sinks)
+        acc[name] = {"sinks": int(len(sinks)), "oracle_s": round(time.perf_counter() - t0, 1)}
+        for mode in ("mixed", "fp64"):
+            g = gpu_fields(prob, sph.Params.for_problem(prob, precision=mode), dev)
+            acc[name][mode] = _field_errors(g, o, sinks)
+    acc["tolerance"] = {"h_rho_omega_rel": 1e-5, "a_dudt_divv_max_norm": 2e-4}
+    out["error_vs_oracle_t0"] = acc
+    return out
+
+
+def forms_combined(dev, steps=3, warmup=3, nrec=12):
+    """The learned-seed + mixed-precision + batched form against the plain
+    form on the 256-instance workload: plain = one context per problem in
+    the FP64 form with the continuity seed, each stepped by sph_step in turn;
+    combined = one batch context in the mixed form, autotuned layout, the
+    step captured as a CUDA graph, the h iteration seeded by the network
+    trained on the batch's own first nrec steps.  Both start from the same
+    state and run the same number of steps."""
+    import torch
+    import paper_2511_11425_gb300 as sph
+    from paper_2511_11425_gb300 import autotune, inputs
+    probs = inputs.batch()
+    ntot = sum(q.n for q in probs)
+    s = torch.cuda.Stream(dev)
+    out = {"workload": "256 independent Sod and Sedov instances (batch workload)",
+           "particles": ntot, "steps": steps}
+    # plain form
+    sims = [sph.Simulation(q, sph.Params.for_problem(q, precision="fp64"), device=dev)
+            for q in probs]
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            for sim in sims:
+                sph.sph_step(sim.ctx, sim.parts, 0.0, s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            for sim in sims:
+                sph.sph_step(sim.ctx, sim.parts, 0.0, s)
+        e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["plain_fp64_per_problem"] = {"value": ntot * steps / (ms * 1e-3),
+                                     "ms_per_step": ms / steps}
+    for sim in sims:
+        sim.close()
+    del sims
+    torch.cuda.empty_cache()
+    # combined form
+    plist = [sph.Params.for_problem(q) for q in probs]
+    parts, offs = sph.Particles.from_problems(probs, dev)
+    tuner = autotune.Autotuner(os.path.join(tempfile.gettempdir(), "sph_autotune.json"), steps=2)
+    plist = tuner.tune(parts, plist, offs)
+    del parts
+    b = sph.BatchSimulation(probs, plist, device=dev)
+    try:
+        with torch.cuda.stream(s):
+            sph.sph_step(b.ctx, b.parts, 0.0, s)
+            sph.sph_mlp_record(b.ctx, True, capacity=2 << 20,
+                               stride=max(1, ntot * nrec // (2 << 20)))
+            for _ in range(nrec):
+                sph.sph_step(b.ctx, b.parts, 0.0, s)
+            sph.sph_mlp_record(b.ctx, False)
+            sph.sph_mlp_set_weights(b.ctx, inputs.mlp_init(3))
+            sph.sph_mlp_train(b.ctx, 1500, batch=8192, lr=2e-3, seed=1, stream=s)
+            sph.sph_mlp_train(b.ctx, 1500, batch=8192, lr=5e-4, seed=2, stream=s)
+            sph.sph_mlp_set_seed_mode(b.ctx, "mlp")
+            sph.sph_step(b.ctx, b.parts, 0.0, s)
+            b.capture(s)
+            for _ in range(warmup - 1):
+                sph.sph_graph_launch(b.ctx, s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                sph.sph_graph_launch(b.ctx, s)
+            e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        b.close()
+    out["learned_mixed_batched"] = {"value": ntot * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                                    "knobs": tuner.report["knobs"]}
+    out["speedup"] = out["learned_mixed_batched"]["value"] / out["plain_fp64_per_problem"]["value"]
+    # accuracy: both arithmetic forms on the t = 0 states of the smallest and
+    # largest instance against the oracle
+    sizes = np.array([q.n for q in probs])
+    acc = {}
+    for k in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        q = probs[k]
+        lo, hi = np.array(q.box_lo), np.array(q.box_hi)
+        c = [0.5 * (lo + hi), lo + 0.3 * (hi - lo)]
+        sinks = _sampled_clusters(q, c, 12)
+        o = _oracle_on(q, sinks)
+        acc["instance_%d_%s_%d" % (k, q.name, q.n)] = {
+            mode: _field_errors(gpu_fields(q, sph.Params.for_problem(q, precision=mode), dev),
+                                o, sinks) for mode in ("mixed", "fp64")}
+    out["error_vs_oracle_t0"] = acc
+    torch.cuda.empty_cache()
+    return out
 
 
 def combine_ranks(ms, n_local, steps, world):
@@ -634,8 +953,10 @@ def run_ours(args, rank, world, local_rank):
     flop_d = FLOPS_DENSITY_PAIR * dpairs
     flop_f = FLOPS_FORCE_PAIR * fpairs + FLOPS_FORCE_AV * fav
     rd = {"kernel": "k_density", "bound": "alu", "achieved": flop_d / (kd * 1e-3) / 1e12,
+          "achieved_at_estimate": FLOPS_DENSITY_PAIR_EST * dpairs / (kd * 1e-3) / 1e12,
           "ms_per_launch": kd / args.steps}
     rf = {"kernel": "k_forces", "bound": "alu", "achieved": flop_f / (kf * 1e-3) / 1e12,
+          "achieved_at_estimate": FLOPS_FORCE_PAIR_EST * fpairs / (kf * 1e-3) / 1e12,
           "ms_per_launch": kf / args.steps}
     dom, other = (rd, rf) if kd >= kf else (rf, rd)
     dom_file = "sph_density.cu" if dom is rd else "sph_forces.cu"
@@ -648,6 +969,10 @@ def run_ours(args, rank, world, local_rank):
             "peak_source": "derived: %d SMs (device properties) x 128 FP32 lanes x 2 flop x "
                            "2.07 GHz" % sms,
             "fp32_fma_measured_tflops": fma_measured,
+            "frac_at_estimate": dom["achieved_at_estimate"] / peak,
+            "flops_per_unit": ("26 per density pair per pass" if dom is rd else
+                               "61 per force pair + 24 per viscous pair") +
+                              " (tally); estimate 30 / 100",
             "ms_per_launch": dom["ms_per_launch"]}
     # the hardware view of the same kernel (ncu, committed summary): pipe
     # utilisation counts every issued instruction, rejected candidates included
@@ -655,7 +980,11 @@ def run_ours(args, rank, world, local_rank):
     if rec and "fma_pipe_active_pct" in rec:
         roof["ncu_pipes_active_pct"] = {"fma": rec["fma_pipe_active_pct"],
                                         "alu": rec["alu_pipe_active_pct"]}
-    other_line = {**other, "frac": other["achieved"] / peak}
+    other_line = {**other, "frac": other["achieved"] / peak,
+                  "frac_at_estimate": other["achieved_at_estimate"] / peak}
+    profile = None
+    if not args.no_profile:
+        profile = phase_profile(prob, params, dev)
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -703,9 +1032,13 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
     forms = None
     if world == 1 and not args.no_forms:
-        forms = {"batch": forms_batch(dev, max(2, min(args.steps, 5)), max(args.warmup, 3))}
+        forms = {"precision": forms_precision(dev)}
+        torch.cuda.empty_cache()
+        forms["batch"] = forms_batch(dev, max(2, min(args.steps, 5)), max(args.warmup, 3))
         torch.cuda.empty_cache()
         forms["learned"] = forms_learned(dev)
+        torch.cuda.empty_cache()
+        forms["combined"] = forms_combined(dev)
         torch.cuda.empty_cache()
     cpu = err = None
     if world == 1 and not args.no_cpu_baseline:
@@ -736,7 +1069,12 @@ def run_ours(args, rank, world, local_rank):
                     "forces_predict_walk_pairs_finalize_kdk_totals": phase["ms_forces"],
                     "of_which_force_kernel": phase["ms_force_kernel"],
                     "walks": phase["ms_walk"]},
-                "roofline": roof, "roofline_other": other_line, "e2e": e2e,
+                "roofline": roof, "roofline_other": other_line,
+                "roofline_hbm": profile["hbm"] if profile else None,
+                "phase_profile": ({"ms_per_step": profile["phase_ms_per_step"],
+                                   "note": "plain steps that all re-sort, totals after each",
+                                   "hbm_peak": profile["peak_source"]} if profile else None),
+                "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
                 "error_vs_oracle": err,
                 "forms": forms, "impl": "ours"}
@@ -756,11 +1094,15 @@ def main(argv=None):
                     help="fixed layout knobs instead of tuning, e.g. curve=morton,bucket_cell=3")
     ap.add_argument("--no-tune", action="store_true",
                     help="run the default layout knobs instead of autotuning them first")
-    ap.add_argument("--workload", default="sedov64", choices=sorted(WORKLOADS),
-                    help="the timed problem: the Sedov-Taylor blast on 64^3 particles "
-                         "(default) or the Kelvin-Helmholtz shear layer on 128^3")
+    ap.add_argument("--workload", default="kh128", choices=sorted(WORKLOADS),
+                    help="the timed problem: the Kelvin-Helmholtz shear layer on 128^3 "
+                         "particles (default) or the Sedov-Taylor blast on 64^3")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="skip the per-phase timing pass (HBM roofline of the "
+                         "memory-bound phases)")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the plain / batched / graph comparison on 256 instances")
+                    help="skip the form comparisons (FP64 against mixed precision, "
+                         "batched, learned seed, combined)")
     args = ap.parse_args(argv)
     _WORKLOAD[0] = args.workload
     rank = int(os.environ.get("RANK", "0"))

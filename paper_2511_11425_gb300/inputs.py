@@ -21,6 +21,9 @@ Problems (sizes as used by the tests and the benchmark):
   collision two spheres with rho ~ 1/r truncated at r=0.02, radii 1 and 0.5,
             approaching at Mach 3, impact parameter 0.5, open boundaries
   batch     list of independent sod / sedov instances with log-uniform sizes
+  soundwave linear travelling sound wave, N BCC (or cubic) cells along x and
+            16 across, A = 1e-3, gamma 5/3, Wendland C6 with 400 neighbours
+            (Sec. 3.1)
 
 Random numbers: SplitMix64 (Steele, Lea & Flood 2014) on the counter
 seed*2^32 + 4*index + stream, mapped to [0,1) with the top 53 bits.
@@ -163,6 +166,45 @@ def kh(n: int = 128, seed: int = 2511, gamma: float = 5.0 / 3.0, alpha: float = 
     u = P0 / ((gamma - 1.0) * rho)
     return Problem("kh", pos, vel, u, m, np.full(N, 2.5 * dx), lo, hi, per, gamma, alpha, beta,
                    extra={"dx": dx})
+
+
+def soundwave(N: int = 32, lattice: str = "bcc", A: float = 1e-3, ncross: int = 16,
+              gamma: float = 5.0 / 3.0, kernel: str = "wc6", n_ngb: float = 400.0,
+              alpha: float = 1.0, beta: float = 2.0) -> Problem:
+    """Linear travelling sound wave (Sec. 3.1): periodic box of unit length in
+    x and ncross cells of side 1/N in y and z, N cells in x (BCC: two
+    particles per cell, or a primitive cubic lattice), unit density and sound
+    speed (P0 = 1/gamma), equal masses.  Particles are displaced by
+    dx = -(A / 2 pi) cos(2 pi x - pi/2), which gives rho = 1 + A cos(2 pi x)
+    to first order; P = P0 (1 + gamma A cos(2 pi x)) fixes u, and the wave
+    travels in +x with v_x = A cos(2 pi x) (the sound speed times the
+    relative density amplitude)."""
+    if lattice not in ("bcc", "cubic"):
+        raise ValueError("lattice must be 'bcc' or 'cubic'")
+    d = 1.0 / N
+    base = _lattice(N, ncross, ncross, (0.0, 0.0, 0.0), d)
+    if lattice == "bcc":
+        pos = np.concatenate([base - 0.25 * d, base + 0.25 * d])
+    else:
+        pos = base
+    x0 = pos[:, 0].copy()
+    pos[:, 0] = x0 - A / (2.0 * math.pi) * np.cos(2.0 * math.pi * x0 - 0.5 * math.pi)
+    lo, hi, per = (0.0, 0.0, 0.0), (1.0, ncross * d, ncross * d), (1, 1, 1)
+    pos = _wrap(pos, lo, hi, per)
+    n = len(pos)
+    vol = 1.0 * (ncross * d) ** 2
+    m = np.full(n, vol / n)
+    xc = pos[:, 0]
+    rho = 1.0 + A * np.cos(2.0 * math.pi * xc)
+    P0 = 1.0 / gamma
+    P = P0 * (1.0 + gamma * A * np.cos(2.0 * math.pi * xc))
+    u = P / ((gamma - 1.0) * rho)
+    vel = np.zeros((n, 3))
+    vel[:, 0] = A * np.cos(2.0 * math.pi * xc)
+    spacing = (vol / n) ** (1.0 / 3.0)
+    h0 = np.full(n, (3.0 * n_ngb / (4.0 * math.pi)) ** (1.0 / 3.0) * spacing)
+    return Problem("soundwave", pos, vel, u, m, h0, lo, hi, per, gamma, alpha, beta,
+                   kernel=kernel, n_ngb=n_ngb, extra={"N": N, "A": A, "lattice": lattice})
 
 
 def uniform(n: int = 16, seed: int = 7, L: float = 1.0, vamp: float = 0.1, u0: float = 1.0,

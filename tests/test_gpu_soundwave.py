@@ -1,0 +1,68 @@
+"""Linear travelling sound wave (Sec. 3.1) on the GPU: after the wave has
+crossed the unit box once (t = 1 at unit sound speed) the density must be
+back to the initial wave, rho = 1 + A cos(2 pi (x - t)).  The L1 error
+(mean over particles of |rho_i - rho_exact(x_i)|) converges close to first
+order with the number N of BCC cells along the wave (the paper measures
+N^-0.898 for BCC, N^-0.769 for a primitive cubic lattice); the FP64 form
+gives the same error at these N, where FP32 round-off is far below the
+discretisation error."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_11425_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2511_11425_gb300 as m
+    m.lib()
+    return m
+
+
+def wave_l1(sph, N, precision="mixed", lattice="bcc"):
+    prob = inputs.soundwave(N, lattice=lattice)
+    A = prob.extra["A"]
+    sim = sph.Simulation(prob, sph.Params.for_problem(prob, precision=precision))
+    steps = 0
+    try:
+        while sim.t < 1.0:
+            sim.step()
+            steps += 1
+            assert steps < 20 * N
+        # a last density pass at the final positions
+        sph.sph_build_cells(sim.ctx, sim.parts)
+        sph.sph_density_h(sim.ctx, sim.parts)
+        g = sim.parts.numpy()
+    finally:
+        sim.close()
+    x = g["x0"]
+    exact = 1.0 + A * np.cos(2.0 * math.pi * (x - sim.t))
+    return float(np.mean(np.abs(g["rho"] - exact))), steps
+
+
+def test_soundwave_converges_at_first_order(sph):
+    Ns = (32, 64, 128)
+    l1 = []
+    for N in Ns:
+        e, steps = wave_l1(sph, N)
+        print("sound wave N=%d: L1 %.3e in %d steps" % (N, e, steps))
+        l1.append(e)
+    slope = np.polyfit(np.log(Ns), np.log(l1), 1)[0]
+    print("L1 slope %.3f (paper: -0.898 on BCC)" % slope)
+    assert np.all(np.diff(l1) < 0)
+    assert -1.5 < slope < -0.6
+    A = inputs.soundwave(32).extra["A"]
+    assert l1[0] < 0.5 * A
+
+
+def test_soundwave_fp64_form_matches_mixed_form(sph):
+    e_m, _ = wave_l1(sph, 64, "mixed")
+    e_d, _ = wave_l1(sph, 64, "fp64")
+    print("sound wave N=64: L1 mixed %.4e, FP64 %.4e" % (e_m, e_d))
+    assert abs(e_m - e_d) < 0.05 * e_d
