@@ -80,6 +80,16 @@ enum { SPH_CURVE_HILBERT = 0, SPH_CURVE_MORTON = 1 };
  * FP64 throughout the pair sums (the per-particle arrays of sph_particles
  * keep their types in both) */
 enum { SPH_PRECISION_MIXED = 0, SPH_PRECISION_FP64 = 1 };
+/* the density the forces use (Sec. 2.3.3): the kernel sum (Eq.
+ * Density_estimate), or the variant in which rho is state integrated with
+ * the mass conservation equation drho/dt = -rho div v.  In the evolved mode
+ * the density pass still finds h and Omega (its kernel sum goes to context
+ * scratch, not to p->rho); p->rho holds the evolved density between steps,
+ * started from the kernel sum by the first density pass of the context;
+ * sph_forces uses rho_pred = rho (1 - dt_old/2 div v_old) (the predictor,
+ * with the div v of the last force pass) and sph_kdk_step kicks rho with
+ * the rate -rho_pred div v like u. */
+enum { SPH_DENSITY_SUMMED = 0, SPH_DENSITY_EVOLVED = 1 };
 
 typedef struct {
     int32_t kernel;        /* SPH_KERNEL_*                                       */
@@ -111,6 +121,11 @@ typedef struct {
                               sums; SPH_PRECISION_FP64: every pair sum, the h
                               iteration and the force accumulators in FP64 (the
                               plain form); must agree across a batch            */
+    int32_t density_mode;  /* SPH_DENSITY_SUMMED (0, default): rho from the kernel
+                              sum; SPH_DENSITY_EVOLVED: rho integrated with the
+                              mass conservation equation (needs SPH_ENERGY_PDV);
+                              must agree across a batch                         */
+    int32_t reserved_;     /* must be 0                                          */
 } sph_params;
 
 typedef struct {

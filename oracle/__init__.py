@@ -18,6 +18,9 @@ What it computes, and where the paper defines it (arXiv:2511.11425):
 * kick-drift-kick with the embedded predictor (Sec. 2.3.6, single global
   time step)                                           -> ``Simulation.step``
 * conserved totals                                     -> ``conserved``
+* interface correction: kernel imbalance, exp(-I^2)-weighted kernel averages
+  of T and P, corrected density from the EOS (Sec. 2.3.4)
+                                                       -> ``interface_correction``
 
 The heavy loops are in ``sph_oracle.c`` (plain C, OpenMP over sinks); this
 file only marshals numpy arrays.  Exact Riemann and Sedov-Taylor solutions
@@ -103,6 +106,10 @@ def lib():
         L.orc_neighbours.restype = C.c_int64
         L.orc_forces.argtypes = [pp, C.c_int64, dp, dp, dp, dp, dp, dp, dp, C.c_int64, ip,
                                  dp, dp, dp, dp, dp, dp]
+        L.orc_imbalance.argtypes = [pp, C.c_int64, dp, dp, dp, i32p, C.c_double, C.c_int64,
+                                    ip, dp]
+        L.orc_interface_averages.argtypes = [pp, C.c_int64, dp, dp, dp, dp, dp, C.c_int64, ip,
+                                             dp, dp]
         _lib = L
     return _lib
 
@@ -222,6 +229,62 @@ def forces(params: Params, pos, vel, m, h, rho, omega, u, sinks=None):
     return out
 
 
+def imbalance_norm(kernel: str) -> float:
+    """alpha of Eq. Kernel_imbalance for `kernel`: the reciprocal of the raw
+    imbalance of a particle on a flat interface between two uniform
+    half-spaces of different material, 2 pi int_0^1 w(q) q^3 dq (the
+    numerator is 2 rho int_{z>0} z W dV = 2 rho pi h int w q^3 dq, the
+    denominator h rho), so that such a particle has I = 1.  Gauss-Legendre
+    quadrature of the kernel as the oracle evaluates it."""
+    x, wq = np.polynomial.legendre.leggauss(64)
+    q = 0.5 * (x + 1.0)
+    w, _ = kernel_eval(kernel, q)
+    return 1.0 / (2.0 * math.pi * 0.5 * float(np.sum(wq * w * q ** 3)))
+
+
+def imbalance(params: Params, pos, m, h, mat, alpha=None, sinks=None):
+    """Kernel imbalance I_i (Sec. 2.3.4, Eq. Kernel_imbalance)."""
+    pos = _d(pos).reshape(-1, 3)
+    m, h = _d(m), _d(h)
+    mat = np.ascontiguousarray(mat, dtype=np.int32)
+    n = len(m)
+    s, ns = _sinks(n, sinks)
+    a = imbalance_norm(params.kernel) if alpha is None else float(alpha)
+    out = np.empty(ns)
+    cp = params.c()
+    lib().orc_imbalance(C.byref(cp), n, _ptr(pos), _ptr(m), _ptr(h),
+                        mat.ctypes.data_as(C.POINTER(C.c_int32)), a, ns,
+                        _ptr(s, C.c_int64) if s is not None else None, _ptr(out))
+    return out
+
+
+def interface_correction(params: Params, pos, m, h, rho, u, mat, r_gas, alpha=None):
+    """Interface correction of Sec. 2.3.4 for every particle, ideal gases
+    with one gamma and a gas constant per material (T = (gamma-1) u / R):
+    I from Eq. Kernel_imbalance, Tbar and Pbar kernel averages weighted by
+    exp(-I^2), P~ = e^{-I^2} P + (1 - e^{-I^2}) Pbar (T~ likewise), and the
+    corrected density from the EOS, rho~ = P~ / (R T~)."""
+    pos = _d(pos).reshape(-1, 3)
+    m, h, rho, u = _d(m), _d(h), _d(rho), _d(u)
+    mat = np.ascontiguousarray(mat, dtype=np.int32)
+    R = np.asarray(r_gas, dtype=np.float64)[mat]
+    g = params.gamma
+    P = (g - 1.0) * rho * u
+    T = (g - 1.0) * u / R
+    I = imbalance(params, pos, m, h, mat, alpha)
+    eI = np.exp(-I * I)
+    n = len(m)
+    tbar = np.empty(n)
+    pbar = np.empty(n)
+    cp = params.c()
+    lib().orc_interface_averages(C.byref(cp), n, _ptr(pos), _ptr(h), _ptr(eI), _ptr(T), _ptr(P),
+                                 n, None, _ptr(tbar), _ptr(pbar))
+    Pt = eI * P + (1.0 - eI) * pbar
+    Tt = eI * T + (1.0 - eI) * tbar
+    return {"I": I, "eI": eI, "P": P, "T": T, "Tbar": tbar, "Pbar": pbar, "P_corr": Pt,
+            "T_corr": Tt, "rho_corr": Pt / (R * Tt)}
+
+
 def conserved(pos, vel, m, u):
     """Totals [M, Px, Py, Pz, Lx, Ly, Lz, E_kin, E_int] in FP64."""
     pos = _d(pos).reshape(-1, 3)
@@ -251,9 +314,17 @@ class Simulation:
     energy='pdv' kicks u with du/dt|H + du/dt|Pi; energy='isentropic' first
     moves u along its adiabat to the new density, u <- u (rho/rho_old)^(gamma-1),
     then kicks with du/dt|Pi only (Sec. 2.3.5, entropy-conserving update).
+
+    density='evolved' is the variant of Sec. 2.3.3 in which the density is
+    integrated with the mass conservation equation drho/dt = -rho div v
+    instead of taken from the kernel sum; the density pass still gives h and
+    Omega.  rho is then state like u: the first step starts it from the
+    kernel sum, the predictor moves it by half the old step with the rate
+    -rho div v_old (div v of the last force evaluation), the forces use that
+    predicted rho, and the two half kicks use the new rate -rho_pred div v.
     """
 
-    def __init__(self, params: Params, pos, vel, m, u, h0, energy="pdv"):
+    def __init__(self, params: Params, pos, vel, m, u, h0, energy="pdv", density="summed"):
         self.p = params
         self.x = _d(pos).reshape(-1, 3).copy()
         self.v = _d(vel).reshape(-1, 3).copy()
@@ -267,6 +338,13 @@ class Simulation:
         self.dt_old = 0.0
         self.t = 0.0
         self.energy = energy
+        if density not in ("summed", "evolved"):
+            raise ValueError("density must be 'summed' or 'evolved'")
+        if density == "evolved" and energy != "pdv":
+            raise ValueError("the evolved density is integrated with the PdV energy equation")
+        self.density = density
+        self.rho = None      # evolved density (state between steps)
+        self.divv_old = None  # div v of the last force evaluation
         self.last = None
 
     def step(self, dt_fixed=None):
@@ -279,13 +357,24 @@ class Simulation:
             self.u = self.u * (d["rho"] / self.rho_old) ** (p.gamma - 1.0)
         v_pred = self.v + 0.5 * self.dt_old * self.a
         u_pred = self.u + 0.5 * self.dt_old * self.udot
-        f = forces(p, self.x, v_pred, self.m, d["h"], d["rho"], d["omega"], u_pred)
+        if self.density == "evolved":
+            if self.rho is None:
+                self.rho = d["rho"].copy()
+                self.divv_old = np.zeros(len(self.m))
+            rho_f = self.rho * (1.0 - 0.5 * self.dt_old * self.divv_old)
+        else:
+            rho_f = d["rho"]
+        f = forces(p, self.x, v_pred, self.m, d["h"], rho_f, d["omega"], u_pred)
         udot = f["dudt_av"] if self.energy == "isentropic" else f["dudt_h"] + f["dudt_av"]
         self.v = self.v + 0.5 * self.dt_old * f["a"]
         self.u = self.u + 0.5 * self.dt_old * udot
         dt = float(dt_fixed) if dt_fixed else float(f["dt"].min())
         self.v = self.v + 0.5 * dt * f["a"]
         self.u = self.u + 0.5 * dt * udot
+        if self.density == "evolved":
+            rhodot = -rho_f * f["divv"]          # mass conservation equation
+            self.rho = self.rho + 0.5 * (self.dt_old + dt) * rhodot
+            self.divv_old = f["divv"]
         self.x = self.x + dt * self.v
         for a in range(3):
             if p.periodic[a]:
@@ -296,7 +385,7 @@ class Simulation:
         self.rho_old = d["rho"]
         self.dt_old = dt
         self.t += dt
-        self.last = {**d, **f, "v_pred": v_pred, "u_pred": u_pred}
+        self.last = {**d, **f, "v_pred": v_pred, "u_pred": u_pred, "rho_forces": rho_f}
         return dt
 
 

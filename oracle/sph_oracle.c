@@ -325,3 +325,62 @@ void orc_forces(const orc_params *p, int64_t n, const double *pos, const double 
         dt_out[s] = dta < dtc ? dta : dtc;
     }
 }
+
+/*
+ * Kernel imbalance of the listed sinks (Sec. 2.3.4, Eq. Kernel_imbalance):
+ *   I_i = alpha |sum_j kappa_ij (r_j - r_i) m_j W_ij(h_i)| / (h_i sum_j m_j W_ij(h_i))
+ * kappa_ij = +1 for particles of the same material, -1 otherwise; the sums
+ * run over every j (the i = j term adds m_i W(0,h_i) to the denominator only).
+ * r_j - r_i is the minimum image of x_j - x_i.
+ */
+void orc_imbalance(const orc_params *p, int64_t n, const double *pos, const double *m,
+                   const double *h, const int32_t *mat, double alpha, int64_t ns,
+                   const int64_t *sinks, double *imb_out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t i = sinks ? sinks[s] : s;
+        double v[3] = {0.0, 0.0, 0.0}, den = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3];
+            separation(p, pos + 3 * i, pos + 3 * j, d);  /* d = r_i - r_j */
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (r >= h[i]) continue;
+            double w = m[j] * W_of(p->kernel, r, h[i]);
+            double kappa = mat[j] == mat[i] ? 1.0 : -1.0;
+            for (int a = 0; a < 3; ++a) v[a] += kappa * (-d[a]) * w;
+            den += w;
+        }
+        double mag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        imb_out[s] = alpha * mag / (h[i] * den);
+    }
+}
+
+/*
+ * Kernel averages of temperature and pressure weighted by exp(-I_j^2)
+ * (Sec. 2.3.4, interface correction pass):
+ *   Tbar_i = sum_j T_j e^{-I_j^2} W_ij(h_i) / sum_j e^{-I_j^2} W_ij(h_i),
+ *   Pbar_i likewise with P_j; every j with r_ij < h_i, i itself included.
+ */
+void orc_interface_averages(const orc_params *p, int64_t n, const double *pos, const double *h,
+                            const double *eI, const double *T, const double *P, int64_t ns,
+                            const int64_t *sinks, double *tbar_out, double *pbar_out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t i = sinks ? sinks[s] : s;
+        double st = 0.0, sp = 0.0, sw = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3];
+            separation(p, pos + 3 * i, pos + 3 * j, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (r >= h[i]) continue;
+            double w = eI[j] * W_of(p->kernel, r, h[i]);
+            st += T[j] * w;
+            sp += P[j] * w;
+            sw += w;
+        }
+        tbar_out[s] = st / sw;
+        pbar_out[s] = sp / sw;
+    }
+}

@@ -27,6 +27,7 @@ KERNELS = {"wc2": 0, "wc4": 1, "wc6": 2, "m4": 3}
 ENERGY = {"pdv": 0, "isentropic": 1}
 CURVES = {"hilbert": 0, "morton": 1}
 PRECISIONS = {"mixed": 0, "fp64": 1}
+DENSITY_MODES = {"summed": 0, "evolved": 1}
 EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph_density_at",
            "sph_forces", "sph_kdk_step", "sph_step", "sph_step_host", "sph_reduce_conserved",
            "sph_set_dt_old", "sph_get_stats", "sph_last_error", "sph_version",
@@ -54,7 +55,8 @@ class c_params(C.Structure):
                 ("h_rel_tol", C.c_double), ("list_margin", C.c_double),
                 ("curve", C.c_int32), ("group_log", C.c_int32),
                 ("bucket_cell", C.c_double), ("group_cell", C.c_double),
-                ("resort_period", C.c_int32), ("precision", C.c_int32)]
+                ("resort_period", C.c_int32), ("precision", C.c_int32),
+                ("density_mode", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class c_particles(C.Structure):
@@ -174,6 +176,7 @@ class Params:
     group_cell: float = 6.0
     resort_period: int = 1
     precision: str = "mixed"
+    density: str = "summed"
 
     def c(self) -> c_params:
         p = c_params()
@@ -187,6 +190,7 @@ class Params:
         p.group_log = int(self.group_log)
         p.resort_period = int(self.resort_period)
         p.precision = PRECISIONS[self.precision]
+        p.density_mode = DENSITY_MODES[self.density]
         for a in range(3):
             p.box_lo[a] = float(self.box_lo[a])
             p.box_hi[a] = float(self.box_hi[a])

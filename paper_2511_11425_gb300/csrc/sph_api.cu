@@ -82,6 +82,10 @@ bool params_ok(const sph_params *prm)
         return false;
     if (prm->resort_period < 0 || prm->resort_period > 64) return false;
     if (prm->precision != SPH_PRECISION_MIXED && prm->precision != SPH_PRECISION_FP64) return false;
+    if (prm->density_mode != SPH_DENSITY_SUMMED && prm->density_mode != SPH_DENSITY_EVOLVED)
+        return false;
+    if (prm->density_mode == SPH_DENSITY_EVOLVED && prm->energy_mode != SPH_ENERGY_PDV) return false;
+    if (prm->reserved_ != 0) return false;
     const double kb = prm->bucket_cell > 0.0 ? prm->bucket_cell : kKappaBucket;
     const double kg = prm->group_cell > 0.0 ? prm->group_cell : kKappaGroup;
     if (!(kg >= kb) || !std::isfinite(kg)) return false;
@@ -227,6 +231,7 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.fvel, np);
     AL(c.fth, np);
     AL(c.ipos, np);
+    if (c.kp.evolved) AL(c.rho_sum, np);
     if (c.kp.fp64) {
         AL(c.pmd, np);
         AL(c.fveld, np);
@@ -275,7 +280,7 @@ void free_ctx(Ctx &c)
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
                     c.list_cnt, c.list_off, c.arena_used, c.list, c.redo, c.node, c.refit,
                     c.pm, c.pmd, c.fveld, c.fthd, c.acc64, c.ipos, c.fpos, c.fvel, c.fth,
-                    c.acc, c.accS, c.mumax, c.rho_old, c.h_seed, c.mirror};
+                    c.acc, c.accS, c.mumax, c.rho_sum, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mptrs[] = {c.mlp.w, c.mlp.m, c.mlp.v, c.mlp.frag, c.mlp.gpart, c.mlp.loss,
@@ -517,6 +522,12 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
         CK(launch_walk(c, *p, WALK_DENSITY, r, c.h_seed, s));
         CK(launch_density(c, *p, c.h_seed, r, 0, 0, nullptr, nullptr, s));
     }
+    // evolved density: the context's first density pass starts it from the
+    // kernel sum
+    if (c.kp.evolved && !c.rho_evolved_init) {
+        CK(cudaMemcpyAsync(p->rho, c.rho_sum, bytes, cudaMemcpyDeviceToDevice, s));
+        c.rho_evolved_init = true;
+    }
     CK(record(c, c.out_dens, s));  // rho, Omega, n_i, iterations are final
     CK(wait_late_inputs(c, s));  // everything before read x, m, h (and rho, id) only
     if (c.mlp.record) CK(launch_mlp_harvest(c, *p, s));
@@ -568,7 +579,8 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     for (int k = 1; k < ninst; ++k)
         if (prm[k].kernel != prm[0].kernel || prm[k].energy_mode != prm[0].energy_mode ||
             prm[k].max_newton != prm[0].max_newton || prm[k].h_rel_tol != prm[0].h_rel_tol ||
-            prm[k].list_margin != prm[0].list_margin || prm[k].precision != prm[0].precision)
+            prm[k].list_margin != prm[0].list_margin || prm[k].precision != prm[0].precision ||
+            prm[k].density_mode != prm[0].density_mode)
             return SPH_ERR_ARG;
     sph_ctx *ctx = new (std::nothrow) sph_ctx;
     if (!ctx) return SPH_ERR_ARG;
@@ -584,6 +596,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.kp.h_rel_tol = (float)prm[0].h_rel_tol;
     c.kp.margin = (float)prm[0].list_margin;
     c.kp.fp64 = prm[0].precision == SPH_PRECISION_FP64 ? 1 : 0;
+    c.kp.evolved = prm[0].density_mode == SPH_DENSITY_EVOLVED ? 1 : 0;
     c.resort_period = prm[0].resort_period > 0 ? prm[0].resort_period : 1;
     c.kp.ninst = ninst;
     const Sizes z = layout_sizes(counts, c.prm);
@@ -886,6 +899,9 @@ extern "C" sph_status sph_graph_capture(sph_ctx *ctx, sph_particles *p, double d
 namespace {
 sph_status capture_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool full)
 {
+    // the start of the evolved density is a one-off copy, not part of a step
+    if (c.kp.evolved && !c.rho_evolved_init)
+        return failf(c, SPH_ERR_STATE, "evolved density: step once before recording a step");
     const uint64_t l0 = c.launches;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     c.err.clear();
@@ -978,7 +994,8 @@ namespace {
 struct ArrDesc {
     size_t off;   // offset of the pointer member in sph_particles
     size_t elem;  // element size
-    int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode, 0 never
+    int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode or with the
+                  // evolved density, 3 with the evolved density, 0 never
     int late;     // first read after the density phase (1): copied in beside the step
     int out;      // final after the density phase (1), after the forces (2), at the end (0)
     int sorted;   // changed only by a re-sort (1: m, id), so unchanged by a refitting step
@@ -1001,7 +1018,7 @@ const ArrDesc kArrays[] = {
     {offsetof(sph_particles, a) + 2 * sizeof(float *), 4, 1, 1, 2, 0, 0},
     {offsetof(sph_particles, dudt_h), 4, 1, 1, 2, 0, 0},
     {offsetof(sph_particles, dudt_av), 4, 1, 1, 2, 0, 0},
-    {offsetof(sph_particles, divv), 4, 0, 0, 2, 0, 0},
+    {offsetof(sph_particles, divv), 4, 3, 1, 2, 0, 0},
     {offsetof(sph_particles, dt_i), 4, 0, 0, 2, 0, 0},
     {offsetof(sph_particles, nngb), 2, 0, 0, 1, 0, 0},
     {offsetof(sph_particles, iters), 1, 0, 0, 1, 0, 0},
@@ -1078,12 +1095,13 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
                         bool skip_sorted = false)
 {
     const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC;
+    const bool evo = c.kp.evolved != 0;
     CopyJob job;
     int na = 0;
     unsigned long long most = 0;
     int64_t b_all = 0;
     for (const ArrDesc &d : kArrays) {
-        if (in && (d.in == 0 || (d.in == 2 && !isen))) continue;
+        if (in && (d.in == 0 || (d.in == 2 && !isen && !evo) || (d.in == 3 && !evo))) continue;
         if (in && ((part == 1 && d.late) || (part == 2 && !d.late))) continue;
         if (!in && part > 0 && d.out != part % 3) continue;
         if (skip_sorted && (in ? d.sort_in : d.sorted)) continue;

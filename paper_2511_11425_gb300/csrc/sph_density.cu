@@ -567,10 +567,13 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     cudaMemsetAsync(c.gflag, 0, sizeof(unsigned) * (size_t)kp.ng, s);
     c.launches += 1;
     const int pr = prof_begin(c, s, SPH_PHASE_DENSITY);
+    // the evolved density mode keeps p.rho as state: the kernel sum goes to
+    // scratch (h and Omega to p as always)
+    float *rho_out = kp.evolved ? c.rho_sum : p.rho;
 #define SPH_DENSITY_LAUNCH(EMIT_, D64_)                                                      \
     k_density<KT, EMIT_, D64_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                                 \
         kp, c.inst, c.pm, c.pmd, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list,     \
-        c.origin, gids, gcnt, (float *)h_seed, p.h, p.rho, p.omega, p.nngb, p.iters, fixed_h,     \
+        c.origin, gids, gcnt, (float *)h_seed, p.h, rho_out, p.omega, p.nngb, p.iters, fixed_h,   \
         (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st)
     SPH_KERNEL_DISPATCH(kp.kernel, KT,
         if (kp.fp64) {

@@ -57,7 +57,7 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
                           const double *__restrict__ dts, float4 *fpos, float4 *fvel, float4 *fth,
                           int4 *ipos, float4 *acc, double *accS, unsigned *mumax, unsigned *dtmin,
                           double4_16a *fveld, double4_16a *fthd, double4_16a *acc64,
-                          DevStatus *st)
+                          const float *__restrict__ divv_old, DevStatus *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kp.ninst) dtmin[i] = 0x7f800000u;  // +inf
@@ -77,6 +77,9 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
         uu += hdt * ud;
     }
     float r = rho[i], om = omega[i], hi = h[i];
+    // evolved density: predicted like u, with the rate -rho div v of the
+    // last force pass
+    if (kp.evolved && hdt > 0.0) r = (float)((double)r * (1.0 - hdt * (double)divv_old[i]));
     float P = (gamma - 1.f) * r * (float)uu;
     float c = sqrtf(gamma * P / r);
     float A = P / (om * r * r);
@@ -624,7 +627,7 @@ cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
                                               p.h, p.rho, p.omega, c.pm, c.dts, c.fpos, c.fvel,
                                               c.fth, c.ipos, c.acc, c.accS, c.mumax, c.dtmin,
                                               c.kp.fp64 ? c.fveld : nullptr, c.fthd, c.acc64,
-                                              c.st);
+                                              p.divv, c.st);
     prof_end(c, s, pr);
     return cudaGetLastError();
 }

@@ -49,7 +49,8 @@ __device__ __forceinline__ void kdk_particle(
     double *y, double *z, double *vx, double *vy, double *vz, double *u, float *h,
     const float *__restrict__ ax, const float *__restrict__ ay, const float *__restrict__ az,
     const float *__restrict__ dudt_h, const float *__restrict__ dudt_av, int energy_mode,
-    const double *__restrict__ dts, float h_next)
+    const double *__restrict__ dts, float h_next, float *rho, const float4 *__restrict__ fth,
+    const float *__restrict__ divv)
 {
     const int k = pinst[i];
     const Inst &I = insts[k];
@@ -64,6 +65,9 @@ __device__ __forceinline__ void kdk_particle(
     vy[i] = v1;
     vz[i] = v2;
     u[i] += kick * ud;
+    // evolved density (mass conservation equation), kicked like u with the
+    // rate -rho_pred div v of this step's force pass
+    if (rho) rho[i] = (float)((double)rho[i] - kick * (double)fth[i].z * (double)divv[i]);
     double p[3] = {x[i] + dt_new * v0, y[i] + dt_new * v1, z[i] + dt_new * v2};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -101,7 +105,7 @@ __global__ void k_kdk(KParams kp, int n, const Inst *__restrict__ insts,
                       const float *__restrict__ az, const float *__restrict__ dudt_h,
                       const float *__restrict__ dudt_av, const float *__restrict__ divv,
                       const double *__restrict__ dts, const float *__restrict__ corr,
-                      const DevStatus *st)
+                      float *rho_ev, const float4 *__restrict__ fth, const DevStatus *st)
 {
     // an error raised earlier in the step leaves the state as it was
     if (st->code != 0) return;
@@ -111,7 +115,7 @@ __global__ void k_kdk(KParams kp, int n, const Inst *__restrict__ insts,
     if (CORR) e += corr[i];
     const float f = expf(e);
     kdk_particle(i, insts, pinst, x, y, z, vx, vy, vz, u, h, ax, ay, az, dudt_h, dudt_av,
-                 kp.energy_mode, dts, h[i] * fminf(fmaxf(f, 0.5f), 2.f));
+                 kp.energy_mode, dts, h[i] * fminf(fmaxf(f, 0.5f), 2.f), rho_ev, fth, divv);
 }
 
 
@@ -190,11 +194,13 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
     if (corr)
         k_kdk<true><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
                                       p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
-                                      p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr, c.st);
+                                      p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr,
+                                      c.kp.evolved ? p.rho : nullptr, c.fth, c.st);
     else
         k_kdk<false><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
                                        p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
-                                       p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr, c.st);
+                                       p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr,
+                                       c.kp.evolved ? p.rho : nullptr, c.fth, c.st);
     k_dt_shift<<<(ni + 127) / 128, 128, 0, s>>>(ni, c.dts, c.st);
     prof_end(c, s, pr);
     return cudaGetLastError();

@@ -138,6 +138,7 @@ struct KParams {
     int key_passes;      // 8-bit radix passes over (instance, curve index) keys
     int any_open;        // some instance has an open axis
     int fp64;            // SPH_PRECISION_FP64: pair sums and h iteration in FP64
+    int evolved;         // SPH_DENSITY_EVOLVED: rho is state (mass conservation)
     float h_rel_tol, margin;
 };
 
@@ -216,6 +217,8 @@ struct Ctx {
     double *accS = nullptr;
     unsigned *mumax = nullptr;
     float *rho_old = nullptr;
+    float *rho_sum = nullptr;         // evolved density mode: the density pass's kernel sum
+    bool rho_evolved_init = false;    // p->rho holds an evolved density
     float *h_seed = nullptr;          // density seeds / re-walk seeds
 
     // lists: kWalkCap slots per group, then an overflow arena of arena_cap
