@@ -101,6 +101,8 @@ UNIT = "particle-steps/s"
 WORKLOADS = {
     "sedov64": "sedov_taylor_64^3 (262,144 particles, periodic unit box, t from 0)",
     "kh128": "kelvin_helmholtz_128^3 (2,097,152 particles, periodic unit box, t from 0)",
+    "kh96": "kelvin_helmholtz_96^3 (884,736 particles, periodic unit box, t from 0; the "
+            "size of the profiler captures)",
 }
 _WORKLOAD = ["kh128"]  # set from --workload
 HBM_PEAK_GBS_FALLBACK = 6800.0
@@ -139,8 +141,8 @@ SORT_BYTES_PER_PASS = 32
 
 def _workload(rank=0):
     from paper_2511_11425_gb300 import inputs
-    if _WORKLOAD[0] == "kh128":
-        return inputs.kh(n=128, seed=2511 + rank)
+    if _WORKLOAD[0] in ("kh128", "kh96"):
+        return inputs.kh(n=int(_WORKLOAD[0][2:]), seed=2511 + rank)
     return inputs.sedov(n=64, seed=2511 + rank)
 
 
@@ -1096,7 +1098,8 @@ def main(argv=None):
                     help="run the default layout knobs instead of autotuning them first")
     ap.add_argument("--workload", default="kh128", choices=sorted(WORKLOADS),
                     help="the timed problem: the Kelvin-Helmholtz shear layer on 128^3 "
-                         "particles (default) or the Sedov-Taylor blast on 64^3")
+                         "particles (default), on 96^3 (profiler captures), or the "
+                         "Sedov-Taylor blast on 64^3")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the per-phase timing pass (HBM roofline of the "
                          "memory-bound phases)")

@@ -125,7 +125,16 @@ typedef struct {
                               sum; SPH_DENSITY_EVOLVED: rho integrated with the
                               mass conservation equation (needs SPH_ENERGY_PDV);
                               must agree across a batch                         */
-    int32_t reserved_;     /* must be 0                                          */
+    int32_t interface_correction; /* 1: the interface correction of Sec. 2.3.4
+                              (mixed precision, summed density; must agree
+                              across a batch); 0: off                         */
+    double  ic_alpha;      /* normalisation of the kernel imbalance (Eq.
+                              Kernel_imbalance); 0 = the kernel's own value, at
+                              which a particle on a flat interface between two
+                              uniform materials has I = 1                     */
+    double  r_gas[4];      /* gas constant of materials 0..3 (ideal gases with
+                              the instance's gamma: T = (gamma-1) u / R,
+                              rho = P / (R T)); used by the interface correction */
 } sph_params;
 
 typedef struct {
@@ -146,6 +155,10 @@ typedef struct {
     uint16_t *nngb;        /* neighbours j != i with r_ij < h_i (sph_density_h)  */
     uint8_t  *iters;       /* Newton iterations taken (sph_density_h)            */
     int64_t  *id;          /* caller's particle ids, permuted with the particles */
+    uint8_t  *mat;         /* material of each particle (index into
+                              sph_params.r_gas), permuted with the particles;
+                              read only with the interface correction on (may
+                              be NULL otherwise)                               */
 } sph_particles;
 
 /* Host-side view of the same state for sph_step_host: HOST pointers, same
@@ -301,6 +314,38 @@ sph_status sph_kdk_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double 
  */
 sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_used,
                     void *stream);
+
+/*
+ * sph_step_rungs: one global step dt0 with hierarchical power-of-two time
+ * steps (Sec. 2.3.6, Time integration).  The step is cut into 2^max_rung
+ * substeps of dt0 / 2^max_rung; a particle on rung r steps 2^(max_rung - r)
+ * substeps at a time and is active on the substeps that its period
+ * divides.  Every substep runs the density pass for all particles, predicts
+ * every particle's v and u to the substep time (v + (tau - T/2) a, tau the
+ * time since its last step boundary, T its period; v, u are half-step
+ * values), evaluates the forces (all pairs that have an active particle take
+ * effect: inactive particles keep their derivatives), kicks the active
+ * particles (closing kick over T/2, new rung r = ceil(log2(dt0 / dt_i))
+ * clamped to [0, max_rung] and raised to (largest rung of the particle's
+ * force partners) - 2, a lower rung only to one whose period divides the
+ * substep, opening kick over half the new period) and drifts every particle.
+ * Rungs start at 0 and persist across calls (sph_get_rungs reads them, in
+ * the particles' current order); a run uses one max_rung (SPH_ERR_STATE
+ * otherwise) and either only hierarchical or only global steps
+ * (sph_set_dt_old(ctx, 0) does not reset the rungs).  The first substep
+ * re-sorts the particles, the others refit the bounds.  Mixed precision and
+ * summed density only (SPH_ERR_ARG); not with the learned seed
+ * (SPH_ERR_STATE).  A failed substep leaves x, v, u as they were after the
+ * substeps before it.  Synchronous (one status read at the end).  FastGas
+ * (density passes for the active particles' neighbourhoods only) is not
+ * built: every substep runs the density pass for every particle.
+ */
+sph_status sph_step_rungs(sph_ctx *ctx, sph_particles *p, double dt0, int32_t max_rung,
+                          void *stream);
+
+/* sph_get_rungs: rung of each of the first n particles (HOST array, current
+ * particle order); zeros before the first sph_step_rungs.  Synchronous. */
+sph_status sph_get_rungs(sph_ctx *ctx, uint8_t *out, int64_t n);
 
 /*
  * sph_step_host: sph_step on HOST arrays.  Copies the arrays a step reads

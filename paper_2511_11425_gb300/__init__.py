@@ -35,6 +35,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_graph_capture", "sph_graph_launch", "sph_graph_totals", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
            "sph_mlp_load_samples", "sph_bucket_layout", "sph_set_list_arena", "sph_set_profiling",
+           "sph_step_rungs", "sph_get_rungs",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
 MLP_NPARAM = 1249
 SEED_MODES = {"analytic": 0, "mlp": 1}
@@ -56,7 +57,8 @@ class c_params(C.Structure):
                 ("curve", C.c_int32), ("group_log", C.c_int32),
                 ("bucket_cell", C.c_double), ("group_cell", C.c_double),
                 ("resort_period", C.c_int32), ("precision", C.c_int32),
-                ("density_mode", C.c_int32), ("reserved_", C.c_int32)]
+                ("density_mode", C.c_int32), ("interface_correction", C.c_int32),
+                ("ic_alpha", C.c_double), ("r_gas", C.c_double * 4)]
 
 
 class c_particles(C.Structure):
@@ -64,7 +66,8 @@ class c_particles(C.Structure):
                 ("u", C.c_void_p), ("m", C.c_void_p), ("h", C.c_void_p), ("rho", C.c_void_p),
                 ("omega", C.c_void_p), ("a", C.c_void_p * 3), ("dudt_h", C.c_void_p),
                 ("dudt_av", C.c_void_p), ("divv", C.c_void_p), ("dt_i", C.c_void_p),
-                ("nngb", C.c_void_p), ("iters", C.c_void_p), ("id", C.c_void_p)]
+                ("nngb", C.c_void_p), ("iters", C.c_void_p), ("id", C.c_void_p),
+                ("mat", C.c_void_p)]
 
 
 class c_stats(C.Structure):
@@ -115,6 +118,8 @@ def lib():
         L.sph_set_dt_old.argtypes = [vp, dbl]
         L.sph_set_list_arena.argtypes = [vp, i64]
         L.sph_set_profiling.argtypes = [vp, C.c_int32]
+        L.sph_step_rungs.argtypes = [vp, pp, dbl, C.c_int32, vp]
+        L.sph_get_rungs.argtypes = [vp, vp, i64]
         fp = C.POINTER(C.c_float)
         L.sph_mlp_set_weights.argtypes = [vp, fp, i64]
         L.sph_mlp_get_weights.argtypes = [vp, fp, i64]
@@ -177,6 +182,9 @@ class Params:
     resort_period: int = 1
     precision: str = "mixed"
     density: str = "summed"
+    interface_correction: bool = False
+    ic_alpha: float = 0.0
+    r_gas: tuple = (1.0, 1.0, 1.0, 1.0)
 
     def c(self) -> c_params:
         p = c_params()
@@ -191,6 +199,10 @@ class Params:
         p.resort_period = int(self.resort_period)
         p.precision = PRECISIONS[self.precision]
         p.density_mode = DENSITY_MODES[self.density]
+        p.interface_correction = 1 if self.interface_correction else 0
+        p.ic_alpha = float(self.ic_alpha)
+        for k in range(4):
+            p.r_gas[k] = float(self.r_gas[k])
         for a in range(3):
             p.box_lo[a] = float(self.box_lo[a])
             p.box_hi[a] = float(self.box_hi[a])
@@ -227,6 +239,7 @@ class Particles:
         self.t["nngb"] = torch.zeros(self.n, dtype=torch.int16, **kw)
         self.t["iters"] = torch.zeros(self.n, dtype=torch.uint8, **kw)
         self.t["id"] = torch.arange(self.n, dtype=torch.int64, **kw)
+        self.t["mat"] = torch.zeros(self.n, dtype=torch.uint8, **kw)
 
     @classmethod
     def from_problem(cls, prob, device="cuda", pin=False):
@@ -238,6 +251,8 @@ class Particles:
         p.t["u"].copy_(torch.from_numpy(prob.u.copy()))
         p.t["m"].copy_(torch.from_numpy(prob.m.astype("float32")))
         p.t["h"].copy_(torch.from_numpy(prob.h0.astype("float32")))
+        if "mat" in prob.extra:
+            p.t["mat"].copy_(torch.from_numpy(prob.extra["mat"].astype("uint8")))
         return p
 
     @classmethod
@@ -268,7 +283,7 @@ class Particles:
             s.v[a] = t["v%d" % a].data_ptr()
             s.a[a] = t["a%d" % a].data_ptr()
         for f in ("u", "m", "h", "rho", "omega", "dudt_h", "dudt_av", "divv", "dt_i", "nngb",
-                  "iters", "id"):
+                  "iters", "id", "mat"):
             setattr(s, f, t[f].data_ptr())
         return s
 
@@ -546,6 +561,21 @@ def sph_phase_times(ctx):
     st = c_stats()
     _check(ctx, lib().sph_get_stats(ctx, C.byref(st)))
     return {name: (st.phase_ms[k], int(st.phase_launches[k])) for k, name in enumerate(PHASES)}
+
+
+def sph_step_rungs(ctx, parts: Particles, dt0: float, max_rung: int, stream=None):
+    """One global step dt0 with hierarchical power-of-two substeps."""
+    s = parts.c()
+    _check(ctx, lib().sph_step_rungs(ctx, C.byref(s), float(dt0), int(max_rung),
+                                     _stream(stream)))
+
+
+def sph_get_rungs(ctx, n: int):
+    """Rungs of the first n particles (current order) as a numpy uint8 array."""
+    import numpy as np
+    a = np.zeros(int(n), dtype=np.uint8)
+    _check(ctx, lib().sph_get_rungs(ctx, C.c_void_p(a.ctypes.data), int(n)))
+    return a
 
 
 def sph_set_list_arena(ctx, entries: int):

@@ -85,7 +85,15 @@ bool params_ok(const sph_params *prm)
     if (prm->density_mode != SPH_DENSITY_SUMMED && prm->density_mode != SPH_DENSITY_EVOLVED)
         return false;
     if (prm->density_mode == SPH_DENSITY_EVOLVED && prm->energy_mode != SPH_ENERGY_PDV) return false;
-    if (prm->reserved_ != 0) return false;
+    if (prm->interface_correction != 0 && prm->interface_correction != 1) return false;
+    if (prm->interface_correction) {
+        // Sec. 2.3.4: not with the evolved density; built for the mixed form
+        if (prm->density_mode != SPH_DENSITY_SUMMED || prm->precision != SPH_PRECISION_MIXED)
+            return false;
+        if (!(prm->ic_alpha >= 0.0) || !std::isfinite(prm->ic_alpha)) return false;
+        for (int k = 0; k < 4; ++k)
+            if (!(prm->r_gas[k] > 0.0) || !std::isfinite(prm->r_gas[k])) return false;
+    }
     const double kb = prm->bucket_cell > 0.0 ? prm->bucket_cell : kKappaBucket;
     const double kg = prm->group_cell > 0.0 ? prm->group_cell : kKappaGroup;
     if (!(kg >= kb) || !std::isfinite(kg)) return false;
@@ -140,6 +148,12 @@ Inst inst_params(const sph_params &prm)
     for (int a = 0; a < 3; ++a)
         I.LQ[a] = I.periodic[a] ? (unsigned)std::llrint((prm.box_hi[a] - prm.box_lo[a]) / qx) : 0u;
     I.eps_abs = (float)(4.0 * std::ldexp(1.0, -23) * fmax(maxext, maxabs));
+    // kernel-imbalance normalisation: 1 / (2 pi int_0^1 w(q) q^3 dq), the
+    // value at which a particle on a flat interface between two uniform
+    // materials has I = 1 (closed forms of the four kernels)
+    const double ic_norm[4] = {24.0 / 5.0, 192.0 / 35.0, 128.0 / 21.0, 140.0 / 31.0};
+    I.ic_alpha = (float)(prm.ic_alpha > 0.0 ? prm.ic_alpha : ic_norm[prm.kernel & 3]);
+    for (int k = 0; k < 4; ++k) I.r_gas[k] = (float)prm.r_gas[k];
     return I;
 }
 
@@ -232,6 +246,10 @@ sph_status allocate(Ctx &c, const Sizes &cap, int ninst)
     AL(c.fth, np);
     AL(c.ipos, np);
     if (c.kp.evolved) AL(c.rho_sum, np);
+    if (c.kp.ic) {
+        AL(c.ic_e, np);
+        AL(c.ic_pt, np);
+    }
     if (c.kp.fp64) {
         AL(c.pmd, np);
         AL(c.fveld, np);
@@ -280,7 +298,7 @@ void free_ctx(Ctx &c)
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
                     c.list_cnt, c.list_off, c.arena_used, c.list, c.redo, c.node, c.refit,
                     c.pm, c.pmd, c.fveld, c.fthd, c.acc64, c.ipos, c.fpos, c.fvel, c.fth,
-                    c.acc, c.accS, c.mumax, c.rho_sum, c.rho_old, c.h_seed, c.mirror};
+                    c.acc, c.accS, c.mumax, c.rho_sum, c.ic_e, c.ic_pt, c.rung, c.rmax, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mptrs[] = {c.mlp.w, c.mlp.m, c.mlp.v, c.mlp.frag, c.mlp.gpart, c.mlp.loss,
@@ -491,6 +509,8 @@ sph_status ensure_layout(Ctx &c, const sph_particles *p)
     if (p->n > c.capacity)
         return failf(c, SPH_ERR_ARG, "n = %lld exceeds the capacity %lld", (long long)p->n,
                      (long long)c.capacity);
+    if (c.kp.ic && p->n > 0 && !p->mat)
+        return failf(c, SPH_ERR_ARG, "the interface correction needs material ids (p->mat)");
     if (c.prm.size() > 1) {
         if (p->n != c.kp.n)
             return failf(c, SPH_ERR_ARG, "a batch context needs exactly %d particles", c.kp.n);
@@ -536,20 +556,29 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
     return SPH_OK;
 }
 
-sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed)
+sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed,
+                    const RungArgs *ra = nullptr)
 {
-    // predictor + EOS on the side stream while the force walk runs here
     if (timed) CK(record(c, c.kev[3], s));
-    CK(cudaEventRecord(c.fork, s));
-    CK(cudaStreamWaitEvent(c.side, c.fork, 0));
-    CK(launch_predict(c, *p, c.side));
-    CK(cudaEventRecord(c.join, c.side));
-    CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
-    CK(cudaStreamWaitEvent(s, c.join, 0));
+    if (c.kp.ic) {
+        // interface correction (Sec. 2.3.4): predictor, then the correction
+        // pass over the density lists, before the force walk replaces them
+        CK(launch_predict(c, *p, s, ra));
+        CK(launch_interface(c, *p, s));
+        CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
+    } else {
+        // predictor + EOS on the side stream while the force walk runs here
+        CK(cudaEventRecord(c.fork, s));
+        CK(cudaStreamWaitEvent(c.side, c.fork, 0));
+        CK(launch_predict(c, *p, c.side, ra));
+        CK(cudaEventRecord(c.join, c.side));
+        CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
+        CK(cudaStreamWaitEvent(s, c.join, 0));
+    }
     if (timed) CK(record(c, c.kev[4], s));
-    CK(launch_forces(c, *p, s));
+    CK(launch_forces(c, *p, s, ra));
     if (timed) CK(record(c, c.kev[5], s));
-    CK(launch_finalize(c, *p, s));
+    CK(launch_finalize(c, *p, s, ra));
     CK(record(c, c.out_force, s));  // a, du/dt, div v, dt_i are final
     return SPH_OK;
 }
@@ -580,7 +609,8 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
         if (prm[k].kernel != prm[0].kernel || prm[k].energy_mode != prm[0].energy_mode ||
             prm[k].max_newton != prm[0].max_newton || prm[k].h_rel_tol != prm[0].h_rel_tol ||
             prm[k].list_margin != prm[0].list_margin || prm[k].precision != prm[0].precision ||
-            prm[k].density_mode != prm[0].density_mode)
+            prm[k].density_mode != prm[0].density_mode ||
+            prm[k].interface_correction != prm[0].interface_correction)
             return SPH_ERR_ARG;
     sph_ctx *ctx = new (std::nothrow) sph_ctx;
     if (!ctx) return SPH_ERR_ARG;
@@ -597,6 +627,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.kp.margin = (float)prm[0].list_margin;
     c.kp.fp64 = prm[0].precision == SPH_PRECISION_FP64 ? 1 : 0;
     c.kp.evolved = prm[0].density_mode == SPH_DENSITY_EVOLVED ? 1 : 0;
+    c.kp.ic = prm[0].interface_correction;
     c.resort_period = prm[0].resort_period > 0 ? prm[0].resort_period : 1;
     c.kp.ninst = ninst;
     const Sizes z = layout_sizes(counts, c.prm);
@@ -727,6 +758,8 @@ extern "C" sph_status sph_forces(sph_ctx *ctx, sph_particles *p, void *stream)
     if (!ctx) return SPH_ERR_ARG;
     Ctx &c = ctx->c;
     if (!particles_ok(p)) return failf(c, SPH_ERR_ARG, "sph_forces: NULL array");
+    if (c.kp.ic && p->n > 0 && !p->mat)
+        return failf(c, SPH_ERR_ARG, "the interface correction needs material ids (p->mat)");
     if (!c.density_valid || p->n != c.n_built)
         return failf(c, SPH_ERR_STATE, "sph_forces needs sph_density_h on these particles first");
     if (p->n == 0) {
@@ -863,6 +896,78 @@ extern "C" sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, 
     return rc;
 }
 
+extern "C" sph_status sph_step_rungs(sph_ctx *ctx, sph_particles *p, double dt0, int32_t max_rung,
+                                     void *stream)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    sph_status rc = ensure_layout(c, p);
+    if (rc) return rc;
+    if (!(dt0 > 0.0) || std::isinf(dt0))
+        return failf(c, SPH_ERR_ARG, "sph_step_rungs: dt0 must be positive and finite");
+    if (max_rung < 0 || max_rung > 20)
+        return failf(c, SPH_ERR_ARG, "sph_step_rungs: max_rung must be in [0, 20]");
+    if (c.kp.fp64 || c.kp.evolved)
+        return failf(c, SPH_ERR_ARG, "sph_step_rungs: mixed precision and summed density only");
+    if (c.mlp.record || c.mlp.seed_mode != SPH_SEED_ANALYTIC)
+        return failf(c, SPH_ERR_STATE, "sph_step_rungs: the learned seed is for global steps");
+    if (!c.rungs_started && c.dt_host[0] > 0.0)
+        return failf(c, SPH_ERR_STATE, "hierarchical steps continue only a run begun with them "
+                     "(sph_set_dt_old(ctx, 0) restarts)");
+    if (c.rungs_started && max_rung != c.rung_R)
+        return failf(c, SPH_ERR_STATE, "sph_step_rungs: max_rung must stay %d", c.rung_R);
+    if (p->n == 0) return SPH_OK;
+    const size_t cap = (size_t)(c.capacity > 0 ? c.capacity : 1);
+    if (!c.rung) {
+        if (dalloc(&c.rung, cap) != cudaSuccess || dalloc(&c.rmax, cap) != cudaSuccess)
+            return failf(c, SPH_ERR_CUDA, "cudaMalloc of the rung arrays failed");
+        CK(cudaMemset(c.rung, 0, cap));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = begin(ctx, s);
+    if (rc) return rc;
+    CK(cudaEventRecord(c.ev0, s));
+    const int nsub = 1 << max_rung;
+    RungArgs ra{c.rung, c.rmax, 0, max_rung, c.rungs_started ? 1 : 0, dt0 / nsub, dt0};
+    for (int sub = 0; sub < nsub && rc == SPH_OK; ++sub) {
+        ra.sub = sub;
+        // the first substep re-sorts (the rungs move with the particles), the
+        // others refit the bounds to the drifted particles
+        if (sub == 0) CK(launch_build(c, *p, s));
+        else CK(launch_refit(c, *p, s));
+        rc = q_density(c, p, nullptr, s, false);
+        if (rc == SPH_OK) rc = q_forces(c, p, s, false, &ra);
+        if (rc == SPH_OK) CK(launch_kdk_rungs(c, *p, ra, s));
+        ra.started = 1;
+    }
+    if (rc) return rc;
+    rc = finish(ctx, s);
+    c.stats.ms_forces = elapsed(c.ev0, c.ev1);
+    density_stats(c);
+    force_stats(c);
+    c.cells_valid = c.density_valid = c.forces_valid = false;
+    c.order_fresh = false;
+    if (rc == SPH_OK) {
+        c.rungs_started = true;
+        c.rung_R = max_rung;
+        c.rho_valid = true;
+    }
+    return rc;
+}
+
+extern "C" sph_status sph_get_rungs(sph_ctx *ctx, uint8_t *out, int64_t n)
+{
+    if (!ctx || !out || n < 0) return SPH_ERR_ARG;
+    Ctx &c = ctx->c;
+    if (n > c.n_built) return failf(c, SPH_ERR_ARG, "n exceeds the particles of the context");
+    if (!c.rung) {
+        std::memset(out, 0, (size_t)n);
+        return SPH_OK;
+    }
+    CK(cudaMemcpy(out, c.rung, (size_t)n, cudaMemcpyDeviceToHost));
+    return SPH_OK;
+}
+
 namespace {
 sph_status capture_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool full);
 }
@@ -995,7 +1100,8 @@ struct ArrDesc {
     size_t off;   // offset of the pointer member in sph_particles
     size_t elem;  // element size
     int in;       // read by a step: 1 always, 2 in SPH_ENERGY_ISENTROPIC mode or with the
-                  // evolved density, 3 with the evolved density, 0 never
+                  // evolved density, 3 with the evolved density, 4 with the interface
+                  // correction (and copied back only then), 0 never
     int late;     // first read after the density phase (1): copied in beside the step
     int out;      // final after the density phase (1), after the forces (2), at the end (0)
     int sorted;   // changed only by a re-sort (1: m, id), so unchanged by a refitting step
@@ -1023,6 +1129,7 @@ const ArrDesc kArrays[] = {
     {offsetof(sph_particles, nngb), 2, 0, 0, 1, 0, 0},
     {offsetof(sph_particles, iters), 1, 0, 0, 1, 0, 0},
     {offsetof(sph_particles, id), 8, 1, 0, 0, 1, 1},
+    {offsetof(sph_particles, mat), 1, 4, 0, 0, 1, 0},
 };
 void *&member(sph_particles &p, const ArrDesc &d)
 {
@@ -1102,6 +1209,7 @@ cudaError_t copy_arrays(Ctx &c, const sph_host_particles *hp, bool in, cudaStrea
     int64_t b_all = 0;
     for (const ArrDesc &d : kArrays) {
         if (in && (d.in == 0 || (d.in == 2 && !isen && !evo) || (d.in == 3 && !evo))) continue;
+        if (d.in == 4 && !c.kp.ic) continue;  // material ids only matter to the correction
         if (in && ((part == 1 && d.late) || (part == 2 && !d.late))) continue;
         if (!in && part > 0 && d.out != part % 3) continue;
         if (skip_sorted && (in ? d.sort_in : d.sorted)) continue;

@@ -321,6 +321,7 @@ struct PermFields {
     float *f4[11];
     uint16_t *f2;
     uint8_t *f1;
+    uint8_t *f1b;  // material ids (may be NULL)
 };
 
 __global__ void k_gather_all(const unsigned *__restrict__ perm, int n, PermFields pf, char *tmp)
@@ -338,6 +339,7 @@ __global__ void k_gather_all(const unsigned *__restrict__ perm, int n, PermField
     for (int f = 0; f < 11; ++f) t4[(size_t)f * n + i] = pf.f4[f][j];
     t2[i] = pf.f2[j];
     t1[i] = pf.f1[j];
+    if (pf.f1b) t1[n + i] = pf.f1b[j];
 }
 
 __global__ void k_copyback_all(int n, PermFields pf, const char *tmp)
@@ -354,6 +356,7 @@ __global__ void k_copyback_all(int n, PermFields pf, const char *tmp)
     for (int f = 0; f < 11; ++f) pf.f4[f][i] = t4[(size_t)f * n + i];
     pf.f2[i] = t2[i];
     pf.f1[i] = t1[i];
+    if (pf.f1b) pf.f1b[i] = t1[n + i];
 }
 
 // ---------------------------------------------------------------------------
@@ -1108,12 +1111,17 @@ cudaError_t launch_build(Ctx &c, const sph_particles &p, cudaStream_t s)
     pf.f4[7] = p.dudt_h; pf.f4[8] = p.dudt_av; pf.f4[9] = p.divv; pf.f4[10] = p.dt_i;
     pf.f2 = p.nngb;
     pf.f1 = p.iters;
+    pf.f1b = p.mat;  // 112 B of scratch per particle hold every array
     pr = prof_begin(c, s, SPH_PHASE_PERMUTE);
     k_gather_all<<<g, 256, 0, s>>>(perm, n, pf, (char *)c.tmp);
     k_copyback_all<<<g, 256, 0, s>>>(n, pf, (const char *)c.tmp);
     prof_end(c, s, pr);
     if (c.mlp.record) {
         cudaError_t e = launch_mlp_permute(c, perm, n, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (c.rung) {  // hierarchical time steps: the rungs move with the particles
+        cudaError_t e = launch_rung_permute(c, perm, n, s);
         if (e != cudaSuccess) return e;
     }
     // bucket layout on the sorted keys

@@ -84,14 +84,22 @@ struct DSums {
     double w = 0.0, q = 0.0;
 };
 
-template <class K, bool WRAP, bool EMIT, bool D64>
+// the interface correction's kernel-imbalance sum (Eq. Kernel_imbalance):
+// sum_j kappa_ij (r_j - r_i) m_j w(q_j), kappa = +1 same material, -1 not
+struct ImbSum {
+    float x = 0.f, y = 0.f, z = 0.f;
+};
+
+template <class K, bool WRAP, bool EMIT, bool D64, bool IC>
 __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, float4 *cand,
-                                              const double4_16a *candd, const int *candj, int c,
-                                              int lane, float px, float py, float pz, float h2,
-                                              float ih, const double *pd, double hd, double ihd,
-                                              bool active, Kahan &Sw, Kahan &Sq, DSums &D,
-                                              int &cnt, int i, long long cap, int &emitted,
-                                              int64_t *ids_out, const int64_t *__restrict__ id_in)
+                                              const double4_16a *candd, const int *candj,
+                                              const unsigned char *candm, int mat_i, ImbSum &V,
+                                              int c, int lane, float px, float py, float pz,
+                                              float h2, float ih, const double *pd, double hd,
+                                              double ihd, bool active, Kahan &Sw, Kahan &Sq,
+                                              DSums &D, int &cnt, int i, long long cap,
+                                              int &emitted, int64_t *ids_out,
+                                              const int64_t *__restrict__ id_in)
 {
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32)
@@ -114,6 +122,18 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
             sw = fmaf(q.w, wv, sw);
             sq = fmaf(q.w * dq, qq * qq, sq);
             ++nh;
+            if (IC) {
+                float dx = q.x - px, dy = q.y - py, dz = q.z - pz;  // r_j - r_i
+                if (WRAP) {
+                    if (bx.per[0]) dx = wrapf(dx, bx.L[0], bx.invL[0]);
+                    if (bx.per[1]) dy = wrapf(dy, bx.L[1], bx.invL[1]);
+                    if (bx.per[2]) dz = wrapf(dz, bx.L[2], bx.invL[2]);
+                }
+                const float kw = (candm[k] == mat_i ? q.w : -q.w) * wv;
+                V.x = fmaf(kw, dx, V.x);
+                V.y = fmaf(kw, dy, V.y);
+                V.z = fmaf(kw, dz, V.z);
+            }
             if (EMIT) {
                 int j = candj[k];
                 if (j != i) {
@@ -158,10 +178,11 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
 
 // D64: the FP64 form (positions from pmd, sums, Newton iteration and the
 // outputs' arithmetic in FP64); otherwise FP32 pairs on cell-relative offsets
-template <class K, bool WRAP, bool EMIT, bool D64>
+template <class K, bool WRAP, bool EMIT, bool D64, bool IC>
 __device__ __forceinline__ void density_bucket(
     const KParams &kp, const Inst &I, const PBox &bx, int A, int i0, int lane, float4 *cand,
-    double4_16a *candd, int *candj, const float4 *__restrict__ pm, const double4_16a *__restrict__ pmd,
+    double4_16a *candd, int *candj, unsigned char *candm, const uint8_t *__restrict__ mat,
+    float *ic_e, const float4 *__restrict__ pm, const double4_16a *__restrict__ pmd,
     const int *__restrict__ bstart, const unsigned *__restrict__ list_cnt,
     const unsigned *__restrict__ list_off, const unsigned *__restrict__ list,
     const int *__restrict__ origin, const float4 *__restrict__ node, float *h_seed, float *h_out,
@@ -192,6 +213,8 @@ __device__ __forceinline__ void density_bucket(
         pd[2] = q.z;
     }
     const Real mi = D64 && valid ? (Real)pmd[i].w : (Real)me.w;
+    const int mat_i = IC && valid ? (int)mat[i] : 0;
+    float out_e = 1.f;  // interface correction: exp(-I^2) at the recorded h
     // Filter the group's list against this bucket's coverage box of balls
     // (radius R): lane w keeps the acceptance bits of entries 32w .. 32w+31
     // of the first 1024.  Longer lists (overflow arena) get the bits of each
@@ -269,6 +292,7 @@ __device__ __forceinline__ void density_bucket(
         }
         Kahan Sw, Sq;
         DSums D;
+        ImbSum V;
         int cnt = 0, c = 0;
         for (unsigned w = 0; w < nwords; ++w) {
           unsigned mw;
@@ -309,6 +333,7 @@ __device__ __forceinline__ void density_bucket(
                 int pos = c + __popc(bal & lt);
                 cand[pos] = make_float4(sp[0], sp[1], sp[2], s.w);
                 if (EMIT) candj[pos] = j;
+                if (IC) candm[pos] = mat[j];
                 if (D64) {
                     // the same source in FP64: its offset from its own bucket
                     // origin plus the exact origin offset (the image the FP32
@@ -332,9 +357,10 @@ __device__ __forceinline__ void density_bucket(
             if (c > kChunk - 32) {
                 __syncwarp();
                 if (!done) cands += c;
-                density_chunk<K, WRAP, EMIT, D64>(bx, I, cand, candd, candj, c, lane, p[0], p[1],
-                                                  p[2], h2, ih, pd, (double)h, ihd, !done, Sw, Sq,
-                                                  D, cnt, i, cap, emitted, ids_out, id_in);
+                density_chunk<K, WRAP, EMIT, D64, IC>(bx, I, cand, candd, candj, candm, mat_i, V,
+                                                      c, lane, p[0], p[1], p[2], h2, ih, pd,
+                                                      (double)h, ihd, !done, Sw, Sq, D, cnt, i,
+                                                      cap, emitted, ids_out, id_in);
                 __syncwarp();
                 c = 0;
             }
@@ -343,9 +369,10 @@ __device__ __forceinline__ void density_bucket(
         if (c > 0) {
             __syncwarp();
             if (!done) cands += c;
-            density_chunk<K, WRAP, EMIT, D64>(bx, I, cand, candd, candj, c, lane, p[0], p[1], p[2],
-                                              h2, ih, pd, (double)h, ihd, !done, Sw, Sq, D, cnt,
-                                              i, cap, emitted, ids_out, id_in);
+            density_chunk<K, WRAP, EMIT, D64, IC>(bx, I, cand, candd, candj, candm, mat_i, V, c,
+                                                  lane, p[0], p[1], p[2], h2, ih, pd, (double)h,
+                                                  ihd, !done, Sw, Sq, D, cnt, i, cap, emitted,
+                                                  ids_out, id_in);
             __syncwarp();
         }
         if (!done) {
@@ -400,6 +427,11 @@ __device__ __forceinline__ void density_bucket(
                     out_rho = (Real)(K::sigma * (float)swv * ih * ih * ih);
                 }
                 out_n = nn;
+                if (IC) {  // Eq. Kernel_imbalance: I = alpha |V| / (h sum m w)
+                    const float vm = sqrtf(fmaf(V.x, V.x, fmaf(V.y, V.y, V.z * V.z)));
+                    const float Ii = I.ic_alpha * vm / ((float)h * (float)swv);
+                    out_e = __expf(-Ii * Ii);
+                }
                 if (!(isfinite(out_rho) && isfinite(out_om) && out_rho > 0))
                     raise_status(st, ST_NONFINITE, i);
                 if ((float)h >= I.hcap) raise_status(st, ST_ARG, i);
@@ -425,6 +457,7 @@ __device__ __forceinline__ void density_bucket(
         nngb_out[i] = (uint16_t)min(out_n, 65535);
         iters_out[i] = (uint8_t)min(iters, 255);
         if (EMIT && count_out) count_out[i] = (uint32_t)out_n;
+        if (IC) ic_e[i] = out_e;
     }
     unsigned long long wp = warp_sum(pairs), wc = warp_sum(cands);
     int wi = (int)warp_max((float)iters);
@@ -436,8 +469,9 @@ __device__ __forceinline__ void density_bucket(
 }
 
 // one sink bucket A (one warp)
-template <class K, bool EMIT, bool D64>
+template <class K, bool EMIT, bool D64, bool IC>
 __device__ __forceinline__ void density_slot(
+    const uint8_t *__restrict__ mat, float *ic_e, unsigned char *candm,
     const KParams &kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const double4_16a *__restrict__ pmd, const int *__restrict__ bstart,
     const int *__restrict__ binst, const unsigned *__restrict__ list_cnt,
@@ -473,24 +507,26 @@ __device__ __forceinline__ void density_slot(
         }
     }
     if (wrap)
-        density_bucket<K, true, EMIT, D64>(kp, I, bx, A, i0, lane, cand, candd, candj, pm, pmd,
+        density_bucket<K, true, EMIT, D64, IC>(kp, I, bx, A, i0, lane, cand, candd, candj, candm,
+                                               mat, ic_e, pm, pmd,
                                            bstart, list_cnt, list_off, list, origin, node, h_seed,
                                            h_out, rho_out, omega_out, nngb_out, iters_out, fixed_h,
                                            cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
                                            gflag, st, me, valid, cen);
     else
-        density_bucket<K, false, EMIT, D64>(kp, I, bx, A, i0, lane, cand, candd, candj, pm, pmd,
+        density_bucket<K, false, EMIT, D64, IC>(kp, I, bx, A, i0, lane, cand, candd, candj,
+                                                candm, mat, ic_e, pm, pmd,
                                             bstart, list_cnt, list_off, list, origin, node, h_seed,
                                             h_out, rho_out, omega_out, nngb_out, iters_out,
                                             fixed_h, cap, count_out, ids_out, id_in, redo_out,
                                             redo_cnt_out, gflag, st, me, valid, cen);
 }
 
-template <class K, bool EMIT, bool D64>
+template <class K, bool EMIT, bool D64, bool IC>
 // 5 blocks of 4 warps per SM: the register cap (96) measured faster than
 // the compiler's own choice (about 128 registers, 4 blocks)
 __global__ void __launch_bounds__(128, 5) k_density(
-    KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
+    const uint8_t *__restrict__ mat, float *ic_e, KParams kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const double4_16a *__restrict__ pmd, const int *__restrict__ bstart,
     const int *__restrict__ binst, const int *__restrict__ gfirst,
     const unsigned *__restrict__ list_cnt, const unsigned *__restrict__ list_off,
@@ -504,12 +540,13 @@ __global__ void __launch_bounds__(128, 5) k_density(
     __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
     __shared__ double4_16a candd_s[D64 ? kWarpsPerBlock : 1][D64 ? kChunk : 1];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
+    __shared__ unsigned char candm_s[IC ? kWarpsPerBlock : 1][IC ? kChunk : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double4_16a *candd = D64 ? candd_s[wib] : nullptr;
     if (!group_ids) {  // every bucket, one warp each
         const int A = blockIdx.x * kWarpsPerBlock + wib;
         if (A < kp.nb)
-            density_slot<K, EMIT, D64>(kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
+            density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
                                        origin, h_seed, h_out, rho_out, omega_out, nngb_out,
                                        iters_out, fixed_h, cap, count_out, ids_out, id_in,
                                        redo_out, redo_cnt_out, gflag, node, st, cand_s[wib],
@@ -525,7 +562,7 @@ __global__ void __launch_bounds__(128, 5) k_density(
         const Inst &Ig = insts[binst[fb]];
         const int j = bi & ((1 << kGroupLog) - 1);
         if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) continue;
-        density_slot<K, EMIT, D64>(kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
+        density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
                                    origin, h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
                                    fixed_h, cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
                                    gflag, node, st, cand_s[wib], candd,
@@ -570,18 +607,20 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     // the evolved density mode keeps p.rho as state: the kernel sum goes to
     // scratch (h and Omega to p as always)
     float *rho_out = kp.evolved ? c.rho_sum : p.rho;
-#define SPH_DENSITY_LAUNCH(EMIT_, D64_)                                                      \
-    k_density<KT, EMIT_, D64_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                                 \
-        kp, c.inst, c.pm, c.pmd, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list,     \
+#define SPH_DENSITY_LAUNCH(EMIT_, D64_, IC_)                                                 \
+    k_density<KT, EMIT_, D64_, IC_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                            \
+        p.mat, c.ic_e, kp, c.inst, c.pm, c.pmd, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list,     \
         c.origin, gids, gcnt, (float *)h_seed, p.h, rho_out, p.omega, p.nngb, p.iters, fixed_h,   \
         (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st)
     SPH_KERNEL_DISPATCH(kp.kernel, KT,
         if (kp.fp64) {
-            if (emit) SPH_DENSITY_LAUNCH(true, true);
-            else SPH_DENSITY_LAUNCH(false, true);
+            if (emit) SPH_DENSITY_LAUNCH(true, true, false);
+            else SPH_DENSITY_LAUNCH(false, true, false);
+        } else if (kp.ic && !emit) {
+            SPH_DENSITY_LAUNCH(false, false, true);
         } else {
-            if (emit) SPH_DENSITY_LAUNCH(true, false);
-            else SPH_DENSITY_LAUNCH(false, false);
+            if (emit) SPH_DENSITY_LAUNCH(true, false, false);
+            else SPH_DENSITY_LAUNCH(false, false, false);
         }
     )
 #undef SPH_DENSITY_LAUNCH

@@ -57,7 +57,8 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
                           const double *__restrict__ dts, float4 *fpos, float4 *fvel, float4 *fth,
                           int4 *ipos, float4 *acc, double *accS, unsigned *mumax, unsigned *dtmin,
                           double4_16a *fveld, double4_16a *fthd, double4_16a *acc64,
-                          const float *__restrict__ divv_old, DevStatus *st)
+                          const float *__restrict__ divv_old, const uint8_t *__restrict__ mat,
+                          float2 *ic_pt, RungArgs ra, DevStatus *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kp.ninst) dtmin[i] = 0x7f800000u;  // +inf
@@ -65,10 +66,19 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
     const int k = pinst[i];
     const Inst &I = insts[k];
     const float gamma = I.gamma;
-    const double hdt = 0.5 * dts[2 * k];
+    // time from the half-step state (v, u) to now: half the old step, or in
+    // a hierarchical step the time since the particle's last boundary (its
+    // whole period when it is active now) less half its period
+    double hdt = 0.5 * dts[2 * k];
+    if (ra.rung) {
+        const int P = 1 << (ra.R - (int)ra.rung[i]);
+        const int phi = ra.sub & (P - 1);
+        hdt = ra.started ? ((double)(phi == 0 ? P : phi) - 0.5 * (double)P) * ra.delta : 0.0;
+        ra.rmax[i] = -1;
+    }
     double v[3] = {vx[i], vy[i], vz[i]};
     double uu = u[i];
-    if (hdt > 0.0) {
+    if (hdt != 0.0) {
         v[0] += hdt * (double)ax[i];
         v[1] += hdt * (double)ay[i];
         v[2] += hdt * (double)az[i];
@@ -95,6 +105,9 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
     fpos[i] = make_float4(q.x, q.y, q.z, hi);
     fvel[i] = make_float4((float)v[0], (float)v[1], (float)v[2], q.w);
     fth[i] = make_float4(A, c, r, om);
+    // interface correction: pressure and temperature (T = (gamma-1) u / R
+    // of the particle's material) for the correction pass
+    if (ic_pt) ic_pt[i] = make_float2(P, (gamma - 1.f) * (float)uu / I.r_gas[mat[i] & 3]);
     // h in fixed-point units (h < fix_lim whenever the force kernel uses it)
     reinterpret_cast<int *>(ipos + i)[3] = __float2int_rn(fminf(hi, I.fix_lim) * I.inv_qx);
     acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -115,6 +128,7 @@ struct SinkState {
     float vx, vy, vz, m;
     float A, c, rho;
     int ix, iy, iz, hq;                // fixed-point position and h (units qx)
+    int rg, rmx;                       // hierarchical steps: rung, largest partner rung
     Kahan ax, ay, az, S;
     float du, mumax;
     int i;
@@ -153,10 +167,10 @@ struct Visc {
 // SELF: the chunk holds the sink bucket's own particles, where only j > i
 // counts (every other source bucket lies after the sink bucket, so all its
 // particles do).  FIX: separations and 1 - q from the fixed-point positions.
-template <class K, bool WRAP, bool SELF, bool FIX>
+template <class K, bool WRAP, bool SELF, bool FIX, bool RUNG>
 __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, ForceStage &S, int c,
                                             SinkState &s, bool valid, int lane, float4 *acc,
-                                            double *accS, unsigned *mumax)
+                                            double *accS, unsigned *mumax, const RungArgs &ra)
 {
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32) {
@@ -269,6 +283,11 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
             atomicMax(&mumax[o.jj], __float_as_uint(o.mneg));
             ++s.av;
         }
+        if (RUNG) {  // the rung limiter needs each particle's largest partner rung
+            const int rj = ra.rung[o.jj];
+            s.rmx = max(s.rmx, rj);
+            if (rung_active(ra.sub, ra.R, rj)) atomicMax(&ra.rmax[o.jj], s.rg);
+        }
         ++s.pairs;
     };
     auto next = [&]() -> int {
@@ -294,7 +313,7 @@ struct SinkBounds {
     float gR2;
 };
 
-template <class K, bool WRAP, bool FIX>
+template <class K, bool WRAP, bool FIX, bool RUNG>
 __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, const PBox &bx,
                                              const Visc &vp, int A, int lane, ForceStage &S,
                                              SinkState &s, bool valid, const SinkBounds sb,
@@ -309,7 +328,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
                                              const int *__restrict__ origin,
                                              const float4 *__restrict__ node, float4 *acc,
                                              double *accS, unsigned *mumax,
-                                             unsigned long long &cands)
+                                             unsigned long long &cands, const RungArgs &ra)
 {
     const unsigned lt = (1u << lane) - 1u;
     // Filter the group's list for this bucket (Sec. 2.3.2 tests with the
@@ -423,7 +442,8 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP, true, FIX>(bx, vp, S, c, s, valid, lane, acc, accS, mumax);
+        force_chunk<K, WRAP, true, FIX, RUNG>(bx, vp, S, c, s, valid, lane, acc, accS, mumax,
+                                               ra);
         c = 0;
     }
     const unsigned nwords = (nl + 31) / 32;
@@ -440,7 +460,8 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
-            force_chunk<K, WRAP, false, FIX>(bx, vp, S, c, s, valid, lane, acc, accS, mumax);
+            force_chunk<K, WRAP, false, FIX, RUNG>(bx, vp, S, c, s, valid, lane, acc, accS,
+                                                mumax, ra);
             c = 0;
         }
       }
@@ -448,14 +469,15 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP, false, FIX>(bx, vp, S, c, s, valid, lane, acc, accS, mumax);
+        force_chunk<K, WRAP, false, FIX, RUNG>(bx, vp, S, c, s, valid, lane, acc, accS,
+                                                mumax, ra);
     }
 }
 
 // 5 blocks of 4 warps per SM (96 registers; the fixed-point pair path spills
 // a few values): measured faster than 4 blocks with the 124 registers the
 // compiler picks without the cap
-template <class K>
+template <class K, bool RUNG>
 __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, const Inst *__restrict__ insts,
                                                 const int *__restrict__ bstart,
                                                 const int *__restrict__ binst,
@@ -468,7 +490,8 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
                                                 const unsigned *__restrict__ list,
                                                 const int *__restrict__ origin,
                                                 const float4 *__restrict__ node, float4 *acc,
-                                                double *accS, unsigned *mumax, DevStatus *st)
+                                                double *accS, unsigned *mumax, RungArgs ra,
+                                                DevStatus *st)
 {
     __shared__ ForceStage stage[kWarpsPerBlock];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -497,6 +520,8 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
         s.A = t.x; s.c = t.y; s.rho = t.z;
         s.ix = p.x; s.iy = p.y; s.iz = p.z;
         s.hq = p.w;
+        s.rg = RUNG && valid ? (int)ra.rung[i] : 0;
+        s.rmx = -1;
         s.du = 0.f;
         s.mumax = 0.f;
         s.i = valid ? i : 0x7fffffff;
@@ -537,21 +562,22 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     const bool fix = !wrap && Emax < I.fix_lim && Hmax < I.fix_lim;
     unsigned long long cands = 0;
     if (fix)
-        force_bucket<K, false, true>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+        force_bucket<K, false, true, RUNG>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
                                      fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
-                                     node, acc, accS, mumax, cands);
+                                     node, acc, accS, mumax, cands, ra);
     else if (wrap)
-        force_bucket<K, true, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+        force_bucket<K, true, false, RUNG>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
                                      fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
-                                     node, acc, accS, mumax, cands);
+                                     node, acc, accS, mumax, cands, ra);
     else
-        force_bucket<K, false, false>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+        force_bucket<K, false, false, RUNG>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
                                       fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
-                                      node, acc, accS, mumax, cands);
+                                      node, acc, accS, mumax, cands, ra);
     if (valid) {
         red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.du);
         red_add_f64(&accS[i], (double)s.S.s - (double)s.S.c);
         if (s.mumax > 0.f) atomicMax(&mumax[i], __float_as_uint(s.mumax));
+        if (RUNG && s.rmx >= 0) atomicMax(&ra.rmax[i], s.rmx);
     }
     unsigned long long wp = warp_sum((unsigned long long)s.pairs);
     unsigned long long wav = warp_sum((unsigned long long)s.av);
@@ -571,12 +597,14 @@ __global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
                            const float4 *__restrict__ fpos, const float4 *__restrict__ fth,
                            float *ax, float *ay, float *az, float *dudt_h, float *dudt_av,
                            float *divv, float *dt_i, unsigned *dtmin,
-                           const double4_16a *__restrict__ acc64, DevStatus *st)
+                           const double4_16a *__restrict__ acc64, RungArgs ra, DevStatus *st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = INFINITY;
     int k = -1;
-    if (i < n) {
+    // hierarchical substep: the inactive particles keep their derivatives
+    const bool act = i < n && (!ra.rung || rung_active(ra.sub, ra.R, (int)ra.rung[i]));
+    if (act) {
         k = pinst[i];
         const Inst &I = insts[k];
         float4 f;
@@ -616,8 +644,10 @@ __global__ void k_finalize(KParams kp, int n, const Inst *__restrict__ insts,
     }
 }
 
-cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
+cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s, const RungArgs *ra)
 {
+    RungArgs r0{};
+    const RungArgs rv = ra ? *ra : r0;
     int n = (int)p.n;
     c.launches += 1;
     const int nt = n > c.kp.ninst ? n : c.kp.ninst;
@@ -627,12 +657,13 @@ cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s)
                                               p.h, p.rho, p.omega, c.pm, c.dts, c.fpos, c.fvel,
                                               c.fth, c.ipos, c.acc, c.accS, c.mumax, c.dtmin,
                                               c.kp.fp64 ? c.fveld : nullptr, c.fthd, c.acc64,
-                                              p.divv, c.st);
+                                              p.divv, p.mat, c.kp.ic ? c.ic_pt : nullptr, rv,
+                                              c.st);
     prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
+cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s, const RungArgs *ra)
 {
     (void)p;
     const int pr = prof_begin(c, s, SPH_PHASE_FORCES);
@@ -643,25 +674,33 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s)
     }
     int g = (c.kp.nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
     c.launches += 1;
+    RungArgs r0{};
+    const RungArgs rv = ra ? *ra : r0;
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
-        k_forces<KT><<<g, 32 * kWarpsPerBlock, 0, s>>>(c.kp, c.inst, c.bstart, c.binst, c.fpos,
-                                                        c.fvel, c.fth, c.ipos, c.list_cnt,
-                                                        c.list_off, c.list, c.origin, c.node,
-                                                        c.acc, c.accS, c.mumax, c.st);
+        if (rv.rung)
+            k_forces<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
+                c.kp, c.inst, c.bstart, c.binst, c.fpos, c.fvel, c.fth, c.ipos, c.list_cnt,
+                c.list_off, c.list, c.origin, c.node, c.acc, c.accS, c.mumax, rv, c.st);
+        else
+            k_forces<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
+                c.kp, c.inst, c.bstart, c.binst, c.fpos, c.fvel, c.fth, c.ipos, c.list_cnt,
+                c.list_off, c.list, c.origin, c.node, c.acc, c.accS, c.mumax, rv, c.st);
     )
     prof_end(c, s, pr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s)
+cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s, const RungArgs *ra)
 {
+    RungArgs r0{};
+    const RungArgs rv = ra ? *ra : r0;
     int n = (int)p.n;
     c.launches += 1;
     const int pr = prof_begin(c, s, SPH_PHASE_FINALIZE);
     k_finalize<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, c.acc, c.accS, c.mumax,
                                                c.fpos, c.fth, p.a[0], p.a[1], p.a[2], p.dudt_h,
                                                p.dudt_av, p.divv, p.dt_i, c.dtmin,
-                                               c.kp.fp64 ? c.acc64 : nullptr, c.st);
+                                               c.kp.fp64 ? c.acc64 : nullptr, rv, c.st);
     prof_end(c, s, pr);
     return cudaGetLastError();
 }

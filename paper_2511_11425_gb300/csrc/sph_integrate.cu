@@ -206,6 +206,112 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// hierarchical time steps (Sec. 2.3.6): substep `sub` of 2^R, length delta.
+// An active particle (its period divides sub) closes its old step with the
+// derivatives just computed (half its old period; none on the very first
+// substep), picks its rung (ceil(log2(dt0 / dt_i)) clamped to [0, R], raised
+// to the largest rung of its force partners less two; a lower rung only to
+// one whose period divides sub, the lowest such) and opens the new step with
+// half the new period.  Every particle drifts by delta; the seed of the next
+// density pass is h exp(delta div v / 3) (factor clamped to [1/2, 2]).
+// ---------------------------------------------------------------------------
+__global__ void k_kdk_rungs(KParams kp, int n, const Inst *__restrict__ insts,
+                            const unsigned short *__restrict__ pinst, double *x, double *y,
+                            double *z, double *vx, double *vy, double *vz, double *u, float *h,
+                            const float *__restrict__ ax, const float *__restrict__ ay,
+                            const float *__restrict__ az, const float *__restrict__ dudt_h,
+                            const float *__restrict__ dudt_av, const float *__restrict__ divv,
+                            const float *__restrict__ dt_i, uint8_t *rung,
+                            const int *__restrict__ rmax, RungArgs ra, const DevStatus *st)
+{
+    if (st->code != 0) return;  // a failed substep leaves the state as it was
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r_old = rung[i];
+    double kick = 0.0;  // the closing and opening half periods of an active particle
+    if (rung_active(ra.sub, ra.R, r_old)) {
+        if (ra.started) kick = 0.5 * (double)(1 << (ra.R - r_old)) * ra.delta;
+        // ceil(log2(dt0 / dt_i)) from the binary exponent (exact at powers of two)
+        int e = 0;
+        const double f = frexp(ra.dt0 / (double)dt_i[i], &e);
+        int want = f == 0.5 ? e - 1 : e;
+        want = max(want, rmax[i] - 2);
+        want = min(max(want, 0), ra.R);
+        int r_new = want;
+        if (want < r_old) {  // a longer step only on a boundary of that step
+            r_new = r_old;
+            for (int r = want; r < r_old; ++r)
+                if (rung_active(ra.sub, ra.R, r)) {
+                    r_new = r;
+                    break;
+                }
+        }
+        rung[i] = (uint8_t)r_new;
+        kick += 0.5 * (double)(1 << (ra.R - r_new)) * ra.delta;
+    }
+    const Inst &I = insts[pinst[i]];
+    double ud = (double)dudt_av[i];
+    if (kp.energy_mode == SPH_ENERGY_PDV) ud += (double)dudt_h[i];
+    const double v0 = vx[i] + kick * (double)ax[i];
+    const double v1 = vy[i] + kick * (double)ay[i];
+    const double v2 = vz[i] + kick * (double)az[i];
+    vx[i] = v0;
+    vy[i] = v1;
+    vz[i] = v2;
+    u[i] += kick * ud;
+    double p[3] = {x[i] + ra.delta * v0, y[i] + ra.delta * v1, z[i] + ra.delta * v2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (I.periodic[a] && !(p[a] >= I.lo[a] && p[a] < I.hi[a])) {
+            double t = p[a] - I.lo[a];
+            t -= I.Ld[a] * floor(t * I.invLd[a]);
+            if (t >= I.Ld[a]) t -= I.Ld[a];
+            if (t < 0.0) t = 0.0;
+            p[a] = I.lo[a] + t;
+        }
+    }
+    x[i] = p[0];
+    y[i] = p[1];
+    z[i] = p[2];
+    const float g = expf((float)ra.delta * divv[i] * (1.f / 3.f));
+    h[i] = h[i] * fminf(fmaxf(g, 0.5f), 2.f);
+}
+
+__global__ void k_rung_gather(const unsigned *__restrict__ perm, int n, const uint8_t *rung,
+                              int *tmp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tmp[i] = rung[perm[i]];
+}
+
+__global__ void k_rung_copyback(int n, const int *__restrict__ tmp, uint8_t *rung)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rung[i] = (uint8_t)tmp[i];
+}
+
+cudaError_t launch_rung_permute(Ctx &c, const unsigned *perm, int n, cudaStream_t s)
+{
+    c.launches += 2;
+    k_rung_gather<<<(n + 255) / 256, 256, 0, s>>>(perm, n, c.rung, c.rmax);
+    k_rung_copyback<<<(n + 255) / 256, 256, 0, s>>>(n, c.rmax, c.rung);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kdk_rungs(Ctx &c, const sph_particles &p, const RungArgs &ra, cudaStream_t s)
+{
+    const int n = (int)p.n;
+    c.launches += 1;
+    const int pr = prof_begin(c, s, SPH_PHASE_KDK);
+    k_kdk_rungs<<<(n + 255) / 256, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2],
+                                                p.v[0], p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1],
+                                                p.a[2], p.dudt_h, p.dudt_av, p.divv, p.dt_i, c.rung,
+                                                c.rmax, ra, c.st);
+    prof_end(c, s, pr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const int nb = c.cons_blocks > 0 ? c.cons_blocks : 1;

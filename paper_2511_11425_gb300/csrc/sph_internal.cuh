@@ -124,6 +124,8 @@ struct Inst {
     float hcap;          // h must stay below half the shortest periodic length
     float qf;            // origin quantum in f32
     float qx, inv_qx;    // fixed-point quantum q 2^-kFixShift and its inverse
+    float ic_alpha;      // kernel-imbalance normalisation (interface correction)
+    float r_gas[4];      // gas constant per material
     float qx2;           // qx^2
     float fix_lim;       // fixed point usable while bucket extents and h stay below
     unsigned LQ[3];      // periodic length in units of qx (rounded; < 2^32)
@@ -139,8 +141,24 @@ struct KParams {
     int any_open;        // some instance has an open axis
     int fp64;            // SPH_PRECISION_FP64: pair sums and h iteration in FP64
     int evolved;         // SPH_DENSITY_EVOLVED: rho is state (mass conservation)
+    int ic;              // interface correction on (Sec. 2.3.4)
     float h_rel_tol, margin;
 };
+
+// the substep of a hierarchical step that a kernel works on (sph_step_rungs):
+// substep `sub` of 2^R of length delta; a particle on rung r has the period
+// 2^(R-r) substeps and is active when sub is a multiple of it.  rung = NULL:
+// a plain global step.
+struct RungArgs {
+    const uint8_t *rung;
+    int *rmax;
+    int sub, R, started;
+    double delta, dt0;
+};
+__host__ __device__ inline bool rung_active(int sub, int R, int r)
+{
+    return (sub & ((1 << (R - r)) - 1)) == 0;
+}
 
 // one block of the bottom-up tree refit: reduce `levels` levels of instance
 // `inst` starting at level `lvl`, block index `blk` within that level
@@ -218,6 +236,14 @@ struct Ctx {
     unsigned *mumax = nullptr;
     float *rho_old = nullptr;
     float *rho_sum = nullptr;         // evolved density mode: the density pass's kernel sum
+    float *ic_e = nullptr;            // interface correction: exp(-I^2) per particle
+    // hierarchical time steps (sph_step_rungs): rung per particle (permuted
+    // with the particles), largest rung of each particle's force partners
+    uint8_t *rung = nullptr;
+    int *rmax = nullptr;
+    bool rungs_started = false;       // derivatives exist (the first substep has none)
+    int rung_R = 0;                   // max_rung of the hierarchical steps so far
+    float2 *ic_pt = nullptr;          // interface correction: P, T from the predictor
     bool rho_evolved_init = false;    // p->rho holds an evolved density
     float *h_seed = nullptr;          // density seeds / re-walk seeds
 
@@ -605,13 +631,22 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
                            cudaStream_t s);
 cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s);
 // forces (sph_forces.cu)
-cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s);
-cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s);
+cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s,
+                           const RungArgs *ra = nullptr);
+cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s,
+                          const RungArgs *ra = nullptr);
 cudaError_t launch_forces64(Ctx &c, cudaStream_t s);  // FP64 form (sph_forces64.cu)
-cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s);
+// interface correction pass (sph_interface.cu)
+cudaError_t launch_interface(Ctx &c, const sph_particles &p, cudaStream_t s);
+cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s,
+                            const RungArgs *ra = nullptr);
 // integration (sph_integrate.cu)
 cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s);
 cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s);
+// hierarchical step: kicks of the active particles, rung choice, drift of all
+cudaError_t launch_kdk_rungs(Ctx &c, const sph_particles &p, const RungArgs &ra, cudaStream_t s);
+// permute the rungs with the particles at a full build
+cudaError_t launch_rung_permute(Ctx &c, const unsigned *perm, int n, cudaStream_t s);
 // learned seed (sph_mlp.cu)
 cudaError_t launch_mlp_permute(Ctx &c, const unsigned *perm, int n, cudaStream_t s);
 cudaError_t launch_mlp_harvest(Ctx &c, const sph_particles &p, cudaStream_t s);

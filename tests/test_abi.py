@@ -44,8 +44,8 @@ def test_binding_names_match_header(libpath):
 def test_struct_layouts_match_header(libpath):
     # sph_particles: n + 21 pointers; sph_params as laid out by a C compiler
     import paper_2511_11425_gb300 as sph
-    assert ctypes.sizeof(sph.c_particles) == 8 + 21 * 8
-    assert ctypes.sizeof(sph.c_params) == 184
+    assert ctypes.sizeof(sph.c_particles) == 8 + 22 * 8
+    assert ctypes.sizeof(sph.c_params) == 224
     assert sph.c_params.h_rel_tol.offset == 128 and sph.c_params.list_margin.offset == 136
     assert sph.c_params.curve.offset == 144 and sph.c_params.group_log.offset == 148
     assert ctypes.sizeof(sph.c_stats) == 112 + 16 * 8 + 16 * 8

@@ -1,0 +1,83 @@
+"""Hierarchical power-of-two time steps (Sec. 2.3.6) on the GPU against the
+oracle's integrator of the same scheme (oracle.RungSimulation), through the
+C ABI (sph_step_rungs): a Sedov blast on 12^3 particles whose hot centre
+sits four rungs above the cold gas, two global steps of 16 substeps.  The
+rungs must agree exactly (the test first checks that no rung decision of
+the oracle lies within 1e-2 of a power-of-two boundary, where FP32 and FP64
+time-step limits could round to different rungs); positions, velocities and
+internal energies within the tolerances of the global-step tracking test."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import norm_err, oracle_params, to_input_order
+from paper_2511_11425_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2511_11425_gb300 as m
+    m.lib()
+    return m
+
+
+def _compare(sph, prob, dt0, R, nglobal):
+    p = oracle_params(prob)
+    o = oracle.RungSimulation(p, prob.pos, prob.vel, prob.m, prob.u, prob.h0, max_rung=R)
+    for _ in range(nglobal):
+        o.global_step(dt0)
+    dist = min(float(np.min(np.abs(r - np.round(r)))) for _, _, r in o.log if len(r))
+    assert dist > 1e-2, dist
+    sim = sph.Simulation(prob)
+    try:
+        for _ in range(nglobal):
+            sph.sph_step_rungs(sim.ctx, sim.parts, dt0, R)
+        g = sim.parts.numpy()
+        rungs = sph.sph_get_rungs(sim.ctx, prob.n)
+    finally:
+        sim.close()
+    order = np.argsort(g["id"], kind="stable")
+    rungs = rungs[order]
+    g = to_input_order(g)
+    L = np.array(prob.box_hi) - np.array(prob.box_lo)
+    dx = g["x"] - o.x
+    dx -= L * np.round(dx / L)
+    errs = {"x": float(np.max(np.abs(dx))), "v": norm_err(g["v"], o.v),
+            "u": norm_err(g["u"], o.u)}
+    print("rungs", np.bincount(rungs, minlength=R + 1), {k: "%.2g" % v for k, v in errs.items()})
+    return errs, rungs, o
+
+
+def test_rungs_track_oracle_sedov(sph):
+    prob = inputs.sedov(n=12)
+    errs, rungs, o = _compare(sph, prob, 0.017, 4, 2)
+    assert np.array_equal(rungs, o.rung)
+    assert len(np.unique(rungs)) >= 3                  # a real hierarchy
+    assert errs["x"] < 1e-6 and errs["v"] < 2e-4 and errs["u"] < 1e-5
+
+
+def test_rungs_arguments(sph):
+    prob = inputs.uniform(n=6, seed=3)
+    sim = sph.Simulation(prob)
+    try:
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_step_rungs(sim.ctx, sim.parts, -1.0, 2)
+        assert e.value.code == 1
+        sph.sph_step_rungs(sim.ctx, sim.parts, 1e-3, 2)
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_step_rungs(sim.ctx, sim.parts, 1e-3, 3)   # one max_rung per run
+        assert e.value.code == 7
+    finally:
+        sim.close()
+    sim = sph.Simulation(prob)
+    try:
+        sim.step(1e-3)
+        with pytest.raises(sph.SphError) as e:                 # begun with global steps
+            sph.sph_step_rungs(sim.ctx, sim.parts, 1e-3, 2)
+        assert e.value.code == 7
+    finally:
+        sim.close()

@@ -99,3 +99,67 @@ def test_evolved_density_is_constant_at_rest():
     # at rest div v = 0 at t = 0; the pressure forces of the jittered lattice
     # start a motion whose divergence moves rho only at second order in t
     assert np.max(np.abs(sim.rho - rho0) / rho0) < 1e-4
+
+
+def _rung_problem():
+    prob = inputs.uniform(n=7, seed=81, jitter=0.3, vamp=0.3)
+    p = oracle.Params(gamma=prob.gamma, alpha=prob.alpha, beta=prob.beta, box_lo=prob.box_lo,
+                      box_hi=prob.box_hi, periodic=prob.periodic)
+    return prob, p
+
+
+def test_single_rung_is_the_global_kick_drift_kick():
+    # R = 0: one substep per global step, every particle active each time:
+    # the hierarchical scheme reduces to the global step of Sec. 2.3.6
+    prob, p = _rung_problem()
+    dt = 2e-3
+    g = oracle.Simulation(p, prob.pos, prob.vel, prob.m, prob.u, prob.h0)
+    r = oracle.RungSimulation(p, prob.pos, prob.vel, prob.m, prob.u, prob.h0, max_rung=0)
+    for _ in range(3):
+        g.step(dt_fixed=dt)
+        r.global_step(dt)
+    assert np.allclose(r.x, g.x, rtol=0, atol=1e-14)
+    assert np.allclose(r.v, g.v, rtol=1e-12, atol=1e-14)
+    assert np.allclose(r.u, g.u, rtol=1e-12, atol=1e-14)
+
+
+def test_all_particles_on_the_top_rung_take_global_substeps():
+    # a global step 2^R times the smallest limit puts every particle whose
+    # limit is within a factor two of the smallest on the top rung R: then
+    # the global step is 2^R global steps of dt0 / 2^R
+    prob, p = _rung_problem()
+    prob.u = np.ones(prob.n)            # one sound speed: limits within a factor two
+    prob.vel = 0.1 * prob.vel
+    d = oracle.density_h(p, prob.pos, prob.m, prob.h0)
+    f = oracle.forces(p, prob.pos, prob.vel, prob.m, d["h"], d["rho"], d["omega"], prob.u)
+    assert f["dt"].max() < 1.6 * f["dt"].min()
+    R = 2
+    dt0 = 2 ** R * float(f["dt"].min()) * 0.98
+    r = oracle.RungSimulation(p, prob.pos, prob.vel, prob.m, prob.u, prob.h0, max_rung=R)
+    r.global_step(dt0)
+    assert np.all(r.rung == R)
+    g = oracle.Simulation(p, prob.pos, prob.vel, prob.m, prob.u, prob.h0)
+    for _ in range(2 ** R):
+        g.step(dt_fixed=dt0 / 2 ** R)
+    assert np.allclose(r.x, g.x, rtol=0, atol=1e-13)
+    assert np.allclose(r.v, g.v, rtol=1e-11, atol=1e-13)
+    assert np.allclose(r.u, g.u, rtol=1e-11, atol=1e-13)
+
+
+def test_rungs_follow_the_time_step_limit_and_the_neighbour_limiter():
+    # a Sedov blast: hot centre on high rungs, cold gas on low ones; every
+    # active particle's new step respects its own limit (unless capped at
+    # the top rung), and moves to a lower rung only where the period divides
+    # the substep
+    prob = inputs.sedov(n=12)
+    p = oracle.Params(gamma=prob.gamma, alpha=prob.alpha, beta=prob.beta, box_lo=prob.box_lo,
+                      box_hi=prob.box_hi, periodic=prob.periodic)
+    R = 4
+    r = oracle.RungSimulation(p, prob.pos, prob.vel, prob.m, prob.u, prob.h0, max_rung=R)
+    dt0 = 0.02
+    r.global_step(dt0)
+    assert r.rung.max() >= 3 and r.rung.min() <= 1      # a real hierarchy
+    for s, (act, new, ratio) in enumerate(r.log):
+        assert np.all(s % 2 ** (R - new) == 0)          # boundaries line up
+        want = np.minimum(np.ceil(ratio), R)
+        assert np.all(new >= want)                       # step <= the particle's limit

@@ -24,6 +24,13 @@ def test_imbalance_normalisation_closed_form():
     # Wendland C2: 2 pi int_0^1 (21/2pi)(1-q)^4 (1+4q) q^3 dq
     #            = 21 (B(4,5) + 4 B(5,5)) = 21 (1/280 + 1/157.5) = 5/24
     assert oracle.imbalance_norm("wc2") == pytest.approx(24.0 / 5.0, rel=1e-12)
+    # Wendland C4: (495/16) (B(4,7) + 6 B(5,7) + 35/3 B(6,7)) = 35/192
+    assert oracle.imbalance_norm("wc4") == pytest.approx(192.0 / 35.0, rel=1e-12)
+    # Wendland C6: (1365/32) (B(4,9) + 8 B(5,9) + 25 B(6,9) + 32 B(7,9)) = 21/128
+    assert oracle.imbalance_norm("wc6") == pytest.approx(128.0 / 21.0, rel=1e-12)
+    # cubic spline: 16 (int_0^1/2 (q^3 - 6 q^5 + 6 q^6) dq + 2 int_1/2^1 (1-q)^3 q^3 dq)
+    #             = 16 (3/448 + 1/140) = 31/140
+    assert oracle.imbalance_norm("m4") == pytest.approx(140.0 / 31.0, rel=1e-12)
 
 
 def test_two_particle_interface_correction_matches_hand_values():
@@ -73,3 +80,40 @@ def test_correction_leaves_a_single_material_alone():
     one = np.zeros(prob.n, dtype=np.int32)
     out = oracle.interface_correction(p, prob.pos, prob.m, d["h"], d["rho"], prob.u, one, [1.0])
     assert np.max(np.abs(out["rho_corr"] / d["rho"] - 1.0)) < 1e-4
+
+
+def slab_problem(n=14):
+    """Two ideal gases in pressure and temperature equilibrium: a slab
+    0.25 < z < 0.75 of material 1 at density 2 (double particle mass, same
+    lattice) in material 0 at density 1; P = 1, gas constants 1 and 1/2 so
+    that T = P / (rho R) = 1 on both sides."""
+    prob = inputs.uniform(n=n, seed=71, jitter=0.1, vamp=0.0)
+    z = prob.pos[:, 2]
+    mat = ((z > 0.25) & (z < 0.75)).astype(np.int32)
+    rho_true = np.where(mat == 1, 2.0, 1.0)
+    prob.m = rho_true / prob.n
+    prob.u = 1.0 / ((prob.gamma - 1.0) * rho_true)
+    prob.extra["mat"] = mat
+    prob.extra["r_gas"] = (1.0, 0.5, 1.0, 1.0)
+    prob.extra["rho_true"] = rho_true
+    return prob
+
+
+def test_correction_moves_the_density_towards_the_eos_at_an_isothermal_interface():
+    prob = slab_problem()
+    p = oracle.Params(gamma=prob.gamma, box_lo=prob.box_lo, box_hi=prob.box_hi,
+                      periodic=prob.periodic)
+    d = oracle.density_h(p, prob.pos, prob.m, prob.h0)
+    ic = oracle.interface_correction(p, prob.pos, prob.m, d["h"], d["rho"], prob.u,
+                                     prob.extra["mat"], prob.extra["r_gas"])
+    rt = prob.extra["rho_true"]
+    err_sum = np.abs(d["rho"] / rt - 1.0)
+    err_ic = np.abs(ic["rho_corr"] / rt - 1.0)
+    # the kernel sum smooths the jump over h; the corrected density takes
+    # P and T from the particles away from the interface
+    assert np.max(err_ic) < 0.75 * np.max(err_sum)
+    assert np.mean(err_ic) < 0.75 * np.mean(err_sum)
+    # away from the interface nothing changes
+    z = prob.pos[:, 2]
+    far = (np.abs(z - 0.25) > 1.05 * np.max(d["h"])) & (np.abs(z - 0.75) > 1.05 * np.max(d["h"]))
+    assert np.max(np.abs(ic["rho_corr"][far] / d["rho"][far] - 1.0)) < 1e-3
