@@ -18,13 +18,16 @@
 // GPU mapping: one warp per sink bucket A, lane = sink particle.  The list
 // holds source buckets B >= A whose bounds pass the gather or scatter test
 // (Sec. 2.3.2); source particles are culled per particle, compacted into a
-// 128-entry shared-memory chunk, and each lane evaluates only its own hits
-// (128-bit mask).  Contributions to the sink stay in registers; the equal
-// and opposite contribution to the source goes straight to L2 as
-// fire-and-forget reductions (the SM does not wait): a xyz and du/dt|Pi as one
-// red.global.add.v4.f32, S as one red.global.add.f64 (which measured as fast
-// as keeping S in the FP32 vector: the reductions are not the bottleneck).
-// j > i is required inside bucket A, so every pair is computed exactly once.
+// 128-entry shared-memory chunk, and each lane marks its hits in a 128-bit
+// mask.  A chunk then takes ceil(hits / 32) rounds: every lane evaluates its
+// own hits up to that count and the surplus of the busier lanes is dealt to
+// the idle ones (force_chunk).  Contributions to a lane's own sink stay in
+// registers; the equal and opposite contribution to the source, and the sink
+// side of a dealt pair, go straight to L2 as fire-and-forget reductions (the
+// SM does not wait): a xyz and du/dt|Pi as one red.global.add.v4.f32, S as
+// one red.global.add.f64 (which measured as fast as keeping S in the FP32
+// vector: the reductions are not the bottleneck).  j > i is required inside
+// bucket A, so every pair is computed exactly once.
 //
 // Precision.  Pair arithmetic is FP32 on positions relative to the sink
 // bucket's origin.  S_i is a sum whose terms cancel (across a shear layer
@@ -34,9 +37,9 @@
 // fixed-point positions (units qx = q 2^-11 relative to the bucket origins),
 // converted to FP32 once, and the kernel factor 1 - q comes from the exact
 // integer N = h^2 - r^2 as (N qx^2 / h^2) / (1 + q) instead of from a rounded
-// q = r/h.  S is accumulated with a Kahan sum per term on the sink side and
-// in FP64 on the source side (the accelerations per 128-candidate chunk,
-// chunks Kahan-summed).  Instances whose buckets or h outgrow the
+// q = r/h.  S is accumulated with a Kahan sum per term on the sink side of a
+// lane's own pairs and in FP64 through L2 otherwise (the accelerations per
+// 128-candidate chunk, chunks Kahan-summed).  Instances whose buckets or h outgrow the
 // fixed-point range (tiny open boxes), and sink buckets whose pairs need a
 // periodic wrap of their own, use FP32 separations and q throughout.
 #include "sph_internal.cuh"
@@ -123,16 +126,29 @@ __global__ void k_predict(KParams kp, int n, const Inst *__restrict__ insts,
 #endif
 constexpr int kForceBlocksPerSM = SPH_FORCE_BLOCKS_PER_SM;
 
+
+// per-lane sink state kept in registers: what the candidate masks need, the
+// sink-side sums and the counters
 struct SinkState {
-    float px, py, pz, h, h2, ih, ih5;  // position, smoothing length, sigma h^-5
-    float vx, vy, vz, m;
-    float A, c, rho;
-    int ix, iy, iz, hq;                // fixed-point position and h (units qx)
+    float px, py, pz, h2;              // position in the sink frame, h^2
     int rg, rmx;                       // hierarchical steps: rung, largest partner rung
     Kahan ax, ay, az, S;
     float du, mumax;
     int i;
     unsigned pairs, av;
+};
+
+// per-warp shared-memory copy of the sink bucket: the pair loop reads the
+// sink of each pair from here, since a lane may evaluate a pair of another
+// lane's sink (load balancing, force_chunk)
+struct SinkStage {
+    union {
+        int4 ipos[32];   // fixed-point path: position (units qx) and h
+        float4 pos[32];  // FP32 path: position in the sink frame
+    };
+    float4 vel[32];  // predicted velocity, m
+    float4 th[32];   // A = P/(Omega rho^2), c, rho, h
+    float2 ih[32];   // 1/h, sigma h^-5
 };
 
 // per-warp shared-memory stage of one chunk of source candidates
@@ -159,18 +175,88 @@ __device__ __forceinline__ void sep3(const PBox &bx, float px, float py, float p
     }
 }
 
+// fire-and-forget reductions of the pair loop.  Nothing in the force kernel
+// reads what they write, so they carry no compiler memory barrier and the
+// next pair's shared-memory loads may be scheduled across them.
+__device__ __forceinline__ void red_v4_nb(float4 *addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+                 "f"(c), "f"(d));
+}
+__device__ __forceinline__ void red_f64_nb(double *addr, double a)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(a));
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+// position (0..127) of the q-th set bit (q from 0) of the 128-bit mask
+// a0 | a1 << 32 | a2 << 64 | a3 << 96; q < popcount of the mask
+__device__ __forceinline__ int select_bit128(unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                             int q)
+{
+    const int c0 = __popc(a0), c1 = __popc(a1), c2 = __popc(a2);
+    int base = 0;
+    unsigned x = a0;
+    if (q >= c0) {
+        q -= c0;
+        base = 32;
+        x = a1;
+        if (q >= c1) {
+            q -= c1;
+            base = 64;
+            x = a2;
+            if (q >= c2) {
+                q -= c2;
+                base = 96;
+                x = a3;
+            }
+        }
+    }
+    int c = __popc(x & 0xffffu);
+    if (q >= c) { q -= c; x >>= 16; base += 16; }
+    c = __popc(x & 0xffu);
+    if (q >= c) { q -= c; x >>= 8; base += 8; }
+    c = __popc(x & 0xfu);
+    if (q >= c) { q -= c; x >>= 4; base += 4; }
+    c = __popc(x & 0x3u);
+    if (q >= c) { q -= c; x >>= 2; base += 2; }
+    if (q >= (int)(x & 1u)) base += 1;
+    return base;
+}
+
 // viscosity parameters and fixed-point quantum of the sink's instance
 struct Visc {
     float alpha, beta, eps_av, qx, qx2;
 };
 
+// One staged chunk of candidates against the 32 sinks.
+//
 // SELF: the chunk holds the sink bucket's own particles, where only j > i
 // counts (every other source bucket lies after the sink bucket, so all its
 // particles do).  FIX: separations and 1 - q from the fixed-point positions.
+//
+// Load balance.  Lane l's hit mask holds c_l pairs; evaluated lane by lane
+// the warp would take max_l c_l rounds, about 2.4 times the mean on a
+// lattice.  Instead the chunk takes m = ceil(T / 32) rounds (T = sum c_l):
+// lane l evaluates its first min(c_l, m) hits itself (sink side summed in
+// registers) and the surplus hits of the lanes with c_l > m are dealt, in
+// lane order, to the free rounds of the lanes with c_l < m; a dealt pair
+// sends both of its sides to L2 as reductions.  RUNG keeps the lane-by-lane
+// loop (the rung limiter tracks each sink's partners in registers).
 template <class K, bool WRAP, bool SELF, bool FIX, bool RUNG>
-__device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, ForceStage &S, int c,
-                                            SinkState &s, bool valid, int lane, float4 *acc,
-                                            double *accS, unsigned *mumax, const RungArgs &ra)
+__device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, ForceStage &S,
+                                            const SinkStage &Q, int c, SinkState &s, bool valid,
+                                            int lane, int i0, float4 *acc, double *accS,
+                                            unsigned *mumax, const RungArgs &ra)
 {
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32) {
@@ -201,14 +287,17 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
     unsigned long long m0 = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
     unsigned long long m1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
     float sax = 0.f, say = 0.f, saz = 0.f;
-    // one pair (i, candidate k): every term, no side effects
+    // one pair (sink of lane o, candidate k): every term, no side effects
     struct PairTerms {
         float dx, dy, dz, cm, Si, mj, du, mneg, cs, Sj, du_j;
         int jj;
         bool app;
     };
-    auto pair_terms = [&](int k) -> PairTerms {
-        PairTerms o;
+    auto pair_terms = [&](int k, int o) -> PairTerms {
+        PairTerms t;
+        const float4 vi = Q.vel[o];
+        const float4 thi = Q.th[o];  // A, c, rho, h
+        const float2 ii = Q.ih[o];   // 1/h, sigma h^-5
         const float4 vj = S.vel[k];
         const float4 tj = S.th[k];
         const float hj = tj.w, ihj = S.ih[k];
@@ -217,78 +306,78 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         if (FIX) {
             // exact integer separation and N = h^2 - r^2 (units qx), each
             // converted to FP32 with one rounding
+            const int4 pi = Q.ipos[o];
             const int4 p = S.ipos[k];
-            const int ex = (int)((unsigned)s.ix - (unsigned)p.x);
-            const int ey = (int)((unsigned)s.iy - (unsigned)p.y);
-            const int ez = (int)((unsigned)s.iz - (unsigned)p.z);
+            const int ex = (int)((unsigned)pi.x - (unsigned)p.x);
+            const int ey = (int)((unsigned)pi.y - (unsigned)p.y);
+            const int ez = (int)((unsigned)pi.z - (unsigned)p.z);
             const long long r2q = (long long)ex * ex + (long long)ey * ey + (long long)ez * ez;
-            const long long ni = (long long)s.hq * s.hq - r2q;
+            const long long ni = (long long)pi.w * pi.w - r2q;
             const long long nj = (long long)p.w * p.w - r2q;
             dx = (float)ex * vp.qx;
             dy = (float)ey * vp.qx;
             dz = (float)ez * vp.qx;
             r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
-            const float qi = r * s.ih, qj = r * ihj;
+            const float qi = r * ii.x, qj = r * ihj;
             // 1 - q = (1 - q^2) / (1 + q) with 1 - q^2 = N qx^2 / h^2
-            const float ti = __fdividef((float)ni * (vp.qx2 * s.ih * s.ih), 1.f + qi);
+            const float ti = __fdividef((float)ni * (vp.qx2 * ii.x * ii.x), 1.f + qi);
             const float tj_ = __fdividef((float)nj * (vp.qx2 * ihj2), 1.f + qj);
-            Fi = ni > 0 ? s.ih5 * K::dwqt(qi, ti) : 0.f;
+            Fi = ni > 0 ? ii.y * K::dwqt(qi, ti) : 0.f;
             Fj = nj > 0 ? K::sigma * ihj2 * ihj2 * ihj * K::dwqt(qj, tj_) : 0.f;
         } else {
+            const float4 pi = Q.pos[o];
             const float4 q = S.pos[k];
-            sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
+            sep3<WRAP>(bx, pi.x, pi.y, pi.z, q, dx, dy, dz);
             r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
-            const float qi = r * s.ih, qj = r * ihj;
-            Fi = qi < 1.f ? s.ih5 * K::dwq(qi) : 0.f;
+            const float qi = r * ii.x, qj = r * ihj;
+            Fi = qi < 1.f ? ii.y * K::dwq(qi) : 0.f;
             Fj = qj < 1.f ? K::sigma * ihj2 * ihj2 * ihj * K::dwq(qj) : 0.f;
         }
-        const float wx = s.vx - vj.x, wy = s.vy - vj.y, wz = s.vz - vj.z;
+        const float wx = vi.x - vj.x, wy = vi.y - vj.y, wz = vi.z - vj.z;
         const float vr = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
         // viscosity, evaluated for every pair and switched by v_ij.r_ij < 0
-        o.app = vr < 0.f;
-        const float hb = 0.5f * (s.h + hj), cb = 0.5f * (s.c + tj.y), rb = 0.5f * (s.rho + tj.z);
+        t.app = vr < 0.f;
+        const float hb = 0.5f * (thi.w + hj), cb = 0.5f * (thi.y + tj.y),
+                    rb = 0.5f * (thi.z + tj.z);
         const float mu = __fdividef(hb * vr, fmaf(vp.eps_av * hb, hb, r2));
-        const float Pi = o.app ? __fdividef(fmaf(-vp.alpha * cb, mu, vp.beta * mu * mu), rb) : 0.f;
+        const float Pi = t.app ? __fdividef(fmaf(-vp.alpha * cb, mu, vp.beta * mu * mu), rb) : 0.f;
         const float Fb = 0.5f * (Fi + Fj);
-        const float coef = fmaf(s.A, Fi, fmaf(tj.x, Fj, Pi * Fb));
+        const float coef = fmaf(thi.x, Fi, fmaf(tj.x, Fj, Pi * Fb));
         const float du = 0.5f * Pi * vr * Fb;
-        o.mneg = o.app ? -mu : 0.f;
-        o.dx = dx;
-        o.dy = dy;
-        o.dz = dz;
-        o.cm = coef * vj.w;
-        o.Si = vj.w * vr * Fi;
-        o.mj = vj.w;
-        o.du = du;
-        o.cs = coef * s.m;
-        o.Sj = s.m * vr * Fj;
-        o.du_j = s.m * du;
-        o.jj = S.idx[k];
-        return o;
+        t.mneg = t.app ? -mu : 0.f;
+        t.dx = dx;
+        t.dy = dy;
+        t.dz = dz;
+        t.cm = coef * vj.w;
+        t.Si = vj.w * vr * Fi;
+        t.mj = vj.w;
+        t.du = du;
+        t.cs = coef * vi.w;
+        t.Sj = vi.w * vr * Fj;
+        t.du_j = vi.w * du;
+        t.jj = S.idx[k];
+        return t;
     };
-    // sink side in registers; source side straight into global memory
-    // (L2 reductions)
-    auto apply = [&](const PairTerms &o) {
-        sax = fmaf(-o.cm, o.dx, sax);
-        say = fmaf(-o.cm, o.dy, say);
-        saz = fmaf(-o.cm, o.dz, saz);
-        s.S.add(o.Si);
-        s.du = fmaf(o.mj, o.du, s.du);
-        s.mumax = fmaxf(s.mumax, o.mneg);
-        red_add_v4(&acc[o.jj], o.cs * o.dx, o.cs * o.dy, o.cs * o.dz, o.du_j);
-        red_add_f64(&accS[o.jj], (double)o.Sj);
-        if (o.app) {
-            atomicMax(&mumax[o.jj], __float_as_uint(o.mneg));
+    // the source side of a pair: straight into global memory (L2 reductions)
+    auto apply_far = [&](const PairTerms &t) {
+        red_v4_nb(&acc[t.jj], t.cs * t.dx, t.cs * t.dy, t.cs * t.dz, t.du_j);
+        red_f64_nb(&accS[t.jj], (double)t.Sj);
+        if (t.app) {
+            atomicMax(&mumax[t.jj], __float_as_uint(t.mneg));
             ++s.av;
         }
-        if (RUNG) {  // the rung limiter needs each particle's largest partner rung
-            const int rj = ra.rung[o.jj];
-            s.rmx = max(s.rmx, rj);
-            if (rung_active(ra.sub, ra.R, rj)) atomicMax(&ra.rmax[o.jj], s.rg);
-        }
         ++s.pairs;
+    };
+    // the sink side of a lane's own pair: registers
+    auto apply_own = [&](const PairTerms &t) {
+        sax = fmaf(-t.cm, t.dx, sax);
+        say = fmaf(-t.cm, t.dy, say);
+        saz = fmaf(-t.cm, t.dz, saz);
+        s.S.add(t.Si);
+        s.du = fmaf(t.mj, t.du, s.du);
+        s.mumax = fmaxf(s.mumax, t.mneg);
     };
     auto next = [&]() -> int {
         int k;
@@ -301,7 +390,66 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         }
         return k;
     };
-    while (m0 | m1) apply(pair_terms(next()));
+    if (RUNG) {
+        while (m0 | m1) {
+            const PairTerms t = pair_terms(next(), lane);
+            apply_own(t);
+            apply_far(t);
+            // the rung limiter needs each particle's largest partner rung
+            const int rj = ra.rung[t.jj];
+            s.rmx = max(s.rmx, rj);
+            if (rung_active(ra.sub, ra.R, rj)) atomicMax(&ra.rmax[t.jj], s.rg);
+        }
+    } else {
+        const int cnt = __popcll(m0) + __popcll(m1);
+        const int T = __reduce_add_sync(kFull, (unsigned)cnt);
+        const int m = (T + 31) >> 5;               // rounds of the chunk
+        const int cmin = (int)__reduce_min_sync(kFull, (unsigned)cnt);
+        const int sur = max(cnt - m, 0), fre = max(m - cnt, 0);
+        const int sex = warp_incl_scan(sur, lane) - sur;   // first surplus index of the lane
+        const int fex = warp_incl_scan(fre, lane) - fre;   // first free slot of the lane
+        const int stot = __shfl_sync(kFull, sex + sur, 31);
+        for (int r = 0; r < m; ++r) {
+            const bool own = r < cnt;
+            int k = own ? next() : 0;
+            int o = lane;
+            bool act = own;
+            if (r >= cmin && stot > 0) {  // warp-uniform: some lane has a free round
+                // surplus index u of this lane's free round, its donor d (the
+                // last lane whose surplus starts at or before u) and the
+                // donor's pending hits (it has taken ranks 0..r itself)
+                const int u = fex + (r - cnt);
+                int d = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int sd = __shfl_sync(kFull, sex, d + step);
+                    if (sd <= u) d += step;
+                }
+                const int sd = __shfl_sync(kFull, sex, d);
+                const unsigned a0 = __shfl_sync(kFull, (unsigned)m0, d);
+                const unsigned a1 = __shfl_sync(kFull, (unsigned)(m0 >> 32), d);
+                const unsigned a2 = __shfl_sync(kFull, (unsigned)m1, d);
+                const unsigned a3 = __shfl_sync(kFull, (unsigned)(m1 >> 32), d);
+                if (!own && u < stot) {
+                    k = select_bit128(a0, a1, a2, a3, m + (u - sd) - (r + 1));
+                    o = d;
+                    act = true;
+                }
+            }
+            if (act) {
+                const PairTerms t = pair_terms(k, o);
+                if (o == lane) {
+                    apply_own(t);
+                } else {  // a dealt pair: the donor's sink side to L2 as well
+                    const int io = i0 + o;
+                    red_v4_nb(&acc[io], -t.cm * t.dx, -t.cm * t.dy, -t.cm * t.dz, t.mj * t.du);
+                    red_f64_nb(&accS[io], (double)t.Si);
+                    if (t.app) atomicMax(&mumax[io], __float_as_uint(t.mneg));
+                }
+                apply_far(t);
+            }
+        }
+    }
     s.ax.add(sax);
     s.ay.add(say);
     s.az.add(saz);
@@ -316,7 +464,8 @@ struct SinkBounds {
 template <class K, bool WRAP, bool FIX, bool RUNG>
 __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, const PBox &bx,
                                              const Visc &vp, int A, int lane, ForceStage &S,
-                                             SinkState &s, bool valid, const SinkBounds sb,
+                                             const SinkStage &Q, SinkState &s, bool valid,
+                                             const SinkBounds sb,
                                              const int *__restrict__ bstart,
                                              const float4 *__restrict__ fpos,
                                              const float4 *__restrict__ fvel,
@@ -442,7 +591,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP, true, FIX, RUNG>(bx, vp, S, c, s, valid, lane, acc, accS, mumax,
+        force_chunk<K, WRAP, true, FIX, RUNG>(bx, vp, S, Q, c, s, valid, lane, bstart[A], acc, accS, mumax,
                                                ra);
         c = 0;
     }
@@ -460,7 +609,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
-            force_chunk<K, WRAP, false, FIX, RUNG>(bx, vp, S, c, s, valid, lane, acc, accS,
+            force_chunk<K, WRAP, false, FIX, RUNG>(bx, vp, S, Q, c, s, valid, lane, bstart[A], acc, accS,
                                                 mumax, ra);
             c = 0;
         }
@@ -469,14 +618,14 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
     if (c > 0) {
         __syncwarp();
         cands += c;
-        force_chunk<K, WRAP, false, FIX, RUNG>(bx, vp, S, c, s, valid, lane, acc, accS,
+        force_chunk<K, WRAP, false, FIX, RUNG>(bx, vp, S, Q, c, s, valid, lane, bstart[A], acc, accS,
                                                 mumax, ra);
     }
 }
 
 // 5 blocks of 4 warps per SM (96 registers; the fixed-point pair path spills
-// a few values): measured faster than 4 blocks with the 124 registers the
-// compiler picks without the cap
+// a few values; 43 KB of shared memory per block): measured faster than 4
+// blocks without spills
 template <class K, bool RUNG>
 __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, const Inst *__restrict__ insts,
                                                 const int *__restrict__ bstart,
@@ -494,6 +643,7 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
                                                 DevStatus *st)
 {
     __shared__ ForceStage stage[kWarpsPerBlock];
+    __shared__ SinkStage sstage[kWarpsPerBlock];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int A = blockIdx.x * kWarpsPerBlock + wib;
     if (A >= kp.nb) return;
@@ -506,20 +656,20 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     if (cnt == 0) return;  // padding slot
     const bool valid = lane < cnt;
     SinkState s;
+    SinkStage &Q = sstage[wib];
+    float hs;
     {
         float4 q = valid ? fpos[i] : make_float4(0.f, 0.f, 0.f, 1.f);
         float4 v = valid ? fvel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 t = valid ? fth[i] : make_float4(0.f, 0.f, 1.f, 1.f);
-        int4 p = valid ? ipos[i] : make_int4(0, 0, 0, 0);
-        s.px = q.x; s.py = q.y; s.pz = q.z; s.h = q.w;
+        hs = q.w;
+        s.px = q.x; s.py = q.y; s.pz = q.z;
         s.h2 = q.w * q.w;
-        s.ih = 1.f / q.w;
-        float ih2 = s.ih * s.ih;
-        s.ih5 = K::sigma * ih2 * ih2 * s.ih;
-        s.vx = v.x; s.vy = v.y; s.vz = v.z; s.m = v.w;
-        s.A = t.x; s.c = t.y; s.rho = t.z;
-        s.ix = p.x; s.iy = p.y; s.iz = p.z;
-        s.hq = p.w;
+        const float ih = 1.f / q.w;
+        const float ih2 = ih * ih;
+        Q.vel[lane] = v;
+        Q.th[lane] = make_float4(t.x, t.y, t.z, q.w);
+        Q.ih[lane] = make_float2(ih, K::sigma * ih2 * ih2 * ih);
         s.rg = RUNG && valid ? (int)ra.rung[i] : 0;
         s.rmx = -1;
         s.du = 0.f;
@@ -540,8 +690,8 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float lo = warp_min(valid ? p[a] : INFINITY), hi = warp_max(valid ? p[a] : -INFINITY);
-            float glo = warp_min(valid ? p[a] - s.h : INFINITY);
-            float ghi = warp_max(valid ? p[a] + s.h : -INFINITY);
+            float glo = warp_min(valid ? p[a] - hs : INFINITY);
+            float ghi = warp_max(valid ? p[a] + hs : -INFINITY);
             sb.bc[a] = 0.5f * (lo + hi);
             sb.br[a] = 0.5f * (hi - lo);
             sb.gc[a] = 0.5f * (glo + ghi);
@@ -552,7 +702,7 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     }
     {
         float dx = s.px - sb.gc[0], dy = s.py - sb.gc[1], dz = s.pz - sb.gc[2];
-        float rr = valid ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + s.h : 0.f;
+        float rr = valid ? sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + hs : 0.f;
         rr = warp_max(rr) * (1.f + 1e-6f) + I.eps_abs;
         sb.gR2 = rr * rr;
     }
@@ -560,17 +710,22 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     // separation fits 2^31 qx (largest bucket extent and largest h below the
     // limit) and no pair needs its own periodic wrap
     const bool fix = !wrap && Emax < I.fix_lim && Hmax < I.fix_lim;
+    if (fix)
+        Q.ipos[lane] = valid ? ipos[i] : make_int4(0, 0, 0, 0);
+    else
+        Q.pos[lane] = make_float4(s.px, s.py, s.pz, 0.f);
+    __syncwarp();
     unsigned long long cands = 0;
     if (fix)
-        force_bucket<K, false, true, RUNG>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+        force_bucket<K, false, true, RUNG>(kp, I, bx, vp, A, lane, stage[wib], Q, s, valid, sb, bstart,
                                      fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
                                      node, acc, accS, mumax, cands, ra);
     else if (wrap)
-        force_bucket<K, true, false, RUNG>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+        force_bucket<K, true, false, RUNG>(kp, I, bx, vp, A, lane, stage[wib], Q, s, valid, sb, bstart,
                                      fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
                                      node, acc, accS, mumax, cands, ra);
     else
-        force_bucket<K, false, false, RUNG>(kp, I, bx, vp, A, lane, stage[wib], s, valid, sb, bstart,
+        force_bucket<K, false, false, RUNG>(kp, I, bx, vp, A, lane, stage[wib], Q, s, valid, sb, bstart,
                                       fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
                                       node, acc, accS, mumax, cands, ra);
     if (valid) {

@@ -31,3 +31,21 @@ def test_error_report_is_exact_and_field_by_field():
     e2 = bench.error_vs_oracle(prob, planted, p)
     assert abs(e2["rho"] - 1e-4) < 1e-9
     assert all(e2[k] < 1e-12 for k in fields if k != "rho")
+
+
+def test_error_report_normalises_by_the_whole_field():
+    # the sample holds the particles where the field is largest, so the max
+    # norm is the whole field's, not the clusters'
+    obuild.build()
+    prob = inputs.uniform(n=12, seed=9, jitter=0.3, vamp=0.3)
+    p = oracle.Params(gamma=prob.gamma, alpha=prob.alpha, beta=prob.beta, box_lo=prob.box_lo,
+                      box_hi=prob.box_hi, periodic=prob.periodic)
+    full = _full_solution(prob, p)
+    k = int(np.argmax(np.abs(full["divv"])))
+    planted = dict(full)
+    planted["divv"] = full["divv"].copy()
+    planted["divv"][k] += 1e-3 * full["divv"][k]
+    e = bench.error_vs_oracle(prob, planted, p)
+    assert abs(e["divv"] - 1e-3) < 1e-9
+    assert set(bench._field_maxima(full).tolist()) <= set(range(prob.n))
+    assert len(bench._field_maxima(full)) == 4 * bench.FIELD_MAXIMA_PER_FIELD

@@ -3,8 +3,9 @@ oracle's integrator of the same scheme (oracle.RungSimulation), through the
 C ABI (sph_step_rungs): a Sedov blast on 12^3 particles whose hot centre
 sits four rungs above the cold gas, two global steps of 16 substeps.  The
 rungs must agree exactly (the test first checks that no rung decision of
-the oracle lies within 1e-2 of a power-of-two boundary, where FP32 and FP64
-time-step limits could round to different rungs); positions, velocities and
+the oracle lies within 2e-3 of a power-of-two boundary in log2 units, where
+FP32 and FP64 time-step limits could round to different rungs: the limits
+of the two agree to about 1e-5 relative, 1.4e-5 in log2 units); positions, velocities and
 internal energies within the tolerances of the global-step tracking test."""
 import numpy as np
 import pytest
@@ -31,7 +32,7 @@ def _compare(sph, prob, dt0, R, nglobal):
     for _ in range(nglobal):
         o.global_step(dt0)
     dist = min(float(np.min(np.abs(r - np.round(r)))) for _, _, r in o.log if len(r))
-    assert dist > 1e-2, dist
+    assert dist > 2e-3, dist
     sim = sph.Simulation(prob)
     try:
         for _ in range(nglobal):
@@ -54,7 +55,7 @@ def _compare(sph, prob, dt0, R, nglobal):
 
 def test_rungs_track_oracle_sedov(sph):
     prob = inputs.sedov(n=12)
-    errs, rungs, o = _compare(sph, prob, 0.017, 4, 2)
+    errs, rungs, o = _compare(sph, prob, 0.018, 4, 2)
     assert np.array_equal(rungs, o.rung)
     assert len(np.unique(rungs)) >= 3                  # a real hierarchy
     assert errs["x"] < 1e-6 and errs["v"] < 2e-4 and errs["u"] < 1e-5
