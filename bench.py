@@ -131,11 +131,11 @@ def hbm_peak_gbs():
 #  predict   v, u, a, du/dt, h, rho, Omega, relative position, instance
 #            read (82), force records, accumulators written (80)          = 162
 #  finalize  accumulators, records read (50), a, du/dt, div v, dt_i (28)  = 78
-#  kdk       x, v, u, a, du/dt, div v, h, instance read (86); x, v, u, h
-#            written (60)                                                 = 146
-#  conserved x, v, u, m read                                              = 60
+#  kdk       x, v, u, a, du/dt, div v, h, instance, m read (90); x, v, u,
+#            h written (60); the conserved totals' block partials of the
+#            new state on the way (the captured step)                     = 150
 HBM_BYTES_PER_PARTICLE = {"keys": 38, "permute": 448, "layout": 28, "buckets": 64,
-                          "predict": 162, "finalize": 78, "kdk": 146, "conserved": 60}
+                          "predict": 162, "finalize": 78, "kdk": 150}
 SORT_BYTES_PER_PASS = 32
 
 
@@ -360,16 +360,22 @@ def phase_profile(prob, params, dev, steps=5, sort_passes=4):
     import paper_2511_11425_gb300 as sph
     import dataclasses
     peak, src = hbm_peak_gbs()
-    # every profiled step re-sorts (so the key, sort, permute and layout
-    # phases are timed) and is followed by the conserved totals
+    # replays of the captured step, as timed (the kick-drift-kick leaves the
+    # conserved totals' partials, folded by the last launch), recorded with
+    # profiling on; every step re-sorts, so the key, sort, permute and
+    # layout phases are timed too
     sim = sph.Simulation(prob, dataclasses.replace(params, resort_period=1), device=dev)
+    s = torch.cuda.Stream(dev)
     try:
-        for _ in range(3):
-            sim.step()
-        sph.sph_set_profiling(sim.ctx, True)
-        for _ in range(steps):
-            sim.step()
-            sim.conserved()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                sph.sph_step(sim.ctx, sim.parts, 0.0, s)
+            sph.sph_set_profiling(sim.ctx, True)
+            sph.sph_graph_capture(sim.ctx, sim.parts, 0.0, s)
+            sph.sph_graph_launch(sim.ctx, s)
+            sph.sph_set_profiling(sim.ctx, True)  # clears the totals so far
+            for _ in range(steps):
+                sph.sph_graph_launch(sim.ctx, s)
         torch.cuda.synchronize(dev)
         times = sph.sph_phase_times(sim.ctx)
     finally:
@@ -1100,7 +1106,8 @@ def run_ours(args, rank, world, local_rank):
                 "roofline": roof, "roofline_other": other_line,
                 "roofline_hbm": profile["hbm"] if profile else None,
                 "phase_profile": ({"ms_per_step": profile["phase_ms_per_step"],
-                                   "note": "plain steps that all re-sort, totals after each",
+                                   "note": "replays of the captured step (totals included) "
+                                           "that all re-sort",
                                    "hbm_peak": profile["peak_source"]} if profile else None),
                 "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,

@@ -104,7 +104,8 @@ typedef struct {
     double  box_hi[3];
     int32_t periodic[3];   /* 1 = periodic axis (minimum image), 0 = open        */
     int32_t max_newton;    /* Newton iteration cap per particle (<= 255)         */
-    double  h_rel_tol;     /* Newton stops when |dh|/h < h_rel_tol               */
+    double  h_rel_tol;     /* error of the reported h relative to the root of the
+                              Newton iteration; see sph_density_h              */
     double  list_margin;   /* density lists gather within h (1 + list_margin)    */
     int32_t curve;         /* particle order: SPH_CURVE_HILBERT or SPH_CURVE_MORTON */
     int32_t group_log;     /* buckets per list walk = 2^group_log (1..3); 0 = 3  */
@@ -252,8 +253,15 @@ sph_status sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream);
  * 4/3 pi h^3 rho(h) = N_ngb m by Newton-Raphson with a bisection safeguard,
  * starting from h_seed (device array of n floats, curve order) or, if
  * h_seed is NULL, from p->h.  Writes p->h, p->rho, p->omega, p->nngb,
- * p->iters; h is the Newton update of the last evaluation (whose step was
- * below h_rel_tol), rho, Omega and nngb are those of the evaluated h.  In SPH_ENERGY_ISENTROPIC mode it also moves u along its adiabat
+ * p->iters; h is the Newton update h + dh of the last evaluation.  Newton
+ * converges quadratically: that update lies |g''/(2 g')| dh^2 from the root
+ * (g'' from the same kernel sums), and the iteration ends once this is below
+ * h_rel_tol h with |dh| < sqrt(h_rel_tol) h (at most 1e-2 h), or once
+ * |dh| < h_rel_tol h.  rho, Omega and nngb are reported at the updated h
+ * (the evaluated sums moved to first order in dh, nngb counted from the
+ * hits within sqrt(h_rel_tol) h of the support radius).  With the interface correction
+ * on, the step itself must be below h_rel_tol h and rho, Omega and nngb are
+ * those of the evaluated h.  In SPH_ENERGY_ISENTROPIC mode it also moves u along its adiabat
  * to the new density, u <- u (rho/rho_old)^(gamma-1), using the rho left in
  * p->rho by the previous call.  Then refreshes the box-of-balls bounds with
  * the new h (Sec. 2.3.3, bounds updated after the density pass).

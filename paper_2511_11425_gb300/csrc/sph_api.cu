@@ -317,6 +317,12 @@ void free_ctx(Ctx &c)
     for (cudaEvent_t e : c.prof.ev)
         if (e) cudaEventDestroy(e);
     c.prof.ev.clear();
+    for (int g = 0; g < 2; ++g) {
+        for (cudaEvent_t e : c.prof.gev[g])
+            if (e) cudaEventDestroy(e);
+        c.prof.gev[g].clear();
+        c.prof.gphase[g].clear();
+    }
 }
 
 // lay out instances of the given particle counts (offsets follow the order)
@@ -421,6 +427,23 @@ void prof_collect(Ctx &c)
         }
     }
     c.prof.phase.clear();
+}
+
+// the same for the launch groups recorded into captured step `slot`, after
+// a replay of it completed
+void prof_collect_graph(Ctx &c, int slot)
+{
+    const std::vector<int> &ph = c.prof.gphase[slot];
+    const std::vector<cudaEvent_t> &ev = c.prof.gev[slot];
+    for (size_t k = 0; k < ph.size(); ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
+            c.prof.ms[ph[k]] += ms;
+            c.prof.launches[ph[k]] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
 }
 
 sph_status begin(sph_ctx *ctx, cudaStream_t s)
@@ -624,6 +647,7 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.kp.energy_mode = prm[0].energy_mode;
     c.kp.max_newton = prm[0].max_newton;
     c.kp.h_rel_tol = (float)prm[0].h_rel_tol;
+    c.kp.h_step_tol = (float)std::min(std::sqrt(prm[0].h_rel_tol), 1e-2);
     c.kp.margin = (float)prm[0].list_margin;
     c.kp.fp64 = prm[0].precision == SPH_PRECISION_FP64 ? 1 : 0;
     c.kp.evolved = prm[0].density_mode == SPH_DENSITY_EVOLVED ? 1 : 0;
@@ -832,7 +856,7 @@ void count_build(Ctx &c, bool full, sph_status rc)
 
 // the whole step queued without host round trips
 sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool timed,
-                      bool full_build)
+                      bool full_build, bool totals)
 {
     if (timed) CK(record(c, c.ev0, s));
     if (full_build) {
@@ -845,7 +869,7 @@ sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s,
     if (rc) return rc;
     rc = q_forces(c, p, s, timed);
     if (rc) return rc;
-    CK(launch_kdk(c, *p, dt_fixed, s));
+    CK(launch_kdk(c, *p, dt_fixed, s, totals));
     return SPH_OK;
 }
 
@@ -887,7 +911,7 @@ extern "C" sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, 
     rc = begin(ctx, s);
     if (rc) return rc;
     const bool full = need_full_build(c);
-    rc = queue_step(c, p, dt_fixed, s, true, full);
+    rc = queue_step(c, p, dt_fixed, s, true, full, false);
     if (rc) return rc;
     rc = finish(ctx, s);
     step_done(c, rc, true);
@@ -1012,12 +1036,16 @@ sph_status capture_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t 
     c.err.clear();
     c.capturing = true;
     sph_status qrc = SPH_OK;
+    c.prof.slot = full ? 0 : 1;
+    c.prof.gphase[c.prof.slot].clear();
     if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) qrc = SPH_ERR_CUDA;
     // phase events are captured too (event record nodes), so a replay reports
-    // the same per-phase times as sph_step
-    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true, full);
-    // the totals of the stepped state ride along (read with sph_graph_totals)
-    if (qrc == SPH_OK && launch_conserved(c, *p, s) != cudaSuccess) qrc = SPH_ERR_CUDA;
+    // the same per-phase times as sph_step (and, with profiling on while
+    // capturing, the same launch groups)
+    // the totals of the stepped state ride along (read with
+    // sph_graph_totals): their block partials come out of the kick-drift-kick
+    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true, full, true);
+    if (qrc == SPH_OK && launch_conserved(c, *p, s, true) != cudaSuccess) qrc = SPH_ERR_CUDA;
     if (qrc == SPH_OK && cudaMemcpyAsync(c.cons_host, c.cons_out, sizeof(double) * 9 * c.kp.ninst,
                                          cudaMemcpyDeviceToHost, s) != cudaSuccess)
         qrc = SPH_ERR_CUDA;
@@ -1072,6 +1100,7 @@ sph_status graph_settle(sph_ctx *ctx, cudaStream_t s, bool full, double *dt_used
 {
     Ctx &c = ctx->c;
     sph_status rc = settle(ctx, s);
+    if (rc == SPH_OK && c.prof.on) prof_collect_graph(c, full ? 0 : 1);
     step_done(c, rc, true);
     count_build(c, full, rc);
     if (rc == SPH_OK) {

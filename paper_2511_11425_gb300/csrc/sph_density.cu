@@ -81,8 +81,12 @@ __device__ __forceinline__ int next_hit(unsigned long long &m0, unsigned long lo
 
 // the FP64 form's per-lane density sums of one pass
 struct DSums {
-    double w = 0.0, q = 0.0;
+    double w = 0.0, q = 0.0, qq = 0.0;
 };
+
+// per-lane record of the hits with q in [1 - tau, 1 + tau) (shared memory):
+// the neighbour count at the Newton-updated h (density_bucket)
+constexpr int kShell = 4;
 
 // the interface correction's kernel-imbalance sum (Eq. Kernel_imbalance):
 // sum_j kappa_ij (r_j - r_i) m_j w(q_j), kappa = +1 same material, -1 not
@@ -97,10 +101,13 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
                                               int c, int lane, float px, float py, float pz,
                                               float h2, float ih, const double *pd, double hd,
                                               double ihd, bool active, Kahan &Sw, Kahan &Sq,
-                                              DSums &D, int &cnt, int i, long long cap,
-                                              int &emitted, int64_t *ids_out,
-                                              const int64_t *__restrict__ id_in)
+                                              Kahan &Sqq, DSums &D, int &cnt, int i,
+                                              long long cap, int &emitted, int64_t *ids_out,
+                                              const int64_t *__restrict__ id_in, float tau,
+                                              float h2e, float *shell, int &ns)
 {
+    // RELAX: the masks reach h (1 + tau); hits beyond h only enter the shell
+    constexpr bool RELAX = !IC && !EMIT;
     const int nwords = (c + 31) >> 5;
     for (int k = c + lane; k < 32 * nwords; k += 32)
         cand[k] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
@@ -111,16 +118,27 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
     hit_masks<WRAP>(bx, cand, nwords, px, py, pz, h2, active, m0, m1);
     int nh = 0;
     if (!D64) {
-        float sw = 0.f, sq = 0.f;
+        float sw = 0.f, sq = 0.f, sqq = 0.f;
         while (m0 | m1) {
             const int k = next_hit(m0, m1);
             const float4 q = cand[k];
             const float r2 = sep2<WRAP>(bx, px, py, pz, q);
             const float r = r2 * rsqrtf(fmaxf(r2, 1e-37f));
             const float qq = r * ih;
+            if (RELAX) {
+                // inside: the support test the masks make without the shell;
+                // shell entries keep q with the sign of that decision
+                const bool inside = r2 < h2e;
+                if (qq >= 1.f - tau) {
+                    if (ns < kShell) shell[ns] = inside ? qq : -qq;
+                    ++ns;
+                }
+                if (!inside) continue;
+            }
             const float wv = K::w(qq), dq = K::dwq(qq);
             sw = fmaf(q.w, wv, sw);
             sq = fmaf(q.w * dq, qq * qq, sq);
+            if (RELAX) sqq = fmaf(q.w * K::d2w(qq), qq * qq, sqq);
             ++nh;
             if (IC) {
                 float dx = q.x - px, dy = q.y - py, dz = q.z - pz;  // r_j - r_i
@@ -144,9 +162,11 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
         }
         Sw.add(sw);
         Sq.add(sq);
+        if (RELAX) Sqq.add(sqq);
     } else {
         const double h2d = hd * hd;
-        double sw = 0.0, sq = 0.0;
+        const double h2o = RELAX ? h2d * (1.0 + (double)tau) * (1.0 + (double)tau) : h2d;
+        double sw = 0.0, sq = 0.0, sqq = 0.0;
         while (m0 | m1) {
             const int k = next_hit(m0, m1);
             const double4_16a q = candd[k];
@@ -157,10 +177,19 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
                     if (bx.per[a]) d[a] -= I.Ld[a] * rint(d[a] * I.invLd[a]);
             }
             const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
-            if (!(r2 < h2d)) continue;
+            if (!(r2 < h2o)) continue;
             const double qq = sqrt(r2) * ihd;
+            if (RELAX) {
+                const bool inside = r2 < h2d;
+                if (qq >= 1.0 - (double)tau) {
+                    if (ns < kShell) shell[ns] = inside ? (float)qq : -(float)qq;
+                    ++ns;
+                }
+                if (!inside) continue;
+            }
             sw = fma(q.w, K::wd(qq), sw);
             sq = fma(q.w * K::dwqd(qq), qq * qq, sq);
+            if (RELAX) sqq = fma(q.w * K::d2wd(qq), qq * qq, sqq);
             ++nh;
             if (EMIT) {
                 int j = candj[k];
@@ -172,6 +201,7 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
         }
         D.w += sw;
         D.q += sq;
+        D.qq += sqq;
     }
     cnt += nh;
 }
@@ -181,9 +211,10 @@ __device__ __forceinline__ void density_chunk(const PBox &bx, const Inst &I, flo
 template <class K, bool WRAP, bool EMIT, bool D64, bool IC>
 __device__ __forceinline__ void density_bucket(
     const KParams &kp, const Inst &I, const PBox &bx, int A, int i0, int lane, float4 *cand,
-    double4_16a *candd, int *candj, unsigned char *candm, const uint8_t *__restrict__ mat,
-    float *ic_e, const float4 *__restrict__ pm, const double4_16a *__restrict__ pmd,
-    const int *__restrict__ bstart, const unsigned *__restrict__ list_cnt,
+    double4_16a *candd, int *candj, unsigned char *candm, float *shell,
+    const uint8_t *__restrict__ mat, float *ic_e, const float4 *__restrict__ pm,
+    const double4_16a *__restrict__ pmd, const int *__restrict__ bstart,
+    const unsigned *__restrict__ list_cnt,
     const unsigned *__restrict__ list_off, const unsigned *__restrict__ list,
     const int *__restrict__ origin, const float4 *__restrict__ node, float *h_seed, float *h_out,
     float *rho_out, float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h,
@@ -192,6 +223,13 @@ __device__ __forceinline__ void density_bucket(
     bool valid, const float *cen)
 {
     using Real = typename std::conditional<D64, double, float>::type;
+    // step rule (Newton ends once its step is below sqrt(h_rel_tol) h, the
+    // outputs moved to the updated h): off for fixed h, the emitting
+    // evaluation and the interface correction
+    constexpr bool RELAX = !IC && !EMIT;
+    const bool relax = RELAX && fixed_h == 0;
+    const float tau = relax ? kp.h_step_tol : 0.f;
+    float *myshell = RELAX ? shell + lane * kShell : nullptr;
     const unsigned lt = (1u << lane) - 1u;
     const int i = i0 + lane;
     const Real n_ngb = (Real)I.n_ngb;
@@ -273,24 +311,29 @@ __device__ __forceinline__ void density_bucket(
         const float hf = D64 ? (float)h * (1.f + 1e-5f) + eps_abs : (float)h;
         const float h2 = hf * hf, ih = 1.f / hf;
         const double ihd = D64 ? 1.0 / (double)h : 0.0;
+        // with the step rule (relax) the masks and the culling reach
+        // h (1 + tau): the shell of hits the count at the updated h needs
+        const float hc = relax ? hf * (1.f + tau) : hf;
+        const float h2m = hc * hc;
         // box of balls and ball of balls of the active lanes (Sec. 2.3.2: a
         // source must overlap both shapes)
         float bc[3], br[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float bl = warp_min(done ? INFINITY : p[a] - hf);
-            float bh = warp_max(done ? -INFINITY : p[a] + hf);
+            float bl = warp_min(done ? INFINITY : p[a] - hc);
+            float bh = warp_max(done ? -INFINITY : p[a] + hc);
             bc[a] = 0.5f * (bl + bh);
             br[a] = 0.5f * (bh - bl);
         }
         float bb2;
         {
             float dx = p[0] - bc[0], dy = p[1] - bc[1], dz = p[2] - bc[2];
-            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + hf;
+            float rr = done ? 0.f : sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + hc;
             rr = warp_max(rr) * (1.f + 1e-6f) + eps_abs;
             bb2 = rr * rr;
         }
-        Kahan Sw, Sq;
+        Kahan Sw, Sq, Sqq;
+        int ns = 0;
         DSums D;
         ImbSum V;
         int cnt = 0, c = 0;
@@ -358,9 +401,10 @@ __device__ __forceinline__ void density_bucket(
                 __syncwarp();
                 if (!done) cands += c;
                 density_chunk<K, WRAP, EMIT, D64, IC>(bx, I, cand, candd, candj, candm, mat_i, V,
-                                                      c, lane, p[0], p[1], p[2], h2, ih, pd,
-                                                      (double)h, ihd, !done, Sw, Sq, D, cnt, i,
-                                                      cap, emitted, ids_out, id_in);
+                                                      c, lane, p[0], p[1], p[2], h2m, ih, pd,
+                                                      (double)h, ihd, !done, Sw, Sq, Sqq, D, cnt,
+                                                      i, cap, emitted, ids_out, id_in, tau, h2,
+                                                      myshell, ns);
                 __syncwarp();
                 c = 0;
             }
@@ -370,9 +414,9 @@ __device__ __forceinline__ void density_bucket(
             __syncwarp();
             if (!done) cands += c;
             density_chunk<K, WRAP, EMIT, D64, IC>(bx, I, cand, candd, candj, candm, mat_i, V, c,
-                                                  lane, p[0], p[1], p[2], h2, ih, pd, (double)h,
-                                                  ihd, !done, Sw, Sq, D, cnt, i, cap, emitted,
-                                                  ids_out, id_in);
+                                                  lane, p[0], p[1], p[2], h2m, ih, pd, (double)h,
+                                                  ihd, !done, Sw, Sq, Sqq, D, cnt, i, cap,
+                                                  emitted, ids_out, id_in, tau, h2, myshell, ns);
             __syncwarp();
         }
         if (!done) {
@@ -389,10 +433,24 @@ __device__ __forceinline__ void density_bucket(
                 Real dg = -fpt * sigma * sqv / (mi * h);
                 if (g < 0) lo = h; else hi = h;
                 Real hn = dg > 0 ? h - g / dg : (Real)NAN;
-                if (isfinite(hn) && fabs(hn - h) < (Real)kp.h_rel_tol * h) {
+                const Real dh = hn - h;
+                // Newton converges quadratically: the updated h lies
+                // |g''/(2 g')| dh^2 from the root, with g''/g' = -(2 S_q +
+                // S_qq)/(S_q h) from the same sums.  Step rule: accept once
+                // that is below h_rel_tol h and |dh| < sqrt(h_rel_tol) h
+                // (the width of the shell of hits; the shell must be whole
+                // and hn inside the list's radius).  Without the step rule
+                // the step itself must be below h_rel_tol h.
+                bool step_ok = false;
+                if (relax && isfinite(hn) && fabs(dh) < (Real)tau * h && ns <= kShell && hn > 0 &&
+                    hn <= (Real)R) {
+                    const Real sqqv = D64 ? (Real)D.qq : (Real)Sqq.s;
+                    const Real curv = fabs((2 * sqv + sqqv) / (2 * sqv));  // |g''/(2g')| h
+                    step_ok = curv * dh * dh < (Real)kp.h_rel_tol * h * h;
+                }
+                if ((isfinite(hn) && fabs(dh) < (Real)kp.h_rel_tol * h) || step_ok) {
                     // converged: report the Newton update of the last
-                    // evaluation (quadratically closer to the root; rho,
-                    // Omega and n_i stay those of the evaluated h)
+                    // evaluation
                     record = true;
                     h_final = hn;
                 } else {
@@ -427,6 +485,27 @@ __device__ __forceinline__ void density_bucket(
                     out_rho = (Real)(K::sigma * (float)swv * ih * ih * ih);
                 }
                 out_n = nn;
+                if (relax && h_final != h) {
+                    // rho, Omega and n_i at the reported h: the sums moved
+                    // to first order in dh (dS_w/dh = -S_q/h and dS_q/dh =
+                    // -(S_q + S_qq)/h with S_qq = sum m q^2 w''(q)), the
+                    // count from the shell of hits near q = 1
+                    const Real dh = h_final - h;
+                    const Real sqqv = D64 ? (Real)D.qq : (Real)Sqq.s;
+                    const Real swn = swv - dh * sqv / h;
+                    const Real sqn = sqv - dh * (sqv + sqqv) / h;
+                    const Real ihn = (Real)1 / h_final;
+                    out_rho = sigma * swn * ihn * ihn * ihn;
+                    out_om = -sqn / (3 * swn);
+                    if (ns <= kShell) {
+                        const float ratio = (float)(h_final / h);
+                        for (int k = 0; k < ns; ++k) {
+                            const float v = myshell[k];
+                            if (ratio >= 1.f && v < 0.f && -v < ratio) ++out_n;
+                            if (ratio < 1.f && v > 0.f && v >= ratio) --out_n;
+                        }
+                    }
+                }
                 if (IC) {  // Eq. Kernel_imbalance: I = alpha |V| / (h sum m w)
                     const float vm = sqrtf(fmaf(V.x, V.x, fmaf(V.y, V.y, V.z * V.z)));
                     const float Ii = I.ic_alpha * vm / ((float)h * (float)swv);
@@ -471,7 +550,7 @@ __device__ __forceinline__ void density_bucket(
 // one sink bucket A (one warp)
 template <class K, bool EMIT, bool D64, bool IC>
 __device__ __forceinline__ void density_slot(
-    const uint8_t *__restrict__ mat, float *ic_e, unsigned char *candm,
+    const uint8_t *__restrict__ mat, float *ic_e, unsigned char *candm, float *shell,
     const KParams &kp, const Inst *__restrict__ insts, const float4 *__restrict__ pm,
     const double4_16a *__restrict__ pmd, const int *__restrict__ bstart,
     const int *__restrict__ binst, const unsigned *__restrict__ list_cnt,
@@ -508,14 +587,14 @@ __device__ __forceinline__ void density_slot(
     }
     if (wrap)
         density_bucket<K, true, EMIT, D64, IC>(kp, I, bx, A, i0, lane, cand, candd, candj, candm,
-                                               mat, ic_e, pm, pmd,
+                                               shell, mat, ic_e, pm, pmd,
                                            bstart, list_cnt, list_off, list, origin, node, h_seed,
                                            h_out, rho_out, omega_out, nngb_out, iters_out, fixed_h,
                                            cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
                                            gflag, st, me, valid, cen);
     else
         density_bucket<K, false, EMIT, D64, IC>(kp, I, bx, A, i0, lane, cand, candd, candj,
-                                                candm, mat, ic_e, pm, pmd,
+                                                candm, shell, mat, ic_e, pm, pmd,
                                             bstart, list_cnt, list_off, list, origin, node, h_seed,
                                             h_out, rho_out, omega_out, nngb_out, iters_out,
                                             fixed_h, cap, count_out, ids_out, id_in, redo_out,
@@ -541,12 +620,14 @@ __global__ void __launch_bounds__(128, 5) k_density(
     __shared__ double4_16a candd_s[D64 ? kWarpsPerBlock : 1][D64 ? kChunk : 1];
     __shared__ int candj_s[EMIT ? kWarpsPerBlock : 1][EMIT ? kChunk : 1];
     __shared__ unsigned char candm_s[IC ? kWarpsPerBlock : 1][IC ? kChunk : 1];
+    constexpr bool RELAX = !IC && !EMIT;
+    __shared__ float shell_s[RELAX ? kWarpsPerBlock : 1][RELAX ? 32 * kShell : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double4_16a *candd = D64 ? candd_s[wib] : nullptr;
     if (!group_ids) {  // every bucket, one warp each
         const int A = blockIdx.x * kWarpsPerBlock + wib;
         if (A < kp.nb)
-            density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
+            density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, RELAX ? shell_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
                                        origin, h_seed, h_out, rho_out, omega_out, nngb_out,
                                        iters_out, fixed_h, cap, count_out, ids_out, id_in,
                                        redo_out, redo_cnt_out, gflag, node, st, cand_s[wib],
@@ -562,7 +643,7 @@ __global__ void __launch_bounds__(128, 5) k_density(
         const Inst &Ig = insts[binst[fb]];
         const int j = bi & ((1 << kGroupLog) - 1);
         if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) continue;
-        density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
+        density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, RELAX ? shell_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
                                    origin, h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
                                    fixed_h, cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
                                    gflag, node, st, cand_s[wib], candd,

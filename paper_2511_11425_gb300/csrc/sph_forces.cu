@@ -39,7 +39,7 @@
 // integer N = h^2 - r^2 as (N qx^2 / h^2) / (1 + q) instead of from a rounded
 // q = r/h.  S is accumulated with a Kahan sum per term on the sink side of a
 // lane's own pairs and in FP64 through L2 otherwise (the accelerations per
-// 128-candidate chunk, chunks Kahan-summed).  Instances whose buckets or h outgrow the
+// 128-candidate chunk, the chunks' partial sums added in FP32).  Instances whose buckets or h outgrow the
 // fixed-point range (tiny open boxes), and sink buckets whose pairs need a
 // periodic wrap of their own, use FP32 separations and q throughout.
 #include "sph_internal.cuh"
@@ -132,9 +132,9 @@ constexpr int kForceBlocksPerSM = SPH_FORCE_BLOCKS_PER_SM;
 struct SinkState {
     float px, py, pz, h2;              // position in the sink frame, h^2
     int rg, rmx;                       // hierarchical steps: rung, largest partner rung
-    Kahan ax, ay, az, S;
+    float ax, ay, az;                  // sums of the chunks' partial sums
+    Kahan S;
     float du, mumax;
-    int i;
     unsigned pairs, av;
 };
 
@@ -278,7 +278,7 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
                 sep3<WRAP>(bx, s.px, s.py, s.pz, q, dx, dy, dz);
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 unsigned hit = __float_as_uint(r2 - fmaxf(s.h2, q.w)) >> 31;
-                if (SELF) hit &= S.idx[32 * ww + b] > s.i ? 1u : 0u;
+                if (SELF) hit &= S.idx[32 * ww + b] > i0 + lane ? 1u : 0u;
                 mw = mw * 2u + hit;
             }
             if (ww == 0) w0 = mw; else if (ww == 1) w1 = mw; else if (ww == 2) w2 = mw; else w3 = mw;
@@ -450,9 +450,9 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
             }
         }
     }
-    s.ax.add(sax);
-    s.ay.add(say);
-    s.az.add(saz);
+    s.ax += sax;
+    s.ay += say;
+    s.az += saz;
     __syncwarp();
 }
 
@@ -477,7 +477,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
                                              const int *__restrict__ origin,
                                              const float4 *__restrict__ node, float4 *acc,
                                              double *accS, unsigned *mumax,
-                                             unsigned long long &cands, const RungArgs &ra)
+                                             unsigned &cands, const RungArgs &ra)
 {
     const unsigned lt = (1u << lane) - 1u;
     // Filter the group's list for this bucket (Sec. 2.3.2 tests with the
@@ -520,33 +520,40 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         const unsigned bal = filter_word(w);
         if (lane == (int)w) myword = bal;
     }
-    // stage the culled particles of source bucket B after the c staged ones
-    auto stage = [&](int B, int c) -> int {
-        // origin offset o_B - o_A in the sink frame (nearest periodic image),
-        // as FP32 and, for the fixed-point path, in units of qx modulo 2^32
-        float3 off;
-        unsigned o3[3];
-        {
-            float d[3];
+    // what staging needs of a source bucket: its first particle and length
+    // and its origin minus the sink bucket's (grid points)
+    struct SrcRec {
+        int j0, len, dk[3];
+    };
+    auto src_rec = [&](int B) -> SrcRec {
+        SrcRec r;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int dk = origin[a * kp.nb + B] - origin[a * kp.nb + A];
-                float f = (float)dk * I.qf;
-                int nimg = 0;
-                if (bx.per[a]) {
-                    nimg = (int)rintf(f * bx.invL[a]);
-                    f -= bx.L[a] * (float)nimg;
-                }
-                d[a] = f;
-                o3[a] = ((unsigned)dk << kFixShift) - (unsigned)nimg * I.LQ[a];
-            }
-            off = make_float3(d[0], d[1], d[2]);
-        }
-        const int j0 = bstart[B];
-        const int j = j0 + lane;
-        const bool vj = lane < bucket_len(bstart, B);
+        for (int a = 0; a < 3; ++a) r.dk[a] = origin[a * kp.nb + B] - origin[a * kp.nb + A];
+        r.j0 = bstart[B];
+        r.len = bucket_len(bstart, B);
+        return r;
+    };
+    // stage the culled particles of the source bucket r after the c staged ones
+    auto stage = [&](const SrcRec &r, int c) -> int {
+        const int j = r.j0 + lane;
+        const bool vj = lane < r.len;
         const float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float sp[3] = {off.x + q.x, off.y + q.y, off.z + q.z};
+        // origin offset in the sink frame (nearest periodic image), as FP32
+        // and, for the fixed-point path, in units of qx modulo 2^32
+        float d[3];
+        unsigned o3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float f = (float)r.dk[a] * I.qf;
+            int nimg = 0;
+            if (bx.per[a]) {
+                nimg = (int)rintf(f * bx.invL[a]);
+                f -= bx.L[a] * (float)nimg;
+            }
+            d[a] = f;
+            o3[a] = ((unsigned)r.dk[a] << kFixShift) - (unsigned)nimg * I.LQ[a];
+        }
+        float sp[3] = {d[0] + q.x, d[1] + q.y, d[2] + q.z};
         // gather: inside the sink's box of balls and ball of balls;
         // scatter: the source's own ball reaches the sink cell bound
         bool gbox = true;
@@ -587,7 +594,7 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         return c;
     };
     // the sink bucket itself (the only source bucket needing j > i)
-    int c = stage(A, 0);
+    int c = stage(src_rec(A), 0);
     if (c > 0) {
         __syncwarp();
         cands += c;
@@ -600,12 +607,25 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
       // words past the first 32 (long lists in the overflow arena) are
       // filtered when reached
       unsigned mw = w < 32 ? __shfl_sync(kFull, myword, w) : filter_word(w);
+      if (!mw) continue;
+      // the records of this word's accepted entries, one per lane, fetched
+      // together (one round of dependent loads per word, not per entry)
+      SrcRec mine{};
+      int myB = -1;
+      if ((mw >> lane) & 1u) {
+          myB = (int)gl[32 * w + lane];
+          if (myB != A) mine = src_rec(myB);
+      }
       while (mw) {
-        const unsigned e = 32 * w + __ffs(mw) - 1;
+        const int l = __ffs(mw) - 1;
         mw &= mw - 1u;
-        const int B = (int)gl[e];
-        if (B == A) continue;
-        c = stage(B, c);
+        if (__shfl_sync(kFull, myB, l) == A) continue;
+        SrcRec r;
+        r.j0 = __shfl_sync(kFull, mine.j0, l);
+        r.len = __shfl_sync(kFull, mine.len, l);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) r.dk[a] = __shfl_sync(kFull, mine.dk[a], l);
+        c = stage(r, c);
         if (c > kChunk - 32) {
             __syncwarp();
             cands += c;
@@ -674,7 +694,7 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
         s.rmx = -1;
         s.du = 0.f;
         s.mumax = 0.f;
-        s.i = valid ? i : 0x7fffffff;
+        s.ax = s.ay = s.az = 0.f;
         s.pairs = 0;
         s.av = 0;
     }
@@ -715,7 +735,7 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     else
         Q.pos[lane] = make_float4(s.px, s.py, s.pz, 0.f);
     __syncwarp();
-    unsigned long long cands = 0;
+    unsigned cands = 0;
     if (fix)
         force_bucket<K, false, true, RUNG>(kp, I, bx, vp, A, lane, stage[wib], Q, s, valid, sb, bstart,
                                      fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
@@ -729,7 +749,7 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
                                       fpos, fvel, fth, ipos, list_cnt, list_off, list, origin,
                                       node, acc, accS, mumax, cands, ra);
     if (valid) {
-        red_add_v4(&acc[i], s.ax.s, s.ay.s, s.az.s, s.du);
+        red_add_v4(&acc[i], s.ax, s.ay, s.az, s.du);
         red_add_f64(&accS[i], (double)s.S.s - (double)s.S.c);
         if (s.mumax > 0.f) atomicMax(&mumax[i], __float_as_uint(s.mumax));
         if (RUNG && s.rmx >= 0) atomicMax(&ra.rmax[i], s.rmx);
@@ -739,7 +759,7 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     if (lane == 0) {
         atomicAdd(&st->force_pairs, wp);
         atomicAdd(&st->force_av_pairs, wav);
-        atomicAdd(&st->force_cand, cands * 32ull);
+        atomicAdd(&st->force_cand, (unsigned long long)cands * 32ull);
     }
 }
 

@@ -50,7 +50,8 @@ __device__ __forceinline__ void kdk_particle(
     const float *__restrict__ ax, const float *__restrict__ ay, const float *__restrict__ az,
     const float *__restrict__ dudt_h, const float *__restrict__ dudt_av, int energy_mode,
     const double *__restrict__ dts, float h_next, float *rho, const float4 *__restrict__ fth,
-    const float *__restrict__ divv)
+    const float *__restrict__ divv, double *xo = nullptr, double *vo = nullptr,
+    double *uo = nullptr)
 {
     const int k = pinst[i];
     const Inst &I = insts[k];
@@ -64,7 +65,8 @@ __device__ __forceinline__ void kdk_particle(
     vx[i] = v0;
     vy[i] = v1;
     vz[i] = v2;
-    u[i] += kick * ud;
+    const double un = u[i] + kick * ud;
+    u[i] = un;
     // evolved density (mass conservation equation), kicked like u with the
     // rate -rho_pred div v of this step's force pass
     if (rho) rho[i] = (float)((double)rho[i] - kick * (double)fth[i].z * (double)divv[i]);
@@ -90,6 +92,15 @@ __device__ __forceinline__ void kdk_particle(
     y[i] = p[1];
     z[i] = p[2];
     h[i] = h_next;
+    if (xo) {
+        xo[0] = p[0];
+        xo[1] = p[1];
+        xo[2] = p[2];
+        vo[0] = v0;
+        vo[1] = v1;
+        vo[2] = v2;
+        *uo = un;
+    }
 }
 
 // The smoothing length is advanced with the drift as the seed of the next
@@ -124,32 +135,27 @@ __global__ void k_kdk(KParams kp, int n, const Inst *__restrict__ insts,
 // instance folds the block partials in order (bit-identical from run to run)
 constexpr int kConsThreads = 256;
 
-__global__ void __launch_bounds__(kConsThreads) k_cons_partial(
-    const Inst *__restrict__ insts, const double *__restrict__ x, const double *__restrict__ y,
-    const double *__restrict__ z, const double *__restrict__ vx, const double *__restrict__ vy,
-    const double *__restrict__ vz, const double *__restrict__ u, const float *__restrict__ m,
-    double *part)
+// one particle into the running sums: momentum q = m v, then L += x × q,
+// 2 E_kin += q·v and E_int += m u as fused multiply-adds (the factor 1/2 of
+// E_kin is applied once, to the total)
+__device__ __forceinline__ void cons_add(double acc[9], double mi, const double p[3],
+                                         const double v[3], double u)
 {
-    const Inst &I = insts[blockIdx.y];
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const int b0 = I.off + blockIdx.x * kConsChunk, b1 = min(b0 + kConsChunk, I.off + I.n);
-    // per particle: momentum q = m v, then L += x × q, 2 E_kin += q·v and
-    // E_int += m u as fused multiply-adds into the running sums (the factor
-    // 1/2 of E_kin is applied once, to the total)
-    for (int i = b0 + threadIdx.x; i < b1; i += kConsThreads) {
-        const double mi = (double)m[i];
-        const double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
-        const double q[3] = {mi * v[0], mi * v[1], mi * v[2]};
-        acc[0] += mi;
-        acc[1] += q[0];
-        acc[2] += q[1];
-        acc[3] += q[2];
-        acc[4] = fma(p[1], q[2], fma(-p[2], q[1], acc[4]));
-        acc[5] = fma(p[2], q[0], fma(-p[0], q[2], acc[5]));
-        acc[6] = fma(p[0], q[1], fma(-p[1], q[0], acc[6]));
-        acc[7] = fma(q[0], v[0], fma(q[1], v[1], fma(q[2], v[2], acc[7])));
-        acc[8] = fma(mi, u[i], acc[8]);
-    }
+    const double q[3] = {mi * v[0], mi * v[1], mi * v[2]};
+    acc[0] += mi;
+    acc[1] += q[0];
+    acc[2] += q[1];
+    acc[3] += q[2];
+    acc[4] = fma(p[1], q[2], fma(-p[2], q[1], acc[4]));
+    acc[5] = fma(p[2], q[0], fma(-p[0], q[2], acc[5]));
+    acc[6] = fma(p[0], q[1], fma(-p[1], q[0], acc[6]));
+    acc[7] = fma(q[0], v[0], fma(q[1], v[1], fma(q[2], v[2], acc[7])));
+    acc[8] = fma(mi, u, acc[8]);
+}
+
+// the block's nine partial sums in a fixed tree order, stored at `out`
+__device__ __forceinline__ void cons_block_store(const double acc[9], double *out)
+{
     __shared__ double sm[9][kConsThreads];
 #pragma unroll
     for (int k = 0; k < 9; ++k) sm[k][threadIdx.x] = acc[k];
@@ -161,8 +167,64 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(
         }
         __syncthreads();
     }
-    if (threadIdx.x < 9)
-        part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 9 + threadIdx.x] = sm[threadIdx.x][0];
+    if (threadIdx.x < 9) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kConsThreads) k_cons_partial(
+    const Inst *__restrict__ insts, const double *__restrict__ x, const double *__restrict__ y,
+    const double *__restrict__ z, const double *__restrict__ vx, const double *__restrict__ vy,
+    const double *__restrict__ vz, const double *__restrict__ u, const float *__restrict__ m,
+    double *part)
+{
+    const Inst &I = insts[blockIdx.y];
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int b0 = I.off + blockIdx.x * kConsChunk, b1 = min(b0 + kConsChunk, I.off + I.n);
+    for (int i = b0 + threadIdx.x; i < b1; i += kConsThreads) {
+        const double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
+        cons_add(acc, (double)m[i], p, v, u[i]);
+    }
+    cons_block_store(acc, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 9);
+}
+
+// the kick-drift-kick of k_kdk with the totals' block partials of the
+// stepped state on the way (the captured step): the same slices and order as
+// k_cons_partial, so k_cons_final gives the same bits.  A step that failed
+// earlier moves nothing and sums the state as it is.
+template <bool CORR>
+__global__ void __launch_bounds__(kConsThreads) k_kdk_cons(
+    KParams kp, const Inst *__restrict__ insts, const unsigned short *__restrict__ pinst,
+    double *x, double *y, double *z, double *vx, double *vy, double *vz, double *u, float *h,
+    const float *__restrict__ ax, const float *__restrict__ ay, const float *__restrict__ az,
+    const float *__restrict__ dudt_h, const float *__restrict__ dudt_av,
+    const float *__restrict__ divv, const double *__restrict__ dts,
+    const float *__restrict__ corr, float *rho_ev, const float4 *__restrict__ fth,
+    const float *__restrict__ m, double *part, const DevStatus *st)
+{
+    const Inst &I = insts[blockIdx.y];
+    const bool move = st->code == 0;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int b0 = I.off + blockIdx.x * kConsChunk, b1 = min(b0 + kConsChunk, I.off + I.n);
+    for (int i = b0 + threadIdx.x; i < b1; i += kConsThreads) {
+        double p[3], v[3], un;
+        if (move) {
+            float e = (float)dts[2 * pinst[i] + 1] * divv[i] * (1.f / 3.f);
+            if (CORR) e += corr[i];
+            const float f = expf(e);
+            kdk_particle(i, insts, pinst, x, y, z, vx, vy, vz, u, h, ax, ay, az, dudt_h, dudt_av,
+                         kp.energy_mode, dts, h[i] * fminf(fmaxf(f, 0.5f), 2.f), rho_ev, fth,
+                         divv, p, v, &un);
+        } else {
+            p[0] = x[i];
+            p[1] = y[i];
+            p[2] = z[i];
+            v[0] = vx[i];
+            v[1] = vy[i];
+            v[2] = vz[i];
+            un = u[i];
+        }
+        cons_add(acc, (double)m[i], p, v, un);
+    }
+    cons_block_store(acc, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 9);
 }
 
 // nine warps per instance, one per total; each lane sums a fixed stride of
@@ -178,7 +240,8 @@ __global__ void k_cons_final(int nblocks, const double *part, double *out)
     if (lane == 0) out[blockIdx.x * 9 + q] = q == 7 ? 0.5 * s : s;  // E_kin = (sum m v^2) / 2
 }
 
-cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s)
+cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s,
+                       bool totals)
 {
     const int n = (int)p.n;
     const int ni = c.kp.ninst;
@@ -191,7 +254,18 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
         if (e != cudaSuccess) return e;
     }
     const int g = (n + 255) / 256;
-    if (corr)
+    const dim3 gc(c.cons_blocks > 0 ? c.cons_blocks : 1, ni);
+    if (totals && corr)
+        k_kdk_cons<true><<<gc, kConsThreads, 0, s>>>(
+            c.kp, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.h,
+            p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr,
+            c.kp.evolved ? p.rho : nullptr, c.fth, p.m, c.cons_part, c.st);
+    else if (totals)
+        k_kdk_cons<false><<<gc, kConsThreads, 0, s>>>(
+            c.kp, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.h,
+            p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr,
+            c.kp.evolved ? p.rho : nullptr, c.fth, p.m, c.cons_part, c.st);
+    else if (corr)
         k_kdk<true><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
                                       p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
                                       p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr,
@@ -312,13 +386,15 @@ cudaError_t launch_kdk_rungs(Ctx &c, const sph_particles &p, const RungArgs &ra,
     return cudaGetLastError();
 }
 
-cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
+cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s,
+                             bool partials_ready)
 {
     const int nb = c.cons_blocks > 0 ? c.cons_blocks : 1;
-    c.launches += 2;
+    c.launches += partials_ready ? 1 : 2;
     const int pr = prof_begin(c, s, SPH_PHASE_CONSERVED);
-    k_cons_partial<<<dim3(nb, c.kp.ninst), kConsThreads, 0, s>>>(
-        c.inst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.m, c.cons_part);
+    if (!partials_ready)
+        k_cons_partial<<<dim3(nb, c.kp.ninst), kConsThreads, 0, s>>>(
+            c.inst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.m, c.cons_part);
     k_cons_final<<<c.kp.ninst, 288, 0, s>>>(nb, c.cons_part, c.cons_out);
     prof_end(c, s, pr);
     return cudaGetLastError();

@@ -143,6 +143,7 @@ struct KParams {
     int evolved;         // SPH_DENSITY_EVOLVED: rho is state (mass conservation)
     int ic;              // interface correction on (Sec. 2.3.4)
     float h_rel_tol, margin;
+    float h_step_tol;    // sqrt(h_rel_tol), at most 1e-2: Newton step that ends the iteration
 };
 
 // the substep of a hierarchical step that a kernel works on (sph_step_rungs):
@@ -172,9 +173,15 @@ struct Prof {
     bool on = false;
     std::vector<cudaEvent_t> ev;  // pool: pair k = events 2k, 2k + 1
     std::vector<int> phase;       // phase of each pair recorded in this call
+    // the same recorded into the captured steps (event record nodes), per
+    // graph: 0 = the re-sorting step, 1 = the refitting step
+    std::vector<cudaEvent_t> gev[2];
+    std::vector<int> gphase[2];
+    int slot = 0;                 // graph being captured
     double ms[SPH_PHASE_COUNT] = {};
     unsigned long long launches[SPH_PHASE_COUNT] = {};
 };
+constexpr int kProfGraph = 1 << 20;  // prof_begin's index offset for captured pairs
 
 struct Ctx {
     std::vector<sph_params> prm;  // per instance
@@ -328,23 +335,34 @@ struct Ctx {
 };
 
 // open a timed launch group of `phase` on stream s (returns its pair index,
-// or -1 when not profiling or capturing); close it with prof_end
+// offset by kProfGraph while a step is being captured, or -1 when not
+// profiling); close it with prof_end
 inline int prof_begin(Ctx &c, cudaStream_t s, int phase)
 {
-    if (!c.prof.on || c.capturing) return -1;
-    const size_t k = c.prof.phase.size();
-    while (c.prof.ev.size() < 2 * (k + 1)) {
+    if (!c.prof.on) return -1;
+    std::vector<cudaEvent_t> &ev = c.capturing ? c.prof.gev[c.prof.slot] : c.prof.ev;
+    std::vector<int> &ph = c.capturing ? c.prof.gphase[c.prof.slot] : c.prof.phase;
+    const size_t k = ph.size();
+    while (ev.size() < 2 * (k + 1)) {
         cudaEvent_t e = nullptr;
         if (cudaEventCreate(&e) != cudaSuccess) return -1;
-        c.prof.ev.push_back(e);
+        ev.push_back(e);
     }
-    if (cudaEventRecord(c.prof.ev[2 * k], s) != cudaSuccess) return -1;
-    c.prof.phase.push_back(phase);
-    return (int)k;
+    // while capturing, an external record makes an event record node (a
+    // plain record would only order the capture's own streams)
+    const cudaError_t e = c.capturing ? cudaEventRecordWithFlags(ev[2 * k], s, cudaEventRecordExternal)
+                                      : cudaEventRecord(ev[2 * k], s);
+    if (e != cudaSuccess) return -1;
+    ph.push_back(phase);
+    return (int)k + (c.capturing ? kProfGraph : 0);
 }
 inline void prof_end(Ctx &c, cudaStream_t s, int k)
 {
-    if (k >= 0) cudaEventRecord(c.prof.ev[2 * k + 1], s);
+    if (k >= kProfGraph)
+        cudaEventRecordWithFlags(c.prof.gev[c.prof.slot][2 * (k - kProfGraph) + 1], s,
+                                 cudaEventRecordExternal);
+    else if (k >= 0)
+        cudaEventRecord(c.prof.ev[2 * k + 1], s);
 }
 
 // ---------------------------------------------------------------------------
@@ -495,6 +513,7 @@ struct Kahan {
 // smoothing kernels, support radius h, dimensionless q = r/h in [0,1):
 //   w(q)        kernel shape (normalisation sigma applied by the caller)
 //   dwq(q)      w'(q)/q, finite at q = 0 for every kernel here
+//   d2w(q)      w''(q) (the first-order move of the h-derivative sum)
 // Cubic spline (M4) and Wendland C2/C4/C6 in their 3D forms (Sec. 2.3).
 // ---------------------------------------------------------------------------
 struct KWC2 {
@@ -526,6 +545,17 @@ struct KWC2 {
         (void)q;
         return -20.f * t * t * t;
     }
+    // w''(q)
+    __device__ __forceinline__ static float d2w(float q)
+    {
+        const float t = 1.f - q;
+        return 20.f * t * t * fmaf(4.f, q, -1.f);
+    }
+    __device__ __forceinline__ static double d2wd(double q)
+    {
+        const double t = 1.0 - q;
+        return 20.0 * t * t * fma(4.0, q, -1.0);
+    }
 };
 struct KWC4 {
     static constexpr float sigma = 4.923856051905513f;  // 495 / (32 pi)
@@ -550,6 +580,16 @@ struct KWC4 {
     {
         float t2 = t * t, t5 = t2 * t2 * t;
         return (-56.f / 3.f) * t5 * fmaf(5.f, q, 1.f);
+    }
+    __device__ __forceinline__ static float d2w(float q)
+    {
+        const float t = 1.f - q, t2 = t * t;
+        return (-56.f / 3.f) * t2 * t2 * fmaf(q, fmaf(-35.f, q, 4.f), 1.f);
+    }
+    __device__ __forceinline__ static double d2wd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t;
+        return (-56.0 / 3.0) * t2 * t2 * fma(q, fma(-35.0, q, 4.0), 1.0);
     }
 };
 struct KWC6 {
@@ -576,6 +616,16 @@ struct KWC6 {
         float t2 = t * t, t4 = t2 * t2, t7 = t4 * t2 * t;
         return -22.f * t7 * fmaf(q, fmaf(16.f, q, 7.f), 1.f);
     }
+    __device__ __forceinline__ static float d2w(float q)
+    {
+        const float t = 1.f - q, t2 = t * t;
+        return -22.f * t2 * t2 * t2 * fmaf(q, fmaf(q, fmaf(-160.f, q, -15.f), 6.f), 1.f);
+    }
+    __device__ __forceinline__ static double d2wd(double q)
+    {
+        const double t = 1.0 - q, t2 = t * t;
+        return -22.0 * t2 * t2 * t2 * fma(q, fma(q, fma(-160.0, q, -15.0), 6.0), 1.0);
+    }
 };
 struct KM4 {
     static constexpr float sigma = 2.5464790894703255f;  // 8 / pi
@@ -599,6 +649,14 @@ struct KM4 {
     __device__ __forceinline__ static float dwqt(float q, float t)
     {
         return q < 0.5f ? fmaf(18.f, q, -12.f) : -6.f * t * t / q;
+    }
+    __device__ __forceinline__ static float d2w(float q)
+    {
+        return q < 0.5f ? fmaf(36.f, q, -12.f) : 12.f * (1.f - q);
+    }
+    __device__ __forceinline__ static double d2wd(double q)
+    {
+        return q < 0.5 ? fma(36.0, q, -12.0) : 12.0 * (1.0 - q);
     }
 };
 
@@ -641,8 +699,13 @@ cudaError_t launch_interface(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s,
                             const RungArgs *ra = nullptr);
 // integration (sph_integrate.cu)
-cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s);
-cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s);
+// totals: the captured step's kick-drift-kick also leaves the conserved
+// totals' block partials of the stepped state (launch_conserved with
+// partials_ready then only folds them)
+cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s,
+                       bool totals = false);
+cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s,
+                             bool partials_ready = false);
 // hierarchical step: kicks of the active particles, rung choice, drift of all
 cudaError_t launch_kdk_rungs(Ctx &c, const sph_particles &p, const RungArgs &ra, cudaStream_t s);
 // permute the rungs with the particles at a full build
