@@ -131,11 +131,11 @@ def hbm_peak_gbs():
 #  predict   v, u, a, du/dt, h, rho, Omega, relative position, instance
 #            read (82), force records, accumulators written (80)          = 162
 #  finalize  accumulators, records read (50), a, du/dt, div v, dt_i (28)  = 78
-#  kdk       x, v, u, a, du/dt, div v, h, instance, m read (90); x, v, u,
-#            h written (60); the conserved totals' block partials of the
-#            new state on the way (the captured step)                     = 150
+#  kdk       x, v, u, a, du/dt, div v, h, instance read (86); x, v, u, h
+#            written (60)                                                 = 146
+#  conserved x, v, u, m read                                              = 60
 HBM_BYTES_PER_PARTICLE = {"keys": 38, "permute": 448, "layout": 28, "buckets": 64,
-                          "predict": 162, "finalize": 78, "kdk": 150}
+                          "predict": 162, "finalize": 78, "kdk": 146, "conserved": 60}
 SORT_BYTES_PER_PASS = 32
 
 
@@ -360,10 +360,9 @@ def phase_profile(prob, params, dev, steps=5, sort_passes=4):
     import paper_2511_11425_gb300 as sph
     import dataclasses
     peak, src = hbm_peak_gbs()
-    # replays of the captured step, as timed (the kick-drift-kick leaves the
-    # conserved totals' partials, folded by the last launch), recorded with
-    # profiling on; every step re-sorts, so the key, sort, permute and
-    # layout phases are timed too
+    # replays of the captured step as timed (conserved totals included),
+    # recorded with profiling on; every step re-sorts, so the key, sort,
+    # permute and layout phases are timed too
     sim = sph.Simulation(prob, dataclasses.replace(params, resort_period=1), device=dev)
     s = torch.cuda.Stream(dev)
     try:

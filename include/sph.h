@@ -328,7 +328,7 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * steps (Sec. 2.3.6, Time integration).  The step is cut into 2^max_rung
  * substeps of dt0 / 2^max_rung; a particle on rung r steps 2^(max_rung - r)
  * substeps at a time and is active on the substeps that its period
- * divides.  Every substep runs the density pass for all particles, predicts
+ * divides.  Every substep runs the density pass, predicts
  * every particle's v and u to the substep time (v + (tau - T/2) a, tau the
  * time since its last step boundary, T its period; v, u are half-step
  * values), evaluates the forces (all pairs that have an active particle take
@@ -344,12 +344,21 @@ sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, double *dt_
  * re-sorts the particles, the others refit the bounds.  Mixed precision and
  * summed density only (SPH_ERR_ARG); not with the learned seed
  * (SPH_ERR_STATE).  A failed substep leaves x, v, u as they were after the
- * substeps before it.  Synchronous (one status read at the end).  FastGas
- * (density passes for the active particles' neighbourhoods only) is not
- * built: every substep runs the density pass for every particle.
+ * substeps before it.  Synchronous (one status read at the end).
+ * FastGas (on by default, sph_set_fastgas): after each substep's density
+ * walk the groups holding an active particle or a listed neighbour of one
+ * are marked (from the density lists, both directions), and the density
+ * pass, the force walk and the force pass run over the marked groups only;
+ * the other particles keep h, rho and Omega of their last pass.  Off, every
+ * substep solves every particle's density and sums every pair.
  */
 sph_status sph_step_rungs(sph_ctx *ctx, sph_particles *p, double dt0, int32_t max_rung,
                           void *stream);
+
+/* sph_set_fastgas: on != 0 restricts the substeps of sph_step_rungs to the
+ * active particles' neighbourhoods (FastGas, Sec. 2.3.6); 0 solves every
+ * particle on every substep.  Takes effect at the next call. */
+sph_status sph_set_fastgas(sph_ctx *ctx, int32_t on);
 
 /* sph_get_rungs: rung of each of the first n particles (HOST array, current
  * particle order); zeros before the first sph_step_rungs.  Synchronous. */

@@ -35,7 +35,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_build_cells", "sph_density_h", "sph
            "sph_graph_capture", "sph_graph_launch", "sph_graph_totals", "sph_mlp_set_weights", "sph_mlp_get_weights",
            "sph_mlp_set_seed_mode", "sph_mlp_record", "sph_mlp_samples", "sph_mlp_get_samples",
            "sph_mlp_load_samples", "sph_bucket_layout", "sph_set_list_arena", "sph_set_profiling",
-           "sph_step_rungs", "sph_get_rungs",
+           "sph_step_rungs", "sph_get_rungs", "sph_set_fastgas",
            "sph_mlp_train", "sph_mlp_grad", "sph_mlp_infer")
 MLP_NPARAM = 1249
 SEED_MODES = {"analytic": 0, "mlp": 1}
@@ -120,6 +120,7 @@ def lib():
         L.sph_set_profiling.argtypes = [vp, C.c_int32]
         L.sph_step_rungs.argtypes = [vp, pp, dbl, C.c_int32, vp]
         L.sph_get_rungs.argtypes = [vp, vp, i64]
+        L.sph_set_fastgas.argtypes = [vp, C.c_int32]
         fp = C.POINTER(C.c_float)
         L.sph_mlp_set_weights.argtypes = [vp, fp, i64]
         L.sph_mlp_get_weights.argtypes = [vp, fp, i64]
@@ -568,6 +569,11 @@ def sph_step_rungs(ctx, parts: Particles, dt0: float, max_rung: int, stream=None
     s = parts.c()
     _check(ctx, lib().sph_step_rungs(ctx, C.byref(s), float(dt0), int(max_rung),
                                      _stream(stream)))
+
+
+def sph_set_fastgas(ctx, on: bool):
+    """FastGas on (default) or off for the substeps of sph_step_rungs."""
+    _check(ctx, lib().sph_set_fastgas(ctx, 1 if on else 0))
 
 
 def sph_get_rungs(ctx, n: int):

@@ -298,7 +298,7 @@ void free_ctx(Ctx &c)
                     c.digit_tot, c.tmp, c.bstart, c.binst, c.origin, c.gfirst, c.gflag,
                     c.list_cnt, c.list_off, c.arena_used, c.list, c.redo, c.node, c.refit,
                     c.pm, c.pmd, c.fveld, c.fthd, c.acc64, c.ipos, c.fpos, c.fvel, c.fth,
-                    c.acc, c.accS, c.mumax, c.rho_sum, c.ic_e, c.ic_pt, c.rung, c.rmax, c.rho_old, c.h_seed, c.mirror};
+                    c.acc, c.accS, c.mumax, c.rho_sum, c.ic_e, c.ic_pt, c.rung, c.rmax, c.bact, c.gmark, c.fg_list, c.rho_old, c.h_seed, c.mirror};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mptrs[] = {c.mlp.w, c.mlp.m, c.mlp.v, c.mlp.frag, c.mlp.gpart, c.mlp.loss,
@@ -544,7 +544,11 @@ sph_status ensure_layout(Ctx &c, const sph_particles *p)
 }
 
 // ---- phases: queue only ------------------------------------------------------
-sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t s, bool timed)
+// fg: a hierarchical substep with FastGas on: after the walk, mark the
+// groups of the active particles and of their neighbours, and solve only
+// those (the others keep h, rho, Omega of their last pass)
+sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t s, bool timed,
+                     const RungArgs *fg = nullptr)
 {
     const size_t bytes = sizeof(float) * (size_t)p->n;
     const bool isen = c.kp.energy_mode == SPH_ENERGY_ISENTROPIC && c.rho_valid;
@@ -556,8 +560,9 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
         CK(cudaMemcpyAsync(c.mlp.seed0, c.h_seed, bytes, cudaMemcpyDeviceToDevice, s));
     if (timed) CK(record(c, c.kev[0], s));
     CK(launch_walk(c, *p, WALK_DENSITY, -1, c.h_seed, s));
+    if (fg) CK(launch_fastgas_mark(c, *fg, s));
     if (timed) CK(record(c, c.kev[1], s));
-    CK(launch_density(c, *p, c.h_seed, -1, 0, 0, nullptr, nullptr, s));
+    CK(launch_density(c, *p, c.h_seed, -1, 0, 0, nullptr, nullptr, s, fg != nullptr));
     if (timed) CK(record(c, c.kev[2], s));
     // groups whose h left the list coverage: re-walk and re-solve on the
     // device (the launches exit at once when nothing is queued)
@@ -579,8 +584,9 @@ sph_status q_density(Ctx &c, sph_particles *p, const float *h_seed, cudaStream_t
     return SPH_OK;
 }
 
+// fastgas: walk and sum only the marked groups (the queue q_density left)
 sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed,
-                    const RungArgs *ra = nullptr)
+                    const RungArgs *ra = nullptr, bool fastgas = false)
 {
     if (timed) CK(record(c, c.kev[3], s));
     if (c.kp.ic) {
@@ -588,18 +594,20 @@ sph_status q_forces(Ctx &c, sph_particles *p, cudaStream_t s, bool timed,
         // pass over the density lists, before the force walk replaces them
         CK(launch_predict(c, *p, s, ra));
         CK(launch_interface(c, *p, s));
-        CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
+        if (fastgas) CK(launch_walk_queue(c, WALK_FORCE, c.fg_list, &c.st->fg_cnt, nullptr, s));
+        else CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
     } else {
         // predictor + EOS on the side stream while the force walk runs here
         CK(cudaEventRecord(c.fork, s));
         CK(cudaStreamWaitEvent(c.side, c.fork, 0));
         CK(launch_predict(c, *p, c.side, ra));
         CK(cudaEventRecord(c.join, c.side));
-        CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
+        if (fastgas) CK(launch_walk_queue(c, WALK_FORCE, c.fg_list, &c.st->fg_cnt, nullptr, s));
+        else CK(launch_walk(c, *p, WALK_FORCE, -1, nullptr, s));
         CK(cudaStreamWaitEvent(s, c.join, 0));
     }
     if (timed) CK(record(c, c.kev[4], s));
-    CK(launch_forces(c, *p, s, ra));
+    CK(launch_forces(c, *p, s, ra, fastgas));
     if (timed) CK(record(c, c.kev[5], s));
     CK(launch_finalize(c, *p, s, ra));
     CK(record(c, c.out_force, s));  // a, du/dt, div v, dt_i are final
@@ -655,6 +663,8 @@ sph_status create_ctx(const sph_params *prm, int ninst, const std::vector<int64_
     c.resort_period = prm[0].resort_period > 0 ? prm[0].resort_period : 1;
     c.kp.ninst = ninst;
     const Sizes z = layout_sizes(counts, c.prm);
+    c.cap_nb = z.nb;
+    c.cap_ng = z.ng;
     sph_status rc = allocate(c, z, ninst);
     if (rc == SPH_OK) rc = set_layout(c, counts);
     if (rc == SPH_OK && cudaDeviceSynchronize() != cudaSuccess) rc = SPH_ERR_CUDA;
@@ -856,7 +866,7 @@ void count_build(Ctx &c, bool full, sph_status rc)
 
 // the whole step queued without host round trips
 sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s, bool timed,
-                      bool full_build, bool totals)
+                      bool full_build)
 {
     if (timed) CK(record(c, c.ev0, s));
     if (full_build) {
@@ -869,7 +879,7 @@ sph_status queue_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t s,
     if (rc) return rc;
     rc = q_forces(c, p, s, timed);
     if (rc) return rc;
-    CK(launch_kdk(c, *p, dt_fixed, s, totals));
+    CK(launch_kdk(c, *p, dt_fixed, s));
     return SPH_OK;
 }
 
@@ -911,7 +921,7 @@ extern "C" sph_status sph_step(sph_ctx *ctx, sph_particles *p, double dt_fixed, 
     rc = begin(ctx, s);
     if (rc) return rc;
     const bool full = need_full_build(c);
-    rc = queue_step(c, p, dt_fixed, s, true, full, false);
+    rc = queue_step(c, p, dt_fixed, s, true, full);
     if (rc) return rc;
     rc = finish(ctx, s);
     step_done(c, rc, true);
@@ -947,6 +957,13 @@ extern "C" sph_status sph_step_rungs(sph_ctx *ctx, sph_particles *p, double dt0,
             return failf(c, SPH_ERR_CUDA, "cudaMalloc of the rung arrays failed");
         CK(cudaMemset(c.rung, 0, cap));
     }
+    if (c.fastgas && !c.bact) {
+        const size_t nbc = (size_t)std::max<int64_t>(c.cap_nb, 1);
+        const size_t ngc = (size_t)std::max<int64_t>(c.cap_ng, 1);
+        if (dalloc(&c.bact, nbc) != cudaSuccess || dalloc(&c.gmark, ngc) != cudaSuccess ||
+            dalloc(&c.fg_list, ngc) != cudaSuccess)
+            return failf(c, SPH_ERR_CUDA, "cudaMalloc of the FastGas arrays failed");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     rc = begin(ctx, s);
     if (rc) return rc;
@@ -959,8 +976,8 @@ extern "C" sph_status sph_step_rungs(sph_ctx *ctx, sph_particles *p, double dt0,
         // others refit the bounds to the drifted particles
         if (sub == 0) CK(launch_build(c, *p, s));
         else CK(launch_refit(c, *p, s));
-        rc = q_density(c, p, nullptr, s, false);
-        if (rc == SPH_OK) rc = q_forces(c, p, s, false, &ra);
+        rc = q_density(c, p, nullptr, s, false, c.fastgas ? &ra : nullptr);
+        if (rc == SPH_OK) rc = q_forces(c, p, s, false, &ra, c.fastgas);
         if (rc == SPH_OK) CK(launch_kdk_rungs(c, *p, ra, s));
         ra.started = 1;
     }
@@ -977,6 +994,13 @@ extern "C" sph_status sph_step_rungs(sph_ctx *ctx, sph_particles *p, double dt0,
         c.rho_valid = true;
     }
     return rc;
+}
+
+extern "C" sph_status sph_set_fastgas(sph_ctx *ctx, int32_t on)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    ctx->c.fastgas = on != 0;
+    return SPH_OK;
 }
 
 extern "C" sph_status sph_get_rungs(sph_ctx *ctx, uint8_t *out, int64_t n)
@@ -1042,10 +1066,9 @@ sph_status capture_step(Ctx &c, sph_particles *p, double dt_fixed, cudaStream_t 
     // phase events are captured too (event record nodes), so a replay reports
     // the same per-phase times as sph_step (and, with profiling on while
     // capturing, the same launch groups)
-    // the totals of the stepped state ride along (read with
-    // sph_graph_totals): their block partials come out of the kick-drift-kick
-    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true, full, true);
-    if (qrc == SPH_OK && launch_conserved(c, *p, s, true) != cudaSuccess) qrc = SPH_ERR_CUDA;
+    if (qrc == SPH_OK) qrc = queue_step(c, p, dt_fixed, s, true, full);
+    // the totals of the stepped state ride along (read with sph_graph_totals)
+    if (qrc == SPH_OK && launch_conserved(c, *p, s) != cudaSuccess) qrc = SPH_ERR_CUDA;
     if (qrc == SPH_OK && cudaMemcpyAsync(c.cons_host, c.cons_out, sizeof(double) * 9 * c.kp.ninst,
                                          cudaMemcpyDeviceToHost, s) != cudaSuccess)
         qrc = SPH_ERR_CUDA;

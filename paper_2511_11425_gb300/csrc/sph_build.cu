@@ -1202,4 +1202,23 @@ cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_walk_queue(Ctx &c, int mode, const unsigned *ids, const unsigned *cnt,
+                              const float *h_walk, cudaStream_t s)
+{
+    const KParams &kp = c.kp;
+    if (kp.ng <= 0) return cudaSuccess;
+    // a queue that may hold every group: one warp slot per group, the
+    // surplus warps leave at once
+    const int g = (kp.ng + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    cudaMemsetAsync(c.arena_used, 0, sizeof(unsigned), s);
+    c.launches += 1;
+    const int pr = prof_begin(c, s, SPH_PHASE_WALK);
+    k_walk<<<g, 32 * kWarpsPerBlock, 0, s>>>(kp, c.inst, c.gfirst, c.bstart, c.binst, mode, c.node,
+                                             c.pm, c.origin, h_walk, ids, cnt, c.list, c.list_cnt,
+                                             c.list_off, c.arena_used, (unsigned)c.arena_cap,
+                                             c.st);
+    prof_end(c, s, pr);
+    return cudaGetLastError();
+}
+
 }  // namespace sph

@@ -346,16 +346,38 @@ __device__ __forceinline__ void density_bucket(
             coverage(cc, cr);
             mw = filter_word(w, cc, cr);
           }
+          if (!mw) continue;
+          // the records of this word's accepted entries, one per lane, fetched
+          // together (one round of dependent loads per word, not per entry):
+          // first particle, length, origin minus the sink bucket's
+          int mj0 = 0, mlen = 0, mdk[3] = {0, 0, 0};
+          if ((mw >> lane) & 1u) {
+              const int Bm = (int)gl[32 * w + lane];
+              mj0 = bstart[Bm];
+              mlen = bucket_len(bstart, Bm);
+#pragma unroll
+              for (int a = 0; a < 3; ++a) mdk[a] = origin[a * kp.nb + Bm] - origin[a * kp.nb + A];
+          }
           while (mw) {
-            const unsigned e = 32 * w + __ffs(mw) - 1;
+            const int l = __ffs(mw) - 1;
             mw &= mw - 1u;
-            const int B = (int)gl[e];
-            const float3 off = origin_offset(I, kp.nb, origin, A, B);
-            const int j0 = bstart[B];
+            const int j0 = __shfl_sync(kFull, mj0, l);
+            const int len = __shfl_sync(kFull, mlen, l);
+            int dk[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dk[a] = __shfl_sync(kFull, mdk[a], l);
+            // origin offset in the sink frame, nearest periodic image
+            float off[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float f = (float)dk[a] * I.qf;
+                if (bx.per[a]) f -= bx.L[a] * rintf(f * bx.invL[a]);
+                off[a] = f;
+            }
             const int j = j0 + lane;
-            const bool vj = lane < bucket_len(bstart, B);
+            const bool vj = lane < len;
             float4 s = vj ? pm[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float sp[3] = {off.x + s.x, off.y + s.y, off.z + s.z};
+            float sp[3] = {off[0] + s.x, off[1] + s.y, off[2] + s.z};
             float nw[3] = {0.f, 0.f, 0.f};  // periodic images moved by the wrap below
             bool in = vj;
             float dd2 = 0.f;
@@ -385,10 +407,9 @@ __device__ __forceinline__ void density_bucket(
                     double o[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        const int dk = origin[a * kp.nb + B] - origin[a * kp.nb + A];
-                        double f = (double)dk * I.q;
+                        double f = (double)dk[a] * I.q;
                         if (bx.per[a]) {
-                            const float fi = (float)dk * I.qf;
+                            const float fi = (float)dk[a] * I.qf;
                             f -= I.Ld[a] * (double)rintf(fi * I.invL[a]);
                         }
                         o[a] = f - I.Ld[a] * (double)nw[a];
@@ -666,19 +687,23 @@ __global__ void k_isentropic(int n, const Inst *__restrict__ insts,
 
 cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, int round,
                            int fixed_h, int64_t cap, uint32_t *count, int64_t *ids,
-                           cudaStream_t s)
+                           cudaStream_t s, bool fastgas)
 {
     const KParams &kp = c.kp;
     if (kp.nb <= 0) return cudaSuccess;
-    // round < 0: every bucket, queueing re-walks for round 0; round r: the
-    // buckets of the groups queued for round r, queueing for round r + 1
-    // a re-walk round covers the queued groups with a small grid-stride grid
-    const int slots = round < 0 ? kp.nb : kp.ng << kGroupLog;
+    // round < 0: every bucket (FastGas: the buckets of the marked groups),
+    // queueing re-walks for round 0; round r: the buckets of the groups
+    // queued for round r, queueing for round r + 1.  A re-walk round covers
+    // the queued groups with a small grid-stride grid, the FastGas pass with
+    // one warp slot per bucket slot of every group (the surplus leaves at once)
+    const int slots = round < 0 && !fastgas ? kp.nb : kp.ng << kGroupLog;
     int g = (slots + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (round >= 0 && g > kRoundBlocks) g = kRoundBlocks;
     const bool emit = ids != nullptr || count != nullptr;
-    const unsigned *gids = round < 0 ? nullptr : c.redo + (size_t)round * kp.ng;
-    const unsigned *gcnt = round < 0 ? nullptr : &c.st->redo_cnt[round];
+    const unsigned *gids = round < 0 ? (fastgas ? c.fg_list : nullptr)
+                                     : c.redo + (size_t)round * kp.ng;
+    const unsigned *gcnt = round < 0 ? (fastgas ? &c.st->fg_cnt : nullptr)
+                                     : &c.st->redo_cnt[round];
     const int next = round + 1;
     unsigned *redo_out = next < kRelistRounds ? c.redo + (size_t)next * kp.ng : nullptr;
     unsigned *redo_cnt_out = next < kRelistRounds ? &c.st->redo_cnt[next] : nullptr;

@@ -646,27 +646,24 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
 // 5 blocks of 4 warps per SM (96 registers; the fixed-point pair path spills
 // a few values; 43 KB of shared memory per block): measured faster than 4
 // blocks without spills
+// one sink bucket A (one warp)
 template <class K, bool RUNG>
-__global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, const Inst *__restrict__ insts,
-                                                const int *__restrict__ bstart,
-                                                const int *__restrict__ binst,
-                                                const float4 *__restrict__ fpos,
-                                                const float4 *__restrict__ fvel,
-                                                const float4 *__restrict__ fth,
-                                                const int4 *__restrict__ ipos,
-                                                const unsigned *__restrict__ list_cnt,
-                                                const unsigned *__restrict__ list_off,
-                                                const unsigned *__restrict__ list,
-                                                const int *__restrict__ origin,
-                                                const float4 *__restrict__ node, float4 *acc,
-                                                double *accS, unsigned *mumax, RungArgs ra,
-                                                DevStatus *st)
+__device__ __forceinline__ void force_sink(const KParams &kp, const Inst *__restrict__ insts,
+                                           const int *__restrict__ bstart,
+                                           const int *__restrict__ binst,
+                                           const float4 *__restrict__ fpos,
+                                           const float4 *__restrict__ fvel,
+                                           const float4 *__restrict__ fth,
+                                           const int4 *__restrict__ ipos,
+                                           const unsigned *__restrict__ list_cnt,
+                                           const unsigned *__restrict__ list_off,
+                                           const unsigned *__restrict__ list,
+                                           const int *__restrict__ origin,
+                                           const float4 *__restrict__ node, float4 *acc,
+                                           double *accS, unsigned *mumax, const RungArgs &ra,
+                                           DevStatus *st, ForceStage *stage,
+                                           SinkStage *sstage, int wib, int lane, int A)
 {
-    __shared__ ForceStage stage[kWarpsPerBlock];
-    __shared__ SinkStage sstage[kWarpsPerBlock];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int A = blockIdx.x * kWarpsPerBlock + wib;
-    if (A >= kp.nb) return;
     const Inst &I = insts[binst[A]];
     const PBox bx = make_pbox(I);
     const Visc vp = {I.alpha, I.beta, I.eps_av, I.qx, I.qx2};
@@ -763,6 +760,50 @@ __global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, c
     }
 }
 
+// every sink bucket, or (QUEUE: FastGas) the buckets of the queued groups,
+// grid-stride
+template <class K, bool RUNG, bool QUEUE>
+__global__ void __launch_bounds__(128, kForceBlocksPerSM) k_forces(KParams kp, const Inst *__restrict__ insts,
+                                                const int *__restrict__ bstart,
+                                                const int *__restrict__ binst,
+                                                const int *__restrict__ gfirst,
+                                                const unsigned *__restrict__ group_ids,
+                                                const unsigned *__restrict__ group_cnt,
+                                                const float4 *__restrict__ fpos,
+                                                const float4 *__restrict__ fvel,
+                                                const float4 *__restrict__ fth,
+                                                const int4 *__restrict__ ipos,
+                                                const unsigned *__restrict__ list_cnt,
+                                                const unsigned *__restrict__ list_off,
+                                                const unsigned *__restrict__ list,
+                                                const int *__restrict__ origin,
+                                                const float4 *__restrict__ node, float4 *acc,
+                                                double *accS, unsigned *mumax, RungArgs ra,
+                                                DevStatus *st)
+{
+    __shared__ ForceStage stage[kWarpsPerBlock];
+    __shared__ SinkStage sstage[kWarpsPerBlock];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bi0 = blockIdx.x * kWarpsPerBlock + wib;
+    if (!QUEUE) {
+        if (bi0 < kp.nb)
+            force_sink<K, RUNG>(kp, insts, bstart, binst, fpos, fvel, fth, ipos, list_cnt,
+                                list_off, list, origin, node, acc, accS, mumax, ra, st, stage,
+                                sstage, wib, lane, bi0);
+        return;
+    }
+    const int nslots = (int)*group_cnt << kGroupLog;
+    for (int bi = bi0; bi < nslots; bi += gridDim.x * kWarpsPerBlock) {
+        const int fb = gfirst[group_ids[bi >> kGroupLog]];
+        const Inst &Ig = insts[binst[fb]];
+        const int j = bi & ((1 << kGroupLog) - 1);
+        if (j >= min(Ig.G, Ig.boff + Ig.nb - fb)) continue;
+        force_sink<K, RUNG>(kp, insts, bstart, binst, fpos, fvel, fth, ipos, list_cnt, list_off,
+                            list, origin, node, acc, accS, mumax, ra, st, stage, sstage, wib,
+                            lane, fb + j);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // finalize: PdV term, div v, time-step limits, global minimum
 // ---------------------------------------------------------------------------
@@ -838,7 +879,8 @@ cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s, const RungArgs *ra)
+cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s, const RungArgs *ra,
+                          bool fastgas)
 {
     (void)p;
     const int pr = prof_begin(c, s, SPH_PHASE_FORCES);
@@ -847,20 +889,25 @@ cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s, const 
         prof_end(c, s, pr);
         return e;
     }
-    int g = (c.kp.nb + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    // FastGas: the buckets of the marked groups, one warp slot per bucket
+    // slot of every group (the surplus leaves at once)
+    const int slots = fastgas ? c.kp.ng << kGroupLog : c.kp.nb;
+    int g = (slots + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const unsigned *gids = fastgas ? c.fg_list : nullptr;
+    const unsigned *gcnt = fastgas ? &c.st->fg_cnt : nullptr;
     c.launches += 1;
     RungArgs r0{};
     const RungArgs rv = ra ? *ra : r0;
+#define SPH_FORCES_LAUNCH(RUNG_, QUEUE_)                                                  \
+    k_forces<KT, RUNG_, QUEUE_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                          \
+        c.kp, c.inst, c.bstart, c.binst, c.gfirst, gids, gcnt, c.fpos, c.fvel, c.fth, c.ipos, \
+        c.list_cnt, c.list_off, c.list, c.origin, c.node, c.acc, c.accS, c.mumax, rv, c.st)
     SPH_KERNEL_DISPATCH(c.kp.kernel, KT,
-        if (rv.rung)
-            k_forces<KT, true><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                c.kp, c.inst, c.bstart, c.binst, c.fpos, c.fvel, c.fth, c.ipos, c.list_cnt,
-                c.list_off, c.list, c.origin, c.node, c.acc, c.accS, c.mumax, rv, c.st);
-        else
-            k_forces<KT, false><<<g, 32 * kWarpsPerBlock, 0, s>>>(
-                c.kp, c.inst, c.bstart, c.binst, c.fpos, c.fvel, c.fth, c.ipos, c.list_cnt,
-                c.list_off, c.list, c.origin, c.node, c.acc, c.accS, c.mumax, rv, c.st);
+        if (rv.rung && fastgas) SPH_FORCES_LAUNCH(true, true);
+        else if (rv.rung) SPH_FORCES_LAUNCH(true, false);
+        else SPH_FORCES_LAUNCH(false, false);
     )
+#undef SPH_FORCES_LAUNCH
     prof_end(c, s, pr);
     return cudaGetLastError();
 }

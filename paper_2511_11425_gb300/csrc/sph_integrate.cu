@@ -50,8 +50,7 @@ __device__ __forceinline__ void kdk_particle(
     const float *__restrict__ ax, const float *__restrict__ ay, const float *__restrict__ az,
     const float *__restrict__ dudt_h, const float *__restrict__ dudt_av, int energy_mode,
     const double *__restrict__ dts, float h_next, float *rho, const float4 *__restrict__ fth,
-    const float *__restrict__ divv, double *xo = nullptr, double *vo = nullptr,
-    double *uo = nullptr)
+    const float *__restrict__ divv)
 {
     const int k = pinst[i];
     const Inst &I = insts[k];
@@ -65,8 +64,7 @@ __device__ __forceinline__ void kdk_particle(
     vx[i] = v0;
     vy[i] = v1;
     vz[i] = v2;
-    const double un = u[i] + kick * ud;
-    u[i] = un;
+    u[i] += kick * ud;
     // evolved density (mass conservation equation), kicked like u with the
     // rate -rho_pred div v of this step's force pass
     if (rho) rho[i] = (float)((double)rho[i] - kick * (double)fth[i].z * (double)divv[i]);
@@ -92,15 +90,6 @@ __device__ __forceinline__ void kdk_particle(
     y[i] = p[1];
     z[i] = p[2];
     h[i] = h_next;
-    if (xo) {
-        xo[0] = p[0];
-        xo[1] = p[1];
-        xo[2] = p[2];
-        vo[0] = v0;
-        vo[1] = v1;
-        vo[2] = v2;
-        *uo = un;
-    }
 }
 
 // The smoothing length is advanced with the drift as the seed of the next
@@ -186,47 +175,6 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(
     cons_block_store(acc, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 9);
 }
 
-// the kick-drift-kick of k_kdk with the totals' block partials of the
-// stepped state on the way (the captured step): the same slices and order as
-// k_cons_partial, so k_cons_final gives the same bits.  A step that failed
-// earlier moves nothing and sums the state as it is.
-template <bool CORR>
-__global__ void __launch_bounds__(kConsThreads) k_kdk_cons(
-    KParams kp, const Inst *__restrict__ insts, const unsigned short *__restrict__ pinst,
-    double *x, double *y, double *z, double *vx, double *vy, double *vz, double *u, float *h,
-    const float *__restrict__ ax, const float *__restrict__ ay, const float *__restrict__ az,
-    const float *__restrict__ dudt_h, const float *__restrict__ dudt_av,
-    const float *__restrict__ divv, const double *__restrict__ dts,
-    const float *__restrict__ corr, float *rho_ev, const float4 *__restrict__ fth,
-    const float *__restrict__ m, double *part, const DevStatus *st)
-{
-    const Inst &I = insts[blockIdx.y];
-    const bool move = st->code == 0;
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const int b0 = I.off + blockIdx.x * kConsChunk, b1 = min(b0 + kConsChunk, I.off + I.n);
-    for (int i = b0 + threadIdx.x; i < b1; i += kConsThreads) {
-        double p[3], v[3], un;
-        if (move) {
-            float e = (float)dts[2 * pinst[i] + 1] * divv[i] * (1.f / 3.f);
-            if (CORR) e += corr[i];
-            const float f = expf(e);
-            kdk_particle(i, insts, pinst, x, y, z, vx, vy, vz, u, h, ax, ay, az, dudt_h, dudt_av,
-                         kp.energy_mode, dts, h[i] * fminf(fmaxf(f, 0.5f), 2.f), rho_ev, fth,
-                         divv, p, v, &un);
-        } else {
-            p[0] = x[i];
-            p[1] = y[i];
-            p[2] = z[i];
-            v[0] = vx[i];
-            v[1] = vy[i];
-            v[2] = vz[i];
-            un = u[i];
-        }
-        cons_add(acc, (double)m[i], p, v, un);
-    }
-    cons_block_store(acc, part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 9);
-}
-
 // nine warps per instance, one per total; each lane sums a fixed stride of
 // the block partials and the warp folds the lanes in a fixed butterfly order
 __global__ void k_cons_final(int nblocks, const double *part, double *out)
@@ -240,8 +188,7 @@ __global__ void k_cons_final(int nblocks, const double *part, double *out)
     if (lane == 0) out[blockIdx.x * 9 + q] = q == 7 ? 0.5 * s : s;  // E_kin = (sum m v^2) / 2
 }
 
-cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s,
-                       bool totals)
+cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s)
 {
     const int n = (int)p.n;
     const int ni = c.kp.ninst;
@@ -254,18 +201,7 @@ cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStre
         if (e != cudaSuccess) return e;
     }
     const int g = (n + 255) / 256;
-    const dim3 gc(c.cons_blocks > 0 ? c.cons_blocks : 1, ni);
-    if (totals && corr)
-        k_kdk_cons<true><<<gc, kConsThreads, 0, s>>>(
-            c.kp, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.h,
-            p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr,
-            c.kp.evolved ? p.rho : nullptr, c.fth, p.m, c.cons_part, c.st);
-    else if (totals)
-        k_kdk_cons<false><<<gc, kConsThreads, 0, s>>>(
-            c.kp, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.h,
-            p.a[0], p.a[1], p.a[2], p.dudt_h, p.dudt_av, p.divv, c.dts, nullptr,
-            c.kp.evolved ? p.rho : nullptr, c.fth, p.m, c.cons_part, c.st);
-    else if (corr)
+    if (corr)
         k_kdk<true><<<g, 256, 0, s>>>(c.kp, n, c.inst, c.pinst, p.x[0], p.x[1], p.x[2], p.v[0],
                                       p.v[1], p.v[2], p.u, p.h, p.a[0], p.a[1], p.a[2],
                                       p.dudt_h, p.dudt_av, p.divv, c.dts, c.mlp.corr,
@@ -386,14 +322,12 @@ cudaError_t launch_kdk_rungs(Ctx &c, const sph_particles &p, const RungArgs &ra,
     return cudaGetLastError();
 }
 
-cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s,
-                             bool partials_ready)
+cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
     const int nb = c.cons_blocks > 0 ? c.cons_blocks : 1;
-    c.launches += partials_ready ? 1 : 2;
+    c.launches += 2;
     const int pr = prof_begin(c, s, SPH_PHASE_CONSERVED);
-    if (!partials_ready)
-        k_cons_partial<<<dim3(nb, c.kp.ninst), kConsThreads, 0, s>>>(
+    k_cons_partial<<<dim3(nb, c.kp.ninst), kConsThreads, 0, s>>>(
             c.inst, p.x[0], p.x[1], p.x[2], p.v[0], p.v[1], p.v[2], p.u, p.m, c.cons_part);
     k_cons_final<<<c.kp.ninst, 288, 0, s>>>(nb, c.cons_part, c.cons_out);
     prof_end(c, s, pr);

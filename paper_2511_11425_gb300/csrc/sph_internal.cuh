@@ -105,7 +105,7 @@ struct DevStatus {
     int max_iters;
     unsigned int relists;                      // groups re-walked in total
     unsigned int redo_cnt[kRelistRounds + 1];  // groups queued for round r
-    unsigned int pad;
+    unsigned int fg_cnt;                       // groups marked by the FastGas pass
 };
 
 // one independent problem (device array; every kernel reads its instance)
@@ -188,6 +188,7 @@ struct Ctx {
     std::vector<Inst> inst_host;
     KParams kp;
     int64_t capacity = 0;
+    int64_t cap_nb = 0, cap_ng = 0;  // bucket slots and groups the buffers hold
     int device = 0;
     std::string err;
     sph_stats stats{};
@@ -248,6 +249,11 @@ struct Ctx {
     // with the particles), largest rung of each particle's force partners
     uint8_t *rung = nullptr;
     int *rmax = nullptr;
+    // FastGas (Sec. 2.3.6): per bucket "holds an active particle", per group
+    // "marked", the queue of marked groups (count in DevStatus::fg_cnt)
+    bool fastgas = true;
+    uint8_t *bact = nullptr;
+    unsigned *gmark = nullptr, *fg_list = nullptr;
     bool rungs_started = false;       // derivatives exist (the first substep has none)
     int rung_R = 0;                   // max_rung of the hierarchical steps so far
     float2 *ic_pt = nullptr;          // interface correction: P, T from the predictor
@@ -682,30 +688,32 @@ cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s);
 // group walk: all groups (round < 0) or the groups queued for re-walk round r
 cudaError_t launch_walk(Ctx &c, const sph_particles &p, int mode, int round, const float *h_walk,
                         cudaStream_t s);
+// the walk of the groups in a device queue (ids, *cnt of them), the overflow
+// arena emptied first
+cudaError_t launch_walk_queue(Ctx &c, int mode, const unsigned *ids, const unsigned *cnt,
+                              const float *h_walk, cudaStream_t s);
 // density (sph_density.cu): round < 0 = all buckets, else the buckets of the
 // groups queued for round r; fixed_h evaluates at the given h once
 cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, int round,
                            int fixed_h, int64_t cap, uint32_t *count, int64_t *ids,
-                           cudaStream_t s);
+                           cudaStream_t s, bool fastgas = false);
 cudaError_t launch_isentropic(Ctx &c, const sph_particles &p, cudaStream_t s);
 // forces (sph_forces.cu)
 cudaError_t launch_predict(Ctx &c, const sph_particles &p, cudaStream_t s,
                            const RungArgs *ra = nullptr);
 cudaError_t launch_forces(Ctx &c, const sph_particles &p, cudaStream_t s,
-                          const RungArgs *ra = nullptr);
+                          const RungArgs *ra = nullptr, bool fastgas = false);
+// FastGas (sph_fastgas.cu): mark the groups of the substep's active
+// particles and of their neighbours (from the density lists) and queue them
+cudaError_t launch_fastgas_mark(Ctx &c, const RungArgs &ra, cudaStream_t s);
 cudaError_t launch_forces64(Ctx &c, cudaStream_t s);  // FP64 form (sph_forces64.cu)
 // interface correction pass (sph_interface.cu)
 cudaError_t launch_interface(Ctx &c, const sph_particles &p, cudaStream_t s);
 cudaError_t launch_finalize(Ctx &c, const sph_particles &p, cudaStream_t s,
                             const RungArgs *ra = nullptr);
 // integration (sph_integrate.cu)
-// totals: the captured step's kick-drift-kick also leaves the conserved
-// totals' block partials of the stepped state (launch_conserved with
-// partials_ready then only folds them)
-cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s,
-                       bool totals = false);
-cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s,
-                             bool partials_ready = false);
+cudaError_t launch_kdk(Ctx &c, const sph_particles &p, double dt_fixed, cudaStream_t s);
+cudaError_t launch_conserved(Ctx &c, const sph_particles &p, cudaStream_t s);
 // hierarchical step: kicks of the active particles, rung choice, drift of all
 cudaError_t launch_kdk_rungs(Ctx &c, const sph_particles &p, const RungArgs &ra, cudaStream_t s);
 // permute the rungs with the particles at a full build
