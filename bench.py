@@ -826,6 +826,64 @@ def forms_batch(dev, steps, warmup):
     return out
 
 
+def forms_rungs(dev, R=6, nglobal=2):
+    """Hierarchical steps (Sec. 2.3.6) on Sedov-Taylor 64^3: one global step
+    dt0 = 2^R x 0.9 x the smallest step limit of the start, taken (a) as 2^R
+    plain global steps of dt0 / 2^R, (b) with rungs, every substep solving
+    every particle, (c) with rungs and FastGas.  Device time per dt0 after one
+    untimed global step; the rung histogram at the end."""
+    import torch
+    import paper_2511_11425_gb300 as sph
+    from paper_2511_11425_gb300 import inputs
+    prob = inputs.sedov(n=64)
+    params = sph.Params.for_problem(prob)
+    sim = sph.Simulation(prob, params, device=dev)
+    try:
+        sph.sph_build_cells(sim.ctx, sim.parts)
+        sph.sph_density_h(sim.ctx, sim.parts)
+        sph.sph_forces(sim.ctx, sim.parts)
+        dt_min = float(sim.parts.t["dt_i"].min().item())
+    finally:
+        sim.close()
+    dt0 = 2 ** R * dt_min * 0.9
+    s = torch.cuda.current_stream(dev)
+    out = {"workload": "sedov_taylor_64^3 (262,144 particles) from t = 0", "max_rung": R,
+           "dt0": dt0}
+
+    def timed(run_one):
+        run_one()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(nglobal):
+            run_one()
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / nglobal
+
+    sim = sph.Simulation(prob, params, device=dev)
+    try:
+        out["global_steps_ms_per_dt0"] = timed(
+            lambda: [sim.step(dt0 / 2 ** R) for _ in range(2 ** R)])
+    finally:
+        sim.close()
+    for name, fg in (("rungs_full_ms_per_dt0", False), ("rungs_fastgas_ms_per_dt0", True)):
+        sim = sph.Simulation(prob, params, device=dev)
+        try:
+            sph.sph_set_fastgas(sim.ctx, fg)
+            out[name] = timed(lambda: sph.sph_step_rungs(sim.ctx, sim.parts, dt0, R))
+            if fg:
+                out["rung_histogram"] = np.bincount(sph.sph_get_rungs(sim.ctx, prob.n),
+                                                    minlength=R + 1).tolist()
+        finally:
+            sim.close()
+    out["fastgas_speedup_over_full_rungs"] = (out["rungs_full_ms_per_dt0"] /
+                                              out["rungs_fastgas_ms_per_dt0"])
+    out["fastgas_speedup_over_global_steps"] = (out["global_steps_ms_per_dt0"] /
+                                                out["rungs_fastgas_ms_per_dt0"])
+    return out
+
+
 def forms_learned(dev, n_total=8_000_000, nrec=50, ncmp=200, tol=1e-5):
     """The learned seed against the continuity seed on the colliding-spheres
     workload: record `nrec` plain steps, train the network on the GPU, then
@@ -1065,14 +1123,16 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
     forms = None
     if world == 1 and not args.no_forms:
-        forms = {"precision": forms_precision(dev)}
-        torch.cuda.empty_cache()
-        forms["batch"] = forms_batch(dev, max(2, min(args.steps, 5)), max(args.warmup, 3))
-        torch.cuda.empty_cache()
-        forms["learned"] = forms_learned(dev)
-        torch.cuda.empty_cache()
-        forms["combined"] = forms_combined(dev)
-        torch.cuda.empty_cache()
+        todo = {"precision": lambda: forms_precision(dev),
+                "batch": lambda: forms_batch(dev, max(2, min(args.steps, 5)),
+                                             max(args.warmup, 3)),
+                "learned": lambda: forms_learned(dev), "rungs": lambda: forms_rungs(dev),
+                "combined": lambda: forms_combined(dev)}
+        only = [f for f in args.forms.split(",") if f] if args.forms else list(todo)
+        forms = {}
+        for name in only:
+            forms[name] = todo[name]()
+            torch.cuda.empty_cache()
     cpu = err = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, err = cpu_baseline(prob, gpu=gpu_fields(stepped, params, dev), err_prob=stepped)
@@ -1135,6 +1195,9 @@ def main(argv=None):
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the per-phase timing pass (HBM roofline of the "
                          "memory-bound phases)")
+    ap.add_argument("--forms", default="",
+                    help="comma-separated subset of the forms to run (precision, batch, "
+                         "learned, rungs, combined); default all")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the form comparisons (FP64 against mixed precision, "
                          "batched, learned seed, combined)")
