@@ -538,6 +538,15 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         const int j = r.j0 + lane;
         const bool vj = lane < r.len;
         const float4 q = vj ? fpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // the other records are loaded with the position, before the cull
+        // decides, so that their L2 latency overlaps the first one
+        float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f), v4 = t4;
+        int4 p4 = make_int4(0, 0, 0, 0);
+        if (vj) {
+            t4 = fth[j];
+            v4 = fvel[j];
+            if (FIX) p4 = ipos[j];
+        }
         // origin offset in the sink frame (nearest periodic image), as FP32
         // and, for the fixed-point path, in units of qx modulo 2^32
         float d[3];
@@ -576,16 +585,16 @@ __device__ __forceinline__ void force_bucket(const KParams &kp, const Inst &I, c
         const unsigned bal = __ballot_sync(kFull, in);
         if (in) {
             const int pos = c + __popc(bal & lt);
-            const float4 t = fth[j];
+            const float4 t = t4;
             S.pos[pos] = make_float4(sp[0], sp[1], sp[2], q.w * q.w);
-            S.vel[pos] = fvel[j];
+            S.vel[pos] = v4;
             S.th[pos] = make_float4(t.x, t.y, t.z, q.w);
             S.ih[pos] = __frcp_rn(q.w);
             S.idx[pos] = j;
             if (FIX) {
                 // the source in the sink frame: its fixed-point position plus
                 // the origin offset, modulo 2^32
-                const int4 p = ipos[j];
+                const int4 p = p4;
                 S.ipos[pos] = make_int4((int)((unsigned)p.x + o3[0]), (int)((unsigned)p.y + o3[1]),
                                         (int)((unsigned)p.z + o3[2]), p.w);
             }
