@@ -341,8 +341,11 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         t.app = vr < 0.f;
         const float hb = 0.5f * (thi.w + hj), cb = 0.5f * (thi.y + tj.y),
                     rb = 0.5f * (thi.z + tj.z);
-        const float mu = __fdividef(hb * vr, fmaf(vp.eps_av * hb, hb, r2));
-        const float Pi = t.app ? __fdividef(fmaf(-vp.alpha * cb, mu, vp.beta * mu * mu), rb) : 0.f;
+        // one reciprocal for mu's denominator and rhobar
+        const float den = fmaf(vp.eps_av * hb, hb, r2);
+        const float rdr = __fdividef(1.f, den * rb);
+        const float mu = hb * vr * (rb * rdr);
+        const float Pi = t.app ? fmaf(-vp.alpha * cb, mu, vp.beta * mu * mu) * (den * rdr) : 0.f;
         const float Fb = 0.5f * (Fi + Fj);
         const float coef = fmaf(thi.x, Fi, fmaf(tj.x, Fj, Pi * Fb));
         const float du = 0.5f * Pi * vr * Fb;
