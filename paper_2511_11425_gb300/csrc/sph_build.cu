@@ -969,52 +969,49 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
         push(acc, top_leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, cur, ncur);
     }
     __syncwarp();
-    for (int lvl = L0 + 1; lvl <= I.logP && !overflow; ++lvl) {
-        const bool leaf = lvl == I.logP;
+    // each round descends two levels where it can: the bounds of a node hold
+    // those of its descendants, so testing the grandchildren of the accepted
+    // nodes directly accepts the same nodes as two rounds of children tests,
+    // with half the rounds of dependent loads.  Per round a lane loads four
+    // nodes: two children of each of two frontier entries, or the four
+    // grandchildren of one.
+    for (int lvl = L0 + 1; lvl <= I.logP && !overflow;) {
+        const int step = lvl < I.logP ? 2 : 1;
+        const int tl = lvl + step - 1;  // level of the nodes tested
+        const bool leaf = tl == I.logP;
+        const int per = step == 2 ? 32 : 64;  // frontier entries per iteration
         int nnext = 0;
-        // two chunks of 32 parents per round: the bounds of all their
-        // children (adjacent node pairs) in one round of loads, then the
-        // tests and pushes in frontier order
-        for (int base = 0; base < ncur; base += 64) {
-            unsigned parent[2];
-            bool have[2];
-            float4 nb[2][2][4];
+        for (int base = 0; base < ncur; base += per) {
+            unsigned nd[4];
+            bool have[4];
+            float4 nb[4][4];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int t = 0; t < 4; ++t) {
+                const int q = step == 2 ? 0 : (t >> 1);
                 const int k = base + 32 * q + lane;
-                have[q] = k < ncur;
-                parent[q] = have[q] ? cur[k] : 1u;
-                const float4 *cn = tn + 8 * (size_t)parent[q];
-#pragma unroll
-                for (int ch = 0; ch < 2; ++ch) {
-                    nb[q][ch][0] = cn[4 * ch];
-                    nb[q][ch][1] = cn[4 * ch + 1];
-                    if (mode == WALK_FORCE) {
-                        nb[q][ch][2] = cn[4 * ch + 2];
-                        nb[q][ch][3] = cn[4 * ch + 3];
-                    } else {
-                        nb[q][ch][2] = nb[q][ch][0];
-                        nb[q][ch][3] = nb[q][ch][1];
-                    }
+                have[t] = k < ncur;
+                const unsigned par = have[t] ? cur[k] : 1u;
+                nd[t] = step == 2 ? 4u * par + (unsigned)t : 2u * par + (unsigned)(t & 1);
+                const float4 *cn = tn + 4 * (size_t)nd[t];
+                nb[t][0] = cn[0];
+                nb[t][1] = cn[1];
+                if (mode == WALK_FORCE) {
+                    nb[t][2] = cn[2];
+                    nb[t][3] = cn[3];
+                } else {
+                    nb[t][2] = nb[t][0];
+                    nb[t][3] = nb[t][1];
                 }
             }
-            bool acc[2][2];
+            bool acc[4];
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+            for (int t = 0; t < 4; ++t)
+                acc[t] = have[t] && accept_b(nd[t], tl, nb[t][0], nb[t][1], nb[t][2], nb[t][3]);
 #pragma unroll
-                for (int ch = 0; ch < 2; ++ch)
-                    acc[q][ch] = have[q] && accept_b(2u * parent[q] + (unsigned)ch, lvl,
-                                                     nb[q][ch][0], nb[q][ch][1], nb[q][ch][2],
-                                                     nb[q][ch][3]);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (base + 32 * q >= ncur) break;  // (warp-uniform)
-#pragma unroll
-                for (int ch = 0; ch < 2; ++ch) {
-                    const unsigned nd = 2u * parent[q] + (unsigned)ch;
-                    push(acc[q][ch], leaf ? (unsigned)I.boff + (nd - (unsigned)I.P) : nd, nxt,
-                         nnext);
-                }
+            for (int t = 0; t < 4; ++t) {
+                if (step == 1 && base + 32 * (t >> 1) >= ncur) break;  // (warp-uniform)
+                push(acc[t], leaf ? (unsigned)I.boff + (nd[t] - (unsigned)I.P) : nd[t], nxt,
+                     nnext);
             }
         }
         __syncwarp();
@@ -1022,6 +1019,7 @@ __device__ __forceinline__ void walk_group(const KParams &kp, const Inst *__rest
         cur = nxt;
         nxt = t;
         ncur = nnext;
+        lvl += step;
     }
     if (overflow) {
         exhaustive();
