@@ -66,16 +66,16 @@ __device__ __forceinline__ void hit_masks(const PBox &bx, const float4 *cand, in
     m1 = (unsigned long long)w2 | ((unsigned long long)w3 << 32);
 }
 
+// lowest set bit of m0 | m1 << 64, cleared; without a branch (lanes differ
+// in which half is empty)
 __device__ __forceinline__ int next_hit(unsigned long long &m0, unsigned long long &m1)
 {
-    int k;
-    if (m0) {
-        k = __ffsll((long long)m0) - 1;
-        m0 &= m0 - 1ull;
-    } else {
-        k = 63 + __ffsll((long long)m1);
-        m1 &= m1 - 1ull;
-    }
+    const bool lo = m0 != 0ull;
+    const unsigned long long w = lo ? m0 : m1;
+    const int k = __ffsll((long long)w) - 1 + (lo ? 0 : 64);
+    const unsigned long long w2 = w & (w - 1ull);
+    m0 = lo ? w2 : m0;
+    m1 = lo ? m1 : w2;
     return k;
 }
 

@@ -382,15 +382,15 @@ __device__ __forceinline__ void force_chunk(const PBox &bx, const Visc &vp, Forc
         s.du = fmaf(t.mj, t.du, s.du);
         s.mumax = fmaxf(s.mumax, t.mneg);
     };
+    // lowest pending hit, without a branch (lanes differ in which half is
+    // empty)
     auto next = [&]() -> int {
-        int k;
-        if (m0) {
-            k = __ffsll((long long)m0) - 1;
-            m0 &= m0 - 1ull;
-        } else {
-            k = 63 + __ffsll((long long)m1);
-            m1 &= m1 - 1ull;
-        }
+        const bool lo = m0 != 0ull;
+        const unsigned long long w = lo ? m0 : m1;
+        const int k = __ffsll((long long)w) - 1 + (lo ? 0 : 64);
+        const unsigned long long w2 = w & (w - 1ull);
+        m0 = lo ? w2 : m0;
+        m1 = lo ? m1 : w2;
         return k;
     };
     if (RUNG) {
