@@ -554,7 +554,8 @@ __global__ void k_pad_fallback(int nb, const Inst *__restrict__ insts,
 // Offsets from the bucket's first particle are formed in FP64 (minimum image
 // on periodic axes) and every reduction runs in FP32 on those offsets.
 // With update_pos = 0 only the box-of-balls is refreshed from the current h
-// (bounds update after the density pass, Sec. 2.3.3).
+// (bounds update after the density pass, Sec. 2.3.3); with update_pos = 2
+// (refit without a re-sort) the origins are kept.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restrict__ insts,
                                                  const int *__restrict__ bstart,
@@ -598,7 +599,32 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
     const int ax = lane < 3 ? lane : 0;  // the axis of lanes 0, 1, 2
     auto sel = [&](const auto *v3) { return ax == 0 ? v3[0] : (ax == 1 ? v3[1] : v3[2]); };
     float rel[3];
-    if (update_pos) {
+    if (update_pos == 2) {
+        // refit (no re-sort): the bucket keeps its origin grid point, and each
+        // lane's offset from it is one FP64 subtraction per axis (nearest
+        // periodic image of the origin)
+        double v[3] = {0.0, 0.0, 0.0};
+        if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
+        const double oa = lane < 3 ? (double)origin[ax * kp.nb + b] * I.q : 0.0;
+        int fix[3];
+        double rdd[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double rd = v[a] - __shfl_sync(kFull, oa, a);
+            if (I.periodic[a] && fabsf((float)rd) > 0.49f * (float)I.Ld[a])
+                rd -= I.Ld[a] * rint(rd * I.invLd[a]);
+            rdd[a] = rd;
+            rel[a] = (float)rd;
+            fix[a] = __double2int_rn(rd * (double)I.inv_qx);
+        }
+        if (ok) {
+            if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
+                raise_status(st, ST_NONFINITE, i);
+            pm[i] = make_float4(rel[0], rel[1], rel[2], m[i]);
+            ipos[i] = make_int4(fix[0], fix[1], fix[2], 0);
+            if (pmd) pmd[i] = make_double4_16a(rdd[0], rdd[1], rdd[2], (double)m[i]);
+        }
+    } else if (update_pos) {
         double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
         double first[3], d[3];
@@ -1157,7 +1183,7 @@ cudaError_t launch_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     c.launches += 1;
     int pr = prof_begin(c, s, SPH_PHASE_BUCKETS);
     k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
-                                 c.origin, c.pm, c.ipos, c.pmd, c.node, 1, c.st);
+                                 c.origin, c.pm, c.ipos, c.pmd, c.node, 2, c.st);
     prof_end(c, s, pr);
     pr = prof_begin(c, s, SPH_PHASE_TREE);
     tree_refit(c, s, 0);
