@@ -553,9 +553,10 @@ __global__ void k_pad_fallback(int nb, const Inst *__restrict__ insts,
 // buckets: origin, relative positions, leaf bounds.  One warp per bucket.
 // Offsets from the bucket's first particle are formed in FP64 (minimum image
 // on periodic axes) and every reduction runs in FP32 on those offsets.
-// With update_pos = 0 only the box-of-balls is refreshed from the current h
-// (bounds update after the density pass, Sec. 2.3.3); with update_pos = 2
-// (refit without a re-sort) the origins are kept.
+// update_pos = 1: a re-sort (new origins); 2: a refit without a re-sort
+// (the origins are kept); 0: only the box of balls from the current h (the
+// bounds update after the density pass, Sec. 2.3.3, is now done by the
+// density kernel for each bucket it solves, so no launcher uses 0).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restrict__ insts,
                                                  const int *__restrict__ bstart,
@@ -1191,14 +1192,12 @@ cudaError_t launch_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// the leaves' boxes of balls were written by the density kernel (each warp
+// for its bucket, with the new h); the upper levels follow here
 cudaError_t launch_bob_refit(Ctx &c, const sph_particles &p, cudaStream_t s)
 {
-    const KParams &kp = c.kp;
-    const int wb = (kp.nb * 32 + 127) / 128;
-    c.launches += 1;
+    (void)p;
     const int pr = prof_begin(c, s, SPH_PHASE_BOB_REFIT);
-    k_buckets<<<wb, 128, 0, s>>>(kp, c.inst, c.bstart, c.binst, p.x[0], p.x[1], p.x[2], p.m, p.h,
-                                 c.origin, c.pm, c.ipos, c.pmd, c.node, 0, c.st);
     tree_refit(c, s, 1);
     prof_end(c, s, pr);
     return cudaGetLastError();

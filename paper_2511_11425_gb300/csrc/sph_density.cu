@@ -580,8 +580,8 @@ __device__ __forceinline__ void density_slot(
     float *omega_out, uint16_t *nngb_out, uint8_t *iters_out, int fixed_h, long long cap,
     uint32_t *count_out, int64_t *ids_out, const int64_t *__restrict__ id_in,
     unsigned *redo_out, unsigned *redo_cnt_out, unsigned *gflag,
-    const float4 *__restrict__ node, DevStatus *st, float4 *cand, double4_16a *candd, int *candj,
-    int A, int lane)
+    const float4 *__restrict__ node, float4 *leaf_out, DevStatus *st, float4 *cand,
+    double4_16a *candd, int *candj, int A, int lane)
 {
     const Inst &I = insts[binst[A]];
     const PBox bx = make_pbox(I);
@@ -620,6 +620,41 @@ __device__ __forceinline__ void density_slot(
                                             h_out, rho_out, omega_out, nngb_out, iters_out,
                                             fixed_h, cap, count_out, ids_out, id_in, redo_out,
                                             redo_cnt_out, gflag, st, me, valid, cen);
+    // the leaf's box of balls with the new h (the bounds update after the
+    // density pass, Sec. 2.3.3): positions relative to the bucket origin
+    // (pm) widened by h, absolute centre in FP64 (origin + offset, one
+    // rounding) with axis a in lane a, half widths inflated by the rounding
+    // allowance.  Only the cell bounds of sources are read above, so the
+    // box of balls of any leaf may change while other warps run.
+    const float hv = valid ? h_out[i] : 0.f;
+    const float pr[3] = {me.x, me.y, me.z};
+    float mnb[3], mxb[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        mnb[a] = warp_min(valid ? pr[a] - hv : INFINITY);
+        mxb[a] = warp_max(valid ? pr[a] + hv : -INFINITY);
+    }
+    const float hmax = warp_max(hv);
+    float oca = 0.f, ora = 0.f;
+    if (lane < 3) {
+        const int ax = lane;
+        const double o = (double)origin[ax * kp.nb + A] * I.q;
+        const float mna = ax == 0 ? mnb[0] : (ax == 1 ? mnb[1] : mnb[2]);
+        const float mxa = ax == 0 ? mxb[0] : (ax == 1 ? mxb[1] : mxb[2]);
+        oca = (float)(o + 0.5 * ((double)mna + (double)mxa));
+        ora = 0.5f * (mxa - mna) + I.eps_abs;
+    }
+    float oc[3], orr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        oc[a] = __shfl_sync(kFull, oca, a);
+        orr[a] = __shfl_sync(kFull, ora, a);
+    }
+    if (lane == 0) {
+        const size_t k = (size_t)I.nbase + I.P + (A - I.boff);
+        leaf_out[4 * k + 2] = make_float4(oc[0], oc[1], oc[2], 0.f);
+        leaf_out[4 * k + 3] = make_float4(orr[0], orr[1], orr[2], hmax);
+    }
 }
 
 template <class K, bool EMIT, bool D64, bool IC>
@@ -635,7 +670,7 @@ __global__ void __launch_bounds__(128, 5) k_density(
     float *h_seed, float *h_out, float *rho_out, float *omega_out, uint16_t *nngb_out,
     uint8_t *iters_out, int fixed_h, long long cap, uint32_t *count_out, int64_t *ids_out,
     const int64_t *__restrict__ id_in, unsigned *redo_out, unsigned *redo_cnt_out,
-    unsigned *gflag, const float4 *__restrict__ node, DevStatus *st)
+    unsigned *gflag, const float4 *__restrict__ node, float4 *leaf_out, DevStatus *st)
 {
     __shared__ float4 cand_s[kWarpsPerBlock][kChunk];
     __shared__ double4_16a candd_s[D64 ? kWarpsPerBlock : 1][D64 ? kChunk : 1];
@@ -651,7 +686,7 @@ __global__ void __launch_bounds__(128, 5) k_density(
             density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, RELAX ? shell_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
                                        origin, h_seed, h_out, rho_out, omega_out, nngb_out,
                                        iters_out, fixed_h, cap, count_out, ids_out, id_in,
-                                       redo_out, redo_cnt_out, gflag, node, st, cand_s[wib],
+                                       redo_out, redo_cnt_out, gflag, node, leaf_out, st, cand_s[wib],
                                        candd, EMIT ? candj_s[wib] : nullptr, A, lane);
         return;
     }
@@ -667,7 +702,7 @@ __global__ void __launch_bounds__(128, 5) k_density(
         density_slot<K, EMIT, D64, IC>(mat, ic_e, IC ? candm_s[wib] : nullptr, RELAX ? shell_s[wib] : nullptr, kp, insts, pm, pmd, bstart, binst, list_cnt, list_off, list,
                                    origin, h_seed, h_out, rho_out, omega_out, nngb_out, iters_out,
                                    fixed_h, cap, count_out, ids_out, id_in, redo_out, redo_cnt_out,
-                                   gflag, node, st, cand_s[wib], candd,
+                                   gflag, node, leaf_out, st, cand_s[wib], candd,
                                    EMIT ? candj_s[wib] : nullptr, fb + j, lane);
     }
 }
@@ -717,7 +752,7 @@ cudaError_t launch_density(Ctx &c, const sph_particles &p, const float *h_seed, 
     k_density<KT, EMIT_, D64_, IC_><<<g, 32 * kWarpsPerBlock, 0, s>>>(                            \
         p.mat, c.ic_e, kp, c.inst, c.pm, c.pmd, c.bstart, c.binst, c.gfirst, c.list_cnt, c.list_off, c.list,     \
         c.origin, gids, gcnt, (float *)h_seed, p.h, rho_out, p.omega, p.nngb, p.iters, fixed_h,   \
-        (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.st)
+        (long long)cap, count, ids, p.id, redo_out, redo_cnt_out, c.gflag, c.node, c.node, c.st)
     SPH_KERNEL_DISPATCH(kp.kernel, KT,
         if (kp.fp64) {
             if (emit) SPH_DENSITY_LAUNCH(true, true, false);
