@@ -554,10 +554,18 @@ __global__ void k_pad_fallback(int nb, const Inst *__restrict__ insts,
 // Offsets from the bucket's first particle are formed in FP64 (minimum image
 // on periodic axes) and every reduction runs in FP32 on those offsets.
 // update_pos = 1: a re-sort (new origins); 2: a refit without a re-sort
-// (the origins are kept); 0: only the box of balls from the current h (the
-// bounds update after the density pass, Sec. 2.3.3, is now done by the
-// density kernel for each bucket it solves, so no launcher uses 0).
+// (the origins are kept).  The box of balls from the h of the density pass
+// (Sec. 2.3.3) is written by the density kernel for each bucket it solves.
 // ---------------------------------------------------------------------------
+
+// round to nearest even of v inv as an int, for inv a power of two and
+// |v inv| < 2^31: v inv is exact, and adding 1.5 2^52 in the same FMA rounds
+// it to an integer held in the low word (one FP64 instruction instead of a
+// multiply and a conversion; the result equals __double2int_rn(v * inv))
+__device__ __forceinline__ int fix_rn(double v, double inv)
+{
+    return __double2loint(fma(v, inv, 6755399441055744.0));
+}
 __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restrict__ insts,
                                                  const int *__restrict__ bstart,
                                                  const int *__restrict__ binst,
@@ -580,11 +588,9 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         if (lane == 0) {
             const size_t k = (size_t)I.nbase + I.P + (b - I.boff);
             const float4 e = make_float4(0.f, 0.f, 0.f, 0.f), er = make_float4(-1.f, -1.f, -1.f, 0.f);
-            if (update_pos) {
-                for (int a = 0; a < 3; ++a) origin[a * kp.nb + b] = 0;
-                node[4 * k + 0] = e;
-                node[4 * k + 1] = er;
-            }
+            for (int a = 0; a < 3; ++a) origin[a * kp.nb + b] = 0;
+            node[4 * k + 0] = e;
+            node[4 * k + 1] = er;
             node[4 * k + 2] = e;
             node[4 * k + 3] = er;
         }
@@ -593,30 +599,33 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
     // FP64 runs at a small fraction of the FP32 rate on this part, and an
     // FP64 instruction costs the pipe about as much for one active lane as
     // for 32: each lane does only its own offset in FP64 (one subtract, one
-    // add, one rounding per axis; the minimum-image wrap only when the offset
-    // could exceed half a period), and the warp-uniform origin and bounds
-    // arithmetic of axis a runs in lane a, all three axes in one instruction.
+    // fused rounding to fixed point and one rounding to FP32 per axis; the
+    // minimum-image wrap only when the offset could exceed half a period),
+    // and the warp-uniform origin and bounds arithmetic runs one axis per
+    // lane, all axes in one instruction.
     const bool ok = lane < cnt;
     const int ax = lane < 3 ? lane : 0;  // the axis of lanes 0, 1, 2
     auto sel = [&](const auto *v3) { return ax == 0 ? v3[0] : (ax == 1 ? v3[1] : v3[2]); };
+    const double inv_qx = (double)I.inv_qx;  // a power of two
     float rel[3];
+    double o3 = 0.0;  // lanes 0, 1, 2: origin of axis `ax` (grid index times q, exact)
     if (update_pos == 2) {
         // refit (no re-sort): the bucket keeps its origin grid point, and each
         // lane's offset from it is one FP64 subtraction per axis (nearest
         // periodic image of the origin)
         double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
-        const double oa = lane < 3 ? (double)origin[ax * kp.nb + b] * I.q : 0.0;
+        if (lane < 3) o3 = (double)origin[ax * kp.nb + b] * I.q;
         int fix[3];
         double rdd[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double rd = v[a] - __shfl_sync(kFull, oa, a);
+            double rd = v[a] - __shfl_sync(kFull, o3, a);
             if (I.periodic[a] && fabsf((float)rd) > 0.49f * (float)I.Ld[a])
                 rd -= I.Ld[a] * rint(rd * I.invLd[a]);
             rdd[a] = rd;
             rel[a] = (float)rd;
-            fix[a] = __double2int_rn(rd * (double)I.inv_qx);
+            fix[a] = fix_rn(rd, inv_qx);
         }
         if (ok) {
             if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
@@ -625,7 +634,7 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
             ipos[i] = make_int4(fix[0], fix[1], fix[2], 0);
             if (pmd) pmd[i] = make_double4_16a(rdd[0], rdd[1], rdd[2], (double)m[i]);
         }
-    } else if (update_pos) {
+    } else {
         double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
         double first[3], d[3];
@@ -647,7 +656,8 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
                 kd = 0.0;
             }
             origin[ax * kp.nb + b] = (int)kd;
-            fo = fa - kd * I.q;
+            o3 = kd * I.q;
+            fo = fa - o3;
         }
         int fix[3];
         double rdd[3];
@@ -656,9 +666,9 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
             const double rd = __shfl_sync(kFull, fo, a) + d[a];
             rdd[a] = rd;
             rel[a] = (float)rd;
-            // fixed point in units of qx (saturates if the bucket is wider
-            // than the fixed-point range; the force kernel then does not use it)
-            fix[a] = __double2int_rn(rd * (double)I.inv_qx);
+            // fixed point in units of qx (garbage if the bucket is wider than
+            // the fixed-point range; the force kernel then does not use it)
+            fix[a] = fix_rn(rd, inv_qx);
         }
         if (ok) {
             if (!(isfinite(rel[0]) && isfinite(rel[1]) && isfinite(rel[2])))
@@ -667,9 +677,6 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
             ipos[i] = make_int4(fix[0], fix[1], fix[2], 0);
             if (pmd) pmd[i] = make_double4_16a(rdd[0], rdd[1], rdd[2], (double)m[i]);
         }
-    } else {
-        float4 r = ok ? pm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        rel[0] = r.x; rel[1] = r.y; rel[2] = r.z;
     }
     const float hi = ok ? h[i] : 0.f;
     if (ok && !(hi > 0.f && isfinite(hi))) raise_status(st, ST_NONFINITE, i);
@@ -683,32 +690,32 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
     }
     const float hmax = warp_max(hi);
     // absolute centres (FP64 add of the origin, then one rounding) and half
-    // widths inflated by the rounding allowance, axis `ax` in lane ax
-    float bca = 0.f, bra = 0.f, oca = 0.f, ora = 0.f;
-    if (lane < 3) {
-        const double o = (double)origin[ax * kp.nb + b] * I.q;
-        const float mna = sel(mn), mxa = sel(mx), mnba = sel(mnb), mxba = sel(mxb);
-        bca = (float)(o + 0.5 * ((double)mna + (double)mxa));
-        bra = 0.5f * (mxa - mna) + I.eps_abs;
-        oca = (float)(o + 0.5 * ((double)mnba + (double)mxba));
-        ora = 0.5f * (mxba - mnba) + I.eps_abs;
+    // widths inflated by the rounding allowance: the bucket box of axis a in
+    // lane a, the box of balls of axis a in lane 3 + a
+    const int a6 = lane < 3 ? lane : (lane < 6 ? lane - 3 : 0);
+    const double o6 = __shfl_sync(kFull, o3, a6);
+    float cen = 0.f, hw = 0.f;
+    if (lane < 6) {
+        auto sel6 = [&](const float *v3) { return a6 == 0 ? v3[0] : (a6 == 1 ? v3[1] : v3[2]); };
+        const bool ball = lane >= 3;
+        const float lo = ball ? sel6(mnb) : sel6(mn), up = ball ? sel6(mxb) : sel6(mx);
+        cen = (float)(o6 + 0.5 * ((double)lo + (double)up));
+        hw = 0.5f * (up - lo) + I.eps_abs;
     }
     float bc[3], br[3], oc[3], orr[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        bc[a] = __shfl_sync(kFull, bca, a);
-        br[a] = __shfl_sync(kFull, bra, a);
-        oc[a] = __shfl_sync(kFull, oca, a);
-        orr[a] = __shfl_sync(kFull, ora, a);
+        bc[a] = __shfl_sync(kFull, cen, a);
+        br[a] = __shfl_sync(kFull, hw, a);
+        oc[a] = __shfl_sync(kFull, cen, 3 + a);
+        orr[a] = __shfl_sync(kFull, hw, 3 + a);
     }
     if (lane == 0) {
         const size_t k = (size_t)I.nbase + I.P + (b - I.boff);
-        if (update_pos) {
-            // .w of the cell half widths: the bucket's largest full extent
-            float ext = 2.f * fmaxf(br[0], fmaxf(br[1], br[2]));
-            node[4 * k + 0] = make_float4(bc[0], bc[1], bc[2], 0.f);
-            node[4 * k + 1] = make_float4(br[0], br[1], br[2], ext);
-        }
+        // .w of the cell half widths: the bucket's largest full extent
+        float ext = 2.f * fmaxf(br[0], fmaxf(br[1], br[2]));
+        node[4 * k + 0] = make_float4(bc[0], bc[1], bc[2], 0.f);
+        node[4 * k + 1] = make_float4(br[0], br[1], br[2], ext);
         node[4 * k + 2] = make_float4(oc[0], oc[1], oc[2], 0.f);
         node[4 * k + 3] = make_float4(orr[0], orr[1], orr[2], hmax);
     }
