@@ -47,7 +47,8 @@ def _stale(lib, deps) -> bool:
 
 
 def _lib_deps():
-    return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+    return sources() + headers + [
         os.path.join(ROOT, "include", "sph.h")]
 
 

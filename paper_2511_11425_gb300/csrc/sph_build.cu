@@ -11,6 +11,7 @@
 // instance has an implicit complete binary tree over its bucket slots.  Every
 // phase is one launch over all instances.
 #include "sph_internal.cuh"
+#include "sph_bits.h"
 
 namespace sph {
 
@@ -598,15 +599,16 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
     }
     // FP64 runs at a small fraction of the FP32 rate on this part, and an
     // FP64 instruction costs the pipe about as much for one active lane as
-    // for 32: each lane does only its own offset in FP64 (one subtract, one
-    // fused rounding to fixed point and one rounding to FP32 per axis; the
-    // minimum-image wrap only when the offset could exceed half a period),
-    // and the warp-uniform origin and bounds arithmetic runs one axis per
-    // lane, all axes in one instruction.
+    // for 32: each lane does only its own offset in FP64 (one subtract and
+    // one fused rounding to fixed point per axis; the minimum-image wrap
+    // only when the offset could exceed half a period), the warp-uniform
+    // origin and bounds arithmetic runs one axis per lane, all axes in one
+    // instruction, and the conversions between the formats run on the
+    // integer pipes (sph_bits.h, the same values as the hardware's).
     const bool ok = lane < cnt;
     const int ax = lane < 3 ? lane : 0;  // the axis of lanes 0, 1, 2
     auto sel = [&](const auto *v3) { return ax == 0 ? v3[0] : (ax == 1 ? v3[1] : v3[2]); };
-    const double inv_qx = (double)I.inv_qx;  // a power of two
+    const double inv_qx = bits::f2d(I.inv_qx);  // a power of two
     float rel[3];
     double o3 = 0.0;  // lanes 0, 1, 2: origin of axis `ax` (grid index times q, exact)
     if (update_pos == 2) {
@@ -615,16 +617,19 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         // periodic image of the origin)
         double v[3] = {0.0, 0.0, 0.0};
         if (ok) { v[0] = x[i]; v[1] = y[i]; v[2] = z[i]; }
-        if (lane < 3) o3 = (double)origin[ax * kp.nb + b] * I.q;
+        if (lane < 3) o3 = bits::i2d_pow2(origin[ax * kp.nb + b], I.q);
         int fix[3];
         double rdd[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double rd = v[a] - __shfl_sync(kFull, o3, a);
-            if (I.periodic[a] && fabsf((float)rd) > 0.49f * (float)I.Ld[a])
+            float rf = bits::d2f(rd);
+            if (I.periodic[a] && fabsf(rf) > 0.49f * I.L[a]) {
                 rd -= I.Ld[a] * rint(rd * I.invLd[a]);
+                rf = bits::d2f(rd);
+            }
             rdd[a] = rd;
-            rel[a] = (float)rd;
+            rel[a] = rf;
             fix[a] = fix_rn(rd, inv_qx);
         }
         if (ok) {
@@ -643,14 +648,17 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         for (int a = 0; a < 3; ++a) {
             first[a] = __shfl_sync(kFull, v[a], 0);
             d[a] = v[a] - first[a];
-            if (I.periodic[a] && fabsf((float)d[a]) > 0.49f * (float)I.Ld[a])
+            float df = bits::d2f(d[a]);
+            if (I.periodic[a] && fabsf(df) > 0.49f * I.L[a]) {
                 d[a] -= I.Ld[a] * rint(d[a] * I.invLd[a]);
-            mnd[a] = warp_min(ok ? (float)d[a] : INFINITY);
+                df = bits::d2f(d[a]);
+            }
+            mnd[a] = warp_min(ok ? df : INFINITY);
         }
         double fo = 0.0;  // first - origin of axis `ax` (lanes 0, 1, 2)
         if (lane < 3) {
             const double fa = sel(first);
-            double kd = floor((fa + (double)sel(mnd)) * I.inv_q);
+            double kd = floor((fa + bits::f2d(sel(mnd))) * I.inv_q);
             if (!(fabs(kd) < 1073741824.0)) {  // the grid index must fit an int
                 raise_status(st, ST_ARG, b);
                 kd = 0.0;
@@ -665,7 +673,7 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         for (int a = 0; a < 3; ++a) {
             const double rd = __shfl_sync(kFull, fo, a) + d[a];
             rdd[a] = rd;
-            rel[a] = (float)rd;
+            rel[a] = bits::d2f(rd);
             // fixed point in units of qx (garbage if the bucket is wider than
             // the fixed-point range; the force kernel then does not use it)
             fix[a] = fix_rn(rd, inv_qx);
@@ -699,7 +707,7 @@ __global__ void __launch_bounds__(128) k_buckets(KParams kp, const Inst *__restr
         auto sel6 = [&](const float *v3) { return a6 == 0 ? v3[0] : (a6 == 1 ? v3[1] : v3[2]); };
         const bool ball = lane >= 3;
         const float lo = ball ? sel6(mnb) : sel6(mn), up = ball ? sel6(mxb) : sel6(mx);
-        cen = (float)(o6 + 0.5 * ((double)lo + (double)up));
+        cen = bits::d2f(o6 + 0.5 * (bits::f2d(lo) + bits::f2d(up)));
         hw = 0.5f * (up - lo) + I.eps_abs;
     }
     float bc[3], br[3], oc[3], orr[3];
