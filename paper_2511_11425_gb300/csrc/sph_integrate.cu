@@ -9,6 +9,7 @@
 // along its adiabat after the density pass (entropy-conserving form).
 // Everything here is FP64 per particle and memory-bound.
 #include "sph_internal.cuh"
+#include "sph_bits.h"
 
 namespace sph {
 
@@ -56,11 +57,13 @@ __device__ __forceinline__ void kdk_particle(
     const Inst &I = insts[k];
     const double dt_old = dts[2 * k], dt_new = dts[2 * k + 1];
     const double kick = 0.5 * (dt_old + dt_new);
-    double ud = (double)dudt_av[i];
-    if (energy_mode == SPH_ENERGY_PDV) ud += (double)dudt_h[i];
-    const double v0 = vx[i] + kick * (double)ax[i];
-    const double v1 = vy[i] + kick * (double)ay[i];
-    const double v2 = vz[i] + kick * (double)az[i];
+    // FP32 -> FP64 on the integer pipes (exact; the FP64 pipe runs at 1/64
+    // of the FP32 rate and carries the kick and drift themselves)
+    double ud = bits::f2d(dudt_av[i]);
+    if (energy_mode == SPH_ENERGY_PDV) ud += bits::f2d(dudt_h[i]);
+    const double v0 = vx[i] + kick * bits::f2d(ax[i]);
+    const double v1 = vy[i] + kick * bits::f2d(ay[i]);
+    const double v2 = vz[i] + kick * bits::f2d(az[i]);
     vx[i] = v0;
     vy[i] = v1;
     vz[i] = v2;
@@ -111,7 +114,7 @@ __global__ void k_kdk(KParams kp, int n, const Inst *__restrict__ insts,
     if (st->code != 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float e = (float)dts[2 * pinst[i] + 1] * divv[i] * (1.f / 3.f);
+    float e = bits::d2f(dts[2 * pinst[i] + 1]) * divv[i] * (1.f / 3.f);
     if (CORR) e += corr[i];
     const float f = expf(e);
     kdk_particle(i, insts, pinst, x, y, z, vx, vy, vz, u, h, ax, ay, az, dudt_h, dudt_av,
@@ -261,11 +264,11 @@ __global__ void k_kdk_rungs(KParams kp, int n, const Inst *__restrict__ insts,
         kick += 0.5 * (double)(1 << (ra.R - r_new)) * ra.delta;
     }
     const Inst &I = insts[pinst[i]];
-    double ud = (double)dudt_av[i];
-    if (kp.energy_mode == SPH_ENERGY_PDV) ud += (double)dudt_h[i];
-    const double v0 = vx[i] + kick * (double)ax[i];
-    const double v1 = vy[i] + kick * (double)ay[i];
-    const double v2 = vz[i] + kick * (double)az[i];
+    double ud = bits::f2d(dudt_av[i]);
+    if (kp.energy_mode == SPH_ENERGY_PDV) ud += bits::f2d(dudt_h[i]);
+    const double v0 = vx[i] + kick * bits::f2d(ax[i]);
+    const double v1 = vy[i] + kick * bits::f2d(ay[i]);
+    const double v2 = vz[i] + kick * bits::f2d(az[i]);
     vx[i] = v0;
     vy[i] = v1;
     vz[i] = v2;
